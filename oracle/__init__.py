@@ -1,0 +1,311 @@
+"""CPU oracle for the trading environments and ensemble rules -- TEST INFRASTRUCTURE.
+
+This package wraps ``finrl_oracle.c``: a plain, slow fp64 / int64 restatement
+of the paper's MDP (Sec. 3.1), its reset/step/reward operations (Sec. 4.2.2),
+the two ensemble rules (Sec. 5.2.1 weighted average, Sec. 5.2.2 majority vote)
+and the episode metrics (Sharpe equation of Sec. 5.2.1, Sec. 6.1 metric list).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it.  It shares no code with the CUDA library, and the
+CUDA library never imports it.
+
+The shared library is compiled on first use with gcc (``-O2 -fopenmp
+-ffp-contract=off``) into ``oracle/_build/``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import hashlib
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "finrl_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_lock = threading.Lock()
+_lib = None
+
+STOCK_ANNUALISATION = 252.0
+CRYPTO_ANNUALISATION = 1.0
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (idempotent); returns its path."""
+    with open(_SRC, "rb") as f:
+        tag = hashlib.sha1(f.read()).hexdigest()[:12]
+    os.makedirs(_BUILD, exist_ok=True)
+    out = os.path.join(_BUILD, f"libfinrl_oracle_{tag}.so")
+    if force or not os.path.exists(out):
+        tmp = out + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-fopenmp",
+               "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, out)
+    return out
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = C.CDLL(build())
+        i32, i64, f64 = C.c_int32, C.c_int64, C.c_double
+        vp = C.c_void_p
+        lib.orc_perturb.argtypes = [i64, i32]
+        lib.orc_perturb.restype = i64
+        lib.orc_fee.argtypes = [i64, i32]
+        lib.orc_fee.restype = i64
+        lib.orc_buy_cost.argtypes = [i64, i64, i32]
+        lib.orc_buy_cost.restype = i64
+        lib.orc_buy_max.argtypes = [i64, i64, i32]
+        lib.orc_buy_max.restype = i64
+        lib.orc_discretise.argtypes = [f64, i32]
+        lib.orc_discretise.restype = i32
+        lib.orc_discretise_many.argtypes = [vp, i64, i32, vp]
+        lib.orc_buy_max_many.argtypes = [vp, vp, vp, i64, vp]
+        lib.orc_perturb_many.argtypes = [vp, vp, i64, vp]
+        lib.orc_net_param_count.argtypes = [i32, vp]
+        lib.orc_net_param_count.restype = i64
+        lib.orc_net_forward.argtypes = [i32, vp, vp, i32, vp, i32, i32, vp, i32]
+        lib.orc_ensemble_mean.argtypes = [i32, i32, vp, vp, vp]
+        lib.orc_argmax.argtypes = [vp, i32]
+        lib.orc_argmax.restype = i32
+        lib.orc_vote.argtypes = [i32, vp]
+        lib.orc_vote.restype = i32
+        lib.orc_metrics_series.argtypes = [i32, vp, f64, vp]
+        lib.orc_stock_run.argtypes = [i32, i32, i32, vp, vp,
+                                      i32, vp, vp, vp, vp,
+                                      i64, i32, i32, i32, i32, i32,
+                                      vp, vp, i32, i32, vp, vp, vp,
+                                      vp, vp, vp, vp, vp, vp, vp, vp, vp, i32]
+        lib.orc_stock_run.restype = i32
+        lib.orc_crypto_run.argtypes = [i32, vp, vp, vp, i32, vp, vp, i64, i32,
+                                       i32, i32, i32, vp, i32, i32, vp, vp,
+                                       vp, vp, vp, vp, vp, vp, vp, vp, vp, i32]
+        lib.orc_crypto_run.restype = i32
+        lib.orc_max_threads.restype = i32
+        _lib = lib
+        return lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _c(a, dt):
+    return None if a is None else np.ascontiguousarray(a, dtype=dt)
+
+
+def max_threads() -> int:
+    return int(_load().orc_max_threads())
+
+
+# ------------------------------------------------------------ scalar rules
+
+def perturb(close: int, bps: int) -> int:
+    return int(_load().orc_perturb(int(close), int(bps)))
+
+
+def fee(notional: int, fee_bps: int) -> int:
+    return int(_load().orc_fee(int(notional), int(fee_bps)))
+
+
+def buy_cost(n: int, p: int, fee_bps: int) -> int:
+    return int(_load().orc_buy_cost(int(n), int(p), int(fee_bps)))
+
+
+def buy_max(cash: int, p: int, fee_bps: int) -> int:
+    return int(_load().orc_buy_max(int(cash), int(p), int(fee_bps)))
+
+
+def discretise(a: float, hmax: int) -> int:
+    return int(_load().orc_discretise(float(a), int(hmax)))
+
+
+def discretise_many(a: np.ndarray, hmax: int) -> np.ndarray:
+    a = _c(a, np.float32).ravel()
+    out = np.empty(a.size, np.int32)
+    _load().orc_discretise_many(_p(a), a.size, int(hmax), _p(out))
+    return out
+
+
+def buy_max_many(cash, p, fee_bps) -> np.ndarray:
+    cash = _c(cash, np.int64).ravel()
+    p = _c(np.broadcast_to(p, cash.shape), np.int64)
+    f = _c(np.broadcast_to(fee_bps, cash.shape), np.int32)
+    out = np.empty(cash.size, np.int64)
+    _load().orc_buy_max_many(_p(cash), _p(p), _p(f), cash.size, _p(out))
+    return out
+
+
+def perturb_many(close, bps) -> np.ndarray:
+    close = _c(close, np.int64)
+    b = _c(np.broadcast_to(bps, close.shape), np.int32)
+    out = np.empty(close.shape, np.int64)
+    _load().orc_perturb_many(_p(close), _p(b), close.size, _p(out))
+    return out
+
+
+# ------------------------------------------------------------------ networks
+
+def net_param_count(dims) -> int:
+    d = _c(dims, np.int32)
+    return int(_load().orc_net_param_count(len(d) - 1, _p(d)))
+
+
+def net_forward(dims, params: np.ndarray, x: np.ndarray, out_act: int,
+                nthreads: int = 0) -> np.ndarray:
+    """fp64 forward of one actor.  params: packed fp32 (W_l[out][in], b_l)."""
+    d = _c(dims, np.int32)
+    params = _c(params, np.float32)
+    x = _c(x, np.float32)
+    n, ldx = x.shape
+    y = np.empty((n, int(d[-1])), np.float64)
+    _load().orc_net_forward(len(d) - 1, _p(d), _p(params), int(out_act), _p(x),
+                            ldx, n, _p(y), nthreads or max_threads())
+    return y
+
+
+def ensemble_mean(a: np.ndarray, w=None) -> np.ndarray:
+    """a[M][K] fp64 -> anchored weighted mean [K]."""
+    a = _c(a, np.float64)
+    M, K = a.shape
+    w = _c(w, np.float64)
+    out = np.empty(K, np.float64)
+    _load().orc_ensemble_mean(M, K, _p(a), _p(w), _p(out))
+    return out
+
+
+def argmax(q) -> int:
+    q = _c(q, np.float64)
+    return int(_load().orc_argmax(_p(q), q.size))
+
+
+def vote(ballots) -> int:
+    b = _c(ballots, np.uint8)
+    return int(_load().orc_vote(b.size, _p(b)))
+
+
+def metrics_series(v, ann: float) -> np.ndarray:
+    v = _c(v, np.int64)
+    out = np.empty(3, np.float64)
+    _load().orc_metrics_series(v.size, _p(v), float(ann), _p(out))
+    return out
+
+
+# ------------------------------------------------------------------ rollouts
+
+def stock_run(market, Ke, start, W, bps, *, init_cash: int, hmax: int,
+              fee_bps: int, T: int, auto_reset: bool = False,
+              act_i32=None, act_f32=None, ensemble=None, nthreads: int = 0,
+              want=("obs", "q", "rew", "rew_f32", "done", "cash", "hold",
+                    "metrics", "act")) -> dict:
+    """Run T steps of N stock envs from reset.
+
+    market: object with ``close`` int64[n_days][K] and ``ind`` f32[n_days][I][K].
+    Exactly one action source: act_i32[T][N][K] (mode 0), act_f32[T][N][K]
+    (mode 1) or ensemble = (dims, params[M][P] f32, weights or None) (mode 2).
+    """
+    close = _c(market.close, np.int64)
+    ind = _c(market.ind, np.float32)
+    n_days, K = close.shape
+    I = ind.shape[1]
+    D = 1 + 2 * K + I * K
+    Ke = _c(Ke, np.int32)
+    N = Ke.size
+    start = _c(start, np.int32)
+    W = _c(W, np.int32)
+    bps = _c(bps, np.int16)
+    mode, M, L = 0, 0, 0
+    dims = params = wts = None
+    ai = af = None
+    if act_i32 is not None:
+        ai = _c(act_i32, np.int32)
+    elif act_f32 is not None:
+        mode, af = 1, _c(act_f32, np.float32)
+    else:
+        mode = 2
+        dims_, params_, w_ = ensemble
+        dims = _c(dims_, np.int32)
+        params = _c(params_, np.float32)
+        M, L = params.shape[0], dims.size - 1
+        wts = _c(w_, np.float64)
+    o = {}
+
+    def mk(name, shape, dt):
+        if name in want:
+            o[name] = np.zeros(shape, dt)
+        return o.get(name)
+
+    obs = mk("obs", (T, N, D), np.float32)
+    act = mk("act", (T, N, K), np.float64) if mode == 2 else None
+    q = mk("q", (T, N, K), np.int32)
+    rew = mk("rew", (T, N), np.int64)
+    rf = mk("rew_f32", (T, N), np.float32)
+    dn = mk("done", (T, N), np.uint8)
+    cash = mk("cash", (T, N), np.int64)
+    hold = mk("hold", (T, N, K), np.int32)
+    met = mk("metrics", (N, 3), np.float64)
+    rc = _load().orc_stock_run(
+        n_days, K, I, _p(close), _p(ind), N, _p(Ke), _p(start), _p(W), _p(bps),
+        int(init_cash), int(hmax), int(fee_bps), int(bool(auto_reset)), int(T),
+        mode, _p(ai), _p(af), M, L, _p(dims), _p(params), _p(wts),
+        _p(obs), _p(act), _p(q), _p(rew), _p(rf), _p(dn), _p(cash), _p(hold),
+        _p(met), nthreads or max_threads())
+    if rc != 0:
+        raise ValueError(f"oracle stock_run rejected its inputs (code {rc})")
+    return o
+
+
+def crypto_run(market, start, W, *, init_cash: int, pmax: int, T: int,
+               auto_reset: bool = False, act_u8=None, ensemble=None,
+               nthreads: int = 0,
+               want=("obs", "act", "agent_act", "rew", "rew_f32", "done",
+                     "cash", "pos", "metrics")) -> dict:
+    """Run T steps of N crypto envs from reset (mode 0: act_u8[T][N];
+    mode 2: ensemble = (dims, params[M][P]))."""
+    mid = _c(market.mid, np.int64)
+    spread = _c(market.spread, np.uint8)
+    fac = _c(market.fac, np.float32)
+    S = mid.size
+    start = _c(start, np.int32)
+    W = _c(W, np.int32)
+    N = start.size
+    mode, M, L = 0, 0, 0
+    dims = params = au = None
+    if act_u8 is not None:
+        au = _c(act_u8, np.uint8)
+    else:
+        mode = 2
+        dims_, params_ = ensemble[:2]
+        dims = _c(dims_, np.int32)
+        params = _c(params_, np.float32)
+        M, L = params.shape[0], dims.size - 1
+    o = {}
+
+    def mk(name, shape, dt):
+        if name in want:
+            o[name] = np.zeros(shape, dt)
+        return o.get(name)
+
+    obs = mk("obs", (T, N, 10), np.float32)
+    act = mk("act", (T, N), np.uint8)
+    agent = mk("agent_act", (T, N, max(M, 1)), np.uint8) if mode == 2 else None
+    rew = mk("rew", (T, N), np.int64)
+    rf = mk("rew_f32", (T, N), np.float32)
+    dn = mk("done", (T, N), np.uint8)
+    cash = mk("cash", (T, N), np.int64)
+    pos = mk("pos", (T, N), np.int32)
+    met = mk("metrics", (N, 3), np.float64)
+    rc = _load().orc_crypto_run(
+        S, _p(mid), _p(spread), _p(fac), N, _p(start), _p(W), int(init_cash),
+        int(pmax), int(bool(auto_reset)), int(T), mode, _p(au), M, L, _p(dims),
+        _p(params), _p(obs), _p(act), _p(agent), _p(rew), _p(rf), _p(dn),
+        _p(cash), _p(pos), _p(met), nthreads or max_threads())
+    if rc != 0:
+        raise ValueError(f"oracle crypto_run rejected its inputs (code {rc})")
+    return o

@@ -1,0 +1,234 @@
+"""Pins for the CPU oracle: each test checks it against something other than
+itself -- exact rational arithmetic, linear search, torch float64, the
+Condorcet binomial sum (Sec. 3.3.1), hand-computed metric series.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_10709_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------- prices/fees
+
+def test_perturb_matches_exact_rational_rounding():
+    # Sec. 5.1: a -1%..+1% change applied to each asset's price; read as an
+    # integer basis-point change rounded half up to the cent, floor 1 cent.
+    st = synth.Stream(7, 900)
+    close = np.concatenate([np.arange(1, 400), st.integers(1, 10**7, 4000)])
+    for bps in (-100, -99, -51, -50, -1, 0, 1, 37, 50, 99, 100):
+        got = oracle.perturb_many(close, np.full(close.shape, bps))
+        for c, g in zip(close.tolist(), got.tolist()):
+            x = Fraction(c) * Fraction(10000 + bps, 10000)
+            want = max(1, math.floor(x + Fraction(1, 2)))
+            assert g == want, (c, bps, g, want)
+
+
+def test_fee_is_ceiling_of_exact_rational():
+    for g in list(range(0, 3000)) + [10**9 + 7, 123456789012]:
+        for f in (0, 1, 10, 25, 250):
+            assert oracle.fee(g, f) == math.ceil(Fraction(g * f, 10000))
+
+
+def _cost_exact(n, p, f):
+    g = n * p
+    return g + math.ceil(Fraction(g * f, 10000))
+
+
+def test_buy_max_equals_linear_search():
+    # the affordable share count must be the largest n whose cost (price plus
+    # rounded-up fee) fits in the cash, found here by plain search
+    st = synth.Stream(11, 901)
+    cases = []
+    for p in (1, 2, 3, 7, 99, 100, 101, 2500, 39999):
+        for f in (0, 1, 10, 250):
+            cash = np.concatenate([np.arange(0, 60), st.integers(0, 300 * p, 40)])
+            for c in cash.tolist():
+                cases.append((c, p, f))
+    cash = np.array([c for c, _, _ in cases])
+    pp = np.array([p for _, p, _ in cases])
+    ff = np.array([f for _, _, f in cases])
+    got = oracle.buy_max_many(cash, pp, ff)
+    for (c, p, f), g in zip(cases, got.tolist()):
+        n = 0
+        while _cost_exact(n + 1, p, f) <= c:
+            n += 1
+        assert g == n, (c, p, f, g, n)
+
+
+# -------------------------------------------------------------- discretise
+
+def _trunc_exact(x: np.ndarray, hmax: int) -> np.ndarray:
+    """trunc(x * hmax) computed exactly from the float's integer mantissa and
+    exponent (x = m * 2^e), with no floating-point rounding at all."""
+    x64 = x.astype(np.float64)
+    mant, ex = np.frexp(x64)                    # x = mant * 2^ex, 0.5 <= |mant| < 1
+    m = np.rint(mant * 2.0 ** 24).astype(np.int64)   # exact: float32 has 24 bits
+    e = ex.astype(np.int64) - 24
+    y = np.abs(m) * hmax
+    sh = -e
+    out = np.where(sh >= 0, y >> np.clip(sh, 0, 63), y << np.clip(-sh, 0, 63))
+    out = np.where(sh > 62, 0, out)
+    return (np.sign(m) * out).astype(np.int64)
+
+
+def test_discretise_exhaustive_near_every_share_boundary():
+    # every float32 within 2^12 ulps of each k/100 boundary (and of 0), plus a
+    # large random sample: trunc(clip(a, -1, 1) * 100) must match exact
+    # integer arithmetic
+    parts = []
+    span = np.arange(-4096, 4097, dtype=np.int64)
+    for k in range(-100, 101):
+        c = np.float32(k / 100.0)
+        bits = np.array([c], np.float32).view(np.int32).astype(np.int64)[0]
+        if c == 0:
+            cand = np.arange(0, 8192, dtype=np.int32).view(np.float32)
+            parts += [cand, -cand]
+            continue
+        parts.append((bits + span).astype(np.int32).view(np.float32))
+    st = synth.Stream(5, 902)
+    parts.append((st.uniform(500_000) * 2 - 1).astype(np.float32))
+    x = np.concatenate(parts)
+    x = x[np.isfinite(x) & (np.abs(x) <= 1.0)]
+    for hmax in (100, 7, 1):
+        got = oracle.discretise_many(x, hmax)
+        want = _trunc_exact(x, hmax)
+        bad = np.nonzero(got != want)[0]
+        assert bad.size == 0, (hmax, x[bad[:5]], got[bad[:5]], want[bad[:5]])
+
+
+def test_discretise_clips_and_zeroes_non_finite():
+    f = np.float32
+    vals = [f(1.0), f(1.0000001), f(7.5), f(-3.0), f(np.inf), f(-np.inf),
+            f(np.nan), f(-0.0), f(0.999999)]
+    got = oracle.discretise_many(np.array(vals, np.float32), 100).tolist()
+    assert got == [100, 100, 100, -100, 0, 0, 0, 0, 99]
+
+
+# ------------------------------------------------------------------ networks
+
+@pytest.mark.parametrize("dims,out_act", [((301, 64, 64, 30), 1),
+                                          ((10, 128, 128, 3), 0),
+                                          ((17, 5, 9), 1), ((3, 1), 0)])
+def test_net_forward_matches_torch_float64(dims, out_act):
+    torch = pytest.importorskip("torch")
+    params = synth.actor_params(dims, 1, seed=3, out_scale=2.0)[0]
+    st = synth.Stream(9, 903)
+    x = (st.normal(40 * dims[0]) * 0.7).reshape(40, dims[0]).astype(np.float32)
+    got = oracle.net_forward(dims, params, x, out_act)
+    h = torch.from_numpy(x.astype(np.float64))
+    layers = synth.unpack_params(dims, params)
+    for l, (W, b) in enumerate(layers):
+        h = h @ torch.from_numpy(W.astype(np.float64)).T + torch.from_numpy(b.astype(np.float64))
+        if l + 1 < len(layers):
+            h = torch.relu(h)
+        elif out_act == 1:
+            h = torch.tanh(h)
+    want = h.numpy()
+    err = np.abs(got - want).max() / max(np.abs(want).max(), 1e-30)
+    assert err <= 1e-12, err
+
+
+# ------------------------------------------------------------------ ensembles
+
+def test_ensemble_mean_identical_agents_is_one_agent():
+    st = synth.Stream(1, 904)
+    a0 = st.uniform(30) * 2 - 1
+    for M in (1, 2, 3, 5, 7):
+        a = np.tile(a0, (M, 1))
+        out = oracle.ensemble_mean(a)
+        assert np.array_equal(out, a0)            # bit-exact, not approximate
+        w = st.uniform(M)
+        out = oracle.ensemble_mean(a, w / w.sum())
+        assert np.array_equal(out, a0)
+
+
+def test_ensemble_mean_is_weighted_average():
+    st = synth.Stream(2, 905)
+    for M in (1, 2, 3, 4):
+        a = st.uniform(M * 30).reshape(M, 30) * 2 - 1
+        w = st.uniform(M)
+        w = w / w.sum()
+        want = (w[:, None] * a).sum(0)
+        assert np.allclose(oracle.ensemble_mean(a, w), want, rtol=0, atol=1e-14)
+        assert np.allclose(oracle.ensemble_mean(a), a.mean(0), rtol=0, atol=1e-14)
+
+
+def test_argmax_ties_go_to_lowest_index():
+    assert oracle.argmax([1.0, 1.0, 0.5]) == 0
+    assert oracle.argmax([0.0, 2.0, 2.0]) == 1
+    assert oracle.argmax([-1.0, -2.0, -0.5]) == 2
+
+
+def test_vote_exhaustive_invariants():
+    # all 3^n ballots for n <= 5: a strict plurality wins, any tie for the
+    # top count holds (1), and the rule ignores the order of the ballots
+    import itertools
+    for n in range(1, 6):
+        for b in itertools.product(range(3), repeat=n):
+            r = oracle.vote(b)
+            cnt = [b.count(a) for a in range(3)]
+            top = max(cnt)
+            winners = [a for a in range(3) if cnt[a] == top]
+            if len(winners) == 1:
+                assert r == winners[0], (b, r)
+            else:
+                assert r == 1, (b, r)
+            if 2 * cnt[r] > n:
+                assert True
+            for a in range(3):
+                if 2 * cnt[a] > n:
+                    assert r == a
+            assert oracle.vote(tuple(reversed(b))) == r
+
+
+@pytest.mark.parametrize("n,p", [(3, 0.6), (5, 0.6), (7, 0.55), (9, 0.7), (4, 0.65)])
+def test_vote_accuracy_matches_condorcet_binomial(n, p):
+    # Sec. 3.3.1: n independent traders each right with probability p; the
+    # majority is right with probability sum_{k > n/2} C(n,k) p^k (1-p)^(n-k).
+    # Binary ballots (right = buy, wrong = sell); an even split holds.
+    trials = 6000
+    st = synth.Stream(13, 906 + n)
+    right = st.uniform(trials * n).reshape(trials, n) < p
+    ballots = np.where(right, 2, 0).astype(np.uint8)
+    hits = sum(oracle.vote(row) == 2 for row in ballots)
+    exact = sum(math.comb(n, k) * p ** k * (1 - p) ** (n - k)
+                for k in range(n // 2 + 1, n + 1))
+    sigma = math.sqrt(exact * (1 - exact) / trials)
+    assert abs(hits / trials - exact) <= 4 * sigma, (hits / trials, exact)
+
+
+# -------------------------------------------------------------------- metrics
+
+def test_metrics_hand_computed_series():
+    with open(os.path.join(GOLDEN, "metrics_series.json")) as f:
+        cases = json.load(f)["cases"]
+    for c in cases:
+        got = oracle.metrics_series(c["v"], c["A"])
+        cr = Fraction(*c["cumret_fraction"])
+        mdd = Fraction(*c["mdd_fraction"])
+        assert abs(got[0] - float(cr)) <= 2e-16 * max(1.0, abs(float(cr))), (c, got)
+        assert abs(got[2] - float(mdd)) <= 2e-16, (c, got)
+        if "sharpe" in c:
+            assert got[1] == c["sharpe"]
+        if "sample_var" in c:
+            want = c["mean"] / math.sqrt(c["sample_var"]) * math.sqrt(c["A"])
+            assert abs(got[1] - want) <= 4 * 2.2e-16 * abs(want), (got[1], want)
+
+
+def test_metrics_random_series_against_numpy():
+    st = synth.Stream(21, 907)
+    v = (1e6 * np.exp(np.cumsum(st.normal(300) * 0.01))).astype(np.int64)
+    got = oracle.metrics_series(v, 252.0)
+    r = v[1:] / v[:-1] - 1.0
+    assert abs(got[1] - r.mean() / r.std(ddof=1) * np.sqrt(252.0)) < 1e-9
+    peak = np.maximum.accumulate(v)
+    assert abs(got[2] - (v / peak - 1.0).min()) < 1e-15
+    assert abs(got[0] - (v[-1] / v[0] - 1.0)) < 1e-15
