@@ -1,0 +1,331 @@
+"""Benchmark: ensemble env-steps/s for 2,048 stock envs x 256 steps with
+3 x (301-256-256-30) actors, BF16 tensor-core path vs the plain FP32 path.
+
+One "step" of this benchmark is one whole rollout: reset 2,048 envs, run 256
+observe -> ensemble -> trade steps, write the FP64 episode metrics.  Inputs
+(market tables, env state, weights) are resident in HBM before timing starts.
+L2 is flushed (a 512 MB write) between timed rollouts, outside the timed
+events.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ensemble env-steps/s at 2048 stock envs vs plain path; p50/p99 request latency"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def _peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return dict(FALLBACK_PEAKS), "fallback"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    return rank, world
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_workload():
+    from paper_2501_10709_gb300 import synth
+    return synth.workload_stock_2048()
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_baseline(w, target_s: float = 12.0):
+    """Time the oracle (as it stands) on a bounded sample of the same workload:
+    the first n envs for all 256 steps, n sized for ~target_s seconds."""
+    import oracle
+    e = w.envs
+    threads = oracle.max_threads()
+
+    def run(n, T):
+        t0 = time.perf_counter()
+        oracle.stock_run(w.market, e.Ke[:n], e.start[:n], e.W[:n], e.bps[:n], init_cash=e.init_cash,
+                         hmax=100, fee_bps=10, T=T, ensemble=(w.dims, w.params, None),
+                         nthreads=threads, want=("metrics",))
+        return time.perf_counter() - t0
+
+    cal_n = max(threads, 8)
+    dt = run(cal_n, 8)
+    per_env_step = dt / (cal_n * 8)
+    n = int(max(threads, min(e.N, target_s / (per_env_step * w.T))))
+    n = max(threads, (n // threads) * threads)
+    dt = run(n, w.T)
+    return {"value": n * w.T / dt, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {n} of {e.N} envs x {w.T} steps, fp64 actors, {dt:.1f} s"}
+
+
+# ----------------------------------------------------------------- GPU arms
+def _flush_l2(buf):
+    buf.add_(1)
+
+
+def time_rollouts(fr, env, ens, T, steps, warmup, metrics, flush, stream, traj=None):
+    import torch
+    for _ in range(warmup):
+        fr.env_reset(env)
+        fr.rollout(env, ens, T, traj=traj, metrics=metrics)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        _flush_l2(flush)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fr.env_reset(env)
+        fr.rollout(env, ens, T, traj=traj, metrics=metrics)
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b) / 1e3)
+    return times
+
+
+def time_kernel(fn, iters, stream):
+    import torch
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(iters):
+        fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / 1e3 / iters
+
+
+def run_gpu(args):
+    import torch
+    import paper_2501_10709_gb300 as fr
+    from paper_2501_10709_gb300 import build as fb
+
+    rank, world = _dist()
+    fb.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    w = build_workload()
+    e = w.envs
+    N, T, M = e.N, w.T, w.params.shape[0]
+    ctx = fr.fr_ctx_create(local)
+    mk = fr.fr_market_create(ctx, w.market)
+    env = fr.env_create(ctx, mk, start=e.start, window=e.W, n_assets=e.Ke, bps=e.bps)
+    ens_bf16 = fr.ensemble_create(ctx, w.dims, w.params, precision=fr.PREC_BF16)
+    ens_fp32 = fr.ensemble_create(ctx, w.dims, w.params, precision=fr.PREC_FP32)
+    metrics = torch.empty(N, 3, dtype=torch.float64, device=dev)
+    flush = torch.zeros(128 * 1024 * 1024, dtype=torch.float32, device=dev)   # 512 MB > L2
+    peaks, peak_src = _peaks()
+
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_bf16 = time_rollouts(fr, env, ens_bf16, T, args.steps, args.warmup, metrics, flush, stream)
+    clk = clocks.stop()
+    t_fp32 = time_rollouts(fr, env, ens_fp32, T, max(2, args.steps // 4), 2, metrics, flush, stream)
+    total = sum(t_bf16)
+    if world > 1:
+        tt = torch.tensor([total], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total = float(tt.item())
+    env_steps = N * T
+    value = world * env_steps * args.steps / total
+    plain_value = env_steps * len(t_fp32) / sum(t_fp32)
+
+    # dominant kernel: the BF16 actor kernel, timed alone on one step's batch
+    obs = torch.empty(N, env.D, device=dev)
+    fr.env_reset(env)
+    fr.env_observe(env, obs)
+    y = torch.empty(M, N, 30, device=dev)
+    k_dt = time_kernel(lambda: fr.ensemble_forward(ens_bf16, obs, y), 50, stream)
+    flops_per_launch = N * M * 2 * sum(w.dims[i] * w.dims[i + 1] for i in range(len(w.dims) - 1))
+    achieved = flops_per_launch / k_dt / 1e12
+    peak = peaks["bf16_tflops"]
+    # the same kernel at a batch large enough to fill every SM
+    nb = 152 * 128 * 4
+    obs_big = obs.repeat(nb // N, 1)
+    y_big = torch.empty(M, nb, 30, device=dev)
+    kb_dt = time_kernel(lambda: fr.ensemble_forward(ens_bf16, obs_big, y_big), 10, stream)
+    big_tflops = nb / N * flops_per_launch / kb_dt / 1e12
+
+    # end to end through the public API with host buffers
+    snap = fr.env_snapshot(env)
+    host_met = torch.empty(N, 3, dtype=torch.float64, pin_memory=True)
+    e2e_times = []
+    for i in range(args.warmup + max(2, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fr.env_restore(env, snap)
+        fr.rollout(env, ens_bf16, T, metrics=metrics)
+        host_met.copy_(metrics, non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_value = world * env_steps / statistics.mean(e2e_times)
+
+    launches_per_rollout = 2 + 4 * T
+    line = {
+        "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "stock 2048 envs x 30 assets x 256 steps, 3 x 301-256-256-30 BF16 "
+                               "actors, mean combine, 1000 GBM days, bps on",
+                   "n_envs": N, "steps_per_rollout": T, "agents": M, "path": "unfused bf16 tcgen05",
+                   "l2": "flushed between timed rollouts (512 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "plain_fp32": {"value": plain_value, "unit": "env-steps/s",
+                       "ms_per_rollout": 1e3 * statistics.mean(t_fp32)},
+        "speedup_vs_plain": value / world / plain_value,
+        "latency": {"p50_ms": None, "p99_ms": None, "note": "serving loop not measured in this run"},
+        "e2e": {"value": e2e_value, "unit": "env-steps/s",
+                "h2d_bytes_per_step": len(snap), "d2h_bytes_per_step": N * 3 * 8},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_tc_forward (2048 rows x 3 agents per launch)",
+                     "peak_source": f"bf16_tflops burst, {peak_src}",
+                     "large_batch": {"rows": nb, "achieved": big_tflops, "frac": big_tflops / peak}},
+        "gpu_launches": launches_per_rollout * args.steps + 1,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm: each step a bounded sample of the
+    same workload on the host cores."""
+    rank, world = _dist()
+    if rank != 0:
+        return
+    import oracle
+    w = build_workload()
+    e = w.envs
+    threads = oracle.max_threads()
+    n = args.ref_envs
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.stock_run(w.market, e.Ke[:n], e.start[:n], e.W[:n], e.bps[:n], init_cash=e.init_cash,
+                         hmax=100, fee_bps=10, T=w.T, ensemble=(w.dims, w.params, None),
+                         nthreads=threads, want=("metrics",))
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = n * w.T * len(times) / total
+    sample = f"first {n} of {e.N} envs x {w.T} steps per step, fp64 actors"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "env-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "stock 2048 envs x 30 assets x 256 steps, 3 x 301-256-256-30 "
+                               "actors, mean combine (oracle sample)", "n_envs": n},
+        "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-envs", type=int, default=32)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,272 @@
+/*
+ * finrl_gb300.h -- C ABI of the GB300 sampling library for the stock- and
+ * crypto-trading environments of "Revisiting Ensemble Methods for Stock
+ * Trading and Crypto Trading Tasks at ACM ICAIF FinRL Contests 2023/2024"
+ * (arXiv 2501.10709).
+ *
+ * The library steps thousands of parallel trading environments (the paper's
+ * VecEnv of SubEnvs, Sec. 4.2.2) on one GPU and evaluates an ensemble of actor
+ * networks (Sec. 5.2) inside the same rollout.  Everything it computes runs
+ * in its own CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions shared by every call
+ *  - Every function returns FR_OK (0) or a negative FR_E* status; no C++
+ *    exception crosses the ABI.  fr_last_error() returns a message for the
+ *    last failure on the calling thread.
+ *  - Handles are opaque, owned by the library and released by *_destroy.
+ *  - "device" pointers are CUDA device addresses on the context's device;
+ *    "host" pointers are ordinary CPU memory.  Device pointers passed in are
+ *    borrowed until the call's work completes on the given stream; host
+ *    pointers are read (or written) before the call returns unless stated.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on that stream unless named *_sync or
+ *    documented otherwise.
+ *  - Money is int64 cents; holdings are integer shares (stock) or lots
+ *    (crypto); neither is ever negative.
+ */
+#ifndef FINRL_GB300_H
+#define FINRL_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define FR_OK 0
+#define FR_EINVAL (-1)      /* bad argument, shape or configuration        */
+#define FR_ENOMEM (-2)      /* allocation failed or HBM budget exceeded     */
+#define FR_EBUSY (-3)       /* resource in use                              */
+#define FR_ETIMEDOUT (-4)   /* a bounded device wait gave up                */
+#define FR_ECUDA (-5)       /* a CUDA runtime call failed                   */
+#define FR_ENOTREADY (-6)   /* asynchronous result not ready yet            */
+#define FR_ENOTFOUND (-7)   /* unknown ticket                               */
+
+#define FR_TASK_STOCK 0
+#define FR_TASK_CRYPTO 1
+
+#define FR_MAX_ASSETS 32        /* K <= 32: one warp lane per asset          */
+#define FR_MAX_INDICATORS 16
+#define FR_CRYPTO_FACTORS 8
+#define FR_CRYPTO_OBS_DIM 10    /* [cash, position, 8 factors]               */
+
+/* Message describing the last failure on this thread ("" if none). */
+const char *fr_last_error(void);
+
+/* Library version string. */
+const char *fr_version(void);
+
+/* --------------------------------------------------------------- context */
+typedef struct fr_ctx fr_ctx;
+
+/* Create a context on CUDA device `device` that may hold at most
+ * `hbm_budget_bytes` of device memory across all objects created from it
+ * (0 = no limit).  Creation that would exceed the budget fails with
+ * FR_ENOMEM. */
+int fr_ctx_create(int device, uint64_t hbm_budget_bytes, fr_ctx **out);
+void fr_ctx_destroy(fr_ctx *ctx);
+/* Device bytes currently held by objects of this context. */
+uint64_t fr_ctx_bytes_in_use(const fr_ctx *ctx);
+/* Number of SMs of the context's device. */
+int fr_ctx_sm_count(const fr_ctx *ctx);
+
+/* ---------------------------------------------------------------- markets */
+typedef struct fr_market fr_market;
+
+/* Market tables, read from host memory at creation and then held resident
+ * on the device (the paper keeps simulation data in GPU memory, Sec. 4.3.2).
+ *  stock : close int64 [n_days][n_assets] cents (>= 1);
+ *          ind float32 [n_days][n_ind][n_assets] technical indicators
+ *          (Sec. 3.1, f_t), indicator-major within a day.
+ *  crypto: mid int64 [n_seconds] cents per lot (>= 1); spread uint8
+ *          [n_seconds] cents; fac float32 [n_seconds][8] factors. */
+typedef struct {
+    int32_t task;             /* FR_TASK_STOCK or FR_TASK_CRYPTO            */
+    int32_t n_days;           /* stock                                      */
+    int32_t n_assets;         /* stock, 1..32                               */
+    int32_t n_ind;            /* stock, 0..16                               */
+    const int64_t *close;     /* host                                       */
+    const float *ind;         /* host                                       */
+    int64_t n_seconds;        /* crypto                                     */
+    const int64_t *mid;       /* host                                       */
+    const uint8_t *spread;    /* host                                       */
+    const float *fac;         /* host                                       */
+} fr_market_desc;
+
+int fr_market_create(fr_ctx *ctx, const fr_market_desc *desc, fr_market **out);
+void fr_market_destroy(fr_market *m);
+
+/* ------------------------------------------------------------ environments */
+typedef struct fr_env fr_env;
+
+/* A batch of N independent environments over one market (the paper's VecEnv
+ * of SubEnvs, Sec. 4.2.2; each trajectory is independent, Sec. 4.2.1).
+ * Env e trades over the window start[e] .. start[e] + window[e] - 1 (days or
+ * seconds): window[e] - 1 steps, after which it is done.
+ *  stock : state [b, p, h, f] of Sec. 3.1, observation dimension
+ *          D = 1 + 2K + I*K for the market's K assets and I indicators:
+ *          [cash*1e-8, p_k*1e-4, h_k*1e-2, f_{i,k} (i outer, k inner)],
+ *          each entry (float)((double)x * c); assets k >= n_assets[e] read 0.
+ *          Prices are the day's close scaled by (1e4 + bps[e][k]) / 1e4,
+ *          rounded half up, floor 1 cent (Sec. 5.1 dataset diversity).
+ *          Actions are share changes (Sec. 3.1): sells first, capped at the
+ *          holding; then buys in ascending asset order, each filled as far as
+ *          cash allows; fee ceil(notional * fee_bps / 1e4) per order.
+ *  crypto: one asset; observation [cash*1e-8, pos/pmax, fac_0..7];
+ *          action {0 sell, 1 hold, 2 buy} of one lot at bid = mid - s/2 or
+ *          ask = bid + s; long-only, at most pmax lots; no fee.
+ *  Reward (both): v_{t+1} - v_t with v = cash + holdings * price
+ *  (Sec. 3.1), int64 cents; a float copy is reward * 1e-6.
+ * K > 32, window < 2 or a window past the market end -> FR_EINVAL. */
+typedef struct {
+    int32_t task;
+    int32_t n_envs;           /* N >= 1                                     */
+    const int32_t *n_assets;  /* host [N] stock: 1..K (NULL = all K)        */
+    const int32_t *window;    /* host [N] >= 2                              */
+    const int32_t *start;     /* host [N] >= 0                              */
+    const int16_t *bps;       /* host [N][K] stock, -100..100 (NULL = 0)    */
+    int64_t init_cash;        /* cents, >= 0                                */
+    int32_t hmax;             /* stock: shares per unit action, 1..1e6      */
+    int32_t fee_bps;          /* stock: 0..10000                            */
+    int32_t pmax;             /* crypto: lots, >= 1                         */
+    int32_t auto_reset;       /* 1: a finished env restarts at once         */
+} fr_env_desc;
+
+int env_create(fr_ctx *ctx, const fr_env_desc *desc, const fr_market *market,
+               fr_env **out);
+void env_destroy(fr_env *env);
+/* N, observation dimension D, market assets K (1 for crypto). */
+int env_dims(const fr_env *env, int32_t *n_envs, int32_t *obs_dim,
+             int32_t *n_assets);
+
+/* reset (Sec. 4.2.2): every env back to its initial state: cash =
+ * init_cash, no holdings, step 0, episode accumulators cleared. */
+int env_reset(fr_env *env, void *stream);
+
+#define FR_ACT_I32_SHARES 0   /* stock: int32 [N][K] share changes          */
+#define FR_ACT_F32_UNIT 1     /* stock: float [N][K] in [-1,1] -> trunc(a*hmax)
+                                 shares; NaN/Inf count as 0                  */
+#define FR_ACT_U8_DISCRETE 2  /* crypto: uint8 [N] 0 sell, 1 hold, 2 buy    */
+
+typedef struct {
+    int32_t kind;             /* FR_ACT_*                                   */
+    const void *data;         /* device                                     */
+} fr_action;
+
+/* Outputs of one step, each a device pointer or NULL. */
+typedef struct {
+    int64_t *rew;             /* [N] reward in cents                        */
+    float *rew_f32;           /* [N] reward * 1e-6                          */
+    uint8_t *done;            /* [N] 1 when the env's window is finished    */
+    float *obs;               /* [N][D] observation after the step          */
+} fr_step_out;
+
+/* step + reward (Sec. 4.2.2): apply one action to every env.  A done env
+ * (without auto_reset) is left unchanged and reports reward 0, done 1. */
+int env_step(fr_env *env, const fr_action *action, const fr_step_out *out,
+             void *stream);
+
+/* Observation of the current state: obs device float [N][ld], ld >= D. */
+int env_observe(fr_env *env, float *obs, int32_t ld, void *stream);
+
+/* Copy of the state: cash [N] int64, holdings [N][K] int32 (crypto: [N]
+ * lots), steps taken [N] int32, done [N] uint8 -- device pointers, any NULL. */
+int env_get_state(fr_env *env, int64_t *cash, int32_t *hold, int32_t *steps,
+                  uint8_t *done, void *stream);
+
+/* Episode metrics [N][3] float64 (device): cumulative return v_T / v_0 - 1,
+ * Sharpe ratio (mean - r_f) / std * sqrt(A) of per-period returns
+ * (Sharpe equation, Sec. 5.2.1; ddof 1, r_f = 0, A = 252 stock, 1 crypto;
+ * 0 with fewer than two periods or zero variance), maximum drawdown
+ * min_t v_t / max_{s<=t} v_s - 1 (Sec. 6.1).  Accumulated in FP64 on the
+ * device as the env steps.  After an auto-reset at the last step the
+ * finished episode is reported. */
+int env_metrics(fr_env *env, double *metrics, void *stream);
+
+/* Checkpoint of the whole env state to host memory (synchronous).  With
+ * host_buf NULL only *len receives the size needed. */
+int env_snapshot(fr_env *env, void *host_buf, size_t cap, size_t *len);
+/* Restore a snapshot taken from an env of the same task and shape. */
+int env_restore(fr_env *env, const void *host_buf, size_t len);
+
+/* Count of non-finite float actions and out-of-range discrete actions seen
+ * since creation (each treated as 0 / hold). */
+int env_error_count(fr_env *env, uint64_t *count);
+
+/* -------------------------------------------------------------- ensembles */
+typedef struct fr_ensemble fr_ensemble;
+
+#define FR_PREC_FP32 0        /* plain unfused fp32 SIMT path               */
+#define FR_PREC_BF16 1        /* tcgen05 BF16 tensor cores, fp32 accumulate */
+#define FR_PREC_FP8 2         /* tcgen05 FP8 E4M3 weights+activations       */
+
+#define FR_COMBINE_MEAN 0     /* Sec. 5.2.1 weighted average of actions     */
+#define FR_COMBINE_VOTE 1     /* Sec. 5.2.2 majority vote of argmax actions */
+
+/* M actors of identical shape (Sec. 6.1 agent networks): L dense layers
+ * dims[0] -> ... -> dims[L], ReLU on hidden layers, tanh (out_act = 1) or
+ * identity (out_act = 0) on the output.  params: host float [M][P], per
+ * layer W_l[out][in] row-major then b_l[out].  weights: host float [M]
+ * (MEAN only; NULL = uniform 1/M).  MEAN combines as
+ *   a = a_0 + sum_{j>=1} w_j (a_j - a_0),
+ * which is the weighted average when the weights sum to one and exactly a_0
+ * for identical agents; VOTE takes each agent's argmax (lowest index on
+ * ties) and returns the action with the strictly largest count, else 1. */
+typedef struct {
+    int32_t n_agents;         /* M, 1..8                                    */
+    int32_t n_layers;         /* L, 1..4                                    */
+    const int32_t *dims;      /* host [L+1]; hidden widths <= 256           */
+    const float *params;      /* host [M][P]                                */
+    const float *weights;     /* host [M] or NULL                           */
+    int32_t precision;        /* FR_PREC_*                                  */
+    int32_t combine;          /* FR_COMBINE_*                               */
+    int32_t out_act;          /* 1 tanh, 0 identity                         */
+} fr_ensemble_desc;
+
+int ensemble_create(fr_ctx *ctx, const fr_ensemble_desc *desc,
+                    fr_ensemble **out);
+void ensemble_destroy(fr_ensemble *ens);
+
+/* Per-agent network outputs: obs device float [n][dims[0]] (packed rows),
+ * y device float [M][n][dims[L]]. */
+int ensemble_forward(const fr_ensemble *ens, const float *obs, int32_t n,
+                     float *y, void *stream);
+
+/* Combined action for n observations (obs device float [n][dims[0]]):
+ * MEAN -> act device float [n][dims[L]]; VOTE -> act device uint8 [n]. */
+int ensemble_act(const fr_ensemble *ens, const float *obs, int32_t n,
+                 void *act, void *stream);
+
+/* Error flags raised on the device by the tensor-core kernels of this
+ * ensemble (a bounded wait that gave up); 0 when none (synchronous). */
+int ensemble_device_errors(const fr_ensemble *ens, uint32_t *flags);
+
+/* ---------------------------------------------------------------- rollout */
+
+/* Optional trajectory: the T x N x D sample tensors of Sec. 4.3.2, each a
+ * device pointer or NULL.  Row t holds the observation the step acted on,
+ * the combined action, the reward and the done flag. */
+typedef struct {
+    float *obs;               /* [T][N][obs_ld]                             */
+    int32_t obs_ld;           /* >= D (0 = D)                               */
+    void *act;                /* stock float [T][N][K]; crypto uint8 [T][N] */
+    int64_t *rew;             /* [T][N]                                     */
+    float *rew_f32;           /* [T][N]                                     */
+    uint8_t *done;            /* [T][N]                                     */
+} fr_traj;
+
+/* T steps of observe -> ensemble -> step for every env (the simulation
+ * phase of Sec. 3.2, parallel over trajectories as in Sec. 4.2.1).  The
+ * ensemble's precision picks the path: FP32 runs the plain unfused kernels
+ * (one launch per stage per step); BF16/FP8 run one fused persistent
+ * kernel per rollout with tcgen05 tensor-core actors.  metrics: device
+ * float64 [N][3] as env_metrics, written at the end, or NULL. */
+int rollout(fr_env *env, const fr_ensemble *ens, int32_t T,
+            const fr_traj *traj, double *metrics, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FINRL_GB300_H */

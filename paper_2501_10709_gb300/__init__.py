@@ -1,0 +1,276 @@
+"""GB300 sampling library for the FinRL stock and crypto trading environments.
+
+A thin Python binding over the C ABI of ``libfinrl_gb300.so`` (declared in
+``include/finrl_gb300.h``): every function here only marshals arguments --
+numpy arrays for host tables, torch CUDA tensors for device buffers, the
+current torch stream -- and calls the library function of the same name.
+All computation runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import (ACT_F32_UNIT, ACT_I32_SHARES, ACT_U8_DISCRETE, COMBINE_MEAN,
+                   COMBINE_VOTE, PREC_BF16, PREC_FP8, PREC_FP32, TASK_CRYPTO,
+                   TASK_STOCK, FrError)
+
+__all__ = [
+    "fr_ctx_create", "fr_market_create", "env_create", "env_reset", "env_step",
+    "env_observe", "env_get_state", "env_metrics", "env_snapshot", "env_restore",
+    "env_error_count", "env_dims", "ensemble_create", "ensemble_forward",
+    "ensemble_act", "ensemble_device_errors", "rollout", "FrError", "lib",
+    "ACT_I32_SHARES", "ACT_F32_UNIT", "ACT_U8_DISCRETE", "PREC_FP32", "PREC_BF16",
+    "PREC_FP8", "COMBINE_MEAN", "COMBINE_VOTE", "TASK_STOCK", "TASK_CRYPTO",
+]
+
+
+def lib():
+    return _lib.load()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dptr(t, dtype=None, numel=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, needs {numel}")
+    return t.data_ptr()
+
+
+def _hptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+class _Handle:
+    _destroy = None
+
+    def __init__(self, ptr, keep=()):
+        self.ptr = ptr
+        self._keep = keep
+
+    def close(self):
+        if self.ptr:
+            getattr(lib(), self._destroy)(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def _as_parameter_(self):
+        return self.ptr
+
+
+class Ctx(_Handle):
+    _destroy = "fr_ctx_destroy"
+
+    @property
+    def bytes_in_use(self) -> int:
+        return int(lib().fr_ctx_bytes_in_use(self.ptr))
+
+    @property
+    def sm_count(self) -> int:
+        return int(lib().fr_ctx_sm_count(self.ptr))
+
+
+class Market(_Handle):
+    _destroy = "fr_market_destroy"
+
+
+class Env(_Handle):
+    _destroy = "env_destroy"
+
+
+class Ensemble(_Handle):
+    _destroy = "ensemble_destroy"
+
+
+def fr_ctx_create(device: int = 0, hbm_budget_bytes: int = 0) -> Ctx:
+    out = C.c_void_p()
+    _lib.check(lib().fr_ctx_create(int(device), int(hbm_budget_bytes), C.byref(out)), "fr_ctx_create")
+    return Ctx(out.value)
+
+
+def fr_market_create(ctx: Ctx, market) -> Market:
+    """market: an object with close/ind (stock) or mid/spread/fac (crypto)."""
+    d = _lib.MarketDesc()
+    keep = []
+    if hasattr(market, "close"):
+        close = np.ascontiguousarray(market.close, np.int64)
+        ind = np.ascontiguousarray(market.ind, np.float32)
+        keep += [close, ind]
+        d.task, d.n_days, d.n_assets, d.n_ind = TASK_STOCK, close.shape[0], close.shape[1], ind.shape[1]
+        d.close, d.ind = _hptr(close), _hptr(ind)
+    else:
+        mid = np.ascontiguousarray(market.mid, np.int64)
+        spread = np.ascontiguousarray(market.spread, np.uint8)
+        fac = np.ascontiguousarray(market.fac, np.float32)
+        keep += [mid, spread, fac]
+        d.task, d.n_seconds = TASK_CRYPTO, mid.size
+        d.mid, d.spread, d.fac = _hptr(mid), _hptr(spread), _hptr(fac)
+    out = C.c_void_p()
+    _lib.check(lib().fr_market_create(ctx, C.byref(d), C.byref(out)), "fr_market_create")
+    m = Market(out.value, keep=(ctx,))
+    m.task = d.task
+    return m
+
+
+def env_create(ctx: Ctx, market: Market, *, start, window, n_assets=None, bps=None,
+               init_cash: int = 100_000_000, hmax: int = 100, fee_bps: int = 10,
+               pmax: int = 10, auto_reset: bool = False) -> Env:
+    start = np.ascontiguousarray(start, np.int32)
+    window = np.ascontiguousarray(np.broadcast_to(window, start.shape), np.int32)
+    na = None if n_assets is None else np.ascontiguousarray(np.broadcast_to(n_assets, start.shape), np.int32)
+    b = None if bps is None else np.ascontiguousarray(bps, np.int16)
+    d = _lib.EnvDesc(task=market.task, n_envs=start.size, n_assets=_hptr(na), window=_hptr(window),
+                     start=_hptr(start), bps=_hptr(b), init_cash=int(init_cash), hmax=int(hmax),
+                     fee_bps=int(fee_bps), pmax=int(pmax), auto_reset=int(bool(auto_reset)))
+    out = C.c_void_p()
+    _lib.check(lib().env_create(ctx, C.byref(d), market, C.byref(out)), "env_create")
+    env = Env(out.value, keep=(ctx, market))
+    env.N, env.D, env.K = env_dims(env)
+    env.task = market.task
+    return env
+
+
+def env_dims(env: Env):
+    n, d, k = C.c_int32(), C.c_int32(), C.c_int32()
+    _lib.check(lib().env_dims(env, C.byref(n), C.byref(d), C.byref(k)), "env_dims")
+    return n.value, d.value, k.value
+
+
+def env_reset(env: Env, stream=None):
+    _lib.check(lib().env_reset(env, _stream(stream)), "env_reset")
+
+
+def env_step(env: Env, action, kind: int, *, rew=None, rew_f32=None, done=None, obs=None,
+             stream=None):
+    import torch
+    a = _lib.Action(kind=int(kind), data=_dptr(action, name="action"))
+    o = _lib.StepOut(rew=_dptr(rew, torch.int64, env.N, "rew"),
+                     rew_f32=_dptr(rew_f32, torch.float32, env.N, "rew_f32"),
+                     done=_dptr(done, torch.uint8, env.N, "done"),
+                     obs=_dptr(obs, torch.float32, env.N * env.D, "obs"))
+    _lib.check(lib().env_step(env, C.byref(a), C.byref(o), _stream(stream)), "env_step")
+
+
+def env_observe(env: Env, obs, ld: int | None = None, stream=None):
+    import torch
+    ld = ld or env.D
+    _lib.check(lib().env_observe(env, _dptr(obs, torch.float32, env.N * ld, "obs"), int(ld),
+                                 _stream(stream)), "env_observe")
+
+
+def env_get_state(env: Env, cash=None, hold=None, steps=None, done=None, stream=None):
+    import torch
+    _lib.check(lib().env_get_state(env, _dptr(cash, torch.int64, env.N, "cash"),
+                                   _dptr(hold, torch.int32, env.N * env.K, "hold"),
+                                   _dptr(steps, torch.int32, env.N, "steps"),
+                                   _dptr(done, torch.uint8, env.N, "done"), _stream(stream)),
+               "env_get_state")
+
+
+def env_metrics(env: Env, metrics, stream=None):
+    import torch
+    _lib.check(lib().env_metrics(env, _dptr(metrics, torch.float64, env.N * 3, "metrics"),
+                                 _stream(stream)), "env_metrics")
+
+
+def env_snapshot(env: Env) -> bytes:
+    n = C.c_size_t()
+    _lib.check(lib().env_snapshot(env, None, 0, C.byref(n)), "env_snapshot")
+    buf = C.create_string_buffer(n.value)
+    _lib.check(lib().env_snapshot(env, buf, n.value, C.byref(n)), "env_snapshot")
+    return buf.raw[:n.value]
+
+
+def env_restore(env: Env, blob: bytes):
+    _lib.check(lib().env_restore(env, blob, len(blob)), "env_restore")
+
+
+def env_error_count(env: Env) -> int:
+    c = C.c_uint64()
+    _lib.check(lib().env_error_count(env, C.byref(c)), "env_error_count")
+    return c.value
+
+
+def ensemble_create(ctx: Ctx, dims, params, *, weights=None, precision: int = PREC_FP32,
+                    combine: int = COMBINE_MEAN, out_act: int = 1) -> Ensemble:
+    dims = np.ascontiguousarray(dims, np.int32)
+    params = np.ascontiguousarray(params, np.float32)
+    w = None if weights is None else np.ascontiguousarray(weights, np.float32)
+    d = _lib.EnsembleDesc(n_agents=params.shape[0], n_layers=dims.size - 1, dims=_hptr(dims),
+                          params=_hptr(params), weights=_hptr(w), precision=int(precision),
+                          combine=int(combine), out_act=int(out_act))
+    out = C.c_void_p()
+    _lib.check(lib().ensemble_create(ctx, C.byref(d), C.byref(out)), "ensemble_create")
+    e = Ensemble(out.value, keep=(ctx,))
+    e.M, e.dims, e.combine, e.precision = params.shape[0], tuple(int(x) for x in dims), combine, precision
+    return e
+
+
+def ensemble_forward(ens: Ensemble, obs, y, stream=None):
+    import torch
+    n = obs.shape[0]
+    _lib.check(lib().ensemble_forward(ens, _dptr(obs, torch.float32, n * ens.dims[0], "obs"), n,
+                                      _dptr(y, torch.float32, ens.M * n * ens.dims[-1], "y"),
+                                      _stream(stream)), "ensemble_forward")
+
+
+def ensemble_act(ens: Ensemble, obs, act, stream=None):
+    import torch
+    n = obs.shape[0]
+    want = (torch.float32, n * ens.dims[-1]) if ens.combine == COMBINE_MEAN else (torch.uint8, n)
+    _lib.check(lib().ensemble_act(ens, _dptr(obs, torch.float32, n * ens.dims[0], "obs"), n,
+                                  _dptr(act, *want, "act"), _stream(stream)), "ensemble_act")
+
+
+def ensemble_device_errors(ens: Ensemble) -> int:
+    f = C.c_uint32()
+    _lib.check(lib().ensemble_device_errors(ens, C.byref(f)), "ensemble_device_errors")
+    return f.value
+
+
+def rollout(env: Env, ens: Ensemble, T: int, *, traj: dict | None = None, metrics=None,
+            stream=None):
+    """traj: optional dict of device tensors obs [T][N][ld], act, rew, rew_f32, done."""
+    import torch
+    tp = None
+    if traj:
+        t = _lib.Traj()
+        ob = traj.get("obs")
+        ld = int(traj.get("obs_ld", ob.shape[-1] if ob is not None else 0))
+        t.obs = _dptr(ob, torch.float32, T * env.N * max(ld, 1), "traj obs")
+        t.obs_ld = ld
+        act = traj.get("act")
+        if act is not None:
+            if env.task == TASK_STOCK:
+                t.act = _dptr(act, torch.float32, T * env.N * env.K, "traj act")
+            else:
+                t.act = _dptr(act, torch.uint8, T * env.N, "traj act")
+        t.rew = _dptr(traj.get("rew"), torch.int64, T * env.N, "traj rew")
+        t.rew_f32 = _dptr(traj.get("rew_f32"), torch.float32, T * env.N, "traj rew_f32")
+        t.done = _dptr(traj.get("done"), torch.uint8, T * env.N, "traj done")
+        tp = C.byref(t)
+    _lib.check(lib().rollout(env, ens, int(T), tp,
+                             _dptr(metrics, torch.float64, env.N * 3, "metrics"),
+                             _stream(stream)), "rollout")

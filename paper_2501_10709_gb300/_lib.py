@@ -1,0 +1,118 @@
+"""ctypes declarations of the C ABI in ``include/finrl_gb300.h``.
+
+Loading fails loudly when ``libfinrl_gb300.so`` has not been built: there is
+no CPU fallback for anything the library computes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfinrl_gb300.so")
+
+FR_OK, FR_EINVAL, FR_ENOMEM, FR_EBUSY, FR_ETIMEDOUT, FR_ECUDA, FR_ENOTREADY, FR_ENOTFOUND = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+TASK_STOCK, TASK_CRYPTO = 0, 1
+ACT_I32_SHARES, ACT_F32_UNIT, ACT_U8_DISCRETE = 0, 1, 2
+PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
+COMBINE_MEAN, COMBINE_VOTE = 0, 1
+
+i32, i64, u32, u64, f64 = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_double
+vp, cp = C.c_void_p, C.c_char_p
+size_t = C.c_size_t
+
+
+class MarketDesc(C.Structure):
+    _fields_ = [("task", i32), ("n_days", i32), ("n_assets", i32), ("n_ind", i32),
+                ("close", vp), ("ind", vp), ("n_seconds", i64), ("mid", vp),
+                ("spread", vp), ("fac", vp)]
+
+
+class EnvDesc(C.Structure):
+    _fields_ = [("task", i32), ("n_envs", i32), ("n_assets", vp), ("window", vp),
+                ("start", vp), ("bps", vp), ("init_cash", i64), ("hmax", i32),
+                ("fee_bps", i32), ("pmax", i32), ("auto_reset", i32)]
+
+
+class Action(C.Structure):
+    _fields_ = [("kind", i32), ("data", vp)]
+
+
+class StepOut(C.Structure):
+    _fields_ = [("rew", vp), ("rew_f32", vp), ("done", vp), ("obs", vp)]
+
+
+class EnsembleDesc(C.Structure):
+    _fields_ = [("n_agents", i32), ("n_layers", i32), ("dims", vp), ("params", vp),
+                ("weights", vp), ("precision", i32), ("combine", i32), ("out_act", i32)]
+
+
+class Traj(C.Structure):
+    _fields_ = [("obs", vp), ("obs_ld", i32), ("act", vp), ("rew", vp), ("rew_f32", vp),
+                ("done", vp)]
+
+
+# name -> (restype, argtypes); every symbol the header declares
+SIGNATURES = {
+    "fr_last_error": (cp, []),
+    "fr_version": (cp, []),
+    "fr_ctx_create": (i32, [i32, u64, vp]),
+    "fr_ctx_destroy": (None, [vp]),
+    "fr_ctx_bytes_in_use": (u64, [vp]),
+    "fr_ctx_sm_count": (i32, [vp]),
+    "fr_market_create": (i32, [vp, vp, vp]),
+    "fr_market_destroy": (None, [vp]),
+    "env_create": (i32, [vp, vp, vp, vp]),
+    "env_destroy": (None, [vp]),
+    "env_dims": (i32, [vp, vp, vp, vp]),
+    "env_reset": (i32, [vp, vp]),
+    "env_step": (i32, [vp, vp, vp, vp]),
+    "env_observe": (i32, [vp, vp, i32, vp]),
+    "env_get_state": (i32, [vp, vp, vp, vp, vp, vp]),
+    "env_metrics": (i32, [vp, vp, vp]),
+    "env_snapshot": (i32, [vp, vp, size_t, vp]),
+    "env_restore": (i32, [vp, vp, size_t]),
+    "env_error_count": (i32, [vp, vp]),
+    "ensemble_create": (i32, [vp, vp, vp]),
+    "ensemble_destroy": (None, [vp]),
+    "ensemble_forward": (i32, [vp, vp, i32, vp, vp]),
+    "ensemble_act": (i32, [vp, vp, i32, vp, vp]),
+    "ensemble_device_errors": (i32, [vp, vp]),
+    "rollout": (i32, [vp, vp, i32, vp, vp, vp]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load():
+    """Load the CUDA library (raises if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"{LIB_PATH} is not built; run paper_2501_10709_gb300.build.build() "
+                "(this package has no CPU fallback)")
+        lib = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+class FrError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def check(rc: int, what: str = ""):
+    if rc != FR_OK:
+        msg = load().fr_last_error().decode(errors="replace")
+        raise FrError(rc, f"{what}: {msg}" if what else msg)

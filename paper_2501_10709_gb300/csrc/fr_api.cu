@@ -1,0 +1,713 @@
+// fr_api.cu -- the C ABI: contexts with an HBM budget, device-resident market
+// tables, env batches in structure-of-arrays layout, ensembles, and the
+// rollout driver that strings observe -> ensemble -> step together
+// (the simulation phase of Sec. 3.2, parallel over trajectories, Sec. 4.2.1).
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "fr_common.cuh"
+
+namespace fr {
+
+// ------------------------------------------------------------------ errors
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+    return FR_ECUDA;
+}
+
+// ------------------------------------------------------------------ budget
+static std::mutex g_budget_mu;
+
+int ctx_reserve(fr_ctx *ctx, uint64_t bytes)
+{
+    std::lock_guard<std::mutex> lk(g_budget_mu);
+    if (ctx->budget && ctx->used + bytes > ctx->budget) {
+        set_error("HBM budget exceeded: %llu in use + %llu requested > %llu",
+                  (unsigned long long)ctx->used, (unsigned long long)bytes,
+                  (unsigned long long)ctx->budget);
+        return FR_ENOMEM;
+    }
+    ctx->used += bytes;
+    return FR_OK;
+}
+
+void ctx_release(fr_ctx *ctx, uint64_t bytes)
+{
+    std::lock_guard<std::mutex> lk(g_budget_mu);
+    ctx->used = ctx->used >= bytes ? ctx->used - bytes : 0;
+}
+
+int dev_alloc(fr_ctx *ctx, void **p, uint64_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) return FR_OK;
+    int rc = ctx_reserve(ctx, bytes);
+    if (rc) return rc;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        ctx_release(ctx, bytes);
+        *p = nullptr;
+        (void)cudaGetLastError();
+        set_error("cudaMalloc of %llu bytes failed: %s", (unsigned long long)bytes,
+                  cudaGetErrorString(e));
+        return FR_ENOMEM;
+    }
+    return FR_OK;
+}
+
+void dev_free(fr_ctx *ctx, void *p, uint64_t bytes)
+{
+    if (!p) return;
+    cudaFree(p);
+    ctx_release(ctx, bytes);
+}
+
+static int use_device(const fr_ctx *ctx)
+{
+    FR_CUDA(cudaSetDevice(ctx->device));
+    return FR_OK;
+}
+
+// ------------------------------------------------------- plain fp32 forward
+cudaError_t forward_plain(const fr_ensemble *e, const float *obs, int ld, int n, float *y,
+                          float *scratch, cudaStream_t s)
+{
+    int wmax = 0;
+    for (int l = 1; l < e->L; ++l) wmax = std::max(wmax, e->dims[l]);
+    const float *in = obs;
+    int64_t in_stride = 0;
+    int in_ld = ld;
+    for (int l = 0; l < e->L; ++l) {
+        const bool last = l == e->L - 1;
+        const int fin = e->dims[l], fout = e->dims[l + 1];
+        float *out = last ? y : scratch + (int64_t)(l & 1) * e->M * n * wmax;
+        const int64_t out_stride = (int64_t)n * fout;
+        const int act = last ? (e->out_act ? 1 : 2) : 0;
+        cudaError_t err = launch_dense_f32(in, in_stride, in_ld, e->params, e->P, e->w_off[l],
+                                           e->b_off[l], out, out_stride, fout, n, fin, fout,
+                                           act, e->M, s);
+        if (err != cudaSuccess) return err;
+        in = out;
+        in_stride = out_stride;
+        in_ld = fout;
+    }
+    return cudaSuccess;
+}
+
+namespace {
+struct Carve {
+    char *base;
+    uint64_t off = 0;
+    template <class T>
+    T *take(uint64_t count)
+    {
+        off = (off + 255) & ~255ull;
+        T *p = (T *)(base ? base + off : nullptr);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+// Lay out every per-env array in one block; with base NULL only sizes it.
+uint64_t carve_env(EnvView &v, char *base)
+{
+    Carve c{base};
+    const int64_t N = v.N;
+    const int64_t hs = v.task == FR_TASK_STOCK ? KP : 1;
+    v.Ke = c.take<int32_t>(N);
+    v.start = c.take<int32_t>(N);
+    v.W = c.take<int32_t>(N);
+    v.bps = c.take<int16_t>(v.task == FR_TASK_STOCK ? N * KP : 1);
+    // state (contiguous from here: the snapshot covers it all)
+    v.cash = c.take<int64_t>(N);
+    v.hold = c.take<int32_t>(N * hs);
+    v.t = c.take<int32_t>(N);
+    v.done = c.take<uint8_t>(N);
+    v.mu = c.take<double>(N);
+    v.m2 = c.take<double>(N);
+    v.mdd = c.take<double>(N);
+    v.peak = c.take<int64_t>(N);
+    v.vlast = c.take<int64_t>(N);
+    v.latched = c.take<double>(N * 4);
+    v.err = c.take<unsigned long long>(1);
+    return (c.off + 255) & ~255ull;
+}
+}  // namespace
+
+namespace {
+struct SnapHeader {
+    uint32_t magic, version;
+    int32_t task, N, K, I;
+    uint64_t state_off, state_bytes;
+};
+constexpr uint32_t kSnapMagic = 0x4e534652u;  // "FRSN"
+}  // namespace
+
+namespace {
+// per-agent outputs into y[M][n][out]; plain path scratch from the stream-
+// ordered allocator so that calls on different streams never share it
+int forward_any(const fr_ensemble *e, const float *obs, int ld, int n, float *y, cudaStream_t s)
+{
+    if (e->precision != FR_PREC_FP32) return tc_forward(e, obs, ld, n, y, s);
+    void *scratch = nullptr;
+    const uint64_t sb = plain_scratch_bytes(e, n);
+    if (sb) FR_CUDA(cudaMallocAsync(&scratch, sb, s));
+    cudaError_t err = forward_plain(e, obs, ld, n, y, (float *)scratch, s);
+    if (scratch) cudaFreeAsync(scratch, s);
+    FR_CUDA(err);
+    return FR_OK;
+}
+}  // namespace
+
+}  // namespace fr
+
+using namespace fr;
+
+// =================================================================== C ABI
+extern "C" {
+
+const char *fr_last_error(void) { return g_err; }
+
+const char *fr_version(void) { return "finrl_gb300 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------- context
+int fr_ctx_create(int device, uint64_t hbm_budget_bytes, fr_ctx **out)
+{
+    FR_CHECK(out, FR_EINVAL, "fr_ctx_create: out is NULL");
+    *out = nullptr;
+    int n = 0;
+    FR_CUDA(cudaGetDeviceCount(&n));
+    FR_CHECK(device >= 0 && device < n, FR_EINVAL, "fr_ctx_create: device %d of %d", device, n);
+    FR_CUDA(cudaSetDevice(device));
+    fr_ctx *c = new (std::nothrow) fr_ctx();
+    FR_CHECK(c, FR_ENOMEM, "fr_ctx_create: out of host memory");
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    c->used = 0;
+    cudaError_t e1 = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    cudaError_t e2 = cudaDeviceGetAttribute(&c->cc_major, cudaDevAttrComputeCapabilityMajor, device);
+    cudaError_t e3 = cudaDeviceGetAttribute(&c->cc_minor, cudaDevAttrComputeCapabilityMinor, device);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        delete c;
+        return cuda_fail(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3), "device attributes");
+    }
+    *out = c;
+    return FR_OK;
+}
+
+void fr_ctx_destroy(fr_ctx *ctx) { delete ctx; }
+
+uint64_t fr_ctx_bytes_in_use(const fr_ctx *ctx) { return ctx ? ctx->used : 0; }
+
+int fr_ctx_sm_count(const fr_ctx *ctx) { return ctx ? ctx->sm_count : 0; }
+
+// ----------------------------------------------------------------- market
+int fr_market_create(fr_ctx *ctx, const fr_market_desc *d, fr_market **out)
+{
+    FR_CHECK(ctx && d && out, FR_EINVAL, "fr_market_create: NULL argument");
+    *out = nullptr;
+    int rc = use_device(ctx);
+    if (rc) return rc;
+    fr_market *m = new (std::nothrow) fr_market();
+    FR_CHECK(m, FR_ENOMEM, "fr_market_create: out of host memory");
+    m->ctx = ctx;
+    m->task = d->task;
+    if (d->task == FR_TASK_STOCK) {
+        if (!(d->n_days >= 2 && d->n_assets >= 1 && d->n_assets <= FR_MAX_ASSETS &&
+              d->n_ind >= 0 && d->n_ind <= FR_MAX_INDICATORS && d->close &&
+              (d->ind || d->n_ind == 0))) {
+            delete m;
+            set_error("fr_market_create: stock market needs n_days >= 2, 1 <= n_assets <= 32, "
+                      "0 <= n_ind <= 16 and host tables");
+            return FR_EINVAL;
+        }
+        for (int64_t i = 0; i < (int64_t)d->n_days * d->n_assets; ++i) {
+            if (d->close[i] < 1) {
+                delete m;
+                set_error("fr_market_create: close[%lld] = %lld < 1 cent", (long long)i,
+                          (long long)d->close[i]);
+                return FR_EINVAL;
+            }
+        }
+        m->n_days = d->n_days;
+        m->K = d->n_assets;
+        m->I = d->n_ind;
+        const uint64_t cb = (uint64_t)m->n_days * m->K * 8;
+        const uint64_t ib = (uint64_t)m->n_days * m->I * m->K * 4;
+        if ((rc = dev_alloc(ctx, (void **)&m->close, cb)) ||
+            (rc = dev_alloc(ctx, (void **)&m->ind, ib ? ib : 16))) {
+            fr_market_destroy(m);
+            return rc;
+        }
+        m->bytes = cb + (ib ? ib : 16);
+        cudaError_t e = cudaMemcpy(m->close, d->close, cb, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && ib) e = cudaMemcpy(m->ind, d->ind, ib, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            fr_market_destroy(m);
+            return cuda_fail(e, "fr_market_create upload");
+        }
+    } else if (d->task == FR_TASK_CRYPTO) {
+        if (!(d->n_seconds >= 2 && d->mid && d->spread && d->fac)) {
+            delete m;
+            set_error("fr_market_create: crypto market needs n_seconds >= 2 and host tables");
+            return FR_EINVAL;
+        }
+        for (int64_t i = 0; i < d->n_seconds; ++i) {
+            if (d->mid[i] < 1 || (int64_t)d->spread[i] >= 2 * d->mid[i]) {
+                delete m;
+                set_error("fr_market_create: mid/spread at second %lld out of range", (long long)i);
+                return FR_EINVAL;
+            }
+        }
+        m->S = d->n_seconds;
+        m->K = 1;
+        const uint64_t mb = (uint64_t)m->S * 8, sb = (uint64_t)m->S, fb = (uint64_t)m->S * 32;
+        if ((rc = dev_alloc(ctx, (void **)&m->mid, mb)) ||
+            (rc = dev_alloc(ctx, (void **)&m->spread, sb)) ||
+            (rc = dev_alloc(ctx, (void **)&m->fac, fb))) {
+            fr_market_destroy(m);
+            return rc;
+        }
+        m->bytes = mb + sb + fb;
+        cudaError_t e = cudaMemcpy(m->mid, d->mid, mb, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(m->spread, d->spread, sb, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(m->fac, d->fac, fb, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            fr_market_destroy(m);
+            return cuda_fail(e, "fr_market_create upload");
+        }
+    } else {
+        delete m;
+        set_error("fr_market_create: unknown task %d", d->task);
+        return FR_EINVAL;
+    }
+    *out = m;
+    return FR_OK;
+}
+
+void fr_market_destroy(fr_market *m)
+{
+    if (!m) return;
+    cudaSetDevice(m->ctx->device);
+    if (m->task == FR_TASK_STOCK) {
+        dev_free(m->ctx, m->close, (uint64_t)m->n_days * m->K * 8);
+        uint64_t ib = (uint64_t)m->n_days * m->I * m->K * 4;
+        dev_free(m->ctx, m->ind, ib ? ib : 16);
+    } else {
+        dev_free(m->ctx, m->mid, (uint64_t)m->S * 8);
+        dev_free(m->ctx, m->spread, (uint64_t)m->S);
+        dev_free(m->ctx, m->fac, (uint64_t)m->S * 32);
+    }
+    delete m;
+}
+
+// -------------------------------------------------------------------- env
+
+int env_create(fr_ctx *ctx, const fr_env_desc *d, const fr_market *m, fr_env **out)
+{
+    FR_CHECK(ctx && d && m && out, FR_EINVAL, "env_create: NULL argument");
+    *out = nullptr;
+    FR_CHECK(d->task == m->task, FR_EINVAL, "env_create: env task %d on a market of task %d",
+             d->task, m->task);
+    FR_CHECK(d->n_envs >= 1 && d->window && d->start, FR_EINVAL,
+             "env_create: need n_envs >= 1, window[] and start[]");
+    FR_CHECK(d->init_cash >= 0, FR_EINVAL, "env_create: init_cash < 0");
+    const int N = d->n_envs;
+    const bool stock = d->task == FR_TASK_STOCK;
+    if (stock) {
+        FR_CHECK(d->hmax >= 1 && d->hmax <= 1000000, FR_EINVAL, "env_create: hmax %d not in 1..1e6",
+                 d->hmax);
+        FR_CHECK(d->fee_bps >= 0 && d->fee_bps <= BPS_ONE, FR_EINVAL,
+                 "env_create: fee_bps %d not in 0..10000", d->fee_bps);
+    } else {
+        FR_CHECK(d->pmax >= 1, FR_EINVAL, "env_create: pmax < 1");
+    }
+    const int64_t horizon = stock ? m->n_days : m->S;
+    std::vector<int32_t> Ke(N, stock ? m->K : 1);
+    for (int e = 0; e < N; ++e) {
+        if (stock && d->n_assets) Ke[e] = d->n_assets[e];
+        FR_CHECK(Ke[e] >= 1 && Ke[e] <= m->K, FR_EINVAL, "env_create: n_assets[%d] = %d not in 1..%d",
+                 e, Ke[e], m->K);
+        FR_CHECK(d->window[e] >= 2, FR_EINVAL, "env_create: window[%d] = %d < 2", e, d->window[e]);
+        FR_CHECK(d->start[e] >= 0 && (int64_t)d->start[e] + d->window[e] <= horizon, FR_EINVAL,
+                 "env_create: env %d window %d..%d runs past the market end %lld", e,
+                 d->start[e], d->start[e] + d->window[e] - 1, (long long)horizon);
+        if (stock && d->bps) {
+            for (int k = 0; k < m->K; ++k) {
+                const int b = d->bps[(int64_t)e * m->K + k];
+                FR_CHECK(b >= -100 && b <= 100, FR_EINVAL, "env_create: bps[%d][%d] = %d not in -100..100",
+                         e, k, b);
+            }
+        }
+    }
+    int rc = use_device(ctx);
+    if (rc) return rc;
+    fr_env *env = new (std::nothrow) fr_env();
+    FR_CHECK(env, FR_ENOMEM, "env_create: out of host memory");
+    env->ctx = ctx;
+    env->mkt = m;
+    EnvView &v = env->v;
+    v.task = d->task;
+    v.N = N;
+    v.K = stock ? m->K : 1;
+    v.I = stock ? m->I : 0;
+    v.D = stock ? 1 + 2 * m->K + m->I * m->K : FR_CRYPTO_OBS_DIM;
+    v.hmax = d->hmax;
+    v.fee_bps = d->fee_bps;
+    v.pmax = d->pmax;
+    v.auto_reset = d->auto_reset ? 1 : 0;
+    v.init_cash = d->init_cash;
+    v.ann = stock ? 252.0 : 1.0;
+    v.n_days = m->n_days;
+    v.S = m->S;
+    v.close = m->close;
+    v.ind = m->ind;
+    v.mid = m->mid;
+    v.spread = m->spread;
+    v.fac = m->fac;
+    const uint64_t bytes = carve_env(v, nullptr);
+    rc = dev_alloc(ctx, &env->block, bytes);
+    if (rc) {
+        delete env;
+        return rc;
+    }
+    env->bytes = bytes;
+    carve_env(v, (char *)env->block);
+    // host staging of the per-env constants
+    std::vector<int16_t> bps(stock ? (size_t)N * KP : 1, 0);
+    if (stock && d->bps)
+        for (int e = 0; e < N; ++e)
+            for (int k = 0; k < m->K; ++k) bps[(size_t)e * KP + k] = d->bps[(int64_t)e * m->K + k];
+    cudaError_t err = cudaMemcpy((void *)v.Ke, Ke.data(), 4ull * N, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy((void *)v.start, d->start, 4ull * N, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy((void *)v.W, d->window, 4ull * N, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess)
+        err = cudaMemcpy((void *)v.bps, bps.data(), bps.size() * 2, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemset(v.err, 0, 8);
+    if (err == cudaSuccess) err = launch_env_reset(v, 0);
+    if (err == cudaSuccess) err = cudaDeviceSynchronize();
+    if (err != cudaSuccess) {
+        env_destroy(env);
+        return cuda_fail(err, "env_create upload");
+    }
+    *out = env;
+    return FR_OK;
+}
+
+void env_destroy(fr_env *env)
+{
+    if (!env) return;
+    cudaSetDevice(env->ctx->device);
+    dev_free(env->ctx, env->block, env->bytes);
+    dev_free(env->ctx, env->scratch, env->scratch_bytes);
+    delete env;
+}
+
+int env_dims(const fr_env *env, int32_t *n_envs, int32_t *obs_dim, int32_t *n_assets)
+{
+    FR_CHECK(env, FR_EINVAL, "env_dims: NULL env");
+    if (n_envs) *n_envs = env->v.N;
+    if (obs_dim) *obs_dim = env->v.D;
+    if (n_assets) *n_assets = env->v.K;
+    return FR_OK;
+}
+
+int env_reset(fr_env *env, void *stream)
+{
+    FR_CHECK(env, FR_EINVAL, "env_reset: NULL env");
+    int rc = use_device(env->ctx);
+    if (rc) return rc;
+    FR_CUDA(launch_env_reset(env->v, (cudaStream_t)stream));
+    return FR_OK;
+}
+
+int env_step(fr_env *env, const fr_action *a, const fr_step_out *o, void *stream)
+{
+    FR_CHECK(env && a && a->data, FR_EINVAL, "env_step: NULL env or action");
+    const bool stock = env->v.task == FR_TASK_STOCK;
+    FR_CHECK(stock ? (a->kind == FR_ACT_I32_SHARES || a->kind == FR_ACT_F32_UNIT)
+                   : a->kind == FR_ACT_U8_DISCRETE,
+             FR_EINVAL, "env_step: action kind %d does not fit task %d", a->kind, env->v.task);
+    int rc = use_device(env->ctx);
+    if (rc) return rc;
+    fr_step_out none = {nullptr, nullptr, nullptr, nullptr};
+    if (!o) o = &none;
+    FR_CUDA(launch_env_step(env->v, a->kind, a->data, o->rew, o->rew_f32, o->done, o->obs,
+                            env->v.D, (cudaStream_t)stream));
+    return FR_OK;
+}
+
+int env_observe(fr_env *env, float *obs, int32_t ld, void *stream)
+{
+    FR_CHECK(env && obs && ld >= env->v.D, FR_EINVAL, "env_observe: need obs and ld >= D");
+    int rc = use_device(env->ctx);
+    if (rc) return rc;
+    FR_CUDA(launch_env_observe(env->v, obs, ld, (cudaStream_t)stream));
+    return FR_OK;
+}
+
+int env_get_state(fr_env *env, int64_t *cash, int32_t *hold, int32_t *steps, uint8_t *done,
+                  void *stream)
+{
+    FR_CHECK(env, FR_EINVAL, "env_get_state: NULL env");
+    int rc = use_device(env->ctx);
+    if (rc) return rc;
+    FR_CUDA(launch_env_get_state(env->v, cash, hold, steps, done, (cudaStream_t)stream));
+    return FR_OK;
+}
+
+int env_metrics(fr_env *env, double *metrics, void *stream)
+{
+    FR_CHECK(env && metrics, FR_EINVAL, "env_metrics: NULL argument");
+    int rc = use_device(env->ctx);
+    if (rc) return rc;
+    FR_CUDA(launch_env_metrics(env->v, metrics, (cudaStream_t)stream));
+    return FR_OK;
+}
+
+
+int env_snapshot(fr_env *env, void *host_buf, size_t cap, size_t *len)
+{
+    FR_CHECK(env && len, FR_EINVAL, "env_snapshot: NULL argument");
+    const uint64_t off = (uint64_t)((char *)env->v.cash - (char *)env->block);
+    const uint64_t sb = env->bytes - off;
+    *len = sizeof(SnapHeader) + sb;
+    if (!host_buf) return FR_OK;
+    FR_CHECK(cap >= *len, FR_EINVAL, "env_snapshot: buffer of %zu bytes < %zu needed", cap, *len);
+    int rc = use_device(env->ctx);
+    if (rc) return rc;
+    SnapHeader h{kSnapMagic, 1u, env->v.task, env->v.N, env->v.K, env->v.I, off, sb};
+    FR_CUDA(cudaDeviceSynchronize());
+    memcpy(host_buf, &h, sizeof(h));
+    FR_CUDA(cudaMemcpy((char *)host_buf + sizeof(h), env->v.cash, sb, cudaMemcpyDeviceToHost));
+    return FR_OK;
+}
+
+int env_restore(fr_env *env, const void *host_buf, size_t len)
+{
+    FR_CHECK(env && host_buf && len >= sizeof(SnapHeader), FR_EINVAL, "env_restore: bad buffer");
+    SnapHeader h;
+    memcpy(&h, host_buf, sizeof(h));
+    const uint64_t off = (uint64_t)((char *)env->v.cash - (char *)env->block);
+    FR_CHECK(h.magic == kSnapMagic && h.version == 1u && h.task == env->v.task && h.N == env->v.N &&
+                 h.K == env->v.K && h.I == env->v.I && h.state_off == off &&
+                 h.state_bytes == env->bytes - off && len == sizeof(h) + h.state_bytes,
+             FR_EINVAL, "env_restore: snapshot does not match this env's task and shape");
+    int rc = use_device(env->ctx);
+    if (rc) return rc;
+    FR_CUDA(cudaDeviceSynchronize());
+    FR_CUDA(cudaMemcpy(env->v.cash, (const char *)host_buf + sizeof(h), h.state_bytes,
+                       cudaMemcpyHostToDevice));
+    return FR_OK;
+}
+
+int env_error_count(fr_env *env, uint64_t *count)
+{
+    FR_CHECK(env && count, FR_EINVAL, "env_error_count: NULL argument");
+    int rc = use_device(env->ctx);
+    if (rc) return rc;
+    unsigned long long c = 0;
+    FR_CUDA(cudaMemcpy(&c, env->v.err, 8, cudaMemcpyDeviceToHost));
+    *count = c;
+    return FR_OK;
+}
+
+// --------------------------------------------------------------- ensemble
+int ensemble_create(fr_ctx *ctx, const fr_ensemble_desc *d, fr_ensemble **out)
+{
+    FR_CHECK(ctx && d && out && d->dims && d->params, FR_EINVAL, "ensemble_create: NULL argument");
+    *out = nullptr;
+    FR_CHECK(d->n_agents >= 1 && d->n_agents <= MAX_AGENTS, FR_EINVAL,
+             "ensemble_create: n_agents %d not in 1..8", d->n_agents);
+    FR_CHECK(d->n_layers >= 1 && d->n_layers <= MAX_LAYERS, FR_EINVAL,
+             "ensemble_create: n_layers %d not in 1..4", d->n_layers);
+    for (int l = 0; l <= d->n_layers; ++l)
+        FR_CHECK(d->dims[l] >= 1 && d->dims[l] <= 4096, FR_EINVAL, "ensemble_create: dims[%d] = %d", l,
+                 d->dims[l]);
+    for (int l = 1; l < d->n_layers; ++l)
+        FR_CHECK(d->dims[l] <= MAX_HIDDEN, FR_EINVAL, "ensemble_create: hidden width %d > 256",
+                 d->dims[l]);
+    FR_CHECK(d->precision >= FR_PREC_FP32 && d->precision <= FR_PREC_FP8, FR_EINVAL,
+             "ensemble_create: precision %d", d->precision);
+    FR_CHECK(d->combine == FR_COMBINE_MEAN || d->combine == FR_COMBINE_VOTE, FR_EINVAL,
+             "ensemble_create: combine %d", d->combine);
+    FR_CHECK(d->combine != FR_COMBINE_VOTE || d->dims[d->n_layers] <= 3, FR_EINVAL,
+             "ensemble_create: a vote needs at most 3 actions");
+    int rc = use_device(ctx);
+    if (rc) return rc;
+    fr_ensemble *e = new (std::nothrow) fr_ensemble();
+    FR_CHECK(e, FR_ENOMEM, "ensemble_create: out of host memory");
+    e->ctx = ctx;
+    e->M = d->n_agents;
+    e->L = d->n_layers;
+    for (int l = 0; l <= e->L; ++l) e->dims[l] = d->dims[l];
+    e->precision = d->precision;
+    e->combine = d->combine;
+    e->out_act = d->out_act ? 1 : 0;
+    int64_t off = 0;
+    for (int l = 0; l < e->L; ++l) {
+        e->w_off[l] = off;
+        off += (int64_t)e->dims[l + 1] * e->dims[l];
+        e->b_off[l] = off;
+        off += e->dims[l + 1];
+    }
+    e->P = off;
+    for (int j = 0; j < e->M; ++j) e->host_weights[j] = d->weights ? d->weights[j] : 1.0f / (float)e->M;
+    const uint64_t pb = (uint64_t)e->M * e->P * 4;
+    if ((rc = dev_alloc(ctx, (void **)&e->params, pb)) ||
+        (rc = dev_alloc(ctx, (void **)&e->weights, 4ull * MAX_AGENTS))) {
+        ensemble_destroy(e);
+        return rc;
+    }
+    e->bytes = pb + 4ull * MAX_AGENTS;
+    cudaError_t err = cudaMemcpy(e->params, d->params, pb, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess)
+        err = cudaMemcpy(e->weights, e->host_weights, 4ull * MAX_AGENTS, cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) {
+        ensemble_destroy(e);
+        return cuda_fail(err, "ensemble_create upload");
+    }
+    if (e->precision != FR_PREC_FP32) {
+        rc = tc_create(e);
+        if (rc) {
+            ensemble_destroy(e);
+            return rc;
+        }
+    }
+    *out = e;
+    return FR_OK;
+}
+
+void ensemble_destroy(fr_ensemble *e)
+{
+    if (!e) return;
+    cudaSetDevice(e->ctx->device);
+    tc_destroy(e);
+    dev_free(e->ctx, e->params, (uint64_t)e->M * e->P * 4);
+    dev_free(e->ctx, e->weights, 4ull * MAX_AGENTS);
+    delete e;
+}
+
+
+int ensemble_forward(const fr_ensemble *e, const float *obs, int32_t n, float *y, void *stream)
+{
+    FR_CHECK(e && obs && y && n >= 0, FR_EINVAL, "ensemble_forward: bad argument");
+    if (n == 0) return FR_OK;
+    int rc = use_device(e->ctx);
+    if (rc) return rc;
+    return forward_any(e, obs, e->dims[0], n, y, (cudaStream_t)stream);
+}
+
+int ensemble_act(const fr_ensemble *e, const float *obs, int32_t n, void *act, void *stream)
+{
+    FR_CHECK(e && obs && act && n >= 0, FR_EINVAL, "ensemble_act: bad argument");
+    if (n == 0) return FR_OK;
+    int rc = use_device(e->ctx);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int out = e->dims[e->L];
+    float *y = nullptr;
+    FR_CUDA(cudaMallocAsync((void **)&y, 4ull * e->M * n * out, s));
+    rc = forward_any(e, obs, e->dims[0], n, y, s);
+    cudaError_t err = cudaSuccess;
+    if (!rc) {
+        if (e->combine == FR_COMBINE_MEAN)
+            err = launch_combine_mean(y, (int64_t)n * out, out, e->weights, e->M, n, out,
+                                      (float *)act, out, s);
+        else
+            err = launch_combine_vote(y, (int64_t)n * out, out, e->M, n, out, (uint8_t *)act, s);
+    }
+    cudaFreeAsync(y, s);
+    if (rc) return rc;
+    FR_CUDA(err);
+    return FR_OK;
+}
+
+// ---------------------------------------------------------------- rollout
+int rollout(fr_env *env, const fr_ensemble *e, int32_t T, const fr_traj *traj, double *metrics,
+            void *stream)
+{
+    FR_CHECK(env && e && T >= 0, FR_EINVAL, "rollout: bad argument");
+    const EnvView &v = env->v;
+    const bool stock = v.task == FR_TASK_STOCK;
+    FR_CHECK(e->dims[0] == v.D, FR_EINVAL, "rollout: ensemble input %d != observation dim %d",
+             e->dims[0], v.D);
+    FR_CHECK(stock ? (e->combine == FR_COMBINE_MEAN && e->dims[e->L] == v.K)
+                   : (e->combine == FR_COMBINE_VOTE && e->dims[e->L] == 3),
+             FR_EINVAL, "rollout: ensemble output / combine does not fit the task");
+    fr_traj none = {nullptr, 0, nullptr, nullptr, nullptr, nullptr};
+    if (!traj) traj = &none;
+    const int ld = traj->obs_ld ? traj->obs_ld : v.D;
+    FR_CHECK(!traj->obs || ld >= v.D, FR_EINVAL, "rollout: traj obs_ld %d < D %d", ld, v.D);
+    int rc = use_device(env->ctx);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (e->precision != FR_PREC_FP32 && tc_rollout_supported(env, e))
+        return tc_rollout(env, e, T, traj, metrics, s);
+
+    // plain path: one launch per stage per step
+    const int N = v.N, out = e->dims[e->L];
+    const uint64_t obs_b = (4ull * N * v.D + 255) & ~255ull;
+    const uint64_t act_b = ((stock ? 4ull * N * v.K : (uint64_t)N) + 255) & ~255ull;
+    const uint64_t y_b = (4ull * e->M * N * out + 255) & ~255ull;
+    const uint64_t need = obs_b + act_b + y_b + plain_scratch_bytes(e, N);
+    if (env->scratch_bytes < need) {
+        FR_CUDA(cudaStreamSynchronize(s));
+        dev_free(env->ctx, env->scratch, env->scratch_bytes);
+        env->scratch = nullptr;
+        env->scratch_bytes = 0;
+        rc = dev_alloc(env->ctx, &env->scratch, need);
+        if (rc) return rc;
+        env->scratch_bytes = need;
+    }
+    char *sc = (char *)env->scratch;
+    float *obs_s = (float *)sc;
+    void *act_s = sc + obs_b;
+    float *y = (float *)(sc + obs_b + act_b);
+    float *hid = (float *)(sc + obs_b + act_b + y_b);
+    for (int t = 0; t < T; ++t) {
+        const int64_t row = (int64_t)t * N;
+        float *obs_t = traj->obs ? traj->obs + row * ld : obs_s;
+        const int ldt = traj->obs ? ld : v.D;
+        FR_CUDA(launch_env_observe(v, obs_t, ldt, s));
+        if (e->precision == FR_PREC_FP32) {
+            FR_CUDA(forward_plain(e, obs_t, ldt, N, y, hid, s));
+        } else {
+            rc = tc_forward(e, obs_t, ldt, N, y, s);
+            if (rc) return rc;
+        }
+        void *act_t = traj->act ? (stock ? (void *)((float *)traj->act + row * v.K)
+                                         : (void *)((uint8_t *)traj->act + row))
+                                : act_s;
+        if (stock)
+            FR_CUDA(launch_combine_mean(y, (int64_t)N * out, out, e->weights, e->M, N, out,
+                                        (float *)act_t, v.K, s));
+        else
+            FR_CUDA(launch_combine_vote(y, (int64_t)N * out, out, e->M, N, out, (uint8_t *)act_t, s));
+        FR_CUDA(launch_env_step(v, stock ? FR_ACT_F32_UNIT : FR_ACT_U8_DISCRETE, act_t,
+                                traj->rew ? traj->rew + row : nullptr,
+                                traj->rew_f32 ? traj->rew_f32 + row : nullptr,
+                                traj->done ? traj->done + row : nullptr, nullptr, 0, s));
+    }
+    if (metrics) FR_CUDA(launch_env_metrics(v, metrics, s));
+    return FR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,184 @@
+// fr_common.cuh -- internal structures shared by the library's translation
+// units: the device view of an environment batch, the ensemble's device
+// images, error plumbing and launch helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/finrl_gb300.h"
+
+namespace fr {
+
+// ----------------------------------------------------------------- errors
+void set_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define FR_CUDA(call)                                              \
+    do {                                                           \
+        cudaError_t e__ = (call);                                  \
+        if (e__ != cudaSuccess) return ::fr::cuda_fail(e__, #call); \
+    } while (0)
+
+#define FR_CHECK(cond, code, ...)            \
+    do {                                     \
+        if (!(cond)) {                       \
+            ::fr::set_error(__VA_ARGS__);    \
+            return (code);                   \
+        }                                    \
+    } while (0)
+
+// --------------------------------------------------------- device layouts
+constexpr int KP = 32;          // padded asset slots per env (one per lane)
+constexpr int BPS_ONE = 10000;  // basis points per unit
+
+// Device view of an env batch, passed by value to kernels.  Per-env state
+// is structure-of-arrays; holdings and perturbations are [N][32] so one
+// env's row is a single 128-byte (resp. 64-byte) line.
+struct EnvView {
+    int task, N, K, I, D;
+    int hmax, fee_bps, pmax, auto_reset;
+    int64_t init_cash;
+    double ann;                 // Sharpe annualisation factor A
+    // market
+    int n_days;
+    int64_t S;
+    const int64_t *close;       // [n_days][K]
+    const float *ind;           // [n_days][I][K]
+    const int64_t *mid;         // [S]
+    const uint8_t *spread;      // [S]
+    const float *fac;           // [S][8]
+    // per-env constants
+    const int32_t *Ke;          // [N]
+    const int32_t *start;       // [N]
+    const int32_t *W;           // [N]
+    const int16_t *bps;         // [N][32]
+    // state
+    int64_t *cash;              // [N]
+    int32_t *hold;              // stock [N][32] shares; crypto [N] lots
+    int32_t *t;                 // [N] steps taken this episode
+    uint8_t *done;              // [N]
+    // FP64 episode accumulators
+    double *mu, *m2, *mdd;      // [N]
+    int64_t *peak, *vlast;      // [N]
+    double *latched;            // [N][4]: metrics of the last auto-reset episode + valid flag
+    unsigned long long *err;    // [1] non-finite / invalid actions seen
+};
+
+}  // namespace fr
+
+// ---------------------------------------------------------- opaque handles
+struct fr_ctx {
+    int device;
+    int sm_count;
+    uint64_t budget;
+    uint64_t used;
+    int cc_major, cc_minor;
+};
+
+struct fr_market {
+    fr_ctx *ctx;
+    int task;
+    int n_days, K, I;
+    int64_t S;
+    int64_t *close;
+    float *ind;
+    int64_t *mid;
+    uint8_t *spread;
+    float *fac;
+    uint64_t bytes;
+};
+
+struct fr_ensemble;
+
+struct fr_env {
+    fr_ctx *ctx;
+    const fr_market *mkt;
+    fr::EnvView v;
+    void *block;                // single allocation holding all per-env arrays
+    uint64_t bytes;
+    // scratch for the plain rollout path (grown on demand)
+    void *scratch;
+    uint64_t scratch_bytes;
+};
+
+namespace fr {
+
+// Account `bytes` against the context budget; FR_ENOMEM when it would not fit.
+int ctx_reserve(fr_ctx *ctx, uint64_t bytes);
+void ctx_release(fr_ctx *ctx, uint64_t bytes);
+// cudaMalloc with budget accounting.
+int dev_alloc(fr_ctx *ctx, void **p, uint64_t bytes);
+void dev_free(fr_ctx *ctx, void *p, uint64_t bytes);
+
+inline unsigned ceil_div(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+// ------------------------------------------------------- kernel launchers
+// env kernels (fr_env_kernels.cu)
+cudaError_t launch_env_reset(const EnvView &v, cudaStream_t s);
+cudaError_t launch_env_step(const EnvView &v, int kind, const void *act,
+                            int64_t *rew, float *rew_f32, uint8_t *done,
+                            float *obs, int ld_obs, cudaStream_t s);
+cudaError_t launch_env_observe(const EnvView &v, float *obs, int ld, cudaStream_t s);
+cudaError_t launch_env_metrics(const EnvView &v, double *out, cudaStream_t s);
+cudaError_t launch_env_get_state(const EnvView &v, int64_t *cash, int32_t *hold,
+                                 int32_t *steps, uint8_t *done, cudaStream_t s);
+
+}  // namespace fr
+
+// ------------------------------------------------------------- ensembles
+namespace fr {
+constexpr int MAX_AGENTS = 8;
+constexpr int MAX_LAYERS = 4;
+constexpr int MAX_HIDDEN = 256;
+struct TcImage;   // tensor-core weight images (fr_tc.cu)
+}  // namespace fr
+
+struct fr_ensemble {
+    fr_ctx *ctx;
+    int M, L;
+    int dims[fr::MAX_LAYERS + 1];
+    int precision, combine, out_act;
+    int64_t P;                           // fp32 parameters per agent
+    int64_t w_off[fr::MAX_LAYERS], b_off[fr::MAX_LAYERS];
+    float *params;                       // device [M][P] fp32 master copy
+    float *weights;                      // device [M] combine weights
+    float host_weights[fr::MAX_AGENTS];
+    fr::TcImage *tc;                     // tensor-core images or NULL
+    uint64_t bytes;
+};
+
+namespace fr {
+// plain fp32 kernels (fr_plain.cu)
+cudaError_t launch_dense_f32(const float *X, int64_t x_stride, int ldx, const float *P,
+                             int64_t p_stride, int64_t w_off, int64_t b_off, float *Y,
+                             int64_t y_stride, int ldy, int n, int fin, int fout, int act, int M,
+                             cudaStream_t s);
+cudaError_t launch_combine_mean(const float *Y, int64_t y_stride, int ldy, const float *w, int M,
+                                int n, int K, float *out, int ldo, cudaStream_t s);
+cudaError_t launch_combine_vote(const float *Y, int64_t y_stride, int ldy, int M, int n, int nact,
+                                uint8_t *out, cudaStream_t s);
+
+// Bytes of scratch the plain forward needs for n rows (two hidden buffers).
+inline uint64_t plain_scratch_bytes(const fr_ensemble *e, int n)
+{
+    int w = 0;
+    for (int l = 1; l < e->L; ++l) w = e->dims[l] > w ? e->dims[l] : w;
+    return 2ull * (uint64_t)e->M * (uint64_t)n * (uint64_t)w * sizeof(float);
+}
+// Per-agent outputs y[M][n][dims[L]] from obs[n][ld] through the fp32 path.
+cudaError_t forward_plain(const fr_ensemble *e, const float *obs, int ld, int n, float *y,
+                          float *scratch, cudaStream_t s);
+
+// tensor-core path (fr_tc.cu)
+int tc_create(fr_ensemble *e);
+void tc_destroy(fr_ensemble *e);
+// Per-agent outputs through the tcgen05 kernels; obs rows of stride ld.
+int tc_forward(const fr_ensemble *e, const float *obs, int ld, int n, float *y, cudaStream_t s);
+// Whether the fused persistent rollout supports this env / ensemble pair.
+bool tc_rollout_supported(const fr_env *env, const fr_ensemble *e);
+int tc_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, double *metrics,
+               cudaStream_t s);
+}  // namespace fr

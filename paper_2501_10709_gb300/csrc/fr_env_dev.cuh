@@ -1,0 +1,308 @@
+// fr_env_dev.cuh -- device-side accounting of the trading MDP (Sec. 3.1):
+// integer-cent prices with the Sec. 5.1 per-asset perturbation, sells then
+// greedy buys with a rounded-up fee (Sec. 3.2 transaction costs), the
+// total-asset value v = b + p^T h and the reward v_{t+1} - v_t, and the FP64
+// episode accumulators behind the Sharpe ratio (Sec. 5.2.1) and the maximum
+// drawdown (Sec. 6.1).  Every floating-point step uses an explicitly rounded
+// intrinsic so that no FMA contraction changes a result.
+#pragma once
+
+#include "fr_common.cuh"
+
+namespace fr {
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
+
+// Per-asset price after the basis-point change, rounded half up, >= 1 cent.
+__device__ __forceinline__ int64_t perturb(int64_t close, int bps)
+{
+    const int64_t num = close * (int64_t)(BPS_ONE + bps) + BPS_ONE / 2;
+    const int64_t p = num / BPS_ONE;
+    return p < 1 ? 1 : p;
+}
+
+// ceil(g * fee_bps / 1e4) for g >= 0
+__device__ __forceinline__ int64_t fee_of(int64_t g, int fee_bps)
+{
+    return (g * (int64_t)fee_bps + (BPS_ONE - 1)) / BPS_ONE;
+}
+
+__device__ __forceinline__ int64_t cost_of(int64_t n, int64_t p, int fee_bps)
+{
+    const int64_t g = n * p;
+    return g + fee_of(g, fee_bps);
+}
+
+// Largest n with cost_of(n) <= c, for c >= 0, when the caller knows the
+// answer is small (below the order it could not fully fill).  The quotient
+// floor(c*1e4 / (p*(1e4+fee))) is estimated in fp32 and corrected exactly
+// with integer products; the correction loops are bounded because the
+// estimate is within one of the true quotient for quotients below 2^20.
+__device__ __forceinline__ int64_t afford(int64_t c, int64_t p, int fee_bps)
+{
+    if (c <= 0) return 0;
+    const int64_t X = c * BPS_ONE;
+    const int64_t Dn = p * (int64_t)(BPS_ONE + fee_bps);
+    int64_t n = (int64_t)__fdiv_rn((float)X, (float)Dn);
+#pragma unroll 1
+    for (int i = 0; i < 8 && n > 0 && n * Dn > X; ++i) --n;
+#pragma unroll 1
+    for (int i = 0; i < 8 && (n + 1) * Dn <= X; ++i) ++n;
+    if (n > 0 && cost_of(n, p, fee_bps) > c) --n;
+    return n;
+}
+
+// Action in [-1,1] -> share change trunc(a * hmax).  __fmul_rz keeps the
+// product on the zero side of the exact value and integers up to hmax are
+// representable, so the truncation equals that of the exact product.
+__device__ __forceinline__ int32_t discretise(float a, int hmax, bool &bad)
+{
+    bad = !isfinite(a);
+    if (bad) a = 0.0f;
+    a = fminf(fmaxf(a, -1.0f), 1.0f);
+    return (int32_t)__fmul_rz(a, (float)hmax);
+}
+
+__device__ __forceinline__ int64_t warp_sum(int64_t x)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULL_MASK, x, o);
+    return x;
+}
+
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t x, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(FULL_MASK, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+__device__ __forceinline__ float obs_scale(int64_t x, double c)
+{
+    return __double2float_rn(__dmul_rn((double)x, c));
+}
+
+__device__ __forceinline__ float reward_f32(int64_t r)
+{
+    return __double2float_rn(__dmul_rn((double)r, 1e-6));
+}
+
+// ---------------------------------------------------- FP64 episode metrics
+// One period: rho = v1/v0 - 1, Welford mean / sum of squared deviations,
+// running peak and drawdown min(v/peak - 1).  n is the period count after
+// this one.
+__device__ __forceinline__ void acc_push(double &mu, double &m2, double &mdd,
+                                         int64_t &peak, int64_t &vlast, int n,
+                                         int64_t v0, int64_t v1)
+{
+    const double rho = __dsub_rn(__ddiv_rn((double)v1, (double)v0), 1.0);
+    const double delta = __dsub_rn(rho, mu);
+    mu = __dadd_rn(mu, __ddiv_rn(delta, (double)n));
+    m2 = __dadd_rn(m2, __dmul_rn(delta, __dsub_rn(rho, mu)));
+    if (v1 > peak) peak = v1;
+    const double dd = __dsub_rn(__ddiv_rn((double)v1, (double)peak), 1.0);
+    if (dd < mdd) mdd = dd;
+    vlast = v1;
+}
+
+// {cumulative return, Sharpe = (mu - r_f) / sd * sqrt(A), max drawdown}
+__device__ __forceinline__ void acc_final(double mu, double m2, double mdd,
+                                          int64_t vlast, int64_t v0, int n,
+                                          double ann, double *out)
+{
+    out[0] = __dsub_rn(__ddiv_rn((double)vlast, (double)v0), 1.0);
+    double sh = 0.0;
+    if (n >= 2 && m2 != 0.0) {
+        const double sd = __dsqrt_rn(__ddiv_rn(m2, (double)(n - 1)));
+        sh = __dmul_rn(__ddiv_rn(__dsub_rn(mu, 0.0), sd), __dsqrt_rn(ann));
+    }
+    out[1] = sh;
+    out[2] = mdd;
+}
+
+// Episode bookkeeping after a step of env e (one thread): stores the new
+// accumulators, or -- when the window is finished and auto_reset is on --
+// latches the finished episode's metrics and restarts the env.
+__device__ __forceinline__ void finish_step(const EnvView &v, int e, int64_t cash,
+                                            int t1, bool done, int64_t v0, int64_t v1)
+{
+    double mu = v.mu[e], m2 = v.m2[e], mdd = v.mdd[e];
+    int64_t peak = v.peak[e], vlast = v.vlast[e];
+    acc_push(mu, m2, mdd, peak, vlast, t1, v0, v1);
+    if (done && v.auto_reset) {
+        double *L = v.latched + (int64_t)e * 4;
+        acc_final(mu, m2, mdd, vlast, v.init_cash, t1, v.ann, L);
+        L[3] = 1.0;
+        v.cash[e] = v.init_cash;
+        v.t[e] = 0;
+        v.done[e] = 0;
+        v.mu[e] = 0.0;
+        v.m2[e] = 0.0;
+        v.mdd[e] = 0.0;
+        v.peak[e] = v.init_cash;
+        v.vlast[e] = v.init_cash;
+    } else {
+        v.cash[e] = cash;
+        v.t[e] = t1;
+        v.done[e] = done ? 1 : 0;
+        v.mu[e] = mu;
+        v.m2[e] = m2;
+        v.mdd[e] = mdd;
+        v.peak[e] = peak;
+        v.vlast[e] = vlast;
+    }
+}
+
+// ------------------------------------------------------------ stock, warp
+// One step of stock env e by one warp, lane = asset.  q is this lane's
+// share order.  Returns the reward (same on every lane) and the done flag.
+__device__ __forceinline__ int64_t stock_step_warp(const EnvView &v, int e, int lane,
+                                                   int32_t q, bool &done_out)
+{
+    if (v.done[e]) {
+        done_out = true;
+        return 0;
+    }
+    const int K = v.K;
+    const int Ke = v.Ke[e];
+    const int t0 = v.t[e];
+    const int d = v.start[e] + t0;
+    const bool act = lane < Ke;
+    const int fee = v.fee_bps;
+    const int bps = act ? (int)v.bps[(int64_t)e * KP + lane] : 0;
+    const int64_t p = act ? perturb(__ldg(v.close + (int64_t)d * K + lane), bps) : 0;
+    int64_t h = act ? (int64_t)v.hold[(int64_t)e * KP + lane] : 0;
+    int64_t cash = v.cash[e];
+    if (!act) q = 0;
+    const int64_t v0 = cash + warp_sum(p * h);
+
+    // sells: independent per asset, capped at the holding
+    int64_t net = 0;
+    if (q < 0) {
+        int64_t n = -(int64_t)q;
+        if (n > h) n = h;
+        const int64_t g = n * p;
+        h -= n;
+        net = g - fee_of(g, fee);
+    }
+    cash += warp_sum(net);
+
+    // buys: greedy in ascending asset order.  Each round drops the assets
+    // that cannot afford one share, fills every order in full up to the
+    // first one whose prefix cost exceeds the cash, fills that one as far as
+    // the remaining cash allows, and continues after it.
+    const int64_t want = q > 0 ? (int64_t)q : 0;
+    int64_t full = 0, one = 0, nb = 0;
+    if (want > 0) {
+        full = cost_of(want, p, fee);
+        one = cost_of(1, p, fee);
+    }
+    unsigned pending = __ballot_sync(FULL_MASK, want > 0);
+#pragma unroll 1
+    while (pending) {
+        bool mine = (pending >> lane) & 1u;
+        pending &= ~__ballot_sync(FULL_MASK, mine && one > cash);
+        if (!pending) break;
+        mine = (pending >> lane) & 1u;
+        const int64_t x = mine ? full : 0;
+        const int64_t pre = warp_incl_scan(x, lane);
+        const unsigned fail = __ballot_sync(FULL_MASK, mine && pre > cash);
+        if (fail == 0u) {
+            if (mine) nb = want;
+            cash -= __shfl_sync(FULL_MASK, pre, 31);
+            break;
+        }
+        const int f = __ffs(fail) - 1;
+        if (mine && lane < f) nb = want;
+        int64_t cf = cash - (pre - x);
+        if (lane == f) {
+            const int64_t n = afford(cf, p, fee);
+            nb = n;
+            cf -= cost_of(n, p, fee);
+        }
+        cash = __shfl_sync(FULL_MASK, cf, f);
+        pending &= ~((2u << f) - 1u);
+    }
+    h += nb;
+
+    // next day: value at the new prices, reward
+    const int t1 = t0 + 1;
+    const int64_t p1 = act ? perturb(__ldg(v.close + (int64_t)(d + 1) * K + lane), bps) : 0;
+    const int64_t v1 = cash + warp_sum(p1 * h);
+    const bool done = t1 == v.W[e] - 1;
+    if (act) v.hold[(int64_t)e * KP + lane] = (done && v.auto_reset) ? 0 : (int32_t)h;
+    if (lane == 0) finish_step(v, e, cash, t1, done, v0, v1);
+    done_out = done;
+    return v1 - v0;
+}
+
+// Observation of stock env e's current state into o[0..D), lane = asset:
+// [cash*1e-8, p_k*1e-4, h_k*1e-2, f_{i,k} indicator-major], zero beyond Ke.
+__device__ __forceinline__ void stock_obs_warp(const EnvView &v, int e, int lane, float *o)
+{
+    const int K = v.K, I = v.I;
+    const int Ke = v.Ke[e];
+    const int d = v.start[e] + v.t[e];
+    const bool act = lane < Ke;
+    if (lane == 0) o[0] = obs_scale(v.cash[e], 1e-8);
+    if (lane < K) {
+        float pv = 0.0f, hv = 0.0f;
+        if (act) {
+            const int64_t p = perturb(__ldg(v.close + (int64_t)d * K + lane),
+                                      v.bps[(int64_t)e * KP + lane]);
+            pv = obs_scale(p, 1e-4);
+            hv = obs_scale(v.hold[(int64_t)e * KP + lane], 1e-2);
+        }
+        o[1 + lane] = pv;
+        o[1 + K + lane] = hv;
+        const float *f = v.ind + (int64_t)d * I * K;
+        for (int i = 0; i < I; ++i) o[1 + 2 * K + i * K + lane] = act ? __ldg(f + i * K + lane) : 0.0f;
+    }
+}
+
+// ---------------------------------------------------------- crypto, thread
+// One step of crypto env e by one thread; u in {0 sell, 1 hold, 2 buy}.
+__device__ __forceinline__ int64_t crypto_step_thread(const EnvView &v, int e, int u,
+                                                      bool &done_out)
+{
+    if (v.done[e]) {
+        done_out = true;
+        return 0;
+    }
+    const int t0 = v.t[e];
+    const int d = v.start[e] + t0;
+    int64_t cash = v.cash[e];
+    int pos = v.hold[e];
+    const int64_t m0 = __ldg(v.mid + d);
+    const int64_t s = (int64_t)__ldg(v.spread + d);
+    const int64_t v0 = cash + (int64_t)pos * m0;
+    const int64_t bid = m0 - s / 2, ask = bid + s;
+    if (u == 2) {
+        if (pos < v.pmax && cash >= ask) { pos += 1; cash -= ask; }
+    } else if (u == 0) {
+        if (pos > 0) { pos -= 1; cash += bid; }
+    }
+    const int t1 = t0 + 1;
+    const int64_t v1 = cash + (int64_t)pos * __ldg(v.mid + d + 1);
+    const bool done = t1 == v.W[e] - 1;
+    v.hold[e] = (done && v.auto_reset) ? 0 : pos;
+    finish_step(v, e, cash, t1, done, v0, v1);
+    done_out = done;
+    return v1 - v0;
+}
+
+// [cash*1e-8, pos/pmax, fac_0..7] of crypto env e's current state
+__device__ __forceinline__ void crypto_obs_thread(const EnvView &v, int e, float *o)
+{
+    const int d = v.start[e] + v.t[e];
+    o[0] = obs_scale(v.cash[e], 1e-8);
+    o[1] = __double2float_rn(__ddiv_rn((double)v.hold[e], (double)v.pmax));
+    const float *f = v.fac + (int64_t)d * FR_CRYPTO_FACTORS;
+#pragma unroll
+    for (int i = 0; i < FR_CRYPTO_FACTORS; ++i) o[2 + i] = __ldg(f + i);
+}
+
+}  // namespace fr

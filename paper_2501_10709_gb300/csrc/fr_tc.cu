@@ -1,0 +1,408 @@
+// fr_tc.cu -- the ensemble's actor MLPs on the 5th-generation tensor cores.
+//
+// One CTA computes one agent's network (Sec. 6.1: dense layers, ReLU hidden
+// activations) for a tile of 128 observation rows:
+//   * the weights are pre-packed on the host into BF16 "chunks" laid out
+//     exactly as the tcgen05 K-major no-swizzle canonical form, and a
+//     producer warp streams them from global memory (L2-resident) into a
+//     two-stage shared-memory ring with 1-D bulk copies (TMA);
+//   * one thread issues tcgen05.mma (M = 128, N = layer width, K = 16 per
+//     instruction) with the FP32 accumulator in tensor memory (TMEM);
+//   * four epilogue warps read the accumulator back with tcgen05.ld, add the
+//     bias, apply ReLU, and write the next layer's A operand (BF16) straight
+//     into shared memory; the last layer applies tanh or identity.
+#include <cuda_bf16.h>
+#include <string.h>
+
+#include <vector>
+
+#include "fr_common.cuh"
+#include "fr_ptx.cuh"
+
+namespace fr {
+
+constexpr int TC_STAGES = 2;
+constexpr uint32_t TC_CHUNK_MAX = 16384;      // bytes per ring stage
+constexpr int TC_THREADS = 192;               // producer, MMA, 4 epilogue warps
+constexpr uint64_t TC_WAIT_NS = 2000000000ull;
+
+struct TcLayer {
+    int fin, fout;        // true sizes
+    int K, N;             // padded to multiples of 16
+    int KC;               // K columns per streamed chunk
+    int n_chunks;
+    uint32_t off;         // byte offset of the layer's chunks in an agent image
+};
+
+struct TcPlan {
+    int M, L, out_act;
+    int KA;               // K extent of the shared A buffer (max layer K)
+    int tmem_cols;        // power of two >= max N
+    uint32_t agent_bytes;
+    TcLayer layer[MAX_LAYERS];
+};
+
+struct TcImage {
+    TcPlan plan;
+    uint8_t *img;         // device [M][agent_bytes] BF16 chunks
+    float *bias;          // device [M][MAX_LAYERS][256] fp32, zero padded
+    unsigned *err;        // device error flags
+    uint64_t bytes;
+};
+
+namespace {
+
+inline int round16(int x) { return (x + 15) & ~15; }
+
+inline uint16_t f32_to_bf16_rne(float f)
+{
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)((u >> 16) | ((u & 0xffffu) ? 0x40u : 0u));
+    const uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+    return (uint16_t)(u >> 16);
+}
+
+// byte offset of element (n, kk) inside a chunk of a layer with N rows
+inline uint32_t chunk_off(int N, int n, int kk)
+{
+    return (uint32_t)((kk / 8) * (N * 16) + (n / 8) * 128 + (n % 8) * 16 + (kk % 8) * 2);
+}
+
+bool make_plan(const fr_ensemble *e, TcPlan &p)
+{
+    p.M = e->M;
+    p.L = e->L;
+    p.out_act = e->out_act;
+    p.KA = 0;
+    int nmax = 0;
+    uint32_t off = 0;
+    for (int l = 0; l < e->L; ++l) {
+        TcLayer &ly = p.layer[l];
+        ly.fin = e->dims[l];
+        ly.fout = e->dims[l + 1];
+        ly.K = round16(ly.fin);
+        ly.N = round16(ly.fout);
+        if (ly.N > 256 || ly.K > 512) return false;
+        int kc = (int)(TC_CHUNK_MAX / (uint32_t)(ly.N * 2));
+        kc = kc / 16 * 16;
+        ly.KC = kc < ly.K ? kc : ly.K;
+        ly.n_chunks = (ly.K + ly.KC - 1) / ly.KC;
+        ly.off = off;
+        off += (uint32_t)ly.N * ly.K * 2;
+        p.KA = ly.K > p.KA ? ly.K : p.KA;
+        nmax = ly.N > nmax ? ly.N : nmax;
+    }
+    p.agent_bytes = (off + 1023u) & ~1023u;
+    int c = 32;
+    while (c < nmax) c <<= 1;
+    p.tmem_cols = c;
+    return true;
+}
+
+uint32_t tc_smem_bytes(const TcPlan &p)
+{
+    return (uint32_t)(p.KA / 8) * 2048u + TC_STAGES * TC_CHUNK_MAX + 256u + 1024u;
+}
+
+// shared memory of the largest plan (K up to 512): the attribute is set once
+// to this so that every plan's launch fits
+constexpr uint32_t TC_SMEM_MAX = (512u / 8u) * 2048u + TC_STAGES * TC_CHUNK_MAX + 256u + 1024u;
+
+// ------------------------------------------------------------------ kernel
+__global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const uint8_t *__restrict__ img,
+                                                            const float *__restrict__ bias,
+                                                            const float *__restrict__ obs, int ld, int n,
+                                                            float *__restrict__ y, unsigned *err)
+{
+    using namespace ptx;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *A = base;
+    uint8_t *ring = A + (plan.KA / 8) * 2048;
+    uint64_t *bars = (uint64_t *)(ring + TC_STAGES * TC_CHUNK_MAX);
+    uint64_t *full = bars;
+    uint64_t *empty = bars + TC_STAGES;
+    uint64_t *acc_full = bars + 2 * TC_STAGES;
+    uint64_t *a_ready = acc_full + 1;
+    uint32_t *tmem_slot = (uint32_t *)(a_ready + 1);
+    volatile int *abort = (volatile int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row0 = blockIdx.x * 128;
+    const int agent = blockIdx.y;
+    const uint8_t *aimg = img + (size_t)agent * plan.agent_bytes;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(acc_full, 1);
+        mbar_init(a_ready, 128);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        __syncwarp();
+        tmem_alloc(tmem_slot, (uint32_t)plan.tmem_cols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------ weight producer
+        if (lane == 0) {
+            int i = 0;
+            bool ok = true;
+            for (int l = 0; l < plan.L && ok; ++l) {
+                const TcLayer &ly = plan.layer[l];
+                for (int c = 0; c < ly.n_chunks; ++c) {
+                    const int s = i % TC_STAGES;
+                    const uint32_t ph = (uint32_t)(i / TC_STAGES) & 1u;
+                    if (!mbar_wait(&empty[s], ph ^ 1u, abort, err, 1u, TC_WAIT_NS)) { ok = false; break; }
+                    const int kc = min(ly.KC, ly.K - c * ly.KC);
+                    const uint32_t bytes = (uint32_t)(ly.N * kc * 2);
+                    mbar_arrive_expect_tx(&full[s], bytes);
+                    bulk_g2s(ring + s * TC_CHUNK_MAX, aimg + ly.off + (size_t)c * ly.N * ly.KC * 2, bytes,
+                             &full[s]);
+                    ++i;
+                }
+            }
+            // every copy issued must land before the CTA may exit
+            for (int j = i - 1; j >= 0 && j >= i - TC_STAGES; --j) {
+                volatile int no_abort = 0;
+                mbar_wait(&full[j % TC_STAGES], (uint32_t)(j / TC_STAGES) & 1u, &no_abort, err, 8u,
+                          TC_WAIT_NS);
+            }
+        }
+    } else if (warp == 1) {
+        // -------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            int i = 0;
+            const uint32_t a_base = smem_u32(A);
+            for (int l = 0; l < plan.L; ++l) {
+                const TcLayer &ly = plan.layer[l];
+                if (!mbar_wait(a_ready, (uint32_t)l & 1u, abort, err, 2u, TC_WAIT_NS)) break;
+                tc_fence_after();
+                const uint32_t idesc = idesc_bf16(128, ly.N);
+                int kg = 0;
+                bool ok = true;
+                for (int c = 0; c < ly.n_chunks; ++c) {
+                    const int s = i % TC_STAGES;
+                    if (!mbar_wait(&full[s], (uint32_t)(i / TC_STAGES) & 1u, abort, err, 4u, TC_WAIT_NS)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const int kc = min(ly.KC, ly.K - c * ly.KC);
+                    const uint32_t b_base = smem_u32(ring + s * TC_CHUNK_MAX);
+                    for (int kk = 0; kk < kc; kk += 16, kg += 16) {
+                        const uint64_t ad = smem_desc(a_base + (uint32_t)(kg / 8) * 2048u, 2048u, 128u);
+                        const uint64_t bd =
+                            smem_desc(b_base + (uint32_t)(kk / 8) * (uint32_t)(ly.N * 16), (uint32_t)(ly.N * 16), 128u);
+                        mma_bf16(tmem, ad, bd, idesc, kg > 0 ? 1u : 0u);
+                    }
+                    mma_commit(&empty[s]);
+                    ++i;
+                }
+                if (!ok) break;
+                mma_commit(acc_full);
+            }
+        }
+    } else {
+        // ------------------------------------------------------ epilogue
+        const int q = warp & 3;                 // TMEM lane quarter of this warp
+        const int r = q * 32 + lane;            // row of the tile owned by this thread
+        const int grow = row0 + r;
+        const uint32_t a_base = smem_u32(A);
+        // observation tile -> BF16 A operand, one row at a time per warp
+        const TcLayer &l0 = plan.layer[0];
+        for (int rr = 0; rr < 32; ++rr) {
+            const int row = q * 32 + rr;
+            const int g = row0 + row;
+            for (int c = lane; c < l0.K / 8; c += 32) {
+                float v[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int k = c * 8 + i;
+                    v[i] = (g < n && k < l0.fin) ? __ldg(obs + (int64_t)g * ld + k) : 0.0f;
+                }
+                uint32_t w[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+                    w[i] = *(uint32_t *)&b;
+                }
+                st_shared_v4(a_base + (uint32_t)c * 2048u + (uint32_t)(row / 8) * 128u + (uint32_t)(row % 8) * 16u,
+                             w[0], w[1], w[2], w[3]);
+            }
+        }
+        fence_proxy_async_smem();
+        mbar_arrive(a_ready);
+        const uint32_t row_off = (uint32_t)(r / 8) * 128u + (uint32_t)(r % 8) * 16u;
+        for (int l = 0; l < plan.L; ++l) {
+            const TcLayer &ly = plan.layer[l];
+            const bool last = l == plan.L - 1;
+            if (!mbar_wait(acc_full, (uint32_t)l & 1u, abort, err, 16u, TC_WAIT_NS)) break;
+            tc_fence_after();
+            const float *bl = bias + ((size_t)agent * MAX_LAYERS + l) * 256;
+            for (int c0 = 0; c0 < ly.N; c0 += 16) {
+                uint32_t v[16];
+                __syncwarp();
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                tmem_ld_wait();
+                float x[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) x[i] = __uint_as_float(v[i]) + __ldg(bl + c0 + i);
+                if (!last) {
+                    uint32_t w[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        __nv_bfloat162 b = __floats2bfloat162_rn(fmaxf(x[2 * i], 0.0f), fmaxf(x[2 * i + 1], 0.0f));
+                        w[i] = *(uint32_t *)&b;
+                    }
+                    st_shared_v4(a_base + (uint32_t)(c0 / 8) * 2048u + row_off, w[0], w[1], w[2], w[3]);
+                    st_shared_v4(a_base + (uint32_t)(c0 / 8 + 1) * 2048u + row_off, w[4], w[5], w[6], w[7]);
+                } else if (grow < n) {
+                    float *yr = y + ((size_t)agent * n + grow) * ly.fout;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int col = c0 + i;
+                        if (col < ly.fout) yr[col] = plan.out_act ? tanhf(x[i]) : x[i];
+                    }
+                }
+            }
+            if (!last) {
+                fence_proxy_async_smem();
+                tc_fence_before();
+                mbar_arrive(a_ready);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, (uint32_t)plan.tmem_cols);
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- host side
+int tc_create(fr_ensemble *e)
+{
+    if (e->precision != FR_PREC_BF16) {
+        set_error("ensemble_create: precision %d has no tensor-core path in this build", e->precision);
+        return FR_EINVAL;
+    }
+    TcImage *t = new TcImage();
+    if (!make_plan(e, t->plan)) {
+        delete t;
+        set_error("ensemble_create: layer sizes exceed the tensor-core kernel (N <= 256, K <= 512)");
+        return FR_EINVAL;
+    }
+    const TcPlan &p = t->plan;
+    // pack the fp32 master weights into BF16 chunks on the host
+    std::vector<float> host((size_t)e->M * e->P);
+    cudaError_t err = cudaMemcpy(host.data(), e->params, host.size() * 4, cudaMemcpyDeviceToHost);
+    if (err != cudaSuccess) {
+        delete t;
+        return cuda_fail(err, "tc_create weights");
+    }
+    std::vector<uint8_t> img((size_t)e->M * p.agent_bytes, 0);
+    std::vector<float> bias((size_t)e->M * MAX_LAYERS * 256, 0.0f);
+    for (int j = 0; j < e->M; ++j) {
+        const float *P = host.data() + (size_t)j * e->P;
+        uint8_t *aimg = img.data() + (size_t)j * p.agent_bytes;
+        for (int l = 0; l < e->L; ++l) {
+            const TcLayer &ly = p.layer[l];
+            const float *W = P + e->w_off[l];
+            const float *B = P + e->b_off[l];
+            for (int n = 0; n < ly.fout; ++n) {
+                bias[((size_t)j * MAX_LAYERS + l) * 256 + n] = B[n];
+                for (int k = 0; k < ly.fin; ++k) {
+                    const int c = k / ly.KC, kk = k % ly.KC;
+                    const size_t off = ly.off + (size_t)c * ly.N * ly.KC * 2 + chunk_off(ly.N, n, kk);
+                    const uint16_t b = f32_to_bf16_rne(W[(size_t)n * ly.fin + k]);
+                    memcpy(aimg + off, &b, 2);
+                }
+            }
+        }
+    }
+    const uint64_t ib = img.size(), bb = bias.size() * 4;
+    int rc;
+    if ((rc = dev_alloc(e->ctx, (void **)&t->img, ib)) || (rc = dev_alloc(e->ctx, (void **)&t->bias, bb)) ||
+        (rc = dev_alloc(e->ctx, (void **)&t->err, 256))) {
+        dev_free(e->ctx, t->img, ib);
+        dev_free(e->ctx, t->bias, bb);
+        delete t;
+        return rc;
+    }
+    t->bytes = ib + bb + 256;
+    err = cudaMemcpy(t->img, img.data(), ib, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(t->bias, bias.data(), bb, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemset(t->err, 0, 256);
+    if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(k_tc_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)TC_SMEM_MAX);
+    e->tc = t;
+    if (err != cudaSuccess) return cuda_fail(err, "tc_create upload");
+    return FR_OK;
+}
+
+void tc_destroy(fr_ensemble *e)
+{
+    if (!e || !e->tc) return;
+    TcImage *t = e->tc;
+    dev_free(e->ctx, t->img, (uint64_t)e->M * t->plan.agent_bytes);
+    dev_free(e->ctx, t->bias, (uint64_t)e->M * MAX_LAYERS * 256 * 4);
+    dev_free(e->ctx, t->err, 256);
+    delete t;
+    e->tc = nullptr;
+}
+
+int tc_forward(const fr_ensemble *e, const float *obs, int ld, int n, float *y, cudaStream_t s)
+{
+    const TcImage *t = e->tc;
+    FR_CHECK(t, FR_EINVAL, "tensor-core image missing");
+    dim3 grid(ceil_div(n, 128), e->M);
+    k_tc_forward<<<grid, TC_THREADS, tc_smem_bytes(t->plan), s>>>(t->plan, t->img, t->bias, obs, ld, n, y,
+                                                                  t->err);
+    FR_CUDA(cudaGetLastError());
+    return FR_OK;
+}
+
+bool tc_rollout_supported(const fr_env *, const fr_ensemble *) { return false; }
+
+int tc_rollout(fr_env *, const fr_ensemble *, int, const fr_traj *, double *, cudaStream_t)
+{
+    set_error("fused rollout not available for this configuration");
+    return FR_EINVAL;
+}
+
+int tc_device_errors(const fr_ensemble *e, unsigned *flags)
+{
+    *flags = 0;
+    if (!e->tc) return FR_OK;
+    FR_CUDA(cudaMemcpy(flags, e->tc->err, 4, cudaMemcpyDeviceToHost));
+    return FR_OK;
+}
+
+}  // namespace fr
+
+extern "C" int ensemble_device_errors(const fr_ensemble *e, uint32_t *flags)
+{
+    FR_CHECK(e && flags, FR_EINVAL, "ensemble_device_errors: NULL argument");
+    FR_CUDA(cudaSetDevice(e->ctx->device));
+    unsigned f = 0;
+    int rc = fr::tc_device_errors(e, &f);
+    *flags = f;
+    return rc;
+}

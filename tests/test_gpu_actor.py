@@ -1,0 +1,143 @@
+"""Actor networks and ensemble combine on the GPU against the fp64 oracle.
+
+Tolerances: per observation row, ||a_gpu - a_ref||_2 / max(||a_ref||_2, 1e-3)
+<= 2e-2 for BF16 (FP32: 1e-4); discretised stock actions within one share of
+the oracle's on >= 99.9% of entries; crypto argmax / vote agreement >= 99.9%.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2501_10709_gb300 as fr
+from paper_2501_10709_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = {fr.PREC_FP32: 1e-4, fr.PREC_BF16: 2e-2}
+
+
+def _stock_obs(n, seed=21):
+    """Realistic stock observations: states visited by a prescribed-share run."""
+    w = synth.workload_stock_2048(N=256, T=64)
+    q = synth.prescribed_shares(64, 256, 30, seed=seed)
+    o = oracle.stock_run(w.market, w.envs.Ke, w.envs.start, w.envs.W, w.envs.bps,
+                         init_cash=w.envs.init_cash, hmax=100, fee_bps=10, T=64, act_i32=q,
+                         want=("obs",))
+    obs = o["obs"].reshape(-1, o["obs"].shape[-1])
+    return np.ascontiguousarray(obs[np.linspace(0, obs.shape[0] - 1, n).astype(int)])
+
+
+def _crypto_obs(n, seed=22):
+    w = synth.workload_crypto(N=512, T=64, S=60_000)
+    acts = synth.prescribed_discrete(64, 512, seed=seed)
+    o = oracle.crypto_run(w.market, w.envs.start, w.envs.W, init_cash=w.envs.init_cash,
+                          pmax=10, T=64, act_u8=acts, want=("obs",))
+    obs = o["obs"].reshape(-1, 10)
+    return np.ascontiguousarray(obs[np.linspace(0, obs.shape[0] - 1, n).astype(int)])
+
+
+def _rel_err(got, want):
+    return np.linalg.norm(got - want, axis=-1) / np.maximum(np.linalg.norm(want, axis=-1), 1e-3)
+
+
+def _oracle_agents(dims, params, obs, out_act):
+    return np.stack([oracle.net_forward(dims, params[j], obs, out_act) for j in range(params.shape[0])])
+
+
+@pytest.mark.parametrize("precision", [fr.PREC_FP32, fr.PREC_BF16])
+@pytest.mark.parametrize("dims,n", [((301, 64, 64, 30), 1000), ((301, 256, 256, 30), 2048),
+                                    ((301, 256, 256, 30), 129), ((301, 64, 32, 30), 300)])
+def test_stock_actor_outputs(ctx, dev, precision, dims, n):
+    params = synth.actor_params(dims, 3, seed=4)
+    obs = _stock_obs(n)
+    ens = fr.ensemble_create(ctx, dims, params, precision=precision)
+    y = torch.full((3, n, 30), np.nan, device=dev)
+    fr.ensemble_forward(ens, torch.from_numpy(obs).to(dev), y)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy().astype(np.float64)
+    want = _oracle_agents(dims, params, obs, 1)
+    err = _rel_err(got, want)
+    print(f"prec {precision} dims {dims} n {n}: max rel {err.max():.3e} "
+          f"max abs {np.abs(got - want).max():.3e}")
+    assert np.isfinite(got).all()
+    assert err.max() <= REL_TOL[precision]
+    assert fr.ensemble_device_errors(ens) == 0
+
+
+@pytest.mark.parametrize("precision", [fr.PREC_FP32, fr.PREC_BF16])
+def test_stock_ensemble_mean_and_shares(ctx, dev, precision):
+    dims = (301, 256, 256, 30)
+    params = synth.actor_params(dims, 3, seed=5)
+    n = 4096
+    obs = _stock_obs(n, seed=31)
+    ens = fr.ensemble_create(ctx, dims, params, precision=precision)
+    act = torch.empty(n, 30, device=dev)
+    fr.ensemble_act(ens, torch.from_numpy(obs).to(dev), act)
+    torch.cuda.synchronize()
+    got = act.cpu().numpy()
+    want = np.stack([oracle.ensemble_mean(_oracle_agents(dims, params, obs[i:i + 1], 1)[:, 0])
+                     for i in range(0, n, 64)])
+    err = _rel_err(got[::64].astype(np.float64), want)
+    assert err.max() <= REL_TOL[precision]
+    qg = oracle.discretise_many(got[::64], 100).reshape(want.shape)
+    qw = np.array([[oracle.discretise(x, 100) for x in row] for row in want])
+    within = np.mean(np.abs(qg - qw) <= 1)
+    print(f"prec {precision}: exact share match {np.mean(qg == qw):.4f}, within 1 share {within:.5f}")
+    assert within >= 0.999
+
+
+def test_identical_agents_equal_one_agent_on_gpu(ctx, dev):
+    dims = (301, 256, 256, 30)
+    one = synth.actor_params(dims, 1, seed=6)
+    obs = torch.from_numpy(_stock_obs(777)).to(dev)
+    for prec in (fr.PREC_FP32, fr.PREC_BF16):
+        e1 = fr.ensemble_create(ctx, dims, one, precision=prec)
+        e3 = fr.ensemble_create(ctx, dims, np.repeat(one, 3, 0), precision=prec)
+        a1 = torch.empty(777, 30, device=dev)
+        a3 = torch.empty(777, 30, device=dev)
+        fr.ensemble_act(e1, obs, a1)
+        fr.ensemble_act(e3, obs, a3)
+        torch.cuda.synchronize()
+        assert torch.equal(a1, a3)
+
+
+@pytest.mark.parametrize("precision", [fr.PREC_FP32, fr.PREC_BF16])
+def test_crypto_argmax_and_vote_agreement(ctx, dev, precision):
+    dims = (10, 128, 128, 3)
+    params = synth.actor_params(dims, 5, seed=8, out_scale=4.0)
+    n = 8192
+    obs = _crypto_obs(n)
+    ens = fr.ensemble_create(ctx, dims, params, precision=precision, combine=fr.COMBINE_VOTE,
+                             out_act=0)
+    y = torch.empty(5, n, 3, device=dev)
+    act = torch.empty(n, dtype=torch.uint8, device=dev)
+    od = torch.from_numpy(obs).to(dev)
+    fr.ensemble_forward(ens, od, y)
+    fr.ensemble_act(ens, od, act)
+    torch.cuda.synchronize()
+    q = _oracle_agents(dims, params, obs, 0)
+    err = _rel_err(y.cpu().numpy().astype(np.float64), q)
+    assert err.max() <= REL_TOL[precision]
+    am_ref = q.argmax(-1)
+    am = y.cpu().numpy().argmax(-1)
+    agree = np.mean(am == am_ref)
+    vote_ref = np.array([oracle.vote(am_ref[:, i]) for i in range(n)])
+    vote_agree = np.mean(act.cpu().numpy() == vote_ref)
+    srt = np.sort(q, -1)
+    gap = srt[..., -1] - srt[..., -2]
+    print(f"prec {precision}: argmax agreement {agree:.5f}, vote agreement {vote_agree:.5f}, "
+          f"Q-gap p1/p50 {np.percentile(gap, 1):.3e}/{np.percentile(gap, 50):.3e}")
+    assert agree >= 0.999 and vote_agree >= 0.999
+
+
+def test_empty_and_single_row(ctx, dev):
+    dims = (301, 64, 64, 30)
+    params = synth.actor_params(dims, 3, seed=9)
+    ens = fr.ensemble_create(ctx, dims, params, precision=fr.PREC_BF16)
+    obs = torch.from_numpy(_stock_obs(1)).to(dev)
+    act = torch.empty(1, 30, device=dev)
+    fr.ensemble_act(ens, obs, act)
+    fr.ensemble_act(ens, obs[:0], act[:0])
+    torch.cuda.synchronize()
+    assert torch.isfinite(act).all()

@@ -1,0 +1,113 @@
+"""Rollouts (observe -> ensemble -> step for T steps) checked teacher-forced:
+the oracle replays the GPU's emitted actions and must reproduce rewards, done
+flags and observations bit for bit; the oracle's fp64 actors evaluated on the
+GPU's recorded observations must agree with the GPU's actions within the
+stated tolerance."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2501_10709_gb300 as fr
+from paper_2501_10709_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = {fr.PREC_FP32: 1e-4, fr.PREC_BF16: 2e-2}
+
+
+def _traj(T, N, D, K, dev, stock=True):
+    return {
+        "obs": torch.full((T, N, D), np.nan, device=dev),
+        "act": (torch.full((T, N, K), np.nan, device=dev) if stock
+                else torch.full((T, N), 255, dtype=torch.uint8, device=dev)),
+        "rew": torch.zeros(T, N, dtype=torch.int64, device=dev),
+        "rew_f32": torch.zeros(T, N, device=dev),
+        "done": torch.zeros(T, N, dtype=torch.uint8, device=dev),
+    }
+
+
+def _stock_rollout_check(ctx, dev, w, precision, T, sample_rows=256):
+    e = w.envs
+    mk = fr.fr_market_create(ctx, w.market)
+    env = fr.env_create(ctx, mk, start=e.start, window=e.W, n_assets=e.Ke, bps=e.bps)
+    ens = fr.ensemble_create(ctx, w.dims, w.params, precision=precision)
+    tr = _traj(T, e.N, env.D, 30, dev)
+    met = torch.empty(e.N, 3, dtype=torch.float64, device=dev)
+    fr.rollout(env, ens, T, traj=tr, metrics=met)
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in tr.items()}
+    ref = oracle.stock_run(w.market, e.Ke, e.start, e.W, e.bps, init_cash=e.init_cash, hmax=100,
+                           fee_bps=10, T=T, act_f32=g["act"])
+    for k in ("obs", "rew", "rew_f32", "done"):
+        assert np.array_equal(g[k], ref[k]), k
+    assert np.array_equal(met.cpu().numpy(), ref["metrics"])
+    # actors on the GPU's own observations
+    rng = np.random.default_rng(0)
+    rows = rng.choice(T * e.N, size=min(sample_rows, T * e.N), replace=False)
+    obs = g["obs"].reshape(-1, env.D)[rows]
+    act = g["act"].reshape(-1, 30)[rows].astype(np.float64)
+    ys = np.stack([oracle.net_forward(w.dims, w.params[j], obs, 1) for j in range(3)])
+    want = np.stack([oracle.ensemble_mean(ys[:, i]) for i in range(len(rows))])
+    err = np.linalg.norm(act - want, axis=-1) / np.maximum(np.linalg.norm(want, axis=-1), 1e-3)
+    assert err.max() <= REL_TOL[precision], err.max()
+    qg = oracle.discretise_many(act.astype(np.float32), 100)
+    qw = np.array([oracle.discretise(x, 100) for x in want.ravel()])
+    assert np.mean(np.abs(qg - qw) <= 1) >= 0.999
+    return g
+
+
+@pytest.mark.parametrize("precision", [fr.PREC_FP32, fr.PREC_BF16])
+def test_stock_rollout_small_teacher_forced(ctx, dev, precision):
+    w = synth.workload_stock_small()
+    _stock_rollout_check(ctx, dev, w, precision, w.T)
+
+
+@pytest.mark.parametrize("precision", [fr.PREC_FP32, fr.PREC_BF16])
+def test_stock_rollout_2048_envs_teacher_forced(ctx, dev, precision):
+    # the 2,048-env, 301-256-256-30 workload at a shortened horizon
+    w = synth.workload_stock_2048(T=24)
+    _stock_rollout_check(ctx, dev, w, precision, 24)
+
+
+@pytest.mark.parametrize("precision", [fr.PREC_FP32, fr.PREC_BF16])
+def test_crypto_rollout_teacher_forced(ctx, dev, precision):
+    w = synth.workload_crypto(N=1024, T=64, S=40_000)
+    e = w.envs
+    mk = fr.fr_market_create(ctx, w.market)
+    env = fr.env_create(ctx, mk, start=e.start, window=e.W, init_cash=e.init_cash, pmax=e.pmax)
+    ens = fr.ensemble_create(ctx, w.dims, w.params, precision=precision, combine=fr.COMBINE_VOTE,
+                             out_act=0)
+    T = w.T
+    tr = _traj(T, e.N, 10, 1, dev, stock=False)
+    met = torch.empty(e.N, 3, dtype=torch.float64, device=dev)
+    fr.rollout(env, ens, T, traj=tr, metrics=met)
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in tr.items()}
+    ref = oracle.crypto_run(w.market, e.start, e.W, init_cash=e.init_cash, pmax=e.pmax, T=T,
+                            act_u8=g["act"])
+    for k in ("obs", "rew", "rew_f32", "done"):
+        assert np.array_equal(g[k], ref[k]), k
+    assert np.array_equal(met.cpu().numpy(), ref["metrics"])
+    obs = g["obs"].reshape(-1, 10)
+    q = np.stack([oracle.net_forward(w.dims, w.params[j], obs, 0) for j in range(5)])
+    votes = np.array([oracle.vote(b) for b in q.argmax(-1).T])
+    agree = np.mean(votes == g["act"].ravel())
+    print(f"prec {precision}: vote agreement {agree:.5f}")
+    assert agree >= 0.999
+
+
+def test_rollout_zero_steps_and_bad_pairs(ctx, dev):
+    w = synth.workload_stock_small()
+    e = w.envs
+    mk = fr.fr_market_create(ctx, w.market)
+    env = fr.env_create(ctx, mk, start=e.start, window=e.W, bps=e.bps)
+    ens = fr.ensemble_create(ctx, w.dims, w.params, precision=fr.PREC_FP32)
+    met = torch.empty(e.N, 3, dtype=torch.float64, device=dev)
+    fr.rollout(env, ens, 0, metrics=met)
+    torch.cuda.synchronize()
+    assert (met == 0).all()
+    bad = fr.ensemble_create(ctx, (301, 64, 3), synth.actor_params((301, 64, 3), 3),
+                             combine=fr.COMBINE_VOTE, out_act=0)
+    with pytest.raises(fr.FrError):
+        fr.rollout(env, bad, 4)
