@@ -108,7 +108,9 @@ typedef struct fr_env fr_env;
  *  stock : state [b, p, h, f] of Sec. 3.1, observation dimension
  *          D = 1 + 2K + I*K for the market's K assets and I indicators:
  *          [cash*1e-8, p_k*1e-4, h_k*1e-2, f_{i,k} (i outer, k inner)],
- *          each entry (float)((double)x * c); assets k >= n_assets[e] read 0.
+ *          each entry the float32 product (float)x * c_f (one rounding for
+ *          the conversion, one for the product); assets k >= n_assets[e]
+ *          read 0.
  *          Prices are the day's close scaled by (1e4 + bps[e][k]) / 1e4,
  *          rounded half up, floor 1 cent (Sec. 5.1 dataset diversity).
  *          Actions are share changes (Sec. 3.1): sells first, capped at the
@@ -118,7 +120,7 @@ typedef struct fr_env fr_env;
  *          action {0 sell, 1 hold, 2 buy} of one lot at bid = mid - s/2 or
  *          ask = bid + s; long-only, at most pmax lots; no fee.
  *  Reward (both): v_{t+1} - v_t with v = cash + holdings * price
- *  (Sec. 3.1), int64 cents; a float copy is reward * 1e-6.
+ *  (Sec. 3.1), int64 cents; a float copy is (float)reward * 1e-6f.
  * K > 32, window < 2 or a window past the market end -> FR_EINVAL. */
 typedef struct {
     int32_t task;
@@ -201,6 +203,10 @@ typedef struct fr_ensemble fr_ensemble;
 #define FR_PREC_FP32 0        /* plain unfused fp32 SIMT path               */
 #define FR_PREC_BF16 1        /* tcgen05 BF16 tensor cores, fp32 accumulate */
 #define FR_PREC_FP8 2         /* tcgen05 FP8 E4M3 weights+activations       */
+#define FR_PREC_BF16X3 3      /* tcgen05 BF16 with split hi/lo operands:
+                                 x ~ hi + lo, three products per step
+                                 (hi*hi + lo*hi + hi*lo), fp32-class accuracy
+                                 for discrete (argmax / vote) decisions      */
 
 #define FR_COMBINE_MEAN 0     /* Sec. 5.2.1 weighted average of actions     */
 #define FR_COMBINE_VOTE 1     /* Sec. 5.2.2 majority vote of argmax actions */

@@ -293,14 +293,16 @@ static int64_t stock_value(int64_t cash, const int32_t *h, const int64_t *p, int
 }
 
 /* Sec. 3.1 state [b, p, h, f]: cash*1e-8, p*1e-4, h*1e-2, indicators
- * indicator-major (i outer, asset inner); assets k >= Ke are zero. */
+ * indicator-major (i outer, asset inner); assets k >= Ke are zero.  Each
+ * scaled entry is the float32 product of the value rounded to float32 and
+ * the float32 constant. */
 static void stock_obs(const stock_env *e, const int64_t *p, const float *ind,
                       int K, int I, int Ke, int d, float *o)
 {
-    o[0] = (float)((double)e->cash * 1e-8);
+    o[0] = (float)e->cash * 1e-8f;
     for (int k = 0; k < K; ++k) {
-        o[1 + k] = k < Ke ? (float)((double)p[k] * 1e-4) : 0.0f;
-        o[1 + K + k] = k < Ke ? (float)((double)e->h[k] * 1e-2) : 0.0f;
+        o[1 + k] = k < Ke ? (float)p[k] * 1e-4f : 0.0f;
+        o[1 + K + k] = k < Ke ? (float)e->h[k] * 1e-2f : 0.0f;
     }
     for (int i = 0; i < I; ++i)
         for (int k = 0; k < K; ++k)
@@ -444,7 +446,7 @@ int32_t orc_stock_run(int32_t n_days, int32_t K, int32_t I,
                     env.done = dn;
                 }
                 if (rew) rew[row] = r;
-                if (rew_f32) rew_f32[row] = (float)((double)r * 1e-6);
+                if (rew_f32) rew_f32[row] = (float)r * 1e-6f;
                 if (done_out) done_out[row] = dn;
                 if (dn && auto_reset) {
                     if (metrics) acc_final(&env.acc, 252.0, metrics + (int64_t)e * 3);
@@ -517,8 +519,8 @@ int32_t orc_crypto_run(int32_t S, const int64_t *mid, const uint8_t *spread,
             for (int t = 0; t < T; ++t) {
                 const int64_t row = (int64_t)t * N + e;
                 int d = start[e] + tt;
-                o[0] = (float)((double)cash * 1e-8);
-                o[1] = (float)((double)pos / (double)pmax);
+                o[0] = (float)cash * 1e-8f;
+                o[1] = (float)pos / (float)pmax;
                 for (int i = 0; i < 8; ++i) o[2 + i] = fac[(int64_t)d * 8 + i];
                 if (obs) memcpy(obs + row * D, o, sizeof(o));
                 int u = 1;
@@ -553,7 +555,7 @@ int32_t orc_crypto_run(int32_t S, const int64_t *mid, const uint8_t *spread,
                     done = dn;
                 }
                 if (rew) rew[row] = r;
-                if (rew_f32) rew_f32[row] = (float)((double)r * 1e-6);
+                if (rew_f32) rew_f32[row] = (float)r * 1e-6f;
                 if (done_out) done_out[row] = dn;
                 if (dn && auto_reset) {
                     if (metrics) acc_final(&acc, 1.0, metrics + (int64_t)e * 3);

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import (ACT_F32_UNIT, ACT_I32_SHARES, ACT_U8_DISCRETE, COMBINE_MEAN,
-                   COMBINE_VOTE, PREC_BF16, PREC_FP8, PREC_FP32, TASK_CRYPTO,
+                   COMBINE_VOTE, PREC_BF16, PREC_BF16X3, PREC_FP8, PREC_FP32, TASK_CRYPTO,
                    TASK_STOCK, FrError)
 
 __all__ = [
@@ -23,7 +23,7 @@ __all__ = [
     "env_error_count", "env_dims", "ensemble_create", "ensemble_forward",
     "ensemble_act", "ensemble_device_errors", "rollout", "FrError", "lib",
     "ACT_I32_SHARES", "ACT_F32_UNIT", "ACT_U8_DISCRETE", "PREC_FP32", "PREC_BF16",
-    "PREC_FP8", "COMBINE_MEAN", "COMBINE_VOTE", "TASK_STOCK", "TASK_CRYPTO",
+    "PREC_FP8", "PREC_BF16X3", "COMBINE_MEAN", "COMBINE_VOTE", "TASK_STOCK", "TASK_CRYPTO",
 ]
 
 

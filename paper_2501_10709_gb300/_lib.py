@@ -16,7 +16,7 @@ FR_OK, FR_EINVAL, FR_ENOMEM, FR_EBUSY, FR_ETIMEDOUT, FR_ECUDA, FR_ENOTREADY, FR_
     0, -1, -2, -3, -4, -5, -6, -7)
 TASK_STOCK, TASK_CRYPTO = 0, 1
 ACT_I32_SHARES, ACT_F32_UNIT, ACT_U8_DISCRETE = 0, 1, 2
-PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
+PREC_FP32, PREC_BF16, PREC_FP8, PREC_BF16X3 = 0, 1, 2, 3
 COMBINE_MEAN, COMBINE_VOTE = 0, 1
 
 i32, i64, u32, u64, f64 = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_double

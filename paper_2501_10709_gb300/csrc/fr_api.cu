@@ -544,7 +544,7 @@ int ensemble_create(fr_ctx *ctx, const fr_ensemble_desc *d, fr_ensemble **out)
     for (int l = 1; l < d->n_layers; ++l)
         FR_CHECK(d->dims[l] <= MAX_HIDDEN, FR_EINVAL, "ensemble_create: hidden width %d > 256",
                  d->dims[l]);
-    FR_CHECK(d->precision >= FR_PREC_FP32 && d->precision <= FR_PREC_FP8, FR_EINVAL,
+    FR_CHECK(d->precision >= FR_PREC_FP32 && d->precision <= FR_PREC_BF16X3, FR_EINVAL,
              "ensemble_create: precision %d", d->precision);
     FR_CHECK(d->combine == FR_COMBINE_MEAN || d->combine == FR_COMBINE_VOTE, FR_EINVAL,
              "ensemble_create: combine %d", d->combine);
@@ -608,8 +608,9 @@ void ensemble_destroy(fr_ensemble *e)
 
 int ensemble_forward(const fr_ensemble *e, const float *obs, int32_t n, float *y, void *stream)
 {
-    FR_CHECK(e && obs && y && n >= 0, FR_EINVAL, "ensemble_forward: bad argument");
+    FR_CHECK(e && n >= 0, FR_EINVAL, "ensemble_forward: bad argument");
     if (n == 0) return FR_OK;
+    FR_CHECK(obs && y, FR_EINVAL, "ensemble_forward: NULL obs or y");
     int rc = use_device(e->ctx);
     if (rc) return rc;
     return forward_any(e, obs, e->dims[0], n, y, (cudaStream_t)stream);
@@ -617,8 +618,9 @@ int ensemble_forward(const fr_ensemble *e, const float *obs, int32_t n, float *y
 
 int ensemble_act(const fr_ensemble *e, const float *obs, int32_t n, void *act, void *stream)
 {
-    FR_CHECK(e && obs && act && n >= 0, FR_EINVAL, "ensemble_act: bad argument");
+    FR_CHECK(e && n >= 0, FR_EINVAL, "ensemble_act: bad argument");
     if (n == 0) return FR_OK;
+    FR_CHECK(obs && act, FR_EINVAL, "ensemble_act: NULL obs or act");
     int rc = use_device(e->ctx);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;

@@ -80,14 +80,16 @@ __device__ __forceinline__ int64_t warp_incl_scan(int64_t x, int lane)
     return x;
 }
 
-__device__ __forceinline__ float obs_scale(int64_t x, double c)
+// Observation / learner scaling: the value rounded to float32 times a
+// float32 constant, one rounding each, no FP64 on the step path.
+__device__ __forceinline__ float obs_scale(int64_t x, float c)
 {
-    return __double2float_rn(__dmul_rn((double)x, c));
+    return __fmul_rn(__ll2float_rn(x), c);
 }
 
 __device__ __forceinline__ float reward_f32(int64_t r)
 {
-    return __double2float_rn(__dmul_rn((double)r, 1e-6));
+    return __fmul_rn(__ll2float_rn(r), 1e-6f);
 }
 
 // ---------------------------------------------------- FP64 episode metrics
@@ -247,14 +249,14 @@ __device__ __forceinline__ void stock_obs_warp(const EnvView &v, int e, int lane
     const int Ke = v.Ke[e];
     const int d = v.start[e] + v.t[e];
     const bool act = lane < Ke;
-    if (lane == 0) o[0] = obs_scale(v.cash[e], 1e-8);
+    if (lane == 0) o[0] = obs_scale(v.cash[e], 1e-8f);
     if (lane < K) {
         float pv = 0.0f, hv = 0.0f;
         if (act) {
             const int64_t p = perturb(__ldg(v.close + (int64_t)d * K + lane),
                                       v.bps[(int64_t)e * KP + lane]);
-            pv = obs_scale(p, 1e-4);
-            hv = obs_scale(v.hold[(int64_t)e * KP + lane], 1e-2);
+            pv = obs_scale(p, 1e-4f);
+            hv = obs_scale(v.hold[(int64_t)e * KP + lane], 1e-2f);
         }
         o[1 + lane] = pv;
         o[1 + K + lane] = hv;
@@ -298,8 +300,8 @@ __device__ __forceinline__ int64_t crypto_step_thread(const EnvView &v, int e, i
 __device__ __forceinline__ void crypto_obs_thread(const EnvView &v, int e, float *o)
 {
     const int d = v.start[e] + v.t[e];
-    o[0] = obs_scale(v.cash[e], 1e-8);
-    o[1] = __double2float_rn(__ddiv_rn((double)v.hold[e], (double)v.pmax));
+    o[0] = obs_scale(v.cash[e], 1e-8f);
+    o[1] = __fdiv_rn(__int2float_rn(v.hold[e]), __int2float_rn(v.pmax));
     const float *f = v.fac + (int64_t)d * FR_CRYPTO_FACTORS;
 #pragma unroll
     for (int i = 0; i < FR_CRYPTO_FACTORS; ++i) o[2 + i] = __ldg(f + i);

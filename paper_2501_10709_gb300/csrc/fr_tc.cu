@@ -14,6 +14,7 @@
 #include <cuda_bf16.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "fr_common.cuh"
@@ -36,6 +37,7 @@ struct TcLayer {
 
 struct TcPlan {
     int M, L, out_act;
+    int split;            // 1: BF16 operands; 3: hi/lo split, three products
     int KA;               // K extent of the shared A buffer (max layer K)
     int tmem_cols;        // power of two >= max N
     uint32_t agent_bytes;
@@ -64,6 +66,14 @@ inline uint16_t f32_to_bf16_rne(float f)
     return (uint16_t)(u >> 16);
 }
 
+inline float bf16_to_f32(uint16_t b)
+{
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
 // byte offset of element (n, kk) inside a chunk of a layer with N rows
 inline uint32_t chunk_off(int N, int n, int kk)
 {
@@ -72,6 +82,7 @@ inline uint32_t chunk_off(int N, int n, int kk)
 
 bool make_plan(const fr_ensemble *e, TcPlan &p)
 {
+    p.split = e->precision == FR_PREC_BF16X3 ? 3 : 1;
     p.M = e->M;
     p.L = e->L;
     p.out_act = e->out_act;
@@ -85,12 +96,12 @@ bool make_plan(const fr_ensemble *e, TcPlan &p)
         ly.K = round16(ly.fin);
         ly.N = round16(ly.fout);
         if (ly.N > 256 || ly.K > 512) return false;
-        int kc = (int)(TC_CHUNK_MAX / (uint32_t)(ly.N * 2));
+        int kc = (int)(TC_CHUNK_MAX / (uint32_t)(ly.N * 2 * p.split));
         kc = kc / 16 * 16;
         ly.KC = kc < ly.K ? kc : ly.K;
         ly.n_chunks = (ly.K + ly.KC - 1) / ly.KC;
         ly.off = off;
-        off += (uint32_t)ly.N * ly.K * 2;
+        off += (uint32_t)ly.N * ly.K * 2 * p.split;
         p.KA = ly.K > p.KA ? ly.K : p.KA;
         nmax = ly.N > nmax ? ly.N : nmax;
     }
@@ -101,14 +112,27 @@ bool make_plan(const fr_ensemble *e, TcPlan &p)
     return true;
 }
 
+// A operand bytes (one part)
+inline uint32_t a_bytes(const TcPlan &p) { return (uint32_t)(p.KA / 8) * 2048u; }
+
 uint32_t tc_smem_bytes(const TcPlan &p)
 {
-    return (uint32_t)(p.KA / 8) * 2048u + TC_STAGES * TC_CHUNK_MAX + 256u + 1024u;
+    return a_bytes(p) * (p.split == 3 ? 2u : 1u) + TC_STAGES * TC_CHUNK_MAX + 256u + 1024u;
 }
 
-// shared memory of the largest plan (K up to 512): the attribute is set once
-// to this so that every plan's launch fits
-constexpr uint32_t TC_SMEM_MAX = (512u / 8u) * 2048u + TC_STAGES * TC_CHUNK_MAX + 256u + 1024u;
+// Eight floats -> BF16 hi parts (round to nearest) and the BF16 rounding of
+// what hi leaves over (x - hi), packed two per word in K order.
+__device__ __forceinline__ void split_pack8(const float *v, uint32_t *hi, uint32_t *lo)
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
+        hi[i] = *(const uint32_t *)&h;
+        lo[i] = *(const uint32_t *)&l;
+    }
+}
 
 // ------------------------------------------------------------------ kernel
 __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const uint8_t *__restrict__ img,
@@ -120,7 +144,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const ui
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *A = base;
-    uint8_t *ring = A + (plan.KA / 8) * 2048;
+    const uint32_t a_part = (uint32_t)(plan.KA / 8) * 2048u;    // bytes of one A part
+    const bool split = plan.split == 3;
+    uint8_t *ring = A + a_part * (split ? 2u : 1u);
     uint64_t *bars = (uint64_t *)(ring + TC_STAGES * TC_CHUNK_MAX);
     uint64_t *full = bars;
     uint64_t *empty = bars + TC_STAGES;
@@ -166,10 +192,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const ui
                     const uint32_t ph = (uint32_t)(i / TC_STAGES) & 1u;
                     if (!mbar_wait(&empty[s], ph ^ 1u, abort, err, 1u, TC_WAIT_NS)) { ok = false; break; }
                     const int kc = min(ly.KC, ly.K - c * ly.KC);
-                    const uint32_t bytes = (uint32_t)(ly.N * kc * 2);
+                    const uint32_t bytes = (uint32_t)(ly.N * kc * 2 * plan.split);
                     mbar_arrive_expect_tx(&full[s], bytes);
-                    bulk_g2s(ring + s * TC_CHUNK_MAX, aimg + ly.off + (size_t)c * ly.N * ly.KC * 2, bytes,
-                             &full[s]);
+                    bulk_g2s(ring + s * TC_CHUNK_MAX,
+                             aimg + ly.off + (size_t)c * ly.N * ly.KC * 2 * plan.split, bytes, &full[s]);
                     ++i;
                 }
             }
@@ -201,11 +227,18 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const ui
                     tc_fence_after();
                     const int kc = min(ly.KC, ly.K - c * ly.KC);
                     const uint32_t b_base = smem_u32(ring + s * TC_CHUNK_MAX);
+                    const uint32_t lbo_b = (uint32_t)(ly.N * 16);
+                    const uint32_t b_lo = (uint32_t)(ly.N * kc * 2);     // lo part after hi
                     for (int kk = 0; kk < kc; kk += 16, kg += 16) {
-                        const uint64_t ad = smem_desc(a_base + (uint32_t)(kg / 8) * 2048u, 2048u, 128u);
-                        const uint64_t bd =
-                            smem_desc(b_base + (uint32_t)(kk / 8) * (uint32_t)(ly.N * 16), (uint32_t)(ly.N * 16), 128u);
+                        const uint32_t ao = a_base + (uint32_t)(kg / 8) * 2048u;
+                        const uint32_t bo = b_base + (uint32_t)(kk / 8) * lbo_b;
+                        const uint64_t ad = smem_desc(ao, 2048u, 128u);
+                        const uint64_t bd = smem_desc(bo, lbo_b, 128u);
                         mma_bf16(tmem, ad, bd, idesc, kg > 0 ? 1u : 0u);
+                        if (split) {
+                            mma_bf16(tmem, smem_desc(ao + a_part, 2048u, 128u), bd, idesc, 1u);
+                            mma_bf16(tmem, ad, smem_desc(bo + b_lo, lbo_b, 128u), idesc, 1u);
+                        }
                     }
                     mma_commit(&empty[s]);
                     ++i;
@@ -232,14 +265,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const ui
                     const int k = c * 8 + i;
                     v[i] = (g < n && k < l0.fin) ? __ldg(obs + (int64_t)g * ld + k) : 0.0f;
                 }
-                uint32_t w[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-                    w[i] = *(uint32_t *)&b;
-                }
-                st_shared_v4(a_base + (uint32_t)c * 2048u + (uint32_t)(row / 8) * 128u + (uint32_t)(row % 8) * 16u,
-                             w[0], w[1], w[2], w[3]);
+                uint32_t w[4], wl[4];
+                split_pack8(v, w, wl);
+                const uint32_t at = a_base + (uint32_t)c * 2048u + (uint32_t)(row / 8) * 128u + (uint32_t)(row % 8) * 16u;
+                st_shared_v4(at, w[0], w[1], w[2], w[3]);
+                if (split) st_shared_v4(at + a_part, wl[0], wl[1], wl[2], wl[3]);
             }
         }
         fence_proxy_async_smem();
@@ -260,14 +290,18 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const ui
 #pragma unroll
                 for (int i = 0; i < 16; ++i) x[i] = __uint_as_float(v[i]) + __ldg(bl + c0 + i);
                 if (!last) {
-                    uint32_t w[8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        __nv_bfloat162 b = __floats2bfloat162_rn(fmaxf(x[2 * i], 0.0f), fmaxf(x[2 * i + 1], 0.0f));
-                        w[i] = *(uint32_t *)&b;
+                    for (int i = 0; i < 16; ++i) x[i] = fmaxf(x[i], 0.0f);
+                    uint32_t w[8], wl[8];
+                    split_pack8(x, w, wl);
+                    split_pack8(x + 8, w + 4, wl + 4);
+                    const uint32_t at = a_base + (uint32_t)(c0 / 8) * 2048u + row_off;
+                    st_shared_v4(at, w[0], w[1], w[2], w[3]);
+                    st_shared_v4(at + 2048u, w[4], w[5], w[6], w[7]);
+                    if (split) {
+                        st_shared_v4(at + a_part, wl[0], wl[1], wl[2], wl[3]);
+                        st_shared_v4(at + a_part + 2048u, wl[4], wl[5], wl[6], wl[7]);
                     }
-                    st_shared_v4(a_base + (uint32_t)(c0 / 8) * 2048u + row_off, w[0], w[1], w[2], w[3]);
-                    st_shared_v4(a_base + (uint32_t)(c0 / 8 + 1) * 2048u + row_off, w[4], w[5], w[6], w[7]);
                 } else if (grow < n) {
                     float *yr = y + ((size_t)agent * n + grow) * ly.fout;
 #pragma unroll
@@ -298,7 +332,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const ui
 // ------------------------------------------------------------- host side
 int tc_create(fr_ensemble *e)
 {
-    if (e->precision != FR_PREC_BF16) {
+    if (e->precision != FR_PREC_BF16 && e->precision != FR_PREC_BF16X3) {
         set_error("ensemble_create: precision %d has no tensor-core path in this build", e->precision);
         return FR_EINVAL;
     }
@@ -329,9 +363,15 @@ int tc_create(fr_ensemble *e)
                 bias[((size_t)j * MAX_LAYERS + l) * 256 + n] = B[n];
                 for (int k = 0; k < ly.fin; ++k) {
                     const int c = k / ly.KC, kk = k % ly.KC;
-                    const size_t off = ly.off + (size_t)c * ly.N * ly.KC * 2 + chunk_off(ly.N, n, kk);
-                    const uint16_t b = f32_to_bf16_rne(W[(size_t)n * ly.fin + k]);
+                    const int kc = std::min(ly.KC, ly.K - c * ly.KC);
+                    const size_t off = ly.off + (size_t)c * ly.N * ly.KC * 2 * p.split + chunk_off(ly.N, n, kk);
+                    const float wv = W[(size_t)n * ly.fin + k];
+                    const uint16_t b = f32_to_bf16_rne(wv);
                     memcpy(aimg + off, &b, 2);
+                    if (p.split == 3) {
+                        const uint16_t bl = f32_to_bf16_rne(wv - bf16_to_f32(b));
+                        memcpy(aimg + off + (size_t)ly.N * kc * 2, &bl, 2);
+                    }
                 }
             }
         }
@@ -349,9 +389,17 @@ int tc_create(fr_ensemble *e)
     err = cudaMemcpy(t->img, img.data(), ib, cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(t->bias, bias.data(), bb, cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemset(t->err, 0, 256);
+    int optin = 0;
     if (err == cudaSuccess)
-        err = cudaFuncSetAttribute(k_tc_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)TC_SMEM_MAX);
+        err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, e->ctx->device);
+    if (err == cudaSuccess && tc_smem_bytes(p) > (uint32_t)optin) {
+        e->tc = t;
+        set_error("ensemble_create: tensor-core plan needs %u bytes of shared memory > %d",
+                  tc_smem_bytes(p), optin);
+        return FR_EINVAL;
+    }
+    if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(k_tc_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     e->tc = t;
     if (err != cudaSuccess) return cuda_fail(err, "tc_create upload");
     return FR_OK;

@@ -189,7 +189,7 @@ def test_stock_observation_layout():
         assert ob.shape == (1 + 2 * K + I * K,)
         assert ob[0] == np.float32(1.0)                      # 1e8 cents * 1e-8
         p = oracle.perturb_many(mk.close[d, :ke], envs.bps[e, :ke].astype(np.int32))
-        assert np.array_equal(ob[1:1 + ke], (p * 1e-4).astype(np.float32))
+        assert np.array_equal(ob[1:1 + ke], p.astype(np.float32) * np.float32(1e-4))
         assert (ob[1 + ke:1 + K] == 0).all() and (ob[1 + K:1 + 2 * K] == 0).all()
         f = ob[1 + 2 * K:].reshape(I, K)                     # indicator-major
         assert np.array_equal(f[:, :ke], mk.ind[d, :, :ke]) and (f[:, ke:] == 0).all()
