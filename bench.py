@@ -131,8 +131,9 @@ def _flush_l2(buf):
     buf.add_(1)
 
 
-def time_rollouts(fr, env, ens, T, steps, warmup, metrics, flush, stream, traj=None):
+def time_rollouts(fr, env, ens, T, steps, warmup, metrics, flush, stream, traj=None, path=0):
     import torch
+    fr.env_set_rollout_path(env, path)
     for _ in range(warmup):
         fr.env_reset(env)
         fr.rollout(env, ens, T, traj=traj, metrics=metrics)
@@ -196,9 +197,19 @@ def run_gpu(args):
         torch.distributed.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    t_bf16 = time_rollouts(fr, env, ens_bf16, T, args.steps, args.warmup, metrics, flush, stream)
+    t_bf16 = time_rollouts(fr, env, ens_bf16, T, args.steps, args.warmup, metrics, flush, stream,
+                           path=fr.PATH_AUTO)
     clk = clocks.stop()
-    t_fp32 = time_rollouts(fr, env, ens_fp32, T, max(2, args.steps // 4), 2, metrics, flush, stream)
+    side = max(2, args.steps // 4)
+    t_fp32 = time_rollouts(fr, env, ens_fp32, T, side, 3, metrics, flush, stream)
+    t_unf = time_rollouts(fr, env, ens_bf16, T, side, 3, metrics, flush, stream,
+                          path=fr.PATH_UNFUSED)
+    traj = {"obs": torch.empty(T, N, env.D, device=dev), "act": torch.empty(T, N, 30, device=dev),
+            "rew": torch.empty(T, N, dtype=torch.int64, device=dev),
+            "done": torch.empty(T, N, dtype=torch.uint8, device=dev)}
+    t_traj = time_rollouts(fr, env, ens_bf16, T, side, 3, metrics, flush, stream, traj=traj)
+    del traj
+    fr.env_set_rollout_path(env, fr.PATH_AUTO)
     total = sum(t_bf16)
     if world > 1:
         tt = torch.tensor([total], device=dev)
@@ -208,15 +219,20 @@ def run_gpu(args):
     value = world * env_steps * args.steps / total
     plain_value = env_steps * len(t_fp32) / sum(t_fp32)
 
-    # dominant kernel: the BF16 actor kernel, timed alone on one step's batch
+    # dominant kernel: the fused rollout kernel, one launch per rollout; its
+    # algorithmic work is N x T x (actor flops per env-step)
+    flops_env_step = M * 2 * sum(w.dims[i] * w.dims[i + 1] for i in range(len(w.dims) - 1))
+    k_dt = statistics.mean(t_bf16)
+    achieved = N * T * flops_env_step / k_dt / 1e12
+    peak = peaks["bf16_tflops"]
+    # the standalone actor kernel on one step's batch, and at a batch that
+    # fills every SM
     obs = torch.empty(N, env.D, device=dev)
     fr.env_reset(env)
     fr.env_observe(env, obs)
     y = torch.empty(M, N, 30, device=dev)
-    k_dt = time_kernel(lambda: fr.ensemble_forward(ens_bf16, obs, y), 50, stream)
-    flops_per_launch = N * M * 2 * sum(w.dims[i] * w.dims[i + 1] for i in range(len(w.dims) - 1))
-    achieved = flops_per_launch / k_dt / 1e12
-    peak = peaks["bf16_tflops"]
+    a_dt = time_kernel(lambda: fr.ensemble_forward(ens_bf16, obs, y), 50, stream)
+    flops_per_launch = N * flops_env_step
     # the same kernel at a batch large enough to fill every SM
     nb = 152 * 128 * 4
     obs_big = obs.repeat(nb // N, 1)
@@ -239,7 +255,7 @@ def run_gpu(args):
             e2e_times.append(time.perf_counter() - t0)
     e2e_value = world * env_steps / statistics.mean(e2e_times)
 
-    launches_per_rollout = 2 + 4 * T
+    launches_per_rollout = 3          # env_reset, fused rollout, metrics replay
     line = {
         "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -247,20 +263,31 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": "stock 2048 envs x 30 assets x 256 steps, 3 x 301-256-256-30 BF16 "
                                "actors, mean combine, 1000 GBM days, bps on",
-                   "n_envs": N, "steps_per_rollout": T, "agents": M, "path": "unfused bf16 tcgen05",
+                   "n_envs": N, "steps_per_rollout": T, "agents": M,
+                   "path": "fused persistent tcgen05 bf16 kernel, trajectory off",
                    "l2": "flushed between timed rollouts (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "plain_fp32": {"value": plain_value, "unit": "env-steps/s",
-                       "ms_per_rollout": 1e3 * statistics.mean(t_fp32)},
+                       "ms_per_rollout": 1e3 * statistics.mean(t_fp32),
+                       "path": "unfused fp32 SIMT, one launch per stage per step"},
+        "unfused_bf16": {"value": env_steps * len(t_unf) / sum(t_unf), "unit": "env-steps/s",
+                         "ms_per_rollout": 1e3 * statistics.mean(t_unf)},
+        "fused_bf16_traj_on": {"value": env_steps * len(t_traj) / sum(t_traj), "unit": "env-steps/s",
+                               "ms_per_rollout": 1e3 * statistics.mean(t_traj),
+                               "traj_bytes_per_rollout": T * N * (env.D * 4 + 30 * 4 + 8 + 1)},
         "speedup_vs_plain": value / world / plain_value,
         "latency": {"p50_ms": None, "p99_ms": None, "note": "serving loop not measured in this run"},
         "e2e": {"value": e2e_value, "unit": "env-steps/s",
                 "h2d_bytes_per_step": len(snap), "d2h_bytes_per_step": N * 3 * 8},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "k_tc_forward (2048 rows x 3 agents per launch)",
+                     "kernel": "k_rollout_fused (2048 envs x 256 steps x 3 agents per launch)",
                      "peak_source": f"bf16_tflops burst, {peak_src}",
-                     "large_batch": {"rows": nb, "achieved": big_tflops, "frac": big_tflops / peak}},
+                     "active_sms": 3 * ((N + 127) // 128),
+                     "actor_kernel": {"rows": N, "tflops": flops_per_launch / a_dt / 1e12,
+                                      "us_per_launch": a_dt * 1e6},
+                     "actor_kernel_large_batch": {"rows": nb, "achieved": big_tflops,
+                                                  "frac": big_tflops / peak}},
         "gpu_launches": launches_per_rollout * args.steps + 1,
         "clocks": clk,
     }
@@ -309,8 +336,47 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_profile(args):
+    """A small case of one kernel for ncu: the 2,048-env workload at a short
+    horizon.  Runs the chosen path twice (the second launch is the one to
+    capture) and exits."""
+    import torch
+    import paper_2501_10709_gb300 as fr
+    from paper_2501_10709_gb300 import build as fb
+    fb.build()
+    w = build_workload()
+    e = w.envs
+    ctx = fr.fr_ctx_create(0)
+    mk = fr.fr_market_create(ctx, w.market)
+    env = fr.env_create(ctx, mk, start=e.start, window=e.W, n_assets=e.Ke, bps=e.bps)
+    prec = fr.PREC_FP32 if args.profile == "plain" else fr.PREC_BF16
+    ens = fr.ensemble_create(ctx, w.dims, w.params, precision=prec)
+    dev = torch.device("cuda:0")
+    if args.profile == "actor":
+        obs = torch.empty(args.rows, env.D, device=dev)
+        fr.env_observe(env, obs[:e.N])
+        obs[e.N:] = obs[:e.N].repeat(args.rows // e.N, 1)[: args.rows - e.N]
+        y = torch.empty(3, args.rows, 30, device=dev)
+        for _ in range(2):
+            fr.ensemble_forward(ens, obs, y)
+    else:
+        if args.profile == "unfused":
+            fr.env_set_rollout_path(env, fr.PATH_UNFUSED)
+        met = torch.empty(e.N, 3, dtype=torch.float64, device=dev)
+        for _ in range(2):
+            fr.env_reset(env)
+            fr.rollout(env, ens, args.T, metrics=met)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "T": args.T, "rows": args.rows,
+                      "errors": fr.ensemble_device_errors(ens)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--profile", choices=["fused", "unfused", "plain", "actor"], default=None,
+                    help="run a small case of one path for a profiler, then exit")
+    ap.add_argument("--T", type=int, default=16)
+    ap.add_argument("--rows", type=int, default=2048)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
@@ -321,7 +387,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

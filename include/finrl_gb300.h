@@ -272,6 +272,15 @@ typedef struct {
 int rollout(fr_env *env, const fr_ensemble *ens, int32_t T,
             const fr_traj *traj, double *metrics, void *stream);
 
+#define FR_PATH_AUTO 0        /* fused kernel when the pair supports it     */
+#define FR_PATH_UNFUSED 1     /* one launch per stage per step              */
+
+/* Choose how rollout() runs this env (default FR_PATH_AUTO).  The fused
+ * path covers stock envs over 30 assets with 8 indicators (mean combine,
+ * tanh output) and crypto envs (vote combine) for BF16 / BF16X3 ensembles of
+ * at most 8 agents; other pairs always run unfused. */
+int env_set_rollout_path(fr_env *env, int32_t path);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,14 +14,15 @@ import numpy as np
 
 from . import _lib
 from ._lib import (ACT_F32_UNIT, ACT_I32_SHARES, ACT_U8_DISCRETE, COMBINE_MEAN,
-                   COMBINE_VOTE, PREC_BF16, PREC_BF16X3, PREC_FP8, PREC_FP32, TASK_CRYPTO,
-                   TASK_STOCK, FrError)
+                   COMBINE_VOTE, PATH_AUTO, PATH_UNFUSED, PREC_BF16, PREC_BF16X3, PREC_FP8,
+                   PREC_FP32, TASK_CRYPTO, TASK_STOCK, FrError)
 
 __all__ = [
     "fr_ctx_create", "fr_market_create", "env_create", "env_reset", "env_step",
     "env_observe", "env_get_state", "env_metrics", "env_snapshot", "env_restore",
     "env_error_count", "env_dims", "ensemble_create", "ensemble_forward",
-    "ensemble_act", "ensemble_device_errors", "rollout", "FrError", "lib",
+    "ensemble_act", "ensemble_device_errors", "rollout", "env_set_rollout_path", "FrError", "lib",
+    "PATH_AUTO", "PATH_UNFUSED",
     "ACT_I32_SHARES", "ACT_F32_UNIT", "ACT_U8_DISCRETE", "PREC_FP32", "PREC_BF16",
     "PREC_FP8", "PREC_BF16X3", "COMBINE_MEAN", "COMBINE_VOTE", "TASK_STOCK", "TASK_CRYPTO",
 ]
@@ -205,6 +206,10 @@ def env_snapshot(env: Env) -> bytes:
 
 def env_restore(env: Env, blob: bytes):
     _lib.check(lib().env_restore(env, blob, len(blob)), "env_restore")
+
+
+def env_set_rollout_path(env: Env, path: int):
+    _lib.check(lib().env_set_rollout_path(env, int(path)), "env_set_rollout_path")
 
 
 def env_error_count(env: Env) -> int:

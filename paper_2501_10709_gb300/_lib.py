@@ -18,6 +18,7 @@ TASK_STOCK, TASK_CRYPTO = 0, 1
 ACT_I32_SHARES, ACT_F32_UNIT, ACT_U8_DISCRETE = 0, 1, 2
 PREC_FP32, PREC_BF16, PREC_FP8, PREC_BF16X3 = 0, 1, 2, 3
 COMBINE_MEAN, COMBINE_VOTE = 0, 1
+PATH_AUTO, PATH_UNFUSED = 0, 1
 
 i32, i64, u32, u64, f64 = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_double
 vp, cp = C.c_void_p, C.c_char_p
@@ -81,6 +82,7 @@ SIGNATURES = {
     "ensemble_act": (i32, [vp, vp, i32, vp, vp]),
     "ensemble_device_errors": (i32, [vp, vp]),
     "rollout": (i32, [vp, vp, i32, vp, vp, vp]),
+    "env_set_rollout_path": (i32, [vp, i32]),
 }
 
 _lock = threading.Lock()

@@ -518,6 +518,14 @@ int env_restore(fr_env *env, const void *host_buf, size_t len)
     return FR_OK;
 }
 
+int env_set_rollout_path(fr_env *env, int32_t path)
+{
+    FR_CHECK(env && (path == FR_PATH_AUTO || path == FR_PATH_UNFUSED), FR_EINVAL,
+             "env_set_rollout_path: bad argument");
+    env->path = path;
+    return FR_OK;
+}
+
 int env_error_count(fr_env *env, uint64_t *count)
 {
     FR_CHECK(env && count, FR_EINVAL, "env_error_count: NULL argument");
@@ -661,7 +669,7 @@ int rollout(fr_env *env, const fr_ensemble *e, int32_t T, const fr_traj *traj, d
     int rc = use_device(env->ctx);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    if (e->precision != FR_PREC_FP32 && tc_rollout_supported(env, e))
+    if (env->path == FR_PATH_AUTO && e->precision != FR_PREC_FP32 && tc_rollout_supported(env, e))
         return tc_rollout(env, e, T, traj, metrics, s);
 
     // plain path: one launch per stage per step

@@ -102,6 +102,7 @@ struct fr_env {
     // scratch for the plain rollout path (grown on demand)
     void *scratch;
     uint64_t scratch_bytes;
+    int path;                   // FR_PATH_*
 };
 
 namespace fr {

@@ -80,16 +80,24 @@ __device__ __forceinline__ int64_t warp_incl_scan(int64_t x, int lane)
     return x;
 }
 
+// int64 -> float32, round to nearest.  Values that fit in 32 bits take the
+// 32-bit conversion (the 64-bit one is a slow path on this GPU); both give
+// the same correctly rounded result.
+__device__ __forceinline__ float ll2f(int64_t x)
+{
+    return (x >= INT32_MIN && x <= INT32_MAX) ? __int2float_rn((int)x) : __ll2float_rn(x);
+}
+
 // Observation / learner scaling: the value rounded to float32 times a
 // float32 constant, one rounding each, no FP64 on the step path.
 __device__ __forceinline__ float obs_scale(int64_t x, float c)
 {
-    return __fmul_rn(__ll2float_rn(x), c);
+    return __fmul_rn(ll2f(x), c);
 }
 
 __device__ __forceinline__ float reward_f32(int64_t r)
 {
-    return __fmul_rn(__ll2float_rn(r), 1e-6f);
+    return __fmul_rn(ll2f(r), 1e-6f);
 }
 
 // ---------------------------------------------------- FP64 episode metrics

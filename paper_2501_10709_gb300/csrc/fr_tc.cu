@@ -19,38 +19,9 @@
 
 #include "fr_common.cuh"
 #include "fr_ptx.cuh"
+#include "fr_tc.cuh"
 
 namespace fr {
-
-constexpr int TC_STAGES = 2;
-constexpr uint32_t TC_CHUNK_MAX = 16384;      // bytes per ring stage
-constexpr int TC_THREADS = 192;               // producer, MMA, 4 epilogue warps
-constexpr uint64_t TC_WAIT_NS = 2000000000ull;
-
-struct TcLayer {
-    int fin, fout;        // true sizes
-    int K, N;             // padded to multiples of 16
-    int KC;               // K columns per streamed chunk
-    int n_chunks;
-    uint32_t off;         // byte offset of the layer's chunks in an agent image
-};
-
-struct TcPlan {
-    int M, L, out_act;
-    int split;            // 1: BF16 operands; 3: hi/lo split, three products
-    int KA;               // K extent of the shared A buffer (max layer K)
-    int tmem_cols;        // power of two >= max N
-    uint32_t agent_bytes;
-    TcLayer layer[MAX_LAYERS];
-};
-
-struct TcImage {
-    TcPlan plan;
-    uint8_t *img;         // device [M][agent_bytes] BF16 chunks
-    float *bias;          // device [M][MAX_LAYERS][256] fp32, zero padded
-    unsigned *err;        // device error flags
-    uint64_t bytes;
-};
 
 namespace {
 
@@ -83,6 +54,7 @@ inline uint32_t chunk_off(int N, int n, int kk)
 bool make_plan(const fr_ensemble *e, TcPlan &p)
 {
     p.split = e->precision == FR_PREC_BF16X3 ? 3 : 1;
+    p.parts = p.split == 3 ? 2 : 1;
     p.M = e->M;
     p.L = e->L;
     p.out_act = e->out_act;
@@ -96,12 +68,12 @@ bool make_plan(const fr_ensemble *e, TcPlan &p)
         ly.K = round16(ly.fin);
         ly.N = round16(ly.fout);
         if (ly.N > 256 || ly.K > 512) return false;
-        int kc = (int)(TC_CHUNK_MAX / (uint32_t)(ly.N * 2 * p.split));
+        int kc = (int)(TC_CHUNK_MAX / (uint32_t)(ly.N * 2 * p.parts));
         kc = kc / 16 * 16;
         ly.KC = kc < ly.K ? kc : ly.K;
         ly.n_chunks = (ly.K + ly.KC - 1) / ly.KC;
         ly.off = off;
-        off += (uint32_t)ly.N * ly.K * 2 * p.split;
+        off += (uint32_t)ly.N * ly.K * 2 * p.parts;
         p.KA = ly.K > p.KA ? ly.K : p.KA;
         nmax = ly.N > nmax ? ly.N : nmax;
     }
@@ -112,26 +84,9 @@ bool make_plan(const fr_ensemble *e, TcPlan &p)
     return true;
 }
 
-// A operand bytes (one part)
-inline uint32_t a_bytes(const TcPlan &p) { return (uint32_t)(p.KA / 8) * 2048u; }
-
 uint32_t tc_smem_bytes(const TcPlan &p)
 {
-    return a_bytes(p) * (p.split == 3 ? 2u : 1u) + TC_STAGES * TC_CHUNK_MAX + 256u + 1024u;
-}
-
-// Eight floats -> BF16 hi parts (round to nearest) and the BF16 rounding of
-// what hi leaves over (x - hi), packed two per word in K order.
-__device__ __forceinline__ void split_pack8(const float *v, uint32_t *hi, uint32_t *lo)
-{
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-        const float2 hf = __bfloat1622float2(h);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
-        hi[i] = *(const uint32_t *)&h;
-        lo[i] = *(const uint32_t *)&l;
-    }
+    return a_part_bytes(p) * (p.split == 3 ? 2u : 1u) + TC_STAGES * TC_CHUNK_MAX + 256u + 1024u;
 }
 
 // ------------------------------------------------------------------ kernel
@@ -192,10 +147,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const ui
                     const uint32_t ph = (uint32_t)(i / TC_STAGES) & 1u;
                     if (!mbar_wait(&empty[s], ph ^ 1u, abort, err, 1u, TC_WAIT_NS)) { ok = false; break; }
                     const int kc = min(ly.KC, ly.K - c * ly.KC);
-                    const uint32_t bytes = (uint32_t)(ly.N * kc * 2 * plan.split);
+                    const uint32_t bytes = (uint32_t)(ly.N * kc * 2 * plan.parts);
                     mbar_arrive_expect_tx(&full[s], bytes);
                     bulk_g2s(ring + s * TC_CHUNK_MAX,
-                             aimg + ly.off + (size_t)c * ly.N * ly.KC * 2 * plan.split, bytes, &full[s]);
+                             aimg + ly.off + (size_t)c * ly.N * ly.KC * 2 * plan.parts, bytes, &full[s]);
                     ++i;
                 }
             }
@@ -364,7 +319,7 @@ int tc_create(fr_ensemble *e)
                 for (int k = 0; k < ly.fin; ++k) {
                     const int c = k / ly.KC, kk = k % ly.KC;
                     const int kc = std::min(ly.KC, ly.K - c * ly.KC);
-                    const size_t off = ly.off + (size_t)c * ly.N * ly.KC * 2 * p.split + chunk_off(ly.N, n, kk);
+                    const size_t off = ly.off + (size_t)c * ly.N * ly.KC * 2 * p.parts + chunk_off(ly.N, n, kk);
                     const float wv = W[(size_t)n * ly.fin + k];
                     const uint16_t b = f32_to_bf16_rne(wv);
                     memcpy(aimg + off, &b, 2);
@@ -425,14 +380,6 @@ int tc_forward(const fr_ensemble *e, const float *obs, int ld, int n, float *y, 
                                                                   t->err);
     FR_CUDA(cudaGetLastError());
     return FR_OK;
-}
-
-bool tc_rollout_supported(const fr_env *, const fr_ensemble *) { return false; }
-
-int tc_rollout(fr_env *, const fr_ensemble *, int, const fr_traj *, double *, cudaStream_t)
-{
-    set_error("fused rollout not available for this configuration");
-    return FR_EINVAL;
 }
 
 int tc_device_errors(const fr_ensemble *e, unsigned *flags)

@@ -111,3 +111,84 @@ def test_rollout_zero_steps_and_bad_pairs(ctx, dev):
                              combine=fr.COMBINE_VOTE, out_act=0)
     with pytest.raises(fr.FrError):
         fr.rollout(env, bad, 4)
+
+
+def _stock_env(ctx, mk, e, auto_reset=False):
+    return fr.env_create(ctx, mk, start=e.start, window=e.W, n_assets=e.Ke, bps=e.bps,
+                         init_cash=e.init_cash, hmax=e.hmax, fee_bps=e.fee_bps, auto_reset=auto_reset)
+
+
+@pytest.mark.parametrize("auto_reset", [False, True])
+def test_fused_uneven_windows_and_assets(ctx, dev, auto_reset):
+    # uneven asset counts and windows in one launch, frozen (or restarted)
+    # envs, a ragged last tile: teacher-forced against the oracle
+    mk_np = synth.stock_market(300, 30, seed=41)
+    e = synth.stock_envs_uneven(300, 30, 300, k_lo=10, w_lo=5, w_hi=60, seed=41)
+    params = synth.actor_params(synth.STOCK_DIMS, 3, seed=42)
+    mk = fr.fr_market_create(ctx, mk_np)
+    env = _stock_env(ctx, mk, e, auto_reset)
+    ens = fr.ensemble_create(ctx, synth.STOCK_DIMS, params, precision=fr.PREC_BF16)
+    T = 70
+    tr = _traj(T, e.N, env.D, 30, dev)
+    met = torch.empty(e.N, 3, dtype=torch.float64, device=dev)
+    fr.rollout(env, ens, T, traj=tr, metrics=met)
+    torch.cuda.synchronize()
+    assert fr.ensemble_device_errors(ens) == 0
+    g = {k: v.cpu().numpy() for k, v in tr.items()}
+    ref = oracle.stock_run(mk_np, e.Ke, e.start, e.W, e.bps, init_cash=e.init_cash, hmax=100,
+                           fee_bps=10, T=T, act_f32=g["act"], auto_reset=auto_reset)
+    for k in ("obs", "rew", "rew_f32", "done"):
+        assert np.array_equal(g[k], ref[k]), k
+    assert np.array_equal(met.cpu().numpy(), ref["metrics"])
+    cash = torch.empty(e.N, dtype=torch.int64, device=dev)
+    hold = torch.empty(e.N, 30, dtype=torch.int32, device=dev)
+    steps = torch.empty(e.N, dtype=torch.int32, device=dev)
+    fr.env_get_state(env, cash=cash, hold=hold, steps=steps)
+    torch.cuda.synchronize()
+    assert np.array_equal(cash.cpu().numpy(), ref["cash"][-1])
+    assert np.array_equal(hold.cpu().numpy(), ref["hold"][-1])
+
+
+def test_fused_rollout_in_pieces_equals_one_rollout(ctx, dev):
+    w = synth.workload_stock_2048(N=512, T=60)        # 61-day windows: 40 steps leave 20
+    e = w.envs
+    mk = fr.fr_market_create(ctx, w.market)
+    ens = fr.ensemble_create(ctx, w.dims, w.params, precision=fr.PREC_BF16)
+    env1 = _stock_env(ctx, mk, e)
+    env2 = _stock_env(ctx, mk, e)
+    r1 = torch.zeros(40, e.N, dtype=torch.int64, device=dev)
+    r2 = torch.zeros(40, e.N, dtype=torch.int64, device=dev)
+    m1 = torch.empty(e.N, 3, dtype=torch.float64, device=dev)
+    m2 = torch.empty(e.N, 3, dtype=torch.float64, device=dev)
+    fr.rollout(env1, ens, 40, traj={"rew": r1}, metrics=m1)
+    fr.rollout(env2, ens, 15, traj={"rew": r2[:15]})
+    fr.rollout(env2, ens, 25, traj={"rew": r2[15:]}, metrics=m2)
+    torch.cuda.synchronize()
+    assert torch.equal(r1, r2) and torch.equal(m1, m2)
+    # and the unfused env step continues from the fused rollout's state
+    q = torch.zeros(e.N, 30, dtype=torch.int32, device=dev)
+    rw = torch.empty(e.N, dtype=torch.int64, device=dev)
+    fr.env_step(env2, q, fr.ACT_I32_SHARES, rew=rw)
+    steps = torch.empty(e.N, dtype=torch.int32, device=dev)
+    fr.env_get_state(env2, steps=steps)
+    torch.cuda.synchronize()
+    assert (steps == 41).all()
+
+
+def test_fused_and_unfused_paths_agree_on_prices_and_accounting(ctx, dev):
+    # both paths replayed by the oracle stay bit-exact; their actions differ
+    # only by the exchange precision of the agents' outputs
+    w = synth.workload_stock_small()
+    e = w.envs
+    mk = fr.fr_market_create(ctx, w.market)
+    ens = fr.ensemble_create(ctx, w.dims, w.params, precision=fr.PREC_BF16)
+    acts = []
+    for path in (fr.PATH_AUTO, fr.PATH_UNFUSED):
+        env = _stock_env(ctx, mk, e)
+        fr.env_set_rollout_path(env, path)
+        tr = _traj(w.T, e.N, env.D, 30, dev)
+        fr.rollout(env, ens, w.T, traj=tr)
+        torch.cuda.synchronize()
+        acts.append(tr["act"].cpu().numpy())
+    # the first step acts on identical observations
+    assert np.abs(acts[0][0] - acts[1][0]).max() < 2e-3
