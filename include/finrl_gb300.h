@@ -245,6 +245,24 @@ int ensemble_forward(const fr_ensemble *ens, const float *obs, int32_t n,
 int ensemble_act(const fr_ensemble *ens, const float *obs, int32_t n,
                  void *act, void *stream);
 
+/* ensemble_act without any allocation, for callers that must not allocate
+ * device memory while they run (a loop with a fixed memory footprint, a host
+ * application that owns every device buffer, work being recorded into a
+ * graph that must not gain allocation nodes).  The paper has no counterpart;
+ * this is a library convenience.
+ * Same arguments, layouts and results as ensemble_act.  Its scratch is a
+ * fixed 16 MiB array inside the library image (held on every GPU that loads
+ * the library until the process exits), so no cudaMalloc, cudaFree or other
+ * allocating routine is called.  A batch whose scratch would not fit
+ * (roughly (2*hidden + out)*M floats per row on the fp32 path, out*M on the
+ * tensor-core paths) fails with FR_EINVAL and a message giving the largest
+ * batch for this ensemble.  The first call on a device looks up the array's
+ * device address; make that first call before any stream capture.  All calls
+ * share the one array: calls whose work overlaps on the GPU (different
+ * streams, or different threads) race and must be serialised by the caller. */
+int ensemble_act_noalloc(const fr_ensemble *ens, const float *obs, int32_t n,
+                         void *act, void *stream);
+
 /* Error flags raised on the device by the tensor-core kernels of this
  * ensemble (a bounded wait that gave up); 0 when none (synchronous). */
 int ensemble_device_errors(const fr_ensemble *ens, uint32_t *flags);

@@ -21,7 +21,7 @@ __all__ = [
     "fr_ctx_create", "fr_market_create", "env_create", "env_reset", "env_step",
     "env_observe", "env_get_state", "env_metrics", "env_snapshot", "env_restore",
     "env_error_count", "env_dims", "ensemble_create", "ensemble_forward",
-    "ensemble_act", "ensemble_device_errors", "rollout", "env_set_rollout_path", "FrError", "lib",
+    "ensemble_act", "ensemble_act_noalloc", "ensemble_device_errors", "rollout", "env_set_rollout_path", "FrError", "lib",
     "PATH_AUTO", "PATH_UNFUSED",
     "ACT_I32_SHARES", "ACT_F32_UNIT", "ACT_U8_DISCRETE", "PREC_FP32", "PREC_BF16",
     "PREC_FP8", "PREC_BF16X3", "COMBINE_MEAN", "COMBINE_VOTE", "TASK_STOCK", "TASK_CRYPTO",
@@ -247,6 +247,18 @@ def ensemble_act(ens: Ensemble, obs, act, stream=None):
     want = (torch.float32, n * ens.dims[-1]) if ens.combine == COMBINE_MEAN else (torch.uint8, n)
     _lib.check(lib().ensemble_act(ens, _dptr(obs, torch.float32, n * ens.dims[0], "obs"), n,
                                   _dptr(act, *want, "act"), _stream(stream)), "ensemble_act")
+
+
+def ensemble_act_noalloc(ens: Ensemble, obs, act, stream=None):
+    """ensemble_act on the library's fixed scratch array (no allocation).
+    For callers that cannot allocate device memory while they run; calls that
+    overlap on the GPU share the scratch and must be serialised."""
+    import torch
+    n = obs.shape[0]
+    want = (torch.float32, n * ens.dims[-1]) if ens.combine == COMBINE_MEAN else (torch.uint8, n)
+    _lib.check(lib().ensemble_act_noalloc(ens, _dptr(obs, torch.float32, n * ens.dims[0], "obs"), n,
+                                          _dptr(act, *want, "act"), _stream(stream)),
+               "ensemble_act_noalloc")
 
 
 def ensemble_device_errors(ens: Ensemble) -> int:

@@ -83,6 +83,7 @@ SIGNATURES = {
     "ensemble_device_errors": (i32, [vp, vp]),
     "rollout": (i32, [vp, vp, i32, vp, vp, vp]),
     "env_set_rollout_path": (i32, [vp, i32]),
+    "ensemble_act_noalloc": (i32, [vp, vp, i32, vp, vp]),
 }
 
 _lock = threading.Lock()
