@@ -417,6 +417,7 @@ void env_destroy(fr_env *env)
     cudaSetDevice(env->ctx->device);
     dev_free(env->ctx, env->block, env->bytes);
     dev_free(env->ctx, env->scratch, env->scratch_bytes);
+    dev_free(env->ctx, env->slot_of_env, 4ull * env->v.N + 4ull * 32);
     delete env;
 }
 
@@ -607,6 +608,7 @@ void ensemble_destroy(fr_ensemble *e)
 {
     if (!e) return;
     cudaSetDevice(e->ctx->device);
+    f2_release(e);
     tc_destroy(e);
     dev_free(e->ctx, e->params, (uint64_t)e->M * e->P * 4);
     dev_free(e->ctx, e->weights, 4ull * MAX_AGENTS);
@@ -669,8 +671,10 @@ int rollout(fr_env *env, const fr_ensemble *e, int32_t T, const fr_traj *traj, d
     int rc = use_device(env->ctx);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    if (env->path == FR_PATH_AUTO && e->precision != FR_PREC_FP32 && tc_rollout_supported(env, e))
-        return tc_rollout(env, e, T, traj, metrics, s);
+    if (env->path == FR_PATH_AUTO && e->precision != FR_PREC_FP32) {
+        if (f2_supported(env, e)) return f2_rollout(env, e, T, traj, metrics, s);
+        if (tc_rollout_supported(env, e)) return tc_rollout(env, e, T, traj, metrics, s);
+    }
 
     // plain path: one launch per stage per step
     const int N = v.N, out = e->dims[e->L];

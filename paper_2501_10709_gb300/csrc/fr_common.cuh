@@ -103,6 +103,10 @@ struct fr_env {
     void *scratch;
     uint64_t scratch_bytes;
     int path;                   // FR_PATH_*
+    // asset-count slots of the fused stock kernel's indicator table
+    int32_t *slot_of_env;       // device [N] (+ slot_ke [32] after it)
+    int32_t *slot_ke;
+    int n_slots;
 };
 
 namespace fr {
@@ -180,6 +184,14 @@ void tc_destroy(fr_ensemble *e);
 int tc_forward(const fr_ensemble *e, const float *obs, int ld, int n, float *y, cudaStream_t s);
 // Whether the fused persistent rollout supports this env / ensemble pair.
 bool tc_rollout_supported(const fr_env *env, const fr_ensemble *e);
+// FP64 episode accumulators from a rollout's value log (fr_fused.cu)
+cudaError_t launch_metrics_replay(const EnvView &v, const int64_t *vlog, int T, double *metrics,
+                                  cudaStream_t s);
+// fused stock rollout with resident weights (fr_fused2.cu)
+bool f2_supported(const fr_env *env, const fr_ensemble *e);
+int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, double *metrics,
+               cudaStream_t s);
+void f2_release(const fr_ensemble *e);
 int tc_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, double *metrics,
                cudaStream_t s);
 }  // namespace fr

@@ -892,9 +892,15 @@ int tc_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         FR_CUDA(cudaLaunchKernelEx(&cfg, k_rollout_fused<FR_TASK_CRYPTO>, a));
     }
-    k_metrics_replay<<<ceil_div(v.N, 256), 256, 0, s>>>(v, a.vlog, T, metrics);
-    FR_CUDA(cudaGetLastError());
+    FR_CUDA(launch_metrics_replay(v, a.vlog, T, metrics, s));
     return FR_OK;
+}
+
+cudaError_t launch_metrics_replay(const EnvView &v, const int64_t *vlog, int T, double *metrics,
+                                  cudaStream_t s)
+{
+    k_metrics_replay<<<ceil_div(v.N, 256), 256, 0, s>>>(v, vlog, T, metrics);
+    return cudaGetLastError();
 }
 
 }  // namespace fr

@@ -1,0 +1,886 @@
+// fr_fused2.cu -- fused stock rollout with resident weights.
+//
+// One thread-block cluster of 2M CTAs owns a tile of 128 envs for all T
+// steps.  CTA (j, h) -- cluster rank 2j + h -- holds output half h of every
+// hidden layer of agent j, so each agent's BF16 weights stay resident in
+// shared memory, split over a CTA pair, and are never re-read per step:
+//
+//   layer 1  the state is [cash, p, h, f] (Sec. 3.1).  Its indicator block f
+//            depends only on the day and the env's asset count, never on the
+//            actions, so  W1[:, f] f + b1  is precomputed per (day, asset
+//            count) into a table Z by a separate GEMM; per step the tensor
+//            cores only multiply the 61 trajectory-dependent entries
+//            (cash, prices, holdings; K = 64) and the epilogue adds Z;
+//   layer 2  full h1 (both halves: the partner writes its half into this
+//            CTA's A operand through distributed shared memory), N-half;
+//   layer 3  K-split: the half h = 1 CTA sends its partial sums to its
+//            partner, which adds bias, applies tanh and pushes the agent's
+//            actions (fp16) to the env's owner CTA.
+//
+// Env r of the tile is owned by the CTA of rank r mod 2M: one warp per env,
+// lane = asset, state in registers.  The owner combines the agents' actions
+// (anchored weighted mean, Sec. 5.2.1), discretises, trades, and writes the
+// env's next observation row straight into every CTA's A operand.  All
+// waits are mbarriers (remote arrivals released at cluster scope) bounded by
+// the global timer.  The shared buffers need no double buffering: every
+// write of step s + 1 depends, through the step's chain, on every read of
+// step s.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "fr_env_dev.cuh"
+#include "fr_ptx.cuh"
+#include "fr_tc.cuh"
+
+namespace fr {
+
+namespace {
+
+constexpr int F2_THREADS = 256;           // 8 env / epilogue warps; warp 0 also loads and issues
+constexpr int F2_ENV_WARPS = 8;
+constexpr int SK2 = 30, SI2 = 8;
+constexpr int SD2 = 1 + 2 * SK2 + SI2 * SK2;   // 301
+constexpr int NSTATE = 1 + 2 * SK2;            // 61 trajectory-dependent entries
+constexpr int KS = 64;                         // their padded K
+constexpr int NIND = SI2 * SK2;                // 240 indicator entries
+constexpr int64_t VLOG_NONE2 = INT64_MIN;
+
+// One CTA's resident weights: three layers, chunked canonical layout.
+struct F2Layer {
+    int K, N;             // padded
+    int KC, n_chunks;
+    uint32_t off;         // byte offset in the CTA image
+};
+
+struct F2Plan {
+    int M, H1, H2;        // agents, hidden widths
+    int n1, n2;           // N of layer 1 / 2 halves (H/2)
+    F2Layer l1, l2, l3;
+    uint32_t cta_bytes;   // weights per CTA (multiple of 1024)
+    uint32_t a_bytes;     // A operand bytes (max K / 8 * 2048)
+};
+
+struct F2Image {
+    F2Plan plan;
+    uint8_t *img;         // device [M][2][cta_bytes]
+    float *b2;            // device [M][H2]
+    float *b3;            // device [M][32]
+    float *wind;          // device [M][H1*240 + H1]: W1 indicator columns, then b1
+    const fr_ensemble *owner;
+    uint64_t bytes;
+};
+
+struct F2Args {
+    EnvView v;
+    F2Plan plan;
+    const uint8_t *img;
+    const float *b2, *b3;
+    const float *Z;       // [M][n_ctx][H1]
+    const int32_t *slot; // [N] asset-count slot of each env
+    int n_ctx_per_agent;
+    float w[MAX_AGENTS];
+    int T;
+    float *tr_obs;
+    int obs_ld;
+    float *tr_act;
+    int64_t *tr_rew;
+    float *tr_rew_f32;
+    uint8_t *tr_done;
+    int64_t *vlog;
+    unsigned *err;
+};
+
+bool f2_plan(const fr_ensemble *e, F2Plan &p)
+{
+    if (e->L != 3 || e->dims[0] != SD2 || e->dims[3] != SK2 || e->M > 4 || e->M < 2) return false;
+    p.M = e->M;
+    p.H1 = e->dims[1];
+    p.H2 = e->dims[2];
+    if (p.H1 % 64 || p.H2 % 64 || p.H1 > 256 || p.H2 > 256) return false;
+    p.n1 = p.H1 / 2;
+    p.n2 = p.H2 / 2;
+    uint32_t off = 0;
+    auto mk = [&](F2Layer &l, int K, int N) {
+        l.K = K;
+        l.N = N;
+        int kc = (int)(TC_CHUNK_MAX / (uint32_t)(N * 2)) / 16 * 16;
+        l.KC = std::min(kc, K);
+        l.n_chunks = (K + l.KC - 1) / l.KC;
+        l.off = off;
+        off += (uint32_t)(N * K * 2);
+    };
+    mk(p.l1, KS, p.n1);
+    mk(p.l2, p.H1, p.n2);
+    mk(p.l3, p.n2, 32);
+    p.cta_bytes = (off + 1023u) & ~1023u;
+    // A operand: h1 in chunks [0, H1/8) (layer 2), the observation's state
+    // part in its own chunks [H1/8, H1/8 + 8) so that the partner's h1 half
+    // can never land on an observation this CTA's layer 1 is still reading;
+    // h2's half (layer 3) reuses chunks [0, n2/8)
+    p.a_bytes = (uint32_t)(p.H1 / 8 + KS / 8) * 2048u;
+    return true;
+}
+
+// shared-memory carve-up
+struct F2Smem {
+    uint32_t w, a, pbuf, xbuf, ctx, bias, bars, total;
+};
+
+__host__ __device__ inline F2Smem f2_smem(const F2Plan &p)
+{
+    F2Smem s;
+    s.w = 0;
+    s.a = p.cta_bytes;
+    s.pbuf = s.a + p.a_bytes;                       // [128][32] fp32 partial sums
+    s.xbuf = s.pbuf + 128u * 32u * 4u;              // [M][128][32] fp16 agent actions
+    s.ctx = s.xbuf + (uint32_t)p.M * 128u * 64u;    // [128] int32 Z row of each env
+    s.bias = s.ctx + 512u;                          // this CTA's b2 half [128] + b3 [32]
+    s.bars = s.bias + 640u;
+    s.total = s.bars + 256u;
+    return s;
+}
+
+// barrier slots
+enum { B_W = 0, B_OBS, B_ACC, B_H1, B_H2, B_P, B_X, B_COUNT };
+
+__device__ __forceinline__ bool f2_wait(uint64_t *bar, uint32_t parity, volatile int *abort, unsigned *err,
+                                        unsigned code, bool cluster_scope)
+{
+    using namespace ptx;
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0)
+        ok = cluster_scope ? mbar_wait_cluster(bar, parity, abort, err, code, TC_WAIT_NS)
+                           : mbar_wait(bar, parity, abort, err, code, TC_WAIT_NS);
+    ok = __shfl_sync(FULL_MASK, ok, 0);
+    __syncwarp();
+    return ok != 0;
+}
+
+__device__ __forceinline__ void pack8_bf16(const float *v, uint32_t *w)
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        w[i] = *(const uint32_t *)&b;
+    }
+}
+
+// ------------------------------------------------------------- MMA issue
+// One layer of this CTA's agent half: K-steps of 16 over the resident
+// weight chunks, accumulator in TMEM, completion signalled on `acc`.  Issued
+// by lane 0 of env warp 0 at the point where that warp waits on the layer's
+// operands anyway; a dedicated issuer warp would make the block 10 warps,
+// which caps every thread at 168 registers and makes the env code spill.
+__device__ __forceinline__ void f2_layer(const F2Layer &l, uint32_t d_tmem, uint32_t a_at, uint32_t w_base,
+                                         uint64_t *acc)
+{
+    using namespace ptx;
+    fence_proxy_async_smem();
+    tc_fence_after();
+    const uint32_t idesc = idesc_bf16(128, l.N);
+    const uint32_t lbo_b = (uint32_t)(l.N * 16);
+    int kg = 0;
+    for (int c = 0; c < l.n_chunks; ++c) {
+        const int kc = min(l.KC, l.K - c * l.KC);
+        const uint32_t b_base = w_base + l.off + (uint32_t)(c * l.N * l.KC * 2);
+        for (int kk = 0; kk < kc; kk += 16, kg += 16) {
+            const uint64_t ad = smem_desc(a_at + (uint32_t)(kg / 8) * 2048u, 2048u, 128u);
+            const uint64_t bd = smem_desc(b_base + (uint32_t)(kk / 8) * lbo_b, lbo_b, 128u);
+            mma_bf16(d_tmem, ad, bd, idesc, kg > 0 ? 1u : 0u);
+        }
+    }
+    mma_commit(acc);
+}
+
+// --------------------------------------------- owner: one env, warp-wide
+struct OwnEnv {
+    int64_t cash;        // uniform
+    int t, start, W, Ke; // uniform
+    int done;            // uniform
+    int slot;            // uniform, asset-count slot
+    int64_t p;           // this lane's asset price at day start + t
+    int32_t h;           // this lane's holding
+    int bps;             // this lane's perturbation
+};
+
+// the next observation row of env r: chunks 0..7 of the A operand in every
+// CTA of the cluster, plus its Z row index
+__device__ __forceinline__ void own_publish(const F2Args &a, const OwnEnv &s, bool valid, int r, uint32_t a_base,
+                                            uint32_t ctx_addr, int M2, int lane, int64_t trow)
+{
+    using namespace ptx;
+    const float pv = (valid && lane < s.Ke) ? obs_scale(s.p, 1e-4f) : 0.0f;
+    const float hv = (valid && lane < s.Ke) ? __fmul_rn(__int2float_rn(s.h), 1e-2f) : 0.0f;
+    const float cv = valid ? obs_scale(s.cash, 1e-8f) : 0.0f;
+    // lanes 0..7 build chunk `lane` = positions 8*lane .. 8*lane+7
+    float v8[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int pos = 8 * lane + u;
+        const float fp = __shfl_sync(FULL_MASK, pv, (pos - 1) & 31);
+        const float fh = __shfl_sync(FULL_MASK, hv, (pos - 1 - SK2) & 31);
+        v8[u] = pos == 0 ? cv : (pos <= SK2 ? fp : (pos < NSTATE ? fh : 0.0f));
+    }
+    const uint32_t row_off = (uint32_t)(r / 8) * 128u + (uint32_t)(r % 8) * 16u;
+    const uint32_t a_obs = a_base + (uint32_t)(a.plan.H1 / 8) * 2048u;
+    if (lane < 8) {
+        uint32_t w[4];
+        pack8_bf16(v8, w);
+        for (int m = 0; m < M2; ++m)
+            st_cluster_v4(map_shared_rank(a_obs + (uint32_t)lane * 2048u + row_off, (uint32_t)m), w[0], w[1], w[2],
+                          w[3]);
+    } else if (lane < 8 + M2) {
+        const int zrow = valid ? s.slot * a.v.n_days + s.start + s.t : 0;
+        asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(map_shared_rank(ctx_addr + 4u * r, (uint32_t)(lane - 8))),
+                     "r"(zrow)
+                     : "memory");
+    }
+    // fp32 trajectory observation of the step about to be taken
+    if (a.tr_obs && valid && trow >= 0) {
+        float *o = a.tr_obs + trow * a.obs_ld;
+        if (lane == 0) o[0] = cv;
+        if (lane < SK2) {
+            o[1 + lane] = pv;
+            o[1 + SK2 + lane] = hv;
+        }
+        const float *f = a.v.ind + (int64_t)(s.start + s.t) * NIND;
+        for (int i = lane; i < NIND; i += 32) o[NSTATE + i] = (i % SK2) < s.Ke ? __ldg(f + i) : 0.0f;
+    }
+}
+
+template <int NOWN>
+__device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, const F2Smem L_in, uint64_t *bars,
+                            volatile int *abort, int warp, int lane, int rank, int tile)
+{
+    using namespace ptx;
+    const F2Args a = a_in;
+    const F2Smem L = L_in;
+    const EnvView v = a.v;
+    const F2Plan p = a.plan;
+    const float w1 = a.w[1], w2 = a.w[2], w3 = a.w[3];
+    const int M = p.M, M2 = 2 * M;
+    const int j = rank >> 1, hh = rank & 1;
+    const int ew = warp;                           // 0..7
+    const int q = warp & 3;                        // TMEM lane quarter
+    const int col_half = ew >> 2;                  // 0 or 1: which half of the columns this warp reads
+    const int r = q * 32 + lane;                   // epilogue row
+    const uint32_t tmem_row = tmem + ((uint32_t)(q * 32) << 16);
+    const uint32_t a_base = smem_u32(smem + L.a);
+    const uint32_t row_off = (uint32_t)(r / 8) * 128u + (uint32_t)(r % 8) * 16u;
+    const uint32_t pbuf = smem_u32(smem + L.pbuf);
+    const uint32_t xbuf = smem_u32(smem + L.xbuf);
+    const uint32_t ctx_addr = smem_u32(smem + L.ctx);
+    const int32_t *ctxv = (const int32_t *)(smem + L.ctx);
+    uint64_t *obs_ready = &bars[B_OBS], *acc = &bars[B_ACC], *h1r = &bars[B_H1], *h2r = &bars[B_H2];
+    uint64_t *prdy = &bars[B_P], *xrdy = &bars[B_X];
+    const int tile0 = tile * 128;
+    const bool issuer = ew == 0;
+    const uint32_t w_base = smem_u32(smem + L.w);
+    const uint32_t a_obs = a_base + (uint32_t)(p.H1 / 8) * 2048u;
+    if (issuer && lane == 0) {
+        // resident weights: this CTA's image, loaded once
+        const uint8_t *src = a.img + (size_t)rank * p.cta_bytes;
+        mbar_arrive_expect_tx(&bars[B_W], p.cta_bytes);
+        for (uint32_t o = 0; o < p.cta_bytes; o += TC_CHUNK_MAX) {
+            const uint32_t n = min(TC_CHUNK_MAX, p.cta_bytes - o);
+            bulk_g2s(smem + L.w + o, src + o, n, &bars[B_W]);
+        }
+    }
+
+    // owned envs of this warp: rows r0 = rank + M2 * (ew + 8 * i)
+    OwnEnv own[NOWN];
+    int orow[NOWN];
+#pragma unroll
+    for (int i = 0; i < NOWN; ++i) {
+        orow[i] = rank + M2 * (ew + F2_ENV_WARPS * i);
+        const int e = tile0 + orow[i];
+        OwnEnv &s = own[i];
+        s.cash = 0; s.t = 0; s.start = 0; s.W = 2; s.Ke = 0; s.done = 1; s.slot = 0; s.p = 0; s.h = 0; s.bps = 0;
+        if (orow[i] < 128 && e < v.N) {
+            s.cash = v.cash[e];
+            s.t = v.t[e];
+            s.start = v.start[e];
+            s.W = v.W[e];
+            s.Ke = v.Ke[e];
+            s.done = v.done[e];
+            s.slot = a.slot[e];
+            if (lane < s.Ke) {
+                s.h = v.hold[(int64_t)e * KP + lane];
+                s.bps = v.bps[(int64_t)e * KP + lane];
+                s.p = perturb(__ldg(v.close + (int64_t)(s.start + s.t) * SK2 + lane), s.bps);
+            }
+        }
+    }
+    // observation of step 0
+#pragma unroll
+    for (int i = 0; i < NOWN; ++i) {
+        if (orow[i] >= 128) continue;
+        const int e = tile0 + orow[i];
+        own_publish(a, own[i], e < v.N, orow[i], a_base, ctx_addr, M2, lane, e < v.N ? (int64_t)e : -1);
+    }
+    fence_proxy_async_cluster();
+    __syncwarp();
+    if (lane == 0)
+        for (int m = 0; m < M2; ++m) mbar_arrive_remote(map_shared_rank(smem_u32(obs_ready), (uint32_t)m));
+
+    const float *zbase = a.Z + (size_t)j * a.n_ctx_per_agent * p.H1;
+    int T = a.T;
+    if (issuer && !f2_wait(&bars[B_W], 0u, abort, a.err, 1u, false)) T = 0;
+    for (int s = 0; s < T; ++s) {
+        const uint32_t ph = (uint32_t)s & 1u;
+        // ------------------------------------------- E1: + Z + b1 -> ReLU
+        // the observation barrier also publishes each env's Z row: read it
+        // and start the row's loads while layer 1 runs on the tensor cores
+        if (!f2_wait(obs_ready, ph, abort, a.err, 16u, true)) break;
+        if (issuer && lane == 0) f2_layer(p.l1, tmem, a_obs, w_base, acc);
+        const int nc1 = p.n1 / 2;                          // columns per warp (<= 64)
+        const int c01 = col_half * nc1;
+        const float *zrow = zbase + (size_t)ctxv[r] * p.H1 + hh * p.n1 + c01;
+        for (int i = 0; i < nc1; i += 32) asm volatile("prefetch.global.L1 [%0];" ::"l"(zrow + i));
+        if (!f2_wait(acc, (uint32_t)(3 * s) & 1u, abort, a.err, 16u, false)) break;
+        tc_fence_after();
+        {
+            const int nc = nc1;
+            const int c0 = c01;
+            const uint32_t dst_chunk0 = (uint32_t)((hh * p.n1 + c0) / 8);
+            for (int cc = 0; cc < nc; cc += 16) {
+                uint32_t vv[16];
+                __syncwarp();
+                tmem_ld16(tmem_row + (uint32_t)(c0 + cc), vv);
+                tmem_ld_wait();
+                float x[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) x[i] = fmaxf(__uint_as_float(vv[i]) + __ldg(zrow + cc + i), 0.0f);
+                uint32_t w0[4], w1[4];
+                pack8_bf16(x, w0);
+                pack8_bf16(x + 8, w1);
+                const uint32_t at = a_base + (dst_chunk0 + (uint32_t)(cc / 8)) * 2048u + row_off;
+                st_shared_v4(at, w0[0], w0[1], w0[2], w0[3]);
+                st_shared_v4(at + 2048u, w1[0], w1[1], w1[2], w1[3]);
+                const uint32_t pt = map_shared_rank(at, (uint32_t)(rank ^ 1));
+                st_cluster_v4(pt, w0[0], w0[1], w0[2], w0[3]);
+                st_cluster_v4(pt + 2048u, w1[0], w1[1], w1[2], w1[3]);
+            }
+        }
+        fence_proxy_async_smem();
+        fence_proxy_async_cluster();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+            mbar_arrive(h1r);
+            mbar_arrive_remote(map_shared_rank(smem_u32(h1r), (uint32_t)(rank ^ 1)));
+        }
+        if (issuer) {
+            if (!f2_wait(h1r, ph, abort, a.err, 4u, true)) break;
+            if (lane == 0) f2_layer(p.l2, tmem, a_base, w_base, acc);
+            __syncwarp();
+        }
+        // ------------------------------------------------- E2: + b2 -> ReLU
+        if (!f2_wait(acc, (uint32_t)(3 * s + 1) & 1u, abort, a.err, 16u, false)) break;
+        tc_fence_after();
+        {
+            const float *b2 = (const float *)(smem + L.bias);
+            const int nc = p.n2 / 2;
+            const int c0 = col_half * nc;
+            for (int cc = 0; cc < nc; cc += 16) {
+                uint32_t vv[16];
+                __syncwarp();
+                tmem_ld16(tmem_row + (uint32_t)(c0 + cc), vv);
+                tmem_ld_wait();
+                float x[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) x[i] = fmaxf(__uint_as_float(vv[i]) + b2[c0 + cc + i], 0.0f);
+                uint32_t w0[4], w1[4];
+                pack8_bf16(x, w0);
+                pack8_bf16(x + 8, w1);
+                const uint32_t at = a_base + (uint32_t)((c0 + cc) / 8) * 2048u + row_off;
+                st_shared_v4(at, w0[0], w0[1], w0[2], w0[3]);
+                st_shared_v4(at + 2048u, w1[0], w1[1], w1[2], w1[3]);
+            }
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(h2r);
+        if (issuer) {
+            if (!f2_wait(h2r, ph, abort, a.err, 8u, false)) break;
+            if (lane == 0) f2_layer(p.l3, tmem + 128u, a_base, w_base, acc);
+            __syncwarp();
+        }
+        // --------------------------------------- E3: partial sums -> actions
+        if (!f2_wait(acc, (uint32_t)(3 * s + 2) & 1u, abort, a.err, 16u, false)) break;
+        tc_fence_after();
+        if (col_half == 0) {                        // one warp per lane quarter reads the 32 columns
+            uint32_t vv[32];
+            __syncwarp();
+            tmem_ld32(tmem_row + 128u, vv);
+            tmem_ld_wait();
+            if (hh == 1) {                          // partial to the partner
+                const uint32_t dst = map_shared_rank(pbuf + (uint32_t)r * 128u, (uint32_t)(rank ^ 1));
+#pragma unroll
+                for (int c = 0; c < 32; c += 4) st_cluster_v4(dst + 4u * c, vv[c], vv[c + 1], vv[c + 2], vv[c + 3]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive_remote(map_shared_rank(smem_u32(prdy), (uint32_t)(rank ^ 1)));
+            } else {
+                if (!f2_wait(prdy, ph, abort, a.err, 32u, true)) break;
+                const float *b3 = (const float *)(smem + L.bias) + 128;
+                const float *pp = (const float *)(smem + L.pbuf) + r * 32;
+                uint32_t pk[16];
+#pragma unroll
+                for (int c = 0; c < 32; c += 2) {
+                    const float y0 = c < SK2 ? tanhf(__fadd_rn(__fadd_rn(__uint_as_float(vv[c]), pp[c]), b3[c])) : 0.0f;
+                    const float y1 = c + 1 < SK2
+                                         ? tanhf(__fadd_rn(__fadd_rn(__uint_as_float(vv[c + 1]), pp[c + 1]), b3[c + 1]))
+                                         : 0.0f;
+                    const __half2 h2 = __floats2half2_rn(y0, y1);
+                    pk[c / 2] = *(const uint32_t *)&h2;
+                }
+                // to the owner of row r
+                const uint32_t dst = map_shared_rank(xbuf + ((uint32_t)j * 128u + (uint32_t)r) * 64u, (uint32_t)(r % M2));
+                st_cluster_v4(dst, pk[0], pk[1], pk[2], pk[3]);
+                st_cluster_v4(dst + 16u, pk[4], pk[5], pk[6], pk[7]);
+                st_cluster_v4(dst + 32u, pk[8], pk[9], pk[10], pk[11]);
+                st_cluster_v4(dst + 48u, pk[12], pk[13], pk[14], pk[15]);
+                __syncwarp();
+                if (lane == 0)
+                    for (int m = 0; m < M2; ++m) mbar_arrive_remote(map_shared_rank(smem_u32(xrdy), (uint32_t)m));
+            }
+        }
+        tc_fence_before();
+        // --------------------------------------------- owners: trade, publish
+        // next-day prices of the owned envs, loaded before the actions arrive
+        int64_t cnext[NOWN];
+#pragma unroll
+        for (int i = 0; i < NOWN; ++i) {
+            const OwnEnv &st = own[i];
+            const bool ok = orow[i] < 128 && tile0 + orow[i] < v.N && !st.done && lane < st.Ke;
+            cnext[i] = ok ? __ldg(v.close + (int64_t)(st.start + st.t + 1) * SK2 + lane) : 1;
+        }
+        if (!f2_wait(xrdy, ph, abort, a.err, 64u, true)) break;
+#pragma unroll
+        for (int i = 0; i < NOWN; ++i) {
+            if (orow[i] >= 128) continue;
+            const int e = tile0 + orow[i];
+            const bool valid = e < v.N;
+            OwnEnv &st = own[i];
+            // combine (anchored weighted mean) for this lane's asset
+            const uint8_t *xr = smem + L.xbuf + (size_t)orow[i] * 64 + 2 * lane;
+            const float a0 = __half2float(*(const __half *)xr);
+            float act = a0;
+#pragma unroll
+            for (int jj = 1; jj < 4; ++jj) {
+                if (jj < M) {
+                    const float aj = __half2float(*(const __half *)(xr + (size_t)jj * 128 * 64));
+                    const float wj = jj == 1 ? w1 : (jj == 2 ? w2 : w3);
+                    act = __fadd_rn(act, __fmul_rn(wj, __fsub_rn(aj, a0)));
+                }
+            }
+            const int64_t row = (int64_t)s * v.N + e;
+            if (valid && a.tr_act && lane < SK2) a.tr_act[row * SK2 + lane] = act;
+            int64_t rew = 0, vlog = VLOG_NONE2;
+            bool dn_out = true;
+            if (valid && !st.done) {
+                const bool live = lane < st.Ke;
+                float ac = isfinite(act) ? act : 0.0f;
+                ac = fminf(fmaxf(ac, -1.0f), 1.0f);
+                const int32_t qa = live ? (int32_t)__fmul_rz(ac, (float)v.hmax) : 0;
+                const int fee = v.fee_bps;
+                int64_t hcur = st.h;
+                int64_t cash = st.cash;
+                const int64_t v0 = cash + warp_sum(st.p * hcur);
+                // sells, branch-free: capped at the holding
+                const int64_t nsell = qa < 0 ? min((int64_t)(-qa), hcur) : 0;
+                const int64_t gs = nsell * st.p;
+                hcur -= nsell;
+                cash += warp_sum(gs - fee_of(gs, fee));
+                // buys: when every order fits, one scan settles them all
+                const int64_t want = qa > 0 ? (int64_t)qa : 0;
+                const int64_t full = cost_of(want, st.p, fee);
+                const int64_t one = cost_of(1, st.p, fee);
+                int64_t nb = 0;
+                const int64_t total = __shfl_sync(FULL_MASK, warp_incl_scan(full, lane), 31);
+                unsigned pending = __ballot_sync(FULL_MASK, want > 0);
+                if (total <= cash) {
+                    nb = want;
+                    cash -= total;
+                    pending = 0u;
+                }
+                while (pending) {
+                    bool mine = (pending >> lane) & 1u;
+                    pending &= ~__ballot_sync(FULL_MASK, mine && one > cash);
+                    if (!pending) break;
+                    mine = (pending >> lane) & 1u;
+                    const int64_t x = mine ? full : 0;
+                    const int64_t pre = warp_incl_scan(x, lane);
+                    const unsigned fail = __ballot_sync(FULL_MASK, mine && pre > cash);
+                    if (fail == 0u) {
+                        if (mine) nb = want;
+                        cash -= __shfl_sync(FULL_MASK, pre, 31);
+                        break;
+                    }
+                    const int f = __ffs(fail) - 1;
+                    if (mine && lane < f) nb = want;
+                    int64_t cf = cash - (pre - x);
+                    if (lane == f) {
+                        const int64_t n = afford(cf, st.p, fee);
+                        nb = n;
+                        cf -= cost_of(n, st.p, fee);
+                    }
+                    cash = __shfl_sync(FULL_MASK, cf, f);
+                    pending &= ~((2u << f) - 1u);
+                }
+                hcur += nb;
+                st.t += 1;
+                const int64_t p1 = live ? perturb(cnext[i], st.bps) : 0;
+                const int64_t v1 = cash + warp_sum(p1 * hcur);
+                rew = v1 - v0;
+                st.done = st.t == st.W - 1;
+                dn_out = st.done;
+                vlog = st.done ? -v1 - 1 : v1;
+                st.cash = cash;
+                st.h = (int32_t)hcur;
+                st.p = p1;
+                if (st.done && v.auto_reset) {
+                    st.cash = v.init_cash;
+                    st.t = 0;
+                    st.done = 0;
+                    st.h = 0;
+                    st.p = live ? perturb(__ldg(v.close + (int64_t)st.start * SK2 + lane), st.bps) : 0;
+                }
+            }
+            if (valid && lane == 0) {
+                if (a.tr_rew) a.tr_rew[row] = rew;
+                if (a.tr_rew_f32) a.tr_rew_f32[row] = reward_f32(rew);
+                if (a.tr_done) a.tr_done[row] = dn_out ? 1 : 0;
+                a.vlog[row] = vlog;
+            }
+            if (s + 1 < T)
+                own_publish(a, st, valid, orow[i], a_base, ctx_addr, M2, lane, valid ? (int64_t)(s + 1) * v.N + e : -1);
+        }
+        if (s + 1 < T) {
+            fence_proxy_async_cluster();
+            __syncwarp();
+            if (lane == 0)
+                for (int m = 0; m < M2; ++m) mbar_arrive_remote(map_shared_rank(smem_u32(obs_ready), (uint32_t)m));
+        }
+    }
+    // state back to global memory (steps and accumulators: metrics replay)
+#pragma unroll
+    for (int i = 0; i < NOWN; ++i) {
+        const int e = tile0 + orow[i];
+        if (orow[i] >= 128 || e >= v.N) continue;
+        if (lane == 0) {
+            v.cash[e] = own[i].cash;
+            v.done[e] = own[i].done ? 1 : 0;
+        }
+        if (lane < SK2) v.hold[(int64_t)e * KP + lane] = lane < own[i].Ke ? own[i].h : 0;
+    }
+}
+
+__global__ void __launch_bounds__(F2_THREADS, 1) k_rollout_stock2(const __grid_constant__ F2Args a)
+{
+    using namespace ptx;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const F2Plan &p = a.plan;
+    const F2Smem L = f2_smem(p);
+    uint64_t *bars = (uint64_t *)(smem + L.bars);
+    uint32_t *tmem_slot = (uint32_t *)(bars + B_COUNT);
+    volatile int *abort = (volatile int *)(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rank = (int)cluster_ctarank();
+    const int M2 = 2 * p.M;
+    const int tile = blockIdx.y;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[B_W], 1);
+        mbar_init(&bars[B_OBS], (uint32_t)(M2 * F2_ENV_WARPS));   // every owner warp of every CTA
+        mbar_init(&bars[B_ACC], 1);
+        mbar_init(&bars[B_H1], 2u * F2_ENV_WARPS);                 // this CTA's and the partner's E1 warps
+        mbar_init(&bars[B_H2], (uint32_t)F2_ENV_WARPS);            // this CTA's E2 warps
+        mbar_init(&bars[B_P], 4u);                                 // the partner's 4 E3 warps
+        mbar_init(&bars[B_X], (uint32_t)(p.M * 4));                // each agent's 4 E3 warps
+        *abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        __syncwarp();
+        tmem_alloc(tmem_slot, 256u);
+        tmem_relinquish();
+    }
+    if (warp == 2) {
+        // this CTA's b2 half and b3, read by every epilogue warp
+        float *bs = (float *)(smem + L.bias);
+        const int jj = rank >> 1, h2 = rank & 1;
+        for (int i = lane; i < 128; i += 32) bs[i] = i < p.n2 ? a.b2[(size_t)jj * p.H2 + h2 * p.n2 + i] : 0.0f;
+        bs[128 + lane] = a.b3[(size_t)jj * 32 + lane];
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    cluster_sync_all();
+    const uint32_t tmem = *tmem_slot;
+
+    {
+        // owned envs per env warp: ceil(128 / (2M * 8)) = 4, 3, 2 for M = 2..4
+        switch (p.M) {
+        case 2: f2_env_loop<4>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
+        case 3: f2_env_loop<3>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
+        default: f2_env_loop<2>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
+        }
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, 256u);
+    }
+    __syncwarp();
+    cluster_sync_all();
+}
+
+// x[ctx][i*30 + k] = ind[day][i][k] for k < slot_ke, else 0; ctx = slot*days + day
+__global__ void k_ind_rows(const float *ind, int n_days, const int32_t *slot_ke, int n_slots, float *x)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)n_slots * n_days * NIND;
+    if (i >= total) return;
+    const int64_t ctx = i / NIND;
+    const int c = (int)(i % NIND);
+    const int slot = (int)(ctx / n_days), day = (int)(ctx % n_days);
+    x[i] = (c % SK2) < slot_ke[slot] ? ind[(int64_t)day * NIND + c] : 0.0f;
+}
+
+inline uint16_t bf16_rne(float f)
+{
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    const uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+    return (uint16_t)(u >> 16);
+}
+
+inline uint32_t coff(int N, int n, int kk)
+{
+    return (uint32_t)((kk / 8) * (N * 16) + (n / 8) * 128 + (n % 8) * 16 + (kk % 8) * 2);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host
+struct F2Cache {
+    F2Image im;
+};
+
+static void f2_free(fr_ctx *ctx, F2Image &im)
+{
+    dev_free(ctx, im.img, (uint64_t)im.plan.M * 2 * im.plan.cta_bytes);
+    dev_free(ctx, im.b2, (uint64_t)im.plan.M * im.plan.H2 * 4);
+    dev_free(ctx, im.b3, (uint64_t)im.plan.M * 32 * 4);
+    dev_free(ctx, im.wind, (uint64_t)im.plan.M * (im.plan.H1 * NIND + im.plan.H1) * 4);
+    im.img = nullptr;
+}
+
+// Build the per-CTA resident images of an ensemble (host packing, once).
+static int f2_build(const fr_ensemble *e, F2Image &im)
+{
+    F2Plan &p = im.plan;
+    std::vector<float> host((size_t)e->M * e->P);
+    FR_CUDA(cudaMemcpy(host.data(), e->params, host.size() * 4, cudaMemcpyDeviceToHost));
+    std::vector<uint8_t> img((size_t)p.M * 2 * p.cta_bytes, 0);
+    std::vector<float> b2((size_t)p.M * p.H2), b3((size_t)p.M * 32, 0.0f);
+    std::vector<float> wind((size_t)p.M * (p.H1 * NIND + p.H1));
+    auto put = [&](uint8_t *base, const F2Layer &l, int n, int k, float w) {
+        const int c = k / l.KC, kk = k % l.KC;
+        const uint16_t b = bf16_rne(w);
+        memcpy(base + l.off + (size_t)c * l.N * l.KC * 2 + coff(l.N, n, kk), &b, 2);
+    };
+    for (int j = 0; j < p.M; ++j) {
+        const float *P = host.data() + (size_t)j * e->P;
+        const float *W1 = P + e->w_off[0], *B1 = P + e->b_off[0];
+        const float *W2 = P + e->w_off[1], *B2 = P + e->b_off[1];
+        const float *W3 = P + e->w_off[2], *B3 = P + e->b_off[2];
+        for (int hh = 0; hh < 2; ++hh) {
+            uint8_t *base = img.data() + (size_t)(2 * j + hh) * p.cta_bytes;
+            for (int n = 0; n < p.n1; ++n)
+                for (int k = 0; k < NSTATE; ++k) put(base, p.l1, n, k, W1[(size_t)(hh * p.n1 + n) * SD2 + k]);
+            for (int n = 0; n < p.n2; ++n)
+                for (int k = 0; k < p.H1; ++k) put(base, p.l2, n, k, W2[(size_t)(hh * p.n2 + n) * p.H1 + k]);
+            for (int n = 0; n < SK2; ++n)
+                for (int k = 0; k < p.n2; ++k) put(base, p.l3, n, k, W3[(size_t)n * p.H2 + hh * p.n2 + k]);
+        }
+        for (int n = 0; n < p.H2; ++n) b2[(size_t)j * p.H2 + n] = B2[n];
+        for (int n = 0; n < SK2; ++n) b3[(size_t)j * 32 + n] = B3[n];
+        float *wi = wind.data() + (size_t)j * (p.H1 * NIND + p.H1);
+        for (int n = 0; n < p.H1; ++n) {
+            for (int c = 0; c < NIND; ++c) wi[(size_t)n * NIND + c] = W1[(size_t)n * SD2 + NSTATE + c];
+            wi[(size_t)p.H1 * NIND + n] = B1[n];
+        }
+    }
+    int rc;
+    if ((rc = dev_alloc(e->ctx, (void **)&im.img, img.size())) ||
+        (rc = dev_alloc(e->ctx, (void **)&im.b2, b2.size() * 4)) ||
+        (rc = dev_alloc(e->ctx, (void **)&im.b3, b3.size() * 4)) ||
+        (rc = dev_alloc(e->ctx, (void **)&im.wind, wind.size() * 4))) {
+        f2_free(e->ctx, im);
+        return rc;
+    }
+    FR_CUDA(cudaMemcpy(im.img, img.data(), img.size(), cudaMemcpyHostToDevice));
+    FR_CUDA(cudaMemcpy(im.b2, b2.data(), b2.size() * 4, cudaMemcpyHostToDevice));
+    FR_CUDA(cudaMemcpy(im.b3, b3.data(), b3.size() * 4, cudaMemcpyHostToDevice));
+    FR_CUDA(cudaMemcpy(im.wind, wind.data(), wind.size() * 4, cudaMemcpyHostToDevice));
+    im.owner = e;
+    return FR_OK;
+}
+
+bool f2_supported(const fr_env *env, const fr_ensemble *e)
+{
+    const EnvView &v = env->v;
+    if (v.task != FR_TASK_STOCK || v.K != SK2 || v.I != SI2 || e->combine != FR_COMBINE_MEAN ||
+        e->out_act != 1 || e->precision != FR_PREC_BF16)
+        return false;
+    F2Plan p;
+    if (!f2_plan(e, p)) return false;
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, env->ctx->device) != cudaSuccess)
+        return false;
+    return f2_smem(p).total + 1024u <= (uint32_t)optin;
+}
+
+// images are cached per ensemble (keyed by handle); released with the ensemble
+struct F2Entry {
+    const fr_ensemble *ens;
+    F2Image im;
+};
+static std::vector<F2Entry> g_f2;
+static std::mutex g_f2_mu;
+
+void f2_release(const fr_ensemble *e)
+{
+    std::lock_guard<std::mutex> lk(g_f2_mu);
+    for (size_t i = 0; i < g_f2.size(); ++i) {
+        if (g_f2[i].ens == e) {
+            f2_free(e->ctx, g_f2[i].im);
+            g_f2.erase(g_f2.begin() + (long)i);
+            return;
+        }
+    }
+}
+
+int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, double *metrics, cudaStream_t s)
+{
+    const EnvView &v = env->v;
+    F2Image imv;
+    bool found = false;
+    {
+        std::lock_guard<std::mutex> lk(g_f2_mu);
+        for (auto &en : g_f2)
+            if (en.ens == e) {
+                imv = en.im;
+                found = true;
+            }
+        if (!found) {
+            F2Entry en{};
+            en.ens = e;
+            if (!f2_plan(e, en.im.plan)) {
+                set_error("fused rollout: unsupported ensemble shape");
+                return FR_EINVAL;
+            }
+            int rc = f2_build(e, en.im);
+            if (rc) return rc;
+            g_f2.push_back(en);
+            imv = en.im;
+        }
+    }
+    const F2Image *im = &imv;
+    const F2Plan &p = im->plan;
+    if (T == 0) {
+        if (metrics) FR_CUDA(launch_env_metrics(v, metrics, s));
+        return FR_OK;
+    }
+    // asset-count slots of this env batch (host side, from the device copy)
+    if (env->slot_of_env == nullptr) {
+        std::vector<int32_t> ke(v.N);
+        FR_CUDA(cudaMemcpy(ke.data(), v.Ke, 4ull * v.N, cudaMemcpyDeviceToHost));
+        std::vector<int32_t> kes;
+        for (int x : ke)
+            if (std::find(kes.begin(), kes.end(), x) == kes.end()) kes.push_back(x);
+        std::vector<int32_t> slot(v.N);
+        for (int i = 0; i < v.N; ++i) slot[i] = (int32_t)(std::find(kes.begin(), kes.end(), ke[i]) - kes.begin());
+        env->n_slots = (int)kes.size();
+        int rc = dev_alloc(env->ctx, (void **)&env->slot_of_env, 4ull * v.N + 4ull * 32);
+        if (rc) return rc;
+        env->slot_ke = env->slot_of_env + v.N;
+        FR_CUDA(cudaMemcpy(env->slot_of_env, slot.data(), 4ull * v.N, cudaMemcpyHostToDevice));
+        FR_CUDA(cudaMemcpy(env->slot_ke, kes.data(), 4ull * kes.size(), cudaMemcpyHostToDevice));
+    }
+    const int n_ctx = env->n_slots * v.n_days;
+    // scratch: value log, indicator rows, Z table
+    const uint64_t vlog_b = ((uint64_t)T * v.N * 8 + 255) & ~255ull;
+    const uint64_t x_b = ((uint64_t)n_ctx * NIND * 4 + 255) & ~255ull;
+    const uint64_t z_b = (uint64_t)p.M * n_ctx * p.H1 * 4;
+    const uint64_t need = vlog_b + x_b + z_b;
+    if (env->scratch_bytes < need) {
+        FR_CUDA(cudaStreamSynchronize(s));
+        dev_free(env->ctx, env->scratch, env->scratch_bytes);
+        env->scratch = nullptr;
+        env->scratch_bytes = 0;
+        int rc = dev_alloc(env->ctx, &env->scratch, need);
+        if (rc) return rc;
+        env->scratch_bytes = need;
+    }
+    int64_t *vlog = (int64_t *)env->scratch;
+    float *X = (float *)((char *)env->scratch + vlog_b);
+    float *Z = (float *)((char *)env->scratch + vlog_b + x_b);
+    // Z[j][ctx][n] = W1_j[n, indicators] . x[ctx] + b1_j[n]   (per rollout)
+    const int64_t nx = (int64_t)n_ctx * NIND;
+    k_ind_rows<<<ceil_div(nx, 256), 256, 0, s>>>(v.ind, v.n_days, env->slot_ke, env->n_slots, X);
+    FR_CUDA(cudaGetLastError());
+    FR_CUDA(launch_dense_f32(X, 0, NIND, im->wind, (int64_t)p.H1 * NIND + p.H1, 0, (int64_t)p.H1 * NIND, Z,
+                             (int64_t)n_ctx * p.H1, p.H1, n_ctx, NIND, p.H1, 2, p.M, s));
+
+    F2Args a;
+    memset(&a, 0, sizeof(a));
+    a.v = v;
+    a.plan = p;
+    a.img = im->img;
+    a.b2 = im->b2;
+    a.b3 = im->b3;
+    a.Z = Z;
+    a.slot = env->slot_of_env;
+    a.n_ctx_per_agent = n_ctx;
+    for (int jj = 0; jj < MAX_AGENTS; ++jj) a.w[jj] = e->host_weights[jj];
+    a.T = T;
+    a.tr_obs = traj->obs;
+    a.obs_ld = traj->obs_ld ? traj->obs_ld : v.D;
+    a.tr_act = (float *)traj->act;
+    a.tr_rew = traj->rew;
+    a.tr_rew_f32 = traj->rew_f32;
+    a.tr_done = traj->done;
+    a.vlog = vlog;
+    a.err = e->tc->err;
+    const uint32_t smem = f2_smem(p).total + 1024u;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(2 * p.M), ceil_div(v.N, 128), 1);
+    cfg.blockDim = dim3(F2_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)(2 * p.M);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    FR_CUDA(cudaFuncSetAttribute(k_rollout_stock2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FR_CUDA(cudaLaunchKernelEx(&cfg, k_rollout_stock2, a));
+    FR_CUDA(launch_metrics_replay(v, vlog, T, metrics, s));
+    return FR_OK;
+}
+
+}  // namespace fr
