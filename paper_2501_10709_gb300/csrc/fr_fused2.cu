@@ -144,19 +144,53 @@ __host__ __device__ inline F2Smem f2_smem(const F2Plan &p)
 }
 
 // barrier slots
-enum { B_W = 0, B_OBS, B_ACC, B_H1, B_H2, B_P, B_X, B_COUNT };
+enum { B_W = 0, B_OBS, B_ACC, B_H1, B_H2, B_P, B_X, B_END, B_COUNT };
 
+// Bounded wait on an mbarrier phase by the whole warp.  Every lane polls the
+// barrier and the exit is taken on a warp vote, so the warp leaves the wait
+// converged: a wait by one elected lane (the others parked at a shuffle)
+// leaves the warp split after the lane's suspension, and every later
+// warp-collective operation of the step then pays for a reconvergence.  On
+// giving up (time limit, or another warp of the CTA gave up) it sets *abort
+// and bit `code` of *err and returns false.
 __device__ __forceinline__ bool f2_wait(uint64_t *bar, uint32_t parity, volatile int *abort, unsigned *err,
                                         unsigned code, bool cluster_scope)
 {
     using namespace ptx;
-    int ok = 1;
-    if ((threadIdx.x & 31) == 0)
-        ok = cluster_scope ? mbar_wait_cluster(bar, parity, abort, err, code, TC_WAIT_NS)
-                           : mbar_wait(bar, parity, abort, err, code, TC_WAIT_NS);
-    ok = __shfl_sync(FULL_MASK, ok, 0);
+    if (__any_sync(FULL_MASK, *abort != 0)) return false;
+    uint64_t t0 = 0;
+#pragma unroll 1
+    for (uint32_t i = 0;; ++i) {
+        const bool mine = cluster_scope ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity);
+        if (__all_sync(FULL_MASK, mine)) return true;
+        if ((i & 15u) == 15u) {
+            if (__any_sync(FULL_MASK, *abort != 0)) return false;
+            const uint64_t now = __shfl_sync(FULL_MASK, globaltimer(), 0);
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > TC_WAIT_NS) {
+                if ((threadIdx.x & 31) == 0) {
+                    *abort = 1;
+                    atomicOr(err, code);
+                }
+                return false;
+            }
+        }
+    }
+}
+
+// Arrive on `bar` in every CTA of the cluster once this warp's shared-memory
+// writes (local and remote) are visible there: one proxy fence when the
+// writes feed the tensor cores, one release fence, then relaxed arrivals.
+__device__ __forceinline__ void f2_signal_all(uint64_t *bar, int M2, int lane, bool for_mma)
+{
+    using namespace ptx;
+    if (for_mma) fence_proxy_async_cluster();
     __syncwarp();
-    return ok != 0;
+    if (lane == 0) {
+        fence_acq_rel_cluster();
+        for (int m = 0; m < M2; ++m) mbar_arrive_remote_relaxed(map_shared_rank(smem_u32(bar), (uint32_t)m));
+    }
 }
 
 __device__ __forceinline__ void pack8_bf16(const float *v, uint32_t *w)
@@ -174,7 +208,7 @@ __device__ __forceinline__ void pack8_bf16(const float *v, uint32_t *w)
 // by lane 0 of env warp 0 at the point where that warp waits on the layer's
 // operands anyway; a dedicated issuer warp would make the block 10 warps,
 // which caps every thread at 168 registers and makes the env code spill.
-__device__ __forceinline__ void f2_layer(const F2Layer &l, uint32_t d_tmem, uint32_t a_at, uint32_t w_base,
+__device__ __noinline__ void f2_layer(const F2Layer &l, uint32_t d_tmem, uint32_t a_at, uint32_t w_base,
                                          uint64_t *acc)
 {
     using namespace ptx;
@@ -198,6 +232,7 @@ __device__ __forceinline__ void f2_layer(const F2Layer &l, uint32_t d_tmem, uint
 // --------------------------------------------- owner: one env, warp-wide
 struct OwnEnv {
     int64_t cash;        // uniform
+    int64_t v0;          // uniform: total asset value at the start of the step
     int t, start, W, Ke; // uniform
     int done;            // uniform
     int slot;            // uniform, asset-count slot
@@ -206,8 +241,79 @@ struct OwnEnv {
     int bps;             // this lane's perturbation
 };
 
-// the next observation row of env r: chunks 0..7 of the A operand in every
-// CTA of the cluster, plus its Z row index
+// Exact int64 warp sum (mod 2^64, like the serial sum) from three 32-bit
+// hardware reductions: x = hi 2^42 + mid 2^21 + lo with lo, mid in [0, 2^21)
+// and hi in [-2^21, 2^21), so none of the 32-lane partial sums overflows.
+// The three reductions are independent, unlike the five dependent shuffle
+// rounds of a butterfly sum.
+__device__ __forceinline__ int64_t warp_sum_redux(int64_t x)
+{
+    const unsigned lo = (unsigned)x & 0x1fffffu;
+    const unsigned mid = (unsigned)(x >> 21) & 0x1fffffu;
+    const int hi = (int)(x >> 42);
+    const unsigned slo = __reduce_add_sync(FULL_MASK, lo);
+    const unsigned smid = __reduce_add_sync(FULL_MASK, mid);
+    const int shi = __reduce_add_sync(FULL_MASK, hi);
+    return (int64_t)(((uint64_t)(int64_t)shi << 42) + ((uint64_t)smid << 21) + (uint64_t)slo);
+}
+
+// Greedy buys in ascending asset order with partial fills, for the case
+// where the orders do not all fit in `cash`: lanes whose single share no
+// longer fits drop out; a scan finds the first order that does not fit,
+// which buys what the remaining cash affords.  Returns the cash left; nb
+// receives this lane's filled shares.  cash and the loop state stay
+// warp-uniform, so every collective runs on the full warp.
+__device__ __noinline__ int64_t own_buy_greedy(int64_t cash, int64_t want, int64_t full, int64_t p, int fee,
+                                                  int lane, int64_t &nb)
+{
+    const int64_t one = cost_of(1, p, fee);
+    unsigned pending = __ballot_sync(FULL_MASK, want > 0);
+    nb = 0;
+    while (pending) {
+        bool mine = (pending >> lane) & 1u;
+        pending &= ~__ballot_sync(FULL_MASK, mine && one > cash);
+        if (!pending) break;
+        mine = (pending >> lane) & 1u;
+        const int64_t x = mine ? full : 0;
+        const int64_t pre = warp_incl_scan(x, lane);
+        const unsigned fail = __ballot_sync(FULL_MASK, mine && pre > cash);
+        if (fail == 0u) {
+            if (mine) nb = want;
+            cash -= __shfl_sync(FULL_MASK, pre, 31);
+            break;
+        }
+        const int f = __ffs(fail) - 1;
+        if (mine && lane < f) nb = want;
+        int64_t cf = cash - (pre - x);
+        if (lane == f) {
+            const int64_t n = afford(cf, p, fee);
+            nb = n;
+            cf -= cost_of(n, p, fee);
+        }
+        cash = __shfl_sync(FULL_MASK, cf, f);
+        pending &= ~((2u << f) - 1u);
+    }
+    return cash;
+}
+
+// fp32 trajectory observation of the step about to be taken (optional output,
+// out of line)
+__device__ __noinline__ void own_traj_obs(const F2Args &a, float *o, float cv, float pv, float hv, int day, int Ke,
+                                          int lane)
+{
+    if (lane == 0) o[0] = cv;
+    if (lane < SK2) {
+        o[1 + lane] = pv;
+        o[1 + SK2 + lane] = hv;
+    }
+    const float *f = a.v.ind + (int64_t)day * NIND;
+    for (int i = lane; i < NIND; i += 32) o[NSTATE + i] = (i % SK2) < Ke ? __ldg(f + i) : 0.0f;
+}
+
+// The next observation row of env r: chunks 0..7 of the A operand (state
+// positions 0..63: cash, 30 prices, 30 holdings, zero padding) in every CTA
+// of the cluster, plus its Z row index.  Each lane contributes its price and
+// holding as a bf16 pair; lanes 0..7 gather the 8 positions of their chunk.
 __device__ __forceinline__ void own_publish(const F2Args &a, const OwnEnv &s, bool valid, int r, uint32_t a_base,
                                             uint32_t ctx_addr, int M2, int lane, int64_t trow)
 {
@@ -215,40 +321,32 @@ __device__ __forceinline__ void own_publish(const F2Args &a, const OwnEnv &s, bo
     const float pv = (valid && lane < s.Ke) ? obs_scale(s.p, 1e-4f) : 0.0f;
     const float hv = (valid && lane < s.Ke) ? __fmul_rn(__int2float_rn(s.h), 1e-2f) : 0.0f;
     const float cv = valid ? obs_scale(s.cash, 1e-8f) : 0.0f;
-    // lanes 0..7 build chunk `lane` = positions 8*lane .. 8*lane+7
-    float v8[8];
+    const __nv_bfloat162 ph2 = __floats2bfloat162_rn(pv, hv);      // .x price, .y holding
+    const uint32_t mine = *(const uint32_t *)&ph2;
+    const __nv_bfloat16 cb = __float2bfloat16_rn(cv);
+    const uint32_t cbits = (uint32_t)*(const uint16_t *)&cb;
+    uint32_t hw[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
         const int pos = 8 * lane + u;
-        const float fp = __shfl_sync(FULL_MASK, pv, (pos - 1) & 31);
-        const float fh = __shfl_sync(FULL_MASK, hv, (pos - 1 - SK2) & 31);
-        v8[u] = pos == 0 ? cv : (pos <= SK2 ? fp : (pos < NSTATE ? fh : 0.0f));
+        const int src = pos <= SK2 ? pos - 1 : pos - 1 - SK2;
+        const uint32_t g = __shfl_sync(FULL_MASK, mine, src & 31);
+        hw[u] = pos == 0 ? cbits : (pos <= SK2 ? (g & 0xffffu) : (pos < NSTATE ? (g >> 16) : 0u));
     }
     const uint32_t row_off = (uint32_t)(r / 8) * 128u + (uint32_t)(r % 8) * 16u;
     const uint32_t a_obs = a_base + (uint32_t)(a.plan.H1 / 8) * 2048u;
     if (lane < 8) {
-        uint32_t w[4];
-        pack8_bf16(v8, w);
+        const uint32_t w0 = hw[0] | (hw[1] << 16), w1 = hw[2] | (hw[3] << 16);
+        const uint32_t w2 = hw[4] | (hw[5] << 16), w3 = hw[6] | (hw[7] << 16);
         for (int m = 0; m < M2; ++m)
-            st_cluster_v4(map_shared_rank(a_obs + (uint32_t)lane * 2048u + row_off, (uint32_t)m), w[0], w[1], w[2],
-                          w[3]);
+            st_cluster_v4(map_shared_rank(a_obs + (uint32_t)lane * 2048u + row_off, (uint32_t)m), w0, w1, w2, w3);
     } else if (lane < 8 + M2) {
         const int zrow = valid ? s.slot * a.v.n_days + s.start + s.t : 0;
         asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(map_shared_rank(ctx_addr + 4u * r, (uint32_t)(lane - 8))),
                      "r"(zrow)
                      : "memory");
     }
-    // fp32 trajectory observation of the step about to be taken
-    if (a.tr_obs && valid && trow >= 0) {
-        float *o = a.tr_obs + trow * a.obs_ld;
-        if (lane == 0) o[0] = cv;
-        if (lane < SK2) {
-            o[1 + lane] = pv;
-            o[1 + SK2 + lane] = hv;
-        }
-        const float *f = a.v.ind + (int64_t)(s.start + s.t) * NIND;
-        for (int i = lane; i < NIND; i += 32) o[NSTATE + i] = (i % SK2) < s.Ke ? __ldg(f + i) : 0.0f;
-    }
+    if (a.tr_obs && valid && trow >= 0) own_traj_obs(a, a.tr_obs + trow * a.obs_ld, cv, pv, hv, s.start + s.t, s.Ke, lane);
 }
 
 template <int NOWN>
@@ -298,7 +396,8 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         orow[i] = rank + M2 * (ew + F2_ENV_WARPS * i);
         const int e = tile0 + orow[i];
         OwnEnv &s = own[i];
-        s.cash = 0; s.t = 0; s.start = 0; s.W = 2; s.Ke = 0; s.done = 1; s.slot = 0; s.p = 0; s.h = 0; s.bps = 0;
+        s.cash = 0; s.v0 = 0; s.t = 0; s.start = 0; s.W = 2; s.Ke = 0; s.done = 1; s.slot = 0; s.p = 0; s.h = 0;
+        s.bps = 0;
         if (orow[i] < 128 && e < v.N) {
             s.cash = v.cash[e];
             s.t = v.t[e];
@@ -313,6 +412,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                 s.p = perturb(__ldg(v.close + (int64_t)(s.start + s.t) * SK2 + lane), s.bps);
             }
         }
+        s.v0 = s.cash + warp_sum(s.p * (int64_t)s.h);
     }
     // observation of step 0
 #pragma unroll
@@ -321,39 +421,55 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         const int e = tile0 + orow[i];
         own_publish(a, own[i], e < v.N, orow[i], a_base, ctx_addr, M2, lane, e < v.N ? (int64_t)e : -1);
     }
-    fence_proxy_async_cluster();
-    __syncwarp();
-    if (lane == 0)
-        for (int m = 0; m < M2; ++m) mbar_arrive_remote(map_shared_rank(smem_u32(obs_ready), (uint32_t)m));
+    f2_signal_all(obs_ready, M2, lane, true);
 
     const float *zbase = a.Z + (size_t)j * a.n_ctx_per_agent * p.H1;
-    int T = a.T;
-    if (issuer && !f2_wait(&bars[B_W], 0u, abort, a.err, 1u, false)) T = 0;
+    // The step loop has no early exit: its trip count is uniform, so the warp
+    // is provably converged at every warp-collective operation inside it.  A
+    // wait that gives up sets the CTA's abort flag; every later wait then
+    // returns at once and the remaining steps run through without their data
+    // (all of their addresses are independent of it, or clamped).
+    const int T = a.T;
+    if (issuer) f2_wait(&bars[B_W], 0u, abort, a.err, 1u, false);
     for (int s = 0; s < T; ++s) {
         const uint32_t ph = (uint32_t)s & 1u;
         // ------------------------------------------- E1: + Z + b1 -> ReLU
         // the observation barrier also publishes each env's Z row: read it
         // and start the row's loads while layer 1 runs on the tensor cores
-        if (!f2_wait(obs_ready, ph, abort, a.err, 16u, true)) break;
+        f2_wait(obs_ready, ph, abort, a.err, 16u, true);
         if (issuer && lane == 0) f2_layer(p.l1, tmem, a_obs, w_base, acc);
         const int nc1 = p.n1 / 2;                          // columns per warp (<= 64)
         const int c01 = col_half * nc1;
-        const float *zrow = zbase + (size_t)ctxv[r] * p.H1 + hh * p.n1 + c01;
-        for (int i = 0; i < nc1; i += 32) asm volatile("prefetch.global.L1 [%0];" ::"l"(zrow + i));
-        if (!f2_wait(acc, (uint32_t)(3 * s) & 1u, abort, a.err, 16u, false)) break;
+        // all of this warp's Z loads in flight at once, one L2 latency
+        // clamped: after an aborted wait the row index may be stale
+        const int zr = min(max(ctxv[r], 0), a.n_ctx_per_agent - 1);
+        const float4 *zrow = (const float4 *)(zbase + (size_t)zr * p.H1 + hh * p.n1 + c01);
+        float4 zq[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) zq[i] = 4 * i < nc1 ? __ldg(zrow + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        f2_wait(acc, (uint32_t)(3 * s) & 1u, abort, a.err, 16u, false);
         tc_fence_after();
         {
             const int nc = nc1;
             const int c0 = c01;
             const uint32_t dst_chunk0 = (uint32_t)((hh * p.n1 + c0) / 8);
-            for (int cc = 0; cc < nc; cc += 16) {
+#pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4) {
+                const int cc = 16 * q4;
+                if (cc >= nc) continue;
                 uint32_t vv[16];
                 __syncwarp();
                 tmem_ld16(tmem_row + (uint32_t)(c0 + cc), vv);
                 tmem_ld_wait();
                 float x[16];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) x[i] = fmaxf(__uint_as_float(vv[i]) + __ldg(zrow + cc + i), 0.0f);
+                for (int i = 0; i < 4; ++i) {
+                    const float4 z = zq[4 * q4 + i];
+                    x[4 * i + 0] = fmaxf(__uint_as_float(vv[4 * i + 0]) + z.x, 0.0f);
+                    x[4 * i + 1] = fmaxf(__uint_as_float(vv[4 * i + 1]) + z.y, 0.0f);
+                    x[4 * i + 2] = fmaxf(__uint_as_float(vv[4 * i + 2]) + z.z, 0.0f);
+                    x[4 * i + 3] = fmaxf(__uint_as_float(vv[4 * i + 3]) + z.w, 0.0f);
+                }
                 uint32_t w0[4], w1[4];
                 pack8_bf16(x, w0);
                 pack8_bf16(x + 8, w1);
@@ -365,21 +481,21 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                 st_cluster_v4(pt + 2048u, w1[0], w1[1], w1[2], w1[3]);
             }
         }
-        fence_proxy_async_smem();
         fence_proxy_async_cluster();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) {
+            fence_acq_rel_cluster();
             mbar_arrive(h1r);
-            mbar_arrive_remote(map_shared_rank(smem_u32(h1r), (uint32_t)(rank ^ 1)));
+            mbar_arrive_remote_relaxed(map_shared_rank(smem_u32(h1r), (uint32_t)(rank ^ 1)));
         }
         if (issuer) {
-            if (!f2_wait(h1r, ph, abort, a.err, 4u, true)) break;
+            f2_wait(h1r, ph, abort, a.err, 4u, true);
             if (lane == 0) f2_layer(p.l2, tmem, a_base, w_base, acc);
             __syncwarp();
         }
         // ------------------------------------------------- E2: + b2 -> ReLU
-        if (!f2_wait(acc, (uint32_t)(3 * s + 1) & 1u, abort, a.err, 16u, false)) break;
+        f2_wait(acc, (uint32_t)(3 * s + 1) & 1u, abort, a.err, 16u, false);
         tc_fence_after();
         {
             const float *b2 = (const float *)(smem + L.bias);
@@ -406,12 +522,12 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         __syncwarp();
         if (lane == 0) mbar_arrive(h2r);
         if (issuer) {
-            if (!f2_wait(h2r, ph, abort, a.err, 8u, false)) break;
+            f2_wait(h2r, ph, abort, a.err, 8u, false);
             if (lane == 0) f2_layer(p.l3, tmem + 128u, a_base, w_base, acc);
             __syncwarp();
         }
         // --------------------------------------- E3: partial sums -> actions
-        if (!f2_wait(acc, (uint32_t)(3 * s + 2) & 1u, abort, a.err, 16u, false)) break;
+        f2_wait(acc, (uint32_t)(3 * s + 2) & 1u, abort, a.err, 16u, false);
         tc_fence_after();
         if (col_half == 0) {                        // one warp per lane quarter reads the 32 columns
             uint32_t vv[32];
@@ -419,15 +535,30 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
             tmem_ld32(tmem_row + 128u, vv);
             tmem_ld_wait();
             if (hh == 1) {                          // partial to the partner
+                // row r, column group k stored at group k ^ (r & 7): the
+                // partner's 16-byte reads of one group are conflict-free
                 const uint32_t dst = map_shared_rank(pbuf + (uint32_t)r * 128u, (uint32_t)(rank ^ 1));
 #pragma unroll
-                for (int c = 0; c < 32; c += 4) st_cluster_v4(dst + 4u * c, vv[c], vv[c + 1], vv[c + 2], vv[c + 3]);
+                for (int k = 0; k < 8; ++k)
+                    st_cluster_v4(dst + 16u * (uint32_t)(k ^ (r & 7)), vv[4 * k], vv[4 * k + 1], vv[4 * k + 2],
+                                  vv[4 * k + 3]);
                 __syncwarp();
-                if (lane == 0) mbar_arrive_remote(map_shared_rank(smem_u32(prdy), (uint32_t)(rank ^ 1)));
+                if (lane == 0) {
+                    fence_acq_rel_cluster();
+                    mbar_arrive_remote_relaxed(map_shared_rank(smem_u32(prdy), (uint32_t)(rank ^ 1)));
+                }
             } else {
-                if (!f2_wait(prdy, ph, abort, a.err, 32u, true)) break;
+                f2_wait(prdy, ph, abort, a.err, 32u, true);
                 const float *b3 = (const float *)(smem + L.bias) + 128;
-                const float *pp = (const float *)(smem + L.pbuf) + r * 32;
+                float pp[32];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const uint4 g = ld_shared_v4(pbuf + (uint32_t)r * 128u + 16u * (uint32_t)(k ^ (r & 7)));
+                    pp[4 * k + 0] = __uint_as_float(g.x);
+                    pp[4 * k + 1] = __uint_as_float(g.y);
+                    pp[4 * k + 2] = __uint_as_float(g.z);
+                    pp[4 * k + 3] = __uint_as_float(g.w);
+                }
                 uint32_t pk[16];
 #pragma unroll
                 for (int c = 0; c < 32; c += 2) {
@@ -444,30 +575,34 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                 st_cluster_v4(dst + 16u, pk[4], pk[5], pk[6], pk[7]);
                 st_cluster_v4(dst + 32u, pk[8], pk[9], pk[10], pk[11]);
                 st_cluster_v4(dst + 48u, pk[12], pk[13], pk[14], pk[15]);
-                __syncwarp();
-                if (lane == 0)
-                    for (int m = 0; m < M2; ++m) mbar_arrive_remote(map_shared_rank(smem_u32(xrdy), (uint32_t)m));
+                f2_signal_all(xrdy, M2, lane, false);
             }
         }
         tc_fence_before();
         // --------------------------------------------- owners: trade, publish
-        // next-day prices of the owned envs, loaded before the actions arrive
-        int64_t cnext[NOWN];
+        // The next day's prices do not depend on the actions: load them
+        // before the actions arrive.  The owned envs are then processed in
+        // lockstep, so that their reductions overlap instead of forming one
+        // long dependent chain per env.
+        int64_t p1[NOWN];
+        bool run[NOWN];                                 // uniform: env exists and is not done
 #pragma unroll
         for (int i = 0; i < NOWN; ++i) {
             const OwnEnv &st = own[i];
-            const bool ok = orow[i] < 128 && tile0 + orow[i] < v.N && !st.done && lane < st.Ke;
-            cnext[i] = ok ? __ldg(v.close + (int64_t)(st.start + st.t + 1) * SK2 + lane) : 1;
+            run[i] = orow[i] < 128 && tile0 + orow[i] < v.N && !st.done;
+            const bool ok = run[i] && lane < st.Ke;
+            p1[i] = ok ? perturb(__ldg(v.close + (int64_t)(st.start + st.t + 1) * SK2 + lane), st.bps) : 0;
         }
-        if (!f2_wait(xrdy, ph, abort, a.err, 64u, true)) break;
+        f2_wait(xrdy, ph, abort, a.err, 64u, true);
+        const int fee = v.fee_bps;
+        int64_t nsell[NOWN], want[NOWN], full[NOWN], ssum[NOWN], bsum[NOWN], vsum[NOWN];
 #pragma unroll
         for (int i = 0; i < NOWN; ++i) {
-            if (orow[i] >= 128) continue;
+            const OwnEnv &st = own[i];
+            const int rr = orow[i] < 128 ? orow[i] : 127;
             const int e = tile0 + orow[i];
-            const bool valid = e < v.N;
-            OwnEnv &st = own[i];
             // combine (anchored weighted mean) for this lane's asset
-            const uint8_t *xr = smem + L.xbuf + (size_t)orow[i] * 64 + 2 * lane;
+            const uint8_t *xr = smem + L.xbuf + (size_t)rr * 64 + 2 * lane;
             const float a0 = __half2float(*(const __half *)xr);
             float act = a0;
 #pragma unroll
@@ -478,77 +613,55 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                     act = __fadd_rn(act, __fmul_rn(wj, __fsub_rn(aj, a0)));
                 }
             }
+            if (a.tr_act && orow[i] < 128 && e < v.N && lane < SK2) a.tr_act[((int64_t)s * v.N + e) * SK2 + lane] = act;
+            const bool live = run[i] && lane < st.Ke;
+            float ac = isfinite(act) ? act : 0.0f;
+            ac = fminf(fmaxf(ac, -1.0f), 1.0f);
+            const int32_t qa = live ? (int32_t)__fmul_rz(ac, (float)v.hmax) : 0;
+            const int64_t hcur = st.h;
+            // sells capped at the holding; buys as ordered (the common case:
+            // every order fits); the value after both at the next prices
+            nsell[i] = qa < 0 ? min((int64_t)(-qa), hcur) : 0;
+            const int64_t gs = nsell[i] * st.p;
+            want[i] = qa > 0 ? (int64_t)qa : 0;
+            full[i] = cost_of(want[i], st.p, fee);
+            ssum[i] = warp_sum_redux(gs - fee_of(gs, fee));
+            bsum[i] = warp_sum_redux(full[i]);
+            vsum[i] = warp_sum_redux(p1[i] * (hcur - nsell[i] + want[i]));
+        }
+#pragma unroll
+        for (int i = 0; i < NOWN; ++i) {
+            const int e = tile0 + orow[i];
+            const bool valid = orow[i] < 128 && e < v.N;
+            OwnEnv &st = own[i];
             const int64_t row = (int64_t)s * v.N + e;
-            if (valid && a.tr_act && lane < SK2) a.tr_act[row * SK2 + lane] = act;
             int64_t rew = 0, vlog = VLOG_NONE2;
             bool dn_out = true;
-            if (valid && !st.done) {
-                const bool live = lane < st.Ke;
-                float ac = isfinite(act) ? act : 0.0f;
-                ac = fminf(fmaxf(ac, -1.0f), 1.0f);
-                const int32_t qa = live ? (int32_t)__fmul_rz(ac, (float)v.hmax) : 0;
-                const int fee = v.fee_bps;
-                int64_t hcur = st.h;
-                int64_t cash = st.cash;
-                const int64_t v0 = cash + warp_sum(st.p * hcur);
-                // sells, branch-free: capped at the holding
-                const int64_t nsell = qa < 0 ? min((int64_t)(-qa), hcur) : 0;
-                const int64_t gs = nsell * st.p;
-                hcur -= nsell;
-                cash += warp_sum(gs - fee_of(gs, fee));
-                // buys: when every order fits, one scan settles them all
-                const int64_t want = qa > 0 ? (int64_t)qa : 0;
-                const int64_t full = cost_of(want, st.p, fee);
-                const int64_t one = cost_of(1, st.p, fee);
-                int64_t nb = 0;
-                const int64_t total = __shfl_sync(FULL_MASK, warp_incl_scan(full, lane), 31);
-                unsigned pending = __ballot_sync(FULL_MASK, want > 0);
-                if (total <= cash) {
-                    nb = want;
-                    cash -= total;
-                    pending = 0u;
+            if (run[i]) {
+                const int64_t cash1 = st.cash + ssum[i];
+                int64_t cash = cash1 - bsum[i];
+                int64_t nb = want[i];
+                int64_t v1 = cash + vsum[i];
+                if (bsum[i] > cash1) {                 // not every buy fits: greedy partial fills
+                    cash = own_buy_greedy(cash1, want[i], full[i], st.p, fee, lane, nb);
+                    v1 = cash + warp_sum_redux(p1[i] * (st.h - nsell[i] + nb));
                 }
-                while (pending) {
-                    bool mine = (pending >> lane) & 1u;
-                    pending &= ~__ballot_sync(FULL_MASK, mine && one > cash);
-                    if (!pending) break;
-                    mine = (pending >> lane) & 1u;
-                    const int64_t x = mine ? full : 0;
-                    const int64_t pre = warp_incl_scan(x, lane);
-                    const unsigned fail = __ballot_sync(FULL_MASK, mine && pre > cash);
-                    if (fail == 0u) {
-                        if (mine) nb = want;
-                        cash -= __shfl_sync(FULL_MASK, pre, 31);
-                        break;
-                    }
-                    const int f = __ffs(fail) - 1;
-                    if (mine && lane < f) nb = want;
-                    int64_t cf = cash - (pre - x);
-                    if (lane == f) {
-                        const int64_t n = afford(cf, st.p, fee);
-                        nb = n;
-                        cf -= cost_of(n, st.p, fee);
-                    }
-                    cash = __shfl_sync(FULL_MASK, cf, f);
-                    pending &= ~((2u << f) - 1u);
-                }
-                hcur += nb;
+                rew = v1 - st.v0;
                 st.t += 1;
-                const int64_t p1 = live ? perturb(cnext[i], st.bps) : 0;
-                const int64_t v1 = cash + warp_sum(p1 * hcur);
-                rew = v1 - v0;
                 st.done = st.t == st.W - 1;
                 dn_out = st.done;
                 vlog = st.done ? -v1 - 1 : v1;
                 st.cash = cash;
-                st.h = (int32_t)hcur;
-                st.p = p1;
+                st.h = (int32_t)(st.h - nsell[i] + nb);
+                st.p = p1[i];
+                st.v0 = v1;
                 if (st.done && v.auto_reset) {
                     st.cash = v.init_cash;
+                    st.v0 = v.init_cash;
                     st.t = 0;
                     st.done = 0;
                     st.h = 0;
-                    st.p = live ? perturb(__ldg(v.close + (int64_t)st.start * SK2 + lane), st.bps) : 0;
+                    st.p = lane < st.Ke ? perturb(__ldg(v.close + (int64_t)st.start * SK2 + lane), st.bps) : 0;
                 }
             }
             if (valid && lane == 0) {
@@ -557,16 +670,27 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                 if (a.tr_done) a.tr_done[row] = dn_out ? 1 : 0;
                 a.vlog[row] = vlog;
             }
-            if (s + 1 < T)
-                own_publish(a, st, valid, orow[i], a_base, ctx_addr, M2, lane, valid ? (int64_t)(s + 1) * v.N + e : -1);
         }
         if (s + 1 < T) {
-            fence_proxy_async_cluster();
-            __syncwarp();
-            if (lane == 0)
-                for (int m = 0; m < M2; ++m) mbar_arrive_remote(map_shared_rank(smem_u32(obs_ready), (uint32_t)m));
+#pragma unroll
+            for (int i = 0; i < NOWN; ++i) {
+                if (orow[i] >= 128) continue;
+                const int e = tile0 + orow[i];
+                const bool valid = e < v.N;
+                own_publish(a, own[i], valid, orow[i], a_base, ctx_addr, M2, lane,
+                            valid ? (int64_t)(s + 1) * v.N + e : -1);
+            }
         }
+        if (s + 1 < T) f2_signal_all(obs_ready, M2, lane, true);
     }
+    // every MMA this CTA issued has completed before TMEM is released, also
+    // when a wait gave up and the loop ran on without its data
+    if (issuer && lane == 0) {
+        mma_commit(&bars[B_END]);
+        volatile int no_abort = 0;
+        mbar_wait(&bars[B_END], 0u, &no_abort, a.err, 256u, TC_WAIT_NS);
+    }
+    __syncwarp();
     // state back to global memory (steps and accumulators: metrics replay)
 #pragma unroll
     for (int i = 0; i < NOWN; ++i) {
@@ -603,6 +727,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_rollout_stock2(const __grid_c
         mbar_init(&bars[B_H2], (uint32_t)F2_ENV_WARPS);            // this CTA's E2 warps
         mbar_init(&bars[B_P], 4u);                                 // the partner's 4 E3 warps
         mbar_init(&bars[B_X], (uint32_t)(p.M * 4));                // each agent's 4 E3 warps
+        mbar_init(&bars[B_END], 1);                                // the issuer's last commit
         *abort = 0;
         fence_mbar_init();
     }

@@ -130,6 +130,21 @@ __device__ __forceinline__ void mbar_arrive_remote(uint32_t addr)
     asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
 }
 
+// Release fence at cluster scope.  One fence followed by relaxed arrivals
+// on several barriers costs one drain of this thread's outstanding memory
+// operations; a release arrival per barrier drains once per arrival.
+__device__ __forceinline__ void fence_acq_rel_cluster()
+{
+    asm volatile("fence.acq_rel.cluster;" ::: "memory");
+}
+
+// Relaxed arrival on an mbarrier of another CTA of the cluster; preceded by
+// fence_acq_rel_cluster() it releases the writes made before the fence.
+__device__ __forceinline__ void mbar_arrive_remote_relaxed(uint32_t addr)
+{
+    asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
 // ----------------------------------------------------------- bulk copies
 // 1-D bulk copy global -> this CTA's shared memory, completing on `bar`.
 // dst, src 16-byte aligned; bytes a multiple of 16.
