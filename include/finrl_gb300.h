@@ -299,6 +299,16 @@ int rollout(fr_env *env, const fr_ensemble *ens, int32_t T,
  * at most 8 agents; other pairs always run unfused. */
 int env_set_rollout_path(fr_env *env, int32_t path);
 
+/* Kernel timing for roofline measurements (no counterpart in the paper).
+ * With on != 0, every later rollout() of this env records two CUDA events
+ * on its stream around the launch of its main rollout kernel only (the
+ * fused kernel; on the unfused path, nothing is recorded).
+ * env_last_kernel_ms waits for the last recorded pair and returns its
+ * elapsed milliseconds in *ms; FR_EINVAL when no pair was recorded since
+ * timing was switched on.  Timing adds two event records per rollout. */
+int env_set_kernel_timing(fr_env *env, int32_t on);
+int env_last_kernel_ms(fr_env *env, float *ms);
+
 #ifdef __cplusplus
 }
 #endif

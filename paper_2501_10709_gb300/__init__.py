@@ -21,7 +21,7 @@ __all__ = [
     "fr_ctx_create", "fr_market_create", "env_create", "env_reset", "env_step",
     "env_observe", "env_get_state", "env_metrics", "env_snapshot", "env_restore",
     "env_error_count", "env_dims", "ensemble_create", "ensemble_forward",
-    "ensemble_act", "ensemble_act_noalloc", "ensemble_device_errors", "rollout", "env_set_rollout_path", "FrError", "lib",
+    "ensemble_act", "ensemble_act_noalloc", "ensemble_device_errors", "rollout", "env_set_rollout_path", "env_set_kernel_timing", "env_last_kernel_ms", "FrError", "lib",
     "PATH_AUTO", "PATH_UNFUSED",
     "ACT_I32_SHARES", "ACT_F32_UNIT", "ACT_U8_DISCRETE", "PREC_FP32", "PREC_BF16",
     "PREC_FP8", "PREC_BF16X3", "COMBINE_MEAN", "COMBINE_VOTE", "TASK_STOCK", "TASK_CRYPTO",
@@ -210,6 +210,16 @@ def env_restore(env: Env, blob: bytes):
 
 def env_set_rollout_path(env: Env, path: int):
     _lib.check(lib().env_set_rollout_path(env, int(path)), "env_set_rollout_path")
+
+
+def env_set_kernel_timing(env: Env, on: bool):
+    _lib.check(lib().env_set_kernel_timing(env, 1 if on else 0), "env_set_kernel_timing")
+
+
+def env_last_kernel_ms(env: Env) -> float:
+    ms = C.c_float()
+    _lib.check(lib().env_last_kernel_ms(env, C.byref(ms)), "env_last_kernel_ms")
+    return ms.value
 
 
 def env_error_count(env: Env) -> int:

@@ -84,6 +84,8 @@ SIGNATURES = {
     "rollout": (i32, [vp, vp, i32, vp, vp, vp]),
     "env_set_rollout_path": (i32, [vp, i32]),
     "ensemble_act_noalloc": (i32, [vp, vp, i32, vp, vp]),
+    "env_set_kernel_timing": (i32, [vp, i32]),
+    "env_last_kernel_ms": (i32, [vp, vp]),
 }
 
 _lock = threading.Lock()

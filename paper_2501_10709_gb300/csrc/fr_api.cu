@@ -418,6 +418,8 @@ void env_destroy(fr_env *env)
     dev_free(env->ctx, env->block, env->bytes);
     dev_free(env->ctx, env->scratch, env->scratch_bytes);
     dev_free(env->ctx, env->slot_of_env, 4ull * env->v.N + 4ull * 32);
+    for (int i = 0; i < 2; ++i)
+        if (env->k_ev[i]) cudaEventDestroy(env->k_ev[i]);
     delete env;
 }
 
@@ -525,6 +527,41 @@ int env_set_rollout_path(fr_env *env, int32_t path)
              "env_set_rollout_path: bad argument");
     env->path = path;
     return FR_OK;
+}
+
+int env_set_kernel_timing(fr_env *env, int32_t on)
+{
+    FR_CHECK(env, FR_EINVAL, "env_set_kernel_timing: NULL env");
+    int rc = use_device(env->ctx);
+    if (rc) return rc;
+    for (int i = 0; i < 2 && on; ++i)
+        if (!env->k_ev[i]) FR_CUDA(cudaEventCreate(&env->k_ev[i]));
+    env->k_timing = on ? 1 : 0;
+    env->k_recorded = 0;
+    return FR_OK;
+}
+
+int env_last_kernel_ms(fr_env *env, float *ms)
+{
+    FR_CHECK(env && ms, FR_EINVAL, "env_last_kernel_ms: NULL argument");
+    FR_CHECK(env->k_recorded, FR_EINVAL, "env_last_kernel_ms: no kernel timed since timing was switched on");
+    int rc = use_device(env->ctx);
+    if (rc) return rc;
+    FR_CUDA(cudaEventSynchronize(env->k_ev[1]));
+    FR_CUDA(cudaEventElapsedTime(ms, env->k_ev[0], env->k_ev[1]));
+    return FR_OK;
+}
+
+extern "C++" {
+namespace fr {
+cudaError_t env_time_mark(fr_env *env, int which, cudaStream_t s)
+{
+    if (!env->k_timing) return cudaSuccess;
+    const cudaError_t e = cudaEventRecord(env->k_ev[which], s);
+    if (e == cudaSuccess && which == 1) env->k_recorded = 1;
+    return e;
+}
+}  // namespace fr
 }
 
 int env_error_count(fr_env *env, uint64_t *count)

@@ -107,7 +107,17 @@ struct fr_env {
     int32_t *slot_of_env;       // device [N] (+ slot_ke [32] after it)
     int32_t *slot_ke;
     int n_slots;
+    // optional events around the main rollout kernel
+    cudaEvent_t k_ev[2];
+    int k_timing;               // record on the next rollouts
+    int k_recorded;             // a pair has been recorded
 };
+
+namespace fr {
+// Record the timing event `which` (0 before, 1 after the main kernel) on s
+// when timing is on.
+cudaError_t env_time_mark(fr_env *env, int which, cudaStream_t s);
+}  // namespace fr
 
 namespace fr {
 

@@ -113,8 +113,12 @@ __device__ __forceinline__ void acc_push(double &mu, double &m2, double &mdd,
     mu = __dadd_rn(mu, __ddiv_rn(delta, (double)n));
     m2 = __dadd_rn(m2, __dmul_rn(delta, __dsub_rn(rho, mu)));
     if (v1 > peak) peak = v1;
-    const double dd = __dsub_rn(__ddiv_rn((double)v1, (double)peak), 1.0);
-    if (dd < mdd) mdd = dd;
+    // at a new peak the drawdown is exactly 0 and cannot lower mdd (<= 0):
+    // the division is needed only below the peak
+    if (v1 < peak) {
+        const double dd = __dsub_rn(__ddiv_rn((double)v1, (double)peak), 1.0);
+        if (dd < mdd) mdd = dd;
+    }
     vlast = v1;
 }
 

@@ -883,6 +883,7 @@ int tc_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    FR_CUDA(env_time_mark(env, 0, s));
     if (v.task == FR_TASK_STOCK) {
         FR_CUDA(cudaFuncSetAttribute(k_rollout_fused<FR_TASK_STOCK>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -892,6 +893,7 @@ int tc_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         FR_CUDA(cudaLaunchKernelEx(&cfg, k_rollout_fused<FR_TASK_CRYPTO>, a));
     }
+    FR_CUDA(env_time_mark(env, 1, s));
     FR_CUDA(launch_metrics_replay(v, a.vlog, T, metrics, s));
     return FR_OK;
 }
@@ -899,7 +901,10 @@ int tc_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
 cudaError_t launch_metrics_replay(const EnvView &v, const int64_t *vlog, int T, double *metrics,
                                   cudaStream_t s)
 {
-    k_metrics_replay<<<ceil_div(v.N, 256), 256, 0, s>>>(v, vlog, T, metrics);
+    // one thread per env, spread over every SM: the replay is bound by the
+    // FP64 units, and 2,048 envs in blocks of 256 would use 8 SMs
+    const int per_block = std::min(256, std::max(16, (int)ceil_div(v.N, 152) + 15) / 16 * 16);
+    k_metrics_replay<<<ceil_div(v.N, per_block), per_block, 0, s>>>(v, vlog, T, metrics);
     return cudaGetLastError();
 }
 

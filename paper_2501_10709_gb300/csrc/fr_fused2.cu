@@ -310,43 +310,81 @@ __device__ __noinline__ void own_traj_obs(const F2Args &a, float *o, float cv, f
     for (int i = lane; i < NIND; i += 32) o[NSTATE + i] = (i % SK2) < Ke ? __ldg(f + i) : 0.0f;
 }
 
-// The next observation row of env r: chunks 0..7 of the A operand (state
-// positions 0..63: cash, 30 prices, 30 holdings, zero padding) in every CTA
-// of the cluster, plus its Z row index.  Each lane contributes its price and
-// holding as a bf16 pair; lanes 0..7 gather the 8 positions of their chunk.
-__device__ __forceinline__ void own_publish(const F2Args &a, const OwnEnv &s, bool valid, int r, uint32_t a_base,
-                                            uint32_t ctx_addr, int M2, int lane, int64_t trow)
+// The next observation row of env r: state positions 0..63 (cash, 30
+// prices, 30 holdings, zero padding) as BF16, chunk c = positions 8c..8c+7.
+// Every lane builds the words of chunk lane & 7 from the warp's price and
+// holding pairs, so that the stores to the cluster's CTAs spread over all
+// lanes: one 16-byte store per lane per four destination CTAs.
+struct ObsWords {
+    uint32_t w0, w1, w2, w3;
+    int zrow;
+    float pv, hv, cv;
+};
+
+__device__ __forceinline__ ObsWords own_words(const F2Args &a, const OwnEnv &s, bool valid, int lane)
 {
-    using namespace ptx;
-    const float pv = (valid && lane < s.Ke) ? obs_scale(s.p, 1e-4f) : 0.0f;
-    const float hv = (valid && lane < s.Ke) ? __fmul_rn(__int2float_rn(s.h), 1e-2f) : 0.0f;
-    const float cv = valid ? obs_scale(s.cash, 1e-8f) : 0.0f;
-    const __nv_bfloat162 ph2 = __floats2bfloat162_rn(pv, hv);      // .x price, .y holding
+    ObsWords o;
+    o.pv = (valid && lane < s.Ke) ? obs_scale(s.p, 1e-4f) : 0.0f;
+    o.hv = (valid && lane < s.Ke) ? __fmul_rn(__int2float_rn(s.h), 1e-2f) : 0.0f;
+    o.cv = valid ? obs_scale(s.cash, 1e-8f) : 0.0f;
+    const __nv_bfloat162 ph2 = __floats2bfloat162_rn(o.pv, o.hv);      // .x price, .y holding
     const uint32_t mine = *(const uint32_t *)&ph2;
-    const __nv_bfloat16 cb = __float2bfloat16_rn(cv);
+    const __nv_bfloat16 cb = __float2bfloat16_rn(o.cv);
     const uint32_t cbits = (uint32_t)*(const uint16_t *)&cb;
     uint32_t hw[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-        const int pos = 8 * lane + u;
+        const int pos = 8 * (lane & 7) + u;
         const int src = pos <= SK2 ? pos - 1 : pos - 1 - SK2;
         const uint32_t g = __shfl_sync(FULL_MASK, mine, src & 31);
         hw[u] = pos == 0 ? cbits : (pos <= SK2 ? (g & 0xffffu) : (pos < NSTATE ? (g >> 16) : 0u));
     }
-    const uint32_t row_off = (uint32_t)(r / 8) * 128u + (uint32_t)(r % 8) * 16u;
-    const uint32_t a_obs = a_base + (uint32_t)(a.plan.H1 / 8) * 2048u;
-    if (lane < 8) {
-        const uint32_t w0 = hw[0] | (hw[1] << 16), w1 = hw[2] | (hw[3] << 16);
-        const uint32_t w2 = hw[4] | (hw[5] << 16), w3 = hw[6] | (hw[7] << 16);
-        for (int m = 0; m < M2; ++m)
-            st_cluster_v4(map_shared_rank(a_obs + (uint32_t)lane * 2048u + row_off, (uint32_t)m), w0, w1, w2, w3);
-    } else if (lane < 8 + M2) {
-        const int zrow = valid ? s.slot * a.v.n_days + s.start + s.t : 0;
-        asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(map_shared_rank(ctx_addr + 4u * r, (uint32_t)(lane - 8))),
-                     "r"(zrow)
+    o.w0 = hw[0] | (hw[1] << 16);
+    o.w1 = hw[2] | (hw[3] << 16);
+    o.w2 = hw[4] | (hw[5] << 16);
+    o.w3 = hw[6] | (hw[7] << 16);
+    o.zrow = valid ? s.slot * a.v.n_days + s.start + s.t : 0;
+    return o;
+}
+
+// Row r's chunks to CTAs lane >> 3 and 4 + (lane >> 3), its Z row index to
+// CTA `lane`.
+__device__ __forceinline__ void own_store(const ObsWords &o, int r, uint32_t a_obs, uint32_t ctx_addr, int M2,
+                                          int lane)
+{
+    using namespace ptx;
+    const uint32_t at = a_obs + (uint32_t)(lane & 7) * 2048u + (uint32_t)(r / 8) * 128u + (uint32_t)(r % 8) * 16u;
+    const int m0 = lane >> 3;
+    if (m0 < M2) st_cluster_v4(map_shared_rank(at, (uint32_t)m0), o.w0, o.w1, o.w2, o.w3);
+    if (m0 + 4 < M2) st_cluster_v4(map_shared_rank(at, (uint32_t)(m0 + 4)), o.w0, o.w1, o.w2, o.w3);
+    if (lane < M2)
+        asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(map_shared_rank(ctx_addr + 4u * r, (uint32_t)lane)),
+                     "r"(o.zrow)
                      : "memory");
+}
+
+// Publish the next observations of this warp's owned envs: all rows' words
+// first (their shuffles overlap), then all stores, then the optional fp32
+// trajectory rows.  trow[i] < 0: no trajectory row.
+template <int NOWN>
+__device__ __forceinline__ void own_publish_all(const F2Args &a, const OwnEnv *own, const int *orow, int tile0,
+                                                uint32_t a_obs, uint32_t ctx_addr, int M2, int lane, int64_t tbase)
+{
+    ObsWords o[NOWN];
+#pragma unroll
+    for (int i = 0; i < NOWN; ++i) o[i] = own_words(a, own[i], orow[i] < 128 && tile0 + orow[i] < a.v.N, lane);
+#pragma unroll
+    for (int i = 0; i < NOWN; ++i)
+        if (orow[i] < 128) own_store(o[i], orow[i], a_obs, ctx_addr, M2, lane);
+    if (a.tr_obs) {
+#pragma unroll
+        for (int i = 0; i < NOWN; ++i) {
+            const int e = tile0 + orow[i];
+            if (orow[i] < 128 && e < a.v.N)
+                own_traj_obs(a, a.tr_obs + (tbase + e) * a.obs_ld, o[i].cv, o[i].pv, o[i].hv,
+                             own[i].start + own[i].t, own[i].Ke, lane);
+        }
     }
-    if (a.tr_obs && valid && trow >= 0) own_traj_obs(a, a.tr_obs + trow * a.obs_ld, cv, pv, hv, s.start + s.t, s.Ke, lane);
 }
 
 template <int NOWN>
@@ -415,12 +453,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         s.v0 = s.cash + warp_sum(s.p * (int64_t)s.h);
     }
     // observation of step 0
-#pragma unroll
-    for (int i = 0; i < NOWN; ++i) {
-        if (orow[i] >= 128) continue;
-        const int e = tile0 + orow[i];
-        own_publish(a, own[i], e < v.N, orow[i], a_base, ctx_addr, M2, lane, e < v.N ? (int64_t)e : -1);
-    }
+    own_publish_all<NOWN>(a, own, orow, tile0, a_obs, ctx_addr, M2, lane, 0);
     f2_signal_all(obs_ready, M2, lane, true);
 
     const float *zbase = a.Z + (size_t)j * a.n_ctx_per_agent * p.H1;
@@ -562,9 +595,9 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                 uint32_t pk[16];
 #pragma unroll
                 for (int c = 0; c < 32; c += 2) {
-                    const float y0 = c < SK2 ? tanhf(__fadd_rn(__fadd_rn(__uint_as_float(vv[c]), pp[c]), b3[c])) : 0.0f;
+                    const float y0 = c < SK2 ? tanh_approx(__fadd_rn(__fadd_rn(__uint_as_float(vv[c]), pp[c]), b3[c])) : 0.0f;
                     const float y1 = c + 1 < SK2
-                                         ? tanhf(__fadd_rn(__fadd_rn(__uint_as_float(vv[c + 1]), pp[c + 1]), b3[c + 1]))
+                                         ? tanh_approx(__fadd_rn(__fadd_rn(__uint_as_float(vv[c + 1]), pp[c + 1]), b3[c + 1]))
                                          : 0.0f;
                     const __half2 h2 = __floats2half2_rn(y0, y1);
                     pk[c / 2] = *(const uint32_t *)&h2;
@@ -671,16 +704,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                 a.vlog[row] = vlog;
             }
         }
-        if (s + 1 < T) {
-#pragma unroll
-            for (int i = 0; i < NOWN; ++i) {
-                if (orow[i] >= 128) continue;
-                const int e = tile0 + orow[i];
-                const bool valid = e < v.N;
-                own_publish(a, own[i], valid, orow[i], a_base, ctx_addr, M2, lane,
-                            valid ? (int64_t)(s + 1) * v.N + e : -1);
-            }
-        }
+        if (s + 1 < T) own_publish_all<NOWN>(a, own, orow, tile0, a_obs, ctx_addr, M2, lane, (int64_t)(s + 1) * v.N);
         if (s + 1 < T) f2_signal_all(obs_ready, M2, lane, true);
     }
     // every MMA this CTA issued has completed before TMEM is released, also
@@ -1003,7 +1027,9 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     FR_CUDA(cudaFuncSetAttribute(k_rollout_stock2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FR_CUDA(env_time_mark(env, 0, s));
     FR_CUDA(cudaLaunchKernelEx(&cfg, k_rollout_stock2, a));
+    FR_CUDA(env_time_mark(env, 1, s));
     FR_CUDA(launch_metrics_replay(v, vlog, T, metrics, s));
     return FR_OK;
 }

@@ -145,6 +145,15 @@ __device__ __forceinline__ void mbar_arrive_remote_relaxed(uint32_t addr)
     asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
 }
 
+// Hardware tanh approximation (one MUFU operation; relative error about
+// 2^-11, below the fp16 rounding the actor outputs get next).
+__device__ __forceinline__ float tanh_approx(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // ----------------------------------------------------------- bulk copies
 // 1-D bulk copy global -> this CTA's shared memory, completing on `bar`.
 // dst, src 16-byte aligned; bytes a multiple of 16.

@@ -192,3 +192,22 @@ def test_fused_and_unfused_paths_agree_on_prices_and_accounting(ctx, dev):
         acts.append(tr["act"].cpu().numpy())
     # the first step acts on identical observations
     assert np.abs(acts[0][0] - acts[1][0]).max() < 1e-2
+
+
+def test_kernel_timing_hook(ctx, dev):
+    w = synth.workload_stock_2048(N=256, T=8)
+    e = w.envs
+    mk = fr.fr_market_create(ctx, w.market)
+    env = _stock_env(ctx, mk, e)
+    ens = fr.ensemble_create(ctx, w.dims, w.params, precision=fr.PREC_BF16)
+    with pytest.raises(fr.FrError):
+        fr.env_last_kernel_ms(env)                 # nothing recorded yet
+    fr.env_set_kernel_timing(env, True)
+    with pytest.raises(fr.FrError):
+        fr.env_last_kernel_ms(env)
+    fr.rollout(env, ens, 8)
+    ms = fr.env_last_kernel_ms(env)
+    assert 0.0 < ms < 1e3
+    fr.env_set_kernel_timing(env, False)
+    with pytest.raises(fr.FrError):
+        fr.env_last_kernel_ms(env)
