@@ -152,6 +152,24 @@ def time_rollouts(fr, env, ens, T, steps, warmup, metrics, flush, stream, traj=N
     return times
 
 
+def crypto_line(fr, ctx, dev, flush, stream, reps=3):
+    import torch
+    from paper_2501_10709_gb300 import synth
+    w = synth.workload_crypto()
+    e = w.envs
+    mk = fr.fr_market_create(ctx, w.market)
+    env = fr.env_create(ctx, mk, start=e.start, window=e.W, init_cash=e.init_cash, pmax=e.pmax)
+    met = torch.empty(e.N, 3, dtype=torch.float64, device=dev)
+    res = {"workload": f"crypto {e.N} envs x {w.T} steps, 5 x 10-128-128-3 Q-nets, majority vote, "
+                       "480,000 s GBM mid", "unit": "env-steps/s"}
+    for name, prec, T in (("fused_bf16", fr.PREC_BF16, w.T), ("plain_fp32", fr.PREC_FP32, 128)):
+        ens = fr.ensemble_create(ctx, w.dims, w.params, precision=prec, combine=fr.COMBINE_VOTE, out_act=0)
+        ts = time_rollouts(fr, env, ens, T, reps, 3, met, flush, stream)
+        res[name] = {"value": e.N * T * len(ts) / sum(ts), "ms_per_rollout": 1e3 * statistics.mean(ts),
+                     "steps_per_rollout": T}
+    return res
+
+
 def time_kernel(fn, iters, stream):
     import torch
     for _ in range(3):
@@ -251,6 +269,11 @@ def run_gpu(args):
     kb_dt = time_kernel(lambda: fr.ensemble_forward(ens_bf16, obs_big, y_big), 10, stream)
     big_tflops = nb / N * flops_per_launch / kb_dt / 1e12
 
+    # crypto config: 8,192 envs x 1,024 steps, 5 x 10-128-128-3 Q-nets, vote
+    # (fused BF16 path for the full horizon; the plain FP32 path on the first
+    # 128 steps of the same envs, to bound the run time)
+    crypto = crypto_line(fr, ctx, dev, flush, stream) if not args.no_crypto else None
+
     # end to end through the public API with host buffers
     snap = fr.env_snapshot(env)
     host_met = torch.empty(N, 3, dtype=torch.float64, pin_memory=True)
@@ -301,6 +324,7 @@ def run_gpu(args):
                                       "us_per_launch": a_dt * 1e6},
                      "actor_kernel_large_batch": {"rows": nb, "achieved": big_tflops,
                                                   "frac": big_tflops / peak}},
+        "crypto_c3": crypto,
         "gpu_launches": launches_per_rollout * args.steps,
         "clocks": clk,
     }
@@ -395,6 +419,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-crypto", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-envs", type=int, default=32)
     args = ap.parse_args()

@@ -173,14 +173,7 @@ __device__ void fused_mma(const FusedArgs &a, uint32_t tmem, const uint8_t *A, c
 __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volatile int *abort, unsigned *err,
                                           unsigned code, bool cluster_scope)
 {
-    using namespace ptx;
-    int ok = 1;
-    if ((threadIdx.x & 31) == 0)
-        ok = cluster_scope ? mbar_wait_cluster(bar, parity, abort, err, code, TC_WAIT_NS)
-                           : mbar_wait(bar, parity, abort, err, code, TC_WAIT_NS);
-    ok = __shfl_sync(FULL_MASK, ok, 0);
-    __syncwarp();
-    return ok != 0;
+    return ptx::warp_wait_all(bar, parity, cluster_scope, abort, err, code, TC_WAIT_NS);
 }
 
 // Eight floats -> four words of two BF16 (round to nearest), K order.
@@ -461,13 +454,12 @@ __device__ void fused_env(const FusedArgs &a, uint32_t tmem, uint8_t *A, uint8_t
 
         // ------------------------------------------------ 2. the agent's MLP
         const int b = s & 1;
-        bool ok = true;
-        for (int l = 0; l < L && ok; ++l) {
+        // no early exit anywhere in the step loop: a wait that gives up sets
+        // the abort flag, later waits return at once and the loop runs to its
+        // uniform end, so the warp stays converged at every collective
+        for (int l = 0; l < L; ++l) {
             const TcLayer &ly = p.layer[l];
-            if (!warp_wait(acc_full, (uint32_t)(s * L + l) & 1u, abort, a.err, 16u, false)) {
-                ok = false;
-                break;
-            }
+            warp_wait(acc_full, (uint32_t)(s * L + l) & 1u, abort, a.err, 16u, false);
             tc_fence_after();
             const float *bl = a.bias + ((size_t)agent * MAX_LAYERS + l) * 256;
             if (l < L - 1) {
@@ -513,12 +505,14 @@ __device__ void fused_env(const FusedArgs &a, uint32_t tmem, uint8_t *A, uint8_t
                 for (int m = 0; m < M; ++m) st_cluster_u8(map_shared_rank(xoff, (uint32_t)m), (uint32_t)best);
             }
             __syncwarp();                                  // the warp's stores precede lane 0's release
-            if (lane == 0)
-                for (int m = 0; m < M; ++m) mbar_arrive_remote(map_shared_rank(smem_u32(&xready[b]), (uint32_t)m));
+            if (lane == 0) {
+                fence_acq_rel_cluster();                   // one release, then relaxed arrivals
+                for (int m = 0; m < M; ++m)
+                    mbar_arrive_remote_relaxed(map_shared_rank(smem_u32(&xready[b]), (uint32_t)m));
+            }
         }
-        if (!ok) break;
-        // ----------------------------------------- 3. every agent's output in
-        if (!warp_wait(&xready[b], (uint32_t)(s >> 1) & 1u, abort, a.err, 32u, true)) break;
+         // ----------------------------------------- 3. every agent's output in
+        warp_wait(&xready[b], (uint32_t)(s >> 1) & 1u, abort, a.err, 32u, true);
         if (e < 0) continue;
 
         // ------------------------------------ 4. combine, trade, reward, log
@@ -626,7 +620,7 @@ __device__ void fused_env(const FusedArgs &a, uint32_t tmem, uint8_t *A, uint8_t
         } else {
             const uint8_t *xr = xbuf + (size_t)(b * M) * 128 + r;
             int cnt[3] = {0, 0, 0};
-            for (int j = 0; j < M; ++j) cnt[xr[(size_t)j * 128]]++;
+            for (int j = 0; j < M; ++j) cnt[min((int)xr[(size_t)j * 128], 2)]++;   // clamped after an aborted wait
             int best = 0, bc = cnt[0];
             bool tie = false;
 #pragma unroll
@@ -698,7 +692,8 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rollout_fused(const __grid_co
     uint64_t *acc_full = bars + 2 * FU_MAX_STAGES;
     uint64_t *a_ready = acc_full + 1;
     uint64_t *xready = a_ready + 1;                    // [2]
-    uint32_t *tmem_slot = (uint32_t *)(xready + 2);
+    uint64_t *drain = xready + 2;                      // the issuer's last commit
+    uint32_t *tmem_slot = (uint32_t *)(drain + 1);
     volatile int *abort = (volatile int *)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -714,6 +709,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rollout_fused(const __grid_co
         mbar_init(a_ready, 128);
         mbar_init(&xready[0], (uint32_t)(M * 4));        // one arrival per env warp per CTA
         mbar_init(&xready[1], (uint32_t)(M * 4));
+        mbar_init(drain, 1);
         *abort = 0;
         fence_mbar_init();
     }
@@ -731,7 +727,14 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rollout_fused(const __grid_co
     if (warp == 0) {
         if (lane == 0) fused_producer(a, a.img + (size_t)agent * p.agent_bytes, ring, full, empty, abort);
     } else if (warp == 1) {
-        if (lane == 0) fused_mma(a, tmem, A, ring, full, empty, acc_full, a_ready, abort);
+        if (lane == 0) {
+            fused_mma(a, tmem, A, ring, full, empty, acc_full, a_ready, abort);
+            // every MMA issued has completed before TMEM is released, also
+            // when the issuer left early
+            mma_commit(drain);
+            volatile int no_abort = 0;
+            mbar_wait(drain, 0u, &no_abort, a.err, 128u, TC_WAIT_NS);
+        }
     } else {
         fused_env<TASK>(a, tmem, A, xbuf, acc_full, a_ready, xready, abort, warp, lane, agent, tile);
     }

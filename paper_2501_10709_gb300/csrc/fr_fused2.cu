@@ -146,37 +146,10 @@ __host__ __device__ inline F2Smem f2_smem(const F2Plan &p)
 // barrier slots
 enum { B_W = 0, B_OBS, B_ACC, B_H1, B_H2, B_P, B_X, B_END, B_COUNT };
 
-// Bounded wait on an mbarrier phase by the whole warp.  Every lane polls the
-// barrier and the exit is taken on a warp vote, so the warp leaves the wait
-// converged: a wait by one elected lane (the others parked at a shuffle)
-// leaves the warp split after the lane's suspension, and every later
-// warp-collective operation of the step then pays for a reconvergence.  On
-// giving up (time limit, or another warp of the CTA gave up) it sets *abort
-// and bit `code` of *err and returns false.
 __device__ __forceinline__ bool f2_wait(uint64_t *bar, uint32_t parity, volatile int *abort, unsigned *err,
                                         unsigned code, bool cluster_scope)
 {
-    using namespace ptx;
-    if (__any_sync(FULL_MASK, *abort != 0)) return false;
-    uint64_t t0 = 0;
-#pragma unroll 1
-    for (uint32_t i = 0;; ++i) {
-        const bool mine = cluster_scope ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity);
-        if (__all_sync(FULL_MASK, mine)) return true;
-        if ((i & 15u) == 15u) {
-            if (__any_sync(FULL_MASK, *abort != 0)) return false;
-            const uint64_t now = __shfl_sync(FULL_MASK, globaltimer(), 0);
-            if (t0 == 0) {
-                t0 = now;
-            } else if (now - t0 > TC_WAIT_NS) {
-                if ((threadIdx.x & 31) == 0) {
-                    *abort = 1;
-                    atomicOr(err, code);
-                }
-                return false;
-            }
-        }
-    }
+    return ptx::warp_wait_all(bar, parity, cluster_scope, abort, err, code, TC_WAIT_NS);
 }
 
 // Arrive on `bar` in every CTA of the cluster once this warp's shared-memory

@@ -123,6 +123,41 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t *bar, uint32_t parity
     }
 }
 
+// Bounded wait on an mbarrier phase by a whole warp.  Every lane polls the
+// barrier and the exit is taken on a warp vote, so the warp leaves the wait
+// converged.  (A wait by one elected lane while the others park at a shuffle
+// leaves the warp split after the lane's suspension, and every later
+// warp-collective operation in a loop then pays for a reconvergence.)  On
+// giving up -- after limit_ns, or once another warp of the block has set
+// *abort -- it sets *abort and bit `code` of *err and returns false.  Call
+// with all 32 lanes active.
+__device__ __forceinline__ bool warp_wait_all(uint64_t *bar, uint32_t parity, bool cluster_scope,
+                                              volatile int *abort, unsigned *err, unsigned code,
+                                              uint64_t limit_ns)
+{
+    constexpr unsigned ALL = 0xffffffffu;
+    if (__any_sync(ALL, *abort != 0)) return false;
+    uint64_t t0 = 0;
+#pragma unroll 1
+    for (uint32_t i = 0;; ++i) {
+        const bool mine = cluster_scope ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity);
+        if (__all_sync(ALL, mine)) return true;
+        if ((i & 15u) == 15u) {
+            if (__any_sync(ALL, *abort != 0)) return false;
+            const uint64_t now = __shfl_sync(ALL, globaltimer(), 0);
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > limit_ns) {
+                if ((threadIdx.x & 31) == 0) {
+                    *abort = 1;
+                    atomicOr(err, code);
+                }
+                return false;
+            }
+        }
+    }
+}
+
 // Arrive (release, cluster scope) on an mbarrier of another CTA of the
 // cluster; addr is a shared::cluster address from map_shared_rank.
 __device__ __forceinline__ void mbar_arrive_remote(uint32_t addr)
