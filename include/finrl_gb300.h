@@ -309,6 +309,84 @@ int env_set_rollout_path(fr_env *env, int32_t path);
 int env_set_kernel_timing(fr_env *env, int32_t on);
 int env_last_kernel_ms(fr_env *env, float *ms);
 
+/* ---------------------------------------------------------------- serving */
+/* Backtests as requests: many independent backtests (each a group of envs
+ * over one window, Sec. 4.2.1 trajectories) served by one GPU with
+ * continuous batching.  The server owns a pool of `capacity` env slots over
+ * one market and runs the ensemble's rollout on the whole pool in chunks of
+ * `chunk_steps` steps (the fused kernel for BF16 ensembles).  At every chunk
+ * boundary it retires the requests whose windows are complete (their rows of
+ * the episode metrics go to the caller's host buffer) and admits queued
+ * requests into the freed slots in arrival order; a request waits while the
+ * one ahead of it does not fit.  One host thread per server drives the GPU
+ * on its own stream; submit and poll only touch host state and never block
+ * on the GPU.  No counterpart in the paper beyond running many
+ * trajectories in parallel. */
+typedef struct fr_server fr_server;
+
+typedef struct {
+    const fr_market *market;  /* borrowed; outlives the server              */
+    const fr_ensemble *ens;   /* borrowed; combine/output match the task    */
+    int32_t capacity;         /* env slots, >= 1                            */
+    int32_t chunk_steps;      /* steps per rollout launch, >= 1             */
+    int64_t init_cash;        /* cents, >= 0                                */
+    int32_t hmax;             /* stock: 1..1e6                              */
+    int32_t fee_bps;          /* stock: 0..10000                            */
+    int32_t pmax;             /* crypto: >= 1                               */
+} fr_server_desc;
+
+/* Create / destroy.  Destroy stops the worker after its current chunk;
+ * requests not yet complete are dropped (their tickets become unknown). */
+int fr_server_create(fr_ctx *ctx, const fr_server_desc *desc, fr_server **out);
+void fr_server_destroy(fr_server *srv);
+
+/* One backtest: n_envs envs, env i over days (or seconds)
+ * start + i*start_stride .. + window - 1; stock envs trade the first
+ * n_assets assets with per-env per-asset price perturbations drawn from
+ * `seed` uniformly in [-bps_range, bps_range] basis points (Sec. 5.1;
+ * SplitMix64 of seed, env and asset).  metrics: caller-owned host buffer
+ * double [n_envs][3] (cumulative return, Sharpe, max drawdown, as
+ * env_metrics), written by the server before the request reports done; it
+ * must stay valid until then.  want_traj must be 0: the server returns
+ * metrics only.  Errors at submit: bad fields or a window past the market
+ * end -> FR_EINVAL; n_envs > capacity (can never fit) -> FR_ENOMEM; a
+ * server whose worker failed -> that error.  A request that fits later is
+ * queued. */
+typedef struct {
+    int32_t n_envs;
+    int32_t window;           /* >= 2                                       */
+    int32_t start;            /* >= 0                                       */
+    int32_t start_stride;     /* >= 0                                       */
+    int32_t n_assets;         /* stock: 1..K (0 = K)                        */
+    int32_t bps_range;        /* stock: 0..100                              */
+    uint64_t seed;
+    int32_t want_traj;        /* must be 0                                  */
+    double *metrics;          /* host [n_envs][3]                           */
+} fr_request;
+
+typedef struct {
+    int32_t status;           /* FR_OK, or the error that failed it         */
+    int32_t n_envs;
+    double queue_s;           /* submit -> admitted into slots              */
+    double latency_s;         /* submit -> metrics written                  */
+} fr_result;
+
+int backtest_submit(fr_server *srv, const fr_request *req, uint64_t *ticket);
+
+/* Non-blocking.  Running or queued: FR_ENOTREADY, *done = 0.  Complete:
+ * FR_OK, *done = 1, *out filled, and the ticket is released (a later poll
+ * of it returns FR_ENOTFOUND).  Unknown ticket: FR_ENOTFOUND. */
+int backtest_poll(fr_server *srv, uint64_t ticket, fr_result *out, int32_t *done);
+
+typedef struct {
+    uint64_t submitted, completed, queued, running;
+    double env_steps;         /* slot-steps of requests run (their windows) */
+    double pool_steps;        /* capacity x steps launched                  */
+    double busy_s;            /* wall time of the worker's GPU rounds       */
+} fr_server_stats;
+
+int fr_server_stats_get(fr_server *srv, fr_server_stats *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,8 @@ __all__ = [
     "fr_ctx_create", "fr_market_create", "env_create", "env_reset", "env_step",
     "env_observe", "env_get_state", "env_metrics", "env_snapshot", "env_restore",
     "env_error_count", "env_dims", "ensemble_create", "ensemble_forward",
-    "ensemble_act", "ensemble_act_noalloc", "ensemble_device_errors", "rollout", "env_set_rollout_path", "env_set_kernel_timing", "env_last_kernel_ms", "FrError", "lib",
+    "ensemble_act", "ensemble_act_noalloc", "ensemble_device_errors", "rollout", "env_set_rollout_path", "env_set_kernel_timing", "env_last_kernel_ms", "Server", "fr_server_create", "backtest_submit",
+    "backtest_poll", "fr_server_stats", "FrError", "lib",
     "PATH_AUTO", "PATH_UNFUSED",
     "ACT_I32_SHARES", "ACT_F32_UNIT", "ACT_U8_DISCRETE", "PREC_FP32", "PREC_BF16",
     "PREC_FP8", "PREC_BF16X3", "COMBINE_MEAN", "COMBINE_VOTE", "TASK_STOCK", "TASK_CRYPTO",
@@ -301,3 +302,58 @@ def rollout(env: Env, ens: Ensemble, T: int, *, traj: dict | None = None, metric
     _lib.check(lib().rollout(env, ens, int(T), tp,
                              _dptr(metrics, torch.float64, env.N * 3, "metrics"),
                              _stream(stream)), "rollout")
+
+
+# ------------------------------------------------------------------ serving
+class Server(_Handle):
+    """Backtest server (continuous batching over a pool of env slots)."""
+    _destroy = "fr_server_destroy"
+
+    def __init__(self, ptr, keep=()):
+        super().__init__(ptr, keep)
+        self._pending = {}            # ticket -> host metrics buffer the worker writes
+
+    def close(self):
+        super().close()
+        self._pending.clear()
+
+
+def fr_server_create(ctx: Ctx, market: Market, ens: Ensemble, *, capacity: int, chunk_steps: int = 32,
+                     init_cash: int = 100_000_000, hmax: int = 100, fee_bps: int = 10,
+                     pmax: int = 10) -> Server:
+    d = _lib.ServerDesc(market.ptr, ens.ptr, int(capacity), int(chunk_steps), int(init_cash), int(hmax),
+                        int(fee_bps), int(pmax))
+    out = C.c_void_p()
+    _lib.check(lib().fr_server_create(ctx, C.byref(d), C.byref(out)), "fr_server_create")
+    return Server(out.value, keep=(ctx, market, ens))
+
+
+def backtest_submit(srv: Server, *, n_envs: int, window: int, start: int, start_stride: int = 0,
+                    n_assets: int = 0, bps_range: int = 0, seed: int = 0) -> int:
+    met = np.zeros((int(n_envs), 3), dtype=np.float64)
+    r = _lib.Request(int(n_envs), int(window), int(start), int(start_stride), int(n_assets),
+                     int(bps_range), int(seed) & (2**64 - 1), 0, met.ctypes.data_as(C.c_void_p))
+    t = C.c_uint64()
+    _lib.check(lib().backtest_submit(srv, C.byref(r), C.byref(t)), "backtest_submit")
+    srv._pending[t.value] = met
+    return t.value
+
+
+def backtest_poll(srv: Server, ticket: int):
+    """None while queued or running; else a dict with the request's result
+    (status, n_envs, queue_s, latency_s, metrics [n_envs][3])."""
+    res = _lib.Result()
+    done = C.c_int32()
+    rc = lib().backtest_poll(srv, C.c_uint64(int(ticket)), C.byref(res), C.byref(done))
+    if rc == _lib.FR_ENOTREADY:
+        return None
+    _lib.check(rc, "backtest_poll")
+    met = srv._pending.pop(int(ticket))
+    return {"status": res.status, "n_envs": res.n_envs, "queue_s": res.queue_s,
+            "latency_s": res.latency_s, "metrics": met}
+
+
+def fr_server_stats(srv: Server) -> dict:
+    st = _lib.ServerStats()
+    _lib.check(lib().fr_server_stats_get(srv, C.byref(st)), "fr_server_stats_get")
+    return {k: getattr(st, k) for k, _ in st._fields_}

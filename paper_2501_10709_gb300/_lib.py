@@ -55,6 +55,26 @@ class Traj(C.Structure):
                 ("done", vp)]
 
 
+class ServerDesc(C.Structure):
+    _fields_ = [("market", vp), ("ens", vp), ("capacity", i32), ("chunk_steps", i32),
+                ("init_cash", i64), ("hmax", i32), ("fee_bps", i32), ("pmax", i32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("n_envs", i32), ("window", i32), ("start", i32), ("start_stride", i32),
+                ("n_assets", i32), ("bps_range", i32), ("seed", u64), ("want_traj", i32),
+                ("metrics", vp)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", i32), ("n_envs", i32), ("queue_s", f64), ("latency_s", f64)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", u64), ("completed", u64), ("queued", u64), ("running", u64),
+                ("env_steps", f64), ("pool_steps", f64), ("busy_s", f64)]
+
+
 # name -> (restype, argtypes); every symbol the header declares
 SIGNATURES = {
     "fr_last_error": (cp, []),
@@ -86,6 +106,11 @@ SIGNATURES = {
     "ensemble_act_noalloc": (i32, [vp, vp, i32, vp, vp]),
     "env_set_kernel_timing": (i32, [vp, i32]),
     "env_last_kernel_ms": (i32, [vp, vp]),
+    "fr_server_create": (i32, [vp, vp, vp]),
+    "fr_server_destroy": (None, [vp]),
+    "backtest_submit": (i32, [vp, vp, vp]),
+    "backtest_poll": (i32, [vp, u64, vp, vp]),
+    "fr_server_stats_get": (i32, [vp, vp]),
 }
 
 _lock = threading.Lock()
