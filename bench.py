@@ -170,6 +170,52 @@ def crypto_line(fr, ctx, dev, flush, stream, reps=3):
     return res
 
 
+def serving_line(fr, ctx, mk, ens_by_name, duration=10.0, rate=200.0, drain_s=60.0):
+    """Stock backtest requests (Poisson, `rate`/s for `duration` s) against a
+    2,048-slot server; latency = scheduled arrival -> poll returns done."""
+    import numpy as np
+    from paper_2501_10709_gb300 import synth
+    trace = synth.serving_trace_stock(rate, duration)
+    offered = sum(r["n_envs"] * (r["window"] - 1) for r in trace) / duration
+    out = {"workload": f"stock backtests, Poisson {rate:g}/s for {duration:g} s ({len(trace)} requests), "
+                       "N ~ U{1..512} envs, W ~ U{5..500} days, +-1% perturbation; 2,048-slot server, "
+                       "16-step chunks", "requests": len(trace),
+           "offered_env_steps_per_s": offered}
+    for name, ens in ens_by_name.items():
+        srv = fr.fr_server_create(ctx, mk, ens, capacity=2048, chunk_steps=16)
+        # one warm request first (kernel images, Z table)
+        t = fr.backtest_submit(srv, n_envs=8, window=20, start=100)
+        while fr.backtest_poll(srv, t) is None:
+            time.sleep(0.001)
+        pending, lat, i = {}, [], 0
+        t0 = time.perf_counter()
+        while i < len(trace) or pending:
+            now = time.perf_counter() - t0
+            while i < len(trace) and trace[i]["t"] <= now:
+                r = trace[i]
+                tk = fr.backtest_submit(srv, n_envs=r["n_envs"], window=r["window"], start=r["start"],
+                                        bps_range=r["bps_range"], seed=r["seed"])
+                pending[tk] = r["t"]
+                i += 1
+            for tk in list(pending):
+                res = fr.backtest_poll(srv, tk)
+                if res is not None:
+                    lat.append(time.perf_counter() - t0 - pending.pop(tk))
+            if now > duration + drain_s:
+                break
+            time.sleep(0.0005)
+        wall = time.perf_counter() - t0
+        st = fr.fr_server_stats(srv)
+        srv.close()
+        lat = np.array(lat)
+        out[name] = {"p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
+                     "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None,
+                     "completed": int(lat.size), "unfinished": len(pending) + len(trace) - i,
+                     "served_env_steps_per_s": (st["env_steps"] - 8 * 19) / wall,
+                     "wall_s": wall}
+    return out
+
+
 def time_kernel(fn, iters, stream):
     import torch
     for _ in range(3):
@@ -274,6 +320,10 @@ def run_gpu(args):
     # 128 steps of the same envs, to bound the run time)
     crypto = crypto_line(fr, ctx, dev, flush, stream) if not args.no_crypto else None
 
+    # serving (backtest_submit / backtest_poll): p50 / p99 request latency
+    serving = serving_line(fr, ctx, mk, {"fused_bf16": ens_bf16, "plain_fp32": ens_fp32}) \
+        if not args.no_serving else None
+
     # end to end through the public API with host buffers
     snap = fr.env_snapshot(env)
     host_met = torch.empty(N, 3, dtype=torch.float64, pin_memory=True)
@@ -289,7 +339,9 @@ def run_gpu(args):
             e2e_times.append(time.perf_counter() - t0)
     e2e_value = world * env_steps / statistics.mean(e2e_times)
 
-    launches_per_rollout = 5          # env_reset, indicator rows, Z table GEMM, fused rollout, metrics replay
+    # env_reset, fused rollout, metrics replay (the indicator table Z is built
+    # once per env and ensemble, before the timed region)
+    launches_per_rollout = 3
     line = {
         "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -310,7 +362,8 @@ def run_gpu(args):
                                "ms_per_rollout": 1e3 * statistics.mean(t_traj),
                                "traj_bytes_per_rollout": T * N * (env.D * 4 + 30 * 4 + 8 + 1)},
         "speedup_vs_plain": value / world / plain_value,
-        "latency": {"p50_ms": None, "p99_ms": None, "note": "serving loop not measured in this run"},
+        "latency": ({"p50_ms": serving["fused_bf16"]["p50_ms"], "p99_ms": serving["fused_bf16"]["p99_ms"],
+                     "serving": serving} if serving else None),
         "e2e": {"value": e2e_value, "unit": "env-steps/s",
                 "h2d_bytes_per_step": len(snap), "d2h_bytes_per_step": N * 3 * 8},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -420,6 +473,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-crypto", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-envs", type=int, default=32)
     args = ap.parse_args()

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -418,6 +419,7 @@ void env_destroy(fr_env *env)
     dev_free(env->ctx, env->block, env->bytes);
     dev_free(env->ctx, env->scratch, env->scratch_bytes);
     dev_free(env->ctx, env->slot_of_env, 4ull * env->v.N + 4ull * 32);
+    dev_free(env->ctx, env->zbuf, env->zbuf_bytes);
     for (int i = 0; i < 2; ++i)
         if (env->k_ev[i]) cudaEventDestroy(env->k_ev[i]);
     delete env;
@@ -598,8 +600,10 @@ int ensemble_create(fr_ctx *ctx, const fr_ensemble_desc *d, fr_ensemble **out)
              "ensemble_create: a vote needs at most 3 actions");
     int rc = use_device(ctx);
     if (rc) return rc;
+    static std::atomic<uint64_t> serials{0};
     fr_ensemble *e = new (std::nothrow) fr_ensemble();
     FR_CHECK(e, FR_ENOMEM, "ensemble_create: out of host memory");
+    e->serial = ++serials;
     e->ctx = ctx;
     e->M = d->n_agents;
     e->L = d->n_layers;

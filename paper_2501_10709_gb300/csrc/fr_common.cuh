@@ -107,6 +107,11 @@ struct fr_env {
     int32_t *slot_of_env;       // device [N] (+ slot_ke [32] after it)
     int32_t *slot_ke;
     int n_slots;
+    // the fused stock kernel's indicator rows and table Z, kept across
+    // rollouts while the ensemble (by serial) and the slot set are unchanged
+    void *zbuf;
+    uint64_t zbuf_bytes;
+    uint64_t z_serial;          // serial of the ensemble Z was built for; 0 = stale
     // optional events around the main rollout kernel
     cudaEvent_t k_ev[2];
     int k_timing;               // record on the next rollouts
@@ -162,6 +167,7 @@ struct fr_ensemble {
     float *weights;                      // device [M] combine weights
     float host_weights[fr::MAX_AGENTS];
     fr::TcImage *tc;                     // tensor-core images or NULL
+    uint64_t serial;                     // unique per created ensemble (cache key)
     uint64_t bytes;
 };
 

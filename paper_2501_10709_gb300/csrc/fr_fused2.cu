@@ -940,31 +940,46 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
         env->slot_ke = env->slot_of_env + v.N;
         FR_CUDA(cudaMemcpy(env->slot_of_env, slot.data(), 4ull * v.N, cudaMemcpyHostToDevice));
         FR_CUDA(cudaMemcpy(env->slot_ke, kes.data(), 4ull * kes.size(), cudaMemcpyHostToDevice));
+        env->z_serial = 0;
     }
     const int n_ctx = env->n_slots * v.n_days;
-    // scratch: value log, indicator rows, Z table
-    const uint64_t vlog_b = ((uint64_t)T * v.N * 8 + 255) & ~255ull;
+    // indicator rows X and table Z in their own buffer, rebuilt only when the
+    // ensemble or the env's asset-count slots change; the value log in the
+    // env's scratch
     const uint64_t x_b = ((uint64_t)n_ctx * NIND * 4 + 255) & ~255ull;
     const uint64_t z_b = (uint64_t)p.M * n_ctx * p.H1 * 4;
-    const uint64_t need = vlog_b + x_b + z_b;
-    if (env->scratch_bytes < need) {
+    if (env->zbuf_bytes < x_b + z_b) {
+        FR_CUDA(cudaStreamSynchronize(s));
+        dev_free(env->ctx, env->zbuf, env->zbuf_bytes);
+        env->zbuf = nullptr;
+        env->zbuf_bytes = 0;
+        int rc = dev_alloc(env->ctx, &env->zbuf, x_b + z_b);
+        if (rc) return rc;
+        env->zbuf_bytes = x_b + z_b;
+        env->z_serial = 0;
+    }
+    const uint64_t vlog_b = (uint64_t)T * v.N * 8;
+    if (env->scratch_bytes < vlog_b) {
         FR_CUDA(cudaStreamSynchronize(s));
         dev_free(env->ctx, env->scratch, env->scratch_bytes);
         env->scratch = nullptr;
         env->scratch_bytes = 0;
-        int rc = dev_alloc(env->ctx, &env->scratch, need);
+        int rc = dev_alloc(env->ctx, &env->scratch, vlog_b);
         if (rc) return rc;
-        env->scratch_bytes = need;
+        env->scratch_bytes = vlog_b;
     }
     int64_t *vlog = (int64_t *)env->scratch;
-    float *X = (float *)((char *)env->scratch + vlog_b);
-    float *Z = (float *)((char *)env->scratch + vlog_b + x_b);
-    // Z[j][ctx][n] = W1_j[n, indicators] . x[ctx] + b1_j[n]   (per rollout)
-    const int64_t nx = (int64_t)n_ctx * NIND;
-    k_ind_rows<<<ceil_div(nx, 256), 256, 0, s>>>(v.ind, v.n_days, env->slot_ke, env->n_slots, X);
-    FR_CUDA(cudaGetLastError());
-    FR_CUDA(launch_dense_f32(X, 0, NIND, im->wind, (int64_t)p.H1 * NIND + p.H1, 0, (int64_t)p.H1 * NIND, Z,
-                             (int64_t)n_ctx * p.H1, p.H1, n_ctx, NIND, p.H1, 2, p.M, s));
+    float *X = (float *)env->zbuf;
+    float *Z = (float *)((char *)env->zbuf + x_b);
+    if (env->z_serial != e->serial) {
+        // Z[j][ctx][n] = W1_j[n, indicators] . x[ctx] + b1_j[n]
+        const int64_t nx = (int64_t)n_ctx * NIND;
+        k_ind_rows<<<ceil_div(nx, 256), 256, 0, s>>>(v.ind, v.n_days, env->slot_ke, env->n_slots, X);
+        FR_CUDA(cudaGetLastError());
+        FR_CUDA(launch_dense_f32(X, 0, NIND, im->wind, (int64_t)p.H1 * NIND + p.H1, 0, (int64_t)p.H1 * NIND, Z,
+                                 (int64_t)n_ctx * p.H1, p.H1, n_ctx, NIND, p.H1, 2, p.M, s));
+        env->z_serial = e->serial;
+    }
 
     F2Args a;
     memset(&a, 0, sizeof(a));

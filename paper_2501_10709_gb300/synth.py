@@ -353,6 +353,27 @@ def poisson_arrivals(rate: float, duration: float, seed: int = MASTER_SEED) -> n
     return t[t < duration]
 
 
+def serving_trace_stock(rate: float, duration: float, n_days: int = 1000, max_envs: int = 512,
+                        max_window: int = 500, seed: int = MASTER_SEED) -> list:
+    """Stock backtest requests arriving as a Poisson process: per request
+    N ~ U{1..max_envs} envs, window W ~ U{5..max_window} days, a start day
+    uniform over the days with 60 warm-up days before, +-1% per-env price
+    perturbations (bps range 100) from a per-request seed."""
+    times = poisson_arrivals(rate, duration, seed)
+    st = Stream(seed, SUB_ARRIVALS + 1)
+    n = len(times)
+    nenv = st.integers(1, max_envs, n)
+    win = st.integers(5, max_window, n)
+    u = st.uniform(n)
+    seeds = st.u64(n)
+    out = []
+    for i in range(n):
+        lo, hi = 60, n_days - int(win[i])
+        out.append({"t": float(times[i]), "n_envs": int(nenv[i]), "window": int(win[i]),
+                    "start": int(lo + int(u[i] * (hi - lo + 1))), "bps_range": 100, "seed": int(seeds[i])})
+    return out
+
+
 # ----------------------------------------------------------------- workloads
 
 STOCK_DIMS_SMALL = (301, 64, 64, 30)
