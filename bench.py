@@ -216,6 +216,48 @@ def serving_line(fr, ctx, mk, ens_by_name, duration=10.0, rate=200.0, drain_s=60
     return out
 
 
+# Algorithmic DRAM bytes of one stock env-step through env_step with every
+# output: reads action f32[30] 120, per-env constants Ke/start/W 12 + bps
+# int16[32] 64, state cash 8 + hold int32[32] 128 + t 4 + done 1, FP64 / int64
+# accumulators 40 (377 B); writes state 181 (cash, hold line, t, done,
+# accumulators), reward i64 + f32 + done 13, observation f32[301] 1,204
+# (1,398 B).  The market rows are shared by a cohort of 128 envs (L2).
+ENV_STEP_BYTES = 377 + 1398
+
+
+def env_step_line(fr, ctx, mk, w, dev, stream, N=1 << 20, T=4, warm=2):
+    """The standalone stock env-step kernel with trajectory outputs at a size
+    whose state and outputs exceed L2 (HBM roofline probe)."""
+    import torch
+    from paper_2501_10709_gb300 import synth
+    e = synth.stock_envs_cohorts(N, 30, w.market.close.shape[0], T + warm + 2)
+    env = fr.env_create(ctx, mk, start=e.start, window=e.W, n_assets=e.Ke, bps=e.bps)
+    g = torch.Generator(device=dev)
+    g.manual_seed(250110709 + 4)
+    act = torch.rand(N, 30, device=dev, generator=g) * 2 - 1
+    rew = torch.empty(N, dtype=torch.int64, device=dev)
+    rew32 = torch.empty(N, device=dev)
+    done = torch.empty(N, dtype=torch.uint8, device=dev)
+    obs = torch.empty(N, env.D, device=dev)
+    for _ in range(warm):
+        fr.env_step(env, act, fr.ACT_F32_UNIT, rew=rew, rew_f32=rew32, done=done, obs=obs)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(T):
+        fr.env_step(env, act, fr.ACT_F32_UNIT, rew=rew, rew_f32=rew32, done=done, obs=obs)
+    b.record(stream)
+    b.synchronize()
+    dt = a.elapsed_time(b) / 1e3 / T
+    achieved = N * ENV_STEP_BYTES / dt / 1e9
+    del obs, act
+    env.close()
+    return {"kernel": f"k_stock_step<f32 actions> with observation out, {N} envs, {T} timed steps",
+            "bytes_per_env_step": ENV_STEP_BYTES, "us_per_step": dt * 1e6, "achieved": achieved,
+            "unit": "GB/s"}
+
+
 def time_kernel(fn, iters, stream):
     import torch
     for _ in range(3):
@@ -320,6 +362,12 @@ def run_gpu(args):
     # 128 steps of the same envs, to bound the run time)
     crypto = crypto_line(fr, ctx, dev, flush, stream) if not args.no_crypto else None
 
+    # HBM roofline of the standalone env step (state + trajectory > L2)
+    env_step = env_step_line(fr, ctx, mk, w, dev, stream)
+    env_step["peak"] = peaks["hbm_gbs"]
+    env_step["frac"] = env_step["achieved"] / peaks["hbm_gbs"]
+    env_step["peak_source"] = f"hbm_gbs, {peak_src}"
+
     # serving (backtest_submit / backtest_poll): p50 / p99 request latency
     serving = serving_line(fr, ctx, mk, {"fused_bf16": ens_bf16, "plain_fp32": ens_fp32}) \
         if not args.no_serving else None
@@ -376,7 +424,8 @@ def run_gpu(args):
                      "actor_kernel": {"rows": N, "tflops": flops_per_launch / a_dt / 1e12,
                                       "us_per_launch": a_dt * 1e6},
                      "actor_kernel_large_batch": {"rows": nb, "achieved": big_tflops,
-                                                  "frac": big_tflops / peak}},
+                                                  "frac": big_tflops / peak},
+                     "env_step_kernel": env_step},
         "crypto_c3": crypto,
         "gpu_launches": launches_per_rollout * args.steps,
         "clocks": clk,
@@ -442,7 +491,17 @@ def run_profile(args):
     prec = fr.PREC_FP32 if args.profile == "plain" else fr.PREC_BF16
     ens = fr.ensemble_create(ctx, w.dims, w.params, precision=prec)
     dev = torch.device("cuda:0")
-    if args.profile == "actor":
+    if args.profile == "envstep":
+        from paper_2501_10709_gb300 import synth
+        N = args.rows
+        es = synth.stock_envs_cohorts(N, 30, w.market.close.shape[0], 8)
+        env2 = fr.env_create(ctx, mk, start=es.start, window=es.W, n_assets=es.Ke, bps=es.bps)
+        act = torch.rand(N, 30, device=dev) * 2 - 1
+        outs = dict(rew=torch.empty(N, dtype=torch.int64, device=dev), rew_f32=torch.empty(N, device=dev),
+                    done=torch.empty(N, dtype=torch.uint8, device=dev), obs=torch.empty(N, env2.D, device=dev))
+        for _ in range(3):
+            fr.env_step(env2, act, fr.ACT_F32_UNIT, **outs)
+    elif args.profile == "actor":
         obs = torch.empty(args.rows, env.D, device=dev)
         fr.env_observe(env, obs[:e.N])
         obs[e.N:] = obs[:e.N].repeat(args.rows // e.N, 1)[: args.rows - e.N]
@@ -463,7 +522,7 @@ def run_profile(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile", choices=["fused", "unfused", "plain", "actor"], default=None,
+    ap.add_argument("--profile", choices=["fused", "unfused", "plain", "actor", "envstep"], default=None,
                     help="run a small case of one path for a profiler, then exit")
     ap.add_argument("--T", type=int, default=16)
     ap.add_argument("--rows", type=int, default=2048)

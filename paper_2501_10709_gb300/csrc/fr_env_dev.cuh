@@ -70,6 +70,22 @@ __device__ __forceinline__ int64_t warp_sum(int64_t x)
     return x;
 }
 
+// Exact int64 warp sum (mod 2^64, like the serial sum) from three 32-bit
+// hardware reductions: x = hi 2^42 + mid 2^21 + lo with lo, mid in [0, 2^21)
+// and hi in [-2^21, 2^21), so none of the 32-lane partial sums overflows.
+// The three reductions are independent, unlike the five dependent shuffle
+// rounds of a butterfly sum.
+__device__ __forceinline__ int64_t warp_sum_redux(int64_t x)
+{
+    const unsigned lo = (unsigned)x & 0x1fffffu;
+    const unsigned mid = (unsigned)(x >> 21) & 0x1fffffu;
+    const int hi = (int)(x >> 42);
+    const unsigned slo = __reduce_add_sync(FULL_MASK, lo);
+    const unsigned smid = __reduce_add_sync(FULL_MASK, mid);
+    const int shi = __reduce_add_sync(FULL_MASK, hi);
+    return (int64_t)(((uint64_t)(int64_t)shi << 42) + ((uint64_t)smid << 21) + (uint64_t)slo);
+}
+
 __device__ __forceinline__ int64_t warp_incl_scan(int64_t x, int lane)
 {
 #pragma unroll
@@ -171,87 +187,15 @@ __device__ __forceinline__ void finish_step(const EnvView &v, int e, int64_t cas
 }
 
 // ------------------------------------------------------------ stock, warp
-// One step of stock env e by one warp, lane = asset.  q is this lane's
-// share order.  Returns the reward (same on every lane) and the done flag.
-__device__ __forceinline__ int64_t stock_step_warp(const EnvView &v, int e, int lane,
-                                                   int32_t q, bool &done_out)
-{
-    if (v.done[e]) {
-        done_out = true;
-        return 0;
-    }
-    const int K = v.K;
-    const int Ke = v.Ke[e];
-    const int t0 = v.t[e];
-    const int d = v.start[e] + t0;
-    const bool act = lane < Ke;
-    const int fee = v.fee_bps;
-    const int bps = act ? (int)v.bps[(int64_t)e * KP + lane] : 0;
-    const int64_t p = act ? perturb(__ldg(v.close + (int64_t)d * K + lane), bps) : 0;
-    int64_t h = act ? (int64_t)v.hold[(int64_t)e * KP + lane] : 0;
-    int64_t cash = v.cash[e];
-    if (!act) q = 0;
-    const int64_t v0 = cash + warp_sum(p * h);
-
-    // sells: independent per asset, capped at the holding
-    int64_t net = 0;
-    if (q < 0) {
-        int64_t n = -(int64_t)q;
-        if (n > h) n = h;
-        const int64_t g = n * p;
-        h -= n;
-        net = g - fee_of(g, fee);
-    }
-    cash += warp_sum(net);
-
-    // buys: greedy in ascending asset order.  Each round drops the assets
-    // that cannot afford one share, fills every order in full up to the
-    // first one whose prefix cost exceeds the cash, fills that one as far as
-    // the remaining cash allows, and continues after it.
-    const int64_t want = q > 0 ? (int64_t)q : 0;
-    int64_t full = 0, one = 0, nb = 0;
-    if (want > 0) {
-        full = cost_of(want, p, fee);
-        one = cost_of(1, p, fee);
-    }
-    unsigned pending = __ballot_sync(FULL_MASK, want > 0);
-#pragma unroll 1
-    while (pending) {
-        bool mine = (pending >> lane) & 1u;
-        pending &= ~__ballot_sync(FULL_MASK, mine && one > cash);
-        if (!pending) break;
-        mine = (pending >> lane) & 1u;
-        const int64_t x = mine ? full : 0;
-        const int64_t pre = warp_incl_scan(x, lane);
-        const unsigned fail = __ballot_sync(FULL_MASK, mine && pre > cash);
-        if (fail == 0u) {
-            if (mine) nb = want;
-            cash -= __shfl_sync(FULL_MASK, pre, 31);
-            break;
-        }
-        const int f = __ffs(fail) - 1;
-        if (mine && lane < f) nb = want;
-        int64_t cf = cash - (pre - x);
-        if (lane == f) {
-            const int64_t n = afford(cf, p, fee);
-            nb = n;
-            cf -= cost_of(n, p, fee);
-        }
-        cash = __shfl_sync(FULL_MASK, cf, f);
-        pending &= ~((2u << f) - 1u);
-    }
-    h += nb;
-
-    // next day: value at the new prices, reward
-    const int t1 = t0 + 1;
-    const int64_t p1 = act ? perturb(__ldg(v.close + (int64_t)(d + 1) * K + lane), bps) : 0;
-    const int64_t v1 = cash + warp_sum(p1 * h);
-    const bool done = t1 == v.W[e] - 1;
-    if (act) v.hold[(int64_t)e * KP + lane] = (done && v.auto_reset) ? 0 : (int32_t)h;
-    if (lane == 0) finish_step(v, e, cash, t1, done, v0, v1);
-    done_out = done;
-    return v1 - v0;
-}
+// The episode bookkeeping a stock step leaves for finish_step: deferred so
+// that one thread per env can run the FP64 updates of many envs in one warp
+// instruction (the FP64 pipe is narrow on this GPU).
+struct StepFin {
+    int64_t cash, v0, v1;
+    int t1;
+    int done;
+    int valid;                  // 0: the env was already done, nothing to finish
+};
 
 // Observation of stock env e's current state into o[0..D), lane = asset:
 // [cash*1e-8, p_k*1e-4, h_k*1e-2, f_{i,k} indicator-major], zero beyond Ke.

@@ -9,6 +9,7 @@ namespace fr {
 namespace {
 
 constexpr int kBlock = 256;
+constexpr int kStepEnvs = 32;           // envs (warps) per block of the stock step kernel
 
 __global__ void k_env_reset(EnvView v)
 {
@@ -32,34 +33,161 @@ __global__ void k_env_reset(EnvView v)
     }
 }
 
+// One warp per env (lane = asset): every independent load is issued first,
+// then sells (capped at the holding), greedy buys in ascending asset order
+// (one sum settles them when every order fits; otherwise rounds that drop
+// the assets that cannot afford one share, fill every order in full up to the
+// first whose prefix cost exceeds the cash, fill that one as far as the cash
+// allows and continue after it), the value at the next day's prices and the
+// next observation from registers.  The FP64 episode bookkeeping is deferred:
+// the last warp of the block to finish runs it for all 32 envs of the block,
+// one thread per env, so that one instruction of the narrow FP64 pipe serves
+// 32 envs and no warp waits at a block barrier.
 template <int KIND>
-__global__ void __launch_bounds__(kBlock) k_stock_step(EnvView v, const void *act, int64_t *rew,
-                                                        float *rew_f32, uint8_t *done_out,
-                                                        float *obs, int ld)
+__global__ void __launch_bounds__(kStepEnvs * 32) k_stock_step(EnvView v, const void *act, int64_t *rew,
+                                                                float *rew_f32, uint8_t *done_out,
+                                                                float *obs, int ld)
 {
-    const int e = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (e >= v.N) return;                     // uniform per warp
-    int32_t q = 0;
-    if (lane < v.Ke[e]) {
-        if (KIND == FR_ACT_I32_SHARES) {
-            q = ((const int32_t *)act)[(int64_t)e * v.K + lane];
-        } else {
-            bool bad;
-            q = discretise(((const float *)act)[(int64_t)e * v.K + lane], v.hmax, bad);
-            if (bad) atomicAdd(v.err, 1ull);
+    static_assert(kStepEnvs == 32, "one lane per env of the block in the bookkeeping warp");
+    __shared__ StepFin fin_sm[kStepEnvs];
+    __shared__ unsigned arrived;
+    if (threadIdx.x == 0) arrived = 0u;
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int e = blockIdx.x * kStepEnvs + w;
+    const int K = v.K;
+    StepFin fin;
+    fin.valid = 0;
+    if (e < v.N) {                                       // uniform per warp
+        const bool was_done = v.done[e] != 0;
+        const int Ke = v.Ke[e], t0 = v.t[e], start = v.start[e], W = v.W[e];
+        const int64_t cash0 = v.cash[e];
+        const bool live = lane < Ke;
+        const int bps = lane < K ? (int)v.bps[(int64_t)e * KP + lane] : 0;
+        int64_t h = live ? (int64_t)v.hold[(int64_t)e * KP + lane] : 0;
+        int32_t q = 0;
+        if (live) {
+            if (KIND == FR_ACT_I32_SHARES) {
+                q = ((const int32_t *)act)[(int64_t)e * K + lane];
+            } else {
+                bool bad;
+                q = discretise(((const float *)act)[(int64_t)e * K + lane], v.hmax, bad);
+                if (bad) atomicAdd(v.err, 1ull);
+            }
         }
+        const int d = start + t0;
+        const int64_t c0 = live ? __ldg(v.close + (int64_t)d * K + lane) : 0;
+        const int64_t c1 = (live && !was_done) ? __ldg(v.close + (int64_t)(d + 1) * K + lane) : 0;
+        int64_t cash = cash0, r = 0;
+        int t_obs = t0;
+        bool dn = true;
+        int64_t p_obs = live ? perturb(c0, bps) : 0;
+        if (!was_done) {
+            const int fee = v.fee_bps;
+            const int64_t p = p_obs;
+            const int64_t v0 = cash + warp_sum_redux(p * h);
+            int64_t net = 0;
+            if (q < 0) {
+                int64_t n = -(int64_t)q;
+                if (n > h) n = h;
+                const int64_t g = n * p;
+                h -= n;
+                net = g - fee_of(g, fee);
+            }
+            cash += warp_sum_redux(net);
+            const int64_t want = q > 0 ? (int64_t)q : 0;
+            int64_t full = 0, one = 0, nb = 0;
+            if (want > 0) {
+                full = cost_of(want, p, fee);
+                one = cost_of(1, p, fee);
+            }
+            unsigned pending = __ballot_sync(FULL_MASK, want > 0);
+            const int64_t all = warp_sum_redux(full);
+            if (all <= cash) {
+                nb = want;
+                cash -= all;
+                pending = 0u;
+            }
+#pragma unroll 1
+            while (pending) {
+                bool mine = (pending >> lane) & 1u;
+                pending &= ~__ballot_sync(FULL_MASK, mine && one > cash);
+                if (!pending) break;
+                mine = (pending >> lane) & 1u;
+                const int64_t x = mine ? full : 0;
+                const int64_t pre = warp_incl_scan(x, lane);
+                const unsigned fail = __ballot_sync(FULL_MASK, mine && pre > cash);
+                if (fail == 0u) {
+                    if (mine) nb = want;
+                    cash -= __shfl_sync(FULL_MASK, pre, 31);
+                    break;
+                }
+                const int f = __ffs(fail) - 1;
+                if (mine && lane < f) nb = want;
+                int64_t cf = cash - (pre - x);
+                if (lane == f) {
+                    const int64_t n = afford(cf, p, fee);
+                    nb = n;
+                    cf -= cost_of(n, p, fee);
+                }
+                cash = __shfl_sync(FULL_MASK, cf, f);
+                pending &= ~((2u << f) - 1u);
+            }
+            h += nb;
+            const int t1 = t0 + 1;
+            const int64_t p1 = live ? perturb(c1, bps) : 0;
+            const int64_t v1 = cash + warp_sum_redux(p1 * h);
+            dn = t1 == W - 1;
+            r = v1 - v0;
+            fin.cash = cash;
+            fin.v0 = v0;
+            fin.v1 = v1;
+            fin.t1 = t1;
+            fin.done = dn ? 1 : 0;
+            fin.valid = 1;
+            const bool reset = dn && v.auto_reset;
+            if (live) v.hold[(int64_t)e * KP + lane] = reset ? 0 : (int32_t)h;
+            if (reset) {
+                cash = v.init_cash;
+                t_obs = 0;
+                h = 0;
+                p_obs = live ? perturb(__ldg(v.close + (int64_t)start * K + lane), bps) : 0;
+            } else {
+                t_obs = t1;
+                p_obs = p1;
+            }
+        }
+        if (lane == 0) {
+            if (rew) rew[e] = r;
+            if (rew_f32) rew_f32[e] = reward_f32(r);
+            if (done_out) done_out[e] = dn ? 1 : 0;
+            fin_sm[w] = fin;
+        }
+        if (obs) {
+            // [cash*1e-8, p_k*1e-4, h_k*1e-2, f_{i,k} indicator-major], zero beyond Ke
+            float *o = obs + (int64_t)e * ld;
+            if (lane == 0) o[0] = obs_scale(cash, 1e-8f);
+            if (lane < K) {
+                o[1 + lane] = live ? obs_scale(p_obs, 1e-4f) : 0.0f;
+                o[1 + K + lane] = live ? obs_scale(h, 1e-2f) : 0.0f;
+                const float *f = v.ind + (int64_t)(start + t_obs) * v.I * K;
+                for (int i = 0; i < v.I; ++i) o[1 + 2 * K + i * K + lane] = live ? __ldg(f + i * K + lane) : 0.0f;
+            }
+        }
+    } else if (lane == 0) {
+        fin_sm[w].valid = 0;
     }
-    bool done;
-    const int64_t r = stock_step_warp(v, e, lane, q, done);
+    __syncwarp();
+    unsigned last = 0;
     if (lane == 0) {
-        if (rew) rew[e] = r;
-        if (rew_f32) rew_f32[e] = reward_f32(r);
-        if (done_out) done_out[e] = done ? 1 : 0;
+        __threadfence_block();
+        last = atomicAdd(&arrived, 1u) == (unsigned)(kStepEnvs - 1) ? 1u : 0u;
     }
-    if (obs) {
-        __syncwarp();
-        stock_obs_warp(v, e, lane, obs + (int64_t)e * ld);
+    last = __shfl_sync(FULL_MASK, last, 0);
+    if (last) {
+        __threadfence_block();
+        const StepFin f = fin_sm[lane];
+        if (f.valid) finish_step(v, blockIdx.x * kStepEnvs + lane, f.cash, f.t1, f.done != 0, f.v0, f.v1);
     }
 }
 
@@ -141,11 +269,11 @@ cudaError_t launch_env_step(const EnvView &v, int kind, const void *act, int64_t
                             float *rew_f32, uint8_t *done, float *obs, int ld, cudaStream_t s)
 {
     if (v.task == FR_TASK_STOCK) {
-        const unsigned grid = ceil_div((int64_t)v.N * 32, kBlock);
+        const unsigned grid = ceil_div(v.N, kStepEnvs);
         if (kind == FR_ACT_I32_SHARES)
-            k_stock_step<FR_ACT_I32_SHARES><<<grid, kBlock, 0, s>>>(v, act, rew, rew_f32, done, obs, ld);
+            k_stock_step<FR_ACT_I32_SHARES><<<grid, kStepEnvs * 32, 0, s>>>(v, act, rew, rew_f32, done, obs, ld);
         else
-            k_stock_step<FR_ACT_F32_UNIT><<<grid, kBlock, 0, s>>>(v, act, rew, rew_f32, done, obs, ld);
+            k_stock_step<FR_ACT_F32_UNIT><<<grid, kStepEnvs * 32, 0, s>>>(v, act, rew, rew_f32, done, obs, ld);
     } else {
         k_crypto_step<<<ceil_div(v.N, kBlock), kBlock, 0, s>>>(v, (const uint8_t *)act, rew, rew_f32,
                                                                done, obs, ld);

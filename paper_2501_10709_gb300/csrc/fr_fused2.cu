@@ -214,22 +214,6 @@ struct OwnEnv {
     int bps;             // this lane's perturbation
 };
 
-// Exact int64 warp sum (mod 2^64, like the serial sum) from three 32-bit
-// hardware reductions: x = hi 2^42 + mid 2^21 + lo with lo, mid in [0, 2^21)
-// and hi in [-2^21, 2^21), so none of the 32-lane partial sums overflows.
-// The three reductions are independent, unlike the five dependent shuffle
-// rounds of a butterfly sum.
-__device__ __forceinline__ int64_t warp_sum_redux(int64_t x)
-{
-    const unsigned lo = (unsigned)x & 0x1fffffu;
-    const unsigned mid = (unsigned)(x >> 21) & 0x1fffffu;
-    const int hi = (int)(x >> 42);
-    const unsigned slo = __reduce_add_sync(FULL_MASK, lo);
-    const unsigned smid = __reduce_add_sync(FULL_MASK, mid);
-    const int shi = __reduce_add_sync(FULL_MASK, hi);
-    return (int64_t)(((uint64_t)(int64_t)shi << 42) + ((uint64_t)smid << 21) + (uint64_t)slo);
-}
-
 // Greedy buys in ascending asset order with partial fills, for the case
 // where the orders do not all fit in `cash`: lanes whose single share no
 // longer fits drop out; a scan finds the first order that does not fit,
