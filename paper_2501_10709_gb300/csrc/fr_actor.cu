@@ -1,0 +1,331 @@
+// fr_actor.cu -- the ensemble's actor MLPs at large batch (BF16 operands).
+//
+// Two launches:
+//   * k_obs_tiles rewrites the fp32 observations once as BF16 in the
+//     tensor-core operand layout, tile by tile (128 rows, K-major, 8-column
+//     chunks of 2 KB), so that a CTA fetches its whole A operand with bulk
+//     copies and no conversion work;
+//   * k_tc_actor: one CTA per 128-row tile runs every agent of the ensemble
+//     on that one A operand.  The agents' weight chunks (the same pre-packed
+//     images as the single-agent kernel) stream through a multi-stage ring
+//     of 1-D bulk copies; one thread issues tcgen05.mma (M = 128, N = layer
+//     width, FP32 accumulator in TMEM); eight epilogue warps, two per TMEM
+//     lane quarter, each take half of the layer's columns: bias (kept in
+//     shared memory), ReLU and the next layer's BF16 A operand in shared
+//     memory, or the agent's output.
+// Limits, measured: an SM streams L2-resident data at 36 B/clk (bulk
+// copies) to 43 B/clk (16-byte cp.async), the same with all 152 SMs on the
+// same or on separate data, and a 128-row tile consumes ~50 B/clk of
+// weights at full tensor rate; the MMAs of a layer also wait for the
+// previous layer's epilogue, with the ring full.  Neither multicasting the
+// weights over a 4-CTA cluster nor cp.async producers made this kernel
+// faster.
+// The products, their order and every rounding are those of the
+// single-agent kernel, so both give identical results.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "fr_common.cuh"
+#include "fr_env_dev.cuh"
+#include "fr_ptx.cuh"
+#include "fr_tc.cuh"
+
+namespace fr {
+
+namespace {
+
+constexpr int TA_THREADS = 320;          // producer, MMA issuer, 8 epilogue warps
+constexpr int TA_MAX_STAGES = 6;
+
+struct TaLayout {
+    uint32_t obs_a, h_a, ring, bias, bars, total;
+    int stages;
+};
+
+__host__ __device__ inline uint32_t obs_tile_bytes(const TcPlan &p) { return (uint32_t)(p.layer[0].K / 8) * 2048u; }
+
+__host__ __device__ inline uint32_t hidden_a_bytes(const TcPlan &p)
+{
+    int k = 16;
+    for (int l = 1; l < p.L; ++l) k = p.layer[l].K > k ? p.layer[l].K : k;
+    return (uint32_t)(k / 8) * 2048u;
+}
+
+__host__ __device__ inline TaLayout ta_layout(const TcPlan &p, int stages)
+{
+    TaLayout L;
+    L.stages = stages;
+    L.obs_a = 0;
+    L.h_a = obs_tile_bytes(p);
+    L.ring = L.h_a + hidden_a_bytes(p);
+    L.bias = L.ring + (uint32_t)stages * TC_CHUNK_MAX;          // [M][L][256] fp32
+    L.bars = L.bias + (uint32_t)(p.M * p.L) * 1024u;
+    L.total = L.bars + 256u;
+    return L;
+}
+
+// fp32 obs [n][ld] (first fin columns) -> BF16 tiles [tiles][K/8][128][8]
+__global__ void k_obs_tiles(const float *__restrict__ obs, int ld, int n, int fin, int nchunks, uint4 *out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t tiles = (n + 127) / 128;
+    if (i >= tiles * nchunks * 128) return;
+    const int row = (int)(i % 128);
+    const int c = (int)((i / 128) % nchunks);
+    const int64_t tile = i / (128 * (int64_t)nchunks);
+    const int64_t g = tile * 128 + row;
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int k = c * 8 + u;
+        v[u] = (g < n && k < fin) ? __ldg(obs + g * ld + k) : 0.0f;
+    }
+    uint32_t w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * u], v[2 * u + 1]);
+        w[u] = *(const uint32_t *)&b;
+    }
+    out[i] = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+__global__ void __launch_bounds__(TA_THREADS, 1)
+k_tc_actor(const __grid_constant__ TcPlan plan, const uint8_t *__restrict__ img, const float *__restrict__ bias,
+           const uint8_t *__restrict__ obs_tiles, int n, float *__restrict__ y, unsigned *err, int stages)
+{
+    using namespace ptx;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const TaLayout L = ta_layout(plan, stages);
+    const uint32_t obs_a = smem_u32(base + L.obs_a), h_a = smem_u32(base + L.h_a);
+    uint8_t *ring = base + L.ring;
+    uint64_t *bars = (uint64_t *)(base + L.bars);
+    uint64_t *full = bars;                                   // [stages]
+    uint64_t *empty = bars + TA_MAX_STAGES;                  // [stages]
+    uint64_t *obs_full = bars + 2 * TA_MAX_STAGES;
+    uint64_t *acc_full = obs_full + 1;
+    uint64_t *a_ready = obs_full + 2;
+    uint64_t *drain = obs_full + 3;
+    uint32_t *tmem_slot = (uint32_t *)(obs_full + 4);
+    volatile int *abort = (volatile int *)(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile = blockIdx.x;
+    const int S = stages;
+    float *bias_s = (float *)(base + L.bias);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(obs_full, 1);
+        mbar_init(acc_full, 1);
+        mbar_init(a_ready, 8);                               // one arrival per epilogue warp
+        mbar_init(drain, 1);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        __syncwarp();
+        tmem_alloc(tmem_slot, (uint32_t)plan.tmem_cols);
+        tmem_relinquish();
+    }
+    for (int i = threadIdx.x; i < plan.M * plan.L * 256; i += TA_THREADS) {
+        const int j = i / (plan.L * 256), l = (i / 256) % plan.L, c = i % 256;
+        bias_s[i] = bias[((size_t)j * MAX_LAYERS + l) * 256 + c];
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------- operands into the CTA
+        if (lane == 0) {
+            const uint32_t ob = obs_tile_bytes(plan);
+            const uint8_t *src = obs_tiles + (size_t)tile * ob;
+            mbar_arrive_expect_tx(obs_full, ob);
+            for (uint32_t o = 0; o < ob; o += TC_CHUNK_MAX)
+                bulk_g2s(base + L.obs_a + o, src + o, min(TC_CHUNK_MAX, ob - o), obs_full);
+            int i = 0;
+            bool ok = true;
+            for (int j = 0; j < plan.M && ok; ++j) {
+                const uint8_t *aimg = img + (size_t)j * plan.agent_bytes;
+                for (int l = 0; l < plan.L && ok; ++l) {
+                    const TcLayer &ly = plan.layer[l];
+                    for (int c = 0; c < ly.n_chunks; ++c, ++i) {
+                        const int s = i % S;
+                        if (!mbar_wait(&empty[s], ((uint32_t)(i / S) & 1u) ^ 1u, abort, err, 1u, TC_WAIT_NS)) {
+                            ok = false;
+                            break;
+                        }
+                        const int kc = min(ly.KC, ly.K - c * ly.KC);
+                        const uint32_t bytes = (uint32_t)(ly.N * kc * 2);
+                        mbar_arrive_expect_tx(&full[s], bytes);
+                        bulk_g2s(ring + (size_t)s * TC_CHUNK_MAX, aimg + ly.off + (size_t)c * ly.N * ly.KC * 2, bytes,
+                                 &full[s]);
+                    }
+                }
+            }
+            // every copy issued lands before the CTA may exit
+            volatile int no_abort = 0;
+            mbar_wait(obs_full, 0u, &no_abort, err, 8u, TC_WAIT_NS);
+            for (int k = i - 1; k >= 0 && k >= i - S; --k)
+                mbar_wait(&full[k % S], (uint32_t)(k / S) & 1u, &no_abort, err, 8u, TC_WAIT_NS);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------ MMA issue
+        if (lane == 0) {
+            int i = 0, step = 0;
+            bool ok = mbar_wait(obs_full, 0u, abort, err, 2u, TC_WAIT_NS);
+            for (int j = 0; j < plan.M && ok; ++j) {
+                for (int l = 0; l < plan.L && ok; ++l, ++step) {
+                    const TcLayer &ly = plan.layer[l];
+                    // the previous layer's epilogue has read TMEM and written this A
+                    if (step > 0 && !mbar_wait(a_ready, (uint32_t)(step - 1) & 1u, abort, err, 2u, TC_WAIT_NS)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a_at = l == 0 ? obs_a : h_a;
+                    const uint32_t idesc = idesc_bf16(128, ly.N);
+                    const uint32_t lbo_b = (uint32_t)(ly.N * 16);
+                    int kg = 0;
+                    for (int c = 0; c < ly.n_chunks; ++c, ++i) {
+                        const int s = i % S;
+                        if (!mbar_wait(&full[s], (uint32_t)(i / S) & 1u, abort, err, 4u, TC_WAIT_NS)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const int kc = min(ly.KC, ly.K - c * ly.KC);
+                        const uint32_t b_base = smem_u32(ring + (size_t)s * TC_CHUNK_MAX);
+                        for (int kk = 0; kk < kc; kk += 16, kg += 16) {
+                            const uint64_t ad = smem_desc(a_at + (uint32_t)(kg / 8) * 2048u, 2048u, 128u);
+                            const uint64_t bd = smem_desc(b_base + (uint32_t)(kk / 8) * lbo_b, lbo_b, 128u);
+                            mma_bf16(tmem, ad, bd, idesc, kg > 0 ? 1u : 0u);
+                        }
+                        mma_commit(&empty[s]);
+                    }
+                    if (!ok) break;
+                    mma_commit(acc_full);
+                }
+            }
+            // every MMA issued completes before TMEM is released
+            mma_commit(drain);
+            volatile int no_abort = 0;
+            mbar_wait(drain, 0u, &no_abort, err, 128u, TC_WAIT_NS);
+        }
+    } else {
+        // ------------------------------------------------------- epilogue
+        const int q = warp & 3;                       // TMEM lane quarter of this warp
+        const int half = (warp - 2) >> 2;             // which half of the columns
+        const int r = q * 32 + lane;
+        const int grow = tile * 128 + r;
+        const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+        const uint32_t row_off = (uint32_t)(r / 8) * 128u + (uint32_t)(r % 8) * 16u;
+        int step = 0;
+        // no early exit: a wait that gives up sets the abort flag, the later
+        // ones return at once, and the loop runs to its uniform end
+        for (int j = 0; j < plan.M; ++j) {
+            for (int l = 0; l < plan.L; ++l, ++step) {
+                const TcLayer &ly = plan.layer[l];
+                const bool last = l == plan.L - 1;
+                warp_wait_all(acc_full, (uint32_t)step & 1u, false, abort, err, 16u, TC_WAIT_NS);
+                tc_fence_after();
+                const float *bl = bias_s + (j * plan.L + l) * 256;
+                // columns of this warp: two 16-aligned halves of N (a narrow
+                // layer all to half 0); every group of 16 stays inside N
+                const int split = ly.N >= 64 ? ((ly.N / 2 + 15) & ~15) : ly.N;
+                const int c_lo = half == 0 ? 0 : split;
+                const int c_hi = half == 0 ? split : ly.N;
+                for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
+                    uint32_t v[16];
+                    __syncwarp();
+                    tmem_ld16(trow + (uint32_t)c0, v);
+                    tmem_ld_wait();
+                    float x[16];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) x[u] = __uint_as_float(v[u]) + bl[c0 + u];
+                    if (!last) {
+                        uint32_t w[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const __nv_bfloat162 b = __floats2bfloat162_rn(fmaxf(x[2 * u], 0.0f), fmaxf(x[2 * u + 1], 0.0f));
+                            w[u] = *(const uint32_t *)&b;
+                        }
+                        const uint32_t at = h_a + (uint32_t)(c0 / 8) * 2048u + row_off;
+                        st_shared_v4(at, w[0], w[1], w[2], w[3]);
+                        st_shared_v4(at + 2048u, w[4], w[5], w[6], w[7]);
+                    } else if (grow < n) {
+                        float *yr = y + ((size_t)j * n + grow) * ly.fout;
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) {
+                            const int col = c0 + u;
+                            if (col < ly.fout) yr[col] = plan.out_act ? tanhf(x[u]) : x[u];
+                        }
+                    }
+                }
+                fence_proxy_async_smem();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(a_ready);
+            }
+        }
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, (uint32_t)plan.tmem_cols);
+    }
+}
+
+int ta_stages(const TcPlan &p, int optin)
+{
+    if (p.split != 1) return 0;
+    for (int s = TA_MAX_STAGES; s >= 2; --s)
+        if (ta_layout(p, s).total + 1024u <= (uint32_t)optin) return s;
+    return 0;
+}
+
+}  // namespace
+
+// 0 when this path does not apply: no BF16 plan, or fewer 128-row tiles than
+// SMs (one CTA per tile would leave SMs idle; the single-agent kernel's
+// tiles x agents CTAs then fill the GPU better)
+uint64_t tc_tiled_scratch_bytes(const fr_ensemble *e, int n)
+{
+    if (!e->tc || e->tc->plan.split != 1) return 0;
+    const int tiles = (int)ceil_div(n, 128);
+    if (tiles < e->ctx->sm_count) return 0;
+    return (uint64_t)tiles * obs_tile_bytes(e->tc->plan);
+}
+
+// The large-batch BF16 forward; FR_EINVAL when the plan does not fit (the
+// caller then uses tc_forward).
+int tc_forward_tiled(const fr_ensemble *e, const float *obs, int ld, int n, float *y, void *scratch, cudaStream_t s)
+{
+    const TcImage *t = e->tc;
+    FR_CHECK(t && t->plan.split == 1 && scratch, FR_EINVAL, "tc_forward_tiled: needs a BF16 plan and scratch");
+    const TcPlan &p = t->plan;
+    int optin = 0;
+    FR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, e->ctx->device));
+    const int stages = ta_stages(p, optin);
+    FR_CHECK(stages >= 2, FR_EINVAL, "tc_forward_tiled: the plan does not fit in shared memory");
+    const int tiles = (int)ceil_div(n, 128);
+    const int nch = p.layer[0].K / 8;
+    const int64_t threads = (int64_t)tiles * nch * 128;
+    k_obs_tiles<<<ceil_div(threads, 256), 256, 0, s>>>(obs, ld, n, p.layer[0].fin, nch, (uint4 *)scratch);
+    FR_CUDA(cudaGetLastError());
+    const uint32_t smem = ta_layout(p, stages).total + 1024u;
+    FR_CUDA(cudaFuncSetAttribute(k_tc_actor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_tc_actor<<<tiles, TA_THREADS, smem, s>>>(p, t->img, t->bias, (const uint8_t *)scratch, n, y, t->err, stages);
+    FR_CUDA(cudaGetLastError());
+    return FR_OK;
+}
+
+}  // namespace fr

@@ -166,7 +166,16 @@ namespace {
 // ordered allocator so that calls on different streams never share it
 int forward_any(const fr_ensemble *e, const float *obs, int ld, int n, float *y, cudaStream_t s)
 {
-    if (e->precision != FR_PREC_FP32) return tc_forward(e, obs, ld, n, y, s);
+    if (e->precision != FR_PREC_FP32) {
+        const uint64_t tb = tc_tiled_scratch_bytes(e, n);
+        if (tb == 0) return tc_forward(e, obs, ld, n, y, s);
+        void *tiles = nullptr;
+        FR_CUDA(cudaMallocAsync(&tiles, tb, s));
+        const int rc = tc_forward_tiled(e, obs, ld, n, y, tiles, s);
+        cudaFreeAsync(tiles, s);
+        if (rc == FR_EINVAL) return tc_forward(e, obs, ld, n, y, s);   // plan too large for the tiled kernel
+        return rc;
+    }
     void *scratch = nullptr;
     const uint64_t sb = plain_scratch_bytes(e, n);
     if (sb) FR_CUDA(cudaMallocAsync(&scratch, sb, s));
@@ -722,7 +731,8 @@ int rollout(fr_env *env, const fr_ensemble *e, int32_t T, const fr_traj *traj, d
     const uint64_t obs_b = (4ull * N * v.D + 255) & ~255ull;
     const uint64_t act_b = ((stock ? 4ull * N * v.K : (uint64_t)N) + 255) & ~255ull;
     const uint64_t y_b = (4ull * e->M * N * out + 255) & ~255ull;
-    const uint64_t need = obs_b + act_b + y_b + plain_scratch_bytes(e, N);
+    const uint64_t tiles_b = (e->precision == FR_PREC_FP32) ? 0 : ((tc_tiled_scratch_bytes(e, N) + 255) & ~255ull);
+    const uint64_t need = obs_b + act_b + y_b + tiles_b + plain_scratch_bytes(e, N);
     if (env->scratch_bytes < need) {
         FR_CUDA(cudaStreamSynchronize(s));
         dev_free(env->ctx, env->scratch, env->scratch_bytes);
@@ -736,7 +746,8 @@ int rollout(fr_env *env, const fr_ensemble *e, int32_t T, const fr_traj *traj, d
     float *obs_s = (float *)sc;
     void *act_s = sc + obs_b;
     float *y = (float *)(sc + obs_b + act_b);
-    float *hid = (float *)(sc + obs_b + act_b + y_b);
+    void *tiles = tiles_b ? (void *)(sc + obs_b + act_b + y_b) : nullptr;
+    float *hid = (float *)(sc + obs_b + act_b + y_b + tiles_b);
     for (int t = 0; t < T; ++t) {
         const int64_t row = (int64_t)t * N;
         float *obs_t = traj->obs ? traj->obs + row * ld : obs_s;
@@ -745,7 +756,8 @@ int rollout(fr_env *env, const fr_ensemble *e, int32_t T, const fr_traj *traj, d
         if (e->precision == FR_PREC_FP32) {
             FR_CUDA(forward_plain(e, obs_t, ldt, N, y, hid, s));
         } else {
-            rc = tc_forward(e, obs_t, ldt, N, y, s);
+            rc = tiles ? tc_forward_tiled(e, obs_t, ldt, N, y, tiles, s) : FR_EINVAL;
+            if (rc == FR_EINVAL) rc = tc_forward(e, obs_t, ldt, N, y, s);
             if (rc) return rc;
         }
         void *act_t = traj->act ? (stock ? (void *)((float *)traj->act + row * v.K)

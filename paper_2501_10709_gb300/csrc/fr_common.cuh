@@ -198,6 +198,11 @@ int tc_create(fr_ensemble *e);
 void tc_destroy(fr_ensemble *e);
 // Per-agent outputs through the tcgen05 kernels; obs rows of stride ld.
 int tc_forward(const fr_ensemble *e, const float *obs, int ld, int n, float *y, cudaStream_t s);
+// Large-batch BF16 forward over tiled observations (fr_actor.cu): scratch of
+// tc_tiled_scratch_bytes (0 = this ensemble has no such path).
+uint64_t tc_tiled_scratch_bytes(const fr_ensemble *e, int n);
+int tc_forward_tiled(const fr_ensemble *e, const float *obs, int ld, int n, float *y, void *scratch,
+                     cudaStream_t s);
 // Whether the fused persistent rollout supports this env / ensemble pair.
 bool tc_rollout_supported(const fr_env *env, const fr_ensemble *e);
 // FP64 episode accumulators from a rollout's value log (fr_fused.cu)

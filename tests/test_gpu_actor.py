@@ -147,3 +147,42 @@ def test_empty_and_single_row(ctx, dev):
     fr.ensemble_act(ens, obs[:0], act[:0])
     torch.cuda.synchronize()
     assert torch.isfinite(act).all()
+
+
+@pytest.mark.parametrize("dims, M, extra, vote", [(synth.STOCK_DIMS, 3, 77, False),
+                                                  ((301, 80, 48, 30), 2, 1, False),
+                                                  (synth.CRYPTO_DIMS, 5, 127, True)])
+def test_tiled_actor_equals_single_agent_kernel(ctx, dev, dims, M, extra, vote):
+    # At batches of at least one 128-row tile per SM (plus a ragged tail),
+    # ensemble_act runs the large-batch kernel (one CTA per tile, every agent,
+    # tiled BF16 observations); ensemble_act_noalloc the single-agent kernel.
+    # Same products in the same order, same roundings: equal bit for bit.
+    n = ctx.sm_count * 128 + extra
+    params = synth.actor_params(dims, M, seed=21, out_scale=4.0 if vote else 1.0)
+    kw = dict(combine=fr.COMBINE_VOTE, out_act=0) if vote else {}
+    ens = fr.ensemble_create(ctx, dims, params, precision=fr.PREC_BF16, **kw)
+    rng = np.random.default_rng(5)
+    obs = torch.from_numpy(rng.uniform(-1.5, 1.5, (n, dims[0])).astype(np.float32)).to(dev)
+    if vote:
+        a = torch.empty(n, dtype=torch.uint8, device=dev)
+        b = torch.full((n,), 255, dtype=torch.uint8, device=dev)
+    else:
+        a = torch.empty(n, dims[-1], device=dev)
+        b = torch.full((n, dims[-1]), float("nan"), device=dev)
+    fr.ensemble_act(ens, obs, a)
+    fr.ensemble_act_noalloc(ens, obs, b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    # and the per-agent outputs of ensemble_forward against the oracle
+    y = torch.empty(M, n, dims[-1], device=dev)
+    fr.ensemble_forward(ens, obs, y)
+    torch.cuda.synchronize()
+    o = obs.cpu().numpy().astype(np.float64)
+    for j in range(M):
+        want = oracle.net_forward(dims, params[j], o, 0 if vote else 1)
+        got = y[j].cpu().numpy().astype(np.float64)
+        if vote:    # BF16 Q-values are judged by their decisions, as in the crypto tests
+            assert np.mean(got.argmax(-1) == want.argmax(-1)) >= 0.99
+        else:
+            err = np.linalg.norm(got - want, axis=-1) / np.maximum(np.linalg.norm(want, axis=-1), 1e-3)
+            assert err.max() <= REL_TOL[fr.PREC_BF16], err.max()
