@@ -258,6 +258,32 @@ def env_step_line(fr, ctx, mk, w, dev, stream, N=1 << 20, T=4, warm=2):
             "unit": "GB/s"}
 
 
+def uneven_line(fr, ctx, dev, flush, stream, reps=3):
+    """4,096 stock envs with asset counts 10-30 and windows 5-250 days, BF16
+    fused rollout over the longest window, tiles packed by window vs not."""
+    import torch
+    from paper_2501_10709_gb300 import synth
+    w = synth.workload_uneven()
+    e = w.envs
+    mk = fr.fr_market_create(ctx, w.market)
+    env = fr.env_create(ctx, mk, start=e.start, window=e.W, n_assets=e.Ke, bps=e.bps)
+    ens = fr.ensemble_create(ctx, w.dims, w.params, precision=fr.PREC_BF16)
+    met = torch.empty(e.N, 3, dtype=torch.float64, device=dev)
+    work = int((e.W - 1).sum())
+    res = {"workload": f"uneven stock {e.N} envs, assets 10-30, windows 5-250 days, T = {w.T}, "
+                       "3 x 301-256-256-30 BF16", "unit": "env-steps/s (sum of W - 1 per rollout)",
+           "env_steps_per_rollout": work}
+    for name, on in (("packed", True), ("unpacked", False)):
+        fr.env_set_tile_packing(env, on)
+        ts = time_rollouts(fr, env, ens, w.T, reps, 3, met, flush, stream)
+        res[name] = {"value": work * len(ts) / sum(ts), "ms_per_rollout": 1e3 * statistics.mean(ts)}
+    fr.env_set_tile_packing(env, True)
+    res["tile_efficiency_packed"] = fr.env_tile_packing_efficiency(env)
+    W = e.W.astype(float)
+    res["tile_efficiency_unpacked"] = float((W - 1).sum() / (128 * (W.max() - 1) * ((e.N + 127) // 128)))
+    return res
+
+
 def time_kernel(fn, iters, stream):
     import torch
     for _ in range(3):
@@ -361,6 +387,7 @@ def run_gpu(args):
     # (fused BF16 path for the full horizon; the plain FP32 path on the first
     # 128 steps of the same envs, to bound the run time)
     crypto = crypto_line(fr, ctx, dev, flush, stream) if not args.no_crypto else None
+    uneven = uneven_line(fr, ctx, dev, flush, stream)
 
     # HBM roofline of the standalone env step (state + trajectory > L2)
     env_step = env_step_line(fr, ctx, mk, w, dev, stream)
@@ -427,6 +454,7 @@ def run_gpu(args):
                                                   "frac": big_tflops / peak},
                      "env_step_kernel": env_step},
         "crypto_c3": crypto,
+        "uneven_c4": uneven,
         "gpu_launches": launches_per_rollout * args.steps,
         "clocks": clk,
     }

@@ -299,6 +299,17 @@ int rollout(fr_env *env, const fr_ensemble *ens, int32_t T,
  * at most 8 agents; other pairs always run unfused. */
 int env_set_rollout_path(fr_env *env, int32_t path);
 
+/* Tile packing of the fused stock rollout (no counterpart in the paper;
+ * default on).  When a rollout writes no trajectory, auto-reset is off and
+ * the windows differ, the fused kernel processes the envs sorted by window
+ * (longest first) in 128-env tiles and stops each tile after its longest
+ * window, so short windows do not hold tiles for the whole horizon.  Every
+ * env's results are unchanged.  env_tile_packing_efficiency reports, for the
+ * current packing, sum over envs of (W - 1) / sum over tiles of 128 x (the
+ * tile's longest W - 1) (1.0 when not packed). */
+int env_set_tile_packing(fr_env *env, int32_t on);
+int env_tile_packing_efficiency(const fr_env *env, float *eff);
+
 /* Kernel timing for roofline measurements (no counterpart in the paper).
  * With on != 0, every later rollout() of this env records two CUDA events
  * on its stream around the launch of its main rollout kernel only (the

@@ -21,7 +21,8 @@ __all__ = [
     "fr_ctx_create", "fr_market_create", "env_create", "env_reset", "env_step",
     "env_observe", "env_get_state", "env_metrics", "env_snapshot", "env_restore",
     "env_error_count", "env_dims", "ensemble_create", "ensemble_forward",
-    "ensemble_act", "ensemble_act_noalloc", "ensemble_device_errors", "rollout", "env_set_rollout_path", "env_set_kernel_timing", "env_last_kernel_ms", "Server", "fr_server_create", "backtest_submit",
+    "ensemble_act", "ensemble_act_noalloc", "ensemble_device_errors", "rollout", "env_set_rollout_path", "env_set_kernel_timing", "env_last_kernel_ms", "env_set_tile_packing",
+    "env_tile_packing_efficiency", "Server", "fr_server_create", "backtest_submit",
     "backtest_poll", "fr_server_stats", "FrError", "lib",
     "PATH_AUTO", "PATH_UNFUSED",
     "ACT_I32_SHARES", "ACT_F32_UNIT", "ACT_U8_DISCRETE", "PREC_FP32", "PREC_BF16",
@@ -211,6 +212,16 @@ def env_restore(env: Env, blob: bytes):
 
 def env_set_rollout_path(env: Env, path: int):
     _lib.check(lib().env_set_rollout_path(env, int(path)), "env_set_rollout_path")
+
+
+def env_set_tile_packing(env: Env, on: bool):
+    _lib.check(lib().env_set_tile_packing(env, 1 if on else 0), "env_set_tile_packing")
+
+
+def env_tile_packing_efficiency(env: Env) -> float:
+    e = C.c_float()
+    _lib.check(lib().env_tile_packing_efficiency(env, C.byref(e)), "env_tile_packing_efficiency")
+    return e.value
 
 
 def env_set_kernel_timing(env: Env, on: bool):

@@ -429,6 +429,9 @@ void env_destroy(fr_env *env)
     dev_free(env->ctx, env->scratch, env->scratch_bytes);
     dev_free(env->ctx, env->slot_of_env, 4ull * env->v.N + 4ull * 32);
     dev_free(env->ctx, env->zbuf, env->zbuf_bytes);
+    const uint64_t tiles = ceil_div(env->v.N, 128);
+    dev_free(env->ctx, env->pack_perm, 4ull * tiles * 128);
+    dev_free(env->ctx, env->pack_tile_w, 4ull * tiles);
     for (int i = 0; i < 2; ++i)
         if (env->k_ev[i]) cudaEventDestroy(env->k_ev[i]);
     delete env;
@@ -537,6 +540,20 @@ int env_set_rollout_path(fr_env *env, int32_t path)
     FR_CHECK(env && (path == FR_PATH_AUTO || path == FR_PATH_UNFUSED), FR_EINVAL,
              "env_set_rollout_path: bad argument");
     env->path = path;
+    return FR_OK;
+}
+
+int env_set_tile_packing(fr_env *env, int32_t on)
+{
+    FR_CHECK(env, FR_EINVAL, "env_set_tile_packing: NULL env");
+    env->pack_off = on ? 0 : 1;
+    return FR_OK;
+}
+
+int env_tile_packing_efficiency(const fr_env *env, float *eff)
+{
+    FR_CHECK(env && eff, FR_EINVAL, "env_tile_packing_efficiency: NULL argument");
+    *eff = env->pack_state == 2 && !env->pack_off ? env->pack_efficiency : 1.0f;
     return FR_OK;
 }
 

@@ -112,6 +112,13 @@ struct fr_env {
     void *zbuf;
     uint64_t zbuf_bytes;
     uint64_t z_serial;          // serial of the ensemble Z was built for; 0 = stale
+    // tile packing of the fused stock kernel (envs sorted by window into
+    // 128-env tiles; each tile runs until its longest window is over)
+    int pack_state;             // 0 unknown, 1 not packed (uniform windows), 2 packed
+    int32_t *pack_perm;         // device [tiles*128] env at each tile position, -1 empty
+    int32_t *pack_tile_w;       // device [tiles] longest window of each tile
+    float pack_efficiency;      // sum(W_e - 1) / sum over tiles of 128 * (max W - 1)
+    int pack_off;               // packing switched off by the caller
     // optional events around the main rollout kernel
     cudaEvent_t k_ev[2];
     int k_timing;               // record on the next rollouts

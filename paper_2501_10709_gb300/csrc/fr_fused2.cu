@@ -80,6 +80,9 @@ struct F2Args {
     const float *b2, *b3;
     const float *Z;       // [M][n_ctx][H1]
     const int32_t *slot; // [N] asset-count slot of each env
+    const int32_t *perm; // [tiles*128] env at each tile position (NULL = identity; -1 = empty)
+    const int32_t *tile_w; // [tiles] longest window of a tile's envs (NULL = run every tile T steps)
+    int n_pos;            // tile positions holding an env index (N, or tiles*128 with perm)
     int n_ctx_per_agent;
     float w[MAX_AGENTS];
     int T;
@@ -324,20 +327,20 @@ __device__ __forceinline__ void own_store(const ObsWords &o, int r, uint32_t a_o
 // first (their shuffles overlap), then all stores, then the optional fp32
 // trajectory rows.  trow[i] < 0: no trajectory row.
 template <int NOWN>
-__device__ __forceinline__ void own_publish_all(const F2Args &a, const OwnEnv *own, const int *orow, int tile0,
+__device__ __forceinline__ void own_publish_all(const F2Args &a, const OwnEnv *own, const int *orow, const int *eidx,
                                                 uint32_t a_obs, uint32_t ctx_addr, int M2, int lane, int64_t tbase)
 {
     ObsWords o[NOWN];
 #pragma unroll
-    for (int i = 0; i < NOWN; ++i) o[i] = own_words(a, own[i], orow[i] < 128 && tile0 + orow[i] < a.v.N, lane);
+    for (int i = 0; i < NOWN; ++i) o[i] = own_words(a, own[i], eidx[i] >= 0, lane);
 #pragma unroll
     for (int i = 0; i < NOWN; ++i)
         if (orow[i] < 128) own_store(o[i], orow[i], a_obs, ctx_addr, M2, lane);
     if (a.tr_obs) {
 #pragma unroll
         for (int i = 0; i < NOWN; ++i) {
-            const int e = tile0 + orow[i];
-            if (orow[i] < 128 && e < a.v.N)
+            const int e = eidx[i];
+            if (e >= 0)
                 own_traj_obs(a, a.tr_obs + (tbase + e) * a.obs_ld, o[i].cv, o[i].pv, o[i].hv,
                              own[i].start + own[i].t, own[i].Ke, lane);
         }
@@ -385,15 +388,17 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
 
     // owned envs of this warp: rows r0 = rank + M2 * (ew + 8 * i)
     OwnEnv own[NOWN];
-    int orow[NOWN];
+    int orow[NOWN], eidx[NOWN];                    // tile row; env index (-1: no env there)
 #pragma unroll
     for (int i = 0; i < NOWN; ++i) {
         orow[i] = rank + M2 * (ew + F2_ENV_WARPS * i);
-        const int e = tile0 + orow[i];
+        const int pos = tile0 + orow[i];
+        eidx[i] = (orow[i] < 128 && pos < a.n_pos) ? (a.perm ? a.perm[pos] : pos) : -1;
+        const int e = eidx[i];
         OwnEnv &s = own[i];
         s.cash = 0; s.v0 = 0; s.t = 0; s.start = 0; s.W = 2; s.Ke = 0; s.done = 1; s.slot = 0; s.p = 0; s.h = 0;
         s.bps = 0;
-        if (orow[i] < 128 && e < v.N) {
+        if (e >= 0) {
             s.cash = v.cash[e];
             s.t = v.t[e];
             s.start = v.start[e];
@@ -410,7 +415,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         s.v0 = s.cash + warp_sum(s.p * (int64_t)s.h);
     }
     // observation of step 0
-    own_publish_all<NOWN>(a, own, orow, tile0, a_obs, ctx_addr, M2, lane, 0);
+    own_publish_all<NOWN>(a, own, orow, eidx, a_obs, ctx_addr, M2, lane, 0);
     f2_signal_all(obs_ready, M2, lane, true);
 
     const float *zbase = a.Z + (size_t)j * a.n_ctx_per_agent * p.H1;
@@ -419,7 +424,9 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
     // wait that gives up sets the CTA's abort flag; every later wait then
     // returns at once and the remaining steps run through without their data
     // (all of their addresses are independent of it, or clamped).
-    const int T = a.T;
+    // A packed tile runs only until its longest window is over (uniform
+    // across the cluster: one value per tile).
+    const int T = a.tile_w ? min(a.T, max(a.tile_w[tile] - 1, 0)) : a.T;
     if (issuer) f2_wait(&bars[B_W], 0u, abort, a.err, 1u, false);
     for (int s = 0; s < T; ++s) {
         const uint32_t ph = (uint32_t)s & 1u;
@@ -579,7 +586,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
 #pragma unroll
         for (int i = 0; i < NOWN; ++i) {
             const OwnEnv &st = own[i];
-            run[i] = orow[i] < 128 && tile0 + orow[i] < v.N && !st.done;
+            run[i] = eidx[i] >= 0 && !st.done;
             const bool ok = run[i] && lane < st.Ke;
             p1[i] = ok ? perturb(__ldg(v.close + (int64_t)(st.start + st.t + 1) * SK2 + lane), st.bps) : 0;
         }
@@ -590,7 +597,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         for (int i = 0; i < NOWN; ++i) {
             const OwnEnv &st = own[i];
             const int rr = orow[i] < 128 ? orow[i] : 127;
-            const int e = tile0 + orow[i];
+            const int e = eidx[i];
             // combine (anchored weighted mean) for this lane's asset
             const uint8_t *xr = smem + L.xbuf + (size_t)rr * 64 + 2 * lane;
             const float a0 = __half2float(*(const __half *)xr);
@@ -603,7 +610,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                     act = __fadd_rn(act, __fmul_rn(wj, __fsub_rn(aj, a0)));
                 }
             }
-            if (a.tr_act && orow[i] < 128 && e < v.N && lane < SK2) a.tr_act[((int64_t)s * v.N + e) * SK2 + lane] = act;
+            if (a.tr_act && e >= 0 && lane < SK2) a.tr_act[((int64_t)s * v.N + e) * SK2 + lane] = act;
             const bool live = run[i] && lane < st.Ke;
             float ac = isfinite(act) ? act : 0.0f;
             ac = fminf(fmaxf(ac, -1.0f), 1.0f);
@@ -621,8 +628,8 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         }
 #pragma unroll
         for (int i = 0; i < NOWN; ++i) {
-            const int e = tile0 + orow[i];
-            const bool valid = orow[i] < 128 && e < v.N;
+            const int e = eidx[i];
+            const bool valid = e >= 0;
             OwnEnv &st = own[i];
             const int64_t row = (int64_t)s * v.N + e;
             int64_t rew = 0, vlog = VLOG_NONE2;
@@ -661,7 +668,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                 a.vlog[row] = vlog;
             }
         }
-        if (s + 1 < T) own_publish_all<NOWN>(a, own, orow, tile0, a_obs, ctx_addr, M2, lane, (int64_t)(s + 1) * v.N);
+        if (s + 1 < T) own_publish_all<NOWN>(a, own, orow, eidx, a_obs, ctx_addr, M2, lane, (int64_t)(s + 1) * v.N);
         if (s + 1 < T) f2_signal_all(obs_ready, M2, lane, true);
     }
     // every MMA this CTA issued has completed before TMEM is released, also
@@ -672,11 +679,13 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         mbar_wait(&bars[B_END], 0u, &no_abort, a.err, 256u, TC_WAIT_NS);
     }
     __syncwarp();
-    // state back to global memory (steps and accumulators: metrics replay)
+    // state back to global memory (steps and accumulators: metrics replay);
+    // the steps a packed tile did not run are no-steps in the value log
 #pragma unroll
     for (int i = 0; i < NOWN; ++i) {
-        const int e = tile0 + orow[i];
-        if (orow[i] >= 128 || e >= v.N) continue;
+        const int e = eidx[i];
+        if (e < 0) continue;
+        for (int s = T + lane; s < a.T; s += 32) a.vlog[(int64_t)s * v.N + e] = VLOG_NONE2;
         if (lane == 0) {
             v.cash[e] = own[i].cash;
             v.done[e] = own[i].done ? 1 : 0;
@@ -965,8 +974,54 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
         env->z_serial = e->serial;
     }
 
+    // Tile packing (no trajectory, no auto-reset, windows of different
+    // lengths): envs sorted by window, longest first, into 128-env tiles, each
+    // tile running until its longest window is over; the longest tiles get
+    // the lowest block indices, so they start first when the grid takes more
+    // than one wave.  Every env's arithmetic is unchanged.
+    const bool want_traj = traj->obs || traj->act || traj->rew || traj->rew_f32 || traj->done;
+    const bool may_pack = !want_traj && !v.auto_reset && v.N > 128 && !env->pack_off;
+    const int tiles = (int)ceil_div(v.N, 128);
+    if (may_pack && env->pack_state == 0) {
+        std::vector<int32_t> W(v.N);
+        FR_CUDA(cudaMemcpy(W.data(), v.W, 4ull * v.N, cudaMemcpyDeviceToHost));
+        bool uniform = true;
+        for (int i = 1; i < v.N; ++i) uniform = uniform && W[i] == W[0];
+        if (uniform) {
+            env->pack_state = 1;
+        } else {
+            std::vector<int32_t> order(v.N);
+            for (int i = 0; i < v.N; ++i) order[i] = i;
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return W[x] > W[y]; });
+            std::vector<int32_t> perm((size_t)tiles * 128, -1), tw(tiles, 2);
+            double used = 0.0, spent = 0.0;
+            for (int i = 0; i < v.N; ++i) {
+                perm[i] = order[i];
+                used += W[order[i]] - 1;
+            }
+            for (int t = 0; t < tiles; ++t) {
+                tw[t] = W[order[(size_t)t * 128]];
+                spent += 128.0 * (tw[t] - 1);
+            }
+            if (!env->pack_perm) {
+                int rc = dev_alloc(env->ctx, (void **)&env->pack_perm, 4ull * tiles * 128);
+                if (rc) return rc;
+                rc = dev_alloc(env->ctx, (void **)&env->pack_tile_w, 4ull * tiles);
+                if (rc) return rc;
+            }
+            FR_CUDA(cudaMemcpy(env->pack_perm, perm.data(), 4ull * tiles * 128, cudaMemcpyHostToDevice));
+            FR_CUDA(cudaMemcpy(env->pack_tile_w, tw.data(), 4ull * tiles, cudaMemcpyHostToDevice));
+            env->pack_efficiency = spent > 0 ? (float)(used / spent) : 1.0f;
+            env->pack_state = 2;
+        }
+    }
+    const bool packed = may_pack && env->pack_state == 2;
+
     F2Args a;
     memset(&a, 0, sizeof(a));
+    a.perm = packed ? env->pack_perm : nullptr;
+    a.tile_w = packed ? env->pack_tile_w : nullptr;
+    a.n_pos = packed ? tiles * 128 : v.N;
     a.v = v;
     a.plan = p;
     a.img = im->img;

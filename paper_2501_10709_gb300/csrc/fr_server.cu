@@ -224,6 +224,7 @@ void worker_loop(fr_server *s)
             fail_all(s, FR_ECUDA);
             return;
         }
+        if (!admitted.empty()) s->env->pack_state = 0;       // windows changed: re-pack the tiles
         if (ke_changed && s->env->slot_of_env) {
             // the fused stock kernel rebuilds its asset-count slots
             dev_free(s->ctx, s->env->slot_of_env, 4ull * N + 4ull * 32);

@@ -211,3 +211,43 @@ def test_kernel_timing_hook(ctx, dev):
     fr.env_set_kernel_timing(env, False)
     with pytest.raises(fr.FrError):
         fr.env_last_kernel_ms(env)
+
+
+@pytest.mark.parametrize("N", [700, 1000])
+def test_packed_tiles_equal_unpacked(ctx, dev, N):
+    # Without trajectory outputs the fused kernel packs envs by window into
+    # tiles (longest first) and stops each tile after its longest window; with
+    # a trajectory it runs the envs in their own order for all T steps.  Every
+    # env's arithmetic is the same either way: equal metrics and final state.
+    mk_np = synth.stock_market(400, 30, seed=51)
+    e = synth.stock_envs_uneven(N, 30, 400, k_lo=10, w_lo=5, w_hi=120, seed=51)
+    params = synth.actor_params(synth.STOCK_DIMS, 3, seed=52)
+    mk = fr.fr_market_create(ctx, mk_np)
+    ens = fr.ensemble_create(ctx, synth.STOCK_DIMS, params, precision=fr.PREC_BF16)
+    T = 130
+    out = []
+    for with_traj in (False, True):
+        env = _stock_env(ctx, mk, e)
+        met = torch.empty(N, 3, dtype=torch.float64, device=dev)
+        tr = _traj(T, N, env.D, 30, dev) if with_traj else None
+        # two pieces: the packed path keeps each env's steps and state across calls
+        fr.rollout(env, ens, 50, traj=None if tr is None else {k: v[:50] for k, v in tr.items()}, metrics=met)
+        fr.rollout(env, ens, T - 50, traj=None if tr is None else {k: v[50:] for k, v in tr.items()}, metrics=met)
+        cash = torch.empty(N, dtype=torch.int64, device=dev)
+        hold = torch.empty(N, 30, dtype=torch.int32, device=dev)
+        steps = torch.empty(N, dtype=torch.int32, device=dev)
+        done = torch.empty(N, dtype=torch.uint8, device=dev)
+        fr.env_get_state(env, cash=cash, hold=hold, steps=steps, done=done)
+        torch.cuda.synchronize()
+        out.append([x.cpu().numpy() for x in (met, cash, hold, steps, done)])
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+    assert out[0][4].all()                                  # every window finished within T
+    # and with packing switched off, no trajectory
+    env = _stock_env(ctx, mk, e)
+    fr.env_set_tile_packing(env, False)
+    met = torch.empty(N, 3, dtype=torch.float64, device=dev)
+    fr.rollout(env, ens, T, metrics=met)
+    torch.cuda.synchronize()
+    assert np.array_equal(met.cpu().numpy(), out[0][0])
+    assert fr.env_tile_packing_efficiency(env) == 1.0
