@@ -284,6 +284,40 @@ def uneven_line(fr, ctx, dev, flush, stream, reps=3):
     return res
 
 
+def time_graph_rollouts(fr, env, ens, T, steps, warmup, metrics, flush, stream):
+    """The same timed region as time_rollouts, each step one replay of a CUDA
+    graph holding env_reset + rollout (captured after warm-up calls)."""
+    import torch
+    fr.env_set_rollout_path(env, fr.PATH_AUTO)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(warmup):
+            fr.env_reset(env)
+            fr.rollout(env, ens, T, metrics=metrics)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fr.env_reset(env)
+        fr.rollout(env, ens, T, metrics=metrics)
+    for _ in range(warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        _flush_l2(flush)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.replay()
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b) / 1e3)
+    del g
+    return times
+
+
 def time_kernel(fn, iters, stream):
     import torch
     for _ in range(3):
@@ -329,8 +363,7 @@ def run_gpu(args):
         torch.distributed.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    t_bf16 = time_rollouts(fr, env, ens_bf16, T, args.steps, args.warmup, metrics, flush, stream,
-                           path=fr.PATH_AUTO)
+    t_bf16 = time_graph_rollouts(fr, env, ens_bf16, T, args.steps, args.warmup, metrics, flush, stream)
     clk = clocks.stop()
     side = max(2, args.steps // 4)
     t_fp32 = time_rollouts(fr, env, ens_fp32, T, side, 3, metrics, flush, stream)
@@ -425,7 +458,8 @@ def run_gpu(args):
         "config": {"workload": "stock 2048 envs x 30 assets x 256 steps, 3 x 301-256-256-30 BF16 "
                                "actors, mean combine, 1000 GBM days, bps on",
                    "n_envs": N, "steps_per_rollout": T, "agents": M,
-                   "path": "fused persistent tcgen05 bf16 kernel, trajectory off",
+                   "path": "fused persistent tcgen05 bf16 kernel, trajectory off; each step one CUDA graph "
+                           "replay of env_reset + rollout",
                    "l2": "flushed between timed rollouts (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "plain_fp32": {"value": plain_value, "unit": "env-steps/s",

@@ -322,7 +322,7 @@ int tc_forward_tiled(const fr_ensemble *e, const float *obs, int ld, int n, floa
     k_obs_tiles<<<ceil_div(threads, 256), 256, 0, s>>>(obs, ld, n, p.layer[0].fin, nch, (uint4 *)scratch);
     FR_CUDA(cudaGetLastError());
     const uint32_t smem = ta_layout(p, stages).total + 1024u;
-    FR_CUDA(cudaFuncSetAttribute(k_tc_actor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FR_CUDA(set_max_smem_once((const void *)k_tc_actor, e->ctx->device));
     k_tc_actor<<<tiles, TA_THREADS, smem, s>>>(p, t->img, t->bias, (const uint8_t *)scratch, n, y, t->err, stages);
     FR_CUDA(cudaGetLastError());
     return FR_OK;

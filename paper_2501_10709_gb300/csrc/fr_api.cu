@@ -582,6 +582,20 @@ int env_last_kernel_ms(fr_env *env, float *ms)
 
 extern "C++" {
 namespace fr {
+cudaError_t set_max_smem_once(const void *func, int device)
+{
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> done;
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto &d : done)
+        if (d.first == func && d.second == device) return cudaSuccess;
+    int optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess) done.emplace_back(func, device);
+    return e;
+}
+
 cudaError_t env_time_mark(fr_env *env, int which, cudaStream_t s)
 {
     if (!env->k_timing) return cudaSuccess;

@@ -142,6 +142,11 @@ void dev_free(fr_ctx *ctx, void *p, uint64_t bytes);
 
 inline unsigned ceil_div(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in
+// maximum, once per kernel and device (so that rollouts after the first make
+// no such call and can be captured into a CUDA graph).  fr_api.cu.
+cudaError_t set_max_smem_once(const void *func, int device);
+
 // ------------------------------------------------------- kernel launchers
 // env kernels (fr_env_kernels.cu)
 cudaError_t launch_env_reset(const EnvView &v, cudaStream_t s);

@@ -888,12 +888,10 @@ int tc_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     cfg.numAttrs = 1;
     FR_CUDA(env_time_mark(env, 0, s));
     if (v.task == FR_TASK_STOCK) {
-        FR_CUDA(cudaFuncSetAttribute(k_rollout_fused<FR_TASK_STOCK>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FR_CUDA(set_max_smem_once((const void *)k_rollout_fused<FR_TASK_STOCK>, env->ctx->device));
         FR_CUDA(cudaLaunchKernelEx(&cfg, k_rollout_fused<FR_TASK_STOCK>, a));
     } else {
-        FR_CUDA(cudaFuncSetAttribute(k_rollout_fused<FR_TASK_CRYPTO>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FR_CUDA(set_max_smem_once((const void *)k_rollout_fused<FR_TASK_CRYPTO>, env->ctx->device));
         FR_CUDA(cudaLaunchKernelEx(&cfg, k_rollout_fused<FR_TASK_CRYPTO>, a));
     }
     FR_CUDA(env_time_mark(env, 1, s));

@@ -1053,7 +1053,7 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    FR_CUDA(cudaFuncSetAttribute(k_rollout_stock2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FR_CUDA(set_max_smem_once((const void *)k_rollout_stock2, env->ctx->device));
     FR_CUDA(env_time_mark(env, 0, s));
     FR_CUDA(cudaLaunchKernelEx(&cfg, k_rollout_stock2, a));
     FR_CUDA(env_time_mark(env, 1, s));

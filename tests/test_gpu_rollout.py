@@ -251,3 +251,43 @@ def test_packed_tiles_equal_unpacked(ctx, dev, N):
     torch.cuda.synchronize()
     assert np.array_equal(met.cpu().numpy(), out[0][0])
     assert fr.env_tile_packing_efficiency(env) == 1.0
+
+
+@pytest.mark.parametrize("case", ["stock_bf16_fused", "stock_fp32_plain", "crypto_bf16x3_fused"])
+def test_rollout_graph_capture(ctx, dev, case):
+    # after one warm-up call (cached tables, scratch, kernel attributes) a
+    # reset + rollout can be captured into a CUDA graph; replays equal direct calls
+    if case.startswith("stock"):
+        w = synth.workload_stock_2048(N=384, T=24)
+        e = w.envs
+        mk = fr.fr_market_create(ctx, w.market)
+        env = _stock_env(ctx, mk, e)
+        ens = fr.ensemble_create(ctx, w.dims, w.params,
+                                 precision=fr.PREC_BF16 if "bf16" in case else fr.PREC_FP32)
+    else:
+        w = synth.workload_crypto(N=384, T=24, S=40_000)
+        e = w.envs
+        mk = fr.fr_market_create(ctx, w.market)
+        env = fr.env_create(ctx, mk, start=e.start, window=e.W, init_cash=e.init_cash, pmax=e.pmax)
+        ens = fr.ensemble_create(ctx, w.dims, w.params, precision=fr.PREC_BF16X3, combine=fr.COMBINE_VOTE,
+                                 out_act=0)
+    T = w.T
+    met = torch.empty(e.N, 3, dtype=torch.float64, device=dev)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            fr.env_reset(env)
+            fr.rollout(env, ens, T, metrics=met)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    ref = met.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fr.env_reset(env)
+        fr.rollout(env, ens, T, metrics=met)
+    for _ in range(3):
+        met.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(met, ref)
