@@ -37,6 +37,25 @@ def _peaks():
         return dict(FALLBACK_PEAKS), "fallback"
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest of every rank's x (the timed region ends when the slowest
+    replica does); x itself when not distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world: int, units_per_step: int, steps: int, max_total_s: float) -> float:
+    """Whole-job throughput of `world` replicas that each process
+    units_per_step per step: all ranks' units over the slowest rank's time
+    (weak scaling; the replicas share nothing)."""
+    return world * units_per_step * steps / max_total_s
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -375,13 +394,9 @@ def run_gpu(args):
     t_traj = time_rollouts(fr, env, ens_bf16, T, side, 3, metrics, flush, stream, traj=traj)
     del traj
     fr.env_set_rollout_path(env, fr.PATH_AUTO)
-    total = sum(t_bf16)
-    if world > 1:
-        tt = torch.tensor([total], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total = float(tt.item())
+    total = max_over_ranks(sum(t_bf16), device=dev)
     env_steps = N * T
-    value = world * env_steps * args.steps / total
+    value = replica_value(world, env_steps, args.steps, total)
     plain_value = env_steps * len(t_fp32) / sum(t_fp32)
 
     # dominant kernel: the fused rollout kernel, one launch per rollout, timed
