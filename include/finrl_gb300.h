@@ -263,6 +263,25 @@ int ensemble_act(const fr_ensemble *ens, const float *obs, int32_t n,
 int ensemble_act_noalloc(const fr_ensemble *ens, const float *obs, int32_t n,
                          void *act, void *stream);
 
+/* Replace a MEAN ensemble's combine weights (host float [M]); later
+ * ensemble_act / rollout calls use them.  FR_EINVAL for VOTE ensembles or
+ * non-finite weights. */
+int ensemble_set_weights(fr_ensemble *ens, const float *weights);
+
+/* Sharpe-softmax weighting from a validation window (Sec. 5.2.1): each
+ * agent trades the validation envs alone (a single-agent ensemble of the
+ * same precision) for T steps from their current state; its Sharpe ratio is
+ * the mean over the envs of the episode Sharpe (env_metrics); agents with a
+ * Sharpe ratio below `threshold` are discarded (when none reaches it, the
+ * best agent is kept alone, lowest index on ties); the kept agents' weights
+ * are softmax(Sharpe) = exp(S_j - max S) / sum_k exp(S_k - max S), the
+ * discarded ones 0, and they become the ensemble's combine weights.  The
+ * envs are restored to their state before the call.  sharpe (host double
+ * [M]) and weights (host float [M]) receive the results (either may be
+ * NULL).  MEAN ensembles only.  Synchronous. */
+int ensemble_validate(fr_ensemble *ens, fr_env *val_env, int32_t T, double threshold,
+                      double *sharpe, float *weights, void *stream);
+
 /* Error flags raised on the device by the tensor-core kernels of this
  * ensemble (a bounded wait that gave up); 0 when none (synchronous). */
 int ensemble_device_errors(const fr_ensemble *ens, uint32_t *flags);

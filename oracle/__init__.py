@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import ctypes as C
 import hashlib
+import math
 import os
 import subprocess
 import threading
@@ -198,6 +199,43 @@ def metrics_series(v, ann: float) -> np.ndarray:
 
 
 # ------------------------------------------------------------------ rollouts
+
+def sharpe_softmax_weights(sharpe, threshold: float) -> np.ndarray:
+    """Sec. 5.2.1 weights calculation: agents whose validation Sharpe ratio is
+    below `threshold` are discarded (when none reaches it, the best agent,
+    lowest index on ties, is kept alone); the kept agents get
+    softmax(Sharpe) -- exp(S_j - max S) / sum_k exp(S_k - max S), the max
+    taken over the kept agents, the sum in agent order -- the others 0."""
+    S = [float(x) for x in sharpe]
+    keep = [j for j, x in enumerate(S) if x >= threshold]
+    if not keep:
+        best = 0
+        for j in range(1, len(S)):
+            if S[j] > S[best]:
+                best = j
+        keep = [best]
+    m = max(S[j] for j in keep)
+    w = [0.0] * len(S)
+    total = 0.0
+    for j in keep:
+        w[j] = math.exp(S[j] - m)
+        total += w[j]
+    for j in keep:
+        w[j] = w[j] / total
+    return np.array(w, dtype=np.float64)
+
+
+def validation_sharpe(market, Ke, start, W, bps, dims, params, *, init_cash: int, hmax: int,
+                      fee_bps: int, T: int, nthreads: int = 0) -> np.ndarray:
+    """Each agent trading the validation envs alone (fp64 actor): the mean over
+    the envs of the episode Sharpe ratio after T steps."""
+    out = []
+    for j in range(params.shape[0]):
+        r = stock_run(market, Ke, start, W, bps, init_cash=init_cash, hmax=hmax, fee_bps=fee_bps, T=T,
+                      ensemble=(dims, params[j:j + 1], None), nthreads=nthreads, want=("metrics",))
+        out.append(float(np.mean(r["metrics"][:, 1])))
+    return np.array(out)
+
 
 def stock_run(market, Ke, start, W, bps, *, init_cash: int, hmax: int,
               fee_bps: int, T: int, auto_reset: bool = False,

@@ -22,7 +22,7 @@ __all__ = [
     "env_observe", "env_get_state", "env_metrics", "env_snapshot", "env_restore",
     "env_error_count", "env_dims", "ensemble_create", "ensemble_forward",
     "ensemble_act", "ensemble_act_noalloc", "ensemble_device_errors", "rollout", "env_set_rollout_path", "env_set_kernel_timing", "env_last_kernel_ms", "env_set_tile_packing",
-    "env_tile_packing_efficiency", "Server", "fr_server_create", "backtest_submit",
+    "env_tile_packing_efficiency", "ensemble_set_weights", "ensemble_validate", "Server", "fr_server_create", "backtest_submit",
     "backtest_poll", "fr_server_stats", "FrError", "lib",
     "PATH_AUTO", "PATH_UNFUSED",
     "ACT_I32_SHARES", "ACT_F32_UNIT", "ACT_U8_DISCRETE", "PREC_FP32", "PREC_BF16",
@@ -368,3 +368,20 @@ def fr_server_stats(srv: Server) -> dict:
     st = _lib.ServerStats()
     _lib.check(lib().fr_server_stats_get(srv, C.byref(st)), "fr_server_stats_get")
     return {k: getattr(st, k) for k, _ in st._fields_}
+
+
+# ------------------------------------------------------ ensemble weighting
+def ensemble_set_weights(ens: Ensemble, weights):
+    w = np.ascontiguousarray(weights, np.float32)
+    _lib.check(lib().ensemble_set_weights(ens, _hptr(w)), "ensemble_set_weights")
+
+
+def ensemble_validate(ens: Ensemble, env: Env, T: int, threshold: float = 0.0, stream=None):
+    """Sec. 5.2.1 Sharpe-softmax weights from a validation window; returns
+    (sharpe[M] float64, weights[M] float32) and sets the ensemble's weights."""
+    M = ens.M
+    S = np.zeros(M, np.float64)
+    w = np.zeros(M, np.float32)
+    _lib.check(lib().ensemble_validate(ens, env, int(T), float(threshold), _hptr(S), _hptr(w), _stream(stream)),
+               "ensemble_validate")
+    return S, w

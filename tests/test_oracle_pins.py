@@ -232,3 +232,33 @@ def test_metrics_random_series_against_numpy():
     peak = np.maximum.accumulate(v)
     assert abs(got[2] - (v / peak - 1.0).min()) < 1e-15
     assert abs(got[0] - (v[-1] / v[0] - 1.0)) < 1e-15
+
+
+# ------------------------------------------- Sec. 5.2.1 Sharpe-softmax weights
+def test_sharpe_softmax_two_agents_closed_form():
+    w = oracle.sharpe_softmax_weights([0.7, 1.9], -10.0)
+    assert abs(w[0] - 1.0 / (1.0 + math.exp(1.9 - 0.7))) < 1e-15
+    assert abs(w[1] - 1.0 / (1.0 + math.exp(0.7 - 1.9))) < 1e-15
+    assert abs(w.sum() - 1.0) < 1e-15
+
+
+def test_sharpe_softmax_shift_invariance_and_large_values():
+    s = np.array([0.3, -1.2, 2.5, 0.0])
+    w0 = oracle.sharpe_softmax_weights(s, -np.inf)
+    w1 = oracle.sharpe_softmax_weights(s + 500.0, -np.inf)        # exp(500) alone would overflow
+    assert np.isfinite(w1).all() and np.allclose(w0, w1, rtol=0, atol=1e-13)
+    e = np.exp(s - s.max())
+    assert np.allclose(w0, e / e.sum(), rtol=0, atol=1e-15)
+
+
+def test_sharpe_softmax_discards_below_threshold():
+    s = [1.0, -0.5, 0.2, -3.0]
+    w = oracle.sharpe_softmax_weights(s, 0.0)
+    assert w[1] == 0.0 and w[3] == 0.0
+    assert abs(w[0] - math.exp(0.0) / (math.exp(0.0) + math.exp(0.2 - 1.0))) < 1e-15
+    assert abs(w[0] + w[2] - 1.0) < 1e-15
+
+
+def test_sharpe_softmax_all_below_keeps_best_lowest_index():
+    assert list(oracle.sharpe_softmax_weights([-2.0, -1.0, -1.0], 0.0)) == [0.0, 1.0, 0.0]
+    assert list(oracle.sharpe_softmax_weights([-1.0], 5.0)) == [1.0]
