@@ -309,6 +309,25 @@ typedef struct {
 int rollout(fr_env *env, const fr_ensemble *ens, int32_t T,
             const fr_traj *traj, double *metrics, void *stream);
 
+/* Metrics of stored trajectories on the device (the consumer side of the
+ * T x N sample tensors of Sec. 4.3.2).  rew: device int64 [T][N] rewards
+ * v_t - v_{t-1}; done: device uint8 [T][N] or NULL.  Env i's periods are
+ * its rows up to and including its first done row (all T rows when none);
+ * its values are v_0 = v0 (cents, > 0), v_t = v_{t-1} + rew.  out: device
+ * double [N][FR_TRAJ_METRICS] (with r_f = 0, A = ann, returns
+ * rho_t = v_t / v_{t-1} - 1, ratios with a zero denominator reported as 0):
+ *   0 cumulative return v_n / v_0 - 1; 1 Sharpe ratio (Sec. 5.2.1, as
+ *   env_metrics); 2 maximum drawdown (<= 0); 3 annual return
+ *   (v_n / v_0)^(A/n) - 1; 4 annual volatility sd(rho) sqrt(A) (ddof 1);
+ *   5 RoMaD = cumulative return / |MDD|; 6 Sortino = mean(rho) / DD sqrt(A),
+ *   DD = sqrt(sum min(rho, 0)^2 / n); 7 Calmar = annual return / |MDD|;
+ *   8 Omega = sum max(rho, 0) / sum max(-rho, 0); 9 discounted return
+ *   sum_{t=1..n} gamma^t r_t (Sec. 4.3, cents); 10 n.
+ * (Sec. 6.1 metric list.)  Asynchronous on the stream. */
+#define FR_TRAJ_METRICS 11
+int trajectory_metrics(const int64_t *rew, const uint8_t *done, int32_t T, int32_t N, int64_t v0,
+                       double ann, double gamma, double *out, void *stream);
+
 #define FR_PATH_AUTO 0        /* fused kernel when the pair supports it     */
 #define FR_PATH_UNFUSED 1     /* one launch per stage per step              */
 

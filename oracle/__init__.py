@@ -198,6 +198,21 @@ def metrics_series(v, ann: float) -> np.ndarray:
     return out
 
 
+TRAJ_METRICS = ("cumulative_return", "sharpe", "max_drawdown", "annual_return", "annual_volatility", "romad",
+                "sortino", "calmar", "omega", "discounted_return", "periods")
+
+
+def trajectory_metrics(rew, done, v0: int, ann: float, gamma: float) -> np.ndarray:
+    """rew[T][N] int64, done[T][N] uint8 or None -> [N][11] (TRAJ_METRICS)."""
+    rew = _c(rew, np.int64)
+    T, N = rew.shape
+    d = None if done is None else _c(done, np.uint8)
+    out = np.empty((N, 11), np.float64)
+    _load().orc_trajectory_metrics(T, N, _p(rew), _p(d), C.c_int64(int(v0)), C.c_double(float(ann)),
+                                   C.c_double(float(gamma)), _p(out))
+    return out
+
+
 # ------------------------------------------------------------------ rollouts
 
 def sharpe_softmax_weights(sharpe, threshold: float) -> np.ndarray:

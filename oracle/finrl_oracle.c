@@ -268,6 +268,60 @@ void orc_metrics_series(int32_t n, const int64_t *v, double ann, double *out)
     acc_final(&a, ann, out);
 }
 
+/* Sec. 6.1 metric list and Sec. 4.3 discounted trajectory return, from a
+ * stored trajectory: rew[T][N] int64 rewards (v_t - v_{t-1}), done[T][N] (or
+ * NULL); env i's periods are its rows up to and including its first done row
+ * (all T rows when it has none), its values v_0 = v0, v_t = v_{t-1} + rew.
+ * out[N][11]:
+ *   0 cumulative return v_n / v_0 - 1      1 Sharpe (as the episode metrics)
+ *   2 maximum drawdown (<= 0)               3 annual return (v_n/v_0)^(A/n) - 1
+ *   4 annual volatility sd * sqrt(A)        5 RoMaD = cumulative return / |MDD|
+ *   6 Sortino = mean / DD * sqrt(A), DD = sqrt(sum min(rho, 0)^2 / n)
+ *   7 Calmar = annual return / |MDD|
+ *   8 Omega = sum max(rho, 0) / sum max(-rho, 0) (threshold return 0)
+ *   9 discounted return sum_{t=1..n} gamma^t r_t (cents)   10 n
+ * with r_f = 0, sd with ddof 1 (0 below two periods), and every ratio whose
+ * denominator is 0 reported as 0. */
+void orc_trajectory_metrics(int32_t T, int32_t N, const int64_t *rew, const uint8_t *done,
+                            int64_t v0, double ann, double gamma, double *out)
+{
+    for (int i = 0; i < N; ++i) {
+        orc_acc a;
+        acc_reset(&a, v0);
+        double down2 = 0.0, up = 0.0, dn = 0.0, disc = 0.0, g = 1.0;
+        int64_t v = v0;
+        for (int t = 0; t < T; ++t) {
+            const int64_t r = rew[(int64_t)t * N + i];
+            const int64_t v1 = v + r;
+            const double rho = (double)v1 / (double)v - 1.0;
+            acc_push(&a, v, v1);
+            if (rho < 0.0) {
+                down2 += rho * rho;
+                dn += -rho;
+            } else {
+                up += rho;
+            }
+            g *= gamma;
+            disc += g * (double)r;
+            v = v1;
+            if (done && done[(int64_t)t * N + i]) break;
+        }
+        double *o = out + (int64_t)i * 11;
+        acc_final(&a, ann, o);
+        const double n = (double)a.n;
+        const double cr = o[0], mdd = -o[2];
+        o[3] = a.n > 0 ? pow((double)a.vlast / (double)a.v0, ann / n) - 1.0 : 0.0;
+        o[4] = a.n >= 2 ? sqrt(a.m2 / (n - 1.0)) * sqrt(ann) : 0.0;
+        o[5] = mdd != 0.0 ? cr / mdd : 0.0;
+        const double dd = a.n > 0 ? sqrt(down2 / n) : 0.0;
+        o[6] = dd != 0.0 ? a.mu / dd * sqrt(ann) : 0.0;
+        o[7] = mdd != 0.0 ? o[3] / mdd : 0.0;
+        o[8] = dn != 0.0 ? up / dn : 0.0;
+        o[9] = disc;
+        o[10] = n;
+    }
+}
+
 /* ------------------------------------------------------------ stock task */
 
 typedef struct {

@@ -22,7 +22,7 @@ __all__ = [
     "env_observe", "env_get_state", "env_metrics", "env_snapshot", "env_restore",
     "env_error_count", "env_dims", "ensemble_create", "ensemble_forward",
     "ensemble_act", "ensemble_act_noalloc", "ensemble_device_errors", "rollout", "env_set_rollout_path", "env_set_kernel_timing", "env_last_kernel_ms", "env_set_tile_packing",
-    "env_tile_packing_efficiency", "ensemble_set_weights", "ensemble_validate", "Server", "fr_server_create", "backtest_submit",
+    "env_tile_packing_efficiency", "ensemble_set_weights", "ensemble_validate", "trajectory_metrics", "Server", "fr_server_create", "backtest_submit",
     "backtest_poll", "fr_server_stats", "FrError", "lib",
     "PATH_AUTO", "PATH_UNFUSED",
     "ACT_I32_SHARES", "ACT_F32_UNIT", "ACT_U8_DISCRETE", "PREC_FP32", "PREC_BF16",
@@ -385,3 +385,19 @@ def ensemble_validate(ens: Ensemble, env: Env, T: int, threshold: float = 0.0, s
     _lib.check(lib().ensemble_validate(ens, env, int(T), float(threshold), _hptr(S), _hptr(w), _stream(stream)),
                "ensemble_validate")
     return S, w
+
+
+def trajectory_metrics(rew, done=None, *, v0: int = 100_000_000, ann: float = 252.0, gamma: float = 0.99,
+                       out=None, stream=None):
+    """rew [T][N] int64 (device), done [T][N] uint8 or None -> [N][11] float64
+    (cumulative return, Sharpe, MDD, annual return, annual volatility, RoMaD,
+    Sortino, Calmar, Omega, discounted return, periods)."""
+    import torch
+    T, N = rew.shape
+    if out is None:
+        out = torch.empty(N, 11, dtype=torch.float64, device=rew.device)
+    _lib.check(lib().trajectory_metrics(_dptr(rew, torch.int64, T * N, "rew"),
+                                        _dptr(done, torch.uint8, T * N, "done"), int(T), int(N), int(v0),
+                                        float(ann), float(gamma), _dptr(out, torch.float64, N * 11, "out"),
+                                        _stream(stream)), "trajectory_metrics")
+    return out

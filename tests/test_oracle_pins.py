@@ -262,3 +262,70 @@ def test_sharpe_softmax_discards_below_threshold():
 def test_sharpe_softmax_all_below_keeps_best_lowest_index():
     assert list(oracle.sharpe_softmax_weights([-2.0, -1.0, -1.0], 0.0)) == [0.0, 1.0, 0.0]
     assert list(oracle.sharpe_softmax_weights([-1.0], 5.0)) == [1.0]
+
+
+# ---------------------------- Sec. 6.1 metric list from stored trajectories
+def _traj_from_values(v):
+    v = np.asarray(v, np.int64)
+    return np.diff(v).reshape(-1, 1), int(v[0])
+
+
+def test_traj_metrics_constant_growth_closed_forms():
+    # v_t = 1000 * 2^t: rho = 1 every period -> no variance, no downside,
+    # no loss, no drawdown; annual return (2^n)^(A/n) - 1 = 2^A - 1 (A = n = 4,
+    # so that A/n is exact)
+    v = [1000 * 2 ** t for t in range(5)]
+    rew, v0 = _traj_from_values(v)
+    m = oracle.trajectory_metrics(rew, None, v0, 4.0, 0.5)[0]
+    assert m[0] == 15.0 and m[1] == 0.0 and m[2] == 0.0
+    assert m[3] == 15.0 and m[4] == 0.0 and m[5] == 0.0 and m[6] == 0.0 and m[7] == 0.0 and m[8] == 0.0
+    # discounted return: sum_t gamma^t r_t with r_t = 1000 * 2^(t-1), gamma = 1/2 -> 1000/2 per period
+    assert m[9] == 4 * 500.0 and m[10] == 4
+
+
+def test_traj_metrics_constant_loss_sortino_is_minus_sqrt_a():
+    # rho = -1/2 every period: mean = -1/2, downside deviation = 1/2
+    v = [1 << 20 >> t for t in range(5)]
+    rew, v0 = _traj_from_values(v)
+    m = oracle.trajectory_metrics(rew, None, v0, 9.0, 1.0)[0]
+    assert m[6] == -3.0
+    assert m[8] == 0.0                     # no gains
+    assert m[2] == -1.0 + 1.0 / 16.0       # trough / peak - 1
+
+
+def test_traj_metrics_omega_of_one_gain_and_one_loss():
+    # +50% then -25% (both exact in binary): Omega = 0.5 / 0.25 = 2, cumulative
+    # return 1/8, drawdown -1/4, RoMaD 1/2, undiscounted return 200 - 150
+    rew, v0 = _traj_from_values([400, 600, 450])
+    m = oracle.trajectory_metrics(rew, None, v0, 1.0, 1.0)[0]
+    assert m[8] == 2.0 and m[0] == 0.125 and m[2] == -0.25 and m[5] == 0.5 and m[9] == 50.0
+
+
+def test_traj_metrics_scale_invariance_and_done_truncation():
+    rng = np.random.default_rng(9)
+    T, N = 40, 6
+    rew = rng.integers(-5000, 6000, (T, N)).astype(np.int64)
+    done = np.zeros((T, N), np.uint8)
+    done[np.arange(N) * 5 + 3, np.arange(N)] = 1
+    a = oracle.trajectory_metrics(rew, done, 10 ** 6, 252.0, 0.97)
+    b = oracle.trajectory_metrics(rew * 7, done, 7 * 10 ** 6, 252.0, 0.97)
+    assert np.array_equal(a[:, :9], b[:, :9]) and np.array_equal(a[:, 10], b[:, 10])
+    assert np.allclose(b[:, 9], 7 * a[:, 9], rtol=1e-14, atol=0)
+    garbage = rew.copy()
+    for i in range(N):
+        garbage[i * 5 + 4:, i] = 123456789               # rows after the first done are ignored
+    c = oracle.trajectory_metrics(garbage, done, 10 ** 6, 252.0, 0.97)
+    assert np.array_equal(a, c)
+    assert np.array_equal(a[:, 10], np.arange(N) * 5 + 4)
+
+
+def test_traj_metrics_agree_with_the_env_episode_metrics():
+    # the same rollout, its metrics from the env's accumulators and from its
+    # stored rewards: cumulative return, Sharpe and drawdown agree bit for bit
+    w = synth.workload_stock_small()
+    e = w.envs
+    r = oracle.stock_run(w.market, e.Ke, e.start, e.W, e.bps, init_cash=e.init_cash, hmax=100, fee_bps=10,
+                         T=w.T, act_i32=synth.prescribed_shares(w.T, e.N, 30, seed=7),
+                         want=("rew", "done", "metrics"))
+    m = oracle.trajectory_metrics(r["rew"], r["done"], e.init_cash, 252.0, 0.99)
+    assert np.array_equal(m[:, :3], r["metrics"])
