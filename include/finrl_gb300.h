@@ -328,6 +328,31 @@ int rollout(fr_env *env, const fr_ensemble *ens, int32_t T,
 int trajectory_metrics(const int64_t *rew, const uint8_t *done, int32_t T, int32_t N, int64_t v0,
                        double ann, double gamma, double *out, void *stream);
 
+/* Exploring rollouts (training producers; no counterpart in the paper's
+ * evaluation, which acts greedily): applied by rollout() to the combined
+ * action before it is discretised and recorded in the trajectory.
+ *  FR_EXPLORE_GAUSSIAN  (stock) a_k + sigma z_k, z_k standard normal;
+ *  FR_EXPLORE_EPS_GREEDY (crypto) the voted action is replaced, with
+ *      probability floor(eps 2^24) / 2^24, by a uniform action in {0, 1, 2}.
+ * Draws are Philox4x32-10 (Salmon et al. 2011) of key = seed and counter
+ * (env, global step, asset, 0) for z (Box-Muller in float32 from
+ * u = ((x >> 8) + 1/2) 2^-24 of the first two words) and (env, global step,
+ * 0, 1) for the greedy draw (replace when word 2 >> 8 is below the
+ * threshold; action floor(3 (word 3 >> 8) / 2^24)).  The global step of a
+ * rollout's first step is the env's exploration counter, which every
+ * rollout advances by T (not part of snapshots).  kind FR_EXPLORE_NONE or a
+ * NULL x switches exploration off. */
+#define FR_EXPLORE_NONE 0
+#define FR_EXPLORE_GAUSSIAN 1
+#define FR_EXPLORE_EPS_GREEDY 2
+typedef struct {
+    int32_t kind;
+    float sigma;              /* >= 0, finite                               */
+    float eps;                /* 0..1                                       */
+    uint64_t seed;
+} fr_explore;
+int env_set_exploration(fr_env *env, const fr_explore *x);
+
 #define FR_PATH_AUTO 0        /* fused kernel when the pair supports it     */
 #define FR_PATH_UNFUSED 1     /* one launch per stage per step              */
 

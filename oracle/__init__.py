@@ -213,6 +213,33 @@ def trajectory_metrics(rew, done, v0: int, ann: float, gamma: float) -> np.ndarr
     return out
 
 
+def philox4x32_10(ctr, key) -> tuple:
+    c = (C.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (C.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    o = (C.c_uint32 * 4)()
+    _load().orc_philox4x32_10(c, k, o)
+    return tuple(o)
+
+
+def uniform24(x: int) -> float:
+    f = _load().orc_uniform24
+    f.restype = C.c_double
+    return f(C.c_uint32(int(x)))
+
+
+def explore_normal(seed: int, e: int, g: int, k: int) -> float:
+    f = _load().orc_explore_normal
+    f.restype = C.c_double
+    return f(C.c_uint64(int(seed)), C.c_uint32(int(e)), C.c_uint32(int(g)), C.c_uint32(int(k)))
+
+
+def explore_greedy(seed: int, e: int, g: int, eps: float, action: int) -> int:
+    f = _load().orc_explore_greedy
+    f.restype = C.c_int32
+    return int(f(C.c_uint64(int(seed)), C.c_uint32(int(e)), C.c_uint32(int(g)), C.c_double(float(eps)),
+                 C.c_int32(int(action))))
+
+
 # ------------------------------------------------------------------ rollouts
 
 def sharpe_softmax_weights(sharpe, threshold: float) -> np.ndarray:

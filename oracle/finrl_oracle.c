@@ -213,6 +213,62 @@ int32_t orc_vote(int32_t M, const uint8_t *ballots)
     return tie ? 1 : best;
 }
 
+/* ------------------------------------------------ exploration randomness */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw 2011): ten rounds of two 32x32
+ * multiplications; each round maps (c0, c1, c2, c3) with key (k0, k1) to
+ * (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)), and the
+ * key is bumped by the Weyl constants between rounds. */
+void orc_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out)
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3], k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const uint64_t p0 = (uint64_t)M0 * c0, p1 = (uint64_t)M1 * c2;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* A uniform in (0, 1) from the top 24 bits: (x >> 8) 2^-24 + 2^-25 (exact in
+ * float32 and double). */
+double orc_uniform24(uint32_t x)
+{
+    return (double)(x >> 8) * (1.0 / 16777216.0) + 1.0 / 33554432.0;
+}
+
+/* Exploration draws of env e at global step g, component k (seed = key):
+ * z = sqrt(-2 ln u0) cos(2 pi u1), Box-Muller (double) from the first two
+ * words of Philox(ctr = (e, g, k, 0)); greedy replacement when
+ * (x2 >> 8) < floor(eps 2^24) -- probability floor(eps 2^24) / 2^24 -- by
+ * the action floor(3 (x3 >> 8) / 2^24), from Philox(ctr = (e, g, 0, 1)). */
+double orc_explore_normal(uint64_t seed, uint32_t e, uint32_t g, uint32_t k)
+{
+    const uint32_t ctr[4] = {e, g, k, 0u}, key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t x[4];
+    orc_philox4x32_10(ctr, key, x);
+    const double u0 = orc_uniform24(x[0]), u1 = orc_uniform24(x[1]);
+    return sqrt(-2.0 * log(u0)) * cos(2.0 * 3.14159265358979323846 * u1);
+}
+
+int32_t orc_explore_greedy(uint64_t seed, uint32_t e, uint32_t g, double eps, int32_t action)
+{
+    const uint32_t ctr[4] = {e, g, 0u, 1u}, key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t x[4];
+    orc_philox4x32_10(ctr, key, x);
+    const uint32_t thr = (uint32_t)(eps * 16777216.0);
+    if ((x[2] >> 8) < thr) return (int32_t)(((uint64_t)(x[3] >> 8) * 3u) >> 24);
+    return action;
+}
+
 /* ----------------------------------------------------------- episode metrics */
 
 typedef struct {

@@ -22,7 +22,8 @@ __all__ = [
     "env_observe", "env_get_state", "env_metrics", "env_snapshot", "env_restore",
     "env_error_count", "env_dims", "ensemble_create", "ensemble_forward",
     "ensemble_act", "ensemble_act_noalloc", "ensemble_device_errors", "rollout", "env_set_rollout_path", "env_set_kernel_timing", "env_last_kernel_ms", "env_set_tile_packing",
-    "env_tile_packing_efficiency", "ensemble_set_weights", "ensemble_validate", "trajectory_metrics", "Server", "fr_server_create", "backtest_submit",
+    "env_tile_packing_efficiency", "ensemble_set_weights", "ensemble_validate", "trajectory_metrics", "env_set_exploration",
+    "EXPLORE_NONE", "EXPLORE_GAUSSIAN", "EXPLORE_EPS_GREEDY", "Server", "fr_server_create", "backtest_submit",
     "backtest_poll", "fr_server_stats", "FrError", "lib",
     "PATH_AUTO", "PATH_UNFUSED",
     "ACT_I32_SHARES", "ACT_F32_UNIT", "ACT_U8_DISCRETE", "PREC_FP32", "PREC_BF16",
@@ -401,3 +402,14 @@ def trajectory_metrics(rew, done=None, *, v0: int = 100_000_000, ann: float = 25
                                         float(ann), float(gamma), _dptr(out, torch.float64, N * 11, "out"),
                                         _stream(stream)), "trajectory_metrics")
     return out
+
+
+EXPLORE_NONE, EXPLORE_GAUSSIAN, EXPLORE_EPS_GREEDY = _lib.EXPLORE_NONE, _lib.EXPLORE_GAUSSIAN, _lib.EXPLORE_EPS_GREEDY
+
+
+def env_set_exploration(env: Env, kind: int = EXPLORE_NONE, *, sigma: float = 0.0, eps: float = 0.0,
+                        seed: int = 0):
+    """Exploring rollouts: Gaussian noise on stock actions or epsilon-greedy on
+    crypto votes, Philox4x32-10 draws keyed by seed (kind EXPLORE_NONE: off)."""
+    x = _lib.Explore(int(kind), float(sigma), float(eps), int(seed) & (2**64 - 1))
+    _lib.check(lib().env_set_exploration(env, C.byref(x)), "env_set_exploration")

@@ -55,6 +55,13 @@ class Traj(C.Structure):
                 ("done", vp)]
 
 
+class Explore(C.Structure):
+    _fields_ = [("kind", i32), ("sigma", C.c_float), ("eps", C.c_float), ("seed", u64)]
+
+
+EXPLORE_NONE, EXPLORE_GAUSSIAN, EXPLORE_EPS_GREEDY = 0, 1, 2
+
+
 class ServerDesc(C.Structure):
     _fields_ = [("market", vp), ("ens", vp), ("capacity", i32), ("chunk_steps", i32),
                 ("init_cash", i64), ("hmax", i32), ("fee_bps", i32), ("pmax", i32)]
@@ -106,6 +113,7 @@ SIGNATURES = {
     "ensemble_act_noalloc": (i32, [vp, vp, i32, vp, vp]),
     "env_set_kernel_timing": (i32, [vp, i32]),
     "env_last_kernel_ms": (i32, [vp, vp]),
+    "env_set_exploration": (i32, [vp, vp]),
     "trajectory_metrics": (i32, [vp, vp, i32, i32, i64, f64, f64, vp, vp]),
     "ensemble_set_weights": (i32, [vp, vp]),
     "ensemble_validate": (i32, [vp, vp, i32, f64, vp, vp, vp]),

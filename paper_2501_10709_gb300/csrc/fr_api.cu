@@ -543,6 +543,26 @@ int env_set_rollout_path(fr_env *env, int32_t path)
     return FR_OK;
 }
 
+int env_set_exploration(fr_env *env, const fr_explore *x)
+{
+    FR_CHECK(env, FR_EINVAL, "env_set_exploration: NULL env");
+    if (!x || x->kind == FR_EXPLORE_NONE) {
+        env->explore_kind = FR_EXPLORE_NONE;
+        return FR_OK;
+    }
+    const bool stock = env->v.task == FR_TASK_STOCK;
+    FR_CHECK(stock ? x->kind == FR_EXPLORE_GAUSSIAN : x->kind == FR_EXPLORE_EPS_GREEDY, FR_EINVAL,
+             "env_set_exploration: %s envs take %s exploration", stock ? "stock" : "crypto",
+             stock ? "Gaussian" : "epsilon-greedy");
+    FR_CHECK(x->sigma >= 0.0f && isfinite(x->sigma) && x->eps >= 0.0f && x->eps <= 1.0f, FR_EINVAL,
+             "env_set_exploration: need finite sigma >= 0 and eps in [0, 1]");
+    env->explore_kind = x->kind;
+    env->explore_sigma = x->sigma;
+    env->explore_thr = (uint32_t)((double)x->eps * 16777216.0);
+    env->explore_seed = x->seed;
+    return FR_OK;
+}
+
 int env_set_tile_packing(fr_env *env, int32_t on)
 {
     FR_CHECK(env, FR_EINVAL, "env_set_tile_packing: NULL env");
@@ -734,6 +754,9 @@ int ensemble_act(const fr_ensemble *e, const float *obs, int32_t n, void *act, v
 }
 
 // ---------------------------------------------------------------- rollout
+static int plain_rollout(fr_env *env, const fr_ensemble *e, int32_t T, const fr_traj *traj, double *metrics,
+                         cudaStream_t s);
+
 int rollout(fr_env *env, const fr_ensemble *e, int32_t T, const fr_traj *traj, double *metrics,
             void *stream)
 {
@@ -753,9 +776,24 @@ int rollout(fr_env *env, const fr_ensemble *e, int32_t T, const fr_traj *traj, d
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if (env->path == FR_PATH_AUTO && e->precision != FR_PREC_FP32) {
-        if (f2_supported(env, e)) return f2_rollout(env, e, T, traj, metrics, s);
-        if (tc_rollout_supported(env, e)) return tc_rollout(env, e, T, traj, metrics, s);
+        if (f2_supported(env, e)) rc = f2_rollout(env, e, T, traj, metrics, s);
+        else if (tc_rollout_supported(env, e)) rc = tc_rollout(env, e, T, traj, metrics, s);
+        else rc = plain_rollout(env, e, T, traj, metrics, s);
+    } else {
+        rc = plain_rollout(env, e, T, traj, metrics, s);
     }
+    if (rc == FR_OK) env->explore_step += (uint32_t)T;
+    return rc;
+}
+
+// plain path: one launch per stage per step
+static int plain_rollout(fr_env *env, const fr_ensemble *e, int32_t T, const fr_traj *traj, double *metrics,
+                         cudaStream_t s)
+{
+    const EnvView &v = env->v;
+    const bool stock = v.task == FR_TASK_STOCK;
+    const int ld = traj->obs_ld ? traj->obs_ld : v.D;
+    int rc = FR_OK;
 
     // plain path: one launch per stage per step
     const int N = v.N, out = e->dims[e->L];
@@ -799,6 +837,8 @@ int rollout(fr_env *env, const fr_ensemble *e, int32_t T, const fr_traj *traj, d
                                         (float *)act_t, v.K, s));
         else
             FR_CUDA(launch_combine_vote(y, (int64_t)N * out, out, e->M, N, out, (uint8_t *)act_t, s));
+        if (env->explore_kind != FR_EXPLORE_NONE)
+            FR_CUDA(launch_explore(v, act_t, explore_of(env, env->explore_step + (uint32_t)t), s));
         FR_CUDA(launch_env_step(v, stock ? FR_ACT_F32_UNIT : FR_ACT_U8_DISCRETE, act_t,
                                 traj->rew ? traj->rew + row : nullptr,
                                 traj->rew_f32 ? traj->rew_f32 + row : nullptr,

@@ -9,6 +9,7 @@
 #include <string>
 
 #include "../../include/finrl_gb300.h"
+#include "fr_rng.cuh"
 
 namespace fr {
 
@@ -119,6 +120,13 @@ struct fr_env {
     int32_t *pack_tile_w;       // device [tiles] longest window of each tile
     float pack_efficiency;      // sum(W_e - 1) / sum over tiles of 128 * (max W - 1)
     int pack_off;               // packing switched off by the caller
+    // exploration of rollouts (kind, sigma, threshold, seed) and the global
+    // step counter of its draws
+    int explore_kind;
+    float explore_sigma;
+    uint32_t explore_thr;
+    uint64_t explore_seed;
+    uint32_t explore_step;
     // optional events around the main rollout kernel
     cudaEvent_t k_ev[2];
     int k_timing;               // record on the next rollouts
@@ -126,6 +134,20 @@ struct fr_env {
 };
 
 namespace fr {
+// The env's exploration settings for a rollout whose first step is global
+// step g0.
+inline Explore explore_of(const fr_env *env, uint32_t g0)
+{
+    Explore x;
+    x.kind = env->explore_kind;
+    x.sigma = env->explore_sigma;
+    x.thr = env->explore_thr;
+    x.k0 = (uint32_t)env->explore_seed;
+    x.k1 = (uint32_t)(env->explore_seed >> 32);
+    x.g0 = g0;
+    return x;
+}
+
 // Record the timing event `which` (0 before, 1 after the main kernel) on s
 // when timing is on.
 cudaError_t env_time_mark(fr_env *env, int which, cudaStream_t s);
@@ -150,6 +172,9 @@ cudaError_t set_max_smem_once(const void *func, int device);
 // ------------------------------------------------------- kernel launchers
 // env kernels (fr_env_kernels.cu)
 cudaError_t launch_env_reset(const EnvView &v, cudaStream_t s);
+// exploration of a step's combined actions in place (stock float [N][K],
+// crypto uint8 [N]); x.g0 is this step's global step
+cudaError_t launch_explore(const EnvView &v, void *act, const Explore &x, cudaStream_t s);
 cudaError_t launch_env_step(const EnvView &v, int kind, const void *act,
                             int64_t *rew, float *rew_f32, uint8_t *done,
                             float *obs, int ld_obs, cudaStream_t s);

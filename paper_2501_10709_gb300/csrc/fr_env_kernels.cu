@@ -265,6 +265,33 @@ cudaError_t launch_env_reset(const EnvView &v, cudaStream_t s)
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void k_explore_stock(float *act, int N, int K, Explore x)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)N * K) return;
+    const int e = (int)(i / K), k = (int)(i % K);
+    act[i] = __fadd_rn(act[i], __fmul_rn(x.sigma, explore_normal(x, (uint32_t)e, x.g0, (uint32_t)k)));
+}
+
+__global__ void k_explore_crypto(uint8_t *act, int N, Explore x)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < N) act[e] = (uint8_t)explore_greedy(x, (uint32_t)e, x.g0, act[e]);
+}
+}  // namespace
+
+cudaError_t launch_explore(const EnvView &v, void *act, const Explore &x, cudaStream_t s)
+{
+    if (x.kind == FR_EXPLORE_GAUSSIAN) {
+        const int64_t n = (int64_t)v.N * v.K;
+        k_explore_stock<<<ceil_div(n, kBlock), kBlock, 0, s>>>((float *)act, v.N, v.K, x);
+    } else if (x.kind == FR_EXPLORE_EPS_GREEDY) {
+        k_explore_crypto<<<ceil_div(v.N, kBlock), kBlock, 0, s>>>((uint8_t *)act, v.N, x);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_env_step(const EnvView &v, int kind, const void *act, int64_t *rew,
                             float *rew_f32, uint8_t *done, float *obs, int ld, cudaStream_t s)
 {

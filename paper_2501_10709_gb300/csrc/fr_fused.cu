@@ -54,6 +54,7 @@ struct FusedArgs {
     uint8_t *tr_done;
     int64_t *vlog;         // [T][N]
     unsigned *err;
+    Explore ex;            // exploration of the combined actions
 };
 
 __host__ __device__ inline int chunks_per_step(const TcPlan &p)
@@ -553,6 +554,14 @@ __device__ void fused_env(const FusedArgs &a, uint32_t tmem, uint8_t *A, uint8_t
                     }
                 }
             }
+            if (a.ex.kind == FR_EXPLORE_GAUSSIAN) {
+                // the executed (and recorded) action explores: a_k + sigma z_k
+#pragma unroll 1
+                for (int k = 0; k < SK; ++k)
+                    act[k] = __fadd_rn(act[k], __fmul_rn(a.ex.sigma, explore_normal(a.ex, (uint32_t)e,
+                                                                                      a.ex.g0 + (uint32_t)s,
+                                                                                      (uint32_t)k)));
+            }
             if (w_act) {
                 float *ao = (float *)a.tr_act + row * SK;
 #pragma unroll
@@ -628,7 +637,8 @@ __device__ void fused_env(const FusedArgs &a, uint32_t tmem, uint8_t *A, uint8_t
                 if (cnt[c] > bc) { bc = cnt[c]; best = c; tie = false; }
                 else if (cnt[c] == bc) tie = true;
             }
-            const int u = tie ? 1 : best;
+            int u = tie ? 1 : best;
+            if (a.ex.kind == FR_EXPLORE_EPS_GREEDY) u = explore_greedy(a.ex, (uint32_t)e, a.ex.g0 + (uint32_t)s, u);
             if (w_act) ((uint8_t *)a.tr_act)[row] = (uint8_t)u;
             if (!done) {
                 const int64_t m0 = __ldg(v.mid + d);
@@ -872,6 +882,7 @@ int tc_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     a.tr_done = traj->done;
     a.vlog = (int64_t *)env->scratch;
     a.err = e->tc->err;
+    a.ex = explore_of(env, env->explore_step);
 
     const uint32_t smem = fused_smem(v.task, p, stages);
     cudaLaunchConfig_t cfg = {};

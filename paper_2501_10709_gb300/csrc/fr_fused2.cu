@@ -94,6 +94,7 @@ struct F2Args {
     uint8_t *tr_done;
     int64_t *vlog;
     unsigned *err;
+    Explore ex;           // exploration of the combined actions
 };
 
 bool f2_plan(const fr_ensemble *e, F2Plan &p)
@@ -203,6 +204,14 @@ __device__ __noinline__ void f2_layer(const F2Layer &l, uint32_t d_tmem, uint32_
         }
     }
     mma_commit(acc);
+}
+
+// The executed (and recorded) action explores: a + sigma z of env e, global
+// step g, asset k.  Out of line: the step loop stays small when exploration
+// is off.
+__device__ __noinline__ float f2_explore(Explore x, float act, uint32_t e, uint32_t g, uint32_t k)
+{
+    return __fadd_rn(act, __fmul_rn(x.sigma, explore_normal(x, e, g, k)));
 }
 
 // --------------------------------------------- owner: one env, warp-wide
@@ -610,6 +619,8 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                     act = __fadd_rn(act, __fmul_rn(wj, __fsub_rn(aj, a0)));
                 }
             }
+            if (a.ex.kind == FR_EXPLORE_GAUSSIAN && e >= 0 && lane < SK2)
+                act = f2_explore(a.ex, act, (uint32_t)e, a.ex.g0 + (uint32_t)s, (uint32_t)lane);
             if (a.tr_act && e >= 0 && lane < SK2) a.tr_act[((int64_t)s * v.N + e) * SK2 + lane] = act;
             const bool live = run[i] && lane < st.Ke;
             float ac = isfinite(act) ? act : 0.0f;
@@ -1040,6 +1051,7 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     a.tr_done = traj->done;
     a.vlog = vlog;
     a.err = e->tc->err;
+    a.ex = explore_of(env, env->explore_step);
     const uint32_t smem = f2_smem(p).total + 1024u;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(2 * p.M), ceil_div(v.N, 128), 1);

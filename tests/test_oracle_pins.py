@@ -329,3 +329,41 @@ def test_traj_metrics_agree_with_the_env_episode_metrics():
                          want=("rew", "done", "metrics"))
     m = oracle.trajectory_metrics(r["rew"], r["done"], e.init_cash, 252.0, 0.99)
     assert np.array_equal(m[:, :3], r["metrics"])
+
+
+# -------------------------------------------- exploration randomness (Philox)
+def test_philox4x32_10_known_answer_vectors():
+    # the known-answer vectors published with Philox4x32-10 (Salmon et al.
+    # 2011, Random123 distribution)
+    assert oracle.philox4x32_10([0, 0, 0, 0], [0, 0]) == (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)
+    assert oracle.philox4x32_10([0xFFFFFFFF] * 4, [0xFFFFFFFF] * 2) == (0x408F276D, 0x41C83B0E, 0xA20BC7C6,
+                                                                       0x6D5451FD)
+    assert oracle.philox4x32_10([0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344], [0xA4093822, 0x299F31D0]) == \
+        (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1)
+
+
+def test_uniform24_is_open_interval_with_exact_ends():
+    assert oracle.uniform24(0) == 2.0 ** -25
+    assert oracle.uniform24(0xFFFFFFFF) == 1.0 - 2.0 ** -25
+    assert oracle.uniform24(0x80000000) == 0.5 + 2.0 ** -25
+
+
+def test_explore_normal_moments():
+    z = np.array([oracle.explore_normal(1234, e, g, k) for e in range(20) for g in range(50) for k in range(20)])
+    n = z.size
+    assert abs(z.mean()) < 4 / math.sqrt(n)
+    assert abs(z.var() - 1.0) < 4 * math.sqrt(2.0 / n)
+    assert abs(np.mean(np.abs(z) < 1.0) - 0.682689) < 4 * math.sqrt(0.2166 / n)
+
+
+def test_explore_greedy_rate_and_uniform_replacements():
+    eps = 0.05
+    a = np.array([oracle.explore_greedy(99, e, g, eps, 7) for e in range(200) for g in range(100)])
+    n = a.size
+    rep = a != 7
+    p = rep.mean()
+    assert abs(p - eps) < 4 * math.sqrt(eps * (1 - eps) / n)
+    counts = np.bincount(a[rep], minlength=3)
+    assert counts.sum() == rep.sum() and len(counts) == 3
+    assert all(abs(c / rep.sum() - 1 / 3) < 4 * math.sqrt(2 / 9 / rep.sum()) for c in counts)
+    assert all(oracle.explore_greedy(99, e, 0, 0.0, 2) == 2 for e in range(100))     # eps = 0: never
