@@ -277,6 +277,28 @@ def env_step_line(fr, ctx, mk, w, dev, stream, N=1 << 20, T=4, warm=2):
             "unit": "GB/s"}
 
 
+def prep_line(fr, ctx, mk, mk_np, e, stream, iters=20):
+    """On-device data preparation: the 8 indicators from OHLC for the bench
+    market and for ten years of daily data (30 assets), and the per-env
+    perturbation draw for a batch shaped like the bench's envs."""
+    import numpy as np
+    import torch
+    from paper_2501_10709_gb300 import synth
+    env = fr.env_create(ctx, mk, start=e.start, window=e.W, n_assets=e.Ke)
+    res = {}
+    for name, m in (("market_1000d", mk_np), ("market_2520d", synth.stock_market(2520, 30, seed=250110709 + 9))):
+        c, h, lo = (torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (m.close, m.high, m.low))
+        T, K = c.shape
+        out = torch.empty(T, 8, K, device=c.device)
+        dt = time_kernel(lambda: fr.market_indicators(c, h, lo, out=out), iters, stream)
+        res[name] = {"days": T, "assets": K, "us": dt * 1e6, "bytes": T * K * (3 * 8 + 8 * 4),
+                     "bound": "FP64 recurrence latency (EMA / Wilder chains, one lane per asset)"}
+    dt = time_kernel(lambda: fr.env_perturb(env, 12345, 100), iters, stream)
+    res["env_perturb"] = {"envs": env.N, "us": dt * 1e6}
+    env.close()
+    return res
+
+
 def uneven_line(fr, ctx, dev, flush, stream, reps=3):
     """4,096 stock envs with asset counts 10-30 and windows 5-250 days, BF16
     fused rollout over the longest window, tiles packed by window vs not."""
@@ -443,6 +465,8 @@ def run_gpu(args):
     env_step["frac"] = env_step["achieved"] / peaks["hbm_gbs"]
     env_step["peak_source"] = f"hbm_gbs, {peak_src}"
 
+    prep = prep_line(fr, ctx, mk, w.market, w.envs, stream)
+
     # serving (backtest_submit / backtest_poll): p50 / p99 request latency
     serving = serving_line(fr, ctx, mk, {"fused_bf16": ens_bf16, "plain_fp32": ens_fp32}) \
         if not args.no_serving else None
@@ -502,6 +526,7 @@ def run_gpu(args):
                      "actor_kernel_large_batch": {"rows": nb, "achieved": big_tflops,
                                                   "frac": big_tflops / peak},
                      "env_step_kernel": env_step},
+        "data_prep": prep,
         "crypto_c3": crypto,
         "uneven_c4": uneven,
         "gpu_launches": launches_per_rollout * args.steps,

@@ -93,10 +93,47 @@ typedef struct {
     const int64_t *mid;       /* host                                       */
     const uint8_t *spread;    /* host                                       */
     const float *fac;         /* host                                       */
+    const int64_t *high;      /* host, stock with ind == NULL: see below    */
+    const int64_t *low;       /* host                                       */
 } fr_market_desc;
 
+/* A stock market given ind == NULL, n_ind == 8 and daily high / low
+ * (int64 cents [n_days][n_assets], low <= close <= high) computes its
+ * indicator table on the device with market_indicators (below) instead of
+ * reading one; the high / low tables are not kept. */
 int fr_market_create(fr_ctx *ctx, const fr_market_desc *desc, fr_market **out);
 void fr_market_destroy(fr_market *m);
+/* Copy a stock market's resident indicator table (float32
+ * [n_days][n_ind][n_assets]) to dst (host or device), synchronously. */
+int fr_market_copy_indicators(const fr_market *m, float *dst);
+
+/* The 8 technical indicators of the state's f_t (Sec. 3.1; the list of
+ * Sec. 6.1), computed on the device from daily close / high / low (device
+ * int64 cents [n_days][n_assets]) into ind (device float32
+ * [n_days][8][n_assets], indicator-major within a day), each from data up to
+ * its own day only:
+ *   0  MACD(12, 26) / c          4  CCI-30 / 100
+ *   1  (SMA20 + 2 sd20) / c - 1  5  DX-30 / 100
+ *   2  (SMA20 - 2 sd20) / c - 1  6  SMA30 / c - 1
+ *   3  RSI-30 / 100              7  SMA60 / c - 1
+ * Textbook forms in FP64, each operation rounded separately (no fused
+ * multiply-add), stored as the float32 rounding of the double:
+ *  - windows of n trailing days, shorter at the start (t + 1 < n), summed
+ *    from the oldest; sd the population deviation;
+ *  - EMA e_t = a c_t + (1 - a) e_{t-1}, a = 2 / (n + 1), e_0 = c_0;
+ *  - Wilder w_t = w_{t-1} + (x_t - w_{t-1}) / 30, w_0 = x_0;
+ *  - RSI = 100 - 100 / (1 + G / L) over the smoothed gains G and losses L of
+ *    c_t - c_{t-1} (0 at t = 0); 100 when L = 0 < G; 50 when G = L = 0;
+ *  - CCI = (tp - SMA30(tp)) / (0.015 MAD30(tp)), tp = (h + l + c) / 3, 0 when
+ *    the mean absolute deviation is 0;
+ *  - DX = 100 |DI+ - DI-| / (DI+ + DI-), DI = 100 DM / TR over the smoothed
+ *    directional movements (DM+ = h_t - h_{t-1} when it exceeds l_{t-1} - l_t
+ *    and 0, DM- symmetric, both 0 at t = 0) and true range max(h - l,
+ *    |h - c_{t-1}|, |l - c_{t-1}|) with c_{-1} = c_0; 0 when DI+ + DI- = 0.
+ * Closes must be >= 1.  Asynchronous on `stream`; the tables are borrowed
+ * until it completes.  FR_EINVAL for NULL tables or sizes < 1. */
+int market_indicators(const int64_t *close, const int64_t *high, const int64_t *low, int32_t n_days,
+                      int32_t n_assets, float *ind, void *stream);
 
 /* ------------------------------------------------------------ environments */
 typedef struct fr_env fr_env;
@@ -353,6 +390,20 @@ typedef struct {
 } fr_explore;
 int env_set_exploration(fr_env *env, const fr_explore *x);
 
+/* Draw the per-env price perturbations of Sec. 5.1 on the device (each env
+ * sees prices shifted by up to +-bps_range basis points per asset; the paper
+ * uses +-1%, bps_range = 100).  For env e and asset k < the market's K:
+ *   z = splitmix64(seed ^ splitmix64(e << 8 | k)),
+ *   bps[e][k] = z mod (2 bps_range + 1) - bps_range,
+ * splitmix64 the SplitMix64 output function (Steele, Lea, Flood, OOPSLA
+ * 2014): x += 0x9E3779B97F4A7C15, then x ^= x >> 30, x *= 0xBF58476D1CE4E5B9,
+ * x ^= x >> 27, x *= 0x94D049BB133111EB, x ^= x >> 31.  Assets >= K get 0.
+ * The same draw as backtest_submit's, request env index for e.  Replaces the
+ * env's bps table (asynchronous on `stream`); prices use it from the next
+ * step on, so call it before env_reset for a fresh episode.  Stock envs only;
+ * bps_range in 0..100 (FR_EINVAL otherwise). */
+int env_perturb(fr_env *env, uint64_t seed, int32_t bps_range, void *stream);
+
 #define FR_PATH_AUTO 0        /* fused kernel when the pair supports it     */
 #define FR_PATH_UNFUSED 1     /* one launch per stage per step              */
 
@@ -418,7 +469,8 @@ void fr_server_destroy(fr_server *srv);
  * start + i*start_stride .. + window - 1; stock envs trade the first
  * n_assets assets with per-env per-asset price perturbations drawn from
  * `seed` uniformly in [-bps_range, bps_range] basis points (Sec. 5.1;
- * SplitMix64 of seed, env and asset).  metrics: caller-owned host buffer
+ * env_perturb's rule, drawn on the device, with e the env's index within the
+ * request).  metrics: caller-owned host buffer
  * double [n_envs][3] (cumulative return, Sharpe, max drawdown, as
  * env_metrics), written by the server before the request reports done; it
  * must stay valid until then.  want_traj must be 0: the server returns

@@ -240,6 +240,34 @@ def explore_greedy(seed: int, e: int, g: int, eps: float, action: int) -> int:
                  C.c_int32(int(action))))
 
 
+def splitmix64(x: int) -> int:
+    f = _load().orc_splitmix64
+    f.restype = C.c_uint64
+    return int(f(C.c_uint64(int(x) & (2**64 - 1))))
+
+
+def market_table(market) -> np.ndarray:
+    """A stock market's indicator table: its own ``ind`` when set, else the
+    8 indicators from its close / high / low."""
+    ind = getattr(market, "ind", None)
+    return indicators(market.close, market.high, market.low) if ind is None else ind
+
+
+def perturb_bps(seed: int, e: int, k: int, R: int) -> int:
+    f = _load().orc_perturb_bps
+    f.restype = C.c_int32
+    return int(f(C.c_uint64(int(seed) & (2**64 - 1)), C.c_uint32(int(e)), C.c_uint32(int(k)), C.c_int32(int(R))))
+
+
+def indicators(close, high, low) -> np.ndarray:
+    """int64 [T][K] close/high/low -> float32 [T][8][K] (Sec. 6.1 indicators)."""
+    c, h, lo = _c(close, np.int64), _c(high, np.int64), _c(low, np.int64)
+    T, K = c.shape
+    out = np.empty((T, 8, K), np.float32)
+    _load().orc_indicators(T, K, _p(c), _p(h), _p(lo), _p(out))
+    return out
+
+
 # ------------------------------------------------------------------ rollouts
 
 def sharpe_softmax_weights(sharpe, threshold: float) -> np.ndarray:
@@ -286,12 +314,14 @@ def stock_run(market, Ke, start, W, bps, *, init_cash: int, hmax: int,
                     "metrics", "act")) -> dict:
     """Run T steps of N stock envs from reset.
 
-    market: object with ``close`` int64[n_days][K] and ``ind`` f32[n_days][I][K].
+    market: object with ``close`` int64[n_days][K] and either an indicator
+    table ``ind`` f32[n_days][I][K] or ``high`` / ``low`` (the table is then
+    the oracle's own ``indicators``).
     Exactly one action source: act_i32[T][N][K] (mode 0), act_f32[T][N][K]
     (mode 1) or ensemble = (dims, params[M][P] f32, weights or None) (mode 2).
     """
     close = _c(market.close, np.int64)
-    ind = _c(market.ind, np.float32)
+    ind = _c(market_table(market), np.float32)
     n_days, K = close.shape
     I = ind.shape[1]
     D = 1 + 2 * K + I * K

@@ -269,6 +269,120 @@ int32_t orc_explore_greedy(uint64_t seed, uint32_t e, uint32_t g, double eps, in
     return action;
 }
 
+/* ----------------------------------------------- on-device data preparation */
+/* SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014; Stafford's
+ * mix13 finaliser): add the golden gamma, then three xor-shift / multiply
+ * steps.  Written from the published definition. */
+uint64_t orc_splitmix64(uint64_t x)
+{
+    x = x + 0x9E3779B97F4A7C15ull;
+    x = x ^ (x >> 30);
+    x = x * 0xBF58476D1CE4E5B9ull;
+    x = x ^ (x >> 27);
+    x = x * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+/* Sec. 5.1 per-env +-1% price change (R = 100 bps): env e, asset k draws
+ * z = splitmix64(seed ^ splitmix64(e * 256 + k)) and takes z mod (2R + 1) - R. */
+int32_t orc_perturb_bps(uint64_t seed, uint32_t e, uint32_t k, int32_t R)
+{
+    const uint64_t z = orc_splitmix64(seed ^ orc_splitmix64((uint64_t)e * 256u + (uint64_t)k));
+    return (int32_t)(z % (uint64_t)(2 * R + 1)) - R;
+}
+
+/* mean of x[t-m+1 .. t] (m = min(n, t + 1)), summed from the oldest */
+static double win_mean(const double *x, int t, int n, int K, int k)
+{
+    const int t0 = t - n + 1 > 0 ? t - n + 1 : 0;
+    double s = 0.0;
+    for (int u = t0; u <= t; ++u) s += x[(int64_t)u * K + k];
+    return s / (double)(t - t0 + 1);
+}
+
+/* The 8 technical indicators of Sec. 6.1 (textbook forms) from data up to
+ * each day, stored scale-free as float32 ind[day][8][K]:
+ *   MACD(12, 26) / c, (SMA20 + 2 sd20) / c - 1, (SMA20 - 2 sd20) / c - 1,
+ *   RSI-30 / 100, CCI-30 / 100, DX-30 / 100, SMA30 / c - 1, SMA60 / c - 1.
+ * In double: windows over up to n trailing days (shorter at the start),
+ * summed from the oldest; sd population; EMA e_t = a c_t + (1 - a) e_{t-1},
+ * a = 2 / (n + 1), e_0 = c_0; Wilder w_t = w_{t-1} + (x_t - w_{t-1}) / 30,
+ * w_0 = x_0; RSI from Wilder gains / losses of c_t - c_{t-1} (100 without
+ * losses, 50 without either); CCI = (tp - SMA30(tp)) / (0.015 MAD), tp =
+ * (h + l + c) / 3, 0 when MAD = 0; DX = 100 |DI+ - DI-| / (DI+ + DI-) from
+ * Wilder DM+ / DM- / TR (TR with c_{-1} = c_0), 0 when DI+ + DI- = 0. */
+void orc_indicators(int32_t T, int32_t K, const int64_t *close, const int64_t *high, const int64_t *low,
+                    float *ind)
+{
+    double *c = (double *)malloc(sizeof(double) * (size_t)T * K);
+    double *tp = (double *)malloc(sizeof(double) * (size_t)T * K);
+    for (int64_t i = 0; i < (int64_t)T * K; ++i) {
+        c[i] = (double)close[i];
+        tp[i] = ((double)high[i] + (double)low[i] + (double)close[i]) / 3.0;
+    }
+    for (int k = 0; k < K; ++k) {
+        double e12 = c[k], e26 = c[k];
+        const double a12 = 2.0 / 13.0, a26 = 2.0 / 27.0;
+        double gain = 0.0, loss = 0.0, str = 0.0, spd = 0.0, snd = 0.0;
+        for (int t = 0; t < T; ++t) {
+            const double ct = c[(int64_t)t * K + k];
+            const double ht = (double)high[(int64_t)t * K + k], lt = (double)low[(int64_t)t * K + k];
+            const double cp = t > 0 ? c[(int64_t)(t - 1) * K + k] : ct;
+            if (t > 0) {
+                e12 = a12 * ct + (1.0 - a12) * e12;
+                e26 = a26 * ct + (1.0 - a26) * e26;
+            }
+            const double d = ct - cp;
+            const double g = d > 0.0 ? d : 0.0, l = d < 0.0 ? -d : 0.0;
+            const double up = t > 0 ? ht - (double)high[(int64_t)(t - 1) * K + k] : 0.0;
+            const double dn = t > 0 ? (double)low[(int64_t)(t - 1) * K + k] - lt : 0.0;
+            const double pdm = (up > dn && up > 0.0) ? up : 0.0, ndm = (dn > up && dn > 0.0) ? dn : 0.0;
+            double tr = ht - lt;
+            if (fabs(ht - cp) > tr) tr = fabs(ht - cp);
+            if (fabs(lt - cp) > tr) tr = fabs(lt - cp);
+            if (t == 0) {
+                gain = g; loss = l; str = tr; spd = pdm; snd = ndm;
+            } else {
+                gain = gain + (g - gain) / 30.0;
+                loss = loss + (l - loss) / 30.0;
+                str = str + (tr - str) / 30.0;
+                spd = spd + (pdm - spd) / 30.0;
+                snd = snd + (ndm - snd) / 30.0;
+            }
+            const double rsi = (gain == 0.0 && loss == 0.0) ? 50.0
+                               : (loss > 0.0 ? 100.0 - 100.0 / (1.0 + gain / loss) : 100.0);
+            const double sma20 = win_mean(c, t, 20, K, k);
+            const int t20 = t - 19 > 0 ? t - 19 : 0;
+            double v20 = 0.0;
+            for (int u = t20; u <= t; ++u) {
+                const double z = c[(int64_t)u * K + k] - sma20;
+                v20 += z * z;
+            }
+            const double sd20 = sqrt(v20 / (double)(t - t20 + 1));
+            const double smatp = win_mean(tp, t, 30, K, k);
+            const int t30 = t - 29 > 0 ? t - 29 : 0;
+            double mad = 0.0;
+            for (int u = t30; u <= t; ++u) mad += fabs(tp[(int64_t)u * K + k] - smatp);
+            mad = mad / (double)(t - t30 + 1);
+            const double cci = mad > 0.0 ? (tp[(int64_t)t * K + k] - smatp) / (0.015 * mad) : 0.0;
+            const double pdi = 100.0 * spd / (str > 0.0 ? str : 1.0), ndi = 100.0 * snd / (str > 0.0 ? str : 1.0);
+            const double dx = pdi + ndi > 0.0 ? 100.0 * fabs(pdi - ndi) / (pdi + ndi) : 0.0;
+            const double sma30 = win_mean(c, t, 30, K, k), sma60 = win_mean(c, t, 60, K, k);
+            float *o = ind + (int64_t)t * 8 * K + k;
+            o[0 * K] = (float)((e12 - e26) / ct);
+            o[1 * K] = (float)((sma20 + 2.0 * sd20) / ct - 1.0);
+            o[2 * K] = (float)((sma20 - 2.0 * sd20) / ct - 1.0);
+            o[3 * K] = (float)(rsi / 100.0);
+            o[4 * K] = (float)(cci / 100.0);
+            o[5 * K] = (float)(dx / 100.0);
+            o[6 * K] = (float)(sma30 / ct - 1.0);
+            o[7 * K] = (float)(sma60 / ct - 1.0);
+        }
+    }
+    free(c);
+    free(tp);
+}
+
 /* ----------------------------------------------------------- episode metrics */
 
 typedef struct {

@@ -114,16 +114,28 @@ def fr_ctx_create(device: int = 0, hbm_budget_bytes: int = 0) -> Ctx:
     return Ctx(out.value)
 
 
-def fr_market_create(ctx: Ctx, market) -> Market:
-    """market: an object with close/ind (stock) or mid/spread/fac (crypto)."""
+def fr_market_create(ctx: Ctx, market, *, device_indicators: bool = False) -> Market:
+    """market: an object with close/high/low and optionally an indicator
+    table ind (stock), or mid/spread/fac (crypto).  A stock market without
+    ind, or with device_indicators, gets its 8 indicators computed on the
+    device from close/high/low (market_indicators)."""
     d = _lib.MarketDesc()
     keep = []
     if hasattr(market, "close"):
+        device_indicators = device_indicators or getattr(market, "ind", None) is None
         close = np.ascontiguousarray(market.close, np.int64)
-        ind = np.ascontiguousarray(market.ind, np.float32)
-        keep += [close, ind]
-        d.task, d.n_days, d.n_assets, d.n_ind = TASK_STOCK, close.shape[0], close.shape[1], ind.shape[1]
-        d.close, d.ind = _hptr(close), _hptr(ind)
+        d.task, d.n_days, d.n_assets = TASK_STOCK, close.shape[0], close.shape[1]
+        d.close = _hptr(close)
+        keep.append(close)
+        if device_indicators:
+            high = np.ascontiguousarray(market.high, np.int64)
+            low = np.ascontiguousarray(market.low, np.int64)
+            keep += [high, low]
+            d.n_ind, d.high, d.low = 8, _hptr(high), _hptr(low)
+        else:
+            ind = np.ascontiguousarray(market.ind, np.float32)
+            keep.append(ind)
+            d.n_ind, d.ind = ind.shape[1], _hptr(ind)
     else:
         mid = np.ascontiguousarray(market.mid, np.int64)
         spread = np.ascontiguousarray(market.spread, np.uint8)
@@ -135,7 +147,38 @@ def fr_market_create(ctx: Ctx, market) -> Market:
     _lib.check(lib().fr_market_create(ctx, C.byref(d), C.byref(out)), "fr_market_create")
     m = Market(out.value, keep=(ctx,))
     m.task = d.task
+    if d.task == TASK_STOCK:
+        m.shape_ind = (d.n_days, d.n_ind, d.n_assets)
     return m
+
+
+def fr_market_indicators(market: Market) -> np.ndarray:
+    """A stock market's resident indicator table, float32 [n_days][n_ind][K]."""
+    out = np.empty(market.shape_ind, np.float32)
+    _lib.check(lib().fr_market_copy_indicators(market, _hptr(out)), "fr_market_copy_indicators")
+    return out
+
+
+def market_indicators(close, high, low, out=None, stream=None):
+    """The 8 technical indicators from device int64 close/high/low [T][K]
+    -> float32 [T][8][K] on the device."""
+    import torch
+    T, K = close.shape
+    if out is None:
+        out = torch.empty(T, 8, K, dtype=torch.float32, device=close.device)
+    _lib.check(lib().market_indicators(_dptr(close, torch.int64, T * K, "close"),
+                                       _dptr(high, torch.int64, T * K, "high"),
+                                       _dptr(low, torch.int64, T * K, "low"), int(T), int(K),
+                                       _dptr(out, torch.float32, T * 8 * K, "out"), _stream(stream)),
+               "market_indicators")
+    return out
+
+
+def env_perturb(env: Env, seed: int, bps_range: int = 100, stream=None):
+    """Draw the env batch's per-env, per-asset price perturbations on the
+    device (uniform in [-bps_range, bps_range] basis points, SplitMix64)."""
+    _lib.check(lib().env_perturb(env, C.c_uint64(int(seed) & (2**64 - 1)), int(bps_range), _stream(stream)),
+               "env_perturb")
 
 
 def env_create(ctx: Ctx, market: Market, *, start, window, n_assets=None, bps=None,

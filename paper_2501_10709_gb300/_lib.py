@@ -28,7 +28,7 @@ size_t = C.c_size_t
 class MarketDesc(C.Structure):
     _fields_ = [("task", i32), ("n_days", i32), ("n_assets", i32), ("n_ind", i32),
                 ("close", vp), ("ind", vp), ("n_seconds", i64), ("mid", vp),
-                ("spread", vp), ("fac", vp)]
+                ("spread", vp), ("fac", vp), ("high", vp), ("low", vp)]
 
 
 class EnvDesc(C.Structure):
@@ -124,6 +124,9 @@ SIGNATURES = {
     "backtest_submit": (i32, [vp, vp, vp]),
     "backtest_poll": (i32, [vp, u64, vp, vp]),
     "fr_server_stats_get": (i32, [vp, vp]),
+    "fr_market_copy_indicators": (i32, [vp, vp]),
+    "market_indicators": (i32, [vp, vp, vp, i32, i32, vp, vp]),
+    "env_perturb": (i32, [vp, u64, i32, vp]),
 }
 
 _lock = threading.Lock()

@@ -240,9 +240,10 @@ int fr_market_create(fr_ctx *ctx, const fr_market_desc *d, fr_market **out)
     m->ctx = ctx;
     m->task = d->task;
     if (d->task == FR_TASK_STOCK) {
+        const bool prep = !d->ind && d->n_ind == 8 && d->high && d->low;
         if (!(d->n_days >= 2 && d->n_assets >= 1 && d->n_assets <= FR_MAX_ASSETS &&
               d->n_ind >= 0 && d->n_ind <= FR_MAX_INDICATORS && d->close &&
-              (d->ind || d->n_ind == 0))) {
+              (d->ind || d->n_ind == 0 || prep))) {
             delete m;
             set_error("fr_market_create: stock market needs n_days >= 2, 1 <= n_assets <= 32, "
                       "0 <= n_ind <= 16 and host tables");
@@ -268,10 +269,34 @@ int fr_market_create(fr_ctx *ctx, const fr_market_desc *d, fr_market **out)
         }
         m->bytes = cb + (ib ? ib : 16);
         cudaError_t e = cudaMemcpy(m->close, d->close, cb, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && ib) e = cudaMemcpy(m->ind, d->ind, ib, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && ib && !prep) e = cudaMemcpy(m->ind, d->ind, ib, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             fr_market_destroy(m);
             return cuda_fail(e, "fr_market_create upload");
+        }
+        if (prep) {
+            for (int64_t i = 0; i < (int64_t)d->n_days * d->n_assets; ++i) {
+                if (!(d->low[i] <= d->close[i] && d->close[i] <= d->high[i])) {
+                    fr_market_destroy(m);
+                    set_error("fr_market_create: low <= close <= high fails at %lld", (long long)i);
+                    return FR_EINVAL;
+                }
+            }
+            // high / low staged in one temporary allocation, freed after the launch completes
+            int64_t *hl = nullptr;
+            if ((rc = dev_alloc(ctx, (void **)&hl, 2 * cb))) {
+                fr_market_destroy(m);
+                return rc;
+            }
+            e = cudaMemcpy(hl, d->high, cb, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(hl + cb / 8, d->low, cb, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = launch_indicators(m->close, hl, hl + cb / 8, m->n_days, m->K, m->ind, 0);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+            dev_free(ctx, hl, 2 * cb);
+            if (e != cudaSuccess) {
+                fr_market_destroy(m);
+                return cuda_fail(e, "fr_market_create indicators");
+            }
         }
     } else if (d->task == FR_TASK_CRYPTO) {
         if (!(d->n_seconds >= 2 && d->mid && d->spread && d->fac)) {
@@ -309,6 +334,17 @@ int fr_market_create(fr_ctx *ctx, const fr_market_desc *d, fr_market **out)
         return FR_EINVAL;
     }
     *out = m;
+    return FR_OK;
+}
+
+int fr_market_copy_indicators(const fr_market *m, float *dst)
+{
+    FR_CHECK(m && dst, FR_EINVAL, "fr_market_copy_indicators: NULL argument");
+    FR_CHECK(m->task == FR_TASK_STOCK, FR_EINVAL, "fr_market_copy_indicators: stock markets only");
+    int rc = use_device(m->ctx);
+    if (rc) return rc;
+    const uint64_t ib = (uint64_t)m->n_days * m->I * m->K * 4;
+    if (ib) FR_CUDA(cudaMemcpy(dst, m->ind, ib, cudaMemcpyDefault));
     return FR_OK;
 }
 

@@ -180,6 +180,9 @@ cudaError_t launch_env_step(const EnvView &v, int kind, const void *act,
                             float *obs, int ld_obs, cudaStream_t s);
 cudaError_t launch_env_observe(const EnvView &v, float *obs, int ld, cudaStream_t s);
 cudaError_t launch_env_metrics(const EnvView &v, double *out, cudaStream_t s);
+// the 8 indicators of a market from device close / high / low (fr_prep.cu)
+cudaError_t launch_indicators(const int64_t *close, const int64_t *high, const int64_t *low, int T, int K,
+                              float *ind, cudaStream_t s);
 cudaError_t launch_env_get_state(const EnvView &v, int64_t *cash, int32_t *hold,
                                  int32_t *steps, uint8_t *done, cudaStream_t s);
 

@@ -1,4 +1,5 @@
-// fr_rng.cuh -- counter-based randomness of the exploring rollouts.
+// fr_rng.cuh -- counter-based randomness: the exploring rollouts' draws and
+// the per-env price perturbations.
 //
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
 // easy as 1, 2, 3", SC 2011): ten rounds, each mapping counter words
@@ -35,6 +36,26 @@ __host__ __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1,
     out[1] = c1;
     out[2] = c2;
     out[3] = c3;
+}
+
+// SplitMix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014, with Stafford's mix13 finaliser): advance by the
+// golden gamma, then three xor-shift / multiply rounds.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+// The per-env price perturbation of Sec. 5.1 (+-1% at R = 100): basis points
+// of env i, asset k, uniform on [-R, R] as z mod (2R + 1) - R with
+// z = splitmix64(seed ^ splitmix64(i << 8 | k)).
+__host__ __device__ __forceinline__ int16_t perturb_bps(uint64_t seed, uint32_t i, uint32_t k, int R)
+{
+    const uint64_t z = splitmix64(seed ^ splitmix64(((uint64_t)i << 8) | (uint64_t)k));
+    return (int16_t)((int64_t)(z % (uint64_t)(2 * R + 1)) - R);
 }
 
 // Exploration parameters as the kernels take them.

@@ -24,22 +24,34 @@
 namespace fr {
 namespace {
 
-__global__ void k_slot_assign(EnvView v, const int32_t *slot, const int32_t *cst, const int16_t *bps, int n)
+// Constants of one admitted env: its window, asset count and the draw of
+// its price perturbations (request seed, range, index in the request).
+struct SlotCst {
+    int32_t start, window, ke, range, index, pad;
+    uint64_t seed;
+};
+
+// Reset admitted slots; stock slots draw their perturbations on the device
+// (perturb_bps of the request's seed for assets below the market's K).
+__global__ void k_slot_assign(EnvView v, const int32_t *slot, const SlotCst *cst, int n)
 {
     const int i = blockIdx.x;
     if (i >= n) return;
     const int e = slot[i];
     const int lane = threadIdx.x;
+    const SlotCst c = cst[i];
     if (v.task == FR_TASK_STOCK) {
         v.hold[(int64_t)e * KP + lane] = 0;
-        ((int16_t *)v.bps)[(int64_t)e * KP + lane] = bps[(int64_t)i * KP + lane];
+        ((int16_t *)v.bps)[(int64_t)e * KP + lane] =
+            (lane < v.K && c.range > 0) ? perturb_bps(c.seed, (uint32_t)c.index, (uint32_t)lane, c.range)
+                                        : (int16_t)0;
     } else if (lane == 0) {
         v.hold[e] = 0;
     }
     if (lane == 0) {
-        ((int32_t *)v.start)[e] = cst[3 * i + 0];
-        ((int32_t *)v.W)[e] = cst[3 * i + 1];
-        ((int32_t *)v.Ke)[e] = cst[3 * i + 2];
+        ((int32_t *)v.start)[e] = c.start;
+        ((int32_t *)v.W)[e] = c.window;
+        ((int32_t *)v.Ke)[e] = c.ke;
         v.cash[e] = v.init_cash;
         v.t[e] = 0;
         v.done[e] = 0;
@@ -56,14 +68,6 @@ __global__ void k_slot_park(EnvView v, const int32_t *slot, int n)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) v.done[slot[i]] = 1;
-}
-
-inline uint64_t splitmix64(uint64_t x)
-{
-    x += 0x9E3779B97F4A7C15ull;
-    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-    return x ^ (x >> 31);
 }
 
 double now_s()
@@ -93,12 +97,9 @@ struct fr_server {
     fr_env *env = nullptr;
     cudaStream_t stream = nullptr;
     // device / pinned staging
-    int32_t *d_slot = nullptr, *d_cst = nullptr;
-    int16_t *d_bps = nullptr;
-    double *d_met = nullptr;
-    int32_t *h_slot = nullptr, *h_cst = nullptr;
-    int16_t *h_bps = nullptr;
-    double *h_met = nullptr;
+    int32_t *d_slot = nullptr, *h_slot = nullptr;
+    SlotCst *d_cst = nullptr, *h_cst = nullptr;
+    double *d_met = nullptr, *h_met = nullptr;
     std::vector<int32_t> ke_mirror;
     // scheduler state (under mu)
     std::mutex mu;
@@ -131,37 +132,32 @@ void release_all(fr_server *s)
 // slots; returns a CUDA status.
 cudaError_t assign(fr_server *s, const std::vector<SrvReq *> &adm, bool &ke_changed)
 {
-    const int K = s->env->v.K;
     const bool stock = s->env->v.task == FR_TASK_STOCK;
     int n = 0;
     for (SrvReq *q : adm) {
         const fr_request &r = q->r;
-        const int ke = stock ? (r.n_assets > 0 ? r.n_assets : K) : 1;
+        const int ke = stock ? (r.n_assets > 0 ? r.n_assets : s->env->v.K) : 1;
         for (int i = 0; i < r.n_envs; ++i, ++n) {
             const int32_t e = q->slots[i];
             s->h_slot[n] = e;
-            s->h_cst[3 * n + 0] = r.start + i * r.start_stride;
-            s->h_cst[3 * n + 1] = r.window;
-            s->h_cst[3 * n + 2] = ke;
+            SlotCst &c = s->h_cst[n];
+            c.start = r.start + i * r.start_stride;
+            c.window = r.window;
+            c.ke = ke;
+            c.range = stock ? r.bps_range : 0;
+            c.index = i;
+            c.pad = 0;
+            c.seed = r.seed;
             if (s->ke_mirror[e] != ke) ke_changed = true;
             s->ke_mirror[e] = ke;
-            for (int k = 0; k < KP; ++k) {
-                int16_t b = 0;
-                if (stock && k < K && r.bps_range > 0) {
-                    const uint64_t z = splitmix64(r.seed ^ splitmix64(((uint64_t)i << 8) | (uint64_t)k));
-                    b = (int16_t)((int64_t)(z % (uint64_t)(2 * r.bps_range + 1)) - r.bps_range);
-                }
-                s->h_bps[(size_t)n * KP + k] = b;
-            }
         }
     }
     if (n == 0) return cudaSuccess;
     cudaError_t e = cudaMemcpyAsync(s->d_slot, s->h_slot, 4ull * n, cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_cst, s->h_cst, 12ull * n, cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s->d_bps, s->h_bps, 2ull * KP * n, cudaMemcpyHostToDevice, s->stream);
+        e = cudaMemcpyAsync(s->d_cst, s->h_cst, sizeof(SlotCst) * n, cudaMemcpyHostToDevice, s->stream);
     if (e != cudaSuccess) return e;
-    k_slot_assign<<<n, KP, 0, s->stream>>>(s->env->v, s->d_slot, s->d_cst, s->d_bps, n);
+    k_slot_assign<<<n, KP, 0, s->stream>>>(s->env->v, s->d_slot, s->d_cst, n);
     e = cudaGetLastError();
     // the staging buffers are reused by the next admission: wait for the copies
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -298,11 +294,9 @@ void server_free(fr_server *s)
     if (s->env) env_destroy(s->env);
     if (s->d_slot) cudaFree(s->d_slot);
     if (s->d_cst) cudaFree(s->d_cst);
-    if (s->d_bps) cudaFree(s->d_bps);
     if (s->d_met) cudaFree(s->d_met);
     if (s->h_slot) cudaFreeHost(s->h_slot);
     if (s->h_cst) cudaFreeHost(s->h_cst);
-    if (s->h_bps) cudaFreeHost(s->h_bps);
     if (s->h_met) cudaFreeHost(s->h_met);
     if (s->stream) cudaStreamDestroy(s->stream);
     release_all(s);
@@ -354,12 +348,10 @@ int fr_server_create(fr_ctx *ctx, const fr_server_desc *d, fr_server **out)
     s->ke_mirror.assign(N, stock ? m->K : 1);
     cudaError_t ce = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (ce == cudaSuccess) ce = cudaMalloc(&s->d_slot, 4ull * N);
-    if (ce == cudaSuccess) ce = cudaMalloc(&s->d_cst, 12ull * N);
-    if (ce == cudaSuccess) ce = cudaMalloc(&s->d_bps, 2ull * KP * N);
+    if (ce == cudaSuccess) ce = cudaMalloc(&s->d_cst, sizeof(SlotCst) * N);
     if (ce == cudaSuccess) ce = cudaMalloc(&s->d_met, 24ull * N);
     if (ce == cudaSuccess) ce = cudaMallocHost(&s->h_slot, 4ull * N);
-    if (ce == cudaSuccess) ce = cudaMallocHost(&s->h_cst, 12ull * N);
-    if (ce == cudaSuccess) ce = cudaMallocHost(&s->h_bps, 2ull * KP * N);
+    if (ce == cudaSuccess) ce = cudaMallocHost(&s->h_cst, sizeof(SlotCst) * N);
     if (ce == cudaSuccess) ce = cudaMallocHost(&s->h_met, 24ull * N);
     if (ce != cudaSuccess) {
         server_free(s);

@@ -4,14 +4,16 @@ The paper trains and samples on daily OHLCV of the 30 Dow Jones stocks with
 MACD, Bollinger, RSI, CCI, DX and SMA indicators (Sec. 6.1, stock data) and on
 second-level Bitcoin limit-order-book data reduced to 8 factors (Sec. 6.1,
 cryptocurrency data).  Neither dataset exists here, so this module generates
-stand-ins of the same shape: geometric-Brownian-motion prices in integer
-cents, textbook indicators stored scale-free, and backward-looking momentum
-factors.  It also draws actor weights, environment start days, per-asset
-basis-point perturbations and prescribed action sequences.
+stand-ins of the same shape: geometric-Brownian-motion daily OHLCV in
+integer cents (the technical indicators are computed from them, by the
+library on the device and by the oracle on the CPU, not here) and
+backward-looking momentum factors in place of the 8 learned crypto factors.
+It also draws actor weights, environment start days, per-asset basis-point
+perturbations and prescribed action sequences.
 
-This module holds none of the method's arithmetic (no trading, valuation,
-observation or ensemble rule).  Both the CUDA library's tests and the oracle's
-tests draw their inputs from it.
+This module holds none of the method's arithmetic (no indicator, trading,
+valuation, observation or ensemble rule).  Both the CUDA library's tests and
+the oracle's tests draw their inputs from it.
 
 Random numbers: a counter-based SplitMix64 stream (Steele, Lea and Flood,
 "Fast splittable pseudorandom number generators", OOPSLA 2014), so every draw
@@ -85,7 +87,10 @@ class StockMarket:
     high: np.ndarray       # int64 [n_days][K]
     low: np.ndarray        # int64 [n_days][K]
     volume: np.ndarray     # int64 [n_days][K]
-    ind: np.ndarray        # float32 [n_days][I][K], scale-free
+    # the indicator table f_t is not generated here: the library computes it
+    # on the device from close / high / low (market_indicators), the oracle
+    # on the CPU; a caller may set an explicit float32 [n_days][I][K] table
+    ind: np.ndarray | None = None
 
     @property
     def n_days(self):
@@ -97,7 +102,7 @@ class StockMarket:
 
     @property
     def I(self):
-        return self.ind.shape[1]
+        return 8 if self.ind is None else self.ind.shape[1]
 
 
 @dataclass
@@ -113,69 +118,6 @@ class CryptoMarket:
 
 def _round_cents(x: np.ndarray) -> np.ndarray:
     return np.maximum(1, np.rint(x)).astype(np.int64)      # half-even
-
-
-def _ema(x: np.ndarray, span: int) -> np.ndarray:
-    a = 2.0 / (span + 1.0)
-    out = np.empty_like(x)
-    out[0] = x[0]
-    for t in range(1, x.shape[0]):
-        out[t] = a * x[t] + (1.0 - a) * out[t - 1]
-    return out
-
-
-def _wilder(x: np.ndarray, n: int) -> np.ndarray:
-    out = np.empty_like(x)
-    out[0] = x[0]
-    for t in range(1, x.shape[0]):
-        out[t] = out[t - 1] + (x[t] - out[t - 1]) / n
-    return out
-
-
-def _rolling(x: np.ndarray, n: int, fn) -> np.ndarray:
-    """fn over the trailing window of up to n rows (expanding at the start)."""
-    out = np.empty_like(x)
-    for t in range(x.shape[0]):
-        out[t] = fn(x[max(0, t - n + 1):t + 1])
-    return out
-
-
-def stock_indicators(close, high, low) -> np.ndarray:
-    """Textbook MACD(12,26), Bollinger(20, 2 sigma), RSI-30 (Wilder), CCI-30
-    (0.015), DX-30 (Wilder), SMA-30, SMA-60 from data up to each day only,
-    stored scale-free (ratios to the close, or /100) as float32 [T][8][K]."""
-    c = close.astype(np.float64)
-    h = high.astype(np.float64)
-    lo = low.astype(np.float64)
-    T, K = c.shape
-    macd = _ema(c, 12) - _ema(c, 26)
-    sma20 = _rolling(c, 20, lambda w: w.mean(0))
-    sd20 = _rolling(c, 20, lambda w: w.std(0))
-    diff = np.vstack([np.zeros((1, K)), np.diff(c, axis=0)])
-    gain = _wilder(np.maximum(diff, 0.0), 30)
-    loss = _wilder(np.maximum(-diff, 0.0), 30)
-    rsi = np.where(loss > 0, 100.0 - 100.0 / (1.0 + gain / np.where(loss > 0, loss, 1.0)), 100.0)
-    rsi = np.where((gain == 0) & (loss == 0), 50.0, rsi)
-    tp = (h + lo + c) / 3.0
-    sma_tp = _rolling(tp, 30, lambda w: w.mean(0))
-    mad = _rolling(tp, 30, lambda w: np.abs(w - w.mean(0)).mean(0))
-    cci = np.where(mad > 0, (tp - sma_tp) / (0.015 * np.where(mad > 0, mad, 1.0)), 0.0)
-    up = np.vstack([np.zeros((1, K)), h[1:] - h[:-1]])
-    dn = np.vstack([np.zeros((1, K)), lo[:-1] - lo[1:]])
-    pdm = np.where((up > dn) & (up > 0), up, 0.0)
-    ndm = np.where((dn > up) & (dn > 0), dn, 0.0)
-    prev_c = np.vstack([c[:1], c[:-1]])
-    tr = np.maximum.reduce([h - lo, np.abs(h - prev_c), np.abs(lo - prev_c)])
-    str_ = _wilder(tr, 30)
-    pdi = 100.0 * _wilder(pdm, 30) / np.where(str_ > 0, str_, 1.0)
-    ndi = 100.0 * _wilder(ndm, 30) / np.where(str_ > 0, str_, 1.0)
-    dx = np.where(pdi + ndi > 0, 100.0 * np.abs(pdi - ndi) / np.where(pdi + ndi > 0, pdi + ndi, 1.0), 0.0)
-    sma30 = _rolling(c, 30, lambda w: w.mean(0))
-    sma60 = _rolling(c, 60, lambda w: w.mean(0))
-    ind = np.stack([macd / c, (sma20 + 2 * sd20) / c - 1.0, (sma20 - 2 * sd20) / c - 1.0,
-                    rsi / 100.0, cci / 100.0, dx / 100.0, sma30 / c - 1.0,
-                    sma60 / c - 1.0], axis=1)
-    return ind.astype(np.float32)
 
 
 def stock_market(n_days: int, K: int = 30, seed: int = MASTER_SEED,
@@ -200,9 +142,7 @@ def stock_market(n_days: int, K: int = 30, seed: int = MASTER_SEED,
     high = np.maximum(high, close)
     low = np.minimum(low, close)
     volume = np.rint(1e6 * np.exp(0.3 * zv)).astype(np.int64)
-    ind = stock_indicators(close, high, low)
-    return StockMarket(close=close, open=_round_cents(open_f), high=high, low=low,
-                       volume=volume, ind=np.ascontiguousarray(ind))
+    return StockMarket(close=close, open=_round_cents(open_f), high=high, low=low, volume=volume)
 
 
 def crypto_market(S: int, seed: int = MASTER_SEED, vol: float = 1e-4,

@@ -13,29 +13,19 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_2501_10709_gb300 as fr
 from paper_2501_10709_gb300 import _lib, synth
 
 pytestmark = pytest.mark.gpu
 
-M64 = 2**64 - 1
-
-
-def _splitmix64(x):
-    x = (x + 0x9E3779B97F4A7C15) & M64
-    x = ((x ^ (x >> 30)) * 0xBF58476D1CE4E5B9) & M64
-    x = ((x ^ (x >> 27)) * 0x94D049BB133111EB) & M64
-    return x ^ (x >> 31)
-
-
 def _request_bps(n, K, seed, rng):
-    """The per-env, per-asset perturbation the server draws (header contract)."""
+    """The per-env, per-asset perturbation the server draws, from the oracle."""
     b = np.zeros((n, K), np.int16)
     if rng > 0:
         for i in range(n):
             for k in range(K):
-                z = _splitmix64(seed ^ _splitmix64((i << 8) | k))
-                b[i, k] = z % (2 * rng + 1) - rng
+                b[i, k] = oracle.perturb_bps(seed, i, k, rng)
     return b
 
 

@@ -192,7 +192,7 @@ def test_stock_observation_layout():
         assert np.array_equal(ob[1:1 + ke], p.astype(np.float32) * np.float32(1e-4))
         assert (ob[1 + ke:1 + K] == 0).all() and (ob[1 + K:1 + 2 * K] == 0).all()
         f = ob[1 + 2 * K:].reshape(I, K)                     # indicator-major
-        assert np.array_equal(f[:, :ke], mk.ind[d, :, :ke]) and (f[:, ke:] == 0).all()
+        assert np.array_equal(f[:, :ke], oracle.market_table(mk)[d, :, :ke]) and (f[:, ke:] == 0).all()
 
 
 def test_stock_metrics_follow_value_series():

@@ -367,3 +367,130 @@ def test_explore_greedy_rate_and_uniform_replacements():
     assert counts.sum() == rep.sum() and len(counts) == 3
     assert all(abs(c / rep.sum() - 1 / 3) < 4 * math.sqrt(2 / 9 / rep.sum()) for c in counts)
     assert all(oracle.explore_greedy(99, e, 0, 0.0, 2) == 2 for e in range(100))     # eps = 0: never
+
+
+# ---------------------------------------------- data preparation (Sec. 5.1, 6.1)
+def test_splitmix64_published_sequence():
+    # the first outputs of SplitMix64 from state 0 (the generator's published
+    # reference sequence): output n mixes n+1 golden-gamma increments
+    g = 0x9E3779B97F4A7C15
+    want = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F, 0xF88BB8A8724C81EC, 0x1B39896A51A8749B]
+    assert [oracle.splitmix64((n * g) % 2**64) for n in range(5)] == want
+
+
+def test_perturb_bps_range_and_uniformity():
+    R = 100
+    v = np.array([oracle.perturb_bps(2024, e, k, R) for e in range(400) for k in range(30)])
+    assert v.min() == -R and v.max() == R
+    counts = np.bincount(v + R, minlength=2 * R + 1)
+    n, p = v.size, 1.0 / (2 * R + 1)
+    chi2 = float(((counts - n * p) ** 2 / (n * p)).sum())
+    assert chi2 < 200 + 5 * math.sqrt(2 * 200)                     # 200 degrees of freedom
+    assert abs(v.mean()) < 4 * math.sqrt((R * (R + 1) / 3) / n)
+    assert all(oracle.perturb_bps(5, e, k, 0) == 0 for e in range(20) for k in range(30))
+    # different seeds, envs and assets decorrelate
+    a = np.array([oracle.perturb_bps(1, e, 3, R) for e in range(2000)], float)
+    b = np.array([oracle.perturb_bps(2, e, 3, R) for e in range(2000)], float)
+    c = np.array([oracle.perturb_bps(1, e, 4, R) for e in range(2000)], float)
+    assert abs(np.corrcoef(a, b)[0, 1]) < 0.1 and abs(np.corrcoef(a, c)[0, 1]) < 0.1
+
+
+def _ramp(T, c0, d):
+    c = (c0 + d * np.arange(T, dtype=np.int64))[:, None]
+    return c, c.copy(), c.copy()
+
+
+def _ramp_mad(m):
+    j = np.arange(m)
+    return np.abs(j - (m - 1) / 2.0).mean()
+
+
+def test_indicators_of_a_constant_series():
+    c = np.full((120, 2), 123456, np.int64)
+    f = oracle.indicators(c, c, c)
+    want = np.zeros(8, np.float32)
+    want[3] = 0.5                                                  # RSI 50 without gains or losses
+    assert np.array_equal(f, np.broadcast_to(want[None, :, None], f.shape))
+
+
+@pytest.mark.parametrize("d", [250, -250])
+def test_indicators_of_a_linear_ramp(d):
+    # c_t = c0 + d t with h = l = c: every indicator has a closed form
+    T, c0 = 150, 100_000
+    close, high, low = _ramp(T, c0, d)
+    f = oracle.indicators(close, high, low)[:, :, 0].astype(np.float64)
+    t = np.arange(T)
+    ct = (c0 + d * t).astype(np.float64)
+    # EMA of a ramp from e_0 = c_0: e_t = c_t - d (1 - a) / a (1 - (1 - a)^t), (1 - a) / a = (n - 1) / 2
+    macd = d * (12.5 * (1 - (25 / 27) ** t) - 5.5 * (1 - (11 / 13) ** t))
+    assert np.allclose(f[:, 0], macd / ct, rtol=1e-5, atol=1e-8)
+    m20 = np.minimum(t + 1, 20)
+    sma20 = ct - d * (m20 - 1) / 2.0
+    sd20 = abs(d) * np.sqrt((m20 ** 2 - 1) / 12.0)                  # population sd of m equally spaced values
+    assert np.allclose(f[:, 1], (sma20 + 2 * sd20) / ct - 1, rtol=1e-5, atol=1e-7)
+    assert np.allclose(f[:, 2], (sma20 - 2 * sd20) / ct - 1, rtol=1e-5, atol=1e-7)
+    assert f[0, 3] == 0.5 and (f[1:, 3] == (1.0 if d > 0 else 0.0)).all()
+    m30 = np.minimum(t + 1, 30)
+    mad = np.array([abs(d) * _ramp_mad(m) for m in m30])
+    cci = np.where(mad > 0, (d * (m30 - 1) / 2.0) / (0.015 * np.where(mad > 0, mad, 1)), 0.0)
+    assert np.allclose(f[:, 4], cci / 100, rtol=1e-5, atol=1e-7)
+    assert f[0, 5] == 0.0 and (f[1:, 5] == 1.0).all()               # one-sided movement: DX 100
+    assert np.allclose(f[:, 6], -(d * (m30 - 1) / 2.0) / ct, rtol=1e-5, atol=1e-8)
+    m60 = np.minimum(t + 1, 60)
+    assert np.allclose(f[:, 7], -(d * (m60 - 1) / 2.0) / ct, rtol=1e-5, atol=1e-8)
+
+
+def _geometric(x, a, w0=None):
+    """The recurrence e_t = a x_t + (1 - a) e_{t-1}, e_0 = x_0, summed in closed
+    form: e_t = (1 - a)^t x_0 + sum_{j=1..t} a (1 - a)^(t - j) x_j."""
+    T = x.shape[0]
+    t = np.arange(T)
+    W = np.where(t[:, None] >= t[None, :], a * (1 - a) ** np.maximum(t[:, None] - t[None, :], 0), 0.0)
+    W[:, 0] = (1 - a) ** t
+    return W @ x
+
+
+def test_indicators_against_closed_form_recurrences_and_windows():
+    # random OHLC; recurrences by their closed-form weights, windows by
+    # explicit slices, RSI and DX through their algebraically equal forms
+    mk = synth.stock_market(160, 3, seed=11)
+    c, h, lo = (x.astype(np.float64) for x in (mk.close, mk.high, mk.low))
+    f = oracle.indicators(mk.close, mk.high, mk.low).astype(np.float64)
+    T, K = c.shape
+    macd = _geometric(c, 2 / 13) - _geometric(c, 2 / 27)
+    assert np.allclose(f[:, 0], macd / c, rtol=1e-4, atol=2e-7)
+    d = np.vstack([np.zeros((1, K)), c[1:] - c[:-1]])
+    G, L = _geometric(np.maximum(d, 0), 1 / 30), _geometric(np.maximum(-d, 0), 1 / 30)
+    rsi = np.where(G + L > 0, G / np.where(G + L > 0, G + L, 1), 0.5)
+    assert np.allclose(f[:, 3], rsi, rtol=0, atol=1e-6)
+    win = lambda x, t, n: x[max(0, t - n + 1):t + 1]
+    tp = (h + lo + c) / 3
+    for t in range(T):
+        w20 = win(c, t, 20)
+        s20 = np.sqrt(((w20 - w20.mean(0)) ** 2).mean(0))
+        assert np.allclose(f[t, 1], (w20.mean(0) + 2 * s20) / c[t] - 1, rtol=0, atol=1e-6)
+        assert np.allclose(f[t, 2], (w20.mean(0) - 2 * s20) / c[t] - 1, rtol=0, atol=1e-6)
+        wt = win(tp, t, 30)
+        mad = np.abs(wt - wt.mean(0)).mean(0)
+        cci = np.where(mad > 0, (tp[t] - wt.mean(0)) / (0.015 * np.where(mad > 0, mad, 1)), 0)
+        assert np.allclose(f[t, 4], cci / 100, rtol=1e-5, atol=1e-6)
+        assert np.allclose(f[t, 6], win(c, t, 30).mean(0) / c[t] - 1, rtol=0, atol=1e-7)
+        assert np.allclose(f[t, 7], win(c, t, 60).mean(0) / c[t] - 1, rtol=0, atol=1e-7)
+    up = np.vstack([np.zeros((1, K)), h[1:] - h[:-1]])
+    dn = np.vstack([np.zeros((1, K)), lo[:-1] - lo[1:]])
+    pdm, ndm = np.where((up > dn) & (up > 0), up, 0), np.where((dn > up) & (dn > 0), dn, 0)
+    pc = np.vstack([c[:1], c[:-1]])
+    tr = np.max([h - lo, np.abs(h - pc), np.abs(lo - pc)], axis=0)
+    P, N = _geometric(pdm, 1 / 30), _geometric(ndm, 1 / 30)      # DI+ / DI- = P / N: TR cancels
+    dx = np.where(P + N > 0, np.abs(P - N) / np.where(P + N > 0, P + N, 1), 0)
+    assert (_geometric(tr, 1 / 30) > 0).all()
+    assert np.allclose(f[:, 5], dx, rtol=0, atol=1e-6)
+
+
+def test_indicator_windows_see_no_future():
+    mk = synth.stock_market(200, 4, seed=5)
+    full = oracle.indicators(mk.close, mk.high, mk.low)
+    for t in (0, 1, 29, 59, 60, 137):
+        part = oracle.indicators(mk.close[:t + 1], mk.high[:t + 1], mk.low[:t + 1])
+        assert np.array_equal(part, full[:t + 1])
+
