@@ -320,6 +320,20 @@ def uneven_line(fr, ctx, dev, flush, stream, reps=3):
         res[name] = {"value": work * len(ts) / sum(ts), "ms_per_rollout": 1e3 * statistics.mean(ts)}
     fr.env_set_tile_packing(env, True)
     res["tile_efficiency_packed"] = fr.env_tile_packing_efficiency(env)
+    # FP8 E4M3 actors: activation scales calibrated on 4,096 observations the
+    # BF16 ensemble visits in the first 8 steps; FP8 rollouts run the unfused
+    # path (one launch per stage per step)
+    ens8 = fr.ensemble_create(ctx, w.dims, w.params, precision=fr.PREC_FP8)
+    tr = {"obs": torch.empty(8, e.N, env.D, device=dev)}
+    fr.env_reset(env)
+    fr.rollout(env, ens, 8, traj=tr)
+    rows = torch.linspace(0, 8 * e.N - 1, 4096, device=dev).long()
+    fr.ensemble_calibrate_sync(ens8, tr["obs"].reshape(-1, env.D)[rows].contiguous())
+    del tr
+    ts = time_rollouts(fr, env, ens8, w.T, reps, 3, met, flush, stream)
+    res["fp8_unfused"] = {"value": work * len(ts) / sum(ts), "ms_per_rollout": 1e3 * statistics.mean(ts),
+                          "calibration": "4,096 observations from the first 8 BF16 steps"}
+    ens8.close()
     W = e.W.astype(float)
     res["tile_efficiency_unpacked"] = float((W - 1).sum() / (128 * (W.max() - 1) * ((e.N + 127) // 128)))
     return res
@@ -452,6 +466,15 @@ def run_gpu(args):
     y_big = torch.empty(M, nb, 30, device=dev)
     kb_dt = time_kernel(lambda: fr.ensemble_forward(ens_bf16, obs_big, y_big), 10, stream)
     big_tflops = nb / N * flops_per_launch / kb_dt / 1e12
+    # FP8 E4M3 (kind::f8f6f4) at the same batches, scales calibrated on the
+    # observations themselves; its peak is the measured BF16 peak x 2 (the
+    # nominal FP8 / BF16 ratio)
+    ens_fp8 = fr.ensemble_create(ctx, w.dims, w.params, precision=fr.PREC_FP8)
+    fr.ensemble_calibrate_sync(ens_fp8, obs)
+    a8_dt = time_kernel(lambda: fr.ensemble_forward(ens_fp8, obs, y), 50, stream)
+    k8_dt = time_kernel(lambda: fr.ensemble_forward(ens_fp8, obs_big, y_big), 10, stream)
+    fp8_tflops = nb / N * flops_per_launch / k8_dt / 1e12
+    ens_fp8.close()
 
     # crypto config: 8,192 envs x 1,024 steps, 5 x 10-128-128-3 Q-nets, vote
     # (fused BF16 path for the full horizon; the plain FP32 path on the first
@@ -525,6 +548,12 @@ def run_gpu(args):
                                       "us_per_launch": a_dt * 1e6},
                      "actor_kernel_large_batch": {"rows": nb, "achieved": big_tflops,
                                                   "frac": big_tflops / peak},
+                     "actor_kernel_fp8": {"kernel": "k_tc_forward, E4M3 operands (kind::f8f6f4)",
+                                          "rows": N, "us_per_launch": a8_dt * 1e6,
+                                          "tflops": flops_per_launch / a8_dt / 1e12,
+                                          "large_batch_rows": nb, "large_batch_tflops": fp8_tflops,
+                                          "peak": 2 * peak, "frac": fp8_tflops / (2 * peak),
+                                          "peak_source": "measured bf16_tflops burst x 2 (nominal FP8/BF16)"},
                      "env_step_kernel": env_step},
         "data_prep": prep,
         "crypto_c3": crypto,

@@ -239,7 +239,9 @@ typedef struct fr_ensemble fr_ensemble;
 
 #define FR_PREC_FP32 0        /* plain unfused fp32 SIMT path               */
 #define FR_PREC_BF16 1        /* tcgen05 BF16 tensor cores, fp32 accumulate */
-#define FR_PREC_FP8 2         /* tcgen05 FP8 E4M3 weights+activations       */
+#define FR_PREC_FP8 2         /* tcgen05 FP8 E4M3 weights+activations, per-
+                                 channel weight scales, static activation
+                                 scales (ensemble_calibrate_sync)            */
 #define FR_PREC_BF16X3 3      /* tcgen05 BF16 with split hi/lo operands:
                                  x ~ hi + lo, three products per step
                                  (hi*hi + lo*hi + hi*lo), fp32-class accuracy
@@ -271,6 +273,29 @@ typedef struct {
 int ensemble_create(fr_ctx *ctx, const fr_ensemble_desc *desc,
                     fr_ensemble **out);
 void ensemble_destroy(fr_ensemble *ens);
+
+/* FP8 E4M3 ensembles (no counterpart in the paper, whose agents run in
+ * fp32; an inference-precision option of the actors).  Weights: row n of
+ * layer l holds the E4M3 codes (round to nearest even, saturating at +-448)
+ * of W[n][k] * (1 / sw[n]), sw[n] = max_k |W[n][k]| / 448 (1 for a zero
+ * row), all float32 operations.  Activations: layer l's input x (the
+ * observation for l = 0, else the ReLU output of layer l - 1) is quantised
+ * as codes of x * (1 / sx[j][l]) with a static scale per agent j and layer.
+ * The FP32 tensor-core accumulator is dequantised as
+ * fma(acc, sx[j][l] * sw[n], b[n]); hidden layers then take ReLU, the output
+ * tanh or identity.
+ * An FP8 ensemble has no activation scales at creation: ensemble_forward,
+ * ensemble_act and rollout return FR_ENOTREADY until they are set.
+ *  ensemble_set_act_scales: scales host float [M][L], finite and > 0
+ *    (FR_EINVAL otherwise or for a non-FP8 ensemble); synchronous.
+ *  ensemble_get_act_scales: the current scales into host float [M][L].
+ *  ensemble_calibrate_sync: sets sx[j][l] = max |x| / 448 over a calibration
+ *    batch obs (device float [n][dims[0]], n >= 1), x the input of layer l
+ *    of agent j through the fp32 master weights (1 where the maximum is 0);
+ *    runs on `stream` and waits for it. */
+int ensemble_set_act_scales(fr_ensemble *ens, const float *scales);
+int ensemble_get_act_scales(const fr_ensemble *ens, float *scales);
+int ensemble_calibrate_sync(fr_ensemble *ens, const float *obs, int32_t n, void *stream);
 
 /* Per-agent network outputs: obs device float [n][dims[0]] (packed rows),
  * y device float [M][n][dims[L]]. */

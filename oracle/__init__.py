@@ -171,6 +171,86 @@ def net_forward(dims, params: np.ndarray, x: np.ndarray, out_act: int,
     return y
 
 
+# ------------------------------------------------------- FP8 E4M3 actors
+# The FP8 option of the actors has no counterpart in the paper (its agents
+# run in fp32); these follow the format definition and the library's stated
+# quantisation rule, in plain numpy.
+E4M3_MAX = 448.0
+
+
+def e4m3_round(x) -> np.ndarray:
+    """Nearest E4M3 value of each element, ties to even, saturating at +-448.
+
+    E4M3 (OCP 8-bit floating point): sign, 4 exponent bits (bias 7), 3
+    fraction bits; normal binades 2^-6 .. 2^8 with 8 values each, subnormals
+    in steps of 2^-9, largest finite 448, no infinities.  A binade 2^e holds
+    multiples of 2^(e-3); below 2^-6 the step stays 2^-9.  Exact in float64."""
+    x = np.asarray(x, np.float64)
+    a = np.abs(x)
+    _, ex = np.frexp(a)                         # a = m 2^ex, 1/2 <= m < 1
+    step = np.ldexp(1.0, np.maximum(ex - 1, -6) - 3)
+    q = np.minimum(np.rint(a / step) * step, E4M3_MAX)   # rint: ties to even
+    return np.copysign(q, x)
+
+
+def _layers(dims, params):
+    """(W_l float32 [out][in], b_l float32 [out]) from packed parameters."""
+    params = np.asarray(params, np.float32)
+    out, off = [], 0
+    for fin, fout in zip(dims[:-1], dims[1:]):
+        W = params[off:off + fin * fout].reshape(fout, fin)
+        off += fin * fout
+        out.append((W, params[off:off + fout]))
+        off += fout
+    return out
+
+
+def fp8_weights(W):
+    """Per-output-channel E4M3 weights: scale sw[n] = max_k |W[n][k]| / 448
+    (1 for a zero row), codes of W[n][k] * (1 / sw[n]); float32 arithmetic.
+    Returns (code values float64 [out][in], sw float32 [out])."""
+    W = np.asarray(W, np.float32)
+    amax = np.abs(W).max(axis=1)
+    sw = np.where(amax > 0, amax / np.float32(E4M3_MAX), np.float32(1.0)).astype(np.float32)
+    inv = (np.float32(1.0) / sw).astype(np.float32)
+    return e4m3_round(W * inv[:, None]), sw
+
+
+def fp8_forward(dims, params, act_scales, x, out_act: int) -> np.ndarray:
+    """One agent's FP8 forward: each layer's input quantised with its static
+    scale (codes of x * (1 / sx), float32), the E4M3 dot products summed
+    exactly, dequantised by sx * sw[n] (float32 product), bias added in
+    float64; ReLU between layers (the next layer quantises the float32 value
+    of the activation), tanh or identity on the output.  float64 [n][out]."""
+    h = np.asarray(x, np.float32)
+    layers = _layers(dims, params)
+    for l, (W, b) in enumerate(layers):
+        sx = np.float32(act_scales[l])
+        qx = e4m3_round(h * (np.float32(1.0) / sx))
+        qw, sw = fp8_weights(W)
+        acc = qx @ qw.T                      # exact: E4M3 products and sums fit in float64
+        y = acc * (sx * sw).astype(np.float64) + b.astype(np.float64)
+        if l + 1 < len(layers):
+            h = np.maximum(y, 0.0).astype(np.float32)
+        else:
+            return np.tanh(y) if out_act else y
+
+
+def fp8_calibrate(dims, params, obs) -> np.ndarray:
+    """One agent's activation scales [L] float32: max |x_l| / 448 over the
+    batch (1 where it is 0), x_l the input of layer l through the fp64
+    forward of the fp32 master weights."""
+    h = np.asarray(obs, np.float64)
+    out = []
+    layers = _layers(dims, params)
+    for l, (W, b) in enumerate(layers):
+        amax = np.float32(np.abs(h).max())
+        out.append(amax / np.float32(E4M3_MAX) if amax > 0 else np.float32(1.0))
+        if l + 1 < len(layers):
+            h = np.maximum(h @ W.astype(np.float64).T + b.astype(np.float64), 0.0)
+    return np.array(out, np.float32)
+
+
 def ensemble_mean(a: np.ndarray, w=None) -> np.ndarray:
     """a[M][K] fp64 -> anchored weighted mean [K]."""
     a = _c(a, np.float64)

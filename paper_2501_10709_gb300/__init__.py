@@ -24,7 +24,8 @@ __all__ = [
     "ensemble_act", "ensemble_act_noalloc", "ensemble_device_errors", "rollout", "env_set_rollout_path", "env_set_kernel_timing", "env_last_kernel_ms", "env_set_tile_packing",
     "env_tile_packing_efficiency", "ensemble_set_weights", "ensemble_validate", "trajectory_metrics", "env_set_exploration",
     "EXPLORE_NONE", "EXPLORE_GAUSSIAN", "EXPLORE_EPS_GREEDY", "Server", "fr_server_create", "backtest_submit",
-    "backtest_poll", "fr_server_stats", "FrError", "lib",
+    "backtest_poll", "fr_server_stats", "FrError", "lib", "market_indicators", "fr_market_indicators",
+    "env_perturb", "ensemble_set_act_scales", "ensemble_get_act_scales", "ensemble_calibrate_sync",
     "PATH_AUTO", "PATH_UNFUSED",
     "ACT_I32_SHARES", "ACT_F32_UNIT", "ACT_U8_DISCRETE", "PREC_FP32", "PREC_BF16",
     "PREC_FP8", "PREC_BF16X3", "COMBINE_MEAN", "COMBINE_VOTE", "TASK_STOCK", "TASK_CRYPTO",
@@ -297,6 +298,28 @@ def ensemble_create(ctx: Ctx, dims, params, *, weights=None, precision: int = PR
     e = Ensemble(out.value, keep=(ctx,))
     e.M, e.dims, e.combine, e.precision = params.shape[0], tuple(int(x) for x in dims), combine, precision
     return e
+
+
+def ensemble_set_act_scales(ens: Ensemble, scales):
+    """FP8 ensembles: static activation scales, host float [M][L]."""
+    sc = np.ascontiguousarray(scales, np.float32).reshape(ens.M, len(ens.dims) - 1)
+    _lib.check(lib().ensemble_set_act_scales(ens, _hptr(sc)), "ensemble_set_act_scales")
+
+
+def ensemble_get_act_scales(ens: Ensemble) -> np.ndarray:
+    out = np.empty((ens.M, len(ens.dims) - 1), np.float32)
+    _lib.check(lib().ensemble_get_act_scales(ens, _hptr(out)), "ensemble_get_act_scales")
+    return out
+
+
+def ensemble_calibrate_sync(ens: Ensemble, obs, stream=None) -> np.ndarray:
+    """FP8 ensembles: activation scales max |x| / 448 per agent and layer over
+    the calibration batch obs (device [n][dims[0]]); returns them."""
+    import torch
+    n = obs.shape[0]
+    _lib.check(lib().ensemble_calibrate_sync(ens, _dptr(obs, torch.float32, n * ens.dims[0], "obs"), n,
+                                             _stream(stream)), "ensemble_calibrate_sync")
+    return ensemble_get_act_scales(ens)
 
 
 def ensemble_forward(ens: Ensemble, obs, y, stream=None):

@@ -127,6 +127,9 @@ SIGNATURES = {
     "fr_market_copy_indicators": (i32, [vp, vp]),
     "market_indicators": (i32, [vp, vp, vp, i32, i32, vp, vp]),
     "env_perturb": (i32, [vp, u64, i32, vp]),
+    "ensemble_set_act_scales": (i32, [vp, vp]),
+    "ensemble_get_act_scales": (i32, [vp, vp]),
+    "ensemble_calibrate_sync": (i32, [vp, vp, i32, vp]),
 }
 
 _lock = threading.Lock()

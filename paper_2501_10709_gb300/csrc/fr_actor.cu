@@ -299,7 +299,7 @@ int ta_stages(const TcPlan &p, int optin)
 // tiles x agents CTAs then fill the GPU better)
 uint64_t tc_tiled_scratch_bytes(const fr_ensemble *e, int n)
 {
-    if (!e->tc || e->tc->plan.split != 1) return 0;
+    if (!e->tc || e->tc->plan.split != 1 || e->tc->plan.esz != 2) return 0;     // plain BF16 only
     const int tiles = (int)ceil_div(n, 128);
     if (tiles < e->ctx->sm_count) return 0;
     return (uint64_t)tiles * obs_tile_bytes(e->tc->plan);

@@ -753,6 +753,73 @@ void ensemble_destroy(fr_ensemble *e)
 }
 
 
+int ensemble_set_act_scales(fr_ensemble *e, const float *scales)
+{
+    FR_CHECK(e && scales, FR_EINVAL, "ensemble_set_act_scales: NULL argument");
+    int rc = use_device(e->ctx);
+    if (rc) return rc;
+    return tc_set_act_scales(e, scales);
+}
+
+int ensemble_get_act_scales(const fr_ensemble *e, float *scales)
+{
+    FR_CHECK(e && scales, FR_EINVAL, "ensemble_get_act_scales: NULL argument");
+    return tc_get_act_scales(e, scales);
+}
+
+int ensemble_calibrate_sync(fr_ensemble *e, const float *obs, int32_t n, void *stream)
+{
+    FR_CHECK(e && obs && n >= 1, FR_EINVAL, "ensemble_calibrate_sync: NULL argument or n < 1");
+    FR_CHECK(e->precision == FR_PREC_FP8 && e->tc, FR_EINVAL, "ensemble_calibrate_sync: FP8 ensembles only");
+    int rc = use_device(e->ctx);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    int wmax = 0;
+    for (int l = 1; l < e->L; ++l) wmax = std::max(wmax, e->dims[l]);
+    const uint64_t hb = 2ull * e->M * n * (uint64_t)wmax * 4;
+    void *buf = nullptr;
+    unsigned *amax = nullptr;
+    FR_CUDA(cudaMallocAsync(&buf, hb + 4ull * MAX_AGENTS * MAX_LAYERS + 16, s));
+    amax = (unsigned *)((char *)buf + hb);
+    cudaError_t err = cudaMemsetAsync(amax, 0, 4ull * MAX_AGENTS * MAX_LAYERS, s);
+    // activation scale = max |input| / 448 over the calibration batch, per
+    // agent and layer; layer 0's input is the observation, the same for
+    // every agent
+    if (err == cudaSuccess) err = launch_absmax(obs, 0, (int64_t)n * e->dims[0], 1, amax, 1, s);
+    // hidden layers through the fp32 master weights: ReLU outputs of layer l
+    // are layer l + 1's input
+    const float *in = obs;
+    int64_t in_stride = 0;
+    int in_ld = e->dims[0];
+    for (int l = 0; l + 1 < e->L && err == cudaSuccess; ++l) {
+        const int fin = e->dims[l], fout = e->dims[l + 1];
+        float *out = (float *)buf + (int64_t)(l & 1) * e->M * n * wmax;
+        const int64_t out_stride = (int64_t)n * fout;
+        err = launch_dense_f32(in, in_stride, in_ld, e->params, e->P, e->w_off[l], e->b_off[l], out, out_stride,
+                               fout, n, fin, fout, 0, e->M, s);
+        if (err == cudaSuccess) err = launch_absmax(out, out_stride, out_stride, e->M, amax + l + 1, MAX_LAYERS, s);
+        in = out;
+        in_stride = out_stride;
+        in_ld = fout;
+    }
+    unsigned h[MAX_AGENTS * MAX_LAYERS];
+    if (err == cudaSuccess) err = cudaMemcpyAsync(h, amax, sizeof(h), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(buf, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    FR_CUDA(err);
+    float sx[MAX_AGENTS * MAX_LAYERS];
+    for (int j = 0; j < e->M; ++j) {
+        for (int l = 0; l < e->L; ++l) {
+            // layer 0's maximum was recorded once, in slot 0
+            float a;
+            const unsigned bits = l == 0 ? h[0] : h[j * MAX_LAYERS + l];
+            memcpy(&a, &bits, 4);
+            sx[j * e->L + l] = a > 0.0f ? a / 448.0f : 1.0f;     // 448: largest finite E4M3
+        }
+    }
+    return tc_set_act_scales(e, sx);
+}
+
 int ensemble_forward(const fr_ensemble *e, const float *obs, int32_t n, float *y, void *stream)
 {
     FR_CHECK(e && n >= 0, FR_EINVAL, "ensemble_forward: bad argument");

@@ -217,6 +217,10 @@ cudaError_t launch_dense_f32(const float *X, int64_t x_stride, int ldx, const fl
                              int64_t p_stride, int64_t w_off, int64_t b_off, float *Y,
                              int64_t y_stride, int ldy, int n, int fin, int fout, int act, int M,
                              cudaStream_t s);
+// max |x| of M matrices of `count` floats (stride apart) into out[j * out_stride]
+// as float bits (atomic max; out zeroed by the caller)
+cudaError_t launch_absmax(const float *x, int64_t stride, int64_t count, int M, unsigned *out, int out_stride,
+                          cudaStream_t s);
 cudaError_t launch_combine_mean(const float *Y, int64_t y_stride, int ldy, const float *w, int M,
                                 int n, int K, float *out, int ldo, cudaStream_t s);
 cudaError_t launch_combine_vote(const float *Y, int64_t y_stride, int ldy, int M, int n, int nact,
@@ -238,6 +242,9 @@ int tc_create(fr_ensemble *e);
 void tc_destroy(fr_ensemble *e);
 // Per-agent outputs through the tcgen05 kernels; obs rows of stride ld.
 int tc_forward(const fr_ensemble *e, const float *obs, int ld, int n, float *y, cudaStream_t s);
+// FP8 activation scales sx[j][l] (host [M][L]) of an FP8 ensemble (fr_tc.cu)
+int tc_set_act_scales(fr_ensemble *e, const float *scales);
+int tc_get_act_scales(const fr_ensemble *e, float *scales);
 // Large-batch BF16 forward over tiled observations (fr_actor.cu): scratch of
 // tc_tiled_scratch_bytes (0 = this ensemble has no such path).
 uint64_t tc_tiled_scratch_bytes(const fr_ensemble *e, int n);

@@ -131,6 +131,31 @@ cudaError_t launch_dense_f32(const float *X, int64_t x_stride, int ldx, const fl
     return cudaGetLastError();
 }
 
+namespace {
+// Maximum of |x| over `count` floats of matrix j (at x + j * stride), as float
+// bits atomically maxed into out[j * out_stride] (non-negative floats order
+// like their bit patterns).
+__global__ void k_absmax(const float *__restrict__ x, int64_t stride, int64_t count, unsigned *out,
+                         int out_stride)
+{
+    const float *xj = x + (int64_t)blockIdx.y * stride;
+    float m = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(xj[i]));
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out + (int64_t)blockIdx.y * out_stride, __float_as_uint(m));
+}
+}  // namespace
+
+cudaError_t launch_absmax(const float *x, int64_t stride, int64_t count, int M, unsigned *out, int out_stride,
+                          cudaStream_t s)
+{
+    const long long b = ((long long)count + 255) / 256;
+    const unsigned blocks = (unsigned)(b < 1024 ? (b > 0 ? b : 1) : 1024);
+    k_absmax<<<dim3(blocks, M), 256, 0, s>>>(x, stride, count, out, out_stride);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_combine_mean(const float *Y, int64_t y_stride, int ldy, const float *w, int M,
                                 int n, int K, float *out, int ldo, cudaStream_t s)
 {

@@ -11,10 +11,15 @@
 //   * four epilogue warps read the accumulator back with tcgen05.ld, add the
 //     bias, apply ReLU, and write the next layer's A operand (BF16) straight
 //     into shared memory; the last layer applies tanh or identity.
+// With FP8 E4M3 operands the MMA is kind::f8f6f4 (K = 32 per instruction),
+// the epilogue dequantises with the per-channel factor sx * sw before the
+// bias and quantises the next layer's input with the agent's activation scale.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "fr_common.cuh"
@@ -45,16 +50,21 @@ inline float bf16_to_f32(uint16_t b)
     return f;
 }
 
-// byte offset of element (n, kk) inside a chunk of a layer with N rows
-inline uint32_t chunk_off(int N, int n, int kk)
+// byte offset of element (n, kk) inside a chunk of a layer with N rows, for
+// ck elements (of esz bytes) per core-matrix row
+inline uint32_t chunk_off(int N, int n, int kk, int ck, int esz)
 {
-    return (uint32_t)((kk / 8) * (N * 16) + (n / 8) * 128 + (n % 8) * 16 + (kk % 8) * 2);
+    return (uint32_t)((kk / ck) * (N * 16) + (n / 8) * 128 + (n % 8) * 16 + (kk % ck) * esz);
 }
 
 bool make_plan(const fr_ensemble *e, TcPlan &p)
 {
     p.split = e->precision == FR_PREC_BF16X3 ? 3 : 1;
     p.parts = p.split == 3 ? 2 : 1;
+    const bool fp8 = e->precision == FR_PREC_FP8;
+    p.esz = fp8 ? 1 : 2;
+    p.kmma = fp8 ? 32 : 16;
+    p.ck = fp8 ? 16 : 8;
     p.M = e->M;
     p.L = e->L;
     p.out_act = e->out_act;
@@ -65,15 +75,15 @@ bool make_plan(const fr_ensemble *e, TcPlan &p)
         TcLayer &ly = p.layer[l];
         ly.fin = e->dims[l];
         ly.fout = e->dims[l + 1];
-        ly.K = round16(ly.fin);
+        ly.K = (ly.fin + p.kmma - 1) / p.kmma * p.kmma;
         ly.N = round16(ly.fout);
         if (ly.N > 256 || ly.K > 512) return false;
-        int kc = (int)(TC_CHUNK_MAX / (uint32_t)(ly.N * 2 * p.parts));
-        kc = kc / 16 * 16;
+        int kc = (int)(TC_CHUNK_MAX / (uint32_t)(ly.N * p.esz * p.parts));
+        kc = kc / p.kmma * p.kmma;
         ly.KC = kc < ly.K ? kc : ly.K;
         ly.n_chunks = (ly.K + ly.KC - 1) / ly.KC;
         ly.off = off;
-        off += (uint32_t)ly.N * ly.K * 2 * p.parts;
+        off += (uint32_t)ly.N * ly.K * p.esz * p.parts;
         p.KA = ly.K > p.KA ? ly.K : p.KA;
         nmax = ly.N > nmax ? ly.N : nmax;
     }
@@ -92,6 +102,8 @@ uint32_t tc_smem_bytes(const TcPlan &p)
 // ------------------------------------------------------------------ kernel
 __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const uint8_t *__restrict__ img,
                                                             const float *__restrict__ bias,
+                                                            const float *__restrict__ dq,
+                                                            const float *__restrict__ inv_sx,
                                                             const float *__restrict__ obs, int ld, int n,
                                                             float *__restrict__ y, unsigned *err)
 {
@@ -99,8 +111,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const ui
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *A = base;
-    const uint32_t a_part = (uint32_t)(plan.KA / 8) * 2048u;    // bytes of one A part
+    const uint32_t a_part = a_part_bytes(plan);                  // bytes of one A part
     const bool split = plan.split == 3;
+    const bool fp8 = plan.esz == 1;
     uint8_t *ring = A + a_part * (split ? 2u : 1u);
     uint64_t *bars = (uint64_t *)(ring + TC_STAGES * TC_CHUNK_MAX);
     uint64_t *full = bars;
@@ -147,10 +160,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const ui
                     const uint32_t ph = (uint32_t)(i / TC_STAGES) & 1u;
                     if (!mbar_wait(&empty[s], ph ^ 1u, abort, err, 1u, TC_WAIT_NS)) { ok = false; break; }
                     const int kc = min(ly.KC, ly.K - c * ly.KC);
-                    const uint32_t bytes = (uint32_t)(ly.N * kc * 2 * plan.parts);
+                    const uint32_t bytes = (uint32_t)(ly.N * kc * plan.esz * plan.parts);
                     mbar_arrive_expect_tx(&full[s], bytes);
                     bulk_g2s(ring + s * TC_CHUNK_MAX,
-                             aimg + ly.off + (size_t)c * ly.N * ly.KC * 2 * plan.parts, bytes, &full[s]);
+                             aimg + ly.off + (size_t)c * ly.N * ly.KC * plan.esz * plan.parts, bytes, &full[s]);
                     ++i;
                 }
             }
@@ -170,7 +183,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const ui
                 const TcLayer &ly = plan.layer[l];
                 if (!mbar_wait(a_ready, (uint32_t)l & 1u, abort, err, 2u, TC_WAIT_NS)) break;
                 tc_fence_after();
-                const uint32_t idesc = idesc_bf16(128, ly.N);
+                const uint32_t idesc = fp8 ? idesc_e4m3(128, ly.N) : idesc_bf16(128, ly.N);
                 int kg = 0;
                 bool ok = true;
                 for (int c = 0; c < ly.n_chunks; ++c) {
@@ -184,12 +197,16 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const ui
                     const uint32_t b_base = smem_u32(ring + s * TC_CHUNK_MAX);
                     const uint32_t lbo_b = (uint32_t)(ly.N * 16);
                     const uint32_t b_lo = (uint32_t)(ly.N * kc * 2);     // lo part after hi
-                    for (int kk = 0; kk < kc; kk += 16, kg += 16) {
-                        const uint32_t ao = a_base + (uint32_t)(kg / 8) * 2048u;
-                        const uint32_t bo = b_base + (uint32_t)(kk / 8) * lbo_b;
+                    for (int kk = 0; kk < kc; kk += plan.kmma, kg += plan.kmma) {
+                        const uint32_t ao = a_base + (uint32_t)(kg / plan.ck) * 2048u;
+                        const uint32_t bo = b_base + (uint32_t)(kk / plan.ck) * lbo_b;
                         const uint64_t ad = smem_desc(ao, 2048u, 128u);
                         const uint64_t bd = smem_desc(bo, lbo_b, 128u);
-                        mma_bf16(tmem, ad, bd, idesc, kg > 0 ? 1u : 0u);
+                        if (fp8) {
+                            mma_e4m3(tmem, ad, bd, idesc, kg > 0 ? 1u : 0u);
+                        } else {
+                            mma_bf16(tmem, ad, bd, idesc, kg > 0 ? 1u : 0u);
+                        }
                         if (split) {
                             mma_bf16(tmem, smem_desc(ao + a_part, 2048u, 128u), bd, idesc, 1u);
                             mma_bf16(tmem, ad, smem_desc(bo + b_lo, lbo_b, 128u), idesc, 1u);
@@ -208,9 +225,27 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const ui
         const int r = q * 32 + lane;            // row of the tile owned by this thread
         const int grow = row0 + r;
         const uint32_t a_base = smem_u32(A);
-        // observation tile -> BF16 A operand, one row at a time per warp
+        // observation tile -> BF16 (or E4M3) A operand, one row at a time per warp
         const TcLayer &l0 = plan.layer[0];
-        for (int rr = 0; rr < 32; ++rr) {
+        const float *qa = inv_sx + (size_t)agent * MAX_LAYERS;        // FP8 only
+        for (int rr = 0; rr < 32 && fp8; ++rr) {
+            const int row = q * 32 + rr;
+            const int g = row0 + row;
+            const float inv = qa[0];
+            for (int c = lane; c < l0.K / 16; c += 32) {
+                float v[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int k = c * 16 + i;
+                    v[i] = (g < n && k < l0.fin) ? __ldg(obs + (int64_t)g * ld + k) : 0.0f;
+                }
+                uint32_t w[4];
+                e4m3_pack16(v, inv, w);
+                const uint32_t at = a_base + (uint32_t)c * 2048u + (uint32_t)(row / 8) * 128u + (uint32_t)(row % 8) * 16u;
+                st_shared_v4(at, w[0], w[1], w[2], w[3]);
+            }
+        }
+        for (int rr = 0; rr < 32 && !fp8; ++rr) {
             const int row = q * 32 + rr;
             const int g = row0 + row;
             for (int c = lane; c < l0.K / 8; c += 32) {
@@ -236,15 +271,28 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const ui
             if (!mbar_wait(acc_full, (uint32_t)l & 1u, abort, err, 16u, TC_WAIT_NS)) break;
             tc_fence_after();
             const float *bl = bias + ((size_t)agent * MAX_LAYERS + l) * 256;
+            const float *dl = dq + ((size_t)agent * MAX_LAYERS + l) * 256;          // FP8 only
             for (int c0 = 0; c0 < ly.N; c0 += 16) {
                 uint32_t v[16];
                 __syncwarp();
                 tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
                 tmem_ld_wait();
                 float x[16];
+                if (fp8) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) x[i] = __uint_as_float(v[i]) + __ldg(bl + c0 + i);
-                if (!last) {
+                    for (int i = 0; i < 16; ++i)
+                        x[i] = __fmaf_rn(__uint_as_float(v[i]), __ldg(dl + c0 + i), __ldg(bl + c0 + i));
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) x[i] = __uint_as_float(v[i]) + __ldg(bl + c0 + i);
+                }
+                if (!last && fp8) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) x[i] = fmaxf(x[i], 0.0f);
+                    uint32_t w[4];
+                    e4m3_pack16(x, qa[l + 1], w);
+                    st_shared_v4(a_base + (uint32_t)(c0 / 16) * 2048u + row_off, w[0], w[1], w[2], w[3]);
+                } else if (!last) {
 #pragma unroll
                     for (int i = 0; i < 16; ++i) x[i] = fmaxf(x[i], 0.0f);
                     uint32_t w[8], wl[8];
@@ -265,6 +313,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const ui
                         if (col < ly.fout) yr[col] = plan.out_act ? tanhf(x[i]) : x[i];
                     }
                 }
+            }
+            if (!last && fp8 && (ly.N & 31)) {
+                // the next layer's K is rounded up to 32: zero the 16 columns past N
+                st_shared_v4(a_base + (uint32_t)(ly.N / 16) * 2048u + row_off, 0u, 0u, 0u, 0u);
             }
             if (!last) {
                 fence_proxy_async_smem();
@@ -287,7 +339,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const ui
 // ------------------------------------------------------------- host side
 int tc_create(fr_ensemble *e)
 {
-    if (e->precision != FR_PREC_BF16 && e->precision != FR_PREC_BF16X3) {
+    if (e->precision != FR_PREC_BF16 && e->precision != FR_PREC_BF16X3 && e->precision != FR_PREC_FP8) {
         set_error("ensemble_create: precision %d has no tensor-core path in this build", e->precision);
         return FR_EINVAL;
     }
@@ -307,6 +359,7 @@ int tc_create(fr_ensemble *e)
     }
     std::vector<uint8_t> img((size_t)e->M * p.agent_bytes, 0);
     std::vector<float> bias((size_t)e->M * MAX_LAYERS * 256, 0.0f);
+    const bool fp8 = p.esz == 1;
     for (int j = 0; j < e->M; ++j) {
         const float *P = host.data() + (size_t)j * e->P;
         uint8_t *aimg = img.data() + (size_t)j * p.agent_bytes;
@@ -316,11 +369,22 @@ int tc_create(fr_ensemble *e)
             const float *B = P + e->b_off[l];
             for (int n = 0; n < ly.fout; ++n) {
                 bias[((size_t)j * MAX_LAYERS + l) * 256 + n] = B[n];
+                // FP8: per-output-channel scale max_k |W[n][k]| / 448 (1 for a zero row)
+                float amax = 0.0f;
+                for (int k = 0; k < ly.fin; ++k) amax = std::max(amax, std::fabs(W[(size_t)n * ly.fin + k]));
+                const float sw = amax > 0.0f ? amax / E4M3_MAX : 1.0f;
+                const float inv = 1.0f / sw;
+                t->sw[j][l][n] = sw;
                 for (int k = 0; k < ly.fin; ++k) {
                     const int c = k / ly.KC, kk = k % ly.KC;
                     const int kc = std::min(ly.KC, ly.K - c * ly.KC);
-                    const size_t off = ly.off + (size_t)c * ly.N * ly.KC * 2 * p.parts + chunk_off(ly.N, n, kk);
+                    const size_t off = ly.off + (size_t)c * ly.N * ly.KC * p.esz * p.parts +
+                                       chunk_off(ly.N, n, kk, p.ck, p.esz);
                     const float wv = W[(size_t)n * ly.fin + k];
+                    if (fp8) {
+                        aimg[off] = (uint8_t)__nv_cvt_float_to_fp8(wv * inv, __NV_SATFINITE, __NV_E4M3);
+                        continue;
+                    }
                     const uint16_t b = f32_to_bf16_rne(wv);
                     memcpy(aimg + off, &b, 2);
                     if (p.split == 3) {
@@ -332,15 +396,19 @@ int tc_create(fr_ensemble *e)
         }
     }
     const uint64_t ib = img.size(), bb = bias.size() * 4;
+    const uint64_t qb = fp8 ? bb + (uint64_t)e->M * MAX_LAYERS * 4 : 0;   // dq + inv_sx
     int rc;
     if ((rc = dev_alloc(e->ctx, (void **)&t->img, ib)) || (rc = dev_alloc(e->ctx, (void **)&t->bias, bb)) ||
-        (rc = dev_alloc(e->ctx, (void **)&t->err, 256))) {
+        (rc = dev_alloc(e->ctx, (void **)&t->err, 256)) ||
+        (fp8 && (rc = dev_alloc(e->ctx, (void **)&t->dq, qb)))) {
         dev_free(e->ctx, t->img, ib);
         dev_free(e->ctx, t->bias, bb);
+        dev_free(e->ctx, t->err, 256);
         delete t;
         return rc;
     }
-    t->bytes = ib + bb + 256;
+    if (fp8) t->inv_sx = t->dq + (size_t)e->M * MAX_LAYERS * 256;
+    t->bytes = ib + bb + 256 + qb;
     err = cudaMemcpy(t->img, img.data(), ib, cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(t->bias, bias.data(), bb, cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemset(t->err, 0, 256);
@@ -367,17 +435,55 @@ void tc_destroy(fr_ensemble *e)
     dev_free(e->ctx, t->img, (uint64_t)e->M * t->plan.agent_bytes);
     dev_free(e->ctx, t->bias, (uint64_t)e->M * MAX_LAYERS * 256 * 4);
     dev_free(e->ctx, t->err, 256);
+    if (t->dq) dev_free(e->ctx, t->dq, (uint64_t)e->M * MAX_LAYERS * (256 + 1) * 4);
     delete t;
     e->tc = nullptr;
+}
+
+// Set the FP8 activation scales sx[j][l] (host [M][L]): recompute the
+// dequantisation factors and inverse scales on the host and upload them.
+int tc_set_act_scales(fr_ensemble *e, const float *scales)
+{
+    TcImage *t = e->tc;
+    FR_CHECK(t && t->plan.esz == 1, FR_EINVAL, "activation scales apply to FP8 ensembles only");
+    for (int i = 0; i < e->M * e->L; ++i)
+        FR_CHECK(std::isfinite(scales[i]) && scales[i] > 0.0f, FR_EINVAL,
+                 "activation scale %d (%g) must be finite and > 0", i, (double)scales[i]);
+    std::vector<float> dq((size_t)e->M * MAX_LAYERS * 256, 0.0f), inv((size_t)e->M * MAX_LAYERS, 0.0f);
+    for (int j = 0; j < e->M; ++j) {
+        for (int l = 0; l < e->L; ++l) {
+            const float sx = scales[j * e->L + l];
+            t->sx[j][l] = sx;
+            inv[(size_t)j * MAX_LAYERS + l] = 1.0f / sx;
+            for (int n = 0; n < t->plan.layer[l].fout; ++n)
+                dq[((size_t)j * MAX_LAYERS + l) * 256 + n] = sx * t->sw[j][l][n];
+        }
+    }
+    FR_CUDA(cudaMemcpy(t->dq, dq.data(), dq.size() * 4, cudaMemcpyHostToDevice));
+    FR_CUDA(cudaMemcpy(t->inv_sx, inv.data(), inv.size() * 4, cudaMemcpyHostToDevice));
+    t->scaled = true;
+    return FR_OK;
+}
+
+int tc_get_act_scales(const fr_ensemble *e, float *scales)
+{
+    const TcImage *t = e->tc;
+    FR_CHECK(t && t->plan.esz == 1, FR_EINVAL, "activation scales apply to FP8 ensembles only");
+    FR_CHECK(t->scaled, FR_ENOTREADY, "FP8 ensemble has no activation scales yet");
+    for (int j = 0; j < e->M; ++j)
+        for (int l = 0; l < e->L; ++l) scales[j * e->L + l] = t->sx[j][l];
+    return FR_OK;
 }
 
 int tc_forward(const fr_ensemble *e, const float *obs, int ld, int n, float *y, cudaStream_t s)
 {
     const TcImage *t = e->tc;
     FR_CHECK(t, FR_EINVAL, "tensor-core image missing");
+    FR_CHECK(t->plan.esz != 1 || t->scaled, FR_ENOTREADY,
+             "FP8 ensemble needs activation scales (ensemble_set_act_scales or ensemble_calibrate_sync)");
     dim3 grid(ceil_div(n, 128), e->M);
-    k_tc_forward<<<grid, TC_THREADS, tc_smem_bytes(t->plan), s>>>(t->plan, t->img, t->bias, obs, ld, n, y,
-                                                                  t->err);
+    k_tc_forward<<<grid, TC_THREADS, tc_smem_bytes(t->plan), s>>>(t->plan, t->img, t->bias, t->dq, t->inv_sx,
+                                                                  obs, ld, n, y, t->err);
     FR_CUDA(cudaGetLastError());
     return FR_OK;
 }

@@ -88,6 +88,15 @@ int ensemble_validate(fr_ensemble *e, fr_env *env, int32_t T, double threshold, 
         d.out_act = e->out_act;
         fr_ensemble *one = nullptr;
         if ((rc = ensemble_create(e->ctx, &d, &one))) break;
+        if (e->precision == FR_PREC_FP8) {
+            // the agent keeps its own activation scales
+            float sx[MAX_AGENTS * MAX_LAYERS];
+            if (!(rc = tc_get_act_scales(e, sx))) rc = tc_set_act_scales(one, sx + (size_t)j * e->L);
+            if (rc) {
+                ensemble_destroy(one);
+                break;
+            }
+        }
         if (!(rc = env_restore(env, snap.data(), snap.size())) &&
             !(rc = rollout(env, one, T, nullptr, met, s))) {
             const cudaError_t ce = cudaMemcpyAsync(hm.data(), met, 24ull * N, cudaMemcpyDeviceToHost, s);

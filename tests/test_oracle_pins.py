@@ -494,3 +494,90 @@ def test_indicator_windows_see_no_future():
         part = oracle.indicators(mk.close[:t + 1], mk.high[:t + 1], mk.low[:t + 1])
         assert np.array_equal(part, full[:t + 1])
 
+
+
+# ---------------------------------------------------------- FP8 E4M3 actors
+def _e4m3_codes():
+    torch = pytest.importorskip("torch")
+    v = torch.arange(256, dtype=torch.uint8).view(torch.float8_e4m3fn).to(torch.float64).numpy()
+    return np.unique(v[np.isfinite(v)])
+
+
+def test_e4m3_round_agrees_with_torch_float8_cast():
+    # a library routine: torch's float8_e4m3fn conversion (round to nearest
+    # even) on in-range values, every code and every midpoint between codes
+    torch = pytest.importorskip("torch")
+    codes = _e4m3_codes()
+    assert codes.size == 253 and codes.max() == 448.0 and codes[codes > 0].min() == 2.0 ** -9
+    mids = (codes[1:] + codes[:-1]) / 2
+    rng = np.random.default_rng(8)
+    x = np.concatenate([codes, mids, rng.uniform(-448, 448, 50000), rng.normal(0, 0.01, 50000)]).astype(np.float32)
+    want = torch.from_numpy(x).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(oracle.e4m3_round(x), want)
+
+
+def test_e4m3_round_special_cases():
+    r = oracle.e4m3_round
+    assert r(1.0625) == 1.0 and r(1.1875) == 1.25          # ties to the even fraction
+    assert r(2.0 ** -10) == 0.0 and r(3 * 2.0 ** -10) == 2.0 ** -8    # subnormal ties
+    assert r(448.0) == 448.0 and r(460.0) == 448.0 and r(1e9) == 448.0 and r(-500.0) == -448.0
+    assert r(0.0) == 0.0 and r(-2.0 ** -9) == -2.0 ** -9
+
+
+def test_fp8_weights_scale_and_codes():
+    rng = np.random.default_rng(3)
+    W = rng.normal(0, 0.1, (40, 70)).astype(np.float32)
+    W[5] = 0.0
+    q, sw = oracle.fp8_weights(W)
+    assert sw[5] == 1.0 and (q[5] == 0).all()
+    nz = np.arange(40) != 5
+    assert (np.abs(q[nz]).max(axis=1) == 448.0).all()        # each row's extreme maps to +-448
+    # dequantised weights within half an E4M3 step of the original
+    rel = np.abs(q[nz] * sw[nz, None] - W[nz]) / np.maximum(np.abs(W[nz]), 2.0 ** -6 * sw[nz, None])
+    assert rel.max() <= 2.0 ** -4 * (1 + 1e-6)
+
+
+def test_fp8_forward_is_exact_on_representable_networks():
+    # layer 1 = 28 I (row scale 28 / 448 = 1/16, codes 448), inputs powers of
+    # two up to 4 (hidden 28 x = 1.75 2^(j+4), a code), layer 2 code-valued
+    # with a 448 in every row (row scale 1), integer biases, activation scales
+    # 1: every quantisation is exact and every sum fits float64, so the FP8
+    # forward equals the fp64 forward bit for bit
+    codes = _e4m3_codes()
+    rng = np.random.default_rng(4)
+    fin = h = 24
+    fout = 7
+    W1 = np.eye(h, fin, dtype=np.float32) * np.float32(28.0)
+    b1 = np.zeros(h, np.float32)
+    W2 = rng.choice(codes, (fout, h)).astype(np.float32)
+    W2[:, 0] = 448.0
+    b2 = rng.integers(-5, 6, fout).astype(np.float32)
+    params = np.concatenate([W1.ravel(), b1, W2.ravel(), b2])
+    x = np.ldexp(1.0, rng.integers(-6, 3, (50, fin))).astype(np.float32)
+    x[rng.random(x.shape) < 0.2] = 0.0
+    dims = (fin, h, fout)
+    y8 = oracle.fp8_forward(dims, params, [1.0, 1.0], x, 0)
+    assert np.array_equal(y8, oracle.net_forward(dims, params, x, 0))
+    # a scale that is not a power of two breaks exactness, by a bounded amount
+    y8b = oracle.fp8_forward(dims, params, [1.0, 0.3], x, 0)
+    # (hidden / 0.3 stays in the normal range, where rounding errs by at most 2^-4 relative)
+    bound = 2.0 ** -4 * (np.abs(28.0 * x.astype(np.float64)) @ np.abs(W2.astype(np.float64)).T)
+    assert not np.array_equal(y8b, y8) and (np.abs(y8b - y8) <= bound * (1 + 1e-6)).all()
+
+
+def test_fp8_calibration_scales_homogeneously():
+    # zero biases: ReLU networks are positively homogeneous, so doubling the
+    # batch doubles every layer's maximum and scale exactly
+    rng = np.random.default_rng(6)
+    dims = (12, 32, 16, 3)
+    params = synth.actor_params(dims, 1, seed=2)[0].copy()
+    off = 0
+    for fin, fout in zip(dims[:-1], dims[1:]):
+        off += fin * fout
+        params[off:off + fout] = 0
+        off += fout
+    obs = rng.normal(0, 1, (200, 12)).astype(np.float32)
+    s1 = oracle.fp8_calibrate(dims, params, obs)
+    s2 = oracle.fp8_calibrate(dims, params, 2 * obs)
+    assert np.array_equal(s2, 2 * s1)
+    assert s1[0] == np.float32(np.abs(obs).max()) / np.float32(448)
