@@ -299,6 +299,41 @@ def prep_line(fr, ctx, mk, mk_np, e, stream, iters=20):
     return res
 
 
+def replay_line(fr, ctx, env, ens, T, dev, stream, peak_gbs, capacity=1 << 20, B=65536):
+    """Device replay buffer: push of the full trajectory of one 2,048-env x
+    256-step BF16 rollout (524,288 transitions, obs 301 floats) into a
+    1,048,576-transition ring, and a 65,536-transition uniform sample.
+    Algorithmic bytes per transition: read s, s' (2 x 1,204), a (120), r (4),
+    done (1) and write the same (plus the done row read for validity on push)."""
+    import torch
+    N, D = env.N, env.D
+    tr = {"obs": torch.empty(T, N, D, device=dev), "act": torch.empty(T, N, 30, device=dev),
+          "rew_f32": torch.empty(T, N, device=dev), "done": torch.empty(T, N, dtype=torch.uint8, device=dev)}
+    fr.env_reset(env)
+    fr.rollout(env, ens, T, traj=tr)
+    last = torch.empty(N, D, device=dev)
+    fr.env_observe(env, last)
+    rb = fr.replay_create(ctx, env, capacity)
+    per = 2 * (2 * D * 4 + 30 * 4 + 4 + 1)
+    push_dt = time_kernel(lambda: fr.replay_push(rb, env, tr, T, last), 10, stream)
+    size, pushed, _ = fr.replay_size(rb)
+    moved = pushed // 13                                   # 3 warm-up + 10 timed pushes, all rows real
+    out = {"obs": torch.empty(B, D, device=dev), "next_obs": torch.empty(B, D, device=dev),
+           "act": torch.empty(B, 30, device=dev), "rew": torch.empty(B, device=dev),
+           "done": torch.empty(B, dtype=torch.uint8, device=dev)}
+    sample_dt = time_kernel(lambda: fr.replay_sample(rb, B, 1234, 0, out=out), 20, stream)
+    res = {"push": {"transitions": moved, "us": push_dt * 1e6, "bytes": moved * (per + 1),
+                    "achieved": moved * (per + 1) / push_dt / 1e9},
+           "sample": {"transitions": B, "us": sample_dt * 1e6, "bytes": B * per, "achieved": B * per / sample_dt / 1e9},
+           "unit": "GB/s", "peak": peak_gbs, "capacity": capacity, "bytes_per_transition": per}
+    res["push"]["frac"] = res["push"]["achieved"] / peak_gbs
+    res["sample"]["frac"] = res["sample"]["achieved"] / peak_gbs
+    rb.close()
+    del tr, out
+    fr.env_reset(env)
+    return res
+
+
 def uneven_line(fr, ctx, dev, flush, stream, reps=3):
     """4,096 stock envs with asset counts 10-30 and windows 5-250 days, BF16
     fused rollout over the longest window, tiles packed by window vs not."""
@@ -489,12 +524,15 @@ def run_gpu(args):
     env_step["peak_source"] = f"hbm_gbs, {peak_src}"
 
     prep = prep_line(fr, ctx, mk, w.market, w.envs, stream)
+    replay = replay_line(fr, ctx, env, ens_bf16, T, dev, stream, peaks["hbm_gbs"])
 
     # serving (backtest_submit / backtest_poll): p50 / p99 request latency
     serving = serving_line(fr, ctx, mk, {"fused_bf16": ens_bf16, "plain_fp32": ens_fp32}) \
         if not args.no_serving else None
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers, from the reset
+    # state (every env live for the whole horizon)
+    fr.env_reset(env)
     snap = fr.env_snapshot(env)
     host_met = torch.empty(N, 3, dtype=torch.float64, pin_memory=True)
     e2e_times = []
@@ -556,6 +594,7 @@ def run_gpu(args):
                                           "peak_source": "measured bf16_tflops burst x 2 (nominal FP8/BF16)"},
                      "env_step_kernel": env_step},
         "data_prep": prep,
+        "replay": replay,
         "crypto_c3": crypto,
         "uneven_c4": uneven,
         "gpu_launches": launches_per_rollout * args.steps,

@@ -459,6 +459,45 @@ int env_tile_packing_efficiency(const fr_env *env, float *eff);
 int env_set_kernel_timing(fr_env *env, int32_t on);
 int env_last_kernel_ms(fr_env *env, float *ms);
 
+/* ---------------------------------------------------------- replay buffer */
+typedef struct fr_replay fr_replay;
+
+/* The replay buffer of the training process (Sec. 3.2: the reservoir
+ * between the simulation phase and the learning phase), resident on the
+ * device and fed by rollout trajectories (the T x N x D tensors of
+ * Sec. 4.3.2).  A FIFO ring of `capacity` transitions (s, a, r, s', done):
+ * s and s' float [D], a float [K] (stock) or uint8 (crypto), r the
+ * learner's float reward copy, done uint8; shapes from `env`.  The number
+ * of transitions pushed is kept on the device, so push and sample are
+ * asynchronous on their stream (and may be captured into a graph).
+ *  replay_create: capacity 1..2^31-1; FR_ENOMEM past the context budget.
+ *  replay_push: appends the real steps of a T-step trajectory of `env` (obs,
+ *    act, rew_f32 and done required; obs_ld as in fr_traj) in (t, env) order.
+ *    Row (t, e) is a real step unless the env was done before it: without
+ *    auto-reset, done[t-1][e] = 1, or for t = 0 live0[e] = 0 (live0 device
+ *    uint8 [N], NULL = all live); with auto-reset every row is real.  s' of
+ *    row (t, e) is obs[t+1][e], and last_obs[e] (device, rows obs_ld apart:
+ *    the observation after the rollout, env_observe) for t = T - 1 (after
+ *    a done row of an auto-reset env s' is the restarted env's first
+ *    state; done marks it).  Once full, each new transition replaces the
+ *    oldest.
+ *  replay_sample: B transitions drawn uniformly with replacement from the
+ *    current contents: draw b takes position floor(x * size / 2^32) (0 =
+ *    oldest), x the first word of Philox4x32-10 with counter (b, counter low,
+ *    counter high, 3) and key (seed low, seed high).  Outputs (device, each
+ *    may be NULL): obs and next_obs float [B][D], act float [B][K] or uint8
+ *    [B], rew float [B], done uint8 [B], index int64 [B] (the position).  An
+ *    empty buffer writes index -1 and nothing else and sets error bit 0.
+ *  replay_size_sync: current size (min(pushed, capacity)), transitions ever
+ *    pushed and the error bits, after the stream's work so far. */
+int replay_create(fr_ctx *ctx, const fr_env *env, int64_t capacity, fr_replay **out);
+void replay_destroy(fr_replay *rb);
+int replay_push(fr_replay *rb, const fr_env *env, const fr_traj *traj, int32_t T, const float *last_obs,
+                const uint8_t *live0, void *stream);
+int replay_sample(fr_replay *rb, int32_t B, uint64_t seed, uint64_t counter, float *obs, void *act,
+                  float *rew, float *next_obs, uint8_t *done, int64_t *index, void *stream);
+int replay_size_sync(fr_replay *rb, int64_t *size, int64_t *pushed, uint32_t *errors, void *stream);
+
 /* ---------------------------------------------------------------- serving */
 /* Backtests as requests: many independent backtests (each a group of envs
  * over one window, Sec. 4.2.1 trajectories) served by one GPU with

@@ -326,6 +326,50 @@ def splitmix64(x: int) -> int:
     return int(f(C.c_uint64(int(x) & (2**64 - 1))))
 
 
+class ReplayRef:
+    """The replay buffer of Sec. 3.2 restated plainly: a list of transitions
+    in push order, of which the last `capacity` are the contents.
+
+    A trajectory's rows are taken in (t, env) order; a row is a real step
+    unless its env was done before it (done[t-1][e]; not live at t = 0),
+    with auto-reset every row is; s' is obs[t+1][e], or the observation after
+    the rollout at the last row.  A sample draw b takes position
+    floor(x * size / 2^32) of the contents (0 = oldest), x the first word of
+    Philox4x32-10 with counter (b, counter low, counter high, 3) and key
+    (seed low, seed high)."""
+
+    def __init__(self, capacity: int):
+        self.capacity = int(capacity)
+        self.items = []
+
+    def push(self, obs, act, rew_f32, done, last_obs, live0=None, auto_reset=False):
+        T, N = done.shape
+        for t in range(T):
+            for e in range(N):
+                if auto_reset:
+                    real = True
+                elif t == 0:
+                    real = live0 is None or bool(live0[e])
+                else:
+                    real = done[t - 1, e] == 0
+                if not real:
+                    continue
+                nxt = obs[t + 1, e] if t + 1 < T else last_obs[e]
+                self.items.append((obs[t, e], act[t, e], rew_f32[t, e], nxt, done[t, e]))
+
+    def contents(self):
+        return self.items[max(0, len(self.items) - self.capacity):]
+
+    def sample_positions(self, B: int, seed: int, counter: int):
+        size = len(self.contents())
+        key = [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF]
+        out = []
+        for b in range(B):
+            x = philox4x32_10([b, counter & 0xFFFFFFFF, (counter >> 32) & 0xFFFFFFFF, 3], key)[0]
+            out.append((x * size) >> 32 if size else -1)
+        return out
+
+
 def market_table(market) -> np.ndarray:
     """A stock market's indicator table: its own ``ind`` when set, else the
     8 indicators from its close / high / low."""

@@ -26,6 +26,7 @@ __all__ = [
     "EXPLORE_NONE", "EXPLORE_GAUSSIAN", "EXPLORE_EPS_GREEDY", "Server", "fr_server_create", "backtest_submit",
     "backtest_poll", "fr_server_stats", "FrError", "lib", "market_indicators", "fr_market_indicators",
     "env_perturb", "ensemble_set_act_scales", "ensemble_get_act_scales", "ensemble_calibrate_sync",
+    "Replay", "replay_create", "replay_push", "replay_sample", "replay_size",
     "PATH_AUTO", "PATH_UNFUSED",
     "ACT_I32_SHARES", "ACT_F32_UNIT", "ACT_U8_DISCRETE", "PREC_FP32", "PREC_BF16",
     "PREC_FP8", "PREC_BF16X3", "COMBINE_MEAN", "COMBINE_VOTE", "TASK_STOCK", "TASK_CRYPTO",
@@ -360,26 +361,86 @@ def rollout(env: Env, ens: Ensemble, T: int, *, traj: dict | None = None, metric
             stream=None):
     """traj: optional dict of device tensors obs [T][N][ld], act, rew, rew_f32, done."""
     import torch
-    tp = None
-    if traj:
-        t = _lib.Traj()
-        ob = traj.get("obs")
-        ld = int(traj.get("obs_ld", ob.shape[-1] if ob is not None else 0))
-        t.obs = _dptr(ob, torch.float32, T * env.N * max(ld, 1), "traj obs")
-        t.obs_ld = ld
-        act = traj.get("act")
-        if act is not None:
-            if env.task == TASK_STOCK:
-                t.act = _dptr(act, torch.float32, T * env.N * env.K, "traj act")
-            else:
-                t.act = _dptr(act, torch.uint8, T * env.N, "traj act")
-        t.rew = _dptr(traj.get("rew"), torch.int64, T * env.N, "traj rew")
-        t.rew_f32 = _dptr(traj.get("rew_f32"), torch.float32, T * env.N, "traj rew_f32")
-        t.done = _dptr(traj.get("done"), torch.uint8, T * env.N, "traj done")
-        tp = C.byref(t)
+    tp = C.byref(_traj_struct(env, T, traj)) if traj else None
     _lib.check(lib().rollout(env, ens, int(T), tp,
                              _dptr(metrics, torch.float64, env.N * 3, "metrics"),
                              _stream(stream)), "rollout")
+
+
+# ------------------------------------------------------------ replay buffer
+class Replay(_Handle):
+    """Device-resident FIFO replay buffer of transitions (s, a, r, s', done)."""
+    _destroy = "replay_destroy"
+
+
+def replay_create(ctx: Ctx, env: Env, capacity: int) -> Replay:
+    out = C.c_void_p()
+    _lib.check(lib().replay_create(ctx, env, int(capacity), C.byref(out)), "replay_create")
+    rb = Replay(out.value, keep=(ctx,))
+    rb.D, rb.K, rb.task, rb.capacity = env.D, env.K, env.task, int(capacity)
+    return rb
+
+
+def _traj_struct(env, T, traj):
+    import torch
+    t = _lib.Traj()
+    ob = traj.get("obs")
+    ld = int(traj.get("obs_ld", ob.shape[-1] if ob is not None else 0))
+    t.obs = _dptr(ob, torch.float32, T * env.N * max(ld, 1), "traj obs")
+    t.obs_ld = ld
+    act = traj.get("act")
+    if act is not None:
+        if env.task == TASK_STOCK:
+            t.act = _dptr(act, torch.float32, T * env.N * env.K, "traj act")
+        else:
+            t.act = _dptr(act, torch.uint8, T * env.N, "traj act")
+    t.rew = _dptr(traj.get("rew"), torch.int64, T * env.N, "traj rew")
+    t.rew_f32 = _dptr(traj.get("rew_f32"), torch.float32, T * env.N, "traj rew_f32")
+    t.done = _dptr(traj.get("done"), torch.uint8, T * env.N, "traj done")
+    return t
+
+
+def replay_push(rb: Replay, env: Env, traj: dict, T: int, last_obs, live0=None, stream=None):
+    """Append the real steps of a T-step trajectory (obs, act, rew_f32, done);
+    last_obs: the observation after the rollout, live0: uint8 [N] or None."""
+    import torch
+    t = _traj_struct(env, T, traj)
+    ld = t.obs_ld or env.D
+    _lib.check(lib().replay_push(rb, env, C.byref(t), int(T), _dptr(last_obs, torch.float32, env.N * ld, "last_obs"),
+                                 _dptr(live0, torch.uint8, env.N, "live0"), _stream(stream)), "replay_push")
+
+
+def replay_sample(rb: Replay, B: int, seed: int, counter: int = 0, out: dict | None = None, stream=None) -> dict:
+    """B uniform draws with replacement: dict of device tensors obs, act,
+    rew, next_obs, done, index."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if out is None:
+        out = {"obs": torch.empty(B, rb.D, device=dev), "next_obs": torch.empty(B, rb.D, device=dev),
+               "act": (torch.empty(B, rb.K, device=dev) if rb.task == TASK_STOCK
+                       else torch.empty(B, dtype=torch.uint8, device=dev)),
+               "rew": torch.empty(B, device=dev), "done": torch.empty(B, dtype=torch.uint8, device=dev),
+               "index": torch.empty(B, dtype=torch.int64, device=dev)}
+    act = out.get("act")
+    a_ptr = None if act is None else (_dptr(act, torch.float32, B * rb.K, "act") if rb.task == TASK_STOCK
+                                      else _dptr(act, torch.uint8, B, "act"))
+    _lib.check(lib().replay_sample(rb, int(B), C.c_uint64(int(seed) & (2**64 - 1)),
+                                   C.c_uint64(int(counter) & (2**64 - 1)),
+                                   _dptr(out.get("obs"), torch.float32, B * rb.D, "obs"), a_ptr,
+                                   _dptr(out.get("rew"), torch.float32, B, "rew"),
+                                   _dptr(out.get("next_obs"), torch.float32, B * rb.D, "next_obs"),
+                                   _dptr(out.get("done"), torch.uint8, B, "done"),
+                                   _dptr(out.get("index"), torch.int64, B, "index"), _stream(stream)),
+               "replay_sample")
+    return out
+
+
+def replay_size(rb: Replay, stream=None):
+    """(size, pushed, error bits) after the stream's work so far."""
+    size, pushed, err = C.c_int64(), C.c_int64(), C.c_uint32()
+    _lib.check(lib().replay_size_sync(rb, C.byref(size), C.byref(pushed), C.byref(err), _stream(stream)),
+               "replay_size_sync")
+    return size.value, pushed.value, err.value
 
 
 # ------------------------------------------------------------------ serving

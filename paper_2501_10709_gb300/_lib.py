@@ -130,6 +130,11 @@ SIGNATURES = {
     "ensemble_set_act_scales": (i32, [vp, vp]),
     "ensemble_get_act_scales": (i32, [vp, vp]),
     "ensemble_calibrate_sync": (i32, [vp, vp, i32, vp]),
+    "replay_create": (i32, [vp, vp, i64, vp]),
+    "replay_destroy": (None, [vp]),
+    "replay_push": (i32, [vp, vp, vp, i32, vp, vp, vp]),
+    "replay_sample": (i32, [vp, i32, u64, u64, vp, vp, vp, vp, vp, vp, vp]),
+    "replay_size_sync": (i32, [vp, vp, vp, vp, vp]),
 }
 
 _lock = threading.Lock()

@@ -581,3 +581,53 @@ def test_fp8_calibration_scales_homogeneously():
     s2 = oracle.fp8_calibrate(dims, params, 2 * obs)
     assert np.array_equal(s2, 2 * s1)
     assert s1[0] == np.float32(np.abs(obs).max()) / np.float32(448)
+
+
+# ------------------------------------------------------------- replay buffer
+def _tiny_traj():
+    T, N, D = 3, 2, 2
+    obs = np.arange(T * N * D, dtype=np.float32).reshape(T, N, D)
+    act = -np.arange(T * N, dtype=np.float32).reshape(T, N, 1)
+    rew = np.arange(T * N, dtype=np.float32).reshape(T, N)          # row index as the reward
+    done = np.array([[0, 0], [1, 0], [1, 1]], np.uint8)        # env 0 ends at t = 1, env 1 at t = 2
+    last = np.full((N, D), 99.0, np.float32)
+    return obs, act, rew, done, last
+
+
+def _rews(rb):
+    return [int(i[2]) for i in rb.contents()]
+
+
+def test_replay_ref_takes_real_steps_in_order():
+    obs, act, rew, done, last = _tiny_traj()
+    rb = oracle.ReplayRef(100)
+    rb.push(obs, act, rew, done, last)
+    # (t, e) order; row (2, 0) follows env 0's last step and is not a step
+    got = [(int(i[2]), i[0].tolist(), int(i[1][0]), i[3].tolist(), int(i[4])) for i in rb.contents()]
+    assert got == [(0, [0, 1], 0, [4, 5], 0), (1, [2, 3], -1, [6, 7], 0), (2, [4, 5], -2, [8, 9], 1),
+                   (3, [6, 7], -3, [10, 11], 0), (5, [10, 11], -5, [99, 99], 1)]
+    rb2 = oracle.ReplayRef(100)
+    rb2.push(obs, act, rew, done, last, live0=np.array([1, 0], np.uint8))
+    assert _rews(rb2) == [0, 2, 3, 5]
+    rb3 = oracle.ReplayRef(100)
+    rb3.push(obs, act, rew, done, last, auto_reset=True)
+    assert _rews(rb3) == [0, 1, 2, 3, 4, 5] and rb3.contents()[4][3].tolist() == [99, 99]
+
+
+def test_replay_ref_fifo_and_sampling():
+    obs, act, rew, done, last = _tiny_traj()
+    rb = oracle.ReplayRef(4)
+    rb.push(obs, act, rew, done, last)                             # 5 steps, capacity 4: the oldest goes
+    assert _rews(rb) == [1, 2, 3, 5]
+    rb.push(obs, act, rew, done, last)
+    assert len(rb.items) == 10 and _rews(rb) == [1, 2, 3, 5]
+    rb.push(obs[:1], act[:1], rew[:1], done[:1], obs[1])
+    assert _rews(rb) == [3, 5, 0, 1]
+    pos = oracle.ReplayRef(7)
+    pos.items = list(range(7))
+    p = np.array(pos.sample_positions(7000, 123, 5))
+    assert p.min() == 0 and p.max() == 6
+    counts = np.bincount(p, minlength=7)
+    assert ((counts - 1000) ** 2 / 1000).sum() < 6 + 5 * math.sqrt(12)      # chi-square, 6 dof
+    assert pos.sample_positions(50, 123, 5) == list(p[:50]) and pos.sample_positions(50, 123, 6) != list(p[:50])
+    assert oracle.ReplayRef(3).sample_positions(4, 1, 0) == [-1] * 4
