@@ -44,7 +44,7 @@ __global__ void k_env_reset(EnvView v)
 // one thread per env, so that one instruction of the narrow FP64 pipe serves
 // 32 envs and no warp waits at a block barrier.
 template <int KIND>
-__global__ void __launch_bounds__(kStepEnvs * 32) k_stock_step(EnvView v, const void *act, int64_t *rew,
+__global__ void __launch_bounds__(kStepEnvs * 32, 2) k_stock_step(EnvView v, const void *act, int64_t *rew,
                                                                 float *rew_f32, uint8_t *done_out,
                                                                 float *obs, int ld)
 {
