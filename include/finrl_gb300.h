@@ -247,6 +247,10 @@ typedef struct fr_ensemble fr_ensemble;
                                  (hi*hi + lo*hi + hi*lo), fp32-class accuracy
                                  for discrete (argmax / vote) decisions      */
 
+#define FR_HEAD_Q 0           /* outputs are the Q-values (DQN, Double DQN)  */
+#define FR_HEAD_DUELING 1     /* outputs are [V, A_0 .. A_{n-1}] (Dueling DQN):
+                                 Q_a = (V + A_a) - mean_b A_b                */
+
 #define FR_COMBINE_MEAN 0     /* Sec. 5.2.1 weighted average of actions     */
 #define FR_COMBINE_VOTE 1     /* Sec. 5.2.2 majority vote of argmax actions */
 
@@ -258,7 +262,15 @@ typedef struct fr_ensemble fr_ensemble;
  *   a = a_0 + sum_{j>=1} w_j (a_j - a_0),
  * which is the weighted average when the weights sum to one and exactly a_0
  * for identical agents; VOTE takes each agent's argmax (lowest index on
- * ties) and returns the action with the strictly largest count, else 1. */
+ * ties) and returns the action with the strictly largest count, else 1.
+ * heads (VOTE only; Sec. 5.2.2 ensembles of DQN, Double DQN and Dueling DQN
+ * agents): per-agent FR_HEAD_*, host [M], NULL = all FR_HEAD_Q.  With any
+ * dueling agent the network has dims[L] = n_act + 1 outputs and a plain
+ * agent's Q-values are its first n_act outputs; otherwise n_act = dims[L].
+ * A dueling agent's Q-values are computed in float32 as
+ * Q_a = (y_0 + y_{1+a}) - m, m = (y_1 + ... + y_{n_act}) / n_act summed in
+ * index order, each operation rounded once.  Double DQN shares the DQN
+ * forward; it differs only in its learning target (ensemble_q_targets). */
 typedef struct {
     int32_t n_agents;         /* M, 1..8                                    */
     int32_t n_layers;         /* L, 1..4                                    */
@@ -268,11 +280,30 @@ typedef struct {
     int32_t precision;        /* FR_PREC_*                                  */
     int32_t combine;          /* FR_COMBINE_*                               */
     int32_t out_act;          /* 1 tanh, 0 identity                         */
+    const int32_t *heads;     /* host [M] FR_HEAD_* (VOTE only) or NULL     */
 } fr_ensemble_desc;
 
 int ensemble_create(fr_ctx *ctx, const fr_ensemble_desc *desc,
                     fr_ensemble **out);
 void ensemble_destroy(fr_ensemble *ens);
+
+/* Per-agent Q-values after each agent's head: obs device float
+ * [n][dims[0]], q device float [M][n][n_act].  VOTE ensembles only. */
+int ensemble_q(const fr_ensemble *ens, const float *obs, int32_t n, float *q, void *stream);
+
+/* Learning targets of the DQN family from replay samples (the consumer side
+ * of Sec. 3.2 for the crypto agents of Sec. 5.2.2, evaluated on the GPU):
+ * for every agent j of `online` and its counterpart in `target` (same
+ * shapes, heads and precision class),
+ *   a* = argmax_a Q_online_j(s', a) (Double DQN, double_q != 0) or
+ *        argmax_a Q_target_j(s', a) (DQN), lowest index on ties;
+ *   y_j = r + (done ? 0 : gamma * Q_target_j(s', a*)),
+ * float32, each operation rounded once.  next_obs device float
+ * [n][dims[0]], rew device float [n], done device uint8 [n] (NULL = none
+ * done), y device float [M][n].  The update itself is out of scope. */
+int ensemble_q_targets(const fr_ensemble *online, const fr_ensemble *target, const float *next_obs,
+                       const float *rew, const uint8_t *done, int32_t n, float gamma, int32_t double_q,
+                       float *y, void *stream);
 
 /* FP8 E4M3 ensembles (no counterpart in the paper, whose agents run in
  * fp32; an inference-precision option of the actors).  Weights: row n of

@@ -171,6 +171,37 @@ def net_forward(dims, params: np.ndarray, x: np.ndarray, out_act: int,
     return y
 
 
+# ------------------------------------------------- DQN-family heads, targets
+def head_q(y, head: int, n_act: int) -> np.ndarray:
+    """Q-values [..., n_act] from network outputs (float64).  A plain head
+    (DQN, Double DQN) reads the first n_act outputs; a dueling head (Wang et
+    al., ICML 2016) splits them into V = y_0 and A = y_1 .. y_n_act and
+    returns V + A_a - mean_b A_b."""
+    y = np.asarray(y, np.float64)
+    if head == 0:
+        return y[..., :n_act]
+    A = y[..., 1:1 + n_act]
+    return y[..., :1] + A - A.mean(axis=-1, keepdims=True)
+
+
+def q_targets(dims, params_online, params_target, heads, next_obs, rew, done, gamma: float,
+              double_q: bool) -> np.ndarray:
+    """[M][n] float64 learning targets r + (done ? 0 : gamma Q_target(s', a*)):
+    a* = argmax Q_online(s') for Double DQN (van Hasselt et al., AAAI 2016),
+    argmax Q_target(s') for DQN (Mnih et al., Nature 2015); lowest index on
+    ties; Q-values from the fp64 forward through each agent's head."""
+    n_act = dims[-1] - (1 if 1 in list(heads) else 0)
+    rew = np.asarray(rew, np.float64)
+    done = np.zeros(rew.shape, bool) if done is None else np.asarray(done).astype(bool)
+    out = []
+    for j in range(len(heads)):
+        qt = head_q(net_forward(dims, params_target[j], next_obs, 0), heads[j], n_act)
+        qs = head_q(net_forward(dims, params_online[j], next_obs, 0), heads[j], n_act) if double_q else qt
+        a = qs.argmax(axis=-1)                       # first maximum: lowest index on ties
+        out.append(rew + np.where(done, 0.0, gamma * qt[np.arange(len(a)), a]))
+    return np.array(out)
+
+
 # ------------------------------------------------------- FP8 E4M3 actors
 # The FP8 option of the actors has no counterpart in the paper (its agents
 # run in fp32); these follow the format definition and the library's stated

@@ -13,7 +13,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (ACT_F32_UNIT, ACT_I32_SHARES, ACT_U8_DISCRETE, COMBINE_MEAN,
+from ._lib import (ACT_F32_UNIT, ACT_I32_SHARES, ACT_U8_DISCRETE, COMBINE_MEAN, HEAD_DUELING, HEAD_Q,
                    COMBINE_VOTE, PATH_AUTO, PATH_UNFUSED, PREC_BF16, PREC_BF16X3, PREC_FP8,
                    PREC_FP32, TASK_CRYPTO, TASK_STOCK, FrError)
 
@@ -26,7 +26,8 @@ __all__ = [
     "EXPLORE_NONE", "EXPLORE_GAUSSIAN", "EXPLORE_EPS_GREEDY", "Server", "fr_server_create", "backtest_submit",
     "backtest_poll", "fr_server_stats", "FrError", "lib", "market_indicators", "fr_market_indicators",
     "env_perturb", "ensemble_set_act_scales", "ensemble_get_act_scales", "ensemble_calibrate_sync",
-    "Replay", "replay_create", "replay_push", "replay_sample", "replay_size",
+    "Replay", "replay_create", "replay_push", "replay_sample", "replay_size", "ensemble_q", "ensemble_q_targets",
+    "HEAD_Q", "HEAD_DUELING",
     "PATH_AUTO", "PATH_UNFUSED",
     "ACT_I32_SHARES", "ACT_F32_UNIT", "ACT_U8_DISCRETE", "PREC_FP32", "PREC_BF16",
     "PREC_FP8", "PREC_BF16X3", "COMBINE_MEAN", "COMBINE_VOTE", "TASK_STOCK", "TASK_CRYPTO",
@@ -287,18 +288,48 @@ def env_error_count(env: Env) -> int:
 
 
 def ensemble_create(ctx: Ctx, dims, params, *, weights=None, precision: int = PREC_FP32,
-                    combine: int = COMBINE_MEAN, out_act: int = 1) -> Ensemble:
+                    combine: int = COMBINE_MEAN, out_act: int = 1, heads=None) -> Ensemble:
+    """heads: per-agent HEAD_Q / HEAD_DUELING (VOTE ensembles), None = all HEAD_Q."""
     dims = np.ascontiguousarray(dims, np.int32)
     params = np.ascontiguousarray(params, np.float32)
     w = None if weights is None else np.ascontiguousarray(weights, np.float32)
+    hd = None if heads is None else np.ascontiguousarray(heads, np.int32)
     d = _lib.EnsembleDesc(n_agents=params.shape[0], n_layers=dims.size - 1, dims=_hptr(dims),
                           params=_hptr(params), weights=_hptr(w), precision=int(precision),
-                          combine=int(combine), out_act=int(out_act))
+                          combine=int(combine), out_act=int(out_act), heads=_hptr(hd))
     out = C.c_void_p()
     _lib.check(lib().ensemble_create(ctx, C.byref(d), C.byref(out)), "ensemble_create")
     e = Ensemble(out.value, keep=(ctx,))
     e.M, e.dims, e.combine, e.precision = params.shape[0], tuple(int(x) for x in dims), combine, precision
+    e.heads = [HEAD_Q] * e.M if hd is None else [int(x) for x in hd]
+    e.n_act = e.dims[-1] - (1 if HEAD_DUELING in e.heads else 0)
     return e
+
+
+def ensemble_q(ens: Ensemble, obs, q=None, stream=None):
+    """Per-agent Q-values after the heads, device float [M][n][n_act]."""
+    import torch
+    n = obs.shape[0]
+    if q is None:
+        q = torch.empty(ens.M, n, ens.n_act, device=obs.device)
+    _lib.check(lib().ensemble_q(ens, _dptr(obs, torch.float32, n * ens.dims[0], "obs"), n,
+                                _dptr(q, torch.float32, ens.M * n * ens.n_act, "q"), _stream(stream)), "ensemble_q")
+    return q
+
+
+def ensemble_q_targets(online: Ensemble, target: Ensemble, next_obs, rew, done=None, *, gamma: float = 0.99,
+                       double_q: bool = True, y=None, stream=None):
+    """DQN (double_q False) or Double DQN learning targets [M][n] from replay samples."""
+    import torch
+    n = next_obs.shape[0]
+    if y is None:
+        y = torch.empty(online.M, n, device=next_obs.device)
+    _lib.check(lib().ensemble_q_targets(online, target, _dptr(next_obs, torch.float32, n * online.dims[0], "next_obs"),
+                                        _dptr(rew, torch.float32, n, "rew"), _dptr(done, torch.uint8, n, "done"),
+                                        n, float(gamma), 1 if double_q else 0,
+                                        _dptr(y, torch.float32, online.M * n, "y"), _stream(stream)),
+               "ensemble_q_targets")
+    return y
 
 
 def ensemble_set_act_scales(ens: Ensemble, scales):

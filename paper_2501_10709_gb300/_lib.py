@@ -18,6 +18,7 @@ TASK_STOCK, TASK_CRYPTO = 0, 1
 ACT_I32_SHARES, ACT_F32_UNIT, ACT_U8_DISCRETE = 0, 1, 2
 PREC_FP32, PREC_BF16, PREC_FP8, PREC_BF16X3 = 0, 1, 2, 3
 COMBINE_MEAN, COMBINE_VOTE = 0, 1
+HEAD_Q, HEAD_DUELING = 0, 1
 PATH_AUTO, PATH_UNFUSED = 0, 1
 
 i32, i64, u32, u64, f64 = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_double
@@ -47,7 +48,7 @@ class StepOut(C.Structure):
 
 class EnsembleDesc(C.Structure):
     _fields_ = [("n_agents", i32), ("n_layers", i32), ("dims", vp), ("params", vp),
-                ("weights", vp), ("precision", i32), ("combine", i32), ("out_act", i32)]
+                ("weights", vp), ("precision", i32), ("combine", i32), ("out_act", i32), ("heads", vp)]
 
 
 class Traj(C.Structure):
@@ -130,6 +131,8 @@ SIGNATURES = {
     "ensemble_set_act_scales": (i32, [vp, vp]),
     "ensemble_get_act_scales": (i32, [vp, vp]),
     "ensemble_calibrate_sync": (i32, [vp, vp, i32, vp]),
+    "ensemble_q": (i32, [vp, vp, i32, vp, vp]),
+    "ensemble_q_targets": (i32, [vp, vp, vp, vp, vp, i32, C.c_float, i32, vp, vp]),
     "replay_create": (i32, [vp, vp, i64, vp]),
     "replay_destroy": (None, [vp]),
     "replay_push": (i32, [vp, vp, vp, i32, vp, vp, vp]),

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <mutex>
 #include <new>
@@ -692,7 +693,18 @@ int ensemble_create(fr_ctx *ctx, const fr_ensemble_desc *d, fr_ensemble **out)
              "ensemble_create: precision %d", d->precision);
     FR_CHECK(d->combine == FR_COMBINE_MEAN || d->combine == FR_COMBINE_VOTE, FR_EINVAL,
              "ensemble_create: combine %d", d->combine);
-    FR_CHECK(d->combine != FR_COMBINE_VOTE || d->dims[d->n_layers] <= 3, FR_EINVAL,
+    uint32_t dueling = 0;
+    if (d->heads) {
+        for (int j = 0; j < d->n_agents; ++j) {
+            FR_CHECK(d->heads[j] == FR_HEAD_Q || d->heads[j] == FR_HEAD_DUELING, FR_EINVAL,
+                     "ensemble_create: heads[%d] = %d", j, d->heads[j]);
+            if (d->heads[j] == FR_HEAD_DUELING) dueling |= 1u << j;
+        }
+    }
+    FR_CHECK(!dueling || (d->combine == FR_COMBINE_VOTE && d->out_act == 0 && d->dims[d->n_layers] >= 2),
+             FR_EINVAL, "ensemble_create: dueling heads need VOTE, identity output and >= 2 outputs");
+    const int n_act = d->dims[d->n_layers] - (dueling ? 1 : 0);
+    FR_CHECK(d->combine != FR_COMBINE_VOTE || n_act <= 3, FR_EINVAL,
              "ensemble_create: a vote needs at most 3 actions");
     int rc = use_device(ctx);
     if (rc) return rc;
@@ -707,6 +719,9 @@ int ensemble_create(fr_ctx *ctx, const fr_ensemble_desc *d, fr_ensemble **out)
     e->precision = d->precision;
     e->combine = d->combine;
     e->out_act = d->out_act ? 1 : 0;
+    e->dueling = dueling;
+    e->n_act = n_act;
+    for (int j = 0; j < MAX_AGENTS; ++j) e->heads[j] = (dueling >> j) & 1u ? FR_HEAD_DUELING : FR_HEAD_Q;
     int64_t off = 0;
     for (int l = 0; l < e->L; ++l) {
         e->w_off[l] = off;
@@ -820,6 +835,59 @@ int ensemble_calibrate_sync(fr_ensemble *e, const float *obs, int32_t n, void *s
     return tc_set_act_scales(e, sx);
 }
 
+int ensemble_q(const fr_ensemble *e, const float *obs, int32_t n, float *q, void *stream)
+{
+    FR_CHECK(e && n >= 0, FR_EINVAL, "ensemble_q: bad argument");
+    FR_CHECK(e->combine == FR_COMBINE_VOTE, FR_EINVAL, "ensemble_q: VOTE (Q-network) ensembles only");
+    if (n == 0) return FR_OK;
+    FR_CHECK(obs && q, FR_EINVAL, "ensemble_q: NULL obs or q");
+    int rc = use_device(e->ctx);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int out = e->dims[e->L];
+    float *y = nullptr;
+    FR_CUDA(cudaMallocAsync((void **)&y, 4ull * e->M * n * out, s));
+    rc = forward_any(e, obs, e->dims[0], n, y, s);
+    cudaError_t err = cudaSuccess;
+    if (rc == FR_OK) err = launch_heads(y, (int64_t)n * out, out, e->M, n, e->n_act, e->dueling, q, s);
+    cudaFreeAsync(y, s);
+    if (rc) return rc;
+    FR_CUDA(err);
+    return FR_OK;
+}
+
+int ensemble_q_targets(const fr_ensemble *on, const fr_ensemble *tg, const float *next_obs, const float *rew,
+                       const uint8_t *done, int32_t n, float gamma, int32_t double_q, float *y, void *stream)
+{
+    FR_CHECK(on && tg && n >= 0, FR_EINVAL, "ensemble_q_targets: bad argument");
+    FR_CHECK(on->combine == FR_COMBINE_VOTE && tg->combine == FR_COMBINE_VOTE, FR_EINVAL,
+             "ensemble_q_targets: VOTE (Q-network) ensembles only");
+    bool same = on->M == tg->M && on->L == tg->L && on->dueling == tg->dueling && on->ctx->device == tg->ctx->device;
+    for (int l = 0; l <= on->L && same; ++l) same = on->dims[l] == tg->dims[l];
+    FR_CHECK(same, FR_EINVAL, "ensemble_q_targets: online and target differ in shape or heads");
+    FR_CHECK(std::isfinite(gamma), FR_EINVAL, "ensemble_q_targets: gamma not finite");
+    if (n == 0) return FR_OK;
+    FR_CHECK(next_obs && rew && y, FR_EINVAL, "ensemble_q_targets: NULL next_obs, rew or y");
+    int rc = use_device(on->ctx);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int out = on->dims[on->L];
+    const uint64_t yb = 4ull * on->M * n * out;
+    float *ys = nullptr;
+    FR_CUDA(cudaMallocAsync((void **)&ys, 2 * yb, s));
+    float *yon = ys, *ytg = ys + (uint64_t)on->M * n * out;
+    rc = forward_any(tg, next_obs, tg->dims[0], n, ytg, s);
+    if (rc == FR_OK && double_q) rc = forward_any(on, next_obs, on->dims[0], n, yon, s);
+    cudaError_t err = cudaSuccess;
+    if (rc == FR_OK)
+        err = launch_q_targets(yon, ytg, (int64_t)n * out, out, on->M, n, on->n_act, on->dueling, rew, done, gamma,
+                               double_q ? 1 : 0, y, s);
+    cudaFreeAsync(ys, s);
+    if (rc) return rc;
+    FR_CUDA(err);
+    return FR_OK;
+}
+
 int ensemble_forward(const fr_ensemble *e, const float *obs, int32_t n, float *y, void *stream)
 {
     FR_CHECK(e && n >= 0, FR_EINVAL, "ensemble_forward: bad argument");
@@ -848,7 +916,7 @@ int ensemble_act(const fr_ensemble *e, const float *obs, int32_t n, void *act, v
             err = launch_combine_mean(y, (int64_t)n * out, out, e->weights, e->M, n, out,
                                       (float *)act, out, s);
         else
-            err = launch_combine_vote(y, (int64_t)n * out, out, e->M, n, out, (uint8_t *)act, s);
+            err = launch_combine_vote(y, (int64_t)n * out, out, e->M, n, e->n_act, e->dueling, (uint8_t *)act, s);
     }
     cudaFreeAsync(y, s);
     if (rc) return rc;
@@ -869,7 +937,7 @@ int rollout(fr_env *env, const fr_ensemble *e, int32_t T, const fr_traj *traj, d
     FR_CHECK(e->dims[0] == v.D, FR_EINVAL, "rollout: ensemble input %d != observation dim %d",
              e->dims[0], v.D);
     FR_CHECK(stock ? (e->combine == FR_COMBINE_MEAN && e->dims[e->L] == v.K)
-                   : (e->combine == FR_COMBINE_VOTE && e->dims[e->L] == 3),
+                   : (e->combine == FR_COMBINE_VOTE && e->n_act == 3),
              FR_EINVAL, "rollout: ensemble output / combine does not fit the task");
     fr_traj none = {nullptr, 0, nullptr, nullptr, nullptr, nullptr};
     if (!traj) traj = &none;
@@ -939,7 +1007,7 @@ static int plain_rollout(fr_env *env, const fr_ensemble *e, int32_t T, const fr_
             FR_CUDA(launch_combine_mean(y, (int64_t)N * out, out, e->weights, e->M, N, out,
                                         (float *)act_t, v.K, s));
         else
-            FR_CUDA(launch_combine_vote(y, (int64_t)N * out, out, e->M, N, out, (uint8_t *)act_t, s));
+            FR_CUDA(launch_combine_vote(y, (int64_t)N * out, out, e->M, N, e->n_act, e->dueling, (uint8_t *)act_t, s));
         if (env->explore_kind != FR_EXPLORE_NONE)
             FR_CUDA(launch_explore(v, act_t, explore_of(env, env->explore_step + (uint32_t)t), s));
         FR_CUDA(launch_env_step(v, stock ? FR_ACT_F32_UNIT : FR_ACT_U8_DISCRETE, act_t,

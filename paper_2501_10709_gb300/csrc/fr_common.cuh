@@ -206,12 +206,51 @@ struct fr_ensemble {
     float *params;                       // device [M][P] fp32 master copy
     float *weights;                      // device [M] combine weights
     float host_weights[fr::MAX_AGENTS];
+    int heads[fr::MAX_AGENTS];           // FR_HEAD_* per agent
+    uint32_t dueling;                    // bit j: agent j has a dueling head
+    int n_act;                           // actions (dims[L] - 1 with a dueling agent)
     fr::TcImage *tc;                     // tensor-core images or NULL
     uint64_t serial;                     // unique per created ensemble (cache key)
     uint64_t bytes;
 };
 
 namespace fr {
+// Q-values of one agent's output row y: a plain head reads y_a; a dueling
+// head gives (y_0 + y_{1+a}) - m with m = (y_1 + ... + y_n) / n summed in
+// index order, every float32 operation rounded once.
+struct HeadQ {
+    const float *y;
+    bool dueling;
+    int nact;
+    float m;
+    __device__ __forceinline__ HeadQ(const float *y_, bool d, int n) : y(y_), dueling(d), nact(n), m(0.0f)
+    {
+        if (dueling) {
+            float s = 0.0f;
+            for (int b = 0; b < nact; ++b) s = __fadd_rn(s, y[1 + b]);
+            m = __fdiv_rn(s, (float)nact);
+        }
+    }
+    __device__ __forceinline__ float q(int a) const
+    {
+        return dueling ? __fsub_rn(__fadd_rn(y[0], y[1 + a]), m) : y[a];
+    }
+    // argmax, lowest index on ties
+    __device__ __forceinline__ int argmax() const
+    {
+        int best = 0;
+        float bq = q(0);
+        for (int a = 1; a < nact; ++a) {
+            const float qa = q(a);
+            if (qa > bq) {
+                bq = qa;
+                best = a;
+            }
+        }
+        return best;
+    }
+};
+
 // plain fp32 kernels (fr_plain.cu)
 cudaError_t launch_dense_f32(const float *X, int64_t x_stride, int ldx, const float *P,
                              int64_t p_stride, int64_t w_off, int64_t b_off, float *Y,
@@ -223,8 +262,16 @@ cudaError_t launch_absmax(const float *x, int64_t stride, int64_t count, int M, 
                           cudaStream_t s);
 cudaError_t launch_combine_mean(const float *Y, int64_t y_stride, int ldy, const float *w, int M,
                                 int n, int K, float *out, int ldo, cudaStream_t s);
+// Q-values after the heads, q [M][n][nact]; DQN-family learning targets [M][n]
+cudaError_t launch_heads(const float *Y, int64_t y_stride, int ldy, int M, int n, int nact, uint32_t dueling,
+                         float *q, cudaStream_t s);
+cudaError_t launch_q_targets(const float *Yon, const float *Ytg, int64_t y_stride, int ldy, int M, int n, int nact,
+                             uint32_t dueling, const float *rew, const uint8_t *done, float gamma, int double_q,
+                             float *y, cudaStream_t s);
+// majority vote of the agents' argmax actions; agents with bit j of
+// `dueling` set take Q from a dueling head (fr_plain.cu)
 cudaError_t launch_combine_vote(const float *Y, int64_t y_stride, int ldy, int M, int n, int nact,
-                                uint8_t *out, cudaStream_t s);
+                                uint32_t dueling, uint8_t *out, cudaStream_t s);
 
 // Bytes of scratch the plain forward needs for n rows (two hidden buffers).
 inline uint64_t plain_scratch_bytes(const fr_ensemble *e, int n)

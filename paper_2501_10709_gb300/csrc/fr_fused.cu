@@ -821,7 +821,7 @@ int pick_stages(int task, const TcPlan &p, int optin, int *resident)
 
 bool tc_rollout_supported(const fr_env *env, const fr_ensemble *e)
 {
-    if (!e->tc || e->M > 8 || e->tc->plan.esz != 2) return false;     // BF16 operands only
+    if (!e->tc || e->M > 8 || e->tc->plan.esz != 2 || e->dueling) return false;   // BF16, plain heads
     const EnvView &v = env->v;
     const TcPlan &p = e->tc->plan;
     if (v.task == FR_TASK_STOCK) {

@@ -87,6 +87,6 @@ extern "C" int ensemble_act_noalloc(const fr_ensemble *e, const float *obs, int3
     if (e->combine == FR_COMBINE_MEAN)
         FR_CUDA(launch_combine_mean(y, (int64_t)n * out, out, e->weights, e->M, n, out, (float *)act, out, s));
     else
-        FR_CUDA(launch_combine_vote(y, (int64_t)n * out, out, e->M, n, out, (uint8_t *)act, s));
+        FR_CUDA(launch_combine_vote(y, (int64_t)n * out, out, e->M, n, e->n_act, e->dueling, (uint8_t *)act, s));
     return FR_OK;
 }

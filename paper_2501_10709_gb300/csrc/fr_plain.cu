@@ -93,16 +93,13 @@ __global__ void k_combine_mean(const float *__restrict__ Y, int64_t y_stride, in
 // per-agent argmax (lowest index on ties), then the action with the strictly
 // largest count, else hold (1)
 __global__ void k_combine_vote(const float *__restrict__ Y, int64_t y_stride, int ldy, int M,
-                               int n, int nact, uint8_t *__restrict__ out)
+                               int n, int nact, uint32_t dueling, uint8_t *__restrict__ out)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     int cnt[3] = {0, 0, 0};
     for (int j = 0; j < M; ++j) {
-        const float *q = Y + j * y_stride + (int64_t)r * ldy;
-        int best = 0;
-        for (int c = 1; c < nact; ++c)
-            if (q[c] > q[best]) best = c;
+        const int best = HeadQ(Y + j * y_stride + (int64_t)r * ldy, (dueling >> j) & 1u, nact).argmax();
         if (best < 3) cnt[best]++;
     }
     int best = 0, bc = cnt[0];
@@ -114,7 +111,49 @@ __global__ void k_combine_vote(const float *__restrict__ Y, int64_t y_stride, in
     out[r] = (uint8_t)(tie ? 1 : best);
 }
 
+// Q-values after each agent's head: q[j][r][a], a < nact.
+__global__ void k_heads(const float *__restrict__ Y, int64_t y_stride, int ldy, int M, int n, int nact,
+                        uint32_t dueling, float *__restrict__ q)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)M * n) return;
+    const int j = (int)(i / n), r = (int)(i % n);
+    const HeadQ h(Y + j * y_stride + (int64_t)r * ldy, (dueling >> j) & 1u, nact);
+    for (int a = 0; a < nact; ++a) q[i * nact + a] = h.q(a);
+}
+
+// DQN / Double DQN learning targets y[j][r] = r + (done ? 0 : gamma Q_target(s', a*)).
+__global__ void k_q_targets(const float *__restrict__ Yon, const float *__restrict__ Ytg, int64_t y_stride, int ldy,
+                            int M, int n, int nact, uint32_t dueling, const float *__restrict__ rew,
+                            const uint8_t *__restrict__ done, float gamma, int double_q, float *__restrict__ y)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)M * n) return;
+    const int j = (int)(i / n), r = (int)(i % n);
+    const bool d = (dueling >> j) & 1u;
+    const HeadQ tg(Ytg + j * y_stride + (int64_t)r * ldy, d, nact);
+    const int a = double_q ? HeadQ(Yon + j * y_stride + (int64_t)r * ldy, d, nact).argmax() : tg.argmax();
+    const float rr = rew[r];
+    y[i] = (done && done[r]) ? rr : __fadd_rn(rr, __fmul_rn(gamma, tg.q(a)));
+}
+
 }  // namespace
+
+cudaError_t launch_heads(const float *Y, int64_t y_stride, int ldy, int M, int n, int nact, uint32_t dueling,
+                         float *q, cudaStream_t s)
+{
+    k_heads<<<ceil_div((int64_t)M * n, 256), 256, 0, s>>>(Y, y_stride, ldy, M, n, nact, dueling, q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_q_targets(const float *Yon, const float *Ytg, int64_t y_stride, int ldy, int M, int n, int nact,
+                             uint32_t dueling, const float *rew, const uint8_t *done, float gamma, int double_q,
+                             float *y, cudaStream_t s)
+{
+    k_q_targets<<<ceil_div((int64_t)M * n, 256), 256, 0, s>>>(Yon, Ytg, y_stride, ldy, M, n, nact, dueling, rew,
+                                                               done, gamma, double_q, y);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_dense_f32(const float *X, int64_t x_stride, int ldx, const float *P,
                              int64_t p_stride, int64_t w_off, int64_t b_off, float *Y,
@@ -165,9 +204,9 @@ cudaError_t launch_combine_mean(const float *Y, int64_t y_stride, int ldy, const
 }
 
 cudaError_t launch_combine_vote(const float *Y, int64_t y_stride, int ldy, int M, int n, int nact,
-                                uint8_t *out, cudaStream_t s)
+                                uint32_t dueling, uint8_t *out, cudaStream_t s)
 {
-    k_combine_vote<<<ceil_div(n, 256), 256, 0, s>>>(Y, y_stride, ldy, M, n, nact, out);
+    k_combine_vote<<<ceil_div(n, 256), 256, 0, s>>>(Y, y_stride, ldy, M, n, nact, dueling, out);
     return cudaGetLastError();
 }
 

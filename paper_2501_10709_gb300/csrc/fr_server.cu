@@ -319,7 +319,7 @@ int fr_server_create(fr_ctx *ctx, const fr_server_desc *d, fr_server **out)
     FR_CHECK(e->dims[0] == (stock ? 1 + 2 * m->K + m->I * m->K : FR_CRYPTO_OBS_DIM), FR_EINVAL,
              "fr_server_create: ensemble input %d does not match the market's observation", e->dims[0]);
     FR_CHECK(stock ? (e->combine == FR_COMBINE_MEAN && e->dims[e->L] == m->K)
-                   : (e->combine == FR_COMBINE_VOTE && e->dims[e->L] == 3),
+                   : (e->combine == FR_COMBINE_VOTE && e->n_act == 3),
              FR_EINVAL, "fr_server_create: ensemble combine/output does not match the task");
     FR_CUDA(cudaSetDevice(ctx->device));
     int rc = FR_OK;

@@ -86,6 +86,7 @@ int ensemble_validate(fr_ensemble *e, fr_env *env, int32_t T, double threshold, 
         d.precision = e->precision;
         d.combine = e->combine;
         d.out_act = e->out_act;
+        d.heads = &e->heads[j];
         fr_ensemble *one = nullptr;
         if ((rc = ensemble_create(e->ctx, &d, &one))) break;
         if (e->precision == FR_PREC_FP8) {

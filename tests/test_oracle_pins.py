@@ -631,3 +631,39 @@ def test_replay_ref_fifo_and_sampling():
     assert ((counts - 1000) ** 2 / 1000).sum() < 6 + 5 * math.sqrt(12)      # chi-square, 6 dof
     assert pos.sample_positions(50, 123, 5) == list(p[:50]) and pos.sample_positions(50, 123, 6) != list(p[:50])
     assert oracle.ReplayRef(3).sample_positions(4, 1, 0) == [-1] * 4
+
+
+# ------------------------------------------------ DQN-family heads and targets
+def test_dueling_head_hand_example_and_identities():
+    y = np.array([1.0, 2.0, 0.0, 4.0])                          # V = 1, A = (2, 0, 4), mean 2
+    assert oracle.head_q(y, 1, 3).tolist() == [1.0, -1.0, 3.0]
+    assert oracle.head_q(y, 0, 3).tolist() == [1.0, 2.0, 0.0]  # a plain head ignores the extra output
+    rng = np.random.default_rng(2)
+    Y = rng.normal(0, 1, (1000, 4))
+    Q = oracle.head_q(Y, 1, 3)
+    assert np.allclose(Q.mean(-1), Y[:, 0], atol=1e-14)        # the advantages average to zero
+    assert (Q.argmax(-1) == Y[:, 1:].argmax(-1)).all()          # V and the mean do not change the argmax
+
+
+def _linear_q(W, b):
+    # a one-layer Q-network: Q(s) = W s + b
+    return np.concatenate([np.asarray(W, np.float32).ravel(), np.asarray(b, np.float32)])
+
+
+def test_double_and_plain_dqn_targets_by_hand():
+    dims = (2, 3)
+    s1 = np.array([[1.0, 0.0], [0.0, 1.0]], np.float32)
+    on = _linear_q([[0, 0], [1, 0], [0, 1]], [0, 0, 0])         # online argmax: action 1 for s1[0], 2 for s1[1]
+    tg = _linear_q([[5, 5], [1, 0], [2, 3]], [0, 0, 0])         # target Q: (5, 1, 2) and (5, 0, 3)
+    rew = np.array([0.5, -1.0])
+    done = np.array([0, 1], np.uint8)
+    g = 0.9
+    plain = oracle.q_targets(dims, [on], [tg], [0], s1, rew, done, g, False)[0]
+    double = oracle.q_targets(dims, [on], [tg], [0], s1, rew, done, g, True)[0]
+    assert plain.tolist() == [0.5 + 0.9 * 5.0, -1.0]            # max of the target Q; done: no bootstrap
+    assert double.tolist() == [0.5 + 0.9 * 1.0, -1.0]           # target Q at the online argmax
+    same = oracle.q_targets(dims, [tg], [tg], [0], s1, rew, None, g, True)[0]
+    assert same.tolist() == oracle.q_targets(dims, [tg], [tg], [0], s1, rew, None, g, False)[0].tolist()
+    # ties: lowest index (all-zero online Q selects action 0)
+    zero = _linear_q(np.zeros((3, 2)), [0, 0, 0])
+    assert oracle.q_targets(dims, [zero], [tg], [0], s1, rew, None, g, True)[0].tolist() == [0.5 + 4.5, -1.0 + 4.5]
