@@ -141,8 +141,37 @@ def cpu_baseline(w, target_s: float = 12.0):
     n = int(max(threads, min(e.N, target_s / (per_env_step * w.T))))
     n = max(threads, (n // threads) * threads)
     dt = run(n, w.T)
-    return {"value": n * w.T / dt, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
-            "sample": f"first {n} of {e.N} envs x {w.T} steps, fp64 actors, {dt:.1f} s"}
+    out = {"value": n * w.T / dt, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
+           "sample": f"first {n} of {e.N} envs x {w.T} steps, fp64 actors, {dt:.1f} s"}
+    # the same workload on one core (a smaller sample of envs, all 256 steps)
+    t0 = time.perf_counter()
+    n1 = 8
+    oracle.stock_run(w.market, e.Ke[:n1], e.start[:n1], e.W[:n1], e.bps[:n1], init_cash=e.init_cash, hmax=100,
+                     fee_bps=10, T=w.T, ensemble=(w.dims, w.params, None), nthreads=1, want=("metrics",))
+    dt1 = time.perf_counter() - t0
+    out["single_thread"] = {"value": n1 * w.T / dt1, "unit": "env-steps/s", "cores": 1,
+                            "sample": f"first {n1} envs x {w.T} steps, {dt1:.1f} s"}
+    # the 8-env x 34-step parity workload in full, and a 512-env subsample of
+    # the 8,192-env x 1,024-step crypto workload (all 1,024 steps)
+    from paper_2501_10709_gb300 import synth
+    s1 = synth.workload_stock_small()
+    t0 = time.perf_counter()
+    oracle.stock_run(s1.market, s1.envs.Ke, s1.envs.start, s1.envs.W, s1.envs.bps, init_cash=s1.envs.init_cash,
+                     hmax=100, fee_bps=10, T=s1.T, ensemble=(s1.dims, s1.params, None), nthreads=threads,
+                     want=("metrics",))
+    dts = time.perf_counter() - t0
+    out["stock_8env"] = {"value": s1.envs.N * s1.T / dts, "unit": "env-steps/s", "cores": threads,
+                         "sample": f"all 8 envs x {s1.T} steps (3 x 301-64-64-30)"}
+    c = synth.workload_crypto()
+    nc = 512
+    t0 = time.perf_counter()
+    oracle.crypto_run(c.market, c.envs.start[:nc], c.envs.W[:nc], init_cash=c.envs.init_cash, pmax=c.envs.pmax,
+                      T=c.T, ensemble=(c.dims, c.params), nthreads=threads, want=("metrics",))
+    dtc = time.perf_counter() - t0
+    out["crypto_8192env"] = {"value": nc * c.T / dtc, "unit": "env-steps/s", "cores": threads,
+                             "sample": f"first {nc} of {c.envs.N} envs x {c.T} steps (5 x 10-128-128-3), "
+                                       f"{dtc:.1f} s"}
+    return out
 
 
 # ----------------------------------------------------------------- GPU arms

@@ -14,12 +14,16 @@
 //     shared memory), ReLU and the next layer's BF16 A operand in shared
 //     memory, or the agent's output.
 // Limits, measured: an SM streams L2-resident data at 36 B/clk (bulk
-// copies) to 43 B/clk (16-byte cp.async), the same with all 152 SMs on the
-// same or on separate data, and a 128-row tile consumes ~50 B/clk of
-// weights at full tensor rate; the MMAs of a layer also wait for the
-// previous layer's epilogue, with the ring full.  Neither multicasting the
-// weights over a 4-CTA cluster nor cp.async producers made this kernel
-// faster.
+// copies) to 43 B/clk (16-byte cp.async), and a 128-row tile consumes ~50
+// B/clk of weights at full tensor rate.  Per-phase clock counters showed the
+// single MMA-issuing thread, not the copies, setting the pace: a barrier
+// wait and the loop around two MMAs cost ~500 cycles of issue against 256
+// cycles of tensor work.  So the ring streams whole K = 16 steps in 32 KB
+// stages (4 MMAs per wait for a 256-wide layer), the descriptors advance by
+// constant offsets, and the epilogue keeps four TMEM loads in flight.  The
+// MMAs of a layer still wait for the previous layer's epilogue.  Neither
+// multicasting the weights over a 4-CTA cluster nor cp.async producers made
+// this kernel faster.
 // The products, their order and every rounding are those of the
 // single-agent kernel, so both give identical results.
 #include <cuda_bf16.h>
@@ -41,6 +45,7 @@ constexpr int TA_MAX_STAGES = 6;
 struct TaLayout {
     uint32_t obs_a, h_a, ring, bias, bars, total;
     int stages;
+    uint32_t stage_bytes;
 };
 
 __host__ __device__ inline uint32_t obs_tile_bytes(const TcPlan &p) { return (uint32_t)(p.layer[0].K / 8) * 2048u; }
@@ -52,14 +57,15 @@ __host__ __device__ inline uint32_t hidden_a_bytes(const TcPlan &p)
     return (uint32_t)(k / 8) * 2048u;
 }
 
-__host__ __device__ inline TaLayout ta_layout(const TcPlan &p, int stages)
+__host__ __device__ inline TaLayout ta_layout(const TcPlan &p, int stages, uint32_t stage_bytes)
 {
     TaLayout L;
     L.stages = stages;
+    L.stage_bytes = stage_bytes;
     L.obs_a = 0;
     L.h_a = obs_tile_bytes(p);
     L.ring = L.h_a + hidden_a_bytes(p);
-    L.bias = L.ring + (uint32_t)stages * TC_CHUNK_MAX;          // [M][L][256] fp32
+    L.bias = L.ring + (uint32_t)stages * stage_bytes;           // [M][L][256] fp32
     L.bars = L.bias + (uint32_t)(p.M * p.L) * 1024u;
     L.total = L.bars + 256u;
     return L;
@@ -92,12 +98,13 @@ __global__ void k_obs_tiles(const float *__restrict__ obs, int ld, int n, int fi
 
 __global__ void __launch_bounds__(TA_THREADS, 1)
 k_tc_actor(const __grid_constant__ TcPlan plan, const uint8_t *__restrict__ img, const float *__restrict__ bias,
-           const uint8_t *__restrict__ obs_tiles, int n, float *__restrict__ y, unsigned *err, int stages)
+           const uint8_t *__restrict__ obs_tiles, int n, float *__restrict__ y, unsigned *err, int stages,
+           uint32_t stage_bytes)
 {
     using namespace ptx;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const TaLayout L = ta_layout(plan, stages);
+    const TaLayout L = ta_layout(plan, stages, stage_bytes);
     const uint32_t obs_a = smem_u32(base + L.obs_a), h_a = smem_u32(base + L.h_a);
     uint8_t *ring = base + L.ring;
     uint64_t *bars = (uint64_t *)(base + L.bars);
@@ -148,23 +155,29 @@ k_tc_actor(const __grid_constant__ TcPlan plan, const uint8_t *__restrict__ img,
             mbar_arrive_expect_tx(obs_full, ob);
             for (uint32_t o = 0; o < ob; o += TC_CHUNK_MAX)
                 bulk_g2s(base + L.obs_a + o, src + o, min(TC_CHUNK_MAX, ob - o), obs_full);
-            int i = 0;
+            // a layer's image is its K-major core-matrix columns end to end
+            // (N x 16 bytes each, two per K = 16 step), so the ring streams it
+            // in stages of whole K = 16 steps regardless of the image's chunks
+            int i = 0, s = 0;
+            uint32_t ph = 0;
             bool ok = true;
             for (int j = 0; j < plan.M && ok; ++j) {
                 const uint8_t *aimg = img + (size_t)j * plan.agent_bytes;
                 for (int l = 0; l < plan.L && ok; ++l) {
                     const TcLayer &ly = plan.layer[l];
-                    for (int c = 0; c < ly.n_chunks; ++c, ++i) {
-                        const int s = i % S;
-                        if (!mbar_wait(&empty[s], ((uint32_t)(i / S) & 1u) ^ 1u, abort, err, 1u, TC_WAIT_NS)) {
+                    const int steps = ly.K / 16, step_b = ly.N * 32, sps = (int)stage_bytes / step_b;
+                    for (int k16 = 0; k16 < steps; k16 += sps, ++i) {
+                        if (!mbar_wait(&empty[s], ph ^ 1u, abort, err, 1u, TC_WAIT_NS)) {
                             ok = false;
                             break;
                         }
-                        const int kc = min(ly.KC, ly.K - c * ly.KC);
-                        const uint32_t bytes = (uint32_t)(ly.N * kc * 2);
+                        const uint32_t bytes = (uint32_t)(min(sps, steps - k16) * step_b);
                         mbar_arrive_expect_tx(&full[s], bytes);
-                        bulk_g2s(ring + (size_t)s * TC_CHUNK_MAX, aimg + ly.off + (size_t)c * ly.N * ly.KC * 2, bytes,
-                                 &full[s]);
+                        bulk_g2s(ring + (size_t)s * stage_bytes, aimg + ly.off + (size_t)k16 * step_b, bytes, &full[s]);
+                        if (++s == S) {
+                            s = 0;
+                            ph ^= 1u;
+                        }
                     }
                 }
             }
@@ -172,13 +185,20 @@ k_tc_actor(const __grid_constant__ TcPlan plan, const uint8_t *__restrict__ img,
             volatile int no_abort = 0;
             mbar_wait(obs_full, 0u, &no_abort, err, 8u, TC_WAIT_NS);
             for (int k = i - 1; k >= 0 && k >= i - S; --k)
-                mbar_wait(&full[k % S], (uint32_t)(k / S) & 1u, &no_abort, err, 8u, TC_WAIT_NS);
+                mbar_wait(&full[k % S], (uint32_t)(k / S) & 1u, &no_abort, err, 8u, TC_WAIT_NS);   // stages issued
         }
     } else if (warp == 1) {
         // ------------------------------------------------------ MMA issue
+        // One thread issues every MMA, so its loop is latency-bound: the ring
+        // stage and phase advance incrementally, and each layer's operand
+        // descriptors are built once and advanced by constant byte offsets
+        // (2 core-matrix columns of A = 4,096 B and of B = 2 N 16 B per K = 16;
+        // the start-address field holds bytes / 16).
         if (lane == 0) {
-            int i = 0, step = 0;
+            int s = 0, step = 0;
+            uint32_t ph = 0;
             bool ok = mbar_wait(obs_full, 0u, abort, err, 2u, TC_WAIT_NS);
+            const uint32_t ring_u = smem_u32(ring);
             for (int j = 0; j < plan.M && ok; ++j) {
                 for (int l = 0; l < plan.L && ok; ++l, ++step) {
                     const TcLayer &ly = plan.layer[l];
@@ -188,25 +208,32 @@ k_tc_actor(const __grid_constant__ TcPlan plan, const uint8_t *__restrict__ img,
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a_at = l == 0 ? obs_a : h_a;
                     const uint32_t idesc = idesc_bf16(128, ly.N);
                     const uint32_t lbo_b = (uint32_t)(ly.N * 16);
-                    int kg = 0;
-                    for (int c = 0; c < ly.n_chunks; ++c, ++i) {
-                        const int s = i % S;
-                        if (!mbar_wait(&full[s], (uint32_t)(i / S) & 1u, abort, err, 4u, TC_WAIT_NS)) {
+                    const uint64_t b_step = (uint64_t)((2u * lbo_b) >> 4);
+                    uint64_t ad = smem_desc(l == 0 ? obs_a : h_a, 2048u, 128u);
+                    const uint64_t bd_ring = smem_desc(ring_u, lbo_b, 128u);
+                    uint32_t acc = 0u;
+                    const int steps = ly.K / 16, sps = (int)stage_bytes / (ly.N * 32);
+                    for (int k16 = 0; k16 < steps; k16 += sps) {
+                        if (!mbar_wait(&full[s], ph, abort, err, 4u, TC_WAIT_NS)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const int kc = min(ly.KC, ly.K - c * ly.KC);
-                        const uint32_t b_base = smem_u32(ring + (size_t)s * TC_CHUNK_MAX);
-                        for (int kk = 0; kk < kc; kk += 16, kg += 16) {
-                            const uint64_t ad = smem_desc(a_at + (uint32_t)(kg / 8) * 2048u, 2048u, 128u);
-                            const uint64_t bd = smem_desc(b_base + (uint32_t)(kk / 8) * lbo_b, lbo_b, 128u);
-                            mma_bf16(tmem, ad, bd, idesc, kg > 0 ? 1u : 0u);
+                        const int n_mma = min(sps, steps - k16);
+                        uint64_t bd = bd_ring + (uint64_t)(((uint32_t)s * stage_bytes) >> 4);
+                        for (int u = 0; u < n_mma; ++u) {
+                            mma_bf16(tmem, ad, bd, idesc, acc);
+                            acc = 1u;
+                            ad += 256u;
+                            bd += b_step;
                         }
                         mma_commit(&empty[s]);
+                        if (++s == S) {
+                            s = 0;
+                            ph ^= 1u;
+                        }
                     }
                     if (!ok) break;
                     mma_commit(acc_full);
@@ -240,30 +267,48 @@ k_tc_actor(const __grid_constant__ TcPlan plan, const uint8_t *__restrict__ img,
                 const int split = ly.N >= 64 ? ((ly.N / 2 + 15) & ~15) : ly.N;
                 const int c_lo = half == 0 ? 0 : split;
                 const int c_hi = half == 0 ? split : ly.N;
-                for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
-                    uint32_t v[16];
+                // up to four 16-column TMEM loads in flight per wait; the bias
+                // is read as float4 (the 16-column groups are 16-aligned)
+                for (int c4 = c_lo; c4 < c_hi; c4 += 64) {
+                    const int g = min(4, (c_hi - c4) / 16);          // warp-uniform
+                    uint32_t v[4][16];
                     __syncwarp();
-                    tmem_ld16(trow + (uint32_t)c0, v);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (u < g) tmem_ld16(trow + (uint32_t)(c4 + 16 * u), v[u]);
                     tmem_ld_wait();
-                    float x[16];
 #pragma unroll
-                    for (int u = 0; u < 16; ++u) x[u] = __uint_as_float(v[u]) + bl[c0 + u];
-                    if (!last) {
-                        uint32_t w[8];
+                    for (int u4 = 0; u4 < 4; ++u4) {
+                        if (u4 >= g) break;
+                        const int c0 = c4 + 16 * u4;
+                        float x[16];
+                        const float4 *b4 = (const float4 *)(bl + c0);
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            const __nv_bfloat162 b = __floats2bfloat162_rn(fmaxf(x[2 * u], 0.0f), fmaxf(x[2 * u + 1], 0.0f));
-                            w[u] = *(const uint32_t *)&b;
+                        for (int q4 = 0; q4 < 4; ++q4) {
+                            const float4 bb = b4[q4];
+                            x[4 * q4 + 0] = __uint_as_float(v[u4][4 * q4 + 0]) + bb.x;
+                            x[4 * q4 + 1] = __uint_as_float(v[u4][4 * q4 + 1]) + bb.y;
+                            x[4 * q4 + 2] = __uint_as_float(v[u4][4 * q4 + 2]) + bb.z;
+                            x[4 * q4 + 3] = __uint_as_float(v[u4][4 * q4 + 3]) + bb.w;
                         }
-                        const uint32_t at = h_a + (uint32_t)(c0 / 8) * 2048u + row_off;
-                        st_shared_v4(at, w[0], w[1], w[2], w[3]);
-                        st_shared_v4(at + 2048u, w[4], w[5], w[6], w[7]);
-                    } else if (grow < n) {
-                        float *yr = y + ((size_t)j * n + grow) * ly.fout;
+                        if (!last) {
+                            uint32_t w[8];
 #pragma unroll
-                        for (int u = 0; u < 16; ++u) {
-                            const int col = c0 + u;
-                            if (col < ly.fout) yr[col] = plan.out_act ? tanhf(x[u]) : x[u];
+                            for (int u = 0; u < 8; ++u) {
+                                const __nv_bfloat162 b =
+                                    __floats2bfloat162_rn(fmaxf(x[2 * u], 0.0f), fmaxf(x[2 * u + 1], 0.0f));
+                                w[u] = *(const uint32_t *)&b;
+                            }
+                            const uint32_t at = h_a + (uint32_t)(c0 / 8) * 2048u + row_off;
+                            st_shared_v4(at, w[0], w[1], w[2], w[3]);
+                            st_shared_v4(at + 2048u, w[4], w[5], w[6], w[7]);
+                        } else if (grow < n) {
+                            float *yr = y + ((size_t)j * n + grow) * ly.fout;
+#pragma unroll
+                            for (int u = 0; u < 16; ++u) {
+                                const int col = c0 + u;
+                                if (col < ly.fout) yr[col] = plan.out_act ? tanhf(x[u]) : x[u];
+                            }
                         }
                     }
                 }
@@ -284,11 +329,23 @@ k_tc_actor(const __grid_constant__ TcPlan plan, const uint8_t *__restrict__ img,
     }
 }
 
-int ta_stages(const TcPlan &p, int optin)
+// Ring shape: the largest stage (32 or 16 KB, at least one K = 16 step of
+// the widest layer) with 2..TA_MAX_STAGES stages that fits; bigger stages
+// give the single MMA-issuing thread more MMAs per barrier wait.
+int ta_stages(const TcPlan &p, int optin, uint32_t *stage_bytes)
 {
-    if (p.split != 1) return 0;
-    for (int s = TA_MAX_STAGES; s >= 2; --s)
-        if (ta_layout(p, s).total + 1024u <= (uint32_t)optin) return s;
+    if (p.split != 1 || p.esz != 2) return 0;
+    int nmax = 16;
+    for (int l = 0; l < p.L; ++l) nmax = p.layer[l].N > nmax ? p.layer[l].N : nmax;
+    for (uint32_t sb : {32768u, 16384u}) {
+        if (sb < (uint32_t)nmax * 32u) continue;
+        for (int s = TA_MAX_STAGES; s >= 2; --s) {
+            if (ta_layout(p, s, sb).total + 1024u <= (uint32_t)optin) {
+                *stage_bytes = sb;
+                return s;
+            }
+        }
+    }
     return 0;
 }
 
@@ -314,16 +371,18 @@ int tc_forward_tiled(const fr_ensemble *e, const float *obs, int ld, int n, floa
     const TcPlan &p = t->plan;
     int optin = 0;
     FR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, e->ctx->device));
-    const int stages = ta_stages(p, optin);
+    uint32_t stage_bytes = 0;
+    const int stages = ta_stages(p, optin, &stage_bytes);
     FR_CHECK(stages >= 2, FR_EINVAL, "tc_forward_tiled: the plan does not fit in shared memory");
     const int tiles = (int)ceil_div(n, 128);
     const int nch = p.layer[0].K / 8;
     const int64_t threads = (int64_t)tiles * nch * 128;
     k_obs_tiles<<<ceil_div(threads, 256), 256, 0, s>>>(obs, ld, n, p.layer[0].fin, nch, (uint4 *)scratch);
     FR_CUDA(cudaGetLastError());
-    const uint32_t smem = ta_layout(p, stages).total + 1024u;
+    const uint32_t smem = ta_layout(p, stages, stage_bytes).total + 1024u;
     FR_CUDA(set_max_smem_once((const void *)k_tc_actor, e->ctx->device));
-    k_tc_actor<<<tiles, TA_THREADS, smem, s>>>(p, t->img, t->bias, (const uint8_t *)scratch, n, y, t->err, stages);
+    k_tc_actor<<<tiles, TA_THREADS, smem, s>>>(p, t->img, t->bias, (const uint8_t *)scratch, n, y, t->err, stages,
+                                                stage_bytes);
     FR_CUDA(cudaGetLastError());
     return FR_OK;
 }
