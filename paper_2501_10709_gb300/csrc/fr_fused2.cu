@@ -193,15 +193,18 @@ __device__ __noinline__ void f2_layer(const F2Layer &l, uint32_t d_tmem, uint32_
     tc_fence_after();
     const uint32_t idesc = idesc_bf16(128, l.N);
     const uint32_t lbo_b = (uint32_t)(l.N * 16);
-    int kg = 0;
-    for (int c = 0; c < l.n_chunks; ++c) {
-        const int kc = min(l.KC, l.K - c * l.KC);
-        const uint32_t b_base = w_base + l.off + (uint32_t)(c * l.N * l.KC * 2);
-        for (int kk = 0; kk < kc; kk += 16, kg += 16) {
-            const uint64_t ad = smem_desc(a_at + (uint32_t)(kg / 8) * 2048u, 2048u, 128u);
-            const uint64_t bd = smem_desc(b_base + (uint32_t)(kk / 8) * lbo_b, lbo_b, 128u);
-            mma_bf16(d_tmem, ad, bd, idesc, kg > 0 ? 1u : 0u);
-        }
+    // the layer's resident weights are its K-major core-matrix columns end to
+    // end (the image's chunks are contiguous), so both descriptors advance by
+    // constant offsets per K = 16 step: 2 columns of A (4,096 B) and of B
+    // (2 N 16 B), in the start-address field's 16-byte units
+    uint64_t ad = smem_desc(a_at, 2048u, 128u);
+    uint64_t bd = smem_desc(w_base + l.off, lbo_b, 128u);
+    const uint64_t b_step = (uint64_t)((2u * lbo_b) >> 4);
+    mma_bf16(d_tmem, ad, bd, idesc, 0u);
+    for (int k = 16; k < l.K; k += 16) {
+        ad += 256u;
+        bd += b_step;
+        mma_bf16(d_tmem, ad, bd, idesc, 1u);
     }
     mma_commit(acc);
 }
