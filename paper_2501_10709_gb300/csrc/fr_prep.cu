@@ -8,14 +8,15 @@
 // windows summed from the oldest day, recurrences in day order.  So the table
 // is a pure function of the price series, identical on any launch shape.
 //
-// Two roles share one launch.  Recurrence blocks (one per 32 assets; one lane
-// per asset) run the three serial chains, one warp each: EMA-12 / EMA-26 for
-// MACD, Wilder gains / losses for RSI, Wilder TR / DM+ / DM- for DX.  Window
-// blocks (one per asset and 128-day tile, one thread per day) stage the tile
-// plus a 59-day halo of closes and typical prices in shared memory and
-// compute the windowed means, the standard deviation and the mean absolute
-// deviation.  The recurrences bound the launch (a few FP64 divisions per day
-// on the chain); the window blocks run beside them.
+// Two roles share the first launch.  Recurrence blocks (two per 32 assets;
+// one lane per asset) run the six serial chains, one warp each: EMA-12 /
+// EMA-26 together, and one each for the Wilder-smoothed gains, losses, TR,
+// DM+ and DM-, storing each day's states.  Window blocks (one per asset and 128-day tile, one thread per
+// day) stage the tile plus a 59-day halo of closes and typical prices in
+// shared memory and compute the windowed means, the standard deviation and
+// the mean absolute deviation.  A second launch, one thread per (day, asset),
+// turns the states into MACD, RSI and DX, so the chains carry only their own
+// recurrences (at most one FP64 division per day).
 #include "fr_common.cuh"
 
 namespace fr {
@@ -38,79 +39,95 @@ __device__ __forceinline__ void put(float *ind, int K, int t, int col, int k, do
     ind[((int64_t)t * N_IND + col) * K + k] = __double2float_rn(v);
 }
 
-// Chain of warp `role` for asset k over all T days.
+// Chain `role` for asset k over all T days: only a recurrence runs here, one
+// value per day into plane `role` of st[6][T][K]: 0 e12 - e26, 1 / 2 the
+// Wilder-smoothed gains / losses, 3 / 4 / 5 the Wilder-smoothed TR, DM+, DM-
+// (each role derives its own inputs, so every chain carries at most one
+// division per day); the divisions that turn the states into MACD, RSI and
+// DX are off the chains, in k_ind_final, one thread per (day, asset).
 __device__ void indicator_chain(int role, int k, const int64_t *close, const int64_t *high, const int64_t *low,
-                                int T, int K, float *ind)
+                                int T, int K, double *st)
 {
+    double *out = st + (int64_t)role * T * K;
     const double c0 = (double)close[k];
     if (role == 0) {
-        // MACD = EMA12 - EMA26, e_t = a c_t + (1 - a) e_{t-1}, a = 2 / (n + 1), e_0 = c_0
+        // e_t = a c_t + (1 - a) e_{t-1}, a = 2 / (n + 1), e_0 = c_0
         const double a12 = ddiv(2.0, 13.0), a26 = ddiv(2.0, 27.0);
         const double b12 = dsub(1.0, a12), b26 = dsub(1.0, a26);
         double e12 = c0, e26 = c0;
+#pragma unroll 4
         for (int t = 0; t < T; ++t) {
             const double ct = (double)close[(int64_t)t * K + k];
             if (t > 0) {
                 e12 = dadd(dmul(a12, ct), dmul(b12, e12));
                 e26 = dadd(dmul(a26, ct), dmul(b26, e26));
             }
-            put(ind, K, t, 0, k, ddiv(dsub(e12, e26), ct));
+            out[(int64_t)t * K + k] = dsub(e12, e26);
         }
-    } else if (role == 1) {
-        // RSI-30 from Wilder-smoothed gains and losses of c_t - c_{t-1}
-        double gain = 0.0, loss = 0.0, cp = c0;
+    } else if (role <= 2) {
+        // Wilder-smoothed gains (role 1) or losses (role 2) of c_t - c_{t-1}
+        double w = 0.0, cp = c0;
+#pragma unroll 4
         for (int t = 0; t < T; ++t) {
             const double ct = (double)close[(int64_t)t * K + k];
             const double d = dsub(ct, cp);
-            const double g = d > 0.0 ? d : 0.0, l = d < 0.0 ? -d : 0.0;
-            if (t == 0) {
-                gain = g;
-                loss = l;
-            } else {
-                gain = wilder30(gain, g);
-                loss = wilder30(loss, l);
-            }
-            double rsi;
-            if (gain == 0.0 && loss == 0.0) rsi = 50.0;
-            else if (loss > 0.0) rsi = dsub(100.0, ddiv(100.0, dadd(1.0, ddiv(gain, loss))));
-            else rsi = 100.0;
-            put(ind, K, t, 3, k, ddiv(rsi, 100.0));
+            const double x = role == 1 ? (d > 0.0 ? d : 0.0) : (d < 0.0 ? -d : 0.0);
+            w = t == 0 ? x : wilder30(w, x);
+            out[(int64_t)t * K + k] = w;
             cp = ct;
         }
     } else {
-        // DX-30 from Wilder-smoothed DM+, DM- and true range (c_{-1} = c_0)
-        double str = 0.0, spd = 0.0, snd = 0.0, cp = c0;
+        // Wilder-smoothed true range (3), DM+ (4) or DM- (5), c_{-1} = c_0
+        double w = 0.0, cp = c0;
         double hp = (double)high[k], lp = (double)low[k];
+#pragma unroll 4
         for (int t = 0; t < T; ++t) {
             const int64_t i = (int64_t)t * K + k;
             const double ct = (double)close[i], ht = (double)high[i], lt = (double)low[i];
-            const double up = t > 0 ? dsub(ht, hp) : 0.0;
-            const double dn = t > 0 ? dsub(lp, lt) : 0.0;
-            const double pdm = (up > dn && up > 0.0) ? up : 0.0;
-            const double ndm = (dn > up && dn > 0.0) ? dn : 0.0;
-            double tr = dsub(ht, lt);
-            const double th = fabs(dsub(ht, cp)), tl = fabs(dsub(lt, cp));
-            if (th > tr) tr = th;
-            if (tl > tr) tr = tl;
-            if (t == 0) {
-                str = tr;
-                spd = pdm;
-                snd = ndm;
+            double x;
+            if (role == 3) {
+                double tr = dsub(ht, lt);
+                const double th = fabs(dsub(ht, cp)), tl = fabs(dsub(lt, cp));
+                if (th > tr) tr = th;
+                if (tl > tr) tr = tl;
+                x = tr;
             } else {
-                str = wilder30(str, tr);
-                spd = wilder30(spd, pdm);
-                snd = wilder30(snd, ndm);
+                const double up = t > 0 ? dsub(ht, hp) : 0.0;
+                const double dn = t > 0 ? dsub(lp, lt) : 0.0;
+                x = role == 4 ? ((up > dn && up > 0.0) ? up : 0.0) : ((dn > up && dn > 0.0) ? dn : 0.0);
             }
-            const double den = str > 0.0 ? str : 1.0;
-            const double pdi = ddiv(dmul(100.0, spd), den), ndi = ddiv(dmul(100.0, snd), den);
-            const double s = dadd(pdi, ndi);
-            const double dx = s > 0.0 ? ddiv(dmul(100.0, fabs(dsub(pdi, ndi))), s) : 0.0;
-            put(ind, K, t, 5, k, ddiv(dx, 100.0));
+            w = t == 0 ? x : wilder30(w, x);
+            out[i] = w;
             cp = ct;
             hp = ht;
             lp = lt;
         }
     }
+}
+
+// MACD / c, RSI-30 / 100 and DX-30 / 100 of (day, asset) from the chains'
+// states, the same operations as if they ran on the chain.
+__global__ void k_ind_final(const int64_t *__restrict__ close, int T, int K, const double *__restrict__ st,
+                            float *__restrict__ ind)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t TK = (int64_t)T * K;
+    if (i >= TK) return;
+    const int t = (int)(i / K), k = (int)(i % K);
+    const double ct = (double)close[i];
+    put(ind, K, t, 0, k, ddiv(st[i], ct));
+    const double gain = st[TK + i], loss = st[2 * TK + i];
+    double rsi;
+    if (gain == 0.0 && loss == 0.0) rsi = 50.0;
+    else if (loss > 0.0) rsi = dsub(100.0, ddiv(100.0, dadd(1.0, ddiv(gain, loss))));
+    else rsi = 100.0;
+    put(ind, K, t, 3, k, ddiv(rsi, 100.0));
+    const double str = st[3 * TK + i], spd = st[4 * TK + i], snd = st[5 * TK + i];
+    const double den = str > 0.0 ? str : 1.0;
+    const double pdi = ddiv(dmul(100.0, spd), den), ndi = ddiv(dmul(100.0, snd), den);
+    const double s = dadd(pdi, ndi);
+    const double dx = s > 0.0 ? ddiv(dmul(100.0, fabs(dsub(pdi, ndi))), s) : 0.0;
+    put(ind, K, t, 5, k, ddiv(dx, 100.0));
 }
 
 // Mean of x[j - m + 1 .. j] in shared memory, m = min(n, t + 1) days ending at
@@ -126,11 +143,14 @@ __device__ __forceinline__ double win_mean(const double *x, int j, int t, int n,
 __global__ void __launch_bounds__(PREP_TILE) k_indicators(const int64_t *__restrict__ close,
                                                           const int64_t *__restrict__ high,
                                                           const int64_t *__restrict__ low, int T, int K,
-                                                          float *__restrict__ ind, int n_chain, int n_tiles)
+                                                          float *__restrict__ ind, int n_chain, int n_tiles,
+                                                          double *__restrict__ st)
 {
     if ((int)blockIdx.x < n_chain) {
-        const int role = threadIdx.x >> 5, k = blockIdx.x * 32 + (threadIdx.x & 31);
-        if (role < 3 && k < K) indicator_chain(role, k, close, high, low, T, K, ind);
+        // two recurrence blocks per 32 assets, three chains (warps) each
+        const int role = (blockIdx.x & 1) * 3 + (threadIdx.x >> 5);
+        const int k = (blockIdx.x >> 1) * 32 + (threadIdx.x & 31);
+        if ((threadIdx.x >> 5) < 3 && k < K) indicator_chain(role, k, close, high, low, T, K, st);
         return;
     }
     __shared__ double c_s[PREP_TILE + PREP_HALO], tp_s[PREP_TILE + PREP_HALO];
@@ -186,11 +206,21 @@ __global__ void k_perturb(EnvView v, uint64_t seed, int R)
 cudaError_t launch_indicators(const int64_t *close, const int64_t *high, const int64_t *low, int T, int K,
                               float *ind, cudaStream_t s)
 {
-    const int n_chain = (K + 31) / 32, n_tiles = (T + PREP_TILE - 1) / PREP_TILE;
+    const int n_chain = 2 * ((K + 31) / 32), n_tiles = (T + PREP_TILE - 1) / PREP_TILE;
     const long long blocks = (long long)n_chain + (long long)K * n_tiles;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    k_indicators<<<(unsigned)blocks, PREP_TILE, 0, s>>>(close, high, low, T, K, ind, n_chain, n_tiles);
-    return cudaGetLastError();
+    // the chains' states, stream-ordered scratch: 6 doubles per (day, asset)
+    double *st = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&st, 48ull * (uint64_t)T * K, s);
+    if (e != cudaSuccess) return e;
+    k_indicators<<<(unsigned)blocks, PREP_TILE, 0, s>>>(close, high, low, T, K, ind, n_chain, n_tiles, st);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        k_ind_final<<<ceil_div((int64_t)T * K, 256), 256, 0, s>>>(close, T, K, st, ind);
+        e = cudaGetLastError();
+    }
+    const cudaError_t f = cudaFreeAsync(st, s);
+    return e != cudaSuccess ? e : f;
 }
 
 }  // namespace fr
