@@ -94,9 +94,48 @@ bool make_plan(const fr_ensemble *e, TcPlan &p)
     return true;
 }
 
+// Ring stage of the single-agent kernel.  Without split operands a layer's
+// image is its K-major core-matrix columns end to end, streamed in stages of
+// whole MMA steps (N x 32 bytes each: two core columns); 32 KB stages give the
+// MMA-issuing thread up to four MMAs per barrier wait on a 256-wide layer.
+// Split (hi / lo) images keep one chunk per stage.
+inline __host__ __device__ uint32_t tc_stage_bytes(const TcPlan &p) { return p.split == 3 ? TC_CHUNK_MAX : 32768u; }
+
 uint32_t tc_smem_bytes(const TcPlan &p)
 {
-    return a_part_bytes(p) * (p.split == 3 ? 2u : 1u) + TC_STAGES * TC_CHUNK_MAX + 256u + 1024u;
+    return a_part_bytes(p) * (p.split == 3 ? 2u : 1u) + TC_STAGES * tc_stage_bytes(p) + 256u + 1024u;
+}
+
+// Geometry of weight-stream unit u of layer ly: its bytes, its offset in the
+// layer's image, its MMAs and (split images) the lo part's offset within it.
+struct TcUnit {
+    uint32_t bytes, src, lo;
+    int n_mma;
+};
+__device__ __forceinline__ int tc_units(const TcPlan &p, const TcLayer &ly)
+{
+    if (p.split == 3) return ly.n_chunks;
+    const int steps = ly.K / p.kmma, sps = (int)(tc_stage_bytes(p) / (uint32_t)(ly.N * 32));
+    return (steps + sps - 1) / sps;
+}
+__device__ __forceinline__ TcUnit tc_unit(const TcPlan &p, const TcLayer &ly, int u)
+{
+    TcUnit t;
+    if (p.split == 3) {
+        const int kc = min(ly.KC, ly.K - u * ly.KC);
+        t.bytes = (uint32_t)(ly.N * kc * 2 * 2);
+        t.src = (uint32_t)(u * ly.N * ly.KC * 2 * 2);
+        t.lo = (uint32_t)(ly.N * kc * 2);
+        t.n_mma = kc / 16;
+    } else {
+        const int steps = ly.K / p.kmma, step_b = ly.N * 32, sps = (int)(tc_stage_bytes(p) / (uint32_t)step_b);
+        const int k0 = u * sps;
+        t.n_mma = min(sps, steps - k0);
+        t.bytes = (uint32_t)(t.n_mma * step_b);
+        t.src = (uint32_t)(k0 * step_b);
+        t.lo = 0;
+    }
+    return t;
 }
 
 // ------------------------------------------------------------------ kernel
@@ -115,7 +154,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const ui
     const bool split = plan.split == 3;
     const bool fp8 = plan.esz == 1;
     uint8_t *ring = A + a_part * (split ? 2u : 1u);
-    uint64_t *bars = (uint64_t *)(ring + TC_STAGES * TC_CHUNK_MAX);
+    const uint32_t stage_b = tc_stage_bytes(plan);
+    uint64_t *bars = (uint64_t *)(ring + TC_STAGES * stage_b);
     uint64_t *full = bars;
     uint64_t *empty = bars + TC_STAGES;
     uint64_t *acc_full = bars + 2 * TC_STAGES;
@@ -155,15 +195,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const ui
             bool ok = true;
             for (int l = 0; l < plan.L && ok; ++l) {
                 const TcLayer &ly = plan.layer[l];
-                for (int c = 0; c < ly.n_chunks; ++c) {
+                const int nu = tc_units(plan, ly);
+                for (int c = 0; c < nu; ++c) {
                     const int s = i % TC_STAGES;
                     const uint32_t ph = (uint32_t)(i / TC_STAGES) & 1u;
                     if (!mbar_wait(&empty[s], ph ^ 1u, abort, err, 1u, TC_WAIT_NS)) { ok = false; break; }
-                    const int kc = min(ly.KC, ly.K - c * ly.KC);
-                    const uint32_t bytes = (uint32_t)(ly.N * kc * plan.esz * plan.parts);
-                    mbar_arrive_expect_tx(&full[s], bytes);
-                    bulk_g2s(ring + s * TC_CHUNK_MAX,
-                             aimg + ly.off + (size_t)c * ly.N * ly.KC * plan.esz * plan.parts, bytes, &full[s]);
+                    const TcUnit un = tc_unit(plan, ly, c);
+                    mbar_arrive_expect_tx(&full[s], un.bytes);
+                    bulk_g2s(ring + s * stage_b, aimg + ly.off + un.src, un.bytes, &full[s]);
                     ++i;
                 }
             }
@@ -176,44 +215,55 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const ui
         }
     } else if (warp == 1) {
         // -------------------------------------------------- MMA issuer
+        // one thread issues every MMA: the descriptors are built once per
+        // stage and advanced by constant offsets (two core-matrix columns per
+        // MMA: 4,096 B of A and 2 N 16 B of B, in 16-byte units), and the
+        // stage and phase advance incrementally
         if (lane == 0) {
-            int i = 0;
+            int s = 0;
+            uint32_t ph = 0;
             const uint32_t a_base = smem_u32(A);
+            const uint32_t ring_u = smem_u32(ring);
+            const uint64_t a_lo = (uint64_t)(a_part >> 4);
             for (int l = 0; l < plan.L; ++l) {
                 const TcLayer &ly = plan.layer[l];
                 if (!mbar_wait(a_ready, (uint32_t)l & 1u, abort, err, 2u, TC_WAIT_NS)) break;
                 tc_fence_after();
                 const uint32_t idesc = fp8 ? idesc_e4m3(128, ly.N) : idesc_bf16(128, ly.N);
-                int kg = 0;
+                const uint32_t lbo_b = (uint32_t)(ly.N * 16);
+                const uint64_t b_step = (uint64_t)((2u * lbo_b) >> 4);
+                const int nu = tc_units(plan, ly);
+                uint64_t ad = smem_desc(a_base, 2048u, 128u);
+                uint32_t accum = 0u;
                 bool ok = true;
-                for (int c = 0; c < ly.n_chunks; ++c) {
-                    const int s = i % TC_STAGES;
-                    if (!mbar_wait(&full[s], (uint32_t)(i / TC_STAGES) & 1u, abort, err, 4u, TC_WAIT_NS)) {
+                for (int c = 0; c < nu; ++c) {
+                    if (!mbar_wait(&full[s], ph, abort, err, 4u, TC_WAIT_NS)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const int kc = min(ly.KC, ly.K - c * ly.KC);
-                    const uint32_t b_base = smem_u32(ring + s * TC_CHUNK_MAX);
-                    const uint32_t lbo_b = (uint32_t)(ly.N * 16);
-                    const uint32_t b_lo = (uint32_t)(ly.N * kc * 2);     // lo part after hi
-                    for (int kk = 0; kk < kc; kk += plan.kmma, kg += plan.kmma) {
-                        const uint32_t ao = a_base + (uint32_t)(kg / plan.ck) * 2048u;
-                        const uint32_t bo = b_base + (uint32_t)(kk / plan.ck) * lbo_b;
-                        const uint64_t ad = smem_desc(ao, 2048u, 128u);
-                        const uint64_t bd = smem_desc(bo, lbo_b, 128u);
+                    const TcUnit un = tc_unit(plan, ly, c);
+                    uint64_t bd = smem_desc(ring_u + (uint32_t)s * stage_b, lbo_b, 128u);
+                    const uint64_t b_lo = (uint64_t)(un.lo >> 4);
+                    for (int u = 0; u < un.n_mma; ++u) {
                         if (fp8) {
-                            mma_e4m3(tmem, ad, bd, idesc, kg > 0 ? 1u : 0u);
+                            mma_e4m3(tmem, ad, bd, idesc, accum);
                         } else {
-                            mma_bf16(tmem, ad, bd, idesc, kg > 0 ? 1u : 0u);
+                            mma_bf16(tmem, ad, bd, idesc, accum);
                         }
                         if (split) {
-                            mma_bf16(tmem, smem_desc(ao + a_part, 2048u, 128u), bd, idesc, 1u);
-                            mma_bf16(tmem, ad, smem_desc(bo + b_lo, lbo_b, 128u), idesc, 1u);
+                            mma_bf16(tmem, ad + a_lo, bd, idesc, 1u);
+                            mma_bf16(tmem, ad, bd + b_lo, idesc, 1u);
                         }
+                        accum = 1u;
+                        ad += 256u;
+                        bd += b_step;
                     }
                     mma_commit(&empty[s]);
-                    ++i;
+                    if (++s == TC_STAGES) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
                 }
                 if (!ok) break;
                 mma_commit(acc_full);
