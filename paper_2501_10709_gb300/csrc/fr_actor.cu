@@ -43,18 +43,19 @@ constexpr int TA_THREADS = 320;          // producer, MMA issuer, 8 epilogue war
 constexpr int TA_MAX_STAGES = 6;
 
 struct TaLayout {
-    uint32_t obs_a, h_a, ring, bias, bars, total;
+    uint32_t obs_a, h_a, ring, bias, dq, bars, total;
     int stages;
     uint32_t stage_bytes;
 };
 
-__host__ __device__ inline uint32_t obs_tile_bytes(const TcPlan &p) { return (uint32_t)(p.layer[0].K / 8) * 2048u; }
+// operand bytes: 2 KB per core-matrix column of 8 (BF16) or 16 (E4M3) elements
+__host__ __device__ inline uint32_t obs_tile_bytes(const TcPlan &p) { return (uint32_t)(p.layer[0].K / p.ck) * 2048u; }
 
 __host__ __device__ inline uint32_t hidden_a_bytes(const TcPlan &p)
 {
     int k = 16;
     for (int l = 1; l < p.L; ++l) k = p.layer[l].K > k ? p.layer[l].K : k;
-    return (uint32_t)(k / 8) * 2048u;
+    return (uint32_t)(k / p.ck) * 2048u;
 }
 
 __host__ __device__ inline TaLayout ta_layout(const TcPlan &p, int stages, uint32_t stage_bytes)
@@ -66,7 +67,8 @@ __host__ __device__ inline TaLayout ta_layout(const TcPlan &p, int stages, uint3
     L.h_a = obs_tile_bytes(p);
     L.ring = L.h_a + hidden_a_bytes(p);
     L.bias = L.ring + (uint32_t)stages * stage_bytes;           // [M][L][256] fp32
-    L.bars = L.bias + (uint32_t)(p.M * p.L) * 1024u;
+    L.dq = L.bias + (uint32_t)(p.M * p.L) * 1024u;              // FP8: [M][L][256] sx * sw
+    L.bars = L.dq + (p.esz == 1 ? (uint32_t)(p.M * p.L) * 1024u : 0u);
     L.total = L.bars + 256u;
     return L;
 }
@@ -96,10 +98,34 @@ __global__ void k_obs_tiles(const float *__restrict__ obs, int ld, int n, int fi
     out[i] = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
+// fp32 obs [n][ld] -> E4M3 tiles [tiles][K/16][128][16] of obs * inv (the
+// agents' common layer-0 activation scale), the single-agent kernel's codes
+__global__ void k_obs_tiles_e4m3(const float *__restrict__ obs, int ld, int n, int fin, int nchunks, float inv,
+                                 uint4 *out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t tiles = (n + 127) / 128;
+    if (i >= tiles * nchunks * 128) return;
+    const int row = (int)(i % 128);
+    const int c = (int)((i / 128) % nchunks);
+    const int64_t tile = i / (128 * (int64_t)nchunks);
+    const int64_t g = tile * 128 + row;
+    float v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const int k = c * 16 + u;
+        v[u] = (g < n && k < fin) ? __ldg(obs + g * ld + k) : 0.0f;
+    }
+    uint32_t w[4];
+    e4m3_pack16(v, inv, w);
+    out[i] = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+template <bool FP8>
 __global__ void __launch_bounds__(TA_THREADS, 1)
 k_tc_actor(const __grid_constant__ TcPlan plan, const uint8_t *__restrict__ img, const float *__restrict__ bias,
            const uint8_t *__restrict__ obs_tiles, int n, float *__restrict__ y, unsigned *err, int stages,
-           uint32_t stage_bytes)
+           uint32_t stage_bytes, const float *__restrict__ dq, const float *__restrict__ inv_sx)
 {
     using namespace ptx;
     extern __shared__ uint8_t smem_raw[];
@@ -120,6 +146,8 @@ k_tc_actor(const __grid_constant__ TcPlan plan, const uint8_t *__restrict__ img,
     const int tile = blockIdx.x;
     const int S = stages;
     float *bias_s = (float *)(base + L.bias);
+    float *dq_s = (float *)(base + L.dq);                   // FP8 only
+    constexpr bool fp8 = FP8;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -141,6 +169,7 @@ k_tc_actor(const __grid_constant__ TcPlan plan, const uint8_t *__restrict__ img,
     for (int i = threadIdx.x; i < plan.M * plan.L * 256; i += TA_THREADS) {
         const int j = i / (plan.L * 256), l = (i / 256) % plan.L, c = i % 256;
         bias_s[i] = bias[((size_t)j * MAX_LAYERS + l) * 256 + c];
+        if (fp8) dq_s[i] = dq[((size_t)j * MAX_LAYERS + l) * 256 + c];
     }
     tc_fence_before();
     __syncthreads();
@@ -165,7 +194,7 @@ k_tc_actor(const __grid_constant__ TcPlan plan, const uint8_t *__restrict__ img,
                 const uint8_t *aimg = img + (size_t)j * plan.agent_bytes;
                 for (int l = 0; l < plan.L && ok; ++l) {
                     const TcLayer &ly = plan.layer[l];
-                    const int steps = ly.K / 16, step_b = ly.N * 32, sps = (int)stage_bytes / step_b;
+                    const int steps = ly.K / plan.kmma, step_b = ly.N * 32, sps = (int)stage_bytes / step_b;
                     for (int k16 = 0; k16 < steps; k16 += sps, ++i) {
                         if (!mbar_wait(&empty[s], ph ^ 1u, abort, err, 1u, TC_WAIT_NS)) {
                             ok = false;
@@ -208,13 +237,13 @@ k_tc_actor(const __grid_constant__ TcPlan plan, const uint8_t *__restrict__ img,
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t idesc = idesc_bf16(128, ly.N);
+                    const uint32_t idesc = fp8 ? idesc_e4m3(128, ly.N) : idesc_bf16(128, ly.N);
                     const uint32_t lbo_b = (uint32_t)(ly.N * 16);
                     const uint64_t b_step = (uint64_t)((2u * lbo_b) >> 4);
                     uint64_t ad = smem_desc(l == 0 ? obs_a : h_a, 2048u, 128u);
                     const uint64_t bd_ring = smem_desc(ring_u, lbo_b, 128u);
                     uint32_t acc = 0u;
-                    const int steps = ly.K / 16, sps = (int)stage_bytes / (ly.N * 32);
+                    const int steps = ly.K / plan.kmma, sps = (int)stage_bytes / (ly.N * 32);
                     for (int k16 = 0; k16 < steps; k16 += sps) {
                         if (!mbar_wait(&full[s], ph, abort, err, 4u, TC_WAIT_NS)) {
                             ok = false;
@@ -224,7 +253,10 @@ k_tc_actor(const __grid_constant__ TcPlan plan, const uint8_t *__restrict__ img,
                         const int n_mma = min(sps, steps - k16);
                         uint64_t bd = bd_ring + (uint64_t)(((uint32_t)s * stage_bytes) >> 4);
                         for (int u = 0; u < n_mma; ++u) {
-                            mma_bf16(tmem, ad, bd, idesc, acc);
+                            if (fp8)
+                                mma_e4m3(tmem, ad, bd, idesc, acc);
+                            else
+                                mma_bf16(tmem, ad, bd, idesc, acc);
                             acc = 1u;
                             ad += 256u;
                             bd += b_step;
@@ -262,6 +294,8 @@ k_tc_actor(const __grid_constant__ TcPlan plan, const uint8_t *__restrict__ img,
                 warp_wait_all(acc_full, (uint32_t)step & 1u, false, abort, err, 16u, TC_WAIT_NS);
                 tc_fence_after();
                 const float *bl = bias_s + (j * plan.L + l) * 256;
+                const float *dql = dq_s + (j * plan.L + l) * 256;                   // FP8 only
+                const float inv_next = fp8 && !last ? __ldg(inv_sx + (size_t)j * MAX_LAYERS + l + 1) : 1.0f;
                 // columns of this warp: two 16-aligned halves of N (a narrow
                 // layer all to half 0); every group of 16 stays inside N
                 const int split = ly.N >= 64 ? ((ly.N / 2 + 15) & ~15) : ly.N;
@@ -283,13 +317,35 @@ k_tc_actor(const __grid_constant__ TcPlan plan, const uint8_t *__restrict__ img,
                         const int c0 = c4 + 16 * u4;
                         float x[16];
                         const float4 *b4 = (const float4 *)(bl + c0);
+                        if constexpr (FP8) {
+                            // dequantise: fma(acc, sx * sw[n], b[n]); then ReLU and the next
+                            // layer's E4M3 codes of x / sx' (one 16-column core column)
+                            const float4 *d4 = (const float4 *)(dql + c0);
 #pragma unroll
-                        for (int q4 = 0; q4 < 4; ++q4) {
-                            const float4 bb = b4[q4];
-                            x[4 * q4 + 0] = __uint_as_float(v[u4][4 * q4 + 0]) + bb.x;
-                            x[4 * q4 + 1] = __uint_as_float(v[u4][4 * q4 + 1]) + bb.y;
-                            x[4 * q4 + 2] = __uint_as_float(v[u4][4 * q4 + 2]) + bb.z;
-                            x[4 * q4 + 3] = __uint_as_float(v[u4][4 * q4 + 3]) + bb.w;
+                            for (int q4 = 0; q4 < 4; ++q4) {
+                                const float4 bb = b4[q4], dd = d4[q4];
+                                x[4 * q4 + 0] = __fmaf_rn(__uint_as_float(v[u4][4 * q4 + 0]), dd.x, bb.x);
+                                x[4 * q4 + 1] = __fmaf_rn(__uint_as_float(v[u4][4 * q4 + 1]), dd.y, bb.y);
+                                x[4 * q4 + 2] = __fmaf_rn(__uint_as_float(v[u4][4 * q4 + 2]), dd.z, bb.z);
+                                x[4 * q4 + 3] = __fmaf_rn(__uint_as_float(v[u4][4 * q4 + 3]), dd.w, bb.w);
+                            }
+                            if (!last) {
+#pragma unroll
+                                for (int u = 0; u < 16; ++u) x[u] = fmaxf(x[u], 0.0f);
+                                uint32_t w[4];
+                                e4m3_pack16(x, inv_next, w);
+                                st_shared_v4(h_a + (uint32_t)(c0 / 16) * 2048u + row_off, w[0], w[1], w[2], w[3]);
+                                continue;
+                            }
+                        } else {
+#pragma unroll
+                            for (int q4 = 0; q4 < 4; ++q4) {
+                                const float4 bb = b4[q4];
+                                x[4 * q4 + 0] = __uint_as_float(v[u4][4 * q4 + 0]) + bb.x;
+                                x[4 * q4 + 1] = __uint_as_float(v[u4][4 * q4 + 1]) + bb.y;
+                                x[4 * q4 + 2] = __uint_as_float(v[u4][4 * q4 + 2]) + bb.z;
+                                x[4 * q4 + 3] = __uint_as_float(v[u4][4 * q4 + 3]) + bb.w;
+                            }
                         }
                         if (!last) {
                             uint32_t w[8];
@@ -311,6 +367,10 @@ k_tc_actor(const __grid_constant__ TcPlan plan, const uint8_t *__restrict__ img,
                             }
                         }
                     }
+                }
+                if (fp8 && !last && (ly.N & 31) && c_lo < c_hi && c_hi == ly.N) {
+                    // the next layer's K is rounded up to 32: zero the 16 columns past N
+                    st_shared_v4(h_a + (uint32_t)(ly.N / 16) * 2048u + row_off, 0u, 0u, 0u, 0u);
                 }
                 fence_proxy_async_smem();
                 tc_fence_before();
@@ -334,7 +394,7 @@ k_tc_actor(const __grid_constant__ TcPlan plan, const uint8_t *__restrict__ img,
 // give the single MMA-issuing thread more MMAs per barrier wait.
 int ta_stages(const TcPlan &p, int optin, uint32_t *stage_bytes)
 {
-    if (p.split != 1 || p.esz != 2) return 0;
+    if (p.split != 1) return 0;
     int nmax = 16;
     for (int l = 0; l < p.L; ++l) nmax = p.layer[l].N > nmax ? p.layer[l].N : nmax;
     for (uint32_t sb : {32768u, 16384u}) {
@@ -356,7 +416,10 @@ int ta_stages(const TcPlan &p, int optin, uint32_t *stage_bytes)
 // tiles x agents CTAs then fill the GPU better)
 uint64_t tc_tiled_scratch_bytes(const fr_ensemble *e, int n)
 {
-    if (!e->tc || e->tc->plan.split != 1 || e->tc->plan.esz != 2) return 0;     // plain BF16 only
+    if (!e->tc || e->tc->plan.split != 1) return 0;                          // BF16 or FP8, not split
+    // FP8: one observation tile serves every agent, so they must share the
+    // layer-0 activation scale (calibration always gives them the same)
+    if (e->tc->plan.esz == 1 && !(e->tc->scaled && e->tc->shared_l0)) return 0;
     const int tiles = (int)ceil_div(n, 128);
     if (tiles < e->ctx->sm_count) return 0;
     return (uint64_t)tiles * obs_tile_bytes(e->tc->plan);
@@ -367,7 +430,9 @@ uint64_t tc_tiled_scratch_bytes(const fr_ensemble *e, int n)
 int tc_forward_tiled(const fr_ensemble *e, const float *obs, int ld, int n, float *y, void *scratch, cudaStream_t s)
 {
     const TcImage *t = e->tc;
-    FR_CHECK(t && t->plan.split == 1 && scratch, FR_EINVAL, "tc_forward_tiled: needs a BF16 plan and scratch");
+    FR_CHECK(t && t->plan.split == 1 && scratch, FR_EINVAL, "tc_forward_tiled: needs a BF16 or FP8 plan and scratch");
+    const bool fp8 = t->plan.esz == 1;
+    FR_CHECK(!fp8 || (t->scaled && t->shared_l0), FR_EINVAL, "tc_forward_tiled: FP8 needs one layer-0 scale");
     const TcPlan &p = t->plan;
     int optin = 0;
     FR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, e->ctx->device));
@@ -375,14 +440,24 @@ int tc_forward_tiled(const fr_ensemble *e, const float *obs, int ld, int n, floa
     const int stages = ta_stages(p, optin, &stage_bytes);
     FR_CHECK(stages >= 2, FR_EINVAL, "tc_forward_tiled: the plan does not fit in shared memory");
     const int tiles = (int)ceil_div(n, 128);
-    const int nch = p.layer[0].K / 8;
+    const int nch = p.layer[0].K / p.ck;
     const int64_t threads = (int64_t)tiles * nch * 128;
-    k_obs_tiles<<<ceil_div(threads, 256), 256, 0, s>>>(obs, ld, n, p.layer[0].fin, nch, (uint4 *)scratch);
+    if (fp8)
+        k_obs_tiles_e4m3<<<ceil_div(threads, 256), 256, 0, s>>>(obs, ld, n, p.layer[0].fin, nch, 1.0f / t->sx[0][0],
+                                                                (uint4 *)scratch);
+    else
+        k_obs_tiles<<<ceil_div(threads, 256), 256, 0, s>>>(obs, ld, n, p.layer[0].fin, nch, (uint4 *)scratch);
     FR_CUDA(cudaGetLastError());
     const uint32_t smem = ta_layout(p, stages, stage_bytes).total + 1024u;
-    FR_CUDA(set_max_smem_once((const void *)k_tc_actor, e->ctx->device));
-    k_tc_actor<<<tiles, TA_THREADS, smem, s>>>(p, t->img, t->bias, (const uint8_t *)scratch, n, y, t->err, stages,
-                                                stage_bytes);
+    if (fp8) {
+        FR_CUDA(set_max_smem_once((const void *)k_tc_actor<true>, e->ctx->device));
+        k_tc_actor<true><<<tiles, TA_THREADS, smem, s>>>(p, t->img, t->bias, (const uint8_t *)scratch, n, y, t->err,
+                                                         stages, stage_bytes, t->dq, t->inv_sx);
+    } else {
+        FR_CUDA(set_max_smem_once((const void *)k_tc_actor<false>, e->ctx->device));
+        k_tc_actor<false><<<tiles, TA_THREADS, smem, s>>>(p, t->img, t->bias, (const uint8_t *)scratch, n, y, t->err,
+                                                          stages, stage_bytes, t->dq, t->inv_sx);
+    }
     FR_CUDA(cudaGetLastError());
     return FR_OK;
 }

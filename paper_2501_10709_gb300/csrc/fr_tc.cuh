@@ -64,6 +64,7 @@ struct TcImage {
     float sw[MAX_AGENTS][MAX_LAYERS][256];
     float sx[MAX_AGENTS][MAX_LAYERS];
     bool scaled = false;
+    bool shared_l0 = false;   // every agent has the same layer-0 scale
 };
 
 

@@ -186,3 +186,37 @@ def test_tiled_actor_equals_single_agent_kernel(ctx, dev, dims, M, extra, vote):
         else:
             err = np.linalg.norm(got - want, axis=-1) / np.maximum(np.linalg.norm(want, axis=-1), 1e-3)
             assert err.max() <= REL_TOL[fr.PREC_BF16], err.max()
+
+
+@pytest.mark.parametrize("dims, M, extra, shared", [(synth.STOCK_DIMS, 3, 77, True), ((301, 80, 48, 30), 2, 1, True),
+                                                    (synth.STOCK_DIMS, 3, 5, False)])
+def test_tiled_fp8_actor_equals_single_agent_kernel(ctx, dev, dims, M, extra, shared):
+    # FP8: the large-batch kernel quantises one observation tile for every
+    # agent, so it runs when the agents share the layer-0 activation scale
+    # (otherwise the single-agent kernel runs); either way the codes,
+    # products and roundings are the single-agent kernel's: equal bit for bit
+    n = ctx.sm_count * 128 + extra
+    params = synth.actor_params(dims, M, seed=22)
+    ens = fr.ensemble_create(ctx, dims, params, precision=fr.PREC_FP8)
+    L = len(dims) - 1
+    sc = np.tile(np.linspace(0.002, 0.01, L, dtype=np.float32), (M, 1))
+    if not shared:
+        sc[1, 0] *= 1.5
+    fr.ensemble_set_act_scales(ens, sc)
+    rng = np.random.default_rng(6)
+    obs = torch.from_numpy(rng.uniform(-1.5, 1.5, (n, dims[0])).astype(np.float32)).to(dev)
+    a = torch.empty(n, dims[-1], device=dev)
+    b = torch.full((n, dims[-1]), float("nan"), device=dev)
+    fr.ensemble_act(ens, obs, a)
+    fr.ensemble_act_noalloc(ens, obs, b)
+    y = torch.empty(M, n, dims[-1], device=dev)
+    fr.ensemble_forward(ens, obs, y)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    o = obs.cpu().numpy()
+    rows = np.random.default_rng(7).choice(n, 300, replace=False)
+    for j in range(M):
+        want = oracle.fp8_forward(dims, params[j], sc[j], o[rows], 1)
+        got = y[j].cpu().numpy()[rows].astype(np.float64)
+        err = np.linalg.norm(got - want, axis=-1) / np.maximum(np.linalg.norm(want, axis=-1), 1e-3)
+        assert err.max() <= 2e-2
