@@ -272,6 +272,12 @@ def serving_line(fr, ctx, mk, ens_by_name, duration=10.0, rate=200.0, drain_s=60
 # (1,398 B).  The market rows are shared by a cohort of 128 envs (L2).
 ENV_STEP_BYTES = 377 + 1398
 
+# DRAM bytes (read + write) of one 256-step k_rollout_stock2 launch on the
+# 2,048-env workload, from the ncu launch list of `bench.py --profile fused
+# --T 256` (profiles/fused_rollout_stock2_stock2048.md); the kernel is the
+# one this file times.
+K_ROLLOUT_STOCK2_DRAM_BYTES = 3.97e6
+
 
 def env_step_line(fr, ctx, mk, w, dev, stream, N=1 << 20, T=4, warm=2):
     """The standalone stock env-step kernel with trajectory outputs at a size
@@ -605,7 +611,7 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": "env-steps/s",
                 "h2d_bytes_per_step": len(snap), "d2h_bytes_per_step": N * 3 * 8},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": K_ROLLOUT_STOCK2_DRAM_BYTES,
                      "kernel": f"k_rollout_stock2 ({N} envs x {T} steps x {M} agents per launch)",
                      "kernel_ms": 1e3 * k_dt,
                      "flops_per_launch": N * T * flops_env_step,

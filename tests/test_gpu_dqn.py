@@ -147,3 +147,48 @@ def test_heads_errors_and_validation(ctx, dev):
         q = fr.ensemble_q(one, obs)
         torch.cuda.synchronize()
         assert np.array_equal(votes.cpu().numpy(), q[0].argmax(-1).cpu().numpy().astype(np.uint8))
+
+
+def test_rollout_replay_targets_pipeline(ctx, dev):
+    # producer -> reservoir -> consumer (Sec. 3.2) on the device: an
+    # epsilon-greedy crypto rollout of a mixed DQN / Dueling ensemble fills
+    # the replay buffer; a sampled batch gives Double DQN targets.  The
+    # oracle replays the same trajectory into its replay model and evaluates
+    # the targets of the same sampled transitions.
+    w = synth.workload_crypto(N=512, T=40, S=30_000)
+    e = w.envs
+    params = _params(14)
+    mk = fr.fr_market_create(ctx, w.market)
+    env = fr.env_create(ctx, mk, start=e.start, window=np.full(e.N, 30, np.int32), init_cash=e.init_cash,
+                        pmax=e.pmax)
+    ens = fr.ensemble_create(ctx, DIMS, params, precision=fr.PREC_FP32, combine=fr.COMBINE_VOTE, out_act=0,
+                             heads=HEADS)
+    tgt = fr.ensemble_create(ctx, DIMS, _params(15), precision=fr.PREC_FP32, combine=fr.COMBINE_VOTE, out_act=0,
+                             heads=HEADS)
+    fr.env_set_exploration(env, fr.EXPLORE_EPS_GREEDY, eps=0.05, seed=77)
+    T = 36
+    tr = {"obs": torch.empty(T, e.N, 10, device=dev), "act": torch.empty(T, e.N, dtype=torch.uint8, device=dev),
+          "rew_f32": torch.empty(T, e.N, device=dev), "done": torch.empty(T, e.N, dtype=torch.uint8, device=dev)}
+    fr.rollout(env, ens, T, traj=tr)
+    last = torch.empty(e.N, 10, device=dev)
+    fr.env_observe(env, last)
+    rb = fr.replay_create(ctx, env, 100_000)
+    fr.replay_push(rb, env, tr, T, last)
+    B = 2048
+    smp = fr.replay_sample(rb, B, seed=3, counter=1)
+    y = fr.ensemble_q_targets(ens, tgt, smp["next_obs"], smp["rew"], smp["done"], gamma=0.99, double_q=True)
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in tr.items()}
+    ref = oracle.ReplayRef(100_000)
+    ref.push(g["obs"], g["act"], g["rew_f32"], g["done"], last.cpu().numpy())
+    assert fr.replay_size(rb)[0] == len(ref.contents()) < T * e.N       # frozen rows after the 29 steps
+    pos = ref.sample_positions(B, 3, 1)
+    assert np.array_equal(smp["index"].cpu().numpy(), np.array(pos))
+    items = ref.contents()
+    nxt = np.stack([items[p][3] for p in pos])
+    rew = np.array([items[p][2] for p in pos], np.float32)
+    dn = np.array([items[p][4] for p in pos], np.uint8)
+    assert dn.sum() > 0 and np.array_equal(smp["next_obs"].cpu().numpy(), nxt)
+    want = oracle.q_targets(DIMS, params, _params(15), HEADS, nxt, rew, dn, 0.99, True)
+    got = y.cpu().numpy().astype(np.float64)
+    assert np.abs(got - want).max() <= 1e-4 * np.abs(want).max()
