@@ -390,6 +390,17 @@ def uneven_line(fr, ctx, dev, flush, stream, reps=3):
         res[name] = {"value": work * len(ts) / sum(ts), "ms_per_rollout": 1e3 * statistics.mean(ts)}
     fr.env_set_tile_packing(env, True)
     res["tile_efficiency_packed"] = fr.env_tile_packing_efficiency(env)
+    # the autotuner: every launch configuration for this pair timed on probes
+    # of the rollout's own length (packing pays off only over the long
+    # windows) on the env's own state; the fastest then timed as above
+    tune = fr.env_autotune(env, ens, w.T, force=True)
+    ts = time_rollouts(fr, env, ens, w.T, reps, 3, met, flush, stream)
+    res["autotuned"] = {"value": work * len(ts) / sum(ts), "ms_per_rollout": 1e3 * statistics.mean(ts),
+                        "chosen": tune["chosen"],
+                        "candidates": [{k: (round(v, 4) if k == "ms" else v) for k, v in c.items()}
+                                       for c in tune["candidates"]],
+                        "probe_steps": w.T}
+    fr.env_tune_clear(env)
     # FP8 E4M3 actors: activation scales calibrated on 4,096 observations the
     # BF16 ensemble visits in the first 8 steps; FP8 rollouts run the unfused
     # path (one launch per stage per step)

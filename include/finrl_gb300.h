@@ -480,6 +480,48 @@ int env_set_rollout_path(fr_env *env, int32_t path);
 int env_set_tile_packing(fr_env *env, int32_t on);
 int env_tile_packing_efficiency(const fr_env *env, float *eff);
 
+/* Autotuner of the batched rollouts (no counterpart in the paper: the
+ * project's own choice of launch shape).  Times, for this env batch and
+ * ensemble, the launch configurations the library has for the pair and keeps
+ * the fastest for the env's later rollouts:
+ *   path 2  the resident-weight fused stock kernel, tile packing on (packed =
+ *           1) or off (only when the windows differ and auto-reset is off);
+ *   path 1  the first fused kernel with `stages` weight-ring stages: the most
+ *           that fit, the fewest that hold a whole step's weights resident,
+ *           and 2 (weights streamed every step);
+ *   path 0  the unfused path, with (tiled = 1) or without the large-batch
+ *           actor kernel.
+ * Each candidate runs a rollout of T_probe steps (1..4096) on the env's own
+ * state three times (the first a warm-up; the mean of the other two, timed
+ * with CUDA events on `stream`, is reported), the state restored from a host
+ * snapshot before each run and at the end, so the env is left as it was.
+ * The choice is also kept in a process-wide cache keyed by the pair's shape;
+ * a later call with the same shape takes it without timing (cached = 1)
+ * unless flags has FR_TUNE_FORCE.  Synchronous.  Tile packing, ring depth
+ * and the actor kernel never change results; the three paths compute the
+ * same function, each within the stated tolerance of the oracle.
+ * env_tune_set pins one configuration (a path that does not apply to a pair
+ * falls back as the default does: resident fused, first fused, unfused);
+ * path 0..2, stages 0 (the most that fit) or >= 2.
+ * env_tune_clear returns the env to the default choice (the resident fused
+ * kernel, else the first fused kernel, else unfused; packing on). */
+#define FR_TUNE_MAX 8
+#define FR_TUNE_FORCE 1
+typedef struct {
+    int32_t n;                    /* configurations reported                 */
+    int32_t chosen;               /* index of the one kept                   */
+    int32_t cached;               /* 1: taken from the cache, not timed      */
+    int32_t path[FR_TUNE_MAX];
+    int32_t packed[FR_TUNE_MAX];
+    int32_t stages[FR_TUNE_MAX];
+    int32_t tiled[FR_TUNE_MAX];
+    float ms[FR_TUNE_MAX];        /* mean time of a T_probe-step rollout     */
+} fr_tune_report;
+int env_autotune(fr_env *env, const fr_ensemble *ens, int32_t T_probe, int32_t flags, fr_tune_report *out,
+                 void *stream);
+int env_tune_set(fr_env *env, int32_t path, int32_t packed, int32_t stages, int32_t tiled);
+int env_tune_clear(fr_env *env);
+
 /* Kernel timing for roofline measurements (no counterpart in the paper).
  * With on != 0, every later rollout() of this env records two CUDA events
  * on its stream around the launch of its main rollout kernel only (the

@@ -27,7 +27,7 @@ __all__ = [
     "backtest_poll", "fr_server_stats", "FrError", "lib", "market_indicators", "fr_market_indicators",
     "env_perturb", "ensemble_set_act_scales", "ensemble_get_act_scales", "ensemble_calibrate_sync",
     "Replay", "replay_create", "replay_push", "replay_sample", "replay_size", "ensemble_q", "ensemble_q_targets",
-    "HEAD_Q", "HEAD_DUELING",
+    "HEAD_Q", "HEAD_DUELING", "env_autotune", "env_tune_clear", "env_tune_set",
     "PATH_AUTO", "PATH_UNFUSED",
     "ACT_I32_SHARES", "ACT_F32_UNIT", "ACT_U8_DISCRETE", "PREC_FP32", "PREC_BF16",
     "PREC_FP8", "PREC_BF16X3", "COMBINE_MEAN", "COMBINE_VOTE", "TASK_STOCK", "TASK_CRYPTO",
@@ -396,6 +396,29 @@ def rollout(env: Env, ens: Ensemble, T: int, *, traj: dict | None = None, metric
     _lib.check(lib().rollout(env, ens, int(T), tp,
                              _dptr(metrics, torch.float64, env.N * 3, "metrics"),
                              _stream(stream)), "rollout")
+
+
+# ---------------------------------------------------------------- autotuner
+def env_autotune(env: Env, ens: Ensemble, T_probe: int = 16, *, force: bool = False, stream=None) -> dict:
+    """Time the launch configurations for this env / ensemble pair on the
+    env's own state (restored afterwards) and keep the fastest; returns the
+    report: candidates (path, packed, stages, tiled, ms), chosen, cached."""
+    r = _lib.TuneReport()
+    _lib.check(lib().env_autotune(env, ens, int(T_probe), 1 if force else 0, C.byref(r), _stream(stream)),
+               "env_autotune")
+    cands = [dict(path=r.path[i], packed=r.packed[i], stages=r.stages[i], tiled=r.tiled[i], ms=r.ms[i])
+             for i in range(r.n)]
+    return {"candidates": cands, "chosen": r.chosen, "cached": bool(r.cached)}
+
+
+def env_tune_set(env: Env, path: int, packed: bool = True, stages: int = 0, tiled: bool = True):
+    """Pin one launch configuration (see env_autotune's candidates)."""
+    _lib.check(lib().env_tune_set(env, int(path), 1 if packed else 0, int(stages), 1 if tiled else 0),
+               "env_tune_set")
+
+
+def env_tune_clear(env: Env):
+    _lib.check(lib().env_tune_clear(env), "env_tune_clear")
 
 
 # ------------------------------------------------------------ replay buffer

@@ -32,6 +32,11 @@ class MarketDesc(C.Structure):
                 ("spread", vp), ("fac", vp), ("high", vp), ("low", vp)]
 
 
+class TuneReport(C.Structure):
+    _fields_ = [("n", i32), ("chosen", i32), ("cached", i32), ("path", i32 * 8), ("packed", i32 * 8),
+                ("stages", i32 * 8), ("tiled", i32 * 8), ("ms", C.c_float * 8)]
+
+
 class EnvDesc(C.Structure):
     _fields_ = [("task", i32), ("n_envs", i32), ("n_assets", vp), ("window", vp),
                 ("start", vp), ("bps", vp), ("init_cash", i64), ("hmax", i32),
@@ -133,6 +138,9 @@ SIGNATURES = {
     "ensemble_calibrate_sync": (i32, [vp, vp, i32, vp]),
     "ensemble_q": (i32, [vp, vp, i32, vp, vp]),
     "ensemble_q_targets": (i32, [vp, vp, vp, vp, vp, i32, C.c_float, i32, vp, vp]),
+    "env_autotune": (i32, [vp, vp, i32, i32, vp, vp]),
+    "env_tune_clear": (i32, [vp]),
+    "env_tune_set": (i32, [vp, i32, i32, i32, i32]),
     "replay_create": (i32, [vp, vp, i64, vp]),
     "replay_destroy": (None, [vp]),
     "replay_push": (i32, [vp, vp, vp, i32, vp, vp, vp]),

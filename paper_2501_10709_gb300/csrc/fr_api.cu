@@ -947,8 +947,10 @@ int rollout(fr_env *env, const fr_ensemble *e, int32_t T, const fr_traj *traj, d
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if (env->path == FR_PATH_AUTO && e->precision != FR_PREC_FP32) {
-        if (f2_supported(env, e)) rc = f2_rollout(env, e, T, traj, metrics, s);
-        else if (tc_rollout_supported(env, e)) rc = tc_rollout(env, e, T, traj, metrics, s);
+        // an autotuned path when it still applies, else the default order
+        const int tp = env->tune_set ? env->tune_path : -1;
+        if ((tp < 0 || tp == 2) && f2_supported(env, e)) rc = f2_rollout(env, e, T, traj, metrics, s);
+        else if ((tp < 0 || tp >= 1) && tc_rollout_supported(env, e)) rc = tc_rollout(env, e, T, traj, metrics, s);
         else rc = plain_rollout(env, e, T, traj, metrics, s);
     } else {
         rc = plain_rollout(env, e, T, traj, metrics, s);
@@ -971,7 +973,9 @@ static int plain_rollout(fr_env *env, const fr_ensemble *e, int32_t T, const fr_
     const uint64_t obs_b = (4ull * N * v.D + 255) & ~255ull;
     const uint64_t act_b = ((stock ? 4ull * N * v.K : (uint64_t)N) + 255) & ~255ull;
     const uint64_t y_b = (4ull * e->M * N * out + 255) & ~255ull;
-    const uint64_t tiles_b = (e->precision == FR_PREC_FP32) ? 0 : ((tc_tiled_scratch_bytes(e, N) + 255) & ~255ull);
+    const bool tiled_ok = !(env->tune_set && !env->tune_tiled);
+    const uint64_t tiles_b =
+        (e->precision == FR_PREC_FP32 || !tiled_ok) ? 0 : ((tc_tiled_scratch_bytes(e, N) + 255) & ~255ull);
     const uint64_t need = obs_b + act_b + y_b + tiles_b + plain_scratch_bytes(e, N);
     if (env->scratch_bytes < need) {
         FR_CUDA(cudaStreamSynchronize(s));

@@ -127,6 +127,14 @@ struct fr_env {
     uint32_t explore_thr;
     uint64_t explore_seed;
     uint32_t explore_step;
+    // launch configuration chosen by env_autotune (tune_set = 0: the default
+    // choice): path 2 the resident-weight fused kernel, 1 the first fused
+    // kernel, 0 unfused; the first fused kernel's ring stages (0 = the most
+    // that fit); whether the unfused path may use the large-batch actor kernel
+    int tune_set;
+    int tune_path;
+    int tune_stages;
+    int tune_tiled;
     // optional events around the main rollout kernel
     cudaEvent_t k_ev[2];
     int k_timing;               // record on the next rollouts
@@ -307,6 +315,7 @@ bool f2_supported(const fr_env *env, const fr_ensemble *e);
 int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, double *metrics,
                cudaStream_t s);
 void f2_release(const fr_ensemble *e);
+int tc_rollout_max_stages(const fr_env *env, const fr_ensemble *e, int *chunks_per_step_out);
 int tc_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, double *metrics,
                cudaStream_t s);
 }  // namespace fr

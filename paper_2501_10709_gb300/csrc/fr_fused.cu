@@ -960,6 +960,19 @@ bool tc_rollout_supported(const fr_env *env, const fr_ensemble *e)
     return pick_stages(v.task, p, optin, &resident) > 0;
 }
 
+// The first fused kernel's largest ring for this pair (0: the kernel does not
+// apply) and the chunks of one step (the ring holds the weights resident when
+// it has at least that many stages).
+int tc_rollout_max_stages(const fr_env *env, const fr_ensemble *e, int *chunks_per_step_out)
+{
+    if (!tc_rollout_supported(env, e)) return 0;
+    int optin = 0, resident = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, env->ctx->device) != cudaSuccess)
+        return 0;
+    *chunks_per_step_out = chunks_per_step(e->tc->plan);
+    return pick_stages(env->v.task, e->tc->plan, optin, &resident);
+}
+
 int tc_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, double *metrics,
                cudaStream_t s)
 {
@@ -967,8 +980,14 @@ int tc_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     const TcPlan &p = e->tc->plan;
     int optin = 0, resident = 0;
     FR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, env->ctx->device));
-    const int stages = pick_stages(v.task, p, optin, &resident);
+    int stages = pick_stages(v.task, p, optin, &resident);
     FR_CHECK(stages > 0, FR_EINVAL, "fused rollout: plan does not fit in shared memory");
+    if (env->tune_set && env->tune_stages >= 2 && env->tune_stages < stages) {
+        // an autotuned ring: fewer stages; weights stay resident only while a
+        // whole step's chunks still fit
+        stages = env->tune_stages;
+        resident = chunks_per_step(p) <= stages ? 1 : 0;
+    }
     if (T == 0) {
         if (metrics) FR_CUDA(launch_env_metrics(v, metrics, s));
         return FR_OK;
