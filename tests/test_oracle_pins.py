@@ -104,6 +104,24 @@ def test_discretise_exhaustive_near_every_share_boundary():
         assert bad.size == 0, (hmax, x[bad[:5]], got[bad[:5]], want[bad[:5]])
 
 
+def test_discretise_every_float32_in_unit_interval():
+    # all 2,130,706,433 float32 values in [-1, 1] (both signs, subnormals and
+    # zeros included), hmax = 100: the oracle's trunc(x * 100) against the
+    # exact value from the float's bits, trunc(m * 100 * 2^e) with m the
+    # 24-bit significand and e the unbiased exponent - integer shifts only
+    one = 0x3F800000                                   # bit pattern of 1.0f
+    chunk = 1 << 25
+    for lo in range(0, one + 1, chunk):
+        bits = np.arange(lo, min(lo + chunk, one + 1), dtype=np.uint32)
+        ex = (bits >> 23).astype(np.int64)
+        m = (bits & 0x7FFFFF).astype(np.int64) | np.where(ex > 0, 1 << 23, 0)
+        sh = np.where(ex > 0, 150 - ex, 149)           # x = m * 2^(-sh), sh >= 23 here
+        want = np.where(sh >= 40, 0, (m * 100) >> np.minimum(sh, 39))
+        x = bits.view(np.float32)
+        assert np.array_equal(oracle.discretise_many(x, 100), want), hex(lo)
+        assert np.array_equal(oracle.discretise_many(-x, 100), -want), hex(lo)
+
+
 def test_discretise_clips_and_zeroes_non_finite():
     f = np.float32
     vals = [f(1.0), f(1.0000001), f(7.5), f(-3.0), f(np.inf), f(-np.inf),
