@@ -13,9 +13,10 @@
 //            (cash, prices, holdings; K = 64) and the epilogue adds Z;
 //   layer 2  full h1 (both halves: the partner writes its half into this
 //            CTA's A operand through distributed shared memory), N-half;
-//   layer 3  K-split: the half h = 1 CTA sends its partial sums to its
-//            partner, which adds bias, applies tanh and pushes the agent's
-//            actions (fp16) to the env's owner CTA.
+//   layer 3  K-split: both halves send their fp32 partial sums of each row
+//            straight to the env's owner CTA, which adds them and the bias
+//            and applies tanh (one exchange instead of a partner exchange
+//            followed by a push of the finished actions).
 //
 // Env r of the tile is owned by the CTA of rank r mod 2M: one warp per env,
 // lane = asset, state in registers.  The owner combines the agents' actions
@@ -128,9 +129,13 @@ bool f2_plan(const fr_ensemble *e, F2Plan &p)
     return true;
 }
 
+// Rows of the tile owned by one CTA: row r belongs to rank r mod 2M and sits
+// at index r / 2M of that CTA's owned rows.
+__host__ __device__ inline int f2_owned_rows(int M) { return (128 + 2 * M - 1) / (2 * M); }
+
 // shared-memory carve-up
 struct F2Smem {
-    uint32_t w, a, pbuf, xbuf, ctx, bias, bars, total;
+    uint32_t w, a, xbuf, ctx, bias, bars, total;
 };
 
 __host__ __device__ inline F2Smem f2_smem(const F2Plan &p)
@@ -138,17 +143,18 @@ __host__ __device__ inline F2Smem f2_smem(const F2Plan &p)
     F2Smem s;
     s.w = 0;
     s.a = p.cta_bytes;
-    s.pbuf = s.a + p.a_bytes;                       // [128][32] fp32 partial sums
-    s.xbuf = s.pbuf + 128u * 32u * 4u;              // [M][128][32] fp16 agent actions
-    s.ctx = s.xbuf + (uint32_t)p.M * 128u * 64u;    // [128] int32 Z row of each env
-    s.bias = s.ctx + 512u;                          // this CTA's b2 half [128] + b3 [32]
-    s.bars = s.bias + 640u;
+    // [2M][owned rows][32] fp32 layer-3 partial sums of this CTA's owned
+    // rows, one block per sending CTA (agent j, half h at block 2j + h)
+    s.xbuf = s.a + p.a_bytes;
+    s.ctx = s.xbuf + (uint32_t)(2 * p.M * f2_owned_rows(p.M)) * 128u;   // [128] int32 Z row of each env
+    s.bias = s.ctx + 512u;                          // this CTA's b2 half [128], b3 of every agent [4][32]
+    s.bars = s.bias + 1024u;
     s.total = s.bars + 256u;
     return s;
 }
 
 // barrier slots
-enum { B_W = 0, B_OBS, B_ACC, B_H1, B_H2, B_P, B_X, B_END, B_COUNT };
+enum { B_W = 0, B_OBS, B_ACC, B_H1, B_H2, B_X, B_END, B_COUNT };
 
 __device__ __forceinline__ bool f2_wait(uint64_t *bar, uint32_t parity, volatile int *abort, unsigned *err,
                                         unsigned code, bool cluster_scope)
@@ -378,12 +384,12 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
     const uint32_t tmem_row = tmem + ((uint32_t)(q * 32) << 16);
     const uint32_t a_base = smem_u32(smem + L.a);
     const uint32_t row_off = (uint32_t)(r / 8) * 128u + (uint32_t)(r % 8) * 16u;
-    const uint32_t pbuf = smem_u32(smem + L.pbuf);
     const uint32_t xbuf = smem_u32(smem + L.xbuf);
+    const int RO = f2_owned_rows(M);
     const uint32_t ctx_addr = smem_u32(smem + L.ctx);
     const int32_t *ctxv = (const int32_t *)(smem + L.ctx);
     uint64_t *obs_ready = &bars[B_OBS], *acc = &bars[B_ACC], *h1r = &bars[B_H1], *h2r = &bars[B_H2];
-    uint64_t *prdy = &bars[B_P], *xrdy = &bars[B_X];
+    uint64_t *xrdy = &bars[B_X];
     const int tile0 = tile * 128;
     const bool issuer = ew == 0;
     const uint32_t w_base = smem_u32(smem + L.w);
@@ -535,7 +541,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
             if (lane == 0) f2_layer(p.l3, tmem + 128u, a_base, w_base, acc);
             __syncwarp();
         }
-        // --------------------------------------- E3: partial sums -> actions
+        // --------------------------------- E3: partial sums to the owners
         f2_wait(acc, (uint32_t)(3 * s + 2) & 1u, abort, a.err, 16u, false);
         tc_fence_after();
         if (col_half == 0) {                        // one warp per lane quarter reads the 32 columns
@@ -543,49 +549,16 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
             __syncwarp();
             tmem_ld32(tmem_row + 128u, vv);
             tmem_ld_wait();
-            if (hh == 1) {                          // partial to the partner
-                // row r, column group k stored at group k ^ (r & 7): the
-                // partner's 16-byte reads of one group are conflict-free
-                const uint32_t dst = map_shared_rank(pbuf + (uint32_t)r * 128u, (uint32_t)(rank ^ 1));
+            // row r's partial sums to block `rank` of its owner's buffer, at
+            // owned row r / 2M; column group k stored at group k ^ (row & 7),
+            // so that the owner's per-lane reads of one row are conflict-free
+            const uint32_t ri = (uint32_t)(r / M2);
+            const uint32_t dst = map_shared_rank(xbuf + ((uint32_t)rank * (uint32_t)RO + ri) * 128u, (uint32_t)(r % M2));
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    st_cluster_v4(dst + 16u * (uint32_t)(k ^ (r & 7)), vv[4 * k], vv[4 * k + 1], vv[4 * k + 2],
-                                  vv[4 * k + 3]);
-                __syncwarp();
-                if (lane == 0) {
-                    fence_acq_rel_cluster();
-                    mbar_arrive_remote_relaxed(map_shared_rank(smem_u32(prdy), (uint32_t)(rank ^ 1)));
-                }
-            } else {
-                f2_wait(prdy, ph, abort, a.err, 32u, true);
-                const float *b3 = (const float *)(smem + L.bias) + 128;
-                float pp[32];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const uint4 g = ld_shared_v4(pbuf + (uint32_t)r * 128u + 16u * (uint32_t)(k ^ (r & 7)));
-                    pp[4 * k + 0] = __uint_as_float(g.x);
-                    pp[4 * k + 1] = __uint_as_float(g.y);
-                    pp[4 * k + 2] = __uint_as_float(g.z);
-                    pp[4 * k + 3] = __uint_as_float(g.w);
-                }
-                uint32_t pk[16];
-#pragma unroll
-                for (int c = 0; c < 32; c += 2) {
-                    const float y0 = c < SK2 ? tanh_approx(__fadd_rn(__fadd_rn(__uint_as_float(vv[c]), pp[c]), b3[c])) : 0.0f;
-                    const float y1 = c + 1 < SK2
-                                         ? tanh_approx(__fadd_rn(__fadd_rn(__uint_as_float(vv[c + 1]), pp[c + 1]), b3[c + 1]))
-                                         : 0.0f;
-                    const __half2 h2 = __floats2half2_rn(y0, y1);
-                    pk[c / 2] = *(const uint32_t *)&h2;
-                }
-                // to the owner of row r
-                const uint32_t dst = map_shared_rank(xbuf + ((uint32_t)j * 128u + (uint32_t)r) * 64u, (uint32_t)(r % M2));
-                st_cluster_v4(dst, pk[0], pk[1], pk[2], pk[3]);
-                st_cluster_v4(dst + 16u, pk[4], pk[5], pk[6], pk[7]);
-                st_cluster_v4(dst + 32u, pk[8], pk[9], pk[10], pk[11]);
-                st_cluster_v4(dst + 48u, pk[12], pk[13], pk[14], pk[15]);
-                f2_signal_all(xrdy, M2, lane, false);
-            }
+            for (int k = 0; k < 8; ++k)
+                st_cluster_v4(dst + 16u * ((uint32_t)k ^ (ri & 7u)), vv[4 * k], vv[4 * k + 1], vv[4 * k + 2],
+                              vv[4 * k + 3]);
+            f2_signal_all(xrdy, M2, lane, false);
         }
         tc_fence_before();
         // --------------------------------------------- owners: trade, publish
@@ -608,16 +581,25 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
 #pragma unroll
         for (int i = 0; i < NOWN; ++i) {
             const OwnEnv &st = own[i];
-            const int rr = orow[i] < 128 ? orow[i] : 127;
+            const int ri = min(orow[i] / M2, RO - 1);
             const int e = eidx[i];
+            // agent jj's action for this lane's asset: tanh(partial of half 0
+            // + partial of half 1 + b3), rounded to fp16
+            const uint8_t *xr = smem + L.xbuf + (size_t)ri * 128 + 16 * ((lane >> 2) ^ (ri & 7)) + 4 * (lane & 3);
+            const float *b3s = (const float *)(smem + L.bias) + 128;
+            auto agent_act = [&](int jj) {
+                const float p0 = *(const float *)(xr + (size_t)(2 * jj) * RO * 128);
+                const float p1 = *(const float *)(xr + (size_t)(2 * jj + 1) * RO * 128);
+                const float y = lane < SK2 ? tanh_approx(__fadd_rn(__fadd_rn(p0, p1), b3s[32 * jj + lane])) : 0.0f;
+                return __half2float(__float2half_rn(y));
+            };
             // combine (anchored weighted mean) for this lane's asset
-            const uint8_t *xr = smem + L.xbuf + (size_t)rr * 64 + 2 * lane;
-            const float a0 = __half2float(*(const __half *)xr);
+            const float a0 = agent_act(0);
             float act = a0;
 #pragma unroll
             for (int jj = 1; jj < 4; ++jj) {
                 if (jj < M) {
-                    const float aj = __half2float(*(const __half *)(xr + (size_t)jj * 128 * 64));
+                    const float aj = agent_act(jj);
                     const float wj = jj == 1 ? w1 : (jj == 2 ? w2 : w3);
                     act = __fadd_rn(act, __fmul_rn(wj, __fsub_rn(aj, a0)));
                 }
@@ -729,8 +711,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_rollout_stock2(const __grid_c
         mbar_init(&bars[B_ACC], 1);
         mbar_init(&bars[B_H1], 2u * F2_ENV_WARPS);                 // this CTA's and the partner's E1 warps
         mbar_init(&bars[B_H2], (uint32_t)F2_ENV_WARPS);            // this CTA's E2 warps
-        mbar_init(&bars[B_P], 4u);                                 // the partner's 4 E3 warps
-        mbar_init(&bars[B_X], (uint32_t)(p.M * 4));                // each agent's 4 E3 warps
+        mbar_init(&bars[B_X], (uint32_t)(M2 * 4));                 // the 4 E3 warps of every CTA
         mbar_init(&bars[B_END], 1);                                // the issuer's last commit
         *abort = 0;
         fence_mbar_init();
@@ -741,11 +722,11 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_rollout_stock2(const __grid_c
         tmem_relinquish();
     }
     if (warp == 2) {
-        // this CTA's b2 half and b3, read by every epilogue warp
+        // this CTA's b2 half (epilogue 2) and every agent's b3 (owners)
         float *bs = (float *)(smem + L.bias);
         const int jj = rank >> 1, h2 = rank & 1;
         for (int i = lane; i < 128; i += 32) bs[i] = i < p.n2 ? a.b2[(size_t)jj * p.H2 + h2 * p.n2 + i] : 0.0f;
-        bs[128 + lane] = a.b3[(size_t)jj * 32 + lane];
+        for (int i = lane; i < 4 * 32; i += 32) bs[128 + i] = i < p.M * 32 ? a.b3[i] : 0.0f;
     }
     tc_fence_before();
     __syncthreads();
