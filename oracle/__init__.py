@@ -82,7 +82,7 @@ def _load():
                                       i32, vp, vp, vp, vp,
                                       i64, i32, i32, i32, i32, i32,
                                       vp, vp, i32, i32, vp, vp, vp,
-                                      vp, vp, vp, vp, vp, vp, vp, vp, vp, i32]
+                                      vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32]
         lib.orc_stock_run.restype = i32
         lib.orc_crypto_run.argtypes = [i32, vp, vp, vp, i32, vp, vp, i64, i32,
                                        i32, i32, i32, vp, i32, i32, vp, vp,
@@ -466,7 +466,7 @@ def stock_run(market, Ke, start, W, bps, *, init_cash: int, hmax: int,
               fee_bps: int, T: int, auto_reset: bool = False,
               act_i32=None, act_f32=None, ensemble=None, nthreads: int = 0,
               want=("obs", "q", "rew", "rew_f32", "done", "cash", "hold",
-                    "metrics", "act")) -> dict:
+                    "metrics", "act"), buy_order: int = 0) -> dict:
     """Run T steps of N stock envs from reset.
 
     market: object with ``close`` int64[n_days][K] and either an indicator
@@ -474,6 +474,8 @@ def stock_run(market, Ke, start, W, bps, *, init_cash: int, hmax: int,
     the oracle's own ``indicators``).
     Exactly one action source: act_i32[T][N][K] (mode 0), act_f32[T][N][K]
     (mode 1) or ensemble = (dims, params[M][P] f32, weights or None) (mode 2).
+    buy_order: 0 buys in ascending asset order, 1 largest requested count
+    first (ties in ascending asset order).
     """
     close = _c(market.close, np.int64)
     ind = _c(market_table(market), np.float32)
@@ -520,7 +522,7 @@ def stock_run(market, Ke, start, W, bps, *, init_cash: int, hmax: int,
         int(init_cash), int(hmax), int(fee_bps), int(bool(auto_reset)), int(T),
         mode, _p(ai), _p(af), M, L, _p(dims), _p(params), _p(wts),
         _p(obs), _p(act), _p(q), _p(rew), _p(rf), _p(dn), _p(cash), _p(hold),
-        _p(met), nthreads or max_threads())
+        _p(met), nthreads or max_threads(), int(buy_order))
     if rc != 0:
         raise ValueError(f"oracle stock_run rejected its inputs (code {rc})")
     return o

@@ -30,8 +30,9 @@
  * Readings where the paper is silent (each is listed in the design notes):
  *   prices and cash are integer cents, holdings integer shares >= 0;
  *   an action in [-1,1] becomes trunc(a * hmax) shares (round toward zero);
- *   sells execute before buys; buys fill greedily in ascending asset order,
- *   partially when cash runs short; the fee is ceil(notional * fee_bps / 1e4)
+ *   sells execute before buys; buys fill greedily in ascending asset order
+ *   (or, as an option, largest requested count first), partially when cash
+ *   runs short; the fee is ceil(notional * fee_bps / 1e4)
  *   per order on both sides; the perturbed price is
  *   max(1, round-half-up(close * (1e4 + bps) / 1e4)); a W-day window has W-1
  *   steps; argmax ties go to the lowest index; a vote with no strict winner
@@ -544,10 +545,27 @@ static void stock_reset(stock_env *e, int K, int64_t init_cash)
 }
 
 /* Execute integer share changes q[0..Ke) at prices p: sells first (capped at
- * holdings), then greedy buys in ascending asset order under the cash. */
+ * holdings), then greedy buys under the cash, in ascending asset order
+ * (buy_order 0) or largest requested count first with ties in ascending
+ * asset order (buy_order 1); each buy fills as far as the cash allows. */
 static void stock_trade(stock_env *e, const int32_t *q, const int64_t *p,
-                        int Ke, int32_t fee_bps)
+                        int Ke, int32_t fee_bps, int32_t buy_order)
 {
+    int order[Ke];
+    for (int k = 0; k < Ke; ++k) order[k] = k;
+    if (buy_order == 1) {
+        /* stable insertion sort by decreasing q: equal counts keep their
+         * ascending asset order */
+        for (int i = 1; i < Ke; ++i) {
+            const int k = order[i];
+            int j = i;
+            while (j > 0 && q[order[j - 1]] < q[k]) {
+                order[j] = order[j - 1];
+                --j;
+            }
+            order[j] = k;
+        }
+    }
     for (int k = 0; k < Ke; ++k) {
         if (q[k] < 0) {
             int64_t n = -(int64_t)q[k];
@@ -557,7 +575,8 @@ static void stock_trade(stock_env *e, const int32_t *q, const int64_t *p,
             e->cash += g - orc_fee(g, fee_bps);
         }
     }
-    for (int k = 0; k < Ke; ++k) {
+    for (int i = 0; i < Ke; ++i) {
+        const int k = order[i];
         if (q[k] > 0) {
             int64_t n0 = orc_buy_max(e->cash, p[k], fee_bps);
             int64_t n = q[k] < n0 ? q[k] : n0;
@@ -587,6 +606,8 @@ static void stock_trade(stock_env *e, const int32_t *q, const int64_t *p,
  * q[T][N][K] (executed share orders before caps), rew[T][N], rew_f32[T][N],
  * done[T][N], cash[T][N] and hold[T][N][K] after the step, metrics[N][3]
  * (cumulative return, Sharpe with A = 252, MDD) after the last step.
+ * buy_order: 0 ascending asset order, 1 largest requested count first
+ * (see stock_trade).
  */
 int32_t orc_stock_run(int32_t n_days, int32_t K, int32_t I,
                       const int64_t *close, const float *ind,
@@ -600,9 +621,10 @@ int32_t orc_stock_run(int32_t n_days, int32_t K, int32_t I,
                       float *obs, double *act_out, int32_t *q_out,
                       int64_t *rew, float *rew_f32, uint8_t *done_out,
                       int64_t *cash_out, int32_t *hold_out, double *metrics,
-                      int32_t nthreads)
+                      int32_t nthreads, int32_t buy_order)
 {
     const int D = 1 + 2 * K + I * K;
+    if (buy_order != 0 && buy_order != 1) return -3;
     for (int e = 0; e < N; ++e) {
         if (Ke[e] < 1 || Ke[e] > K || W[e] < 2 || start[e] < 0 ||
             start[e] + W[e] > n_days)
@@ -660,7 +682,7 @@ int32_t orc_stock_run(int32_t n_days, int32_t K, int32_t I,
                     dn = 1;
                 } else {
                     int64_t v0 = stock_value(env.cash, env.h, p, ke);
-                    stock_trade(&env, q, p, ke, fee_bps);
+                    stock_trade(&env, q, p, ke, fee_bps, buy_order);
                     env.t += 1;
                     stock_prices(close, eb, K, ke, d + 1, p1);
                     int64_t v1 = stock_value(env.cash, env.h, p1, ke);

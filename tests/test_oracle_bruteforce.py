@@ -24,9 +24,11 @@ def _fee(g, fee_bps):
     return math.ceil(Fraction(g * fee_bps, 10000))
 
 
-def ref_stock_env(close, bps, start, W, init_cash, fee_bps, orders):
+def ref_stock_env(close, bps, start, W, init_cash, fee_bps, orders, largest_first=False):
     """One stock env, exact.  close[day][k]; orders: list of per-step share
-    orders.  Returns per step (reward, cash, holdings, done)."""
+    orders; buys in ascending asset order, or by decreasing requested count
+    (ties ascending) when largest_first.  Returns per step (reward, cash,
+    holdings, done)."""
     K = len(close[0])
     cash, h, t, done = init_cash, [0] * K, 0, False
     out = []
@@ -42,7 +44,8 @@ def ref_stock_env(close, bps, start, W, init_cash, fee_bps, orders):
                 n = min(-q[k], h[k])
                 h[k] -= n
                 cash += n * p[k] - _fee(n * p[k], fee_bps)
-        for k in range(K):
+        buy_seq = sorted(range(K), key=lambda k: (-q[k], k)) if largest_first else range(K)
+        for k in buy_seq:
             if q[k] > 0:
                 n = 0
                 while n < q[k] and (n + 1) * p[k] + _fee((n + 1) * p[k], fee_bps) <= cash:
@@ -81,8 +84,9 @@ def ref_crypto_env(mid, spread, start, W, init_cash, pmax, acts):
 
 # --------------------------------------------------------------- brute force
 
+@pytest.mark.parametrize("buy_order", [0, 1])
 @pytest.mark.parametrize("W,fee_bps,init_cash", [(4, 250, 1500), (3, 10, 2100), (4, 0, 999)])
-def test_stock_all_action_sequences_tiny(W, fee_bps, init_cash):
+def test_stock_all_action_sequences_tiny(W, fee_bps, init_cash, buy_order):
     close = np.array([[310, 655], [290, 700], [333, 640], [301, 689]], np.int64)
     ind = np.zeros((4, 1, 2), np.float32)
     mk = SimpleNamespace(close=close, ind=ind)
@@ -95,14 +99,48 @@ def test_stock_all_action_sequences_tiny(W, fee_bps, init_cash):
     o = oracle.stock_run(mk, np.full(N, 2), np.zeros(N), np.full(N, W),
                          np.tile(np.array(bps_row, np.int16), (N, 1)),
                          init_cash=init_cash, hmax=2, fee_bps=fee_bps, T=T,
-                         act_i32=acts)
+                         act_i32=acts, buy_order=buy_order)
     for e, seq in enumerate(seqs):
-        ref = ref_stock_env(close.tolist(), bps_row, 0, W, init_cash, fee_bps, seq)
+        ref = ref_stock_env(close.tolist(), bps_row, 0, W, init_cash, fee_bps, seq,
+                            largest_first=buy_order == 1)
         for t, (r, c, h, dn) in enumerate(ref):
             assert o["rew"][t, e] == r, (seq, t)
             assert o["cash"][t, e] == c, (seq, t)
             assert o["hold"][t, e].tolist() == h, (seq, t)
             assert o["done"][t, e] == dn, (seq, t)
+
+
+def test_stock_largest_first_three_assets_all_sequences():
+    """Largest-first buys with ties: three assets, orders -1..2 each, two
+    steps, cash for only part of the orders."""
+    close = np.array([[400, 390, 410], [405, 385, 420], [398, 400, 401]], np.int64)
+    ind = np.zeros((3, 1, 3), np.float32)
+    mk = SimpleNamespace(close=close, ind=ind)
+    per_step = list(itertools.product(range(-1, 3), repeat=3))
+    seqs = list(itertools.product(per_step, repeat=2))
+    N, T, W, cash0, fee = len(seqs), 2, 3, 1700, 30
+    acts = np.array(seqs, np.int32).transpose(1, 0, 2).copy()
+    bps_row = [0, 55, -100]
+    o = oracle.stock_run(mk, np.full(N, 3), np.zeros(N), np.full(N, W),
+                         np.tile(np.array(bps_row, np.int16), (N, 1)),
+                         init_cash=cash0, hmax=2, fee_bps=fee, T=T, act_i32=acts,
+                         buy_order=1, want=("rew", "cash", "hold", "done"))
+    differs = 0
+    for e, seq in enumerate(seqs):
+        ref = ref_stock_env(close.tolist(), bps_row, 0, W, cash0, fee, seq, largest_first=True)
+        asc = ref_stock_env(close.tolist(), bps_row, 0, W, cash0, fee, seq)
+        differs += ref != asc
+        for t, (r, c, h, dn) in enumerate(ref):
+            assert (o["rew"][t, e], o["cash"][t, e], o["hold"][t, e].tolist(), o["done"][t, e]) == (r, c, h, dn), (seq, t)
+    assert differs > 100            # the case exercises the order
+
+
+def test_stock_buy_order_rejects_unknown():
+    close = np.array([[400], [405]], np.int64)
+    mk = SimpleNamespace(close=close, ind=np.zeros((2, 1, 1), np.float32))
+    with pytest.raises(ValueError):
+        oracle.stock_run(mk, [1], [0], [2], np.zeros((1, 1), np.int16), init_cash=1000, hmax=1,
+                         fee_bps=0, T=1, act_i32=np.ones((1, 1, 1), np.int32), buy_order=2)
 
 
 def test_crypto_all_action_sequences_tiny():

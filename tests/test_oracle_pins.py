@@ -63,6 +63,36 @@ def test_buy_max_equals_linear_search():
         assert g == n, (c, p, f, g, n)
 
 
+def test_buy_order_hand_example():
+    # two buy orders at 1,000 cents a share, no fee, cash for three shares:
+    # ascending order fills asset 0 (1 share) then 2 of asset 1's 4; largest
+    # first fills asset 1 (3 of 4) and leaves asset 0 without cash
+    from types import SimpleNamespace
+    mk = SimpleNamespace(close=np.array([[1000, 1000], [1000, 1000]], np.int64),
+                         ind=np.zeros((2, 1, 2), np.float32))
+    q = np.array([[[1, 4]]], np.int32)
+    runs = [oracle.stock_run(mk, [2], [0], [2], np.zeros((1, 2), np.int16), init_cash=3000, hmax=4,
+                             fee_bps=0, T=1, act_i32=q, buy_order=b) for b in (0, 1)]
+    assert runs[0]["hold"][0, 0].tolist() == [1, 2] and runs[0]["cash"][0, 0] == 0
+    assert runs[1]["hold"][0, 0].tolist() == [0, 3] and runs[1]["cash"][0, 0] == 0
+    # equal counts keep the ascending asset order: cash for 2 of 2 x 2 orders
+    q = np.array([[[2, 2]]], np.int32)
+    r = oracle.stock_run(mk, [2], [0], [2], np.zeros((1, 2), np.int16), init_cash=2000, hmax=4,
+                         fee_bps=0, T=1, act_i32=q, buy_order=1)
+    assert r["hold"][0, 0].tolist() == [2, 0]
+
+
+def test_buy_order_is_irrelevant_when_every_order_fits():
+    # rich envs (cash far above any day's orders): both orders give the same run
+    mk = synth.stock_market(120, 30, 5)
+    envs = synth.stock_envs_uneven(64, 30, 120, k_lo=1, w_lo=2, w_hi=45, seed=5)
+    q = synth.prescribed_shares(30, 64, 30, 100, 5)
+    runs = [oracle.stock_run(mk, envs.Ke, envs.start, envs.W, envs.bps, init_cash=10 ** 12, hmax=100,
+                             fee_bps=10, T=30, act_i32=q, buy_order=b) for b in (0, 1)]
+    for k in ("rew", "cash", "hold", "done", "metrics"):
+        assert np.array_equal(runs[0][k], runs[1][k]), k
+
+
 # -------------------------------------------------------------- discretise
 
 def _trunc_exact(x: np.ndarray, hmax: int) -> np.ndarray:
