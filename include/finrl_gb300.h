@@ -151,8 +151,12 @@ typedef struct fr_env fr_env;
  *          Prices are the day's close scaled by (1e4 + bps[e][k]) / 1e4,
  *          rounded half up, floor 1 cent (Sec. 5.1 dataset diversity).
  *          Actions are share changes (Sec. 3.1): sells first, capped at the
- *          holding; then buys in ascending asset order, each filled as far as
- *          cash allows; fee ceil(notional * fee_bps / 1e4) per order.
+ *          holding; then buys in ascending asset order (buy_order
+ *          FR_BUY_ASCENDING) or largest requested count first, equal counts
+ *          in ascending asset order (FR_BUY_LARGEST_FIRST), each filled as
+ *          far as cash allows; fee ceil(notional * fee_bps / 1e4) per order.
+ *          The fused rollout kernels take ascending order only; rollouts of
+ *          largest-first envs run the unfused path.
  *  crypto: one asset; observation [cash*1e-8, pos/pmax, fac_0..7];
  *          action {0 sell, 1 hold, 2 buy} of one lot at bid = mid - s/2 or
  *          ask = bid + s; long-only, at most pmax lots; no fee.
@@ -171,7 +175,12 @@ typedef struct {
     int32_t fee_bps;          /* stock: 0..10000                            */
     int32_t pmax;             /* crypto: lots, >= 1                         */
     int32_t auto_reset;       /* 1: a finished env restarts at once         */
+    int32_t buy_order;        /* stock: FR_BUY_ASCENDING (0) or
+                                 FR_BUY_LARGEST_FIRST (1); crypto: 0        */
 } fr_env_desc;
+
+#define FR_BUY_ASCENDING 0
+#define FR_BUY_LARGEST_FIRST 1
 
 int env_create(fr_ctx *ctx, const fr_env_desc *desc, const fr_market *market,
                fr_env **out);

@@ -13,7 +13,8 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (ACT_F32_UNIT, ACT_I32_SHARES, ACT_U8_DISCRETE, COMBINE_MEAN, HEAD_DUELING, HEAD_Q,
+from ._lib import (ACT_F32_UNIT, ACT_I32_SHARES, ACT_U8_DISCRETE, BUY_ASCENDING, BUY_LARGEST_FIRST,
+                   COMBINE_MEAN, HEAD_DUELING, HEAD_Q,
                    COMBINE_VOTE, PATH_AUTO, PATH_UNFUSED, PREC_BF16, PREC_BF16X3, PREC_FP8,
                    PREC_FP32, TASK_CRYPTO, TASK_STOCK, FrError)
 
@@ -28,7 +29,7 @@ __all__ = [
     "env_perturb", "ensemble_set_act_scales", "ensemble_get_act_scales", "ensemble_calibrate_sync",
     "Replay", "replay_create", "replay_push", "replay_sample", "replay_size", "ensemble_q", "ensemble_q_targets",
     "HEAD_Q", "HEAD_DUELING", "env_autotune", "env_tune_clear", "env_tune_set",
-    "PATH_AUTO", "PATH_UNFUSED",
+    "PATH_AUTO", "PATH_UNFUSED", "BUY_ASCENDING", "BUY_LARGEST_FIRST",
     "ACT_I32_SHARES", "ACT_F32_UNIT", "ACT_U8_DISCRETE", "PREC_FP32", "PREC_BF16",
     "PREC_FP8", "PREC_BF16X3", "COMBINE_MEAN", "COMBINE_VOTE", "TASK_STOCK", "TASK_CRYPTO",
 ]
@@ -186,14 +187,18 @@ def env_perturb(env: Env, seed: int, bps_range: int = 100, stream=None):
 
 def env_create(ctx: Ctx, market: Market, *, start, window, n_assets=None, bps=None,
                init_cash: int = 100_000_000, hmax: int = 100, fee_bps: int = 10,
-               pmax: int = 10, auto_reset: bool = False) -> Env:
+               pmax: int = 10, auto_reset: bool = False, buy_order: int = 0) -> Env:
+    """buy_order (stock): BUY_ASCENDING fills a step's buys in ascending asset
+    order, BUY_LARGEST_FIRST largest requested count first (equal counts in
+    ascending asset order)."""
     start = np.ascontiguousarray(start, np.int32)
     window = np.ascontiguousarray(np.broadcast_to(window, start.shape), np.int32)
     na = None if n_assets is None else np.ascontiguousarray(np.broadcast_to(n_assets, start.shape), np.int32)
     b = None if bps is None else np.ascontiguousarray(bps, np.int16)
     d = _lib.EnvDesc(task=market.task, n_envs=start.size, n_assets=_hptr(na), window=_hptr(window),
                      start=_hptr(start), bps=_hptr(b), init_cash=int(init_cash), hmax=int(hmax),
-                     fee_bps=int(fee_bps), pmax=int(pmax), auto_reset=int(bool(auto_reset)))
+                     fee_bps=int(fee_bps), pmax=int(pmax), auto_reset=int(bool(auto_reset)),
+                     buy_order=int(buy_order))
     out = C.c_void_p()
     _lib.check(lib().env_create(ctx, C.byref(d), market, C.byref(out)), "env_create")
     env = Env(out.value, keep=(ctx, market))

@@ -20,6 +20,7 @@ PREC_FP32, PREC_BF16, PREC_FP8, PREC_BF16X3 = 0, 1, 2, 3
 COMBINE_MEAN, COMBINE_VOTE = 0, 1
 HEAD_Q, HEAD_DUELING = 0, 1
 PATH_AUTO, PATH_UNFUSED = 0, 1
+BUY_ASCENDING, BUY_LARGEST_FIRST = 0, 1
 
 i32, i64, u32, u64, f64 = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_double
 vp, cp = C.c_void_p, C.c_char_p
@@ -40,7 +41,7 @@ class TuneReport(C.Structure):
 class EnvDesc(C.Structure):
     _fields_ = [("task", i32), ("n_envs", i32), ("n_assets", vp), ("window", vp),
                 ("start", vp), ("bps", vp), ("init_cash", i64), ("hmax", i32),
-                ("fee_bps", i32), ("pmax", i32), ("auto_reset", i32)]
+                ("fee_bps", i32), ("pmax", i32), ("auto_reset", i32), ("buy_order", i32)]
 
 
 class Action(C.Structure):

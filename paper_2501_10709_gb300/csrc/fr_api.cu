@@ -386,6 +386,8 @@ int env_create(fr_ctx *ctx, const fr_env_desc *d, const fr_market *m, fr_env **o
     } else {
         FR_CHECK(d->pmax >= 1, FR_EINVAL, "env_create: pmax < 1");
     }
+    FR_CHECK(d->buy_order == FR_BUY_ASCENDING || (stock && d->buy_order == FR_BUY_LARGEST_FIRST), FR_EINVAL,
+             "env_create: buy_order %d not valid for this task", d->buy_order);
     const int64_t horizon = stock ? m->n_days : m->S;
     std::vector<int32_t> Ke(N, stock ? m->K : 1);
     for (int e = 0; e < N; ++e) {
@@ -420,6 +422,7 @@ int env_create(fr_ctx *ctx, const fr_env_desc *d, const fr_market *m, fr_env **o
     v.fee_bps = d->fee_bps;
     v.pmax = d->pmax;
     v.auto_reset = d->auto_reset ? 1 : 0;
+    v.buy_order = d->buy_order;
     v.init_cash = d->init_cash;
     v.ann = stock ? 252.0 : 1.0;
     v.n_days = m->n_days;

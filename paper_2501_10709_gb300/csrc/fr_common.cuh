@@ -41,6 +41,7 @@ constexpr int BPS_ONE = 10000;  // basis points per unit
 struct EnvView {
     int task, N, K, I, D;
     int hmax, fee_bps, pmax, auto_reset;
+    int buy_order;              // FR_BUY_ASCENDING / FR_BUY_LARGEST_FIRST (stock)
     int64_t init_cash;
     double ann;                 // Sharpe annualisation factor A
     // market

@@ -39,11 +39,14 @@ __global__ void k_env_reset(EnvView v)
 // the assets that cannot afford one share, fill every order in full up to the
 // first whose prefix cost exceeds the cash, fill that one as far as the cash
 // allows and continue after it), the value at the next day's prices and the
-// next observation from registers.  The FP64 episode bookkeeping is deferred:
+// next observation from registers.  BYSIZE: the buys execute largest
+// requested count first (equal counts in ascending asset order): when not
+// every order fits, the orders are moved to the lanes of their execution
+// positions, filled by the same rounds, and the fills moved back.  The FP64 episode bookkeeping is deferred:
 // the last warp of the block to finish runs it for all 32 envs of the block,
 // one thread per env, so that one instruction of the narrow FP64 pipe serves
 // 32 envs and no warp waits at a block barrier.
-template <int KIND>
+template <int KIND, bool BYSIZE>
 __global__ void __launch_bounds__(kStepEnvs * 32, 2) k_stock_step(EnvView v, const void *act, int64_t *rew,
                                                                 float *rew_f32, uint8_t *done_out,
                                                                 float *obs, int ld)
@@ -108,31 +111,55 @@ __global__ void __launch_bounds__(kStepEnvs * 32, 2) k_stock_step(EnvView v, con
                 cash -= all;
                 pending = 0u;
             }
+            int rank = lane;                     // execution position of this lane's order
+            int64_t bw = want, bf = full, bo = one, bp = p;
+            if (BYSIZE && pending) {
+                // rank: orders with a larger count, or an equal count at a
+                // lower asset index, go first (a permutation of 0..31: the
+                // lanes without a buy follow in lane order)
+                rank = 0;
+#pragma unroll 1
+                for (int j = 0; j < 32; ++j) {
+                    const int64_t wj = __shfl_sync(FULL_MASK, want, j);
+                    rank += (wj > want || (wj == want && j < lane)) ? 1 : 0;
+                }
+                int src = 0;                     // the lane whose order executes at position `lane`
+#pragma unroll 1
+                for (int j = 0; j < 32; ++j)
+                    if (__shfl_sync(FULL_MASK, rank, j) == lane) src = j;
+                bw = __shfl_sync(FULL_MASK, want, src);
+                bf = __shfl_sync(FULL_MASK, full, src);
+                bo = __shfl_sync(FULL_MASK, one, src);
+                bp = __shfl_sync(FULL_MASK, p, src);
+                pending = __ballot_sync(FULL_MASK, bw > 0);
+            }
+            int64_t bn = nb;                     // fill at this lane's position
 #pragma unroll 1
             while (pending) {
                 bool mine = (pending >> lane) & 1u;
-                pending &= ~__ballot_sync(FULL_MASK, mine && one > cash);
+                pending &= ~__ballot_sync(FULL_MASK, mine && bo > cash);
                 if (!pending) break;
                 mine = (pending >> lane) & 1u;
-                const int64_t x = mine ? full : 0;
+                const int64_t x = mine ? bf : 0;
                 const int64_t pre = warp_incl_scan(x, lane);
                 const unsigned fail = __ballot_sync(FULL_MASK, mine && pre > cash);
                 if (fail == 0u) {
-                    if (mine) nb = want;
+                    if (mine) bn = bw;
                     cash -= __shfl_sync(FULL_MASK, pre, 31);
                     break;
                 }
                 const int f = __ffs(fail) - 1;
-                if (mine && lane < f) nb = want;
+                if (mine && lane < f) bn = bw;
                 int64_t cf = cash - (pre - x);
                 if (lane == f) {
-                    const int64_t n = afford(cf, p, fee);
-                    nb = n;
-                    cf -= cost_of(n, p, fee);
+                    const int64_t n = afford(cf, bp, fee);
+                    bn = n;
+                    cf -= cost_of(n, bp, fee);
                 }
                 cash = __shfl_sync(FULL_MASK, cf, f);
                 pending &= ~((2u << f) - 1u);
             }
+            nb = BYSIZE ? __shfl_sync(FULL_MASK, bn, rank) : bn;
             h += nb;
             const int t1 = t0 + 1;
             const int64_t p1 = live ? perturb(c1, bps) : 0;
@@ -297,10 +324,18 @@ cudaError_t launch_env_step(const EnvView &v, int kind, const void *act, int64_t
 {
     if (v.task == FR_TASK_STOCK) {
         const unsigned grid = ceil_div(v.N, kStepEnvs);
-        if (kind == FR_ACT_I32_SHARES)
-            k_stock_step<FR_ACT_I32_SHARES><<<grid, kStepEnvs * 32, 0, s>>>(v, act, rew, rew_f32, done, obs, ld);
-        else
-            k_stock_step<FR_ACT_F32_UNIT><<<grid, kStepEnvs * 32, 0, s>>>(v, act, rew, rew_f32, done, obs, ld);
+        const bool by_size = v.buy_order == FR_BUY_LARGEST_FIRST;
+        if (kind == FR_ACT_I32_SHARES) {
+            if (by_size)
+                k_stock_step<FR_ACT_I32_SHARES, true><<<grid, kStepEnvs * 32, 0, s>>>(v, act, rew, rew_f32, done, obs, ld);
+            else
+                k_stock_step<FR_ACT_I32_SHARES, false><<<grid, kStepEnvs * 32, 0, s>>>(v, act, rew, rew_f32, done, obs, ld);
+        } else {
+            if (by_size)
+                k_stock_step<FR_ACT_F32_UNIT, true><<<grid, kStepEnvs * 32, 0, s>>>(v, act, rew, rew_f32, done, obs, ld);
+            else
+                k_stock_step<FR_ACT_F32_UNIT, false><<<grid, kStepEnvs * 32, 0, s>>>(v, act, rew, rew_f32, done, obs, ld);
+        }
     } else {
         k_crypto_step<<<ceil_div(v.N, kBlock), kBlock, 0, s>>>(v, (const uint8_t *)act, rew, rew_f32,
                                                                done, obs, ld);

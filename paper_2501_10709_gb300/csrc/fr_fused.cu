@@ -946,7 +946,7 @@ bool tc_rollout_supported(const fr_env *env, const fr_ensemble *e)
     const TcPlan &p = e->tc->plan;
     if (v.task == FR_TASK_STOCK) {
         if (v.K != SK || v.I != SI || e->combine != FR_COMBINE_MEAN || e->dims[0] != SD ||
-            e->dims[e->L] != SK || e->out_act != 1)
+            e->dims[e->L] != SK || e->out_act != 1 || v.buy_order != FR_BUY_ASCENDING)
             return false;
     } else {
         if (e->combine != FR_COMBINE_VOTE || e->dims[0] != FR_CRYPTO_OBS_DIM || e->dims[e->L] != 3 ||

@@ -852,7 +852,7 @@ bool f2_supported(const fr_env *env, const fr_ensemble *e)
 {
     const EnvView &v = env->v;
     if (v.task != FR_TASK_STOCK || v.K != SK2 || v.I != SI2 || e->combine != FR_COMBINE_MEAN ||
-        e->out_act != 1 || e->precision != FR_PREC_BF16)
+        e->out_act != 1 || e->precision != FR_PREC_BF16 || v.buy_order != FR_BUY_ASCENDING)
         return false;
     F2Plan p;
     if (!f2_plan(e, p)) return false;
