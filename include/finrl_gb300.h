@@ -607,7 +607,12 @@ typedef struct {
 } fr_server_desc;
 
 /* Create / destroy.  Destroy stops the worker after its current chunk;
- * requests not yet complete are dropped (their tickets become unknown). */
+ * requests not yet complete are dropped (their tickets become unknown).
+ * A rollout chunk that fails with a CUDA error fails every request and every
+ * later submit (the context may be unusable); one that fails otherwise (e.g.
+ * FR_ENOMEM when the HBM budget cannot cover the rollout's scratch) fails
+ * the requests of that chunk with that status, frees their slots, and the
+ * server goes on with the queued requests. */
 int fr_server_create(fr_ctx *ctx, const fr_server_desc *desc, fr_server **out);
 void fr_server_destroy(fr_server *srv);
 
@@ -655,9 +660,27 @@ typedef struct {
     double env_steps;         /* slot-steps of requests run (their windows) */
     double pool_steps;        /* capacity x steps launched                  */
     double busy_s;            /* wall time of the worker's GPU rounds       */
+    uint64_t failed;          /* requests finished with an error status     */
 } fr_server_stats;
 
 int fr_server_stats_get(fr_server *srv, fr_server_stats *out);
+
+/* ------------------------------------------------- host fault injection
+ * For tests of the error paths, process-wide, on the host only: no GPU work
+ * is faulted, each injected failure returns the error code the real failure
+ * would.  Of the next events of `kind`, the first `skip` proceed and the
+ * `count` after them fail; count 0 disarms the kind.
+ *  FR_FAULT_ALLOC   a device allocation charged to a context fails: the call
+ *                   that needed it returns FR_ENOMEM
+ *  FR_FAULT_SUBMIT  backtest_submit rejects the request: FR_EBUSY, nothing
+ *                   is queued
+ *  FR_FAULT_POLL    backtest_poll drops its answer: FR_ENOTREADY, *done = 0;
+ *                   a finished result stays for the next poll
+ * FR_EINVAL for an unknown kind or a negative skip / count. */
+#define FR_FAULT_ALLOC 1
+#define FR_FAULT_SUBMIT 2
+#define FR_FAULT_POLL 3
+int fr_fault_inject(int32_t kind, int32_t skip, int32_t count);
 
 #ifdef __cplusplus
 }

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import (ACT_F32_UNIT, ACT_I32_SHARES, ACT_U8_DISCRETE, BUY_ASCENDING, BUY_LARGEST_FIRST,
-                   COMBINE_MEAN, HEAD_DUELING, HEAD_Q,
+                   COMBINE_MEAN, FAULT_ALLOC, FAULT_POLL, FAULT_SUBMIT, HEAD_DUELING, HEAD_Q,
                    COMBINE_VOTE, PATH_AUTO, PATH_UNFUSED, PREC_BF16, PREC_BF16X3, PREC_FP8,
                    PREC_FP32, TASK_CRYPTO, TASK_STOCK, FrError)
 
@@ -30,6 +30,7 @@ __all__ = [
     "Replay", "replay_create", "replay_push", "replay_sample", "replay_size", "ensemble_q", "ensemble_q_targets",
     "HEAD_Q", "HEAD_DUELING", "env_autotune", "env_tune_clear", "env_tune_set",
     "PATH_AUTO", "PATH_UNFUSED", "BUY_ASCENDING", "BUY_LARGEST_FIRST",
+    "fr_fault_inject", "FAULT_ALLOC", "FAULT_SUBMIT", "FAULT_POLL",
     "ACT_I32_SHARES", "ACT_F32_UNIT", "ACT_U8_DISCRETE", "PREC_FP32", "PREC_BF16",
     "PREC_FP8", "PREC_BF16X3", "COMBINE_MEAN", "COMBINE_VOTE", "TASK_STOCK", "TASK_CRYPTO",
 ]
@@ -555,6 +556,14 @@ def fr_server_stats(srv: Server) -> dict:
     st = _lib.ServerStats()
     _lib.check(lib().fr_server_stats_get(srv, C.byref(st)), "fr_server_stats_get")
     return {k: getattr(st, k) for k, _ in st._fields_}
+
+
+def fr_fault_inject(kind: int, skip: int = 0, count: int = 1):
+    """Host fault injection for tests: of the next events of `kind`
+    (FAULT_ALLOC, FAULT_SUBMIT, FAULT_POLL) the first `skip` proceed and the
+    `count` after them fail with the error the real failure returns;
+    count 0 disarms the kind."""
+    _lib.check(lib().fr_fault_inject(int(kind), int(skip), int(count)), "fr_fault_inject")
 
 
 # ------------------------------------------------------ ensemble weighting

@@ -21,6 +21,7 @@ COMBINE_MEAN, COMBINE_VOTE = 0, 1
 HEAD_Q, HEAD_DUELING = 0, 1
 PATH_AUTO, PATH_UNFUSED = 0, 1
 BUY_ASCENDING, BUY_LARGEST_FIRST = 0, 1
+FAULT_ALLOC, FAULT_SUBMIT, FAULT_POLL = 1, 2, 3
 
 i32, i64, u32, u64, f64 = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_double
 vp, cp = C.c_void_p, C.c_char_p
@@ -86,7 +87,7 @@ class Result(C.Structure):
 
 class ServerStats(C.Structure):
     _fields_ = [("submitted", u64), ("completed", u64), ("queued", u64), ("running", u64),
-                ("env_steps", f64), ("pool_steps", f64), ("busy_s", f64)]
+                ("env_steps", f64), ("pool_steps", f64), ("busy_s", f64), ("failed", u64)]
 
 
 # name -> (restype, argtypes); every symbol the header declares
@@ -131,6 +132,7 @@ SIGNATURES = {
     "backtest_submit": (i32, [vp, vp, vp]),
     "backtest_poll": (i32, [vp, u64, vp, vp]),
     "fr_server_stats_get": (i32, [vp, vp]),
+    "fr_fault_inject": (i32, [i32, i32, i32]),
     "fr_market_copy_indicators": (i32, [vp, vp]),
     "market_indicators": (i32, [vp, vp, vp, i32, i32, vp, vp]),
     "env_perturb": (i32, [vp, u64, i32, vp]),

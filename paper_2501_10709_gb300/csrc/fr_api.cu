@@ -56,10 +56,33 @@ void ctx_release(fr_ctx *ctx, uint64_t bytes)
     ctx->used = ctx->used >= bytes ? ctx->used - bytes : 0;
 }
 
+// Host fault injection: per kind, events to let through, then events to fail.
+static std::mutex g_fault_mu;
+static std::atomic<int> g_fault_armed{0};
+static int32_t g_fault_skip[4], g_fault_count[4];
+
+bool fault_hit(int kind)
+{
+    if (g_fault_armed.load(std::memory_order_relaxed) == 0) return false;
+    std::lock_guard<std::mutex> lk(g_fault_mu);
+    if (kind < 1 || kind > 3 || g_fault_count[kind] <= 0) return false;
+    if (g_fault_skip[kind] > 0) {
+        --g_fault_skip[kind];
+        return false;
+    }
+    if (--g_fault_count[kind] == 0 && g_fault_count[1] + g_fault_count[2] + g_fault_count[3] == 0)
+        g_fault_armed.store(0, std::memory_order_relaxed);
+    return true;
+}
+
 int dev_alloc(fr_ctx *ctx, void **p, uint64_t bytes)
 {
     *p = nullptr;
     if (bytes == 0) return FR_OK;
+    if (fault_hit(FR_FAULT_ALLOC)) {
+        set_error("device allocation of %llu bytes failed (injected fault)", (unsigned long long)bytes);
+        return FR_ENOMEM;
+    }
     int rc = ctx_reserve(ctx, bytes);
     if (rc) return rc;
     cudaError_t e = cudaMalloc(p, bytes);
@@ -198,9 +221,22 @@ const char *fr_last_error(void) { return g_err; }
 
 const char *fr_version(void) { return "finrl_gb300 0.1 (sm_103a)"; }
 
+int fr_fault_inject(int32_t kind, int32_t skip, int32_t count)
+{
+    FR_CHECK(kind >= FR_FAULT_ALLOC && kind <= FR_FAULT_POLL && skip >= 0 && count >= 0, FR_EINVAL,
+             "fr_fault_inject: kind %d, skip %d, count %d", kind, skip, count);
+    std::lock_guard<std::mutex> lk(g_fault_mu);
+    g_fault_skip[kind] = skip;
+    g_fault_count[kind] = count;
+    g_fault_armed.store(g_fault_count[1] + g_fault_count[2] + g_fault_count[3] > 0 ? 1 : 0,
+                        std::memory_order_relaxed);
+    return FR_OK;
+}
+
 // ---------------------------------------------------------------- context
 int fr_ctx_create(int device, uint64_t hbm_budget_bytes, fr_ctx **out)
 {
+    FR_NVTX("fr_ctx_create");
     FR_CHECK(out, FR_EINVAL, "fr_ctx_create: out is NULL");
     *out = nullptr;
     int n = 0;
@@ -232,6 +268,7 @@ int fr_ctx_sm_count(const fr_ctx *ctx) { return ctx ? ctx->sm_count : 0; }
 // ----------------------------------------------------------------- market
 int fr_market_create(fr_ctx *ctx, const fr_market_desc *d, fr_market **out)
 {
+    FR_NVTX("fr_market_create");
     FR_CHECK(ctx && d && out, FR_EINVAL, "fr_market_create: NULL argument");
     *out = nullptr;
     int rc = use_device(ctx);
@@ -340,6 +377,7 @@ int fr_market_create(fr_ctx *ctx, const fr_market_desc *d, fr_market **out)
 
 int fr_market_copy_indicators(const fr_market *m, float *dst)
 {
+    FR_NVTX("fr_market_copy_indicators");
     FR_CHECK(m && dst, FR_EINVAL, "fr_market_copy_indicators: NULL argument");
     FR_CHECK(m->task == FR_TASK_STOCK, FR_EINVAL, "fr_market_copy_indicators: stock markets only");
     int rc = use_device(m->ctx);
@@ -351,6 +389,7 @@ int fr_market_copy_indicators(const fr_market *m, float *dst)
 
 void fr_market_destroy(fr_market *m)
 {
+    FR_NVTX("fr_market_destroy");
     if (!m) return;
     cudaSetDevice(m->ctx->device);
     if (m->task == FR_TASK_STOCK) {
@@ -369,6 +408,7 @@ void fr_market_destroy(fr_market *m)
 
 int env_create(fr_ctx *ctx, const fr_env_desc *d, const fr_market *m, fr_env **out)
 {
+    FR_NVTX("env_create");
     FR_CHECK(ctx && d && m && out, FR_EINVAL, "env_create: NULL argument");
     *out = nullptr;
     FR_CHECK(d->task == m->task, FR_EINVAL, "env_create: env task %d on a market of task %d",
@@ -463,6 +503,7 @@ int env_create(fr_ctx *ctx, const fr_env_desc *d, const fr_market *m, fr_env **o
 
 void env_destroy(fr_env *env)
 {
+    FR_NVTX("env_destroy");
     if (!env) return;
     cudaSetDevice(env->ctx->device);
     dev_free(env->ctx, env->block, env->bytes);
@@ -479,6 +520,7 @@ void env_destroy(fr_env *env)
 
 int env_dims(const fr_env *env, int32_t *n_envs, int32_t *obs_dim, int32_t *n_assets)
 {
+    FR_NVTX("env_dims");
     FR_CHECK(env, FR_EINVAL, "env_dims: NULL env");
     if (n_envs) *n_envs = env->v.N;
     if (obs_dim) *obs_dim = env->v.D;
@@ -488,6 +530,7 @@ int env_dims(const fr_env *env, int32_t *n_envs, int32_t *obs_dim, int32_t *n_as
 
 int env_reset(fr_env *env, void *stream)
 {
+    FR_NVTX("env_reset");
     FR_CHECK(env, FR_EINVAL, "env_reset: NULL env");
     int rc = use_device(env->ctx);
     if (rc) return rc;
@@ -497,6 +540,7 @@ int env_reset(fr_env *env, void *stream)
 
 int env_step(fr_env *env, const fr_action *a, const fr_step_out *o, void *stream)
 {
+    FR_NVTX("env_step");
     FR_CHECK(env && a && a->data, FR_EINVAL, "env_step: NULL env or action");
     const bool stock = env->v.task == FR_TASK_STOCK;
     FR_CHECK(stock ? (a->kind == FR_ACT_I32_SHARES || a->kind == FR_ACT_F32_UNIT)
@@ -513,6 +557,7 @@ int env_step(fr_env *env, const fr_action *a, const fr_step_out *o, void *stream
 
 int env_observe(fr_env *env, float *obs, int32_t ld, void *stream)
 {
+    FR_NVTX("env_observe");
     FR_CHECK(env && obs && ld >= env->v.D, FR_EINVAL, "env_observe: need obs and ld >= D");
     int rc = use_device(env->ctx);
     if (rc) return rc;
@@ -523,6 +568,7 @@ int env_observe(fr_env *env, float *obs, int32_t ld, void *stream)
 int env_get_state(fr_env *env, int64_t *cash, int32_t *hold, int32_t *steps, uint8_t *done,
                   void *stream)
 {
+    FR_NVTX("env_get_state");
     FR_CHECK(env, FR_EINVAL, "env_get_state: NULL env");
     int rc = use_device(env->ctx);
     if (rc) return rc;
@@ -532,6 +578,7 @@ int env_get_state(fr_env *env, int64_t *cash, int32_t *hold, int32_t *steps, uin
 
 int env_metrics(fr_env *env, double *metrics, void *stream)
 {
+    FR_NVTX("env_metrics");
     FR_CHECK(env && metrics, FR_EINVAL, "env_metrics: NULL argument");
     int rc = use_device(env->ctx);
     if (rc) return rc;
@@ -542,6 +589,7 @@ int env_metrics(fr_env *env, double *metrics, void *stream)
 
 int env_snapshot(fr_env *env, void *host_buf, size_t cap, size_t *len)
 {
+    FR_NVTX("env_snapshot");
     FR_CHECK(env && len, FR_EINVAL, "env_snapshot: NULL argument");
     const uint64_t off = (uint64_t)((char *)env->v.cash - (char *)env->block);
     const uint64_t sb = env->bytes - off;
@@ -559,6 +607,7 @@ int env_snapshot(fr_env *env, void *host_buf, size_t cap, size_t *len)
 
 int env_restore(fr_env *env, const void *host_buf, size_t len)
 {
+    FR_NVTX("env_restore");
     FR_CHECK(env && host_buf && len >= sizeof(SnapHeader), FR_EINVAL, "env_restore: bad buffer");
     SnapHeader h;
     memcpy(&h, host_buf, sizeof(h));
@@ -577,6 +626,7 @@ int env_restore(fr_env *env, const void *host_buf, size_t len)
 
 int env_set_rollout_path(fr_env *env, int32_t path)
 {
+    FR_NVTX("env_set_rollout_path");
     FR_CHECK(env && (path == FR_PATH_AUTO || path == FR_PATH_UNFUSED), FR_EINVAL,
              "env_set_rollout_path: bad argument");
     env->path = path;
@@ -585,6 +635,7 @@ int env_set_rollout_path(fr_env *env, int32_t path)
 
 int env_set_exploration(fr_env *env, const fr_explore *x)
 {
+    FR_NVTX("env_set_exploration");
     FR_CHECK(env, FR_EINVAL, "env_set_exploration: NULL env");
     if (!x || x->kind == FR_EXPLORE_NONE) {
         env->explore_kind = FR_EXPLORE_NONE;
@@ -605,6 +656,7 @@ int env_set_exploration(fr_env *env, const fr_explore *x)
 
 int env_set_tile_packing(fr_env *env, int32_t on)
 {
+    FR_NVTX("env_set_tile_packing");
     FR_CHECK(env, FR_EINVAL, "env_set_tile_packing: NULL env");
     env->pack_off = on ? 0 : 1;
     return FR_OK;
@@ -612,6 +664,7 @@ int env_set_tile_packing(fr_env *env, int32_t on)
 
 int env_tile_packing_efficiency(const fr_env *env, float *eff)
 {
+    FR_NVTX("env_tile_packing_efficiency");
     FR_CHECK(env && eff, FR_EINVAL, "env_tile_packing_efficiency: NULL argument");
     *eff = env->pack_state == 2 && !env->pack_off ? env->pack_efficiency : 1.0f;
     return FR_OK;
@@ -619,6 +672,7 @@ int env_tile_packing_efficiency(const fr_env *env, float *eff)
 
 int env_set_kernel_timing(fr_env *env, int32_t on)
 {
+    FR_NVTX("env_set_kernel_timing");
     FR_CHECK(env, FR_EINVAL, "env_set_kernel_timing: NULL env");
     int rc = use_device(env->ctx);
     if (rc) return rc;
@@ -631,6 +685,7 @@ int env_set_kernel_timing(fr_env *env, int32_t on)
 
 int env_last_kernel_ms(fr_env *env, float *ms)
 {
+    FR_NVTX("env_last_kernel_ms");
     FR_CHECK(env && ms, FR_EINVAL, "env_last_kernel_ms: NULL argument");
     FR_CHECK(env->k_recorded, FR_EINVAL, "env_last_kernel_ms: no kernel timed since timing was switched on");
     int rc = use_device(env->ctx);
@@ -668,6 +723,7 @@ cudaError_t env_time_mark(fr_env *env, int which, cudaStream_t s)
 
 int env_error_count(fr_env *env, uint64_t *count)
 {
+    FR_NVTX("env_error_count");
     FR_CHECK(env && count, FR_EINVAL, "env_error_count: NULL argument");
     int rc = use_device(env->ctx);
     if (rc) return rc;
@@ -680,6 +736,7 @@ int env_error_count(fr_env *env, uint64_t *count)
 // --------------------------------------------------------------- ensemble
 int ensemble_create(fr_ctx *ctx, const fr_ensemble_desc *d, fr_ensemble **out)
 {
+    FR_NVTX("ensemble_create");
     FR_CHECK(ctx && d && out && d->dims && d->params, FR_EINVAL, "ensemble_create: NULL argument");
     *out = nullptr;
     FR_CHECK(d->n_agents >= 1 && d->n_agents <= MAX_AGENTS, FR_EINVAL,
@@ -761,6 +818,7 @@ int ensemble_create(fr_ctx *ctx, const fr_ensemble_desc *d, fr_ensemble **out)
 
 void ensemble_destroy(fr_ensemble *e)
 {
+    FR_NVTX("ensemble_destroy");
     if (!e) return;
     cudaSetDevice(e->ctx->device);
     f2_release(e);
@@ -773,6 +831,7 @@ void ensemble_destroy(fr_ensemble *e)
 
 int ensemble_set_act_scales(fr_ensemble *e, const float *scales)
 {
+    FR_NVTX("ensemble_set_act_scales");
     FR_CHECK(e && scales, FR_EINVAL, "ensemble_set_act_scales: NULL argument");
     int rc = use_device(e->ctx);
     if (rc) return rc;
@@ -781,12 +840,14 @@ int ensemble_set_act_scales(fr_ensemble *e, const float *scales)
 
 int ensemble_get_act_scales(const fr_ensemble *e, float *scales)
 {
+    FR_NVTX("ensemble_get_act_scales");
     FR_CHECK(e && scales, FR_EINVAL, "ensemble_get_act_scales: NULL argument");
     return tc_get_act_scales(e, scales);
 }
 
 int ensemble_calibrate_sync(fr_ensemble *e, const float *obs, int32_t n, void *stream)
 {
+    FR_NVTX("ensemble_calibrate_sync");
     FR_CHECK(e && obs && n >= 1, FR_EINVAL, "ensemble_calibrate_sync: NULL argument or n < 1");
     FR_CHECK(e->precision == FR_PREC_FP8 && e->tc, FR_EINVAL, "ensemble_calibrate_sync: FP8 ensembles only");
     int rc = use_device(e->ctx);
@@ -840,6 +901,7 @@ int ensemble_calibrate_sync(fr_ensemble *e, const float *obs, int32_t n, void *s
 
 int ensemble_q(const fr_ensemble *e, const float *obs, int32_t n, float *q, void *stream)
 {
+    FR_NVTX("ensemble_q");
     FR_CHECK(e && n >= 0, FR_EINVAL, "ensemble_q: bad argument");
     FR_CHECK(e->combine == FR_COMBINE_VOTE, FR_EINVAL, "ensemble_q: VOTE (Q-network) ensembles only");
     if (n == 0) return FR_OK;
@@ -862,6 +924,7 @@ int ensemble_q(const fr_ensemble *e, const float *obs, int32_t n, float *q, void
 int ensemble_q_targets(const fr_ensemble *on, const fr_ensemble *tg, const float *next_obs, const float *rew,
                        const uint8_t *done, int32_t n, float gamma, int32_t double_q, float *y, void *stream)
 {
+    FR_NVTX("ensemble_q_targets");
     FR_CHECK(on && tg && n >= 0, FR_EINVAL, "ensemble_q_targets: bad argument");
     FR_CHECK(on->combine == FR_COMBINE_VOTE && tg->combine == FR_COMBINE_VOTE, FR_EINVAL,
              "ensemble_q_targets: VOTE (Q-network) ensembles only");
@@ -893,6 +956,7 @@ int ensemble_q_targets(const fr_ensemble *on, const fr_ensemble *tg, const float
 
 int ensemble_forward(const fr_ensemble *e, const float *obs, int32_t n, float *y, void *stream)
 {
+    FR_NVTX("ensemble_forward");
     FR_CHECK(e && n >= 0, FR_EINVAL, "ensemble_forward: bad argument");
     if (n == 0) return FR_OK;
     FR_CHECK(obs && y, FR_EINVAL, "ensemble_forward: NULL obs or y");
@@ -903,6 +967,7 @@ int ensemble_forward(const fr_ensemble *e, const float *obs, int32_t n, float *y
 
 int ensemble_act(const fr_ensemble *e, const float *obs, int32_t n, void *act, void *stream)
 {
+    FR_NVTX("ensemble_act");
     FR_CHECK(e && n >= 0, FR_EINVAL, "ensemble_act: bad argument");
     if (n == 0) return FR_OK;
     FR_CHECK(obs && act, FR_EINVAL, "ensemble_act: NULL obs or act");
@@ -934,6 +999,7 @@ static int plain_rollout(fr_env *env, const fr_ensemble *e, int32_t T, const fr_
 int rollout(fr_env *env, const fr_ensemble *e, int32_t T, const fr_traj *traj, double *metrics,
             void *stream)
 {
+    FR_NVTX("rollout");
     FR_CHECK(env && e && T >= 0, FR_EINVAL, "rollout: bad argument");
     const EnvView &v = env->v;
     const bool stock = v.task == FR_TASK_STOCK;

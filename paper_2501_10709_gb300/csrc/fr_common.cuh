@@ -8,6 +8,8 @@
 
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/finrl_gb300.h"
 #include "fr_rng.cuh"
 
@@ -30,6 +32,31 @@ int cuda_fail(cudaError_t e, const char *what);
             return (code);                   \
         }                                    \
     } while (0)
+
+// NVTX range, in the library's own domain "finrl_gb300", on the calling host
+// thread for the duration of an ABI call: a profiler shows which call issued
+// which launches (e.g. ncu --nvtx --nvtx-include "finrl_gb300@rollout/").
+// Without an attached tool each push / pop is one test of a null pointer.
+struct NvtxScope {
+    explicit NvtxScope(const char *name)
+    {
+        nvtxEventAttributes_t a = {};
+        a.version = NVTX_VERSION;
+        a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+        a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+        a.message.ascii = name;
+        nvtxDomainRangePushEx(domain(), &a);
+    }
+    ~NvtxScope() { nvtxDomainRangePop(domain()); }
+    NvtxScope(const NvtxScope &) = delete;
+    NvtxScope &operator=(const NvtxScope &) = delete;
+    static nvtxDomainHandle_t domain()
+    {
+        static const nvtxDomainHandle_t d = nvtxDomainCreateA("finrl_gb300");
+        return d;
+    }
+};
+#define FR_NVTX(name) ::fr::NvtxScope fr_nvtx_scope_(name)
 
 // --------------------------------------------------------- device layouts
 constexpr int KP = 32;          // padded asset slots per env (one per lane)
@@ -169,6 +196,8 @@ int ctx_reserve(fr_ctx *ctx, uint64_t bytes);
 void ctx_release(fr_ctx *ctx, uint64_t bytes);
 // cudaMalloc with budget accounting.
 int dev_alloc(fr_ctx *ctx, void **p, uint64_t bytes);
+// true when an armed host fault injection (fr_fault_inject) fails this event
+bool fault_hit(int kind);
 void dev_free(fr_ctx *ctx, void *p, uint64_t bytes);
 
 inline unsigned ceil_div(long long a, long long b) { return (unsigned)((a + b - 1) / b); }

@@ -58,6 +58,7 @@ using namespace fr;
 extern "C" int trajectory_metrics(const int64_t *rew, const uint8_t *done, int32_t T, int32_t N, int64_t v0,
                                   double ann, double gamma, double *out, void *stream)
 {
+    FR_NVTX("trajectory_metrics");
     FR_CHECK(T >= 0 && N >= 0 && v0 > 0 && ann > 0.0 && isfinite(gamma), FR_EINVAL,
              "trajectory_metrics: need T, N >= 0, v0 > 0, ann > 0, finite gamma");
     if (N == 0) return FR_OK;

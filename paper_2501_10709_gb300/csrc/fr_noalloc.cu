@@ -54,6 +54,7 @@ using namespace fr;
 extern "C" int ensemble_act_noalloc(const fr_ensemble *e, const float *obs, int32_t n, void *act,
                                     void *stream)
 {
+    FR_NVTX("ensemble_act_noalloc");
     FR_CHECK(e && n >= 0, FR_EINVAL, "ensemble_act_noalloc: bad argument");
     if (n == 0) return FR_OK;
     FR_CHECK(obs && act, FR_EINVAL, "ensemble_act_noalloc: NULL obs or act");

@@ -232,6 +232,7 @@ extern "C" {
 int market_indicators(const int64_t *close, const int64_t *high, const int64_t *low, int32_t n_days,
                       int32_t n_assets, float *ind, void *stream)
 {
+    FR_NVTX("market_indicators");
     FR_CHECK(close && high && low && ind, FR_EINVAL, "market_indicators: NULL table");
     FR_CHECK(n_days >= 1 && n_assets >= 1 && (int64_t)n_days * n_assets <= ((int64_t)1 << 40), FR_EINVAL,
              "market_indicators: n_days %d and n_assets %d must be >= 1", n_days, n_assets);
@@ -241,6 +242,7 @@ int market_indicators(const int64_t *close, const int64_t *high, const int64_t *
 
 int env_perturb(fr_env *env, uint64_t seed, int32_t bps_range, void *stream)
 {
+    FR_NVTX("env_perturb");
     FR_CHECK(env, FR_EINVAL, "env_perturb: NULL env");
     FR_CHECK(env->v.task == FR_TASK_STOCK, FR_EINVAL, "env_perturb: stock envs only");
     FR_CHECK(bps_range >= 0 && bps_range <= 100, FR_EINVAL, "env_perturb: bps_range %d not in 0..100",

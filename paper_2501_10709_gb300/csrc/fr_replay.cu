@@ -202,6 +202,7 @@ extern "C" {
 
 int replay_create(fr_ctx *ctx, const fr_env *env, int64_t capacity, fr_replay **out)
 {
+    FR_NVTX("replay_create");
     FR_CHECK(ctx && env && out, FR_EINVAL, "replay_create: NULL argument");
     *out = nullptr;
     FR_CHECK(capacity >= 1 && capacity <= 0x7fffffffLL, FR_EINVAL, "replay_create: capacity %lld not in 1..2^31-1",
@@ -255,6 +256,7 @@ int replay_create(fr_ctx *ctx, const fr_env *env, int64_t capacity, fr_replay **
 
 void replay_destroy(fr_replay *rb)
 {
+    FR_NVTX("replay_destroy");
     if (!rb) return;
     cudaSetDevice(rb->ctx->device);
     dev_free(rb->ctx, rb->block, rb->bytes);
@@ -264,6 +266,7 @@ void replay_destroy(fr_replay *rb)
 int replay_push(fr_replay *rb, const fr_env *env, const fr_traj *tr, int32_t T, const float *last_obs,
                 const uint8_t *live0, void *stream)
 {
+    FR_NVTX("replay_push");
     FR_CHECK(rb && env && tr && last_obs, FR_EINVAL, "replay_push: NULL argument");
     FR_CHECK(env->v.task == rb->task && env->v.D == rb->b.D && (rb->b.act_u8 || env->v.K == rb->b.K), FR_EINVAL,
              "replay_push: env shape does not match the buffer");
@@ -295,6 +298,7 @@ int replay_push(fr_replay *rb, const fr_env *env, const fr_traj *tr, int32_t T, 
 int replay_sample(fr_replay *rb, int32_t B, uint64_t seed, uint64_t counter, float *obs, void *act, float *rew,
                   float *next_obs, uint8_t *done, int64_t *index, void *stream)
 {
+    FR_NVTX("replay_sample");
     FR_CHECK(rb && B >= 0, FR_EINVAL, "replay_sample: bad argument");
     if (B == 0) return FR_OK;
     FR_CUDA(cudaSetDevice(rb->ctx->device));
@@ -308,6 +312,7 @@ int replay_sample(fr_replay *rb, int32_t B, uint64_t seed, uint64_t counter, flo
 
 int replay_size_sync(fr_replay *rb, int64_t *size, int64_t *pushed, uint32_t *errors, void *stream)
 {
+    FR_NVTX("replay_size_sync");
     FR_CHECK(rb, FR_EINVAL, "replay_size_sync: NULL buffer");
     FR_CUDA(cudaSetDevice(rb->ctx->device));
     int64_t h[4] = {0, 0, 0, 0};

@@ -174,17 +174,53 @@ void fail_all(fr_server *s, int rc)
         q->t_done = t;
         s->live.erase(q->ticket);
         s->finished[q->ticket] = q;
+        s->st.failed += 1;
     }
     for (SrvReq *q : s->queue) {
         q->status = rc;
         q->t_done = t;
         s->live.erase(q->ticket);
         s->finished[q->ticket] = q;
+        s->st.failed += 1;
     }
     s->running.clear();
     s->queue.clear();
     s->st.running = 0;
     s->st.queued = 0;
+}
+
+// A chunk failed without a CUDA error (the context is still usable): the
+// running requests finish with status rc, their slots are parked and freed,
+// and the queued requests stay.  Returns a CUDA status (parking the slots).
+cudaError_t fail_running(fr_server *s, int rc)
+{
+    int n = 0;
+    for (SrvReq *q : s->running)
+        for (int32_t e : q->slots) s->h_slot[n++] = e;
+    cudaError_t ce = cudaSuccess;
+    if (n > 0) {
+        ce = cudaMemcpyAsync(s->d_slot, s->h_slot, 4ull * n, cudaMemcpyHostToDevice, s->stream);
+        if (ce == cudaSuccess) {
+            k_slot_park<<<ceil_div(n, 128), 128, 0, s->stream>>>(s->env->v, s->d_slot, n);
+            ce = cudaGetLastError();
+        }
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
+    }
+    if (ce != cudaSuccess) return ce;
+    std::lock_guard<std::mutex> lk(s->mu);
+    const double t = now_s();
+    for (SrvReq *q : s->running) {
+        q->status = rc;
+        q->t_done = t;
+        s->free_slots.insert(s->free_slots.end(), q->slots.begin(), q->slots.end());
+        s->live.erase(q->ticket);
+        s->finished[q->ticket] = q;
+        s->st.failed += 1;
+    }
+    s->running.clear();
+    std::sort(s->free_slots.begin(), s->free_slots.end());
+    s->st.running = 0;
+    return cudaSuccess;
 }
 
 void worker_loop(fr_server *s)
@@ -228,9 +264,18 @@ void worker_loop(fr_server *s)
             s->env->slot_ke = nullptr;
         }
         int rc = rollout(s->env, s->ens, chunk, nullptr, nullptr, s->stream);
-        if (rc) {
+        if (rc == FR_ECUDA) {
             fail_all(s, rc);
             return;
+        }
+        if (rc) {
+            ce = fail_running(s, rc);
+            if (ce != cudaSuccess) {
+                cuda_fail(ce, "server: parking failed requests");
+                fail_all(s, FR_ECUDA);
+                return;
+            }
+            continue;
         }
         // the worker alone touches running requests' progress
         std::vector<SrvReq *> done;
@@ -309,6 +354,7 @@ extern "C" {
 
 int fr_server_create(fr_ctx *ctx, const fr_server_desc *d, fr_server **out)
 {
+    FR_NVTX("fr_server_create");
     FR_CHECK(ctx && d && out && d->market && d->ens, FR_EINVAL, "fr_server_create: NULL argument");
     *out = nullptr;
     FR_CHECK(d->capacity >= 1 && d->chunk_steps >= 1, FR_EINVAL,
@@ -384,6 +430,7 @@ int fr_server_create(fr_ctx *ctx, const fr_server_desc *d, fr_server **out)
 
 void fr_server_destroy(fr_server *s)
 {
+    FR_NVTX("fr_server_destroy");
     if (!s) return;
     {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -398,6 +445,7 @@ void fr_server_destroy(fr_server *s)
 
 int backtest_submit(fr_server *s, const fr_request *r, uint64_t *ticket)
 {
+    FR_NVTX("backtest_submit");
     FR_CHECK(s && r && ticket, FR_EINVAL, "backtest_submit: NULL argument");
     FR_CHECK(r->n_envs >= 1 && r->window >= 2 && r->start >= 0 && r->start_stride >= 0 && r->metrics, FR_EINVAL,
              "backtest_submit: need n_envs >= 1, window >= 2, start >= 0, start_stride >= 0, metrics");
@@ -416,6 +464,7 @@ int backtest_submit(fr_server *s, const fr_request *r, uint64_t *ticket)
     }
     FR_CHECK(r->n_envs <= s->d.capacity, FR_ENOMEM,
              "backtest_submit: %d envs can never fit the server's %d slots", r->n_envs, s->d.capacity);
+    FR_CHECK(!fault_hit(FR_FAULT_SUBMIT), FR_EBUSY, "backtest_submit: request rejected (injected fault)");
     SrvReq *q = new (std::nothrow) SrvReq();
     FR_CHECK(q, FR_ENOMEM, "backtest_submit: out of host memory");
     q->r = *r;
@@ -440,9 +489,14 @@ int backtest_submit(fr_server *s, const fr_request *r, uint64_t *ticket)
 
 int backtest_poll(fr_server *s, uint64_t ticket, fr_result *out, int32_t *done)
 {
+    FR_NVTX("backtest_poll");
     FR_CHECK(s && out && done, FR_EINVAL, "backtest_poll: NULL argument");
-    std::lock_guard<std::mutex> lk(s->mu);
     *done = 0;
+    if (fault_hit(FR_FAULT_POLL)) {
+        set_error("backtest_poll: answer dropped (injected fault)");
+        return FR_ENOTREADY;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
     auto it = s->finished.find(ticket);
     if (it != s->finished.end()) {
         SrvReq *q = it->second;
@@ -462,6 +516,7 @@ int backtest_poll(fr_server *s, uint64_t ticket, fr_result *out, int32_t *done)
 
 int fr_server_stats_get(fr_server *s, fr_server_stats *out)
 {
+    FR_NVTX("fr_server_stats_get");
     FR_CHECK(s && out, FR_EINVAL, "fr_server_stats_get: NULL argument");
     std::lock_guard<std::mutex> lk(s->mu);
     *out = s->st;

@@ -552,6 +552,7 @@ int tc_device_errors(const fr_ensemble *e, unsigned *flags)
 
 extern "C" int ensemble_device_errors(const fr_ensemble *e, uint32_t *flags)
 {
+    FR_NVTX("ensemble_device_errors");
     FR_CHECK(e && flags, FR_EINVAL, "ensemble_device_errors: NULL argument");
     FR_CUDA(cudaSetDevice(e->ctx->device));
     unsigned f = 0;

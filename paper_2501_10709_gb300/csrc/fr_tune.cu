@@ -71,6 +71,7 @@ extern "C" {
 int env_autotune(fr_env *env, const fr_ensemble *e, int32_t T_probe, int32_t flags, fr_tune_report *out,
                  void *stream)
 {
+    FR_NVTX("env_autotune");
     FR_CHECK(env && e && out, FR_EINVAL, "env_autotune: NULL argument");
     FR_CHECK(T_probe >= 1 && T_probe <= 4096, FR_EINVAL, "env_autotune: T_probe %d not in 1..4096", T_probe);
     FR_CHECK(env->ctx == e->ctx || env->ctx->device == e->ctx->device, FR_EINVAL,
@@ -176,6 +177,7 @@ int env_autotune(fr_env *env, const fr_ensemble *e, int32_t T_probe, int32_t fla
 
 int env_tune_set(fr_env *env, int32_t path, int32_t packed, int32_t stages, int32_t tiled)
 {
+    FR_NVTX("env_tune_set");
     FR_CHECK(env, FR_EINVAL, "env_tune_set: NULL env");
     FR_CHECK(path >= 0 && path <= 2 && (stages == 0 || stages >= 2), FR_EINVAL,
              "env_tune_set: path %d or stages %d out of range", path, stages);
@@ -185,6 +187,7 @@ int env_tune_set(fr_env *env, int32_t path, int32_t packed, int32_t stages, int3
 
 int env_tune_clear(fr_env *env)
 {
+    FR_NVTX("env_tune_clear");
     FR_CHECK(env, FR_EINVAL, "env_tune_clear: NULL env");
     env->tune_set = 0;
     env->pack_off = 0;

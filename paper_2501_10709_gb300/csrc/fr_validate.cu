@@ -45,6 +45,7 @@ extern "C" {
 
 int ensemble_set_weights(fr_ensemble *e, const float *w)
 {
+    FR_NVTX("ensemble_set_weights");
     FR_CHECK(e && w, FR_EINVAL, "ensemble_set_weights: NULL argument");
     FR_CHECK(e->combine == FR_COMBINE_MEAN, FR_EINVAL, "ensemble_set_weights: weights apply to MEAN only");
     for (int j = 0; j < e->M; ++j)
@@ -58,6 +59,7 @@ int ensemble_set_weights(fr_ensemble *e, const float *w)
 int ensemble_validate(fr_ensemble *e, fr_env *env, int32_t T, double threshold, double *sharpe,
                       float *weights, void *stream)
 {
+    FR_NVTX("ensemble_validate");
     FR_CHECK(e && env && T >= 1, FR_EINVAL, "ensemble_validate: bad argument");
     FR_CHECK(e->combine == FR_COMBINE_MEAN, FR_EINVAL, "ensemble_validate: weights apply to MEAN ensembles");
     FR_CHECK(isfinite(threshold) || threshold == -INFINITY, FR_EINVAL, "ensemble_validate: threshold");

@@ -53,3 +53,14 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(ImportError):
         _lib.load()
+
+
+def test_fault_injection_knob_checks_its_arguments(built_lib):
+    import paper_2501_10709_gb300 as fr
+    for bad in ((0, 0, 1), (4, 0, 1), (fr.FAULT_ALLOC, -1, 1), (fr.FAULT_POLL, 0, -2)):
+        with pytest.raises(fr.FrError) as ei:
+            fr.fr_fault_inject(*bad)
+        assert ei.value.code == fr._lib.FR_EINVAL
+    for k in (fr.FAULT_ALLOC, fr.FAULT_SUBMIT, fr.FAULT_POLL):
+        fr.fr_fault_inject(k, 2, 1)
+        fr.fr_fault_inject(k, 0, 0)                     # disarmed again
