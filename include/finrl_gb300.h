@@ -677,6 +677,17 @@ int fr_server_stats_get(fr_server *srv, fr_server_stats *out);
  *  FR_FAULT_POLL    backtest_poll drops its answer: FR_ENOTREADY, *done = 0;
  *                   a finished result stays for the next poll
  * FR_EINVAL for an unknown kind or a negative skip / count. */
+/* Device check of the bounded waits behind FR_ETIMEDOUT: one block waits,
+ * with the limit limit_us (1..2e6), on mbarrier phases that nothing
+ * completes, in both forms the fused kernels use (one thread; a whole warp
+ * with a warp vote), and once on a phase that does complete.  Synchronous.
+ * Returns FR_ETIMEDOUT when a wait gave up -- the designed outcome: *flags =
+ * 3 (bit 0 the one-thread wait, bit 1 the warp wait; bit 2 would mean the
+ * completed phase was missed) and waited_ns[2] (nullable) the time each of
+ * the first two waited -- and the context stays usable.  FR_OK if no wait
+ * gave up; FR_ECUDA on a launch or copy error. */
+int fr_wait_selftest(fr_ctx *ctx, int32_t limit_us, uint32_t *flags, uint64_t *waited_ns);
+
 #define FR_FAULT_ALLOC 1
 #define FR_FAULT_SUBMIT 2
 #define FR_FAULT_POLL 3

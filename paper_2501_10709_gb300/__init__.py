@@ -30,7 +30,7 @@ __all__ = [
     "Replay", "replay_create", "replay_push", "replay_sample", "replay_size", "ensemble_q", "ensemble_q_targets",
     "HEAD_Q", "HEAD_DUELING", "env_autotune", "env_tune_clear", "env_tune_set",
     "PATH_AUTO", "PATH_UNFUSED", "BUY_ASCENDING", "BUY_LARGEST_FIRST",
-    "fr_fault_inject", "FAULT_ALLOC", "FAULT_SUBMIT", "FAULT_POLL",
+    "fr_fault_inject", "FAULT_ALLOC", "FAULT_SUBMIT", "FAULT_POLL", "fr_wait_selftest",
     "ACT_I32_SHARES", "ACT_F32_UNIT", "ACT_U8_DISCRETE", "PREC_FP32", "PREC_BF16",
     "PREC_FP8", "PREC_BF16X3", "COMBINE_MEAN", "COMBINE_VOTE", "TASK_STOCK", "TASK_CRYPTO",
 ]
@@ -564,6 +564,18 @@ def fr_fault_inject(kind: int, skip: int = 0, count: int = 1):
     `count` after them fail with the error the real failure returns;
     count 0 disarms the kind."""
     _lib.check(lib().fr_fault_inject(int(kind), int(skip), int(count)), "fr_fault_inject")
+
+
+def fr_wait_selftest(ctx: Ctx, limit_us: int = 50_000) -> dict:
+    """Run the device check of the bounded waits: returns status
+    (FR_ETIMEDOUT is the designed outcome), the error bits the waits set and
+    the ns each of the two abandoned waits took."""
+    flags = C.c_uint32()
+    w = (C.c_uint64 * 2)()
+    rc = lib().fr_wait_selftest(ctx, int(limit_us), C.byref(flags), w)
+    if rc not in (_lib.FR_OK, _lib.FR_ETIMEDOUT):
+        _lib.check(rc, "fr_wait_selftest")
+    return {"status": rc, "flags": flags.value, "waited_ns": (w[0], w[1])}
 
 
 # ------------------------------------------------------ ensemble weighting

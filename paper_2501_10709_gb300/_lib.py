@@ -133,6 +133,7 @@ SIGNATURES = {
     "backtest_poll": (i32, [vp, u64, vp, vp]),
     "fr_server_stats_get": (i32, [vp, vp]),
     "fr_fault_inject": (i32, [i32, i32, i32]),
+    "fr_wait_selftest": (i32, [vp, i32, vp, vp]),
     "fr_market_copy_indicators": (i32, [vp, vp]),
     "market_indicators": (i32, [vp, vp, vp, i32, i32, vp, vp]),
     "env_perturb": (i32, [vp, u64, i32, vp]),

@@ -1,7 +1,8 @@
 """Error paths under host-side fault injection (fr_fault_inject): a failed
 device allocation, a rejected submit and dropped polls each surface as their
-error code and leave the other requests intact.  Nothing here faults, traps
-or stalls the GPU: every injected failure is made on the host."""
+error code and leave the other requests intact.  Nothing here faults or traps
+the GPU: those failures are made on the host.  The one device-side case is
+the bounded-wait check, whose waits give up by design after 50 ms."""
 import time
 
 import numpy as np
@@ -145,3 +146,29 @@ def test_dropped_polls_keep_the_result(ctx, dev):
     srv.close()
     assert got is not None and got["status"] == _lib.FR_OK
     assert np.array_equal(got["metrics"], _standalone(ctx, mk, ens, dev, r))
+
+
+def test_bounded_waits_give_up_and_the_context_stays_usable(ctx, dev):
+    # both wait forms of the fused kernels, on barriers nothing completes,
+    # limited to 50 ms: each gives up, sets its error bit and returns
+    r = fr.fr_wait_selftest(ctx, limit_us=50_000)
+    assert r["status"] == _lib.FR_ETIMEDOUT
+    assert r["flags"] == 3                                     # bit 2: the completed control wait
+    for ns in r["waited_ns"]:
+        assert 50e6 <= ns < 1e9
+    with pytest.raises(fr.FrError):
+        fr.fr_wait_selftest(ctx, limit_us=0)
+    # the context still runs work exactly
+    w = synth.workload_stock_small()
+    e = w.envs
+    mk = fr.fr_market_create(ctx, w.market)
+    env = fr.env_create(ctx, mk, start=e.start, window=e.W, n_assets=e.Ke, bps=e.bps)
+    acts = synth.prescribed_shares(4, e.N, 30, seed=9)
+    rew = torch.empty(4, e.N, dtype=torch.int64, device=dev)
+    a = torch.from_numpy(acts).to(dev)
+    for t in range(4):
+        fr.env_step(env, a[t], fr.ACT_I32_SHARES, rew=rew[t])
+    torch.cuda.synchronize()
+    ref = oracle.stock_run(w.market, e.Ke, e.start, e.W, e.bps, init_cash=e.init_cash, hmax=100,
+                           fee_bps=10, T=4, act_i32=acts, want=("rew",))
+    assert np.array_equal(rew.cpu().numpy(), ref["rew"])
