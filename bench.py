@@ -121,6 +121,20 @@ def build_workload():
 
 
 # ---------------------------------------------------------------- CPU oracle
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), else the machine type."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
+
+
 def cpu_baseline(w, target_s: float = 12.0):
     """Time the oracle (as it stands) on a bounded sample of the same workload:
     the first n envs for all 256 steps, n sized for ~target_s seconds."""
@@ -142,7 +156,8 @@ def cpu_baseline(w, target_s: float = 12.0):
     n = max(threads, (n // threads) * threads)
     dt = run(n, w.T)
     out = {"value": n * w.T / dt, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
-           "sample": f"first {n} of {e.N} envs x {w.T} steps, fp64 actors, {dt:.1f} s"}
+           "sample": f"first {n} of {e.N} envs x {w.T} steps, fp64 actors, {dt:.1f} s",
+           "cpu_model": cpu_model()}
     # the same workload on one core (a smaller sample of envs, all 256 steps)
     t0 = time.perf_counter()
     n1 = 8
@@ -685,7 +700,7 @@ def run_reference(args):
         "config": {"workload": "stock 2048 envs x 30 assets x 256 steps, 3 x 301-256-256-30 "
                                "actors, mean combine (oracle sample)", "n_envs": n},
         "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }), flush=True)

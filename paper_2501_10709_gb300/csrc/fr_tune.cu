@@ -41,7 +41,8 @@ std::vector<int64_t> tune_key(const fr_env *env, const fr_ensemble *e, bool unev
     const EnvView &v = env->v;
     std::vector<int64_t> k = {v.task,      v.N,          v.K,           v.I,        v.D,
                               uneven,      v.auto_reset, e->M,          e->L,       e->precision,
-                              e->combine,  e->out_act,   e->dueling,    env->ctx->sm_count, env->ctx->device};
+                              e->combine,  e->out_act,   e->dueling,    env->ctx->sm_count, env->ctx->device,
+                              v.buy_order};
     for (int l = 0; l <= e->L; ++l) k.push_back(e->dims[l]);
     return k;
 }
