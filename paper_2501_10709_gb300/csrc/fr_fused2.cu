@@ -133,6 +133,14 @@ bool f2_plan(const fr_ensemble *e, F2Plan &p)
 // at index r / 2M of that CTA's owned rows.
 __host__ __device__ inline int f2_owned_rows(int M) { return (128 + 2 * M - 1) / (2 * M); }
 
+// Layer-3 partial-sum bytes a CTA receives per step from the other 2M - 1
+// CTAs: 128 bytes for each of its owned rows from each.
+__host__ __device__ inline uint32_t f2_x_tx_bytes(int M, int rank)
+{
+    const int rows = (127 - rank) / (2 * M) + 1;
+    return (uint32_t)(rows * (2 * M - 1)) * 128u;
+}
+
 // shared-memory carve-up
 struct F2Smem {
     uint32_t w, a, xbuf, ctx, bias, bars, total;
@@ -386,6 +394,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
     const uint32_t row_off = (uint32_t)(r / 8) * 128u + (uint32_t)(r % 8) * 16u;
     const uint32_t xbuf = smem_u32(smem + L.xbuf);
     const int RO = f2_owned_rows(M);
+    const uint32_t x_tx = f2_x_tx_bytes(M, rank);
     const uint32_t ctx_addr = smem_u32(smem + L.ctx);
     const int32_t *ctxv = (const int32_t *)(smem + L.ctx);
     uint64_t *obs_ready = &bars[B_OBS], *acc = &bars[B_ACC], *h1r = &bars[B_H1], *h2r = &bars[B_H2];
@@ -551,14 +560,28 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
             tmem_ld_wait();
             // row r's partial sums to block `rank` of its owner's buffer, at
             // owned row r / 2M; column group k stored at group k ^ (row & 7),
-            // so that the owner's per-lane reads of one row are conflict-free
+            // so that the owner's per-lane reads of one row are conflict-free.
+            // Another CTA's rows go by asynchronous stores that complete bytes
+            // on the owner's barrier (no fence here); this CTA's own rows by
+            // plain stores and one local arrival per warp.
             const uint32_t ri = (uint32_t)(r / M2);
-            const uint32_t dst = map_shared_rank(xbuf + ((uint32_t)rank * (uint32_t)RO + ri) * 128u, (uint32_t)(r % M2));
+            const uint32_t owner = (uint32_t)(r % M2);
+            const uint32_t at = xbuf + ((uint32_t)rank * (uint32_t)RO + ri) * 128u;
+            if (owner == (uint32_t)rank) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-                st_cluster_v4(dst + 16u * ((uint32_t)k ^ (ri & 7u)), vv[4 * k], vv[4 * k + 1], vv[4 * k + 2],
-                              vv[4 * k + 3]);
-            f2_signal_all(xrdy, M2, lane, false);
+                for (int k = 0; k < 8; ++k)
+                    st_shared_v4(at + 16u * ((uint32_t)k ^ (ri & 7u)), vv[4 * k], vv[4 * k + 1], vv[4 * k + 2],
+                                 vv[4 * k + 3]);
+            } else {
+                const uint32_t dst = map_shared_rank(at, owner);
+                const uint32_t rbar = map_shared_rank(smem_u32(xrdy), owner);
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    st_async_v4(dst + 16u * ((uint32_t)k ^ (ri & 7u)), vv[4 * k], vv[4 * k + 1], vv[4 * k + 2],
+                                vv[4 * k + 3], rbar);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(xrdy);
         }
         tc_fence_before();
         // --------------------------------------------- owners: trade, publish
@@ -576,6 +599,8 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
             p1[i] = ok ? perturb(__ldg(v.close + (int64_t)(st.start + st.t + 1) * SK2 + lane), st.bps) : 0;
         }
         f2_wait(xrdy, ph, abort, a.err, 64u, true);
+        // arm the next phase: one arrival, the bytes the other CTAs send
+        if (ew == 0 && lane == 0) mbar_arrive_expect_tx(xrdy, x_tx);
         const int fee = v.fee_bps;
         int64_t nsell[NOWN], want[NOWN], full[NOWN], ssum[NOWN], bsum[NOWN], vsum[NOWN];
 #pragma unroll
@@ -667,6 +692,13 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         if (s + 1 < T) own_publish_all<NOWN>(a, own, orow, eidx, a_obs, ctx_addr, M2, lane, (int64_t)(s + 1) * v.N);
         if (s + 1 < T) f2_signal_all(obs_ready, M2, lane, true);
     }
+    // the other CTAs' asynchronous stores of the last step have landed
+    // before this CTA can exit, also when a wait gave up and the loop ran on
+    // without its data (bounded; a no-op when the last phase completed)
+    if (T > 0 && ew == 0 && lane == 0) {
+        volatile int no_abort = 0;
+        mbar_wait_cluster(xrdy, (uint32_t)(T - 1) & 1u, &no_abort, a.err, 32u, TC_WAIT_NS);
+    }
     // every MMA this CTA issued has completed before TMEM is released, also
     // when a wait gave up and the loop ran on without its data
     if (issuer && lane == 0) {
@@ -711,7 +743,10 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_rollout_stock2(const __grid_c
         mbar_init(&bars[B_ACC], 1);
         mbar_init(&bars[B_H1], 2u * F2_ENV_WARPS);                 // this CTA's and the partner's E1 warps
         mbar_init(&bars[B_H2], (uint32_t)F2_ENV_WARPS);            // this CTA's E2 warps
-        mbar_init(&bars[B_X], (uint32_t)(M2 * 4));                 // the 4 E3 warps of every CTA
+        // this CTA's 4 E3 warps, plus one arming arrival per phase that
+        // expects the other CTAs' bytes; phase 0 armed here
+        mbar_init(&bars[B_X], 5u);
+        mbar_arrive_expect_tx(&bars[B_X], f2_x_tx_bytes(p.M, rank));
         mbar_init(&bars[B_END], 1);                                // the issuer's last commit
         *abort = 0;
         fence_mbar_init();

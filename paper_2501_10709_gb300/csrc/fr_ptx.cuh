@@ -406,6 +406,19 @@ __device__ __forceinline__ void st_cluster_v4(uint32_t addr, uint32_t a, uint32_
                  : "memory");
 }
 
+// Asynchronous 16-byte store into another CTA's shared memory whose bytes
+// complete a transaction count on the mbarrier `bar` of that CTA (both are
+// shared::cluster addresses of the same CTA): the receiver arms the barrier
+// with the bytes it expects and its phase completes when they have landed,
+// so the sender needs no fence or arrival.
+__device__ __forceinline__ void st_async_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d,
+                                            uint32_t bar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1,%2,%3,%4}, [%5];" ::"r"(addr),
+                 "r"(a), "r"(b), "r"(c), "r"(d), "r"(bar)
+                 : "memory");
+}
+
 __device__ __forceinline__ void st_cluster_u8(uint32_t addr, uint32_t v)
 {
     asm volatile("st.shared::cluster.u8 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
