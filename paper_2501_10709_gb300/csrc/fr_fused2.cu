@@ -133,6 +133,19 @@ bool f2_plan(const fr_ensemble *e, F2Plan &p)
 // at index r / 2M of that CTA's owned rows.
 __host__ __device__ inline int f2_owned_rows(int M) { return (128 + 2 * M - 1) / (2 * M); }
 
+// Observation bytes a CTA receives per step from the other CTAs: the 64
+// BF16 state entries (128 bytes) and the Z row index (4 bytes) of every row
+// it does not own.
+__host__ __device__ inline uint32_t f2_obs_tx_bytes(int M, int rank)
+{
+    const int rows = (127 - rank) / (2 * M) + 1;
+    return (uint32_t)(128 - rows) * 132u;
+}
+
+// h1 bytes a CTA receives per step from its partner: 128 rows of the
+// partner's H1 / 2 columns in BF16.
+__host__ __device__ inline uint32_t f2_h1_tx_bytes(const F2Plan &p) { return 128u * (uint32_t)p.n1 * 2u; }
+
 // Layer-3 partial-sum bytes a CTA receives per step from the other 2M - 1
 // CTAs: 128 bytes for each of its owned rows from each.
 __host__ __device__ inline uint32_t f2_x_tx_bytes(int M, int rank)
@@ -168,20 +181,6 @@ __device__ __forceinline__ bool f2_wait(uint64_t *bar, uint32_t parity, volatile
                                         unsigned code, bool cluster_scope)
 {
     return ptx::warp_wait_all(bar, parity, cluster_scope, abort, err, code, TC_WAIT_NS);
-}
-
-// Arrive on `bar` in every CTA of the cluster once this warp's shared-memory
-// writes (local and remote) are visible there: one proxy fence when the
-// writes feed the tensor cores, one release fence, then relaxed arrivals.
-__device__ __forceinline__ void f2_signal_all(uint64_t *bar, int M2, int lane, bool for_mma)
-{
-    using namespace ptx;
-    if (for_mma) fence_proxy_async_cluster();
-    __syncwarp();
-    if (lane == 0) {
-        fence_acq_rel_cluster();
-        for (int m = 0; m < M2; ++m) mbar_arrive_remote_relaxed(map_shared_rank(smem_u32(bar), (uint32_t)m));
-    }
 }
 
 __device__ __forceinline__ void pack8_bf16(const float *v, uint32_t *w)
@@ -333,20 +332,34 @@ __device__ __forceinline__ ObsWords own_words(const F2Args &a, const OwnEnv &s, 
     return o;
 }
 
+// One 16-byte piece of a published row into CTA m: this CTA's own operand by
+// a plain store, another CTA's by an asynchronous store that completes its
+// bytes on that CTA's observation barrier.
+__device__ __forceinline__ void own_put16(const ObsWords &o, uint32_t at, int m, int rank, uint32_t obs_bar)
+{
+    using namespace ptx;
+    if (m == rank) st_shared_v4(at, o.w0, o.w1, o.w2, o.w3);
+    else st_async_v4(map_shared_rank(at, (uint32_t)m), o.w0, o.w1, o.w2, o.w3, map_shared_rank(obs_bar, (uint32_t)m));
+}
+
 // Row r's chunks to CTAs lane >> 3 and 4 + (lane >> 3), its Z row index to
 // CTA `lane`.
 __device__ __forceinline__ void own_store(const ObsWords &o, int r, uint32_t a_obs, uint32_t ctx_addr, int M2,
-                                          int lane)
+                                          int lane, int rank, uint32_t obs_bar)
 {
     using namespace ptx;
     const uint32_t at = a_obs + (uint32_t)(lane & 7) * 2048u + (uint32_t)(r / 8) * 128u + (uint32_t)(r % 8) * 16u;
     const int m0 = lane >> 3;
-    if (m0 < M2) st_cluster_v4(map_shared_rank(at, (uint32_t)m0), o.w0, o.w1, o.w2, o.w3);
-    if (m0 + 4 < M2) st_cluster_v4(map_shared_rank(at, (uint32_t)(m0 + 4)), o.w0, o.w1, o.w2, o.w3);
-    if (lane < M2)
-        asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(map_shared_rank(ctx_addr + 4u * r, (uint32_t)lane)),
-                     "r"(o.zrow)
-                     : "memory");
+    if (m0 < M2) own_put16(o, at, m0, rank, obs_bar);
+    if (m0 + 4 < M2) own_put16(o, at, m0 + 4, rank, obs_bar);
+    if (lane < M2) {
+        const uint32_t c = ctx_addr + 4u * (uint32_t)r;
+        if (lane == rank)
+            asm volatile("st.shared.u32 [%0], %1;" ::"r"(c), "r"(o.zrow) : "memory");
+        else
+            st_async_b32(map_shared_rank(c, (uint32_t)lane), (uint32_t)o.zrow,
+                         map_shared_rank(obs_bar, (uint32_t)lane));
+    }
 }
 
 // Publish the next observations of this warp's owned envs: all rows' words
@@ -354,14 +367,19 @@ __device__ __forceinline__ void own_store(const ObsWords &o, int r, uint32_t a_o
 // trajectory rows.  trow[i] < 0: no trajectory row.
 template <int NOWN>
 __device__ __forceinline__ void own_publish_all(const F2Args &a, const OwnEnv *own, const int *orow, const int *eidx,
-                                                uint32_t a_obs, uint32_t ctx_addr, int M2, int lane, int64_t tbase)
+                                                uint32_t a_obs, uint32_t ctx_addr, int M2, int lane, int64_t tbase,
+                                                int rank, uint64_t *obs_bar)
 {
     ObsWords o[NOWN];
 #pragma unroll
     for (int i = 0; i < NOWN; ++i) o[i] = own_words(a, own[i], eidx[i] >= 0, lane);
+    const uint32_t ob = ptx::smem_u32(obs_bar);
 #pragma unroll
     for (int i = 0; i < NOWN; ++i)
-        if (orow[i] < 128) own_store(o[i], orow[i], a_obs, ctx_addr, M2, lane);
+        if (orow[i] < 128) own_store(o[i], orow[i], a_obs, ctx_addr, M2, lane, rank, ob);
+    // this CTA's own rows: one local arrival once the warp's plain stores are done
+    __syncwarp();
+    if (lane == 0) ptx::mbar_arrive(obs_bar);
     if (a.tr_obs) {
 #pragma unroll
         for (int i = 0; i < NOWN; ++i) {
@@ -395,6 +413,9 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
     const uint32_t xbuf = smem_u32(smem + L.xbuf);
     const int RO = f2_owned_rows(M);
     const uint32_t x_tx = f2_x_tx_bytes(M, rank);
+    const uint32_t obs_tx = f2_obs_tx_bytes(M, rank);
+    const uint32_t h1_tx = f2_h1_tx_bytes(p);
+    const uint32_t h1r_partner = map_shared_rank(smem_u32(&bars[B_H1]), (uint32_t)(rank ^ 1));
     const uint32_t ctx_addr = smem_u32(smem + L.ctx);
     const int32_t *ctxv = (const int32_t *)(smem + L.ctx);
     uint64_t *obs_ready = &bars[B_OBS], *acc = &bars[B_ACC], *h1r = &bars[B_H1], *h2r = &bars[B_H2];
@@ -442,8 +463,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         s.v0 = s.cash + warp_sum(s.p * (int64_t)s.h);
     }
     // observation of step 0
-    own_publish_all<NOWN>(a, own, orow, eidx, a_obs, ctx_addr, M2, lane, 0);
-    f2_signal_all(obs_ready, M2, lane, true);
+    own_publish_all<NOWN>(a, own, orow, eidx, a_obs, ctx_addr, M2, lane, 0, rank, obs_ready);
 
     const float *zbase = a.Z + (size_t)j * a.n_ctx_per_agent * p.H1;
     // The step loop has no early exit: its trip count is uniform, so the warp
@@ -461,6 +481,9 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         // the observation barrier also publishes each env's Z row: read it
         // and start the row's loads while layer 1 runs on the tensor cores
         f2_wait(obs_ready, ph, abort, a.err, 16u, true);
+        // arm the next phase: the owner warps' local arrivals follow, the
+        // bytes of the other CTAs' rows are expected
+        if (issuer && lane == 0 && !*abort) mbar_arrive_expect_tx(obs_ready, obs_tx);
         if (issuer && lane == 0) f2_layer(p.l1, tmem, a_obs, w_base, acc);
         const int nc1 = p.n1 / 2;                          // columns per warp (<= 64)
         const int c01 = col_half * nc1;
@@ -500,21 +523,19 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                 const uint32_t at = a_base + (dst_chunk0 + (uint32_t)(cc / 8)) * 2048u + row_off;
                 st_shared_v4(at, w0[0], w0[1], w0[2], w0[3]);
                 st_shared_v4(at + 2048u, w1[0], w1[1], w1[2], w1[3]);
+                // the partner's copy: asynchronous stores that complete their
+                // bytes on the partner's h1 barrier
                 const uint32_t pt = map_shared_rank(at, (uint32_t)(rank ^ 1));
-                st_cluster_v4(pt, w0[0], w0[1], w0[2], w0[3]);
-                st_cluster_v4(pt + 2048u, w1[0], w1[1], w1[2], w1[3]);
+                st_async_v4(pt, w0[0], w0[1], w0[2], w0[3], h1r_partner);
+                st_async_v4(pt + 2048u, w1[0], w1[1], w1[2], w1[3], h1r_partner);
             }
         }
-        fence_proxy_async_cluster();
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) {
-            fence_acq_rel_cluster();
-            mbar_arrive(h1r);
-            mbar_arrive_remote_relaxed(map_shared_rank(smem_u32(h1r), (uint32_t)(rank ^ 1)));
-        }
+        if (lane == 0) mbar_arrive(h1r);
         if (issuer) {
             f2_wait(h1r, ph, abort, a.err, 4u, true);
+            if (lane == 0 && !*abort) mbar_arrive_expect_tx(h1r, h1_tx);     // arm the next phase
             if (lane == 0) f2_layer(p.l2, tmem, a_base, w_base, acc);
             __syncwarp();
         }
@@ -600,7 +621,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         }
         f2_wait(xrdy, ph, abort, a.err, 64u, true);
         // arm the next phase: one arrival, the bytes the other CTAs send
-        if (ew == 0 && lane == 0) mbar_arrive_expect_tx(xrdy, x_tx);
+        if (ew == 0 && lane == 0 && !*abort) mbar_arrive_expect_tx(xrdy, x_tx);
         const int fee = v.fee_bps;
         int64_t nsell[NOWN], want[NOWN], full[NOWN], ssum[NOWN], bsum[NOWN], vsum[NOWN];
 #pragma unroll
@@ -689,14 +710,17 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                 a.vlog[row] = vlog;
             }
         }
-        if (s + 1 < T) own_publish_all<NOWN>(a, own, orow, eidx, a_obs, ctx_addr, M2, lane, (int64_t)(s + 1) * v.N);
-        if (s + 1 < T) f2_signal_all(obs_ready, M2, lane, true);
+        if (s + 1 < T)
+            own_publish_all<NOWN>(a, own, orow, eidx, a_obs, ctx_addr, M2, lane, (int64_t)(s + 1) * v.N, rank,
+                                  obs_ready);
     }
     // the other CTAs' asynchronous stores of the last step have landed
     // before this CTA can exit, also when a wait gave up and the loop ran on
     // without its data (bounded; a no-op when the last phase completed)
     if (T > 0 && ew == 0 && lane == 0) {
         volatile int no_abort = 0;
+        mbar_wait_cluster(obs_ready, (uint32_t)(T - 1) & 1u, &no_abort, a.err, 32u, TC_WAIT_NS);
+        mbar_wait_cluster(h1r, (uint32_t)(T - 1) & 1u, &no_abort, a.err, 32u, TC_WAIT_NS);
         mbar_wait_cluster(xrdy, (uint32_t)(T - 1) & 1u, &no_abort, a.err, 32u, TC_WAIT_NS);
     }
     // every MMA this CTA issued has completed before TMEM is released, also
@@ -734,14 +758,19 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_rollout_stock2(const __grid_c
     volatile int *abort = (volatile int *)(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rank = (int)cluster_ctarank();
-    const int M2 = 2 * p.M;
     const int tile = blockIdx.y;
 
     if (threadIdx.x == 0) {
         mbar_init(&bars[B_W], 1);
-        mbar_init(&bars[B_OBS], (uint32_t)(M2 * F2_ENV_WARPS));   // every owner warp of every CTA
+        // this CTA's owner warps (its own rows) plus one arming arrival per
+        // phase that expects the other CTAs' rows; phase 0 armed here
+        mbar_init(&bars[B_OBS], (uint32_t)F2_ENV_WARPS + 1u);
+        mbar_arrive_expect_tx(&bars[B_OBS], f2_obs_tx_bytes(p.M, rank));
         mbar_init(&bars[B_ACC], 1);
-        mbar_init(&bars[B_H1], 2u * F2_ENV_WARPS);                 // this CTA's and the partner's E1 warps
+        // this CTA's E1 warps plus one arming arrival per phase that expects
+        // the partner's half; phase 0 armed here
+        mbar_init(&bars[B_H1], (uint32_t)F2_ENV_WARPS + 1u);
+        mbar_arrive_expect_tx(&bars[B_H1], f2_h1_tx_bytes(p));
         mbar_init(&bars[B_H2], (uint32_t)F2_ENV_WARPS);            // this CTA's E2 warps
         // this CTA's 4 E3 warps, plus one arming arrival per phase that
         // expects the other CTAs' bytes; phase 0 armed here
