@@ -45,7 +45,8 @@ struct FusedArgs {
     float w[MAX_AGENTS];
     int T;
     int stages;
-    int resident;          // every chunk stays in its own ring stage
+    int resident;          // the agent's whole image stays in shared memory
+    uint32_t ring_bytes;   // weight region: stages x TC_CHUNK_MAX, or the image
     float *tr_obs;
     int obs_ld;
     void *tr_act;
@@ -71,10 +72,16 @@ __host__ __device__ inline uint32_t xbuf_bytes(int task, int M)
     return ((2u * (uint32_t)M * 128u * xrow_bytes(task)) + 15u) & ~15u;
 }
 
-__host__ __device__ inline uint32_t fused_smem(int task, const TcPlan &p, int stages)
+__host__ __device__ inline uint32_t fused_smem(int task, const TcPlan &p, uint32_t ring_bytes)
 {
-    return a_part_bytes(p) * (p.split == 3 ? 2u : 1u) + (uint32_t)stages * TC_CHUNK_MAX +
-           xbuf_bytes(task, p.M) + 256u + 1024u;
+    return a_part_bytes(p) * (p.split == 3 ? 2u : 1u) + ring_bytes + xbuf_bytes(task, p.M) + 256u + 1024u;
+}
+
+// Byte offset of chunk c of layer l in the agent's image; a resident copy
+// keeps every chunk at this offset (the image is its chunks end to end).
+__host__ __device__ inline uint32_t chunk_off(const TcPlan &p, const TcLayer &ly, int c)
+{
+    return ly.off + (uint32_t)c * (uint32_t)(ly.N * ly.KC * 2 * p.parts);
 }
 
 // ----------------------------------------------------- weight producer
@@ -100,9 +107,10 @@ __device__ void fused_producer(const FusedArgs &a, const uint8_t *aimg, uint8_t 
                 }
                 const int kc = min(ly.KC, ly.K - c * ly.KC);
                 const uint32_t bytes = (uint32_t)(ly.N * kc * 2 * p.parts);
+                const uint32_t off = chunk_off(p, ly, c);
                 mbar_arrive_expect_tx(&full[st], bytes);
-                bulk_g2s(ring + (size_t)st * TC_CHUNK_MAX,
-                         aimg + ly.off + (size_t)c * ly.N * ly.KC * 2 * p.parts, bytes, &full[st]);
+                bulk_g2s(ring + (a.resident ? (size_t)off : (size_t)st * TC_CHUNK_MAX), aimg + off, bytes,
+                         &full[st]);
                 ++i;
             }
         }
@@ -147,7 +155,8 @@ __device__ void fused_mma(const FusedArgs &a, uint32_t tmem, const uint8_t *A, c
                 }
                 tc_fence_after();
                 const int kc = min(ly.KC, ly.K - c * ly.KC);
-                const uint32_t b_base = smem_u32(ring + (size_t)st * TC_CHUNK_MAX);
+                const uint32_t b_base =
+                    smem_u32(ring + (a.resident ? (size_t)chunk_off(p, ly, c) : (size_t)st * TC_CHUNK_MAX));
                 const uint32_t b_lo = (uint32_t)(ly.N * kc * 2);
                 for (int kk = 0; kk < kc; kk += 16, kg += 16) {
                     const uint32_t ao = a_base + (uint32_t)(kg / 8) * 2048u;
@@ -686,7 +695,11 @@ __device__ void fused_env(const FusedArgs &a, uint32_t tmem, uint8_t *A, uint8_t
 }
 
 template <int TASK>
-__global__ void __launch_bounds__(FU_THREADS, 1) k_rollout_fused(const __grid_constant__ FusedArgs a)
+// Crypto tiles are small enough (resident weights ~40 KB, A operand 32 KB,
+// 128 TMEM columns) for three CTAs per SM, so a 5-agent ensemble over
+// 64 tiles runs in one wave.
+__global__ void __launch_bounds__(FU_THREADS, TASK == FR_TASK_CRYPTO ? 3 : 1)
+    k_rollout_fused(const __grid_constant__ FusedArgs a)
 {
     using namespace ptx;
     extern __shared__ uint8_t smem_raw[];
@@ -695,7 +708,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rollout_fused(const __grid_co
     const int M = p.M;
     uint8_t *A = base;
     uint8_t *ring = A + a_part_bytes(p) * (p.split == 3 ? 2u : 1u);
-    uint8_t *xbuf = ring + (size_t)a.stages * TC_CHUNK_MAX;
+    uint8_t *xbuf = ring + a.ring_bytes;
     uint64_t *bars = (uint64_t *)(xbuf + xbuf_bytes(TASK, M));
     uint64_t *full = bars;
     uint64_t *empty = bars + FU_MAX_STAGES;
@@ -925,12 +938,21 @@ __global__ void __launch_bounds__(256) k_metrics_replay2(EnvView v, const int64_
     }
 }
 
-int pick_stages(int task, const TcPlan &p, int optin, int *resident)
+// Weights resident (one barrier per chunk, the image packed end to end) when
+// a step's chunks fit the barrier set and the image fits beside the A
+// operand; else the largest streaming ring of TC_CHUNK_MAX stages.
+int pick_stages(int task, const TcPlan &p, int optin, int *resident, uint32_t *ring_bytes)
 {
     const int nps = chunks_per_step(p);
+    if (nps <= FU_MAX_STAGES && fused_smem(task, p, p.agent_bytes) <= (uint32_t)optin) {
+        *resident = 1;
+        *ring_bytes = p.agent_bytes;
+        return nps;
+    }
     for (int s = FU_MAX_STAGES; s >= 2; --s) {
-        if (fused_smem(task, p, s) <= (uint32_t)optin) {
-            *resident = nps <= s ? 1 : 0;
+        if (fused_smem(task, p, (uint32_t)s * TC_CHUNK_MAX) <= (uint32_t)optin) {
+            *resident = 0;
+            *ring_bytes = (uint32_t)s * TC_CHUNK_MAX;
             return s;
         }
     }
@@ -954,10 +976,11 @@ bool tc_rollout_supported(const fr_env *env, const fr_ensemble *e)
             return false;
     }
     int optin = 0, resident = 0;
+    uint32_t ring_bytes = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, env->ctx->device) !=
         cudaSuccess)
         return false;
-    return pick_stages(v.task, p, optin, &resident) > 0;
+    return pick_stages(v.task, p, optin, &resident, &ring_bytes) > 0;
 }
 
 // The first fused kernel's largest ring for this pair (0: the kernel does not
@@ -967,10 +990,11 @@ int tc_rollout_max_stages(const fr_env *env, const fr_ensemble *e, int *chunks_p
 {
     if (!tc_rollout_supported(env, e)) return 0;
     int optin = 0, resident = 0;
+    uint32_t ring_bytes = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, env->ctx->device) != cudaSuccess)
         return 0;
     *chunks_per_step_out = chunks_per_step(e->tc->plan);
-    return pick_stages(env->v.task, e->tc->plan, optin, &resident);
+    return pick_stages(env->v.task, e->tc->plan, optin, &resident, &ring_bytes);
 }
 
 int tc_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, double *metrics,
@@ -979,14 +1003,15 @@ int tc_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     const EnvView &v = env->v;
     const TcPlan &p = e->tc->plan;
     int optin = 0, resident = 0;
+    uint32_t ring_bytes = 0;
     FR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, env->ctx->device));
-    int stages = pick_stages(v.task, p, optin, &resident);
+    int stages = pick_stages(v.task, p, optin, &resident, &ring_bytes);
     FR_CHECK(stages > 0, FR_EINVAL, "fused rollout: plan does not fit in shared memory");
     if (env->tune_set && env->tune_stages >= 2 && env->tune_stages < stages) {
-        // an autotuned ring: fewer stages; weights stay resident only while a
-        // whole step's chunks still fit
+        // an autotuned ring: fewer stages, the weights streamed
         stages = env->tune_stages;
-        resident = chunks_per_step(p) <= stages ? 1 : 0;
+        resident = 0;
+        ring_bytes = (uint32_t)stages * TC_CHUNK_MAX;
     }
     if (T == 0) {
         if (metrics) FR_CUDA(launch_env_metrics(v, metrics, s));
@@ -1013,6 +1038,7 @@ int tc_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     a.T = T;
     a.stages = stages;
     a.resident = resident;
+    a.ring_bytes = ring_bytes;
     a.tr_obs = traj->obs;
     a.obs_ld = traj->obs_ld ? traj->obs_ld : v.D;
     a.tr_act = traj->act;
@@ -1023,7 +1049,7 @@ int tc_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     a.err = e->tc->err;
     a.ex = explore_of(env, env->explore_step);
 
-    const uint32_t smem = fused_smem(v.task, p, stages);
+    const uint32_t smem = fused_smem(v.task, p, ring_bytes);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)p.M, ceil_div(v.N, 128), 1);
     cfg.blockDim = dim3(FU_THREADS, 1, 1);
