@@ -512,17 +512,41 @@ __device__ void fused_env(const FusedArgs &a, uint32_t tmem, uint8_t *A, uint8_t
                 int best = 0;
                 for (int i = 1; i < ly.fout && i < 3; ++i)
                     if (qv[i] > qv[best]) best = i;
-                for (int m = 0; m < M; ++m) st_cluster_u8(map_shared_rank(xoff, (uint32_t)m), (uint32_t)best);
+                // four rows' bytes in one word (lane 4k holds rows 4k..4k+3):
+                // this CTA's copy by a plain store, the others' by asynchronous
+                // stores that complete their bytes on that CTA's barrier
+                uint32_t w4 = (uint32_t)best;
+                w4 |= (uint32_t)__shfl_down_sync(FULL_MASK, best, 1) << 8;
+                w4 |= (uint32_t)__shfl_down_sync(FULL_MASK, best, 2) << 16;
+                w4 |= (uint32_t)__shfl_down_sync(FULL_MASK, best, 3) << 24;
+                if ((lane & 3) == 0) {
+                    for (int m = 0; m < M; ++m) {
+                        if (m == agent)
+                            asm volatile("st.shared.u32 [%0], %1;" ::"r"(xoff), "r"(w4) : "memory");
+                        else
+                            st_async_b32(map_shared_rank(xoff, (uint32_t)m), w4,
+                                         map_shared_rank(smem_u32(&xready[b]), (uint32_t)m));
+                    }
+                }
             }
-            __syncwarp();                                  // the warp's stores precede lane 0's release
-            if (lane == 0) {
-                fence_acq_rel_cluster();                   // one release, then relaxed arrivals
-                for (int m = 0; m < M; ++m)
-                    mbar_arrive_remote_relaxed(map_shared_rank(smem_u32(&xready[b]), (uint32_t)m));
+            if (TASK == FR_TASK_STOCK) {
+                __syncwarp();                              // the warp's stores precede lane 0's release
+                if (lane == 0) {
+                    fence_acq_rel_cluster();               // one release, then relaxed arrivals
+                    for (int m = 0; m < M; ++m)
+                        mbar_arrive_remote_relaxed(map_shared_rank(smem_u32(&xready[b]), (uint32_t)m));
+                }
+            } else {
+                __syncwarp();                              // the own copy precedes the local arrival
+                if (lane == 0) mbar_arrive(&xready[b]);
             }
         }
          // ----------------------------------------- 3. every agent's output in
         warp_wait(&xready[b], (uint32_t)(s >> 1) & 1u, abort, a.err, 32u, true);
+        // crypto: arm this buffer's next use (step s + 2) with the other
+        // CTAs' bytes; every byte of that use depends on this wait
+        if (TASK == FR_TASK_CRYPTO && warp == 2 && lane == 0 && !*abort)
+            mbar_arrive_expect_tx(&xready[b], (uint32_t)(M - 1) * 128u);
         if (e < 0) continue;
 
         // ------------------------------------ 4. combine, trade, reward, log
@@ -681,6 +705,13 @@ __device__ void fused_env(const FusedArgs &a, uint32_t tmem, uint8_t *A, uint8_t
         if (w_log) a.vlog[row] = vlog;
     }
 
+    // crypto: the other CTAs' asynchronous stores of the last two steps have
+    // landed before this CTA can exit, also after a wait gave up (bounded)
+    if (TASK == FR_TASK_CRYPTO && warp == 2 && lane == 0) {
+        volatile int no_abort = 0;
+        for (int s = a.T > 2 ? a.T - 2 : 0; s < a.T; ++s)
+            mbar_wait_cluster(&xready[s & 1], (uint32_t)(s >> 1) & 1u, &no_abort, a.err, 32u, TC_WAIT_NS);
+    }
     // state back to global memory (steps and accumulators: metrics pass)
     if (agent == 0 && e >= 0) {
         v.cash[e] = cash;
@@ -730,8 +761,17 @@ __global__ void __launch_bounds__(FU_THREADS, TASK == FR_TASK_CRYPTO ? 3 : 1)
         }
         mbar_init(acc_full, 1);
         mbar_init(a_ready, 128);
-        mbar_init(&xready[0], (uint32_t)(M * 4));        // one arrival per env warp per CTA
-        mbar_init(&xready[1], (uint32_t)(M * 4));
+        if (TASK == FR_TASK_STOCK) {
+            mbar_init(&xready[0], (uint32_t)(M * 4));    // one arrival per env warp per CTA
+            mbar_init(&xready[1], (uint32_t)(M * 4));
+        } else {
+            // this CTA's 4 env warps plus one arming arrival per use that
+            // expects the other CTAs' bytes; the first use of each armed here
+            mbar_init(&xready[0], 5u);
+            mbar_init(&xready[1], 5u);
+            mbar_arrive_expect_tx(&xready[0], (uint32_t)(M - 1) * 128u);
+            mbar_arrive_expect_tx(&xready[1], (uint32_t)(M - 1) * 128u);
+        }
         mbar_init(drain, 1);
         *abort = 0;
         fence_mbar_init();
