@@ -14,17 +14,20 @@ namespace fr {
 constexpr unsigned FULL_MASK = 0xffffffffu;
 
 // Per-asset price after the basis-point change, rounded half up, >= 1 cent.
+// close >= 1 (checked at market creation) and bps >= -100, so the numerator
+// is positive and the division is done unsigned (fewer instructions than the
+// signed one, same quotient).
 __device__ __forceinline__ int64_t perturb(int64_t close, int bps)
 {
-    const int64_t num = close * (int64_t)(BPS_ONE + bps) + BPS_ONE / 2;
-    const int64_t p = num / BPS_ONE;
+    const uint64_t num = (uint64_t)close * (uint64_t)(BPS_ONE + bps) + (uint64_t)(BPS_ONE / 2);
+    const int64_t p = (int64_t)(num / (uint64_t)BPS_ONE);
     return p < 1 ? 1 : p;
 }
 
-// ceil(g * fee_bps / 1e4) for g >= 0
+// ceil(g * fee_bps / 1e4) for g >= 0, fee_bps >= 0 (unsigned division)
 __device__ __forceinline__ int64_t fee_of(int64_t g, int fee_bps)
 {
-    return (g * (int64_t)fee_bps + (BPS_ONE - 1)) / BPS_ONE;
+    return (int64_t)(((uint64_t)g * (uint64_t)fee_bps + (uint64_t)(BPS_ONE - 1)) / (uint64_t)BPS_ONE);
 }
 
 __device__ __forceinline__ int64_t cost_of(int64_t n, int64_t p, int fee_bps)

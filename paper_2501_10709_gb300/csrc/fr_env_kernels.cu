@@ -99,11 +99,8 @@ __global__ void __launch_bounds__(kStepEnvs * 32, 2) k_stock_step(EnvView v, con
             }
             cash += warp_sum_redux(net);
             const int64_t want = q > 0 ? (int64_t)q : 0;
-            int64_t full = 0, one = 0, nb = 0;
-            if (want > 0) {
-                full = cost_of(want, p, fee);
-                one = cost_of(1, p, fee);
-            }
+            int64_t full = 0, nb = 0;
+            if (want > 0) full = cost_of(want, p, fee);
             unsigned pending = __ballot_sync(FULL_MASK, want > 0);
             const int64_t all = warp_sum_redux(full);
             if (all <= cash) {
@@ -112,6 +109,8 @@ __global__ void __launch_bounds__(kStepEnvs * 32, 2) k_stock_step(EnvView v, con
                 pending = 0u;
             }
             int rank = lane;                     // execution position of this lane's order
+            // the one-share cost only matters when not every order fits
+            const int64_t one = pending && want > 0 ? cost_of(1, p, fee) : 0;
             int64_t bw = want, bf = full, bo = one, bp = p;
             if (BYSIZE && pending) {
                 // rank: orders with a larger count, or an equal count at a
