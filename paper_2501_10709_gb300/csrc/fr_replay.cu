@@ -97,6 +97,31 @@ struct RpBuf {
     int D, Dp, K, Kp, act_u8;
 };
 
+// Copy two rows of D floats (either pair may be absent: NULL source or
+// destination) by one warp, with up to ten loads per row and lane in flight
+// before the stores (a plain strided loop keeps one per row in flight).
+__device__ __forceinline__ void rp_copy2(float *dst, const float *src, float *ndst, const float *nsrc, int D,
+                                         int lane)
+{
+    for (int k0 = 0; k0 < D; k0 += 320) {
+        float x[10], y[10];
+#pragma unroll
+        for (int u = 0; u < 10; ++u) {
+            const int k = k0 + lane + 32 * u;
+            x[u] = (src && k < D) ? __ldg(src + k) : 0.0f;
+            y[u] = (nsrc && k < D) ? __ldg(nsrc + k) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 10; ++u) {
+            const int k = k0 + lane + 32 * u;
+            if (k < D) {
+                if (dst) dst[k] = x[u];
+                if (ndst) ndst[k] = y[u];
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(RP_ROWS) k_rp_scatter(RpBuf b, int64_t rows, int N, int ld, const float *obs,
                                                         const void *act, const float *rew, const uint8_t *done,
                                                         const float *last_obs, const uint8_t *live0,
@@ -125,12 +150,7 @@ __global__ void __launch_bounds__(RP_ROWS) k_rp_scatter(RpBuf b, int64_t rows, i
         const int64_t e = row % N;
         const float *src = obs + row * ld;
         const float *nsrc = row + N < rows ? obs + (row + N) * ld : last_obs + e * ld;   // t < T - 1: obs[t+1][e]
-        float *dst = b.obs + slot * b.Dp;
-        float *ndst = b.next + slot * b.Dp;
-        for (int k = lane; k < b.D; k += 32) {
-            dst[k] = __ldg(src + k);
-            ndst[k] = __ldg(nsrc + k);
-        }
+        rp_copy2(b.obs + slot * b.Dp, src, b.next + slot * b.Dp, nsrc, b.D, lane);
         if (b.act_u8) {
             if (lane == 0) ((uint8_t *)b.act)[slot] = ((const uint8_t *)act)[row];
         } else {
@@ -165,10 +185,8 @@ __global__ void __launch_bounds__(256) k_rp_sample(RpBuf b, int B, uint32_t k0, 
         return;
     }
     const int64_t slot = (total - size + idx) % b.C;
-    for (int k = lane; k < b.D; k += 32) {
-        if (obs) obs[i * b.D + k] = b.obs[slot * b.Dp + k];
-        if (next) next[i * b.D + k] = b.next[slot * b.Dp + k];
-    }
+    rp_copy2(obs ? obs + i * b.D : nullptr, obs ? b.obs + slot * b.Dp : nullptr, next ? next + i * b.D : nullptr,
+             next ? b.next + slot * b.Dp : nullptr, b.D, lane);
     if (act) {
         if (b.act_u8) {
             if (lane == 0) ((uint8_t *)act)[i] = ((const uint8_t *)b.act)[slot];
