@@ -220,7 +220,16 @@ __device__ __forceinline__ void stock_obs_warp(const EnvView &v, int e, int lane
         o[1 + lane] = pv;
         o[1 + K + lane] = hv;
         const float *f = v.ind + (int64_t)d * I * K;
-        for (int i = 0; i < I; ++i) o[1 + 2 * K + i * K + lane] = act ? __ldg(f + i * K + lane) : 0.0f;
+        float *oi = o + 1 + 2 * K + lane;
+        if (I == 8) {                                    // the usual count: every load in flight
+            float fv[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) fv[i] = act ? __ldg(f + i * K + lane) : 0.0f;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) oi[i * K] = fv[i];
+        } else {
+            for (int i = 0; i < I; ++i) oi[i * K] = act ? __ldg(f + i * K + lane) : 0.0f;
+        }
     }
 }
 

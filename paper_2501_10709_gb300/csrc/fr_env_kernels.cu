@@ -203,7 +203,16 @@ __global__ void __launch_bounds__(kStepEnvs * 32, kStepBlocks) k_stock_step(EnvV
                 o[1 + lane] = live ? obs_scale(p_obs, 1e-4f) : 0.0f;
                 o[1 + K + lane] = live ? obs_scale(h, 1e-2f) : 0.0f;
                 const float *f = v.ind + (int64_t)(start + t_obs) * v.I * K;
-                for (int i = 0; i < v.I; ++i) o[1 + 2 * K + i * K + lane] = live ? __ldg(f + i * K + lane) : 0.0f;
+                float *oi = o + 1 + 2 * K + lane;
+                if (v.I == 8) {                          // the usual count: every load in flight
+                    float fv[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) fv[i] = live ? __ldg(f + i * K + lane) : 0.0f;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) oi[i * K] = fv[i];
+                } else {
+                    for (int i = 0; i < v.I; ++i) oi[i * K] = live ? __ldg(f + i * K + lane) : 0.0f;
+                }
             }
         }
     } else if (lane == 0) {
