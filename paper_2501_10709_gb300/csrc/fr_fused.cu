@@ -12,10 +12,15 @@
 //           every env thread then forms the anchored weighted mean
 //           (Sec. 5.2.1), discretises, trades, and builds the next
 //           observation row straight into the BF16 A operand;
-//   crypto: each CTA pushes its argmax (one byte per env); every env thread
-//           takes the majority vote (Sec. 5.2.2) and trades one lot.
-// Arrivals are remote mbarrier arrivals (release, cluster scope), waited on
-// with acquire at cluster scope.  No FP64 runs per step: each step's
+//   crypto: each CTA pushes its argmax (one byte per env, four rows per
+//           word); every env thread takes the majority vote (Sec. 5.2.2)
+//           and trades one lot.
+// Stock pushes are followed by remote mbarrier arrivals (release, cluster
+// scope); crypto pushes are asynchronous stores that complete transaction
+// bytes on the receiving barrier.  Both are waited on with acquire at
+// cluster scope.  When a step's weight chunks fit the barrier set, the
+// agent's weights stay resident, packed as in its image (crypto: about
+// 75 KB per CTA, three CTAs per SM).  No FP64 runs per step: each step's
 // post-trade value goes to a value log, and a follow-up kernel replays the
 // log in time order through the FP64 Welford / peak / drawdown accumulators.
 #include <cuda_fp16.h>

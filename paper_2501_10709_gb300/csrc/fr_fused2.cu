@@ -21,9 +21,11 @@
 // Env r of the tile is owned by the CTA of rank r mod 2M: one warp per env,
 // lane = asset, state in registers.  The owner combines the agents' actions
 // (anchored weighted mean, Sec. 5.2.1), discretises, trades, and writes the
-// env's next observation row straight into every CTA's A operand.  All
-// waits are mbarriers (remote arrivals released at cluster scope) bounded by
-// the global timer.  The shared buffers need no double buffering: every
+// env's next observation row straight into every CTA's A operand.  The
+// step's three cluster exchanges (observation rows, h1 halves, layer-3
+// partial sums) are asynchronous stores that complete transaction bytes on
+// the receiving CTA's mbarrier, armed once per phase; all waits are bounded
+// by the global timer.  The shared buffers need no double buffering: every
 // write of step s + 1 depends, through the step's chain, on every read of
 // step s.
 #include <cuda_fp16.h>
