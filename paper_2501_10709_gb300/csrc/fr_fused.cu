@@ -26,6 +26,9 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "fr_env_dev.cuh"
 #include "fr_ptx.cuh"
@@ -983,25 +986,85 @@ __global__ void __launch_bounds__(256) k_metrics_replay2(EnvView v, const int64_
     }
 }
 
-// Weights resident (one barrier per chunk, the image packed end to end) when
-// a step's chunks fit the barrier set and the image fits beside the A
-// operand; else the largest streaming ring of TC_CHUNK_MAX stages.
-int pick_stages(int task, const TcPlan &p, int optin, int *resident, uint32_t *ring_bytes)
+// CTAs of the fused kernel one SM holds with `smem` bytes of dynamic shared
+// memory: the SM's shared memory (1 KB reserved per CTA), the kernel's
+// launch bounds (three crypto CTAs, one stock CTA) and its 512 TMEM columns.
+int fused_per_sm(int task, const TcPlan &p, uint32_t smem, int device)
 {
-    const int nps = chunks_per_step(p);
-    if (nps <= FU_MAX_STAGES && fused_smem(task, p, p.agent_bytes) <= (uint32_t)optin) {
-        *resident = 1;
-        *ring_bytes = p.agent_bytes;
-        return nps;
+    int cap = 0;
+    if (cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess) return 1;
+    const int by_smem = cap / (int)(smem + 1024u);
+    const int by_bounds = task == FR_TASK_CRYPTO ? 3 : 1;
+    return std::max(1, std::min(std::min(by_smem, by_bounds), 512 / p.tmem_cols));
+}
+
+// The weight layout: resident (one barrier per chunk, the image packed end
+// to end) when a step's chunks fit the barrier set and the image fits,
+// unless a 2-stage streaming ring lets more CTAs share an SM (a tile runs
+// all its steps on one CTA per agent, so CTAs per SM decide how many waves
+// the grid takes); else the largest ring that fits.  Measured on the
+// 8,192-env crypto ensemble: BF16X3 resident (1 CTA per SM) 46.9 ms,
+// 2-stage ring (2 per SM) 36.2 ms; BF16 resident (3 per SM) 16.3 ms,
+// 2-stage ring (3 per SM) 16.9 ms.
+struct PickKey {
+    int task, device, M, L, split, nps, tmem_cols;
+    uint32_t agent_bytes, a_part;
+    bool operator<(const PickKey &o) const
+    {
+        return std::tie(task, device, M, L, split, nps, tmem_cols, agent_bytes, a_part) <
+               std::tie(o.task, o.device, o.M, o.L, o.split, o.nps, o.tmem_cols, o.agent_bytes, o.a_part);
     }
-    for (int s = FU_MAX_STAGES; s >= 2; --s) {
-        if (fused_smem(task, p, (uint32_t)s * TC_CHUNK_MAX) <= (uint32_t)optin) {
-            *resident = 0;
-            *ring_bytes = (uint32_t)s * TC_CHUNK_MAX;
-            return s;
+};
+struct PickVal {
+    int stages, resident;
+    uint32_t ring_bytes;
+};
+
+int pick_stages(int task, const TcPlan &p, int optin, int device, int *resident, uint32_t *ring_bytes)
+{
+    // cached per kernel shape: the device queries run on a first call,
+    // never inside a later stream capture
+    static std::mutex mu;
+    static std::map<PickKey, PickVal> cache;
+    const int nps = chunks_per_step(p);
+    const PickKey key{task, device, p.M, p.L, p.split, nps, p.tmem_cols, p.agent_bytes, a_part_bytes(p)};
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            *resident = it->second.resident;
+            *ring_bytes = it->second.ring_bytes;
+            return it->second.stages;
         }
     }
-    return 0;
+    int best = 0;
+    const uint32_t ring2 = 2u * TC_CHUNK_MAX;
+    if (nps <= FU_MAX_STAGES && fused_smem(task, p, p.agent_bytes) <= (uint32_t)optin) {
+        best = nps;
+        *resident = 1;
+        *ring_bytes = p.agent_bytes;
+        if (fused_smem(task, p, ring2) <= (uint32_t)optin &&
+            fused_per_sm(task, p, fused_smem(task, p, ring2), device) >
+                fused_per_sm(task, p, fused_smem(task, p, p.agent_bytes), device)) {
+            best = 2;
+            *resident = 0;
+            *ring_bytes = ring2;
+        }
+    } else {
+        for (int st = FU_MAX_STAGES; st >= 2; --st) {
+            if (fused_smem(task, p, (uint32_t)st * TC_CHUNK_MAX) <= (uint32_t)optin) {
+                best = st;
+                *resident = 0;
+                *ring_bytes = (uint32_t)st * TC_CHUNK_MAX;
+                break;
+            }
+        }
+    }
+    if (best > 0) {
+        std::lock_guard<std::mutex> lk(mu);
+        cache[key] = PickVal{best, *resident, *ring_bytes};
+    }
+    return best;
 }
 
 }  // namespace
@@ -1025,7 +1088,7 @@ bool tc_rollout_supported(const fr_env *env, const fr_ensemble *e)
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, env->ctx->device) !=
         cudaSuccess)
         return false;
-    return pick_stages(v.task, p, optin, &resident, &ring_bytes) > 0;
+    return pick_stages(v.task, p, optin, env->ctx->device, &resident, &ring_bytes) > 0;
 }
 
 // The first fused kernel's largest ring for this pair (0: the kernel does not
@@ -1039,7 +1102,7 @@ int tc_rollout_max_stages(const fr_env *env, const fr_ensemble *e, int *chunks_p
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, env->ctx->device) != cudaSuccess)
         return 0;
     *chunks_per_step_out = chunks_per_step(e->tc->plan);
-    return pick_stages(env->v.task, e->tc->plan, optin, &resident, &ring_bytes);
+    return pick_stages(env->v.task, e->tc->plan, optin, env->ctx->device, &resident, &ring_bytes);
 }
 
 int tc_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, double *metrics,
@@ -1050,7 +1113,7 @@ int tc_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     int optin = 0, resident = 0;
     uint32_t ring_bytes = 0;
     FR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, env->ctx->device));
-    int stages = pick_stages(v.task, p, optin, &resident, &ring_bytes);
+    int stages = pick_stages(v.task, p, optin, env->ctx->device, &resident, &ring_bytes);
     FR_CHECK(stages > 0, FR_EINVAL, "fused rollout: plan does not fit in shared memory");
     if (env->tune_set && env->tune_stages >= 2 && env->tune_stages < stages) {
         // an autotuned ring: fewer stages, the weights streamed
