@@ -292,7 +292,7 @@ ENV_STEP_BYTES = 377 + 1398
 # 2,048-env workload, from the ncu launch list of `bench.py --profile fused
 # --T 256` (profiles/fused_rollout_stock2_stock2048.md); the kernel is the
 # one this file times.
-K_ROLLOUT_STOCK2_DRAM_BYTES = 4.06e6
+K_ROLLOUT_STOCK2_DRAM_BYTES = 3.99e6
 
 
 def env_step_line(fr, ctx, mk, w, dev, stream, N=1 << 20, T=4, warm=2):
