@@ -43,6 +43,7 @@ extern "C" {
 #define FR_ECUDA (-5)       /* a CUDA runtime call failed                   */
 #define FR_ENOTREADY (-6)   /* asynchronous result not ready yet            */
 #define FR_ENOTFOUND (-7)   /* unknown ticket                               */
+#define FR_ECANCELED (-8)   /* a request cancelled before it completed      */
 
 #define FR_TASK_STOCK 0
 #define FR_TASK_CRYPTO 1
@@ -639,6 +640,9 @@ typedef struct {
     uint64_t seed;
     int32_t want_traj;        /* must be 0                                  */
     double *metrics;          /* host [n_envs][3]                           */
+    double timeout_s;         /* > 0: a request not complete this long after
+                                 submit ends with status FR_ETIMEDOUT (checked
+                                 at chunk boundaries); 0 = none             */
 } fr_request;
 
 typedef struct {
@@ -654,6 +658,13 @@ int backtest_submit(fr_server *srv, const fr_request *req, uint64_t *ticket);
  * FR_OK, *done = 1, *out filled, and the ticket is released (a later poll
  * of it returns FR_ENOTFOUND).  Unknown ticket: FR_ENOTFOUND. */
 int backtest_poll(fr_server *srv, uint64_t ticket, fr_result *out, int32_t *done);
+
+/* Cancel a request.  Queued: it completes at once with status FR_ECANCELED.
+ * Running: it is retired at the next chunk boundary with status
+ * FR_ECANCELED (its slots freed, its metrics buffer left unwritten).
+ * Complete but not yet polled: no effect.  Either way the ticket is polled
+ * as usual.  Unknown ticket: FR_ENOTFOUND.  Other requests are unaffected. */
+int backtest_cancel(fr_server *srv, uint64_t ticket);
 
 typedef struct {
     uint64_t submitted, completed, queued, running;

@@ -25,7 +25,7 @@ __all__ = [
     "ensemble_act", "ensemble_act_noalloc", "ensemble_device_errors", "rollout", "env_set_rollout_path", "env_set_kernel_timing", "env_last_kernel_ms", "env_set_tile_packing",
     "env_tile_packing_efficiency", "ensemble_set_weights", "ensemble_validate", "trajectory_metrics", "env_set_exploration",
     "EXPLORE_NONE", "EXPLORE_GAUSSIAN", "EXPLORE_EPS_GREEDY", "Server", "fr_server_create", "backtest_submit",
-    "backtest_poll", "fr_server_stats", "FrError", "lib", "market_indicators", "fr_market_indicators",
+    "backtest_poll", "backtest_cancel", "fr_server_stats", "FrError", "lib", "market_indicators", "fr_market_indicators",
     "env_perturb", "ensemble_set_act_scales", "ensemble_get_act_scales", "ensemble_calibrate_sync",
     "Replay", "replay_create", "replay_push", "replay_sample", "replay_size", "ensemble_q", "ensemble_q_targets",
     "HEAD_Q", "HEAD_DUELING", "env_autotune", "env_tune_clear", "env_tune_set",
@@ -528,10 +528,11 @@ def fr_server_create(ctx: Ctx, market: Market, ens: Ensemble, *, capacity: int, 
 
 
 def backtest_submit(srv: Server, *, n_envs: int, window: int, start: int, start_stride: int = 0,
-                    n_assets: int = 0, bps_range: int = 0, seed: int = 0) -> int:
+                    n_assets: int = 0, bps_range: int = 0, seed: int = 0, timeout_s: float = 0.0) -> int:
     met = np.zeros((int(n_envs), 3), dtype=np.float64)
     r = _lib.Request(int(n_envs), int(window), int(start), int(start_stride), int(n_assets),
-                     int(bps_range), int(seed) & (2**64 - 1), 0, met.ctypes.data_as(C.c_void_p))
+                     int(bps_range), int(seed) & (2**64 - 1), 0, met.ctypes.data_as(C.c_void_p),
+                     float(timeout_s))
     t = C.c_uint64()
     _lib.check(lib().backtest_submit(srv, C.byref(r), C.byref(t)), "backtest_submit")
     srv._pending[t.value] = met
@@ -550,6 +551,12 @@ def backtest_poll(srv: Server, ticket: int):
     met = srv._pending.pop(int(ticket))
     return {"status": res.status, "n_envs": res.n_envs, "queue_s": res.queue_s,
             "latency_s": res.latency_s, "metrics": met}
+
+
+def backtest_cancel(srv: Server, ticket: int):
+    """Cancel a queued or running request (its poll then reports status
+    FR_ECANCELED); no effect on a complete one."""
+    _lib.check(lib().backtest_cancel(srv, C.c_uint64(int(ticket))), "backtest_cancel")
 
 
 def fr_server_stats(srv: Server) -> dict:

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "libfinrl_gb300.so")
 
 FR_OK, FR_EINVAL, FR_ENOMEM, FR_EBUSY, FR_ETIMEDOUT, FR_ECUDA, FR_ENOTREADY, FR_ENOTFOUND = (
     0, -1, -2, -3, -4, -5, -6, -7)
+FR_ECANCELED = -8
 TASK_STOCK, TASK_CRYPTO = 0, 1
 ACT_I32_SHARES, ACT_F32_UNIT, ACT_U8_DISCRETE = 0, 1, 2
 PREC_FP32, PREC_BF16, PREC_FP8, PREC_BF16X3 = 0, 1, 2, 3
@@ -78,7 +79,7 @@ class ServerDesc(C.Structure):
 class Request(C.Structure):
     _fields_ = [("n_envs", i32), ("window", i32), ("start", i32), ("start_stride", i32),
                 ("n_assets", i32), ("bps_range", i32), ("seed", u64), ("want_traj", i32),
-                ("metrics", vp)]
+                ("metrics", vp), ("timeout_s", f64)]
 
 
 class Result(C.Structure):
@@ -131,6 +132,7 @@ SIGNATURES = {
     "fr_server_destroy": (None, [vp]),
     "backtest_submit": (i32, [vp, vp, vp]),
     "backtest_poll": (i32, [vp, u64, vp, vp]),
+    "backtest_cancel": (i32, [vp, u64]),
     "fr_server_stats_get": (i32, [vp, vp]),
     "fr_fault_inject": (i32, [i32, i32, i32]),
     "fr_wait_selftest": (i32, [vp, i32, vp, vp]),

@@ -82,7 +82,16 @@ struct SrvReq {
     int steps_run = 0;
     double t_submit = 0, t_admit = 0, t_done = 0;
     int status = FR_OK;
+    bool cancel = false;       // set by backtest_cancel while running
 };
+
+// FR_OK, or why a request must leave now: cancelled or past its deadline.
+int leave_reason(const SrvReq *q, double t)
+{
+    if (q->cancel) return FR_ECANCELED;
+    if (q->r.timeout_s > 0.0 && t - q->t_submit > q->r.timeout_s) return FR_ETIMEDOUT;
+    return FR_OK;
+}
 
 }  // namespace
 }  // namespace fr
@@ -223,6 +232,67 @@ cudaError_t fail_running(fr_server *s, int rc)
     return cudaSuccess;
 }
 
+// At a chunk boundary: queued requests past their deadline finish at once;
+// running ones that were cancelled or are past their deadline are parked
+// and their slots freed.  Returns a CUDA status (parking the slots).
+cudaError_t retire_leavers(fr_server *s)
+{
+    std::vector<SrvReq *> gone;
+    std::vector<int> why;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        const double t = now_s();
+        for (auto it = s->queue.begin(); it != s->queue.end();) {
+            SrvReq *q = *it;
+            const int st = leave_reason(q, t);
+            if (st == FR_OK) {
+                ++it;
+                continue;
+            }
+            q->status = st;
+            q->t_done = t;
+            s->live.erase(q->ticket);
+            s->finished[q->ticket] = q;
+            s->st.failed += 1;
+            it = s->queue.erase(it);
+        }
+        s->st.queued = s->queue.size();
+        for (SrvReq *q : s->running) {
+            const int st = leave_reason(q, t);
+            if (st != FR_OK) {
+                gone.push_back(q);
+                why.push_back(st);
+            }
+        }
+    }
+    if (gone.empty()) return cudaSuccess;
+    int n = 0;
+    for (SrvReq *q : gone)
+        for (int32_t e : q->slots) s->h_slot[n++] = e;
+    cudaError_t ce = cudaMemcpyAsync(s->d_slot, s->h_slot, 4ull * n, cudaMemcpyHostToDevice, s->stream);
+    if (ce == cudaSuccess) {
+        k_slot_park<<<ceil_div(n, 128), 128, 0, s->stream>>>(s->env->v, s->d_slot, n);
+        ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
+    if (ce != cudaSuccess) return ce;
+    std::lock_guard<std::mutex> lk(s->mu);
+    const double t = now_s();
+    for (size_t i = 0; i < gone.size(); ++i) {
+        SrvReq *q = gone[i];
+        q->status = why[i];
+        q->t_done = t;
+        s->running.erase(std::find(s->running.begin(), s->running.end(), q));
+        s->free_slots.insert(s->free_slots.end(), q->slots.begin(), q->slots.end());
+        s->live.erase(q->ticket);
+        s->finished[q->ticket] = q;
+        s->st.failed += 1;
+    }
+    std::sort(s->free_slots.begin(), s->free_slots.end());
+    s->st.running = s->running.size();
+    return cudaSuccess;
+}
+
 void worker_loop(fr_server *s)
 {
     cudaSetDevice(s->ctx->device);
@@ -230,6 +300,14 @@ void worker_loop(fr_server *s)
     const int N = s->d.capacity;
     for (;;) {
         std::vector<SrvReq *> admitted;
+        {
+            const cudaError_t rc = retire_leavers(s);
+            if (rc != cudaSuccess) {
+                cuda_fail(rc, "server: retiring cancelled requests");
+                fail_all(s, FR_ECUDA);
+                return;
+            }
+        }
         {
             std::unique_lock<std::mutex> lk(s->mu);
             s->cv.wait_for(lk, std::chrono::milliseconds(2),
@@ -450,6 +528,8 @@ int backtest_submit(fr_server *s, const fr_request *r, uint64_t *ticket)
     FR_CHECK(r->n_envs >= 1 && r->window >= 2 && r->start >= 0 && r->start_stride >= 0 && r->metrics, FR_EINVAL,
              "backtest_submit: need n_envs >= 1, window >= 2, start >= 0, start_stride >= 0, metrics");
     FR_CHECK(!r->want_traj, FR_EINVAL, "backtest_submit: the server returns metrics only (want_traj must be 0)");
+    FR_CHECK(r->timeout_s >= 0.0 && r->timeout_s < 1e12, FR_EINVAL, "backtest_submit: timeout_s %g not in [0, 1e12)",
+             r->timeout_s);
     const fr_market *m = s->mkt;
     const bool stock = m->task == FR_TASK_STOCK;
     const int64_t horizon = stock ? m->n_days : m->S;
@@ -512,6 +592,34 @@ int backtest_poll(fr_server *s, uint64_t ticket, fr_result *out, int32_t *done)
     if (s->live.count(ticket)) return FR_ENOTREADY;
     set_error("backtest_poll: unknown ticket %llu", (unsigned long long)ticket);
     return FR_ENOTFOUND;
+}
+
+int backtest_cancel(fr_server *s, uint64_t ticket)
+{
+    FR_NVTX("backtest_cancel");
+    FR_CHECK(s, FR_EINVAL, "backtest_cancel: NULL server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->finished.count(ticket)) return FR_OK;                  // complete: no effect
+    auto it = s->live.find(ticket);
+    if (it == s->live.end()) {
+        set_error("backtest_cancel: unknown ticket %llu", (unsigned long long)ticket);
+        return FR_ENOTFOUND;
+    }
+    SrvReq *q = it->second;
+    auto qi = std::find(s->queue.begin(), s->queue.end(), q);
+    if (qi != s->queue.end()) {                                   // queued: finish now
+        s->queue.erase(qi);
+        q->status = FR_ECANCELED;
+        q->t_done = now_s();
+        s->live.erase(it);
+        s->finished[ticket] = q;
+        s->st.failed += 1;
+        s->st.queued = s->queue.size();
+    } else {
+        q->cancel = true;                                         // running: next chunk boundary
+    }
+    s->cv.notify_all();
+    return FR_OK;
 }
 
 int fr_server_stats_get(fr_server *s, fr_server_stats *out)

@@ -149,3 +149,62 @@ def test_server_errors(ctx, dev):
         bad = fr.ensemble_create(ctx, (301, 64, 3), synth.actor_params((301, 64, 3), 3),
                                  combine=fr.COMBINE_VOTE, out_act=0)
         fr.fr_server_create(ctx, mk, bad, capacity=8)
+
+
+def _crypto_server(ctx, capacity=64, chunk=8):
+    w = synth.workload_crypto(N=64, T=64, S=200_000)
+    mk = fr.fr_market_create(ctx, w.market)
+    ens = fr.ensemble_create(ctx, w.dims, w.params, precision=fr.PREC_BF16, combine=fr.COMBINE_VOTE, out_act=0)
+    return mk, ens, fr.fr_server_create(ctx, mk, ens, capacity=capacity, chunk_steps=chunk)
+
+
+def _until(pred, timeout_s=60.0):
+    t0 = time.time()
+    while not pred():
+        assert time.time() - t0 < timeout_s
+        time.sleep(0.001)
+
+
+def test_cancel_queued_and_running_requests(ctx, dev):
+    # a 100,000-step request runs for thousands of chunks, so it is surely
+    # still running when it is cancelled; the request queued behind it then
+    # runs and is exact
+    mk, ens, srv = _crypto_server(ctx)
+    long_req = dict(n_envs=64, window=100_000, start=4000, start_stride=7)
+    short = dict(n_envs=64, window=300, start=9000, start_stride=11)
+    ta = fr.backtest_submit(srv, **long_req)
+    _until(lambda: fr.fr_server_stats(srv)["running"] == 1)
+    tb = fr.backtest_submit(srv, **short)                        # queued behind the long one
+    tc = fr.backtest_submit(srv, **short)
+    fr.backtest_cancel(srv, tc)                                  # queued: finishes at once
+    rc = fr.backtest_poll(srv, tc)
+    assert rc is not None and rc["status"] == _lib.FR_ECANCELED
+    fr.backtest_cancel(srv, ta)                                  # running: next chunk boundary
+    res = _wait_all(srv, [ta, tb])
+    with pytest.raises(fr.FrError) as ei:
+        fr.backtest_cancel(srv, 10 ** 9)
+    assert ei.value.code == _lib.FR_ENOTFOUND
+    st = fr.fr_server_stats(srv)
+    srv.close()
+    assert res[ta]["status"] == _lib.FR_ECANCELED
+    assert res[tb]["status"] == _lib.FR_OK
+    assert st["failed"] == 2 and st["completed"] == 1
+    assert np.array_equal(res[tb]["metrics"], _standalone(ctx, mk, ens, dev, short, 1, stock=False))
+
+
+def test_request_timeouts_running_and_queued(ctx, dev):
+    mk, ens, srv = _crypto_server(ctx)
+    long_req = dict(n_envs=64, window=100_000, start=4000, start_stride=7)
+    short = dict(n_envs=64, window=300, start=9000, start_stride=11)
+    ta = fr.backtest_submit(srv, **long_req, timeout_s=0.05)     # times out while running
+    _until(lambda: fr.fr_server_stats(srv)["running"] == 1)
+    tb = fr.backtest_submit(srv, **short, timeout_s=0.01)        # times out while queued
+    tc = fr.backtest_submit(srv, **short)                        # no deadline: runs after
+    res = _wait_all(srv, [ta, tb, tc])
+    with pytest.raises(fr.FrError):
+        fr.backtest_submit(srv, **short, timeout_s=-1.0)
+    srv.close()
+    assert res[ta]["status"] == _lib.FR_ETIMEDOUT
+    assert res[tb]["status"] == _lib.FR_ETIMEDOUT
+    assert res[tc]["status"] == _lib.FR_OK
+    assert np.array_equal(res[tc]["metrics"], _standalone(ctx, mk, ens, dev, short, 1, stock=False))
