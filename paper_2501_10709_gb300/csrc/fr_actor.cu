@@ -22,8 +22,8 @@
 // stages (4 MMAs per wait for a 256-wide layer), the descriptors advance by
 // constant offsets, and the epilogue keeps four TMEM loads in flight.  The
 // MMAs of a layer still wait for the previous layer's epilogue.  Neither
-// multicasting the weights over a 4-CTA cluster nor cp.async producers made
-// this kernel faster.
+// one weight copy delivered to all CTAs of a 4-CTA cluster nor cp.async
+// producers made this kernel faster.
 // The products, their order and every rounding are those of the
 // single-agent kernel, so both give identical results.
 #include <cuda_bf16.h>
