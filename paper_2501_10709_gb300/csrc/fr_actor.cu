@@ -74,28 +74,64 @@ __host__ __device__ inline TaLayout ta_layout(const TcPlan &p, int stages, uint3
 }
 
 // fp32 obs [n][ld] (first fin columns) -> BF16 tiles [tiles][K/8][128][8]
-__global__ void k_obs_tiles(const float *__restrict__ obs, int ld, int n, int fin, int nchunks, uint4 *out)
+// (the BF16 operand of the large-batch kernels), HBM-bound: a block stages
+// 32 observation rows in shared memory with coalesced loads (consecutive
+// threads, consecutive floats), then each thread writes 16-byte core-matrix
+// rows; within a core column row r sits at byte 16 r, so a warp's 32 rows
+// are 512 contiguous bytes.  Reads from the stage are conflict-free for odd
+// row lengths (lanes r and r' hit banks 301 r and 301 r' mod 32).
+constexpr int OT_ROWS = 32;
+constexpr int OT_THREADS = 256;
+
+__global__ void __launch_bounds__(OT_THREADS) k_obs_tiles2(const float *__restrict__ obs, int ld, int n, int fin,
+                                                             int nchunks, uint4 *out)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t tiles = (n + 127) / 128;
-    if (i >= tiles * nchunks * 128) return;
-    const int row = (int)(i % 128);
-    const int c = (int)((i / 128) % nchunks);
-    const int64_t tile = i / (128 * (int64_t)nchunks);
-    const int64_t g = tile * 128 + row;
-    float v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        const int k = c * 8 + u;
-        v[u] = (g < n && k < fin) ? __ldg(obs + g * ld + k) : 0.0f;
+    extern __shared__ float st[];                       // [OT_ROWS][fin]
+    const int64_t r0 = (int64_t)blockIdx.x * OT_ROWS;
+    const int rows = (int)max((int64_t)0, min((int64_t)OT_ROWS, (int64_t)n - r0));
+    if (ld == fin && (((uintptr_t)obs) & 15u) == 0) {
+        // packed rows: the block's rows are one span starting 16-byte aligned
+        // (32 rows x fin floats is a multiple of 4 floats); float4 loads, four
+        // in flight per thread, the span's tail and the rows past n scalar
+        const int tot = OT_ROWS * fin, have = rows * fin, have4 = have / 4;
+        const float4 *src4 = (const float4 *)(obs + r0 * ld);
+        float4 *st4 = (float4 *)st;
+        int i = threadIdx.x;
+        for (; i + 3 * OT_THREADS < have4; i += 4 * OT_THREADS) {
+            const float4 a = __ldg(src4 + i), b = __ldg(src4 + i + OT_THREADS), c = __ldg(src4 + i + 2 * OT_THREADS),
+                         d = __ldg(src4 + i + 3 * OT_THREADS);
+            st4[i] = a;
+            st4[i + OT_THREADS] = b;
+            st4[i + 2 * OT_THREADS] = c;
+            st4[i + 3 * OT_THREADS] = d;
+        }
+        for (; i < have4; i += OT_THREADS) st4[i] = __ldg(src4 + i);
+        for (int k = 4 * have4 + threadIdx.x; k < tot; k += OT_THREADS) st[k] = k < have ? __ldg(obs + r0 * ld + k) : 0.0f;
+    } else {
+        for (int i = threadIdx.x; i < OT_ROWS * fin; i += OT_THREADS) {
+            const int r = i / fin, k = i - r * fin;
+            st[i] = r < rows ? __ldg(obs + (r0 + r) * ld + k) : 0.0f;
+        }
     }
-    uint32_t w[4];
+    __syncthreads();
+    const int64_t tile = r0 / 128;
+    const int rt = (int)(r0 % 128);                     // first row's index within its tile
+    for (int i = threadIdx.x; i < OT_ROWS * nchunks; i += OT_THREADS) {
+        const int c = i / OT_ROWS, r = i % OT_ROWS;
+        float v[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * u], v[2 * u + 1]);
-        w[u] = *(const uint32_t *)&b;
+        for (int u = 0; u < 8; ++u) {
+            const int k = c * 8 + u;
+            v[u] = k < fin ? st[r * fin + k] : 0.0f;
+        }
+        uint32_t w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * u], v[2 * u + 1]);
+            w[u] = *(const uint32_t *)&b;
+        }
+        out[(tile * nchunks + c) * 128 + rt + r] = make_uint4(w[0], w[1], w[2], w[3]);
     }
-    out[i] = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 // fp32 obs [n][ld] -> E4M3 tiles [tiles][K/16][128][16] of obs * inv (the
@@ -389,6 +425,393 @@ k_tc_actor(const __grid_constant__ TcPlan plan, const uint8_t *__restrict__ img,
     }
 }
 
+// ------------------------------------------------------------------------
+// k_tc_actor2: the BF16 large-batch forward, pipelined over half layers,
+// with the hidden activations in tensor memory.  Persistent: CTA b takes
+// tiles b, b + grid, ...; each tile's M agents are M "chains" of L layers.
+//
+// Each layer's outputs are computed in at most two "groups" of <= 128
+// columns (a 256-wide layer in two halves), group after group for the whole
+// batch.  Tensor memory (512 columns) holds two 128-column accumulator
+// regions, used by groups alternately, and two 128-column BF16 operand
+// buffers H0 / H1, used by hidden layers alternately (hidden layer lambda of
+// the batch writes H[lambda & 1]; the next layer reads its A operand from
+// there).  While the epilogue turns group g's accumulator into its half of
+// the next layer's operand, the tensor cores run group g + 1; the next
+// layer's first group starts on the K steps whose operand half is ready.
+//
+// Warps: 0 producer (observation tiles and the weight ring, one bulk copy
+// per stage from the grouped weight image), 1 MMA issuer, 2.. epilogue
+// (warp w reads TMEM lane quarter w % 4 and every TB_SUBS-th 16-column block
+// of a group).  Producer and MMA warps run warp-uniform loops and one
+// elected lane issues.  Per output element the products, their order and
+// every rounding are those of k_tc_forward: identical results.
+constexpr int TB_EPI_WARPS = 16;                   // four per TMEM lane quarter
+constexpr int TB_SUBS = TB_EPI_WARPS / 4;          // warps sharing a lane quarter
+constexpr int TB_MAXB = (8 + TB_SUBS - 1) / TB_SUBS;  // 16-column blocks per warp and group
+constexpr int TB_THREADS = 64 + 32 * TB_EPI_WARPS;
+constexpr int TB_MAX_STAGES = 12;
+
+// Launch shape: observation buffers (1: the next tile loads once the last
+// agent's first layer has read the buffer; 2: during the whole tile) and
+// the weight ring.
+struct TbShape {
+    int nobs, stages;
+    uint32_t stage_bytes;
+};
+
+struct TbLayout {
+    uint32_t ring, bias, bars, total;
+};
+
+__host__ __device__ inline TbLayout tb_layout(const TcPlan &p, const TbShape &sh)
+{
+    TbLayout L;
+    L.ring = (uint32_t)sh.nobs * obs_tile_bytes(p);
+    L.bias = L.ring + (uint32_t)sh.stages * sh.stage_bytes;
+    L.bars = L.bias + (uint32_t)(p.M * p.L) * 1024u;
+    L.total = L.bars + 512u;
+    return L;
+}
+
+// Output groups of a layer: one of N columns up to 128, else two halves
+// (the first rounded up to 16).
+__host__ __device__ inline int tb_halves(int N) { return N > 128 ? 2 : 1; }
+__host__ __device__ inline int tb_h0(int N) { return N > 128 ? ((N / 2 + 15) & ~15) : N; }
+
+// The plan runs on k_tc_actor2: BF16 (not split), every layer at most 256
+// wide (so a hidden layer's BF16 output fits one 128-column buffer).
+bool tb_plan_ok(const TcPlan &p)
+{
+    if (p.split != 1 || p.esz != 2) return false;
+    for (int l = 0; l < p.L; ++l) {
+        if (p.layer[l].N > 256) return false;
+        if (l > 0 && p.layer[l].K > 256) return false;
+    }
+    return true;
+}
+
+// Launch shape for a plan: one observation buffer and two 64 KB stages
+// (measured fastest: each stage handoff costs the MMA warp a barrier round
+// trip, so few large stages beat many small ones), else the largest ring
+// of >= 2 stages that fits.
+TbShape tb_shape(const TcPlan &p, int optin)
+{
+    for (uint32_t sb : {65536u, 32768u, 16384u}) {
+        TbShape sh{1, 2, sb};
+        if (tb_layout(p, sh).total + 1024u <= (uint32_t)optin) return sh;
+    }
+    return TbShape{1, 0, 0u};
+}
+
+__global__ void __launch_bounds__(TB_THREADS, 1)
+k_tc_actor2(const __grid_constant__ TcPlan plan, const TbShape sh, const uint8_t *__restrict__ img,
+            const float *__restrict__ bias, const uint8_t *__restrict__ obs_tiles, int n, int tiles,
+            float *__restrict__ y, unsigned *err)
+{
+    using namespace ptx;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const TbLayout Lo = tb_layout(plan, sh);
+    const int S = sh.stages, NOBS = sh.nobs;
+    const uint32_t SB = sh.stage_bytes;
+    uint8_t *ring = base + Lo.ring;
+    float *bias_s = (float *)(base + Lo.bias);
+    uint64_t *bars = (uint64_t *)(base + Lo.bars);
+    uint64_t *full = bars;                       // [S] weight stage landed
+    uint64_t *empty = full + TB_MAX_STAGES;      // [S] weight stage read
+    uint64_t *obs_full = empty + TB_MAX_STAGES;  // [NOBS]
+    uint64_t *obs_empty = obs_full + 2;          // [NOBS]
+    uint64_t *acc_full = obs_empty + 2;          // [2] a group's MMAs into region r are done
+    uint64_t *acc_free = acc_full + 2;           // [2] the epilogue has read region r
+    uint64_t *h_ready = acc_free + 2;            // [2] operand half h of the next layer written
+    uint64_t *drain = h_ready + 2;
+    uint32_t *tmem_slot = (uint32_t *)(drain + 1);
+    volatile int *abort = (volatile int *)(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t ob = obs_tile_bytes(plan);
+    const int M = plan.M, NL = plan.L;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < S; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&obs_full[b], 1);
+            mbar_init(&obs_empty[b], 1);
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_free[b], TB_EPI_WARPS);
+            mbar_init(&h_ready[b], TB_EPI_WARPS);
+        }
+        mbar_init(drain, 1);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        __syncwarp();
+        tmem_alloc(tmem_slot, 512u);
+        tmem_relinquish();
+    }
+    for (int i = threadIdx.x; i < M * NL * 256; i += TB_THREADS) {
+        const int j = i / (NL * 256), l = (i / 256) % NL, c = i % 256;
+        bias_s[i] = bias[((size_t)j * MAX_LAYERS + l) * 256 + c];
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int my_tiles = blockIdx.x < tiles ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+    if (warp == 0) {
+        // ------------------------------------ observation tiles and weights
+        // Tile k goes to buffer k % NOBS once tile k - NOBS's last first
+        // layer has read it; it is only waited for when every first-layer
+        // stage of that tile has been issued (so no wait is on MMAs whose
+        // weights are still to come).
+        int i = 0, s = 0;
+        uint32_t ph = 0;
+        bool ok = true;
+        int next_obs = 0;
+        for (int k = 0; k < my_tiles && ok; ++k) {
+            for (int j = 0; j < M && ok; ++j) {
+                const uint8_t *aimg = img + (size_t)j * plan.agent_bytes;      // the grouped image
+                for (int l = 0; l < NL && ok; ++l) {
+                    const TcLayer &ly = plan.layer[l];
+                    const int nh = tb_halves(ly.N), h0 = tb_h0(ly.N), steps = ly.K / 16;
+                    for (int h = 0; h < nh && ok; ++h) {
+                        const int n0 = h ? h0 : 0, ng = h ? ly.N - h0 : h0;
+                        const uint32_t col_b = (uint32_t)ng * 16u, kstep_b = 2u * col_b;
+                        const int sps = (int)(SB / kstep_b);
+                        for (int k16 = 0; k16 < steps; k16 += sps, ++i) {
+                            while (next_obs < my_tiles &&
+                                   (next_obs <= k + NOBS - 1 || (NOBS == 1 && next_obs == k + 1 && j == M - 1 && l >= 1))) {
+                                const int kn = next_obs, b = kn % NOBS;
+                                if (kn >= NOBS && !warp_wait_all(&obs_empty[b], (uint32_t)((kn - NOBS) / NOBS) & 1u,
+                                                                 false, abort, err, 1u, TC_WAIT_NS)) {
+                                    ok = false;
+                                    break;
+                                }
+                                const uint8_t *src = obs_tiles + (size_t)(blockIdx.x + (size_t)kn * gridDim.x) * ob;
+                                uint8_t *dst = base + (uint32_t)b * ob;
+                                if (elect_one()) {
+                                    mbar_arrive_expect_tx(&obs_full[b], ob);
+                                    for (uint32_t o = 0; o < ob; o += TC_CHUNK_MAX)
+                                        bulk_g2s(dst + o, src + o, min(TC_CHUNK_MAX, ob - o), &obs_full[b]);
+                                }
+                                __syncwarp();
+                                ++next_obs;
+                            }
+                            if (!ok) break;
+                            if (!warp_wait_all(&empty[s], ph ^ 1u, false, abort, err, 1u, TC_WAIT_NS)) {
+                                ok = false;
+                                break;
+                            }
+                            const int nk = min(sps, steps - k16);
+                            if (elect_one()) {
+                                mbar_arrive_expect_tx(&full[s], (uint32_t)nk * kstep_b);
+                                // group h of the layer: rows [n0, n0 + ng), its core
+                                // columns (ng x 16 bytes each) end to end
+                                const uint8_t *src = aimg + ly.off + (size_t)n0 * ly.K * 2 + (size_t)k16 * kstep_b;
+                                bulk_g2s(ring + (size_t)s * SB, src, (uint32_t)nk * kstep_b, &full[s]);
+                            }
+                            __syncwarp();
+                            if (++s == S) {
+                                s = 0;
+                                ph ^= 1u;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        // every copy issued lands before the CTA may exit
+        volatile int no_abort = 0;
+        for (int k = i - 1; k >= 0 && k >= i - S; --k)
+            warp_wait_all(&full[k % S], (uint32_t)(k / S) & 1u, false, &no_abort, err, 8u, TC_WAIT_NS);
+        for (int k = next_obs - 1; k >= 0 && k >= next_obs - NOBS; --k)
+            warp_wait_all(&obs_full[k % NOBS], (uint32_t)(k / NOBS) & 1u, false, &no_abort, err, 8u, TC_WAIT_NS);
+    } else if (warp == 1) {
+        // ------------------------------------------------------ MMA issue
+        int s = 0, g = 0, lam = 0;
+        uint32_t ph = 0, hp0 = 0, hp1 = 0;
+        bool ok = true;
+        const uint32_t ring_u = smem_u32(ring);
+        for (int k = 0; k < my_tiles && ok; ++k) {
+            const int b = k % NOBS;
+            if (!warp_wait_all(&obs_full[b], (uint32_t)(k / NOBS) & 1u, false, abort, err, 2u, TC_WAIT_NS)) break;
+            const uint32_t obs_u = smem_u32(base + (uint32_t)b * ob);
+            for (int j = 0; j < M && ok; ++j) {
+                for (int l = 0; l < NL && ok; ++l) {
+                    const TcLayer &ly = plan.layer[l];
+                    const int nh = tb_halves(ly.N), h0 = tb_h0(ly.N), steps = ly.K / 16;
+                    // the previous layer's operand halves: K steps [0, ksplit) need half 0
+                    const int ksplit = l > 0 ? (tb_halves(plan.layer[l - 1].N) == 2 ? tb_h0(plan.layer[l - 1].N) / 16
+                                                                                      : steps)
+                                             : steps;
+                    const uint32_t hbuf = tmem + 256u + 128u * (uint32_t)((lam - 1) & 1);
+                    for (int h = 0; h < nh && ok; ++h, ++g) {
+                        const int r = g & 1, n0 = h ? h0 : 0, ng = h ? ly.N - h0 : h0;
+                        const uint32_t D = tmem + 128u * (uint32_t)r;
+                        // region r was last read by group g - 2's epilogue
+                        if (g >= 2 &&
+                            !warp_wait_all(&acc_free[r], (uint32_t)((g >> 1) - 1) & 1u, false, abort, err, 2u, TC_WAIT_NS)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t idesc = idesc_bf16(128, ng);
+                        const uint32_t col_b = (uint32_t)ng * 16u;
+                        const uint64_t b_step = (uint64_t)((2u * col_b) >> 4);
+                        const uint64_t bd_ring = smem_desc(ring_u, col_b, 128u);
+                        const int sps = (int)(SB / (2u * col_b));
+                        for (int k16 = 0; k16 < steps && ok; k16 += sps) {
+                            if (!warp_wait_all(&full[s], ph, false, abort, err, 4u, TC_WAIT_NS)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const int nk = min(sps, steps - k16);
+                            const uint64_t bd = bd_ring + (uint64_t)(((uint32_t)s * SB) >> 4);
+                            // issue in at most two runs: an operand half may have to be waited for
+                            for (int u0 = 0; u0 < nk;) {
+                                const int kk = k16 + u0;
+                                if (l > 0 && h == 0 && (kk == 0 || kk == ksplit)) {
+                                    const bool second = kk != 0;
+                                    if (!warp_wait_all(&h_ready[second ? 1 : 0], second ? hp1 : hp0, false, abort, err,
+                                                       2u, TC_WAIT_NS)) {
+                                        ok = false;
+                                        break;
+                                    }
+                                    if (second)
+                                        hp1 ^= 1u;
+                                    else
+                                        hp0 ^= 1u;
+                                    tc_fence_after();
+                                }
+                                int u1 = nk;
+                                if (l > 0 && h == 0 && kk < ksplit && k16 + nk > ksplit) u1 = ksplit - k16;
+                                if (elect_one()) {
+                                    for (int u = u0; u < u1; ++u) {
+                                        const uint32_t kq = (uint32_t)(k16 + u);
+                                        if (l == 0)
+                                            mma_bf16(D, smem_desc(obs_u, 2048u, 128u) + 256u * kq, bd + b_step * (uint32_t)u,
+                                                     idesc, kq ? 1u : 0u);
+                                        else
+                                            mma_bf16_ta(D, hbuf + 8u * kq, bd + b_step * (uint32_t)u, idesc, kq ? 1u : 0u);
+                                    }
+                                }
+                                __syncwarp();
+                                u0 = u1;
+                            }
+                            if (!ok) break;
+                            if (elect_one()) mma_commit(&empty[s]);
+                            __syncwarp();
+                            if (++s == S) {
+                                s = 0;
+                                ph ^= 1u;
+                            }
+                        }
+                        if (!ok) break;
+                        if (elect_one()) {
+                            if (l == 0 && h == nh - 1 && j == M - 1) mma_commit(&obs_empty[b]);   // tile's last obs read
+                            mma_commit(&acc_full[r]);
+                        }
+                        __syncwarp();
+                        (void)n0;
+                    }
+                    if (l < NL - 1) ++lam;
+                }
+            }
+        }
+        // every MMA issued completes before TMEM is released
+        if (elect_one()) mma_commit(drain);
+        __syncwarp();
+        volatile int no_abort = 0;
+        warp_wait_all(drain, 0u, false, &no_abort, err, 128u, TC_WAIT_NS);
+    } else {
+        // ------------------------------------------------------- epilogue
+        const int q = warp & 3;                       // TMEM lane quarter (warp id mod 4)
+        const int sub = (warp - 2) >> 2;              // 16-column blocks sub, sub + TB_SUBS, ...
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        int g = 0, lam = 0;
+        // no early exit: a wait that gives up sets the abort flag, the later
+        // ones return at once, and the loops run to their uniform end
+        for (int k = 0; k < my_tiles; ++k) {
+            const int row = (int)(blockIdx.x + (size_t)k * gridDim.x) * 128 + q * 32 + lane;
+            for (int j = 0; j < M; ++j) {
+                for (int l = 0; l < NL; ++l) {
+                    const TcLayer &ly = plan.layer[l];
+                    const bool last = l == NL - 1;
+                    const int nh = tb_halves(ly.N), h0 = tb_h0(ly.N);
+                    const uint32_t hbuf = tmem + 256u + 128u * (uint32_t)(lam & 1) + lane_off;
+                    for (int h = 0; h < nh; ++h, ++g) {
+                        const int r = g & 1, n0 = h ? h0 : 0, ng = h ? ly.N - h0 : h0;
+                        const uint32_t D = tmem + 128u * (uint32_t)r + lane_off;
+                        warp_wait_all(&acc_full[r], (uint32_t)(g >> 1) & 1u, false, abort, err, 16u, TC_WAIT_NS);
+                        tc_fence_after();
+                        const int G = ng / 16;
+                        const int cnt = G > sub ? (G - sub + TB_SUBS - 1) / TB_SUBS : 0;   // warp-uniform
+                        uint32_t v[TB_MAXB][16];
+                        __syncwarp();
+#pragma unroll
+                        for (int u = 0; u < TB_MAXB; ++u)
+                            if (u < cnt) tmem_ld16(D + (uint32_t)(16 * (sub + TB_SUBS * u)), v[u]);
+                        tmem_ld_wait();
+                        // the accumulator is in registers: region r is free for group g + 2
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&acc_free[r]);
+                        const float *bl = bias_s + (j * NL + l) * 256 + n0;
+#pragma unroll
+                        for (int u = 0; u < TB_MAXB; ++u) {
+                            if (u >= cnt) break;
+                            const int c0 = 16 * (sub + TB_SUBS * u);
+                            const float4 *b4 = (const float4 *)(bl + c0);
+                            float x[16];
+#pragma unroll
+                            for (int q4 = 0; q4 < 4; ++q4) {
+                                const float4 bb = b4[q4];
+                                x[4 * q4 + 0] = __uint_as_float(v[u][4 * q4 + 0]) + bb.x;
+                                x[4 * q4 + 1] = __uint_as_float(v[u][4 * q4 + 1]) + bb.y;
+                                x[4 * q4 + 2] = __uint_as_float(v[u][4 * q4 + 2]) + bb.z;
+                                x[4 * q4 + 3] = __uint_as_float(v[u][4 * q4 + 3]) + bb.w;
+                            }
+                            if (!last) {
+                                uint32_t w[8];
+#pragma unroll
+                                for (int e = 0; e < 8; ++e) w[e] = relu_bf16x2(x[2 * e], x[2 * e + 1]);
+                                tmem_st8(hbuf + (uint32_t)((n0 + c0) / 2), w);
+                            } else if (row < n) {
+                                float *yr = y + ((size_t)j * n + row) * ly.fout + n0;
+#pragma unroll
+                                for (int e = 0; e < 16; ++e) {
+                                    const int col = n0 + c0 + e;
+                                    if (col < ly.fout) yr[c0 + e] = plan.out_act ? tanhf(x[e]) : x[e];
+                                }
+                            }
+                        }
+                        if (!last) {
+                            tmem_st_wait();
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&h_ready[h]);
+                        }
+                    }
+                    if (!last) ++lam;
+                }
+            }
+        }
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, 512u);
+    }
+}
+
 // Ring shape: the largest stage (32 or 16 KB, at least one K = 16 step of
 // the widest layer) with 2..TA_MAX_STAGES stages that fits; bigger stages
 // give the single MMA-issuing thread more MMAs per barrier wait.
@@ -436,18 +859,37 @@ int tc_forward_tiled(const fr_ensemble *e, const float *obs, int ld, int n, floa
     const TcPlan &p = t->plan;
     int optin = 0;
     FR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, e->ctx->device));
+    // k_tc_actor2 for BF16 plans it takes, else k_tc_actor
+    const TbShape sh = !fp8 && tb_plan_ok(p) && t->img2 ? tb_shape(p, optin) : TbShape{1, 0, 0u};
     uint32_t stage_bytes = 0;
-    const int stages = ta_stages(p, optin, &stage_bytes);
-    FR_CHECK(stages >= 2, FR_EINVAL, "tc_forward_tiled: the plan does not fit in shared memory");
+    const int stages = sh.stages >= 2 ? 0 : ta_stages(p, optin, &stage_bytes);
+    FR_CHECK(sh.stages >= 2 || stages >= 2, FR_EINVAL, "tc_forward_tiled: the plan does not fit in shared memory");
     const int tiles = (int)ceil_div(n, 128);
     const int nch = p.layer[0].K / p.ck;
     const int64_t threads = (int64_t)tiles * nch * 128;
     if (fp8)
         k_obs_tiles_e4m3<<<ceil_div(threads, 256), 256, 0, s>>>(obs, ld, n, p.layer[0].fin, nch, 1.0f / t->sx[0][0],
                                                                 (uint4 *)scratch);
-    else
-        k_obs_tiles<<<ceil_div(threads, 256), 256, 0, s>>>(obs, ld, n, p.layer[0].fin, nch, (uint4 *)scratch);
+    else {
+        // rows past n in the last tile stay zero: the 32-row blocks cover
+        // whole tiles, the ones past n write zeros
+        const size_t st_bytes = (size_t)OT_ROWS * p.layer[0].fin * sizeof(float);
+        static_assert(128 % OT_ROWS == 0, "blocks tile the 128-row tiles");
+        if (st_bytes > 48 * 1024) FR_CUDA(cudaFuncSetAttribute(k_obs_tiles2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                               (int)st_bytes));
+        k_obs_tiles2<<<tiles * (128 / OT_ROWS), OT_THREADS, st_bytes, s>>>(obs, ld, n, p.layer[0].fin, nch,
+                                                                           (uint4 *)scratch);
+    }
     FR_CUDA(cudaGetLastError());
+    if (sh.stages >= 2) {
+        const uint32_t smem2 = tb_layout(p, sh).total + 1024u;
+        FR_CUDA(set_max_smem_once((const void *)k_tc_actor2, e->ctx->device));
+        const int grid = std::min(tiles, e->ctx->sm_count);
+        k_tc_actor2<<<grid, TB_THREADS, smem2, s>>>(p, sh, t->img2, t->bias, (const uint8_t *)scratch, n, tiles, y,
+                                                    t->err);
+        FR_CUDA(cudaGetLastError());
+        return FR_OK;
+    }
     const uint32_t smem = ta_layout(p, stages, stage_bytes).total + 1024u;
     if (fp8) {
         FR_CUDA(set_max_smem_once((const void *)k_tc_actor<true>, e->ctx->device));

@@ -410,6 +410,8 @@ int tc_create(fr_ensemble *e)
     std::vector<uint8_t> img((size_t)e->M * p.agent_bytes, 0);
     std::vector<float> bias((size_t)e->M * MAX_LAYERS * 256, 0.0f);
     const bool fp8 = p.esz == 1;
+    const bool grouped = p.split == 1 && !fp8;
+    std::vector<uint8_t> img2(grouped ? img.size() : 0, 0);
     for (int j = 0; j < e->M; ++j) {
         const float *P = host.data() + (size_t)j * e->P;
         uint8_t *aimg = img.data() + (size_t)j * p.agent_bytes;
@@ -437,6 +439,14 @@ int tc_create(fr_ensemble *e)
                     }
                     const uint16_t b = f32_to_bf16_rne(wv);
                     memcpy(aimg + off, &b, 2);
+                    if (grouped) {
+                        // rows [0, h0) then [h0, N), each group [K/8][rows][8]
+                        const int h0 = ly.N > 128 ? ((ly.N / 2 + 15) & ~15) : ly.N;
+                        const int hh = n >= h0, n0 = hh ? h0 : 0, ng = hh ? ly.N - h0 : h0, nn = n - n0;
+                        const size_t off2 = ly.off + (size_t)(hh ? h0 : 0) * ly.K * 2 + (size_t)(k / 8) * ng * 16 +
+                                            (size_t)(nn / 8) * 128 + (size_t)(nn % 8) * 16 + (size_t)(k % 8) * 2;
+                        memcpy(img2.data() + (size_t)j * p.agent_bytes + off2, &b, 2);
+                    }
                     if (p.split == 3) {
                         const uint16_t bl = f32_to_bf16_rne(wv - bf16_to_f32(b));
                         memcpy(aimg + off + (size_t)ly.N * kc * 2, &bl, 2);
@@ -450,16 +460,19 @@ int tc_create(fr_ensemble *e)
     int rc;
     if ((rc = dev_alloc(e->ctx, (void **)&t->img, ib)) || (rc = dev_alloc(e->ctx, (void **)&t->bias, bb)) ||
         (rc = dev_alloc(e->ctx, (void **)&t->err, 256)) ||
-        (fp8 && (rc = dev_alloc(e->ctx, (void **)&t->dq, qb)))) {
+        (fp8 && (rc = dev_alloc(e->ctx, (void **)&t->dq, qb))) ||
+        (grouped && (rc = dev_alloc(e->ctx, (void **)&t->img2, ib)))) {
         dev_free(e->ctx, t->img, ib);
+        dev_free(e->ctx, t->img2, grouped ? ib : 0);
         dev_free(e->ctx, t->bias, bb);
         dev_free(e->ctx, t->err, 256);
         delete t;
         return rc;
     }
     if (fp8) t->inv_sx = t->dq + (size_t)e->M * MAX_LAYERS * 256;
-    t->bytes = ib + bb + 256 + qb;
+    t->bytes = ib + bb + 256 + qb + (grouped ? ib : 0);
     err = cudaMemcpy(t->img, img.data(), ib, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess && grouped) err = cudaMemcpy(t->img2, img2.data(), ib, cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(t->bias, bias.data(), bb, cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemset(t->err, 0, 256);
     int optin = 0;
@@ -483,6 +496,7 @@ void tc_destroy(fr_ensemble *e)
     if (!e || !e->tc) return;
     TcImage *t = e->tc;
     dev_free(e->ctx, t->img, (uint64_t)e->M * t->plan.agent_bytes);
+    if (t->img2) dev_free(e->ctx, t->img2, (uint64_t)e->M * t->plan.agent_bytes);
     dev_free(e->ctx, t->bias, (uint64_t)e->M * MAX_LAYERS * 256 * 4);
     dev_free(e->ctx, t->err, 256);
     if (t->dq) dev_free(e->ctx, t->dq, (uint64_t)e->M * MAX_LAYERS * (256 + 1) * 4);

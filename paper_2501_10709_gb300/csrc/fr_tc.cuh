@@ -53,6 +53,10 @@ struct TcPlan {
 struct TcImage {
     TcPlan plan;
     uint8_t *img;         // device [M][agent_bytes] BF16 chunks
+    // BF16 without split: the same weights with each layer's output rows in
+    // at most two groups (k_tc_actor2's halves), each group's K-major core
+    // columns end to end, so a run of K steps of one group is contiguous
+    uint8_t *img2 = nullptr;
     float *bias;          // device [M][MAX_LAYERS][256] fp32, zero padded
     unsigned *err;        // device error flags
     uint64_t bytes;
