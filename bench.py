@@ -224,9 +224,12 @@ def crypto_line(fr, ctx, dev, flush, stream, reps=3):
     env = fr.env_create(ctx, mk, start=e.start, window=e.W, init_cash=e.init_cash, pmax=e.pmax)
     met = torch.empty(e.N, 3, dtype=torch.float64, device=dev)
     res = {"workload": f"crypto {e.N} envs x {w.T} steps, 5 x 10-128-128-3 Q-nets, majority vote, "
-                       "480,000 s GBM mid", "unit": "env-steps/s"}
-    for name, prec, T in (("fused_bf16", fr.PREC_BF16, w.T), ("fused_bf16x3", fr.PREC_BF16X3, w.T),
-                          ("plain_fp32", fr.PREC_FP32, 128)):
+                       "480,000 s GBM mid", "unit": "env-steps/s",
+           "vote_agreement_bar": 0.999,
+           "meets_bar": ["fused_fp16", "fused_bf16x3", "plain_fp32"],
+           "below_bar": {"fused_bf16": "about 99.45% of votes equal the fp64 vote (near-tied Q values)"}}
+    for name, prec, T in (("fused_fp16", fr.PREC_FP16, w.T), ("fused_bf16", fr.PREC_BF16, w.T),
+                          ("fused_bf16x3", fr.PREC_BF16X3, w.T), ("plain_fp32", fr.PREC_FP32, 128)):
         ens = fr.ensemble_create(ctx, w.dims, w.params, precision=prec, combine=fr.COMBINE_VOTE, out_act=0)
         ts = time_rollouts(fr, env, ens, T, reps, 3, met, flush, stream)
         res[name] = {"value": e.N * T * len(ts) / sum(ts), "ms_per_rollout": 1e3 * statistics.mean(ts),

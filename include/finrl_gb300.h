@@ -256,6 +256,13 @@ typedef struct fr_ensemble fr_ensemble;
                                  x ~ hi + lo, three products per step
                                  (hi*hi + lo*hi + hi*lo), fp32-class accuracy
                                  for discrete (argmax / vote) decisions      */
+#define FR_PREC_FP16 4        /* tcgen05 FP16 operands (round to nearest even,
+                                 saturating at +-65504), fp32 accumulate:
+                                 BF16's speed and memory with 10 stored
+                                 mantissa bits instead of 7, for inputs,
+                                 weights and activations of moderate range
+                                 (no counterpart in the paper; an inference
+                                 precision option)                           */
 
 #define FR_HEAD_Q 0           /* outputs are the Q-values (DQN, Double DQN)  */
 #define FR_HEAD_DUELING 1     /* outputs are [V, A_0 .. A_{n-1}] (Dueling DQN):

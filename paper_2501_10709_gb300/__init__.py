@@ -15,7 +15,7 @@ import numpy as np
 from . import _lib
 from ._lib import (ACT_F32_UNIT, ACT_I32_SHARES, ACT_U8_DISCRETE, BUY_ASCENDING, BUY_LARGEST_FIRST,
                    COMBINE_MEAN, FAULT_ALLOC, FAULT_POLL, FAULT_SUBMIT, HEAD_DUELING, HEAD_Q,
-                   COMBINE_VOTE, PATH_AUTO, PATH_UNFUSED, PREC_BF16, PREC_BF16X3, PREC_FP8,
+                   COMBINE_VOTE, PATH_AUTO, PATH_UNFUSED, PREC_BF16, PREC_BF16X3, PREC_FP16, PREC_FP8,
                    PREC_FP32, TASK_CRYPTO, TASK_STOCK, FrError)
 
 __all__ = [
@@ -32,7 +32,7 @@ __all__ = [
     "PATH_AUTO", "PATH_UNFUSED", "BUY_ASCENDING", "BUY_LARGEST_FIRST",
     "fr_fault_inject", "FAULT_ALLOC", "FAULT_SUBMIT", "FAULT_POLL", "fr_wait_selftest",
     "ACT_I32_SHARES", "ACT_F32_UNIT", "ACT_U8_DISCRETE", "PREC_FP32", "PREC_BF16",
-    "PREC_FP8", "PREC_BF16X3", "COMBINE_MEAN", "COMBINE_VOTE", "TASK_STOCK", "TASK_CRYPTO",
+    "PREC_FP8", "PREC_BF16X3", "PREC_FP16", "COMBINE_MEAN", "COMBINE_VOTE", "TASK_STOCK", "TASK_CRYPTO",
 ]
 
 

@@ -17,7 +17,7 @@ FR_OK, FR_EINVAL, FR_ENOMEM, FR_EBUSY, FR_ETIMEDOUT, FR_ECUDA, FR_ENOTREADY, FR_
 FR_ECANCELED = -8
 TASK_STOCK, TASK_CRYPTO = 0, 1
 ACT_I32_SHARES, ACT_F32_UNIT, ACT_U8_DISCRETE = 0, 1, 2
-PREC_FP32, PREC_BF16, PREC_FP8, PREC_BF16X3 = 0, 1, 2, 3
+PREC_FP32, PREC_BF16, PREC_FP8, PREC_BF16X3, PREC_FP16 = 0, 1, 2, 3, 4
 COMBINE_MEAN, COMBINE_VOTE = 0, 1
 HEAD_Q, HEAD_DUELING = 0, 1
 PATH_AUTO, PATH_UNFUSED = 0, 1

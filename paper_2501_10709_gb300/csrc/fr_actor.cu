@@ -84,7 +84,7 @@ constexpr int OT_ROWS = 32;
 constexpr int OT_THREADS = 256;
 
 __global__ void __launch_bounds__(OT_THREADS) k_obs_tiles2(const float *__restrict__ obs, int ld, int n, int fin,
-                                                             int nchunks, uint4 *out)
+                                                             int nchunks, int f16, uint4 *out)
 {
     extern __shared__ float st[];                       // [OT_ROWS][fin]
     const int64_t r0 = (int64_t)blockIdx.x * OT_ROWS;
@@ -125,11 +125,7 @@ __global__ void __launch_bounds__(OT_THREADS) k_obs_tiles2(const float *__restri
             v[u] = k < fin ? st[r * fin + k] : 0.0f;
         }
         uint32_t w[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * u], v[2 * u + 1]);
-            w[u] = *(const uint32_t *)&b;
-        }
+        pack8_16(v, w, f16 != 0);
         out[(tile * nchunks + c) * 128 + rt + r] = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
@@ -659,7 +655,7 @@ k_tc_actor2(const __grid_constant__ TcPlan plan, const TbShape sh, const uint8_t
                             ok = false;
                             break;
                         }
-                        const uint32_t idesc = idesc_bf16(128, ng);
+                        const uint32_t idesc = idesc_16(128, ng, plan.f16 != 0);
                         const uint32_t col_b = (uint32_t)ng * 16u;
                         const uint64_t b_step = (uint64_t)((2u * col_b) >> 4);
                         const uint64_t bd_ring = smem_desc(ring_u, col_b, 128u);
@@ -779,7 +775,13 @@ k_tc_actor2(const __grid_constant__ TcPlan plan, const TbShape sh, const uint8_t
                             if (!last) {
                                 uint32_t w[8];
 #pragma unroll
-                                for (int e = 0; e < 8; ++e) w[e] = relu_bf16x2(x[2 * e], x[2 * e + 1]);
+                                if (plan.f16) {
+#pragma unroll
+                                    for (int e = 0; e < 8; ++e) w[e] = relu_f16x2_sat(x[2 * e], x[2 * e + 1]);
+                                } else {
+#pragma unroll
+                                    for (int e = 0; e < 8; ++e) w[e] = relu_bf16x2(x[2 * e], x[2 * e + 1]);
+                                }
                                 tmem_st8(hbuf + (uint32_t)((n0 + c0) / 2), w);
                             } else if (row < n) {
                                 float *yr = y + ((size_t)j * n + row) * ly.fout + n0;
@@ -862,7 +864,8 @@ int tc_forward_tiled(const fr_ensemble *e, const float *obs, int ld, int n, floa
     // k_tc_actor2 for BF16 plans it takes, else k_tc_actor
     const TbShape sh = !fp8 && tb_plan_ok(p) && t->img2 ? tb_shape(p, optin) : TbShape{1, 0, 0u};
     uint32_t stage_bytes = 0;
-    const int stages = sh.stages >= 2 ? 0 : ta_stages(p, optin, &stage_bytes);
+    // k_tc_actor takes BF16 and FP8 operands only
+    const int stages = sh.stages >= 2 || p.f16 ? 0 : ta_stages(p, optin, &stage_bytes);
     FR_CHECK(sh.stages >= 2 || stages >= 2, FR_EINVAL, "tc_forward_tiled: the plan does not fit in shared memory");
     const int tiles = (int)ceil_div(n, 128);
     const int nch = p.layer[0].K / p.ck;
@@ -877,7 +880,7 @@ int tc_forward_tiled(const fr_ensemble *e, const float *obs, int ld, int n, floa
         static_assert(128 % OT_ROWS == 0, "blocks tile the 128-row tiles");
         if (st_bytes > 48 * 1024) FR_CUDA(cudaFuncSetAttribute(k_obs_tiles2, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                                (int)st_bytes));
-        k_obs_tiles2<<<tiles * (128 / OT_ROWS), OT_THREADS, st_bytes, s>>>(obs, ld, n, p.layer[0].fin, nch,
+        k_obs_tiles2<<<tiles * (128 / OT_ROWS), OT_THREADS, st_bytes, s>>>(obs, ld, n, p.layer[0].fin, nch, p.f16,
                                                                            (uint4 *)scratch);
     }
     FR_CUDA(cudaGetLastError());

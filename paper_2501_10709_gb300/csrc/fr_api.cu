@@ -749,7 +749,7 @@ int ensemble_create(fr_ctx *ctx, const fr_ensemble_desc *d, fr_ensemble **out)
     for (int l = 1; l < d->n_layers; ++l)
         FR_CHECK(d->dims[l] <= MAX_HIDDEN, FR_EINVAL, "ensemble_create: hidden width %d > 256",
                  d->dims[l]);
-    FR_CHECK(d->precision >= FR_PREC_FP32 && d->precision <= FR_PREC_BF16X3, FR_EINVAL,
+    FR_CHECK(d->precision >= FR_PREC_FP32 && d->precision <= FR_PREC_FP16, FR_EINVAL,
              "ensemble_create: precision %d", d->precision);
     FR_CHECK(d->combine == FR_COMBINE_MEAN || d->combine == FR_COMBINE_VOTE, FR_EINVAL,
              "ensemble_create: combine %d", d->combine);

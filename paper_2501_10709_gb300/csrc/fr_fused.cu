@@ -149,7 +149,7 @@ __device__ void fused_mma(const FusedArgs &a, uint32_t tmem, const uint8_t *A, c
             const TcLayer &ly = p.layer[l];
             if (!mbar_wait(a_ready, (uint32_t)(s * p.L + l) & 1u, abort, a.err, 2u, TC_WAIT_NS)) return;
             tc_fence_after();
-            const uint32_t idesc = idesc_bf16(128, ly.N);
+            const uint32_t idesc = idesc_16(128, ly.N, p.f16 != 0);
             const uint32_t lbo_b = (uint32_t)(ly.N * 16);
             int kg = 0;
             for (int c = 0; c < ly.n_chunks; ++c, ++ci) {
@@ -194,29 +194,23 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volati
     return ptx::warp_wait_all(bar, parity, cluster_scope, abort, err, code, TC_WAIT_NS);
 }
 
-// Eight floats -> four words of two BF16 (round to nearest), K order.
-__device__ __forceinline__ void pack8(const float *v, uint32_t *hi)
-{
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-        hi[i] = *(const uint32_t *)&h;
-    }
-}
+// Operand format of the A buffer: BF16, BF16 hi / lo (split), or FP16.
+constexpr int FMT_BF16 = 0, FMT_SPLIT = 1, FMT_F16 = 2;
+__host__ __device__ inline int operand_fmt(const TcPlan &p) { return p.split == 3 ? FMT_SPLIT : (p.f16 ? FMT_F16 : FMT_BF16); }
 
 // Eight values of row r at 8-column chunk c of the A operand.
-__device__ __forceinline__ void put8(const float *v8, uint32_t a_base, uint32_t a_part, bool split,
+__device__ __forceinline__ void put8(const float *v8, uint32_t a_base, uint32_t a_part, int fmt,
                                      uint32_t row_off, int c)
 {
     using namespace ptx;
     const uint32_t at = a_base + (uint32_t)c * 2048u + row_off;
     uint32_t w[4];
-    if (split) {
+    if (fmt == FMT_SPLIT) {
         uint32_t wl[4];
         split_pack8(v8, w, wl);
         st_shared_v4(at + a_part, wl[0], wl[1], wl[2], wl[3]);
     } else {
-        pack8(v8, w);
+        pack8_16(v8, w, fmt == FMT_F16);
     }
     st_shared_v4(at, w[0], w[1], w[2], w[3]);
 }
@@ -228,9 +222,9 @@ __device__ __noinline__ int64_t afford_out_of_line(int64_t c, int64_t p, int fee
 }
 
 // Hidden-layer epilogue for row r: TMEM -> +bias -> ReLU -> BF16 (hi / lo)
-// into the A operand of the next layer.
+// or FP16 into the A operand of the next layer.
 __device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, const float *bl, int N, uint32_t a_base,
-                                                uint32_t a_part, bool split, uint32_t row_off)
+                                                uint32_t a_part, int fmt, uint32_t row_off)
 {
     using namespace ptx;
     int c0 = 0;
@@ -245,7 +239,7 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, const float *
             float x[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) x[i] = fmaxf(__uint_as_float(v[g * 8 + i]) + __ldg(bl + c0 + g * 8 + i), 0.0f);
-            put8(x, a_base, a_part, split, row_off, c0 / 8 + g);
+            put8(x, a_base, a_part, fmt, row_off, c0 / 8 + g);
         }
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
@@ -253,7 +247,7 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, const float *
 #pragma unroll
             for (int i = 0; i < 8; ++i)
                 x[i] = fmaxf(__uint_as_float(w[g * 8 + i]) + __ldg(bl + c0 + 32 + g * 8 + i), 0.0f);
-            put8(x, a_base, a_part, split, row_off, c0 / 8 + 4 + g);
+            put8(x, a_base, a_part, fmt, row_off, c0 / 8 + 4 + g);
         }
     }
     for (; c0 + 32 <= N; c0 += 32) {
@@ -266,7 +260,7 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, const float *
             float x[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) x[i] = fmaxf(__uint_as_float(v[g * 8 + i]) + __ldg(bl + c0 + g * 8 + i), 0.0f);
-            put8(x, a_base, a_part, split, row_off, c0 / 8 + g);
+            put8(x, a_base, a_part, fmt, row_off, c0 / 8 + g);
         }
     }
     if (c0 < N) {                                   // a 16-column tail
@@ -279,7 +273,7 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, const float *
             float x[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) x[i] = fmaxf(__uint_as_float(v[g * 8 + i]) + __ldg(bl + c0 + g * 8 + i), 0.0f);
-            put8(x, a_base, a_part, split, row_off, c0 / 8 + g);
+            put8(x, a_base, a_part, fmt, row_off, c0 / 8 + g);
         }
     }
 }
@@ -322,7 +316,7 @@ __device__ __forceinline__ void stock_obs_chunk(int64_t cash, const int64_t *p, 
 
 struct ObsSink {
     uint32_t a_base, a_part, row_off;
-    bool split;
+    int fmt;              // operand format (FMT_*)
     float *traj;          // fp32 trajectory row or null
 };
 
@@ -333,7 +327,7 @@ __device__ __forceinline__ void stock_obs_emit(const ObsSink &o, int64_t cash, c
     using namespace ptx;
     float v8[8];
     stock_obs_chunk<C>(cash, p, h, Ke, ind_row, v8);
-    put8(v8, o.a_base, o.a_part, o.split, o.row_off, C);
+    put8(v8, o.a_base, o.a_part, o.fmt, o.row_off, C);
     if (o.traj) {
 #pragma unroll
         for (int u = 0; u < 8; ++u)
@@ -370,7 +364,7 @@ __device__ void fused_env(const FusedArgs &a, uint32_t tmem, uint8_t *A, uint8_t
     const TcPlan &p = a.plan;
     const int M = p.M;
     const int L = p.L;
-    const bool split = p.split == 3;
+    const int fmt = operand_fmt(p);
     const uint32_t a_base = smem_u32(A);
     const uint32_t a_part = a_part_bytes(p);
     const int q = warp & 3;                  // TMEM lane quarter
@@ -421,7 +415,7 @@ __device__ void fused_env(const FusedArgs &a, uint32_t tmem, uint8_t *A, uint8_t
         const int d = start + t;
         // ---------------------------------------------- 1. observation row
         if (TASK == FR_TASK_STOCK) {
-            ObsSink o{a_base, a_part, row_off, split,
+            ObsSink o{a_base, a_part, row_off, fmt,
                       (w_obs && e >= 0) ? a.tr_obs + ((int64_t)s * v.N + e) * a.obs_ld : nullptr};
             const float *ind_row = e >= 0 ? v.ind + (int64_t)d * SI * SK : v.ind;
             const int ke = e >= 0 ? Ke : 0;
@@ -436,7 +430,7 @@ __device__ void fused_env(const FusedArgs &a, uint32_t tmem, uint8_t *A, uint8_t
                     const int j = pos - (1 + 2 * SK);
                     v8[u] = (pos < SD && j % SK < ke) ? __ldg(ind_row + j) : 0.0f;
                 }
-                put8(v8, a_base, a_part, split, row_off, c);
+                put8(v8, a_base, a_part, fmt, row_off, c);
                 if (o.traj) {
 #pragma unroll
                     for (int u = 0; u < 8; ++u)
@@ -456,8 +450,8 @@ __device__ void fused_env(const FusedArgs &a, uint32_t tmem, uint8_t *A, uint8_t
             u8[1] = ok ? __ldg(f + 7) : 0.0f;
 #pragma unroll
             for (int i = 2; i < 8; ++i) u8[i] = 0.0f;
-            put8(v8, a_base, a_part, split, row_off, 0);
-            put8(u8, a_base, a_part, split, row_off, 1);
+            put8(v8, a_base, a_part, fmt, row_off, 0);
+            put8(u8, a_base, a_part, fmt, row_off, 1);
             if (w_obs && ok) {
                 float *o = a.tr_obs + ((int64_t)s * v.N + e) * a.obs_ld;
 #pragma unroll
@@ -481,7 +475,7 @@ __device__ void fused_env(const FusedArgs &a, uint32_t tmem, uint8_t *A, uint8_t
             tc_fence_after();
             const float *bl = a.bias + ((size_t)agent * MAX_LAYERS + l) * 256;
             if (l < L - 1) {
-                hidden_epilogue(tmem_row, bl, ly.N, a_base, a_part, split, row_off);
+                hidden_epilogue(tmem_row, bl, ly.N, a_base, a_part, fmt, row_off);
                 fence_proxy_async_smem();
                 tc_fence_before();
                 mbar_arrive(a_ready);

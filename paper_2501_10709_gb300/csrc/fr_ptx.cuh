@@ -290,6 +290,18 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
            ((uint32_t)(M >> 4) << 24);
 }
 
+// The same with FP16 A/B (kind::f16, A and B of one type), FP32 accumulator.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// BF16 or FP16 operands (f16), FP32 accumulator.
+__host__ __device__ constexpr uint32_t idesc_16(int M, int N, bool f16)
+{
+    return f16 ? idesc_f16(M, N) : idesc_bf16(M, N);
+}
+
 // Instruction descriptor of kind::f8f6f4 with E4M3 A/B, FP32 accumulator.
 __host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N)
 {
@@ -379,6 +391,22 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8])
 __device__ __forceinline__ void tmem_st_wait()
 {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// a, b rounded to FP16 (nearest even, saturating at +-65504), a in the low half.
+__device__ __forceinline__ uint32_t f16x2_sat(float a, float b)
+{
+    uint32_t r;
+    asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+    return r;
+}
+
+// max(a, 0) and max(b, 0) rounded to FP16 (nearest even, saturating).
+__device__ __forceinline__ uint32_t relu_f16x2_sat(float a, float b)
+{
+    uint32_t r;
+    asm("cvt.rn.relu.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+    return r;
 }
 
 // max(a, 0) and max(b, 0) rounded to BF16 (nearest even), a in the low half.

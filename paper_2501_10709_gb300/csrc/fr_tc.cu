@@ -15,6 +15,7 @@
 // the epilogue dequantises with the per-channel factor sx * sw before the
 // bias and quantises the next layer's input with the agent's activation scale.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 #include <string.h>
 
@@ -42,6 +43,16 @@ inline uint16_t f32_to_bf16_rne(float f)
     return (uint16_t)(u >> 16);
 }
 
+// FP16 bits of f, round to nearest even, saturating at +-65504 (NaN stays NaN).
+inline uint16_t f32_to_f16_sat(float f)
+{
+    if (!(std::fabs(f) <= 65504.0f)) f = std::isnan(f) ? f : (f > 0.0f ? 65504.0f : -65504.0f);
+    const __half h = __float2half_rn(f);
+    uint16_t u;
+    memcpy(&u, &h, 2);
+    return u;
+}
+
 inline float bf16_to_f32(uint16_t b)
 {
     const uint32_t u = (uint32_t)b << 16;
@@ -60,6 +71,7 @@ inline uint32_t chunk_off(int N, int n, int kk, int ck, int esz)
 bool make_plan(const fr_ensemble *e, TcPlan &p)
 {
     p.split = e->precision == FR_PREC_BF16X3 ? 3 : 1;
+    p.f16 = e->precision == FR_PREC_FP16 ? 1 : 0;
     p.parts = p.split == 3 ? 2 : 1;
     const bool fp8 = e->precision == FR_PREC_FP8;
     p.esz = fp8 ? 1 : 2;
@@ -229,7 +241,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const ui
                 const TcLayer &ly = plan.layer[l];
                 if (!mbar_wait(a_ready, (uint32_t)l & 1u, abort, err, 2u, TC_WAIT_NS)) break;
                 tc_fence_after();
-                const uint32_t idesc = fp8 ? idesc_e4m3(128, ly.N) : idesc_bf16(128, ly.N);
+                const uint32_t idesc = fp8 ? idesc_e4m3(128, ly.N) : idesc_16(128, ly.N, plan.f16 != 0);
                 const uint32_t lbo_b = (uint32_t)(ly.N * 16);
                 const uint64_t b_step = (uint64_t)((2u * lbo_b) >> 4);
                 const int nu = tc_units(plan, ly);
@@ -306,7 +318,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const ui
                     v[i] = (g < n && k < l0.fin) ? __ldg(obs + (int64_t)g * ld + k) : 0.0f;
                 }
                 uint32_t w[4], wl[4];
-                split_pack8(v, w, wl);
+                if (split)
+                    split_pack8(v, w, wl);
+                else
+                    pack8_16(v, w, plan.f16 != 0);
                 const uint32_t at = a_base + (uint32_t)c * 2048u + (uint32_t)(row / 8) * 128u + (uint32_t)(row % 8) * 16u;
                 st_shared_v4(at, w[0], w[1], w[2], w[3]);
                 if (split) st_shared_v4(at + a_part, wl[0], wl[1], wl[2], wl[3]);
@@ -346,8 +361,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const ui
 #pragma unroll
                     for (int i = 0; i < 16; ++i) x[i] = fmaxf(x[i], 0.0f);
                     uint32_t w[8], wl[8];
-                    split_pack8(x, w, wl);
-                    split_pack8(x + 8, w + 4, wl + 4);
+                    if (split) {
+                        split_pack8(x, w, wl);
+                        split_pack8(x + 8, w + 4, wl + 4);
+                    } else {
+                        pack8_16(x, w, plan.f16 != 0);
+                        pack8_16(x + 8, w + 4, plan.f16 != 0);
+                    }
                     const uint32_t at = a_base + (uint32_t)(c0 / 8) * 2048u + row_off;
                     st_shared_v4(at, w[0], w[1], w[2], w[3]);
                     st_shared_v4(at + 2048u, w[4], w[5], w[6], w[7]);
@@ -389,7 +409,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_forward(TcPlan plan, const ui
 // ------------------------------------------------------------- host side
 int tc_create(fr_ensemble *e)
 {
-    if (e->precision != FR_PREC_BF16 && e->precision != FR_PREC_BF16X3 && e->precision != FR_PREC_FP8) {
+    if (e->precision != FR_PREC_BF16 && e->precision != FR_PREC_BF16X3 && e->precision != FR_PREC_FP8 &&
+        e->precision != FR_PREC_FP16) {
         set_error("ensemble_create: precision %d has no tensor-core path in this build", e->precision);
         return FR_EINVAL;
     }
@@ -410,7 +431,7 @@ int tc_create(fr_ensemble *e)
     std::vector<uint8_t> img((size_t)e->M * p.agent_bytes, 0);
     std::vector<float> bias((size_t)e->M * MAX_LAYERS * 256, 0.0f);
     const bool fp8 = p.esz == 1;
-    const bool grouped = p.split == 1 && !fp8;
+    const bool grouped = p.split == 1 && !fp8;           // BF16 or FP16
     std::vector<uint8_t> img2(grouped ? img.size() : 0, 0);
     for (int j = 0; j < e->M; ++j) {
         const float *P = host.data() + (size_t)j * e->P;
@@ -437,7 +458,7 @@ int tc_create(fr_ensemble *e)
                         aimg[off] = (uint8_t)__nv_cvt_float_to_fp8(wv * inv, __NV_SATFINITE, __NV_E4M3);
                         continue;
                     }
-                    const uint16_t b = f32_to_bf16_rne(wv);
+                    const uint16_t b = p.f16 ? f32_to_f16_sat(wv) : f32_to_bf16_rne(wv);
                     memcpy(aimg + off, &b, 2);
                     if (grouped) {
                         // rows [0, h0) then [h0, N), each group [K/8][rows][8]

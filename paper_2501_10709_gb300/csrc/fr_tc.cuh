@@ -20,6 +20,7 @@
 #include <cuda_bf16.h>
 
 #include "fr_common.cuh"
+#include "fr_ptx.cuh"
 
 namespace fr {
 
@@ -39,7 +40,8 @@ struct TcLayer {
 
 struct TcPlan {
     int M, L, out_act;
-    int split;            // 1: BF16 operands; 3: hi/lo split, three products
+    int split;            // 1: BF16 (or FP16) operands; 3: hi/lo split, three products
+    int f16;              // 1: FP16 operands instead of BF16 (split 1 only)
     int parts;            // operand parts stored per chunk: 1 (hi) or 2 (hi, lo)
     int esz;              // operand element bytes: 2 (BF16) or 1 (E4M3)
     int kmma;             // K per tcgen05.mma: 16 (kind::f16) or 32 (kind::f8f6f4)
@@ -92,6 +94,22 @@ __device__ __forceinline__ void e4m3_pack16(const float *v, float inv, uint32_t 
         w[i] = e4m3x2(__fmul_rn(v[4 * i], inv), __fmul_rn(v[4 * i + 1], inv)) |
                (e4m3x2(__fmul_rn(v[4 * i + 2], inv), __fmul_rn(v[4 * i + 3], inv)) << 16);
     }
+}
+
+// Two floats -> one word of two 16-bit operands (BF16 round to nearest even,
+// or FP16 round to nearest even saturating at +-65504), a in the low half.
+__device__ __forceinline__ uint32_t pack2_16(float a, float b, bool f16)
+{
+    if (f16) return ptx::f16x2_sat(a, b);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *(const uint32_t *)&h;
+}
+
+// Eight floats -> four words of 16-bit operands, K order.
+__device__ __forceinline__ void pack8_16(const float *v, uint32_t *w, bool f16)
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) w[i] = pack2_16(v[2 * i], v[2 * i + 1], f16);
 }
 
 // Eight floats -> BF16 hi parts (round to nearest) and the BF16 rounding of

@@ -14,7 +14,9 @@ from paper_2501_10709_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-REL_TOL = {fr.PREC_FP32: 1e-4, fr.PREC_BF16: 2e-2, fr.PREC_BF16X3: 2e-3}
+# FP16 (10 stored mantissa bits against BF16's 7): BF16's bar scaled by the
+# ratio of the unit roundoffs, 2e-2 * 2^-11 / 2^-8
+REL_TOL = {fr.PREC_FP32: 1e-4, fr.PREC_BF16: 2e-2, fr.PREC_BF16X3: 2e-3, fr.PREC_FP16: 2.5e-3}
 
 
 def _stock_obs(n, seed=21):
@@ -45,7 +47,7 @@ def _oracle_agents(dims, params, obs, out_act):
     return np.stack([oracle.net_forward(dims, params[j], obs, out_act) for j in range(params.shape[0])])
 
 
-@pytest.mark.parametrize("precision", [fr.PREC_FP32, fr.PREC_BF16, fr.PREC_BF16X3])
+@pytest.mark.parametrize("precision", [fr.PREC_FP32, fr.PREC_BF16, fr.PREC_BF16X3, fr.PREC_FP16])
 @pytest.mark.parametrize("dims,n", [((301, 64, 64, 30), 1000), ((301, 256, 256, 30), 2048),
                                     ((301, 256, 256, 30), 129), ((301, 64, 32, 30), 300)])
 def test_stock_actor_outputs(ctx, dev, precision, dims, n):
@@ -65,7 +67,7 @@ def test_stock_actor_outputs(ctx, dev, precision, dims, n):
     assert fr.ensemble_device_errors(ens) == 0
 
 
-@pytest.mark.parametrize("precision", [fr.PREC_FP32, fr.PREC_BF16])
+@pytest.mark.parametrize("precision", [fr.PREC_FP32, fr.PREC_BF16, fr.PREC_FP16])
 def test_stock_ensemble_mean_and_shares(ctx, dev, precision):
     dims = (301, 256, 256, 30)
     params = synth.actor_params(dims, 3, seed=5)
@@ -91,7 +93,7 @@ def test_identical_agents_equal_one_agent_on_gpu(ctx, dev):
     dims = (301, 256, 256, 30)
     one = synth.actor_params(dims, 1, seed=6)
     obs = torch.from_numpy(_stock_obs(777)).to(dev)
-    for prec in (fr.PREC_FP32, fr.PREC_BF16):
+    for prec in (fr.PREC_FP32, fr.PREC_BF16, fr.PREC_FP16):
         e1 = fr.ensemble_create(ctx, dims, one, precision=prec)
         e3 = fr.ensemble_create(ctx, dims, np.repeat(one, 3, 0), precision=prec)
         a1 = torch.empty(777, 30, device=dev)
@@ -102,7 +104,7 @@ def test_identical_agents_equal_one_agent_on_gpu(ctx, dev):
         assert torch.equal(a1, a3)
 
 
-@pytest.mark.parametrize("precision", [fr.PREC_FP32, fr.PREC_BF16X3, fr.PREC_BF16])
+@pytest.mark.parametrize("precision", [fr.PREC_FP32, fr.PREC_BF16X3, fr.PREC_BF16, fr.PREC_FP16])
 def test_crypto_argmax_and_vote_agreement(ctx, dev, precision):
     dims = (10, 128, 128, 3)
     params = synth.actor_params(dims, 5, seed=8, out_scale=4.0)
@@ -133,7 +135,10 @@ def test_crypto_argmax_and_vote_agreement(ctx, dev, precision):
         # argmax of rows whose Q gap is below its error (reported, not the bar)
         assert agree >= 0.99 and vote_agree >= 0.99
     else:
-        assert err.max() <= REL_TOL[precision]
+        # FP16 Q-values: rows whose Q norm is near the 1e-3 floor carry the
+        # absolute error of three FP16 roundings, so the bound here is the
+        # stated actor bar 2e-2; the decisions carry the 99.9% bar
+        assert err.max() <= (2e-2 if precision == fr.PREC_FP16 else REL_TOL[precision])
         assert agree >= 0.999 and vote_agree >= 0.999
 
 
@@ -149,13 +154,16 @@ def test_empty_and_single_row(ctx, dev):
     assert torch.isfinite(act).all()
 
 
-@pytest.mark.parametrize("dims, M, waves, extra, vote", [(synth.STOCK_DIMS, 3, 1, 77, False),
-                                                         (synth.STOCK_DIMS, 3, 4, 77, False),
-                                                         ((301, 80, 48, 30), 2, 1, 1, False),
-                                                         ((301, 80, 48, 30), 2, 3, 0, False),
-                                                         (synth.CRYPTO_DIMS, 5, 1, 127, True),
-                                                         (synth.CRYPTO_DIMS, 5, 5, 3, True)])
-def test_tiled_actor_equals_single_agent_kernel(ctx, dev, dims, M, waves, extra, vote):
+@pytest.mark.parametrize("dims, M, waves, extra, vote, precision",
+                         [(synth.STOCK_DIMS, 3, 1, 77, False, fr.PREC_BF16),
+                          (synth.STOCK_DIMS, 3, 4, 77, False, fr.PREC_BF16),
+                          ((301, 80, 48, 30), 2, 1, 1, False, fr.PREC_BF16),
+                          ((301, 80, 48, 30), 2, 3, 0, False, fr.PREC_BF16),
+                          (synth.CRYPTO_DIMS, 5, 1, 127, True, fr.PREC_BF16),
+                          (synth.CRYPTO_DIMS, 5, 5, 3, True, fr.PREC_BF16),
+                          (synth.STOCK_DIMS, 3, 2, 5, False, fr.PREC_FP16),
+                          (synth.CRYPTO_DIMS, 5, 2, 9, True, fr.PREC_FP16)])
+def test_tiled_actor_equals_single_agent_kernel(ctx, dev, dims, M, waves, extra, vote, precision):
     # At batches of at least one 128-row tile per SM (plus a ragged tail),
     # ensemble_act runs the large-batch kernel (persistent CTAs taking every
     # agent of a tile, tiled BF16 observations double-buffered, several tiles
@@ -164,7 +172,7 @@ def test_tiled_actor_equals_single_agent_kernel(ctx, dev, dims, M, waves, extra,
     n = waves * ctx.sm_count * 128 + extra
     params = synth.actor_params(dims, M, seed=21, out_scale=4.0 if vote else 1.0)
     kw = dict(combine=fr.COMBINE_VOTE, out_act=0) if vote else {}
-    ens = fr.ensemble_create(ctx, dims, params, precision=fr.PREC_BF16, **kw)
+    ens = fr.ensemble_create(ctx, dims, params, precision=precision, **kw)
     rng = np.random.default_rng(5)
     obs = torch.from_numpy(rng.uniform(-1.5, 1.5, (n, dims[0])).astype(np.float32)).to(dev)
     if vote:
@@ -188,10 +196,10 @@ def test_tiled_actor_equals_single_agent_kernel(ctx, dev, dims, M, waves, extra,
         want = oracle.net_forward(dims, params[j], o, 0 if vote else 1)
         got = y[j].cpu().numpy().astype(np.float64)[rows]
         if vote:    # BF16 Q-values are judged by their decisions, as in the crypto tests
-            assert np.mean(got.argmax(-1) == want.argmax(-1)) >= 0.99
+            assert np.mean(got.argmax(-1) == want.argmax(-1)) >= (0.99 if precision == fr.PREC_BF16 else 0.999)
         else:
             err = np.linalg.norm(got - want, axis=-1) / np.maximum(np.linalg.norm(want, axis=-1), 1e-3)
-            assert err.max() <= REL_TOL[fr.PREC_BF16], err.max()
+            assert err.max() <= REL_TOL[precision], err.max()
 
 
 @pytest.mark.parametrize("dims, M, extra, shared", [(synth.STOCK_DIMS, 3, 77, True), ((301, 80, 48, 30), 2, 1, True),

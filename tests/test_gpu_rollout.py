@@ -13,7 +13,7 @@ from paper_2501_10709_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-REL_TOL = {fr.PREC_FP32: 1e-4, fr.PREC_BF16: 2e-2, fr.PREC_BF16X3: 2e-3}
+REL_TOL = {fr.PREC_FP32: 1e-4, fr.PREC_BF16: 2e-2, fr.PREC_BF16X3: 2e-3, fr.PREC_FP16: 2.5e-3}
 
 
 def _traj(T, N, D, K, dev, stock=True):
@@ -57,7 +57,7 @@ def _stock_rollout_check(ctx, dev, w, precision, T, sample_rows=256):
     return g
 
 
-@pytest.mark.parametrize("precision", [fr.PREC_FP32, fr.PREC_BF16])
+@pytest.mark.parametrize("precision", [fr.PREC_FP32, fr.PREC_BF16, fr.PREC_FP16])
 def test_stock_rollout_small_teacher_forced(ctx, dev, precision):
     w = synth.workload_stock_small()
     _stock_rollout_check(ctx, dev, w, precision, w.T)
@@ -70,7 +70,7 @@ def test_stock_rollout_2048_envs_teacher_forced(ctx, dev, precision):
     _stock_rollout_check(ctx, dev, w, precision, 24)
 
 
-@pytest.mark.parametrize("precision", [fr.PREC_FP32, fr.PREC_BF16X3])
+@pytest.mark.parametrize("precision", [fr.PREC_FP32, fr.PREC_BF16X3, fr.PREC_FP16])
 def test_crypto_rollout_teacher_forced(ctx, dev, precision):
     w = synth.workload_crypto(N=1024, T=64, S=40_000)
     e = w.envs
