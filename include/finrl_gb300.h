@@ -591,52 +591,82 @@ int replay_size_sync(fr_replay *rb, int64_t *size, int64_t *pushed, uint32_t *er
 /* ---------------------------------------------------------------- serving */
 /* Backtests as requests: many independent backtests (each a group of envs
  * over one window, Sec. 4.2.1 trajectories) served by one GPU with
- * continuous batching.  The server owns a pool of `capacity` env slots over
- * one market and runs the ensemble's rollout on the whole pool in chunks of
- * `chunk_steps` steps (the fused kernel for BF16 ensembles).  At every chunk
- * boundary it retires the requests whose windows are complete (their rows of
- * the episode metrics go to the caller's host buffer) and admits queued
- * requests into the freed slots in arrival order; a request waits while the
- * one ahead of it does not fit.  One host thread per server drives the GPU
- * on its own stream; submit and poll only touch host state and never block
- * on the GPU.  No counterpart in the paper beyond running many
- * trajectories in parallel. */
+ * continuous batching.  A server owns one or more pools; a pool is an env
+ * batch of `capacity` slots over one market, run with one ensemble in
+ * chunks of `chunk_steps` steps on its own stream by its own host thread, so
+ * the chunks of different pools (a stock and a crypto pool, say) overlap
+ * on the device.  At every chunk boundary a pool retires the requests whose
+ * windows are complete (their rows of the episode metrics go to the
+ * caller's host buffer) and admits its queued requests in arrival order
+ * while the freed slots and the server's HBM budget cover them; a request
+ * waits while the one ahead of it in its pool does not fit.  Env state
+ * stays resident in the pool; a request that records its trajectory keeps
+ * it on the device (Sec. 4.3.2) until the caller fetches or releases it.
+ * Submit, poll, fetch and release never wait for a running chunk.  No
+ * counterpart in the paper beyond running many trajectories in parallel. */
 typedef struct fr_server fr_server;
 
 typedef struct {
-    const fr_market *market;  /* borrowed; outlives the server              */
-    const fr_ensemble *ens;   /* borrowed; combine/output match the task    */
-    int32_t capacity;         /* env slots, >= 1                            */
-    int32_t chunk_steps;      /* steps per rollout launch, >= 1             */
-    int64_t init_cash;        /* cents, >= 0                                */
+    const fr_market *market;  /* the first pool's market (borrowed; outlives
+                                 the server)                                */
+    const fr_ensemble *ens;   /* the first pool's ensemble (borrowed);
+                                 combine/output match the market's task     */
+    int32_t capacity;         /* the first pool's env slots, >= 1           */
+    int32_t chunk_steps;      /* the first pool's steps per launch, >= 1    */
+    int64_t init_cash;        /* cents, >= 0 (every pool)                   */
     int32_t hmax;             /* stock: 1..1e6                              */
     int32_t fee_bps;          /* stock: 0..10000                            */
     int32_t pmax;             /* crypto: >= 1                               */
+    uint64_t hbm_budget;      /* bytes of device memory the server may hold
+                                 for admitted requests (below); 0 = no server
+                                 limit (trajectory buffers are still bounded
+                                 by the context's budget)                   */
 } fr_server_desc;
 
-/* Create / destroy.  Destroy stops the worker after its current chunk;
- * requests not yet complete are dropped (their tickets become unknown).
+/* Create / destroy.  Destroy stops the workers after their current chunks;
+ * requests not yet complete are dropped (their tickets become unknown) and
+ * trajectories not fetched are freed.
  * A rollout chunk that fails with a CUDA error fails every request and every
  * later submit (the context may be unusable); one that fails otherwise (e.g.
- * FR_ENOMEM when the HBM budget cannot cover the rollout's scratch) fails
- * the requests of that chunk with that status, frees their slots, and the
- * server goes on with the queued requests. */
+ * FR_ENOMEM when the context's budget cannot cover the rollout's scratch)
+ * fails the requests of that chunk with that status, frees their slots, and
+ * the pool goes on with its queued requests. */
 int fr_server_create(fr_ctx *ctx, const fr_server_desc *desc, fr_server **out);
 void fr_server_destroy(fr_server *srv);
+
+/* Add a pool to the server for another (market, ensemble) pair, e.g. the
+ * crypto pool beside a stock pool; its worker starts at once.  FR_EINVAL
+ * when the ensemble does not match the market's observation and task, or
+ * already has a pool in this server. */
+int fr_server_add_pool(fr_server *srv, const fr_market *market, const fr_ensemble *ens, int32_t capacity,
+                       int32_t chunk_steps);
 
 /* One backtest: n_envs envs, env i over days (or seconds)
  * start + i*start_stride .. + window - 1; stock envs trade the first
  * n_assets assets with per-env per-asset price perturbations drawn from
  * `seed` uniformly in [-bps_range, bps_range] basis points (Sec. 5.1;
  * env_perturb's rule, drawn on the device, with e the env's index within the
- * request).  metrics: caller-owned host buffer
+ * request).  The request goes to the pool of `ens`, or with ens NULL to the
+ * first pool of `task`.  metrics: caller-owned host buffer
  * double [n_envs][3] (cumulative return, Sharpe, max drawdown, as
  * env_metrics), written by the server before the request reports done; it
- * must stay valid until then.  want_traj must be 0: the server returns
- * metrics only.  Errors at submit: bad fields or a window past the market
- * end -> FR_EINVAL; n_envs > capacity (can never fit) -> FR_ENOMEM; a
- * server whose worker failed -> that error.  A request that fits later is
- * queued. */
+ * must stay valid until then.  want_traj = 1: the server also records the
+ * request's T x N x D trajectory (T = window - 1 rows of n_envs envs:
+ * observation, combined action, reward, done, as rollout's fr_traj) into a
+ * device buffer of its own, kept after completion until backtest_fetch_traj
+ * or backtest_release.
+ * HBM budget: a request is charged n_envs times its pool's state bytes per
+ * slot, plus with want_traj T * n_envs * (4 D + 4 K + 9) bytes (stock) or
+ * T * n_envs * (4 D + 10) (crypto); a pool admits its queue head only when
+ * the server's charged bytes plus the head's stay within hbm_budget.  The
+ * slot charge returns when the request completes or fails; the trajectory
+ * charge when it is fetched or released.
+ * Errors at submit: bad fields, a task or ensemble no pool serves, or a
+ * window past the market end -> FR_EINVAL; n_envs above the pool's capacity
+ * or a charge above hbm_budget (can never fit) -> FR_ENOMEM; a server whose
+ * worker failed -> that error.  A request that fits later is queued; one
+ * whose trajectory buffer the context's budget cannot hold at admission
+ * completes with status FR_ENOMEM. */
 typedef struct {
     int32_t n_envs;
     int32_t window;           /* >= 2                                       */
@@ -645,11 +675,13 @@ typedef struct {
     int32_t n_assets;         /* stock: 1..K (0 = K)                        */
     int32_t bps_range;        /* stock: 0..100                              */
     uint64_t seed;
-    int32_t want_traj;        /* must be 0                                  */
+    int32_t want_traj;        /* 0 or 1                                     */
     double *metrics;          /* host [n_envs][3]                           */
     double timeout_s;         /* > 0: a request not complete this long after
                                  submit ends with status FR_ETIMEDOUT (checked
                                  at chunk boundaries); 0 = none             */
+    int32_t task;             /* FR_TASK_STOCK or FR_TASK_CRYPTO            */
+    const fr_ensemble *ens;   /* the pool's ensemble, or NULL               */
 } fr_request;
 
 typedef struct {
@@ -657,28 +689,54 @@ typedef struct {
     int32_t n_envs;
     double queue_s;           /* submit -> admitted into slots              */
     double latency_s;         /* submit -> metrics written                  */
+    int32_t task;
+    int32_t traj_steps;       /* rows of the kept trajectory (0: none)      */
+    uint64_t traj_bytes;      /* device bytes it holds until fetched        */
 } fr_result;
 
 int backtest_submit(fr_server *srv, const fr_request *req, uint64_t *ticket);
 
 /* Non-blocking.  Running or queued: FR_ENOTREADY, *done = 0.  Complete:
- * FR_OK, *done = 1, *out filled, and the ticket is released (a later poll
- * of it returns FR_ENOTFOUND).  Unknown ticket: FR_ENOTFOUND. */
+ * FR_OK, *done = 1, *out filled; the ticket is then released (a later poll
+ * returns FR_ENOTFOUND) unless a trajectory is kept, which keeps the ticket
+ * until backtest_fetch_traj or backtest_release.  Unknown ticket:
+ * FR_ENOTFOUND. */
 int backtest_poll(fr_server *srv, uint64_t ticket, fr_result *out, int32_t *done);
+
+/* Copy a completed request's kept trajectory into dst (device or host
+ * pointers, each nullable: obs float [T][n_envs][obs_ld] (obs_ld >= D, 0 = D),
+ * act float [T][n_envs][K] (stock) or uint8 [T][n_envs] (crypto), rew int64
+ * [T][n_envs], done uint8 [T][n_envs]; rew_f32 is not kept and is ignored),
+ * on `stream`, wait for the copies, then free the server's copy, return its
+ * budget charge and release the ticket.  FR_ENOTREADY while the request
+ * runs; FR_ENOTFOUND for a ticket without a kept trajectory. */
+int backtest_fetch_traj(fr_server *srv, uint64_t ticket, const fr_traj *dst, void *stream);
+
+/* Free a completed request's kept trajectory without copying it and
+ * release the ticket (FR_ENOTREADY while it runs, FR_ENOTFOUND unknown). */
+int backtest_release(fr_server *srv, uint64_t ticket);
 
 /* Cancel a request.  Queued: it completes at once with status FR_ECANCELED.
  * Running: it is retired at the next chunk boundary with status
- * FR_ECANCELED (its slots freed, its metrics buffer left unwritten).
- * Complete but not yet polled: no effect.  Either way the ticket is polled
- * as usual.  Unknown ticket: FR_ENOTFOUND.  Other requests are unaffected. */
+ * FR_ECANCELED (its slots freed, its metrics buffer left unwritten, no
+ * trajectory kept).  Complete but not yet polled: no effect.  Either way the
+ * ticket is polled as usual.  Unknown ticket: FR_ENOTFOUND.  Other requests
+ * are unaffected. */
 int backtest_cancel(fr_server *srv, uint64_t ticket);
 
 typedef struct {
     uint64_t submitted, completed, queued, running;
-    double env_steps;         /* slot-steps of requests run (their windows) */
-    double pool_steps;        /* capacity x steps launched                  */
-    double busy_s;            /* wall time of the worker's GPU rounds       */
-    uint64_t failed;          /* requests finished with an error status     */
+    double env_steps;         /* slot-steps of requests completed (windows) */
+    double pool_steps;        /* capacity x steps launched, all pools       */
+    double busy_s;            /* wall time of the workers' GPU rounds       */
+    uint64_t failed;          /* requests finished with an error other than
+                                 FR_ECANCELED and FR_ETIMEDOUT              */
+    uint64_t canceled;        /* finished with FR_ECANCELED                 */
+    uint64_t timed_out;       /* finished with FR_ETIMEDOUT                 */
+    uint64_t bytes_reserved;  /* budget bytes charged now                   */
+    uint64_t bytes_peak;      /* the most charged at once                   */
+    uint64_t budget;          /* hbm_budget (0 = none)                      */
+    uint64_t pools;
 } fr_server_stats;
 
 int fr_server_stats_get(fr_server *srv, fr_server_stats *out);

@@ -25,7 +25,8 @@ __all__ = [
     "ensemble_act", "ensemble_act_noalloc", "ensemble_device_errors", "rollout", "env_set_rollout_path", "env_set_kernel_timing", "env_last_kernel_ms", "env_set_tile_packing",
     "env_tile_packing_efficiency", "ensemble_set_weights", "ensemble_validate", "trajectory_metrics", "env_set_exploration",
     "EXPLORE_NONE", "EXPLORE_GAUSSIAN", "EXPLORE_EPS_GREEDY", "Server", "fr_server_create", "backtest_submit",
-    "backtest_poll", "backtest_cancel", "fr_server_stats", "FrError", "lib", "market_indicators", "fr_market_indicators",
+    "backtest_poll", "backtest_cancel", "fr_server_stats", "fr_server_add_pool", "backtest_fetch_traj",
+    "backtest_release", "FrError", "lib", "market_indicators", "fr_market_indicators",
     "env_perturb", "ensemble_set_act_scales", "ensemble_get_act_scales", "ensemble_calibrate_sync",
     "Replay", "replay_create", "replay_push", "replay_sample", "replay_size", "ensemble_q", "ensemble_q_targets",
     "HEAD_Q", "HEAD_DUELING", "env_autotune", "env_tune_clear", "env_tune_set",
@@ -505,12 +506,14 @@ def replay_size(rb: Replay, stream=None):
 
 # ------------------------------------------------------------------ serving
 class Server(_Handle):
-    """Backtest server (continuous batching over a pool of env slots)."""
+    """Backtest server (continuous batching over pools of env slots)."""
     _destroy = "fr_server_destroy"
 
-    def __init__(self, ptr, keep=()):
+    def __init__(self, ptr, keep=(), task=0):
         super().__init__(ptr, keep)
+        self.task = task              # the first pool's task (requests default to it)
         self._pending = {}            # ticket -> host metrics buffer the worker writes
+        self._shape = {}              # ticket -> (task, n_envs, window, D, K) of kept trajectories
 
     def close(self):
         super().close()
@@ -519,20 +522,29 @@ class Server(_Handle):
 
 def fr_server_create(ctx: Ctx, market: Market, ens: Ensemble, *, capacity: int, chunk_steps: int = 32,
                      init_cash: int = 100_000_000, hmax: int = 100, fee_bps: int = 10,
-                     pmax: int = 10) -> Server:
+                     pmax: int = 10, hbm_budget: int = 0) -> Server:
     d = _lib.ServerDesc(market.ptr, ens.ptr, int(capacity), int(chunk_steps), int(init_cash), int(hmax),
-                        int(fee_bps), int(pmax))
+                        int(fee_bps), int(pmax), int(hbm_budget))
     out = C.c_void_p()
     _lib.check(lib().fr_server_create(ctx, C.byref(d), C.byref(out)), "fr_server_create")
-    return Server(out.value, keep=(ctx, market, ens))
+    return Server(out.value, keep=(ctx, market, ens), task=market.task)
+
+
+def fr_server_add_pool(srv: Server, market: Market, ens: Ensemble, *, capacity: int, chunk_steps: int = 32):
+    """Another pool (market, ensemble) in the same server, e.g. crypto beside stock."""
+    _lib.check(lib().fr_server_add_pool(srv, market.ptr, ens.ptr, int(capacity), int(chunk_steps)),
+               "fr_server_add_pool")
+    srv._keep = tuple(srv._keep) + (market, ens)
 
 
 def backtest_submit(srv: Server, *, n_envs: int, window: int, start: int, start_stride: int = 0,
-                    n_assets: int = 0, bps_range: int = 0, seed: int = 0, timeout_s: float = 0.0) -> int:
+                    n_assets: int = 0, bps_range: int = 0, seed: int = 0, timeout_s: float = 0.0,
+                    task: int = None, ens: Ensemble = None, want_traj: bool = False) -> int:
     met = np.zeros((int(n_envs), 3), dtype=np.float64)
+    task = srv.task if task is None else int(task)
     r = _lib.Request(int(n_envs), int(window), int(start), int(start_stride), int(n_assets),
-                     int(bps_range), int(seed) & (2**64 - 1), 0, met.ctypes.data_as(C.c_void_p),
-                     float(timeout_s))
+                     int(bps_range), int(seed) & (2**64 - 1), 1 if want_traj else 0, met.ctypes.data_as(C.c_void_p),
+                     float(timeout_s), task, ens.ptr if ens is not None else None)
     t = C.c_uint64()
     _lib.check(lib().backtest_submit(srv, C.byref(r), C.byref(t)), "backtest_submit")
     srv._pending[t.value] = met
@@ -541,7 +553,9 @@ def backtest_submit(srv: Server, *, n_envs: int, window: int, start: int, start_
 
 def backtest_poll(srv: Server, ticket: int):
     """None while queued or running; else a dict with the request's result
-    (status, n_envs, queue_s, latency_s, metrics [n_envs][3])."""
+    (status, n_envs, queue_s, latency_s, task, traj_steps, traj_bytes,
+    metrics [n_envs][3]).  A kept trajectory (traj_steps > 0) is then
+    fetched with backtest_fetch_traj or dropped with backtest_release."""
     res = _lib.Result()
     done = C.c_int32()
     rc = lib().backtest_poll(srv, C.c_uint64(int(ticket)), C.byref(res), C.byref(done))
@@ -549,8 +563,35 @@ def backtest_poll(srv: Server, ticket: int):
         return None
     _lib.check(rc, "backtest_poll")
     met = srv._pending.pop(int(ticket))
+    if res.traj_steps:
+        srv._shape[int(ticket)] = (res.task, res.n_envs, res.traj_steps)
     return {"status": res.status, "n_envs": res.n_envs, "queue_s": res.queue_s,
-            "latency_s": res.latency_s, "metrics": met}
+            "latency_s": res.latency_s, "task": res.task, "traj_steps": res.traj_steps,
+            "traj_bytes": res.traj_bytes, "metrics": met}
+
+
+def backtest_fetch_traj(srv: Server, ticket: int, *, D: int, K: int = 30, device="cuda", stream=None) -> dict:
+    """The kept trajectory of a completed request as tensors on `device`
+    (obs [T][n][D], act [T][n][K] float (stock) or [T][n] uint8 (crypto), rew
+    int64 [T][n], done uint8 [T][n]); the server's copy is freed."""
+    import torch
+    task, n, T = srv._shape.pop(int(ticket))
+    out = {"obs": torch.empty(T, n, D, device=device),
+           "act": (torch.empty(T, n, K, device=device) if task == _lib.TASK_STOCK
+                   else torch.empty(T, n, dtype=torch.uint8, device=device)),
+           "rew": torch.empty(T, n, dtype=torch.int64, device=device),
+           "done": torch.empty(T, n, dtype=torch.uint8, device=device)}
+    tr = _lib.Traj(out["obs"].data_ptr(), D, out["act"].data_ptr(), out["rew"].data_ptr(), None,
+                   out["done"].data_ptr())
+    _lib.check(lib().backtest_fetch_traj(srv, C.c_uint64(int(ticket)), C.byref(tr), _stream(stream)),
+               "backtest_fetch_traj")
+    return out
+
+
+def backtest_release(srv: Server, ticket: int):
+    """Drop a completed request's kept trajectory without copying it."""
+    srv._shape.pop(int(ticket), None)
+    _lib.check(lib().backtest_release(srv, C.c_uint64(int(ticket))), "backtest_release")
 
 
 def backtest_cancel(srv: Server, ticket: int):

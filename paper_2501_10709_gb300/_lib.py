@@ -73,22 +73,25 @@ EXPLORE_NONE, EXPLORE_GAUSSIAN, EXPLORE_EPS_GREEDY = 0, 1, 2
 
 class ServerDesc(C.Structure):
     _fields_ = [("market", vp), ("ens", vp), ("capacity", i32), ("chunk_steps", i32),
-                ("init_cash", i64), ("hmax", i32), ("fee_bps", i32), ("pmax", i32)]
+                ("init_cash", i64), ("hmax", i32), ("fee_bps", i32), ("pmax", i32), ("hbm_budget", u64)]
 
 
 class Request(C.Structure):
     _fields_ = [("n_envs", i32), ("window", i32), ("start", i32), ("start_stride", i32),
                 ("n_assets", i32), ("bps_range", i32), ("seed", u64), ("want_traj", i32),
-                ("metrics", vp), ("timeout_s", f64)]
+                ("metrics", vp), ("timeout_s", f64), ("task", i32), ("ens", vp)]
 
 
 class Result(C.Structure):
-    _fields_ = [("status", i32), ("n_envs", i32), ("queue_s", f64), ("latency_s", f64)]
+    _fields_ = [("status", i32), ("n_envs", i32), ("queue_s", f64), ("latency_s", f64),
+                ("task", i32), ("traj_steps", i32), ("traj_bytes", u64)]
 
 
 class ServerStats(C.Structure):
     _fields_ = [("submitted", u64), ("completed", u64), ("queued", u64), ("running", u64),
-                ("env_steps", f64), ("pool_steps", f64), ("busy_s", f64), ("failed", u64)]
+                ("env_steps", f64), ("pool_steps", f64), ("busy_s", f64), ("failed", u64),
+                ("canceled", u64), ("timed_out", u64), ("bytes_reserved", u64), ("bytes_peak", u64),
+                ("budget", u64), ("pools", u64)]
 
 
 # name -> (restype, argtypes); every symbol the header declares
@@ -133,6 +136,9 @@ SIGNATURES = {
     "backtest_submit": (i32, [vp, vp, vp]),
     "backtest_poll": (i32, [vp, u64, vp, vp]),
     "backtest_cancel": (i32, [vp, u64]),
+    "fr_server_add_pool": (i32, [vp, vp, vp, i32, i32]),
+    "backtest_fetch_traj": (i32, [vp, u64, vp, vp]),
+    "backtest_release": (i32, [vp, u64]),
     "fr_server_stats_get": (i32, [vp, vp]),
     "fr_fault_inject": (i32, [i32, i32, i32]),
     "fr_wait_selftest": (i32, [vp, i32, vp, vp]),
