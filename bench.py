@@ -62,6 +62,41 @@ def _dist():
     return rank, world
 
 
+def _free_port() -> int:
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def launch_replicas(n: int, argv: list) -> int:
+    """Run this script as n replicas, one process per GPU, through torch's
+    launcher on 127.0.0.1 (each rank gets RANK / LOCAL_RANK / WORLD_SIZE and
+    runs its own copy of the workload); rank 0's JSON line passes through.
+    Returns the launcher's exit status."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", f"--master-port={_free_port()}", os.path.abspath(__file__)] + list(argv)
+    return subprocess.call(cmd)
+
+
+def replica_check():
+    """The launcher and the timing reduction without a GPU (gloo): every
+    rank reports a stand-in time; rank 0 prints the max and the whole-job
+    value of 100 units per rank and step over 2 steps."""
+    import torch.distributed as dist
+    rank, world = _dist()
+    dist.init_process_group("gloo")
+    t = 0.1 * (rank + 1)
+    m = max_over_ranks(t)
+    v = replica_value(world, 100, 2, m)
+    dist.barrier()
+    dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps({"replica_check": True, "n_gpus": world, "max_s": m, "value": v}), flush=True)
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -283,6 +318,83 @@ def serving_line(fr, ctx, mk, ens_by_name, duration=10.0, rate=200.0, drain_s=60
     return out
 
 
+def serving_c5_line(fr, ctx, mk_stock, w_stock, duration=5.0, rate=200.0, drain_s=10.0, budget=150e9):
+    """The mixed serving workload: one Poisson trace at `rate`/s for
+    `duration` s, half stock backtests (N ~ U{1..512}, W ~ U{5..500} days)
+    and half crypto (N ~ U{1..2048}, W ~ U{3,600..86,400} s), 10% recording
+    their trajectories, against one server with a stock pool (2,048 slots,
+    16-step chunks) and a crypto pool (8,192 slots, 256-step chunks) under a
+    150 GB HBM budget; then at most drain_s s of drain.  Latency = scheduled
+    arrival -> poll reports done (kept trajectories are then released).
+    The same trace runs on the fused 16-bit path (stock BF16, crypto FP16)
+    and on the plain FP32 path."""
+    import numpy as np
+    from paper_2501_10709_gb300 import synth
+    wc = synth.workload_crypto()
+    mk_c = fr.fr_market_create(ctx, wc.market)
+    trace = synth.serving_trace_mixed(rate, duration)
+    off = {t: sum(r["n_envs"] * (r["window"] - 1) for r in trace if r["task"] == t) / duration for t in (0, 1)}
+    out = {"workload": f"Poisson {rate:g}/s for {duration:g} s ({len(trace)} requests), 50/50 stock/crypto, "
+                       f"10% recording trajectories; stock N ~ U{{1..512}}, W ~ U{{5..500}} days; crypto "
+                       f"N ~ U{{1..2048}}, W ~ U{{3600..86400}} s; pools of 2,048 stock and 8,192 crypto slots; "
+                       f"HBM budget {budget / 1e9:g} GB; drain at most {drain_s:g} s",
+           "requests": {"stock": sum(r["task"] == 0 for r in trace), "crypto": sum(r["task"] == 1 for r in trace)},
+           "offered_env_steps_per_s": {"stock": off[0], "crypto": off[1]}}
+    paths = {"fused_16bit": (fr.PREC_BF16, fr.PREC_FP16), "plain_fp32": (fr.PREC_FP32, fr.PREC_FP32)}
+    for name, (ps, pc) in paths.items():
+        ens_s = fr.ensemble_create(ctx, w_stock.dims, w_stock.params, precision=ps)
+        ens_c = fr.ensemble_create(ctx, wc.dims, wc.params, precision=pc, combine=fr.COMBINE_VOTE, out_act=0)
+        srv = fr.fr_server_create(ctx, mk_stock, ens_s, capacity=2048, chunk_steps=16, hbm_budget=int(budget))
+        fr.fr_server_add_pool(srv, mk_c, ens_c, capacity=8192, chunk_steps=256)
+        for task, req in ((0, dict(n_envs=8, window=20, start=100)), (1, dict(n_envs=8, window=600, start=4000))):
+            t = fr.backtest_submit(srv, task=task, **req)        # warm: kernel images, tables
+            while fr.backtest_poll(srv, t) is None:
+                time.sleep(0.001)
+        st0 = fr.fr_server_stats(srv)
+        pending, lat, i = {}, {0: [], 1: []}, 0
+        served = {0: 0.0, 1: 0.0}
+        t0 = time.perf_counter()
+        while i < len(trace) or pending:
+            now = time.perf_counter() - t0
+            while i < len(trace) and trace[i]["t"] <= now:
+                r = dict(trace[i])
+                ta = r.pop("t")
+                tk = fr.backtest_submit(srv, **r)
+                pending[tk] = (ta, r["task"], r["n_envs"] * (r["window"] - 1))
+                i += 1
+            for tk in list(pending):
+                res = fr.backtest_poll(srv, tk)
+                if res is not None:
+                    ta, task, work = pending.pop(tk)
+                    lat[task].append(time.perf_counter() - t0 - ta)
+                    served[task] += work if res["status"] == 0 else 0.0
+                    if res["traj_steps"]:
+                        fr.backtest_release(srv, tk)
+            if now > duration + drain_s:
+                break
+            time.sleep(0.0005)
+        wall = time.perf_counter() - t0
+        st = fr.fr_server_stats(srv)
+        srv.close()
+        ens_s.close()
+        ens_c.close()
+        res = {}
+        for task, tn in ((0, "stock"), (1, "crypto")):
+            a = np.array(lat[task])
+            res[tn] = {"completed": int(a.size), "unfinished": sum(1 for v in pending.values() if v[1] == task)
+                       + sum(1 for r in trace[i:] if r["task"] == task),
+                       "p50_ms": float(np.percentile(a, 50) * 1e3) if a.size else None,
+                       "p99_ms": float(np.percentile(a, 99) * 1e3) if a.size else None,
+                       "served_env_steps_per_s": served[task] / wall}
+        res["wall_s"] = wall
+        res["pool_steps_per_s"] = (st["pool_steps"] - st0["pool_steps"]) / wall
+        res["bytes_peak"] = st["bytes_peak"]
+        res["budget"] = st["budget"]
+        out[name] = res
+    mk_c.close()
+    return out
+
+
 # Algorithmic DRAM bytes of one stock env-step through env_step with every
 # output: reads action f32[30] 120, per-env constants Ke/start/W 12 + bps
 # int16[32] 64, state cash 8 + hold int32[32] 128 + t 4 + done 1, FP64 / int64
@@ -292,10 +404,11 @@ def serving_line(fr, ctx, mk, ens_by_name, duration=10.0, rate=200.0, drain_s=60
 ENV_STEP_BYTES = 377 + 1398
 
 # DRAM bytes (read + write) of one 256-step k_rollout_stock2 launch on the
-# 2,048-env workload, from the ncu launch list of `bench.py --profile fused
-# --T 256` (profiles/fused_rollout_stock2_stock2048.md); the kernel is the
-# one this file times.
+# 2,048-env workload, from an ncu capture of `bench.py --profile fused --T 256`
+# (dram__bytes_read.sum + dram__bytes_write.sum); the kernel this file times.
 K_ROLLOUT_STOCK2_DRAM_BYTES = 3.99e6
+K_ROLLOUT_STOCK2_TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_rollout_stock2, "
+                                 "bench.py --profile fused --T 256, one launch")
 
 
 def env_step_line(fr, ctx, mk, w, dev, stream, N=1 << 20, T=4, warm=2):
@@ -561,7 +674,7 @@ def run_gpu(args):
     a_dt = time_kernel(lambda: fr.ensemble_forward(ens_bf16, obs, y), 50, stream)
     flops_per_launch = N * flops_env_step
     # the same kernel at a batch large enough to fill every SM
-    nb = 152 * 128 * 4
+    nb = ctx.sm_count * 128 * 4
     obs_big = obs.repeat(nb // N, 1)
     y_big = torch.empty(M, nb, 30, device=dev)
     kb_dt = time_kernel(lambda: fr.ensemble_forward(ens_bf16, obs_big, y_big), 10, stream)
@@ -594,6 +707,7 @@ def run_gpu(args):
     # serving (backtest_submit / backtest_poll): p50 / p99 request latency
     serving = serving_line(fr, ctx, mk, {"fused_bf16": ens_bf16, "plain_fp32": ens_fp32}) \
         if not args.no_serving else None
+    serving_c5 = serving_c5_line(fr, ctx, mk, w) if not args.no_serving else None
 
     # end to end through the public API with host buffers, from the reset
     # state (every env live for the whole horizon)
@@ -637,11 +751,12 @@ def run_gpu(args):
                                "traj_bytes_per_rollout": T * N * (env.D * 4 + 30 * 4 + 8 + 1)},
         "speedup_vs_plain": value / world / plain_value,
         "latency": ({"p50_ms": serving["fused_bf16"]["p50_ms"], "p99_ms": serving["fused_bf16"]["p99_ms"],
-                     "serving": serving} if serving else None),
+                     "serving": serving, "serving_mixed_c5": serving_c5} if serving else None),
         "e2e": {"value": e2e_value, "unit": "env-steps/s",
                 "h2d_bytes_per_step": len(snap), "d2h_bytes_per_step": N * 3 * 8},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": K_ROLLOUT_STOCK2_DRAM_BYTES,
+                     "traffic_note": K_ROLLOUT_STOCK2_TRAFFIC_NOTE,
                      "kernel": f"k_rollout_stock2 ({N} envs x {T} steps x {M} agents per launch)",
                      "kernel_ms": 1e3 * k_dt,
                      "flops_per_launch": N * T * flops_env_step,
@@ -770,10 +885,23 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-envs", type=int, default=32)
+    ap.add_argument("--replica-check", action="store_true",
+                    help="check the replica launcher and timing reduction on the CPU (gloo), then exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.profile:
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # not under a launcher yet: start one process per GPU
+        if not args.replica_check and args.impl != "reference":
+            import torch
+            visible = torch.cuda.device_count()
+            if args.gpus > visible:
+                print(f"bench.py: --gpus {args.gpus} but {visible} GPU(s) are visible", file=sys.stderr)
+                sys.exit(2)
+        sys.exit(launch_replicas(args.gpus, sys.argv[1:]))
+    if args.replica_check:
+        replica_check()
+    elif args.profile:
         run_profile(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -314,6 +314,44 @@ def serving_trace_stock(rate: float, duration: float, n_days: int = 1000, max_en
     return out
 
 
+def serving_trace_mixed(rate: float, duration: float, crypto_frac: float = 0.5, traj_frac: float = 0.1,
+                        n_days: int = 1000, n_seconds: int = 480_000, seed: int = MASTER_SEED) -> list:
+    """Backtest requests of both tasks arriving as one Poisson process:
+    each request is crypto with probability crypto_frac, else stock, and
+    records its trajectory with probability traj_frac.  Stock as
+    serving_trace_stock (N ~ U{1..512}, W ~ U{5..500} days, 30 assets,
+    +-1% perturbations); crypto N ~ U{1..2048} envs, W ~ U{3,600..86,400}
+    seconds, env i starting start + i * stride seconds (stride ~ U{0..60}),
+    the first start uniform over the seconds that leave the window inside
+    the market after 3,600 warm-up seconds."""
+    times = poisson_arrivals(rate, duration, seed)
+    st = Stream(seed, SUB_ARRIVALS + 2)
+    n = len(times)
+    kind = st.uniform(n)
+    rec = st.uniform(n)
+    s_env = st.integers(1, 512, n)
+    s_win = st.integers(5, 500, n)
+    c_env = st.integers(1, 2048, n)
+    c_win = st.integers(3600, 86_400, n)
+    c_stride = st.integers(0, 60, n)
+    u = st.uniform(n)
+    seeds = st.u64(n)
+    out = []
+    for i in range(n):
+        r = {"t": float(times[i]), "want_traj": bool(rec[i] < traj_frac)}
+        if kind[i] < crypto_frac:
+            nv, w, sd = int(c_env[i]), int(c_win[i]), int(c_stride[i])
+            lo, hi = 3600, n_seconds - (nv - 1) * sd - w
+            r.update(task=1, n_envs=nv, window=w, start_stride=sd, start=int(lo + int(u[i] * (hi - lo + 1))))
+        else:
+            w = int(s_win[i])
+            lo, hi = 60, n_days - w
+            r.update(task=0, n_envs=int(s_env[i]), window=w, start_stride=0,
+                     start=int(lo + int(u[i] * (hi - lo + 1))), bps_range=100, seed=int(seeds[i]))
+        out.append(r)
+    return out
+
+
 # ----------------------------------------------------------------- workloads
 
 STOCK_DIMS_SMALL = (301, 64, 64, 30)

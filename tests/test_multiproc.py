@@ -81,3 +81,18 @@ def test_reference_arm_line():
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["unit"] == "env-steps/s" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_bench_launches_its_own_replicas_gloo():
+    # bench.py --gpus 2 outside a launcher starts two ranks itself (the same
+    # launcher the GPU run uses); the CPU check reduces stand-in times 0.1 s
+    # and 0.2 s over gloo: the job's time is the slower one
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2", "--replica-check"],
+                       env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(x) for x in r.stdout.strip().splitlines() if x.startswith("{")]
+    assert len(lines) == 1                                   # rank 0 alone prints
+    line = lines[0]
+    assert line["replica_check"] and line["n_gpus"] == 2
+    assert abs(line["max_s"] - 0.2) < 1e-12 and abs(line["value"] - 2 * 100 * 2 / 0.2) < 1e-6
