@@ -629,10 +629,17 @@ def run_gpu(args):
 
     if world > 1:
         torch.distributed.barrier()
+    # the headline: every rollout rebuilds the fused kernel's indicator
+    # table (the first layer's action-independent part), as a producer whose
+    # actors change between rollouts must; the same with the table kept is
+    # reported beside it
+    fr.env_set_table_cache(env, False)
     clocks = ClockSampler(local)
     clocks.start()
     t_bf16 = time_graph_rollouts(fr, env, ens_bf16, T, args.steps, args.warmup, metrics, flush, stream)
     clk = clocks.stop()
+    fr.env_set_table_cache(env, True)
+    t_cached = time_graph_rollouts(fr, env, ens_bf16, T, max(3, args.steps // 2), args.warmup, metrics, flush, stream)
     side = max(2, args.steps // 4)
     t_fp32 = time_rollouts(fr, env, ens_fp32, T, side, 3, metrics, flush, stream)
     t_unf = time_rollouts(fr, env, ens_bf16, T, side, 3, metrics, flush, stream,
@@ -654,6 +661,10 @@ def run_gpu(args):
     # env-step) -- the full 301-wide first layer, although the kernel itself
     # multiplies only the 61 trajectory-dependent inputs
     flops_env_step = M * 2 * sum(w.dims[i] * w.dims[i + 1] for i in range(len(w.dims) - 1))
+    # what the kernel's tensor cores multiply: the first layer over the 61
+    # trajectory-dependent inputs padded to K = 64 (the indicator part comes
+    # from the table), the output layer padded to N = 32
+    flops_exec = M * 2 * (64 * w.dims[1] + w.dims[1] * w.dims[2] + w.dims[2] * 32)
     fr.env_set_kernel_timing(env, True)
     k_times = []
     for _ in range(max(3, args.steps)):
@@ -726,9 +737,9 @@ def run_gpu(args):
             e2e_times.append(time.perf_counter() - t0)
     e2e_value = world * env_steps / statistics.mean(e2e_times)
 
-    # env_reset, fused rollout, metrics replay (the indicator table Z is built
-    # once per env and ensemble, before the timed region)
-    launches_per_rollout = 3
+    # env_reset, the indicator table (rows, then the dense fp32 layer part),
+    # the fused rollout kernel, the metrics replay
+    launches_per_rollout = 5
     line = {
         "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -738,9 +749,11 @@ def run_gpu(args):
                                "actors, mean combine, 1000 GBM days, bps on",
                    "n_envs": N, "steps_per_rollout": T, "agents": M,
                    "path": "fused persistent tcgen05 bf16 kernel, trajectory off; each step one CUDA graph "
-                           "replay of env_reset + rollout",
+                           "replay of env_reset + rollout, the indicator table rebuilt in every rollout",
                    "l2": "flushed between timed rollouts (512 MB write)",
                    "parallelism": f"replicas x{world}"},
+        "fused_bf16_table_kept": {"value": env_steps * len(t_cached) / sum(t_cached), "unit": "env-steps/s",
+                                  "ms_per_rollout": 1e3 * statistics.mean(t_cached)},
         "plain_fp32": {"value": plain_value, "unit": "env-steps/s",
                        "ms_per_rollout": 1e3 * statistics.mean(t_fp32),
                        "path": "unfused fp32 SIMT, one launch per stage per step"},
@@ -760,6 +773,8 @@ def run_gpu(args):
                      "kernel": f"k_rollout_stock2 ({N} envs x {T} steps x {M} agents per launch)",
                      "kernel_ms": 1e3 * k_dt,
                      "flops_per_launch": N * T * flops_env_step,
+                     "tensor_executed_flops_per_launch": N * T * flops_exec,
+                     "tensor_executed_frac_of_algorithmic": flops_exec / flops_env_step,
                      "peak_source": f"bf16_tflops burst, {peak_src}",
                      "active_sms": 2 * M * ((N + 127) // 128),
                      "actor_kernel": {"rows": N, "tflops": flops_per_launch / a_dt / 1e12,

@@ -356,20 +356,26 @@ int ensemble_act(const fr_ensemble *ens, const float *obs, int32_t n,
                  void *act, void *stream);
 
 /* ensemble_act without any allocation, for callers that must not allocate
- * device memory while they run (a loop with a fixed memory footprint, a host
- * application that owns every device buffer, work being recorded into a
- * graph that must not gain allocation nodes).  The paper has no counterpart;
- * this is a library convenience.
- * Same arguments, layouts and results as ensemble_act.  Its scratch is a
- * fixed 16 MiB array inside the library image (held on every GPU that loads
- * the library until the process exits), so no cudaMalloc, cudaFree or other
- * allocating routine is called.  A batch whose scratch would not fit
- * (roughly (2*hidden + out)*M floats per row on the fp32 path, out*M on the
+ * device memory while they run: a real-time trading or serving loop that
+ * reserved all its memory up front and must not stall in the allocator or
+ * fail on fragmentation mid-run, or a host application or plugin framework
+ * that owns every device buffer and forbids a library from allocating behind
+ * its back.  The paper has no counterpart; this is a library convenience.
+ * Same arguments, layouts and results as ensemble_act (on the tensor-core
+ * precisions it always runs the single-agent kernel, which gives the same
+ * results as the large-batch one).  Its scratch is a fixed 16 MiB array
+ * inside the library image (held on every GPU that loads the library until
+ * the process exits), so no cudaMalloc, cudaFree or other allocating routine
+ * is called.  A batch whose scratch would not fit (roughly
+ * (2*hidden + out)*M floats per row on the fp32 path, out*M on the
  * tensor-core paths) fails with FR_EINVAL and a message giving the largest
  * batch for this ensemble.  The first call on a device looks up the array's
- * device address; make that first call before any stream capture.  All calls
- * share the one array: calls whose work overlaps on the GPU (different
- * streams, or different threads) race and must be serialised by the caller. */
+ * device address and keeps it for the life of the process; make that first
+ * call before any stream capture.  After cudaDeviceReset no handle of this
+ * library, this call included, may be used again.  All calls share the one
+ * array and it keeps the last call's contents: calls whose work overlaps on
+ * the GPU (different streams, or different threads) race and must be
+ * serialised by the caller. */
 int ensemble_act_noalloc(const fr_ensemble *ens, const float *obs, int32_t n,
                          void *act, void *stream);
 
@@ -496,6 +502,15 @@ int env_set_rollout_path(fr_env *env, int32_t path);
  * tile's longest W - 1) (1.0 when not packed). */
 int env_set_tile_packing(fr_env *env, int32_t on);
 int env_tile_packing_efficiency(const fr_env *env, float *eff);
+
+/* The fused stock kernel's indicator table: the indicator part of the first
+ * layer, W1[:, f] f + b1 for every (day, asset count) (the f block of the
+ * state, Sec. 3.1, does not depend on the actions).  on = 1 (the default):
+ * built by the first rollout and kept while the ensemble and the envs' asset
+ * counts stay the same; on = 0: rebuilt by every rollout on its stream (the
+ * cost a producer pays when its actors change between rollouts; the launches
+ * are captured with the rollout into a graph).  No counterpart in the paper. */
+int env_set_table_cache(fr_env *env, int32_t on);
 
 /* Autotuner of the batched rollouts (no counterpart in the paper: the
  * project's own choice of launch shape).  Times, for this env batch and

@@ -662,6 +662,14 @@ int env_set_tile_packing(fr_env *env, int32_t on)
     return FR_OK;
 }
 
+int env_set_table_cache(fr_env *env, int32_t on)
+{
+    FR_NVTX("env_set_table_cache");
+    FR_CHECK(env, FR_EINVAL, "env_set_table_cache: NULL env");
+    env->z_cache_off = on ? 0 : 1;
+    return FR_OK;
+}
+
 int env_tile_packing_efficiency(const fr_env *env, float *eff)
 {
     FR_NVTX("env_tile_packing_efficiency");

@@ -141,6 +141,7 @@ struct fr_env {
     void *zbuf;
     uint64_t zbuf_bytes;
     uint64_t z_serial;          // serial of the ensemble Z was built for; 0 = stale
+    int z_cache_off;            // rebuild Z on every rollout
     // tile packing of the fused stock kernel (envs sorted by window into
     // 128-env tiles; each tile runs until its longest window is over)
     int pack_state;             // 0 unknown, 1 not packed (uniform windows), 2 packed

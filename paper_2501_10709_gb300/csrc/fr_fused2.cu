@@ -1025,7 +1025,7 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     int64_t *vlog = (int64_t *)env->scratch;
     float *X = (float *)env->zbuf;
     float *Z = (float *)((char *)env->zbuf + x_b);
-    if (env->z_serial != e->serial) {
+    if (env->z_serial != e->serial || env->z_cache_off) {
         // Z[j][ctx][n] = W1_j[n, indicators] . x[ctx] + b1_j[n]
         const int64_t nx = (int64_t)n_ctx * NIND;
         k_ind_rows<<<ceil_div(nx, 256), 256, 0, s>>>(v.ind, v.n_days, env->slot_ke, env->n_slots, X);

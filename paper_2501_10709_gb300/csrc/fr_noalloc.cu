@@ -2,10 +2,10 @@
 //
 // ensemble_act takes its scratch (the hidden activations of the plain fp32
 // path and the per-agent outputs before they are combined) from the
-// stream-ordered allocator.  Some callers cannot allow that: code running
-// inside a region whose memory is fixed up front (a real-time loop with a
-// no-allocation guarantee, a plugin host that owns every device buffer, a
-// capture that must not add allocation nodes).  ensemble_act_noalloc runs the
+// stream-ordered allocator.  Some callers cannot allow that: a real-time
+// loop that reserved its memory up front and must not stall in (or fail in)
+// the allocator mid-run, or a plugin host that owns every device buffer and
+// forbids the library to allocate behind its back.  ensemble_act_noalloc runs the
 // same kernels on a scratch area that is part of this library's image: a
 // file-scope device array of fixed size that every GPU loading the library
 // holds until the process exits.  It calls no cudaMalloc, cudaFree or other

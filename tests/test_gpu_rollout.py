@@ -291,3 +291,31 @@ def test_rollout_graph_capture(ctx, dev, case):
         g.replay()
         torch.cuda.synchronize()
         assert torch.equal(met, ref)
+
+
+def test_indicator_table_rebuilt_each_rollout_equals_kept(ctx, dev):
+    # the fused stock kernel's indicator table rebuilt by every rollout (as
+    # the benchmark's headline times it, inside a captured graph) gives the
+    # same rollout bit for bit as the kept table
+    w = synth.workload_stock_2048(N=256, T=24)
+    e = w.envs
+    mk = fr.fr_market_create(ctx, w.market)
+    ens = fr.ensemble_create(ctx, w.dims, w.params, precision=fr.PREC_BF16)
+    env = fr.env_create(ctx, mk, start=e.start, window=e.W, n_assets=e.Ke, bps=e.bps)
+    out = []
+    for keep in (True, False, False):
+        fr.env_set_table_cache(env, keep)
+        fr.env_reset(env)
+        met = torch.empty(e.N, 3, dtype=torch.float64, device=dev)
+        fr.rollout(env, ens, w.T, metrics=met)
+        out.append(met)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    met_g = torch.empty(e.N, 3, dtype=torch.float64, device=dev)
+    with torch.cuda.graph(g, stream=side):
+        fr.env_reset(env)
+        fr.rollout(env, ens, w.T, metrics=met_g)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out[0], out[1]) and torch.equal(out[1], out[2]) and torch.equal(out[0], met_g)

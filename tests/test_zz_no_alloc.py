@@ -41,6 +41,10 @@ def test_noalloc_matches_ensemble_act_twice(precision):
         g, r = got.cpu().numpy().astype(np.float64), ref.cpu().numpy().astype(np.float64)
         err = np.linalg.norm(g - r, axis=-1) / np.maximum(np.linalg.norm(r, axis=-1), 1e-3)
         assert np.isfinite(g).all() and err.max() <= REL_TOL[precision], err.max()
+        if precision == fr.PREC_BF16:
+            # below one 128-row tile per SM ensemble_act runs the same
+            # single-agent tensor-core kernel: identical results
+            assert torch.equal(got, ref)
     # and against the fp64 oracle on a sample of rows
     o = obs.cpu().numpy()[:64]
     want = np.stack([oracle.ensemble_mean(np.stack([oracle.net_forward(dims, params[j], o[i:i + 1], 1)[0]
