@@ -396,6 +396,34 @@ def test_uniform24_is_open_interval_with_exact_ends():
     assert oracle.uniform24(0x80000000) == 0.5 + 2.0 ** -25
 
 
+def test_explore_normal_known_value_from_the_published_philox_words():
+    # Philox4x32-10 of counter (0, 0, 0, 0) under key (0, 0) is the published
+    # known-answer vector (0x6627E8D5, 0xE169C58D, ...) (Salmon et al. 2011);
+    # the exploration normal of seed 0, env 0, step 0, asset 0 is Box-Muller
+    # of its first two words as uniforms (x >> 8) 2^-24 + 2^-25: computed here
+    # by hand from those words, so a swap of the two uniforms, sin for cos or
+    # other words would fail
+    u0 = (0x6627E8D5 >> 8) / 2.0 ** 24 + 2.0 ** -25
+    u1 = (0xE169C58D >> 8) / 2.0 ** 24 + 2.0 ** -25
+    want = math.sqrt(-2.0 * math.log(u0)) * math.cos(2.0 * math.pi * u1)
+    assert oracle.explore_normal(0, 0, 0, 0) == pytest.approx(want, rel=1e-14, abs=1e-14)
+    for other in (math.sqrt(-2.0 * math.log(u1)) * math.cos(2.0 * math.pi * u0),
+                  math.sqrt(-2.0 * math.log(u0)) * math.sin(2.0 * math.pi * u1)):
+        assert abs(other - want) > 1e-3
+
+
+def test_explore_greedy_rule_from_philox_words():
+    # the greedy draw of (env e, step g) uses words 2 and 3 of Philox(e, g, 0, 1):
+    # replace when (x2 >> 8) < floor(eps 2^24), by action floor(3 (x3 >> 8) / 2^24)
+    for e, g in [(0, 0), (5, 17), (123456, 7)]:
+        x = oracle.philox4x32_10([e, g, 0, 1], [99, 0])
+        r2, r3 = x[2] >> 8, x[3] >> 8
+        for eps in (0.0, r2 / 2.0 ** 24, (r2 + 1) / 2.0 ** 24, 1.0):
+            thr = int(eps * 2 ** 24)
+            want = (r3 * 3) >> 24 if r2 < thr else 7
+            assert oracle.explore_greedy(99, e, g, eps, 7) == want
+
+
 def test_explore_normal_moments():
     z = np.array([oracle.explore_normal(1234, e, g, k) for e in range(20) for g in range(50) for k in range(20)])
     n = z.size
