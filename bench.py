@@ -516,9 +516,10 @@ def uneven_line(fr, ctx, dev, flush, stream, reps=3):
     res = {"workload": f"uneven stock {e.N} envs, assets 10-30, windows 5-250 days, T = {w.T}, "
                        "3 x 301-256-256-30 BF16", "unit": "env-steps/s (sum of W - 1 per rollout)",
            "env_steps_per_rollout": work}
+    # each timed rollout one CUDA graph replay of env_reset + rollout
     for name, on in (("packed", True), ("unpacked", False)):
         fr.env_set_tile_packing(env, on)
-        ts = time_rollouts(fr, env, ens, w.T, reps, 3, met, flush, stream)
+        ts = time_graph_rollouts(fr, env, ens, w.T, reps, 3, met, flush, stream)
         res[name] = {"value": work * len(ts) / sum(ts), "ms_per_rollout": 1e3 * statistics.mean(ts)}
     fr.env_set_tile_packing(env, True)
     res["tile_efficiency_packed"] = fr.env_tile_packing_efficiency(env)
@@ -526,7 +527,7 @@ def uneven_line(fr, ctx, dev, flush, stream, reps=3):
     # of the rollout's own length (packing pays off only over the long
     # windows) on the env's own state; the fastest then timed as above
     tune = fr.env_autotune(env, ens, w.T, force=True)
-    ts = time_rollouts(fr, env, ens, w.T, reps, 3, met, flush, stream)
+    ts = time_graph_rollouts(fr, env, ens, w.T, reps, 3, met, flush, stream, keep_path=True)
     res["autotuned"] = {"value": work * len(ts) / sum(ts), "ms_per_rollout": 1e3 * statistics.mean(ts),
                         "chosen": tune["chosen"],
                         "candidates": [{k: (round(v, 4) if k == "ms" else v) for k, v in c.items()}
@@ -543,7 +544,7 @@ def uneven_line(fr, ctx, dev, flush, stream, reps=3):
     rows = torch.linspace(0, 8 * e.N - 1, 4096, device=dev).long()
     fr.ensemble_calibrate_sync(ens8, tr["obs"].reshape(-1, env.D)[rows].contiguous())
     del tr
-    ts = time_rollouts(fr, env, ens8, w.T, reps, 3, met, flush, stream)
+    ts = time_graph_rollouts(fr, env, ens8, w.T, reps, 3, met, flush, stream)
     res["fp8_unfused"] = {"value": work * len(ts) / sum(ts), "ms_per_rollout": 1e3 * statistics.mean(ts),
                           "calibration": "4,096 observations from the first 8 BF16 steps"}
     ens8.close()
@@ -552,11 +553,13 @@ def uneven_line(fr, ctx, dev, flush, stream, reps=3):
     return res
 
 
-def time_graph_rollouts(fr, env, ens, T, steps, warmup, metrics, flush, stream):
+def time_graph_rollouts(fr, env, ens, T, steps, warmup, metrics, flush, stream, keep_path=False):
     """The same timed region as time_rollouts, each step one replay of a CUDA
-    graph holding env_reset + rollout (captured after warm-up calls)."""
+    graph holding env_reset + rollout (captured after warm-up calls);
+    keep_path: leave the env's path choice (an autotuned one) as it is."""
     import torch
-    fr.env_set_rollout_path(env, fr.PATH_AUTO)
+    if not keep_path:
+        fr.env_set_rollout_path(env, fr.PATH_AUTO)
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):

@@ -287,6 +287,7 @@ int fr_market_create(fr_ctx *ctx, const fr_market_desc *d, fr_market **out)
                       "0 <= n_ind <= 16 and host tables");
             return FR_EINVAL;
         }
+        m->close_max = 1;
         for (int64_t i = 0; i < (int64_t)d->n_days * d->n_assets; ++i) {
             if (d->close[i] < 1) {
                 delete m;
@@ -294,6 +295,7 @@ int fr_market_create(fr_ctx *ctx, const fr_market_desc *d, fr_market **out)
                           (long long)d->close[i]);
                 return FR_EINVAL;
             }
+            m->close_max = std::max(m->close_max, d->close[i]);
         }
         m->n_days = d->n_days;
         m->K = d->n_assets;
@@ -463,6 +465,21 @@ int env_create(fr_ctx *ctx, const fr_env_desc *d, const fr_market *m, fr_env **o
     v.pmax = d->pmax;
     v.auto_reset = d->auto_reset ? 1 : 0;
     v.buy_order = d->buy_order;
+    // The step kernel's 32-bit accounting is exact when, for every price the
+    // env can see (perturbed by at most +100 bps): the perturbation's
+    // numerator close * (1e4 + bps) + 5e3 fits 32 bits; an order's notional
+    // (at most hmax shares) plus its fee fits 31 bits and notional * fee_bps
+    // + 9,999 fits 32 bits; and K such amounts (a step's sell proceeds or buy
+    // costs) sum within 32 bits.
+    if (stock) {
+        const uint64_t cmax = (uint64_t)m->close_max;
+        const uint64_t pmax = (cmax * (uint64_t)(BPS_ONE + 100) + BPS_ONE / 2) / BPS_ONE;
+        const uint64_t gmax = pmax * (uint64_t)d->hmax;
+        const uint64_t fmax = (gmax * (uint64_t)d->fee_bps + BPS_ONE - 1) / BPS_ONE;
+        v.narrow = cmax * (uint64_t)(BPS_ONE + 100) + BPS_ONE / 2 < (1ull << 32) &&
+                   gmax * (uint64_t)d->fee_bps + BPS_ONE < (1ull << 32) && gmax + fmax < (1ull << 31) &&
+                   (uint64_t)m->K * (gmax + fmax) < (1ull << 32);
+    }
     v.init_cash = d->init_cash;
     v.ann = stock ? 252.0 : 1.0;
     v.n_days = m->n_days;

@@ -69,6 +69,7 @@ struct EnvView {
     int task, N, K, I, D;
     int hmax, fee_bps, pmax, auto_reset;
     int buy_order;              // FR_BUY_ASCENDING / FR_BUY_LARGEST_FIRST (stock)
+    int narrow;                 // stock: prices, orders and step sums fit 32 bits (env_create proves it)
     int64_t init_cash;
     double ann;                 // Sharpe annualisation factor A
     // market
@@ -112,6 +113,7 @@ struct fr_market {
     int task;
     int n_days, K, I;
     int64_t S;
+    int64_t close_max;          // largest close (stock), for the range proofs of the step kernel
     int64_t *close;
     float *ind;
     int64_t *mid;

@@ -52,7 +52,9 @@ __global__ void k_env_reset(EnvView v)
 // with 32-env blocks (2 per SM), 945 us with 16-env and 979 us with 4-env
 // blocks -- a block's slot is held until its slowest warp and its
 // bookkeeping finish, and small blocks turn over sooner.
-template <int KIND, bool BYSIZE>
+// NARROW: the prices, orders and a step's sums of sells and buys run in
+// 32-bit arithmetic (env_create proved the ranges; same results).
+template <int KIND, bool BYSIZE, bool NARROW>
 __global__ void __launch_bounds__(kStepEnvs * 32, kStepBlocks) k_stock_step(EnvView v, const void *act, int64_t *rew,
                                                                 float *rew_f32, uint8_t *done_out,
                                                                 float *obs, int ld)
@@ -90,25 +92,32 @@ __global__ void __launch_bounds__(kStepEnvs * 32, kStepBlocks) k_stock_step(EnvV
         int64_t cash = cash0, r = 0;
         int t_obs = t0;
         bool dn = true;
-        int64_t p_obs = live ? perturb(c0, bps) : 0;
+        int64_t p_obs = live ? (NARROW ? (int64_t)perturb32((uint32_t)c0, bps) : perturb(c0, bps)) : 0;
         if (!was_done) {
             const int fee = v.fee_bps;
             const int64_t p = p_obs;
-            const int64_t v0 = cash + warp_sum_redux(p * h);
+            // holdings are int32 >= 0 and prices below 2^32: one 32 x 32 -> 64-bit product
+            const int64_t v0 = cash + warp_sum_redux(NARROW ? (int64_t)((uint64_t)(uint32_t)p * (uint32_t)h) : p * h);
             int64_t net = 0;
+            uint32_t net32 = 0u;
             if (q < 0) {
                 int64_t n = -(int64_t)q;
                 if (n > h) n = h;
-                const int64_t g = n * p;
                 h -= n;
-                net = g - fee_of(g, fee);
+                if (NARROW) {
+                    const uint32_t g = (uint32_t)n * (uint32_t)p;
+                    net32 = g - fee_of32(g, fee);
+                } else {
+                    const int64_t g = n * p;
+                    net = g - fee_of(g, fee);
+                }
             }
-            cash += warp_sum_redux(net);
+            cash += NARROW ? (int64_t)__reduce_add_sync(FULL_MASK, net32) : warp_sum_redux(net);
             const int64_t want = q > 0 ? (int64_t)q : 0;
             int64_t full = 0, nb = 0;
-            if (want > 0) full = cost_of(want, p, fee);
+            if (want > 0) full = NARROW ? (int64_t)cost_of32((uint32_t)want, (uint32_t)p, fee) : cost_of(want, p, fee);
             unsigned pending = __ballot_sync(FULL_MASK, want > 0);
-            const int64_t all = warp_sum_redux(full);
+            const int64_t all = NARROW ? (int64_t)__reduce_add_sync(FULL_MASK, (uint32_t)full) : warp_sum_redux(full);
             if (all <= cash) {
                 nb = want;
                 cash -= all;
@@ -167,8 +176,8 @@ __global__ void __launch_bounds__(kStepEnvs * 32, kStepBlocks) k_stock_step(EnvV
             nb = BYSIZE ? __shfl_sync(FULL_MASK, bn, rank) : bn;
             h += nb;
             const int t1 = t0 + 1;
-            const int64_t p1 = live ? perturb(c1, bps) : 0;
-            const int64_t v1 = cash + warp_sum_redux(p1 * h);
+            const int64_t p1 = live ? (NARROW ? (int64_t)perturb32((uint32_t)c1, bps) : perturb(c1, bps)) : 0;
+            const int64_t v1 = cash + warp_sum_redux(NARROW ? (int64_t)((uint64_t)(uint32_t)p1 * (uint32_t)h) : p1 * h);
             dn = t1 == W - 1;
             r = v1 - v0;
             fin.cash = cash;
@@ -341,17 +350,20 @@ cudaError_t launch_env_step(const EnvView &v, int kind, const void *act, int64_t
     if (v.task == FR_TASK_STOCK) {
         const unsigned grid = ceil_div(v.N, kStepEnvs);
         const bool by_size = v.buy_order == FR_BUY_LARGEST_FIRST;
+        const unsigned bs = kStepEnvs * 32;
+#define FR_STEP(K_, B_, N_) k_stock_step<K_, B_, N_><<<grid, bs, 0, s>>>(v, act, rew, rew_f32, done, obs, ld)
         if (kind == FR_ACT_I32_SHARES) {
             if (by_size)
-                k_stock_step<FR_ACT_I32_SHARES, true><<<grid, kStepEnvs * 32, 0, s>>>(v, act, rew, rew_f32, done, obs, ld);
+                v.narrow ? FR_STEP(FR_ACT_I32_SHARES, true, true) : FR_STEP(FR_ACT_I32_SHARES, true, false);
             else
-                k_stock_step<FR_ACT_I32_SHARES, false><<<grid, kStepEnvs * 32, 0, s>>>(v, act, rew, rew_f32, done, obs, ld);
+                v.narrow ? FR_STEP(FR_ACT_I32_SHARES, false, true) : FR_STEP(FR_ACT_I32_SHARES, false, false);
         } else {
             if (by_size)
-                k_stock_step<FR_ACT_F32_UNIT, true><<<grid, kStepEnvs * 32, 0, s>>>(v, act, rew, rew_f32, done, obs, ld);
+                v.narrow ? FR_STEP(FR_ACT_F32_UNIT, true, true) : FR_STEP(FR_ACT_F32_UNIT, true, false);
             else
-                k_stock_step<FR_ACT_F32_UNIT, false><<<grid, kStepEnvs * 32, 0, s>>>(v, act, rew, rew_f32, done, obs, ld);
+                v.narrow ? FR_STEP(FR_ACT_F32_UNIT, false, true) : FR_STEP(FR_ACT_F32_UNIT, false, false);
         }
+#undef FR_STEP
     } else {
         k_crypto_step<<<ceil_div(v.N, kBlock), kBlock, 0, s>>>(v, (const uint8_t *)act, rew, rew_f32,
                                                                done, obs, ld);

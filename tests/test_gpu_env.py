@@ -222,3 +222,24 @@ def test_hbm_budget_is_enforced():
         fr.env_create(c, mk, start=w.envs.start, window=w.envs.W, bps=w.envs.bps)
     assert ei.value.code == fr._lib.FR_ENOMEM
     assert c.bytes_in_use <= 1 << 20
+
+
+@pytest.mark.parametrize("scale, hmax", [(1, 100), (3000, 100), (1, 60000)])
+def test_stock_step_32_and_64_bit_accounting(ctx, dev, scale, hmax):
+    # The step kernel runs its prices, orders and sums in 32-bit arithmetic
+    # when env_create proves they fit (the bench's market); prices scaled
+    # x3,000 (up to millions of dollars a share) or 60,000-share orders fail
+    # that proof and take the 64-bit forms.  Both are bit-exact against the
+    # oracle, partial fills included (cash for few of the orders).
+    w = synth.workload_stock_small()
+    mkt = SimpleNamespace(close=np.ascontiguousarray(w.market.close * scale), ind=w.market.ind,
+                          high=w.market.high * scale, low=w.market.low * scale)
+    e = w.envs
+    mk = fr.fr_market_create(ctx, mkt)
+    env = fr.env_create(ctx, mk, start=e.start, window=e.W, n_assets=e.Ke, bps=e.bps, init_cash=e.init_cash,
+                        hmax=hmax, fee_bps=10)
+    acts = synth.prescribed_unit(w.T, e.N, 30)
+    ref = oracle.stock_run(mkt, e.Ke, e.start, e.W, e.bps, init_cash=e.init_cash, hmax=hmax,
+                           fee_bps=10, T=w.T, act_f32=acts)
+    res = _run_stock_steps(env, acts, fr.ACT_F32_UNIT, dev)
+    _check_stock(res, ref, w.T)
