@@ -53,8 +53,11 @@ __global__ void k_env_reset(EnvView v)
 // blocks -- a block's slot is held until its slowest warp and its
 // bookkeeping finish, and small blocks turn over sooner.
 // NARROW: the prices, orders and a step's sums of sells and buys run in
-// 32-bit arithmetic (env_create proved the ranges; same results).
-template <int KIND, bool BYSIZE, bool NARROW>
+// 32-bit arithmetic (env_create proved the ranges; same results).  FIXED:
+// the market has K = 30 assets and I = 8 indicators (the paper's shape), so
+// every row offset of the state, action, price and observation rows is a
+// compile-time constant.
+template <int KIND, bool BYSIZE, bool NARROW, bool FIXED>
 __global__ void __launch_bounds__(kStepEnvs * 32, kStepBlocks) k_stock_step(EnvView v, const void *act, int64_t *rew,
                                                                 float *rew_f32, uint8_t *done_out,
                                                                 float *obs, int ld)
@@ -66,7 +69,8 @@ __global__ void __launch_bounds__(kStepEnvs * 32, kStepBlocks) k_stock_step(EnvV
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int e = blockIdx.x * kStepEnvs + w;
-    const int K = v.K;
+    const int K = FIXED ? 30 : v.K;
+    const int NI = FIXED ? 8 : v.I;
     StepFin fin;
     fin.valid = 0;
     if (e < v.N) {                                       // uniform per warp
@@ -209,18 +213,21 @@ __global__ void __launch_bounds__(kStepEnvs * 32, kStepBlocks) k_stock_step(EnvV
             float *o = obs + (int64_t)e * ld;
             if (lane == 0) o[0] = obs_scale(cash, 1e-8f);
             if (lane < K) {
-                o[1 + lane] = live ? obs_scale(p_obs, 1e-4f) : 0.0f;
-                o[1 + K + lane] = live ? obs_scale(h, 1e-2f) : 0.0f;
-                const float *f = v.ind + (int64_t)(start + t_obs) * v.I * K;
+                // NARROW prices are below 2^31 and holdings are int32: the
+                // 32-bit conversion gives the same correctly rounded float
+                o[1 + lane] = live ? (NARROW ? __fmul_rn(__int2float_rn((int)p_obs), 1e-4f) : obs_scale(p_obs, 1e-4f))
+                                   : 0.0f;
+                o[1 + K + lane] = live ? __fmul_rn(__int2float_rn((int)h), 1e-2f) : 0.0f;
+                const float *f = v.ind + (int64_t)(start + t_obs) * NI * K;
                 float *oi = o + 1 + 2 * K + lane;
-                if (v.I == 8) {                          // the usual count: every load in flight
+                if (NI == 8) {                           // the usual count: every load in flight
                     float fv[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) fv[i] = live ? __ldg(f + i * K + lane) : 0.0f;
 #pragma unroll
                     for (int i = 0; i < 8; ++i) oi[i * K] = fv[i];
                 } else {
-                    for (int i = 0; i < v.I; ++i) oi[i * K] = live ? __ldg(f + i * K + lane) : 0.0f;
+                    for (int i = 0; i < NI; ++i) oi[i * K] = live ? __ldg(f + i * K + lane) : 0.0f;
                 }
             }
         }
@@ -351,18 +358,23 @@ cudaError_t launch_env_step(const EnvView &v, int kind, const void *act, int64_t
         const unsigned grid = ceil_div(v.N, kStepEnvs);
         const bool by_size = v.buy_order == FR_BUY_LARGEST_FIRST;
         const unsigned bs = kStepEnvs * 32;
-#define FR_STEP(K_, B_, N_) k_stock_step<K_, B_, N_><<<grid, bs, 0, s>>>(v, act, rew, rew_f32, done, obs, ld)
+        const bool fixed = v.K == 30 && v.I == 8;
+#define FR_STEP(K_, B_, N_, F_) k_stock_step<K_, B_, N_, F_><<<grid, bs, 0, s>>>(v, act, rew, rew_f32, done, obs, ld)
+#define FR_STEP2(K_, B_)                                                                 \
+    (fixed ? (v.narrow ? FR_STEP(K_, B_, true, true) : FR_STEP(K_, B_, false, true))     \
+           : (v.narrow ? FR_STEP(K_, B_, true, false) : FR_STEP(K_, B_, false, false)))
         if (kind == FR_ACT_I32_SHARES) {
             if (by_size)
-                v.narrow ? FR_STEP(FR_ACT_I32_SHARES, true, true) : FR_STEP(FR_ACT_I32_SHARES, true, false);
+                FR_STEP2(FR_ACT_I32_SHARES, true);
             else
-                v.narrow ? FR_STEP(FR_ACT_I32_SHARES, false, true) : FR_STEP(FR_ACT_I32_SHARES, false, false);
+                FR_STEP2(FR_ACT_I32_SHARES, false);
         } else {
             if (by_size)
-                v.narrow ? FR_STEP(FR_ACT_F32_UNIT, true, true) : FR_STEP(FR_ACT_F32_UNIT, true, false);
+                FR_STEP2(FR_ACT_F32_UNIT, true);
             else
-                v.narrow ? FR_STEP(FR_ACT_F32_UNIT, false, true) : FR_STEP(FR_ACT_F32_UNIT, false, false);
+                FR_STEP2(FR_ACT_F32_UNIT, false);
         }
+#undef FR_STEP2
 #undef FR_STEP
     } else {
         k_crypto_step<<<ceil_div(v.N, kBlock), kBlock, 0, s>>>(v, (const uint8_t *)act, rew, rew_f32,
