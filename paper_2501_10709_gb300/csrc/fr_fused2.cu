@@ -308,10 +308,13 @@ struct ObsWords {
     float pv, hv, cv;
 };
 
+template <bool NARROW>
 __device__ __forceinline__ ObsWords own_words(const F2Args &a, const OwnEnv &s, bool valid, int lane)
 {
     ObsWords o;
-    o.pv = (valid && lane < s.Ke) ? obs_scale(s.p, 1e-4f) : 0.0f;
+    // NARROW prices are below 2^31: the 32-bit conversion rounds the same
+    o.pv = (valid && lane < s.Ke) ? (NARROW ? __fmul_rn(__int2float_rn((int)s.p), 1e-4f) : obs_scale(s.p, 1e-4f))
+                                  : 0.0f;
     o.hv = (valid && lane < s.Ke) ? __fmul_rn(__int2float_rn(s.h), 1e-2f) : 0.0f;
     o.cv = valid ? obs_scale(s.cash, 1e-8f) : 0.0f;
     const __nv_bfloat162 ph2 = __floats2bfloat162_rn(o.pv, o.hv);      // .x price, .y holding
@@ -367,14 +370,14 @@ __device__ __forceinline__ void own_store(const ObsWords &o, int r, uint32_t a_o
 // Publish the next observations of this warp's owned envs: all rows' words
 // first (their shuffles overlap), then all stores, then the optional fp32
 // trajectory rows.  trow[i] < 0: no trajectory row.
-template <int NOWN>
+template <int NOWN, bool NARROW>
 __device__ __forceinline__ void own_publish_all(const F2Args &a, const OwnEnv *own, const int *orow, const int *eidx,
                                                 uint32_t a_obs, uint32_t ctx_addr, int M2, int lane, int64_t tbase,
                                                 int rank, uint64_t *obs_bar)
 {
     ObsWords o[NOWN];
 #pragma unroll
-    for (int i = 0; i < NOWN; ++i) o[i] = own_words(a, own[i], eidx[i] >= 0, lane);
+    for (int i = 0; i < NOWN; ++i) o[i] = own_words<NARROW>(a, own[i], eidx[i] >= 0, lane);
     const uint32_t ob = ptx::smem_u32(obs_bar);
 #pragma unroll
     for (int i = 0; i < NOWN; ++i)
@@ -393,7 +396,10 @@ __device__ __forceinline__ void own_publish_all(const F2Args &a, const OwnEnv *o
     }
 }
 
-template <int NOWN>
+// NARROW: the env's prices, orders and a step's sells and buys fit 32 bits
+// (EnvView::narrow, proved by env_create): the accounting runs in 32-bit
+// arithmetic, with the same results.
+template <int NOWN, bool NARROW>
 __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, const F2Smem L_in, uint64_t *bars,
                             volatile int *abort, int warp, int lane, int rank, int tile)
 {
@@ -459,13 +465,14 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
             if (lane < s.Ke) {
                 s.h = v.hold[(int64_t)e * KP + lane];
                 s.bps = v.bps[(int64_t)e * KP + lane];
-                s.p = perturb(__ldg(v.close + (int64_t)(s.start + s.t) * SK2 + lane), s.bps);
+                const int64_t c = __ldg(v.close + (int64_t)(s.start + s.t) * SK2 + lane);
+                s.p = NARROW ? (int64_t)perturb32((uint32_t)c, s.bps) : perturb(c, s.bps);
             }
         }
         s.v0 = s.cash + warp_sum(s.p * (int64_t)s.h);
     }
     // observation of step 0
-    own_publish_all<NOWN>(a, own, orow, eidx, a_obs, ctx_addr, M2, lane, 0, rank, obs_ready);
+    own_publish_all<NOWN, NARROW>(a, own, orow, eidx, a_obs, ctx_addr, M2, lane, 0, rank, obs_ready);
 
     const float *zbase = a.Z + (size_t)j * a.n_ctx_per_agent * p.H1;
     // The step loop has no early exit: its trip count is uniform, so the warp
@@ -479,6 +486,16 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
     if (issuer) f2_wait(&bars[B_W], 0u, abort, a.err, 1u, false);
     for (int s = 0; s < T; ++s) {
         const uint32_t ph = (uint32_t)s & 1u;
+        // The next day's closes do not depend on the actions: their loads
+        // start here, a whole step of latency before the owners need them.
+        int64_t c1[NOWN];
+#pragma unroll
+        for (int i = 0; i < NOWN; ++i) {
+            const OwnEnv &st = own[i];
+            c1[i] = (eidx[i] >= 0 && !st.done && lane < st.Ke)
+                        ? __ldg(v.close + (int64_t)(st.start + st.t + 1) * SK2 + lane)
+                        : 0;
+        }
         // ------------------------------------------- E1: + Z + b1 -> ReLU
         // the observation barrier also publishes each env's Z row: read it
         // and start the row's loads while layer 1 runs on the tensor cores
@@ -608,10 +625,8 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         }
         tc_fence_before();
         // --------------------------------------------- owners: trade, publish
-        // The next day's prices do not depend on the actions: load them
-        // before the actions arrive.  The owned envs are then processed in
-        // lockstep, so that their reductions overlap instead of forming one
-        // long dependent chain per env.
+        // The owned envs are processed in lockstep, so that their reductions
+        // overlap instead of forming one long dependent chain per env.
         int64_t p1[NOWN];
         bool run[NOWN];                                 // uniform: env exists and is not done
 #pragma unroll
@@ -619,7 +634,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
             const OwnEnv &st = own[i];
             run[i] = eidx[i] >= 0 && !st.done;
             const bool ok = run[i] && lane < st.Ke;
-            p1[i] = ok ? perturb(__ldg(v.close + (int64_t)(st.start + st.t + 1) * SK2 + lane), st.bps) : 0;
+            p1[i] = ok ? (NARROW ? (int64_t)perturb32((uint32_t)c1[i], st.bps) : perturb(c1[i], st.bps)) : 0;
         }
         f2_wait(xrdy, ph, abort, a.err, 64u, true);
         // arm the next phase: one arrival, the bytes the other CTAs send
@@ -663,12 +678,24 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
             // sells capped at the holding; buys as ordered (the common case:
             // every order fits); the value after both at the next prices
             nsell[i] = qa < 0 ? min((int64_t)(-qa), hcur) : 0;
-            const int64_t gs = nsell[i] * st.p;
             want[i] = qa > 0 ? (int64_t)qa : 0;
-            full[i] = cost_of(want[i], st.p, fee);
-            ssum[i] = warp_sum_redux(gs - fee_of(gs, fee));
-            bsum[i] = warp_sum_redux(full[i]);
-            vsum[i] = warp_sum_redux(p1[i] * (hcur - nsell[i] + want[i]));
+            if (NARROW) {
+                // orders of at most hmax shares: notionals, fees and a step's
+                // sums below 2^32; holdings int32 (one 32 x 32 -> 64 product)
+                const uint32_t p32 = (uint32_t)st.p, gs = (uint32_t)nsell[i] * p32;
+                const uint32_t f32 = cost_of32((uint32_t)want[i], p32, fee);
+                full[i] = (int64_t)f32;
+                ssum[i] = (int64_t)__reduce_add_sync(FULL_MASK, gs - fee_of32(gs, fee));
+                bsum[i] = (int64_t)__reduce_add_sync(FULL_MASK, f32);
+                vsum[i] = warp_sum_redux(
+                    (int64_t)((uint64_t)(uint32_t)p1[i] * (uint32_t)(hcur - nsell[i] + want[i])));
+            } else {
+                const int64_t gs = nsell[i] * st.p;
+                full[i] = cost_of(want[i], st.p, fee);
+                ssum[i] = warp_sum_redux(gs - fee_of(gs, fee));
+                bsum[i] = warp_sum_redux(full[i]);
+                vsum[i] = warp_sum_redux(p1[i] * (hcur - nsell[i] + want[i]));
+            }
         }
 #pragma unroll
         for (int i = 0; i < NOWN; ++i) {
@@ -702,7 +729,8 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                     st.t = 0;
                     st.done = 0;
                     st.h = 0;
-                    st.p = lane < st.Ke ? perturb(__ldg(v.close + (int64_t)st.start * SK2 + lane), st.bps) : 0;
+                    const int64_t c0 = lane < st.Ke ? __ldg(v.close + (int64_t)st.start * SK2 + lane) : 1;
+                    st.p = lane < st.Ke ? (NARROW ? (int64_t)perturb32((uint32_t)c0, st.bps) : perturb(c0, st.bps)) : 0;
                 }
             }
             if (valid && lane == 0) {
@@ -713,8 +741,8 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
             }
         }
         if (s + 1 < T)
-            own_publish_all<NOWN>(a, own, orow, eidx, a_obs, ctx_addr, M2, lane, (int64_t)(s + 1) * v.N, rank,
-                                  obs_ready);
+            own_publish_all<NOWN, NARROW>(a, own, orow, eidx, a_obs, ctx_addr, M2, lane, (int64_t)(s + 1) * v.N,
+                                          rank, obs_ready);
     }
     // the other CTAs' asynchronous stores of the last step have landed
     // before this CTA can exit, also when a wait gave up and the loop ran on
@@ -748,6 +776,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
     }
 }
 
+template <bool NARROW>
 __global__ void __launch_bounds__(F2_THREADS, 1) k_rollout_stock2(const __grid_constant__ F2Args a)
 {
     using namespace ptx;
@@ -803,9 +832,9 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_rollout_stock2(const __grid_c
     {
         // owned envs per env warp: ceil(128 / (2M * 8)) = 4, 3, 2 for M = 2..4
         switch (p.M) {
-        case 2: f2_env_loop<4>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
-        case 3: f2_env_loop<3>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
-        default: f2_env_loop<2>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
+        case 2: f2_env_loop<4, NARROW>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
+        case 3: f2_env_loop<3, NARROW>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
+        default: f2_env_loop<2, NARROW>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
         }
     }
     __syncwarp();
@@ -1115,9 +1144,13 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    FR_CUDA(set_max_smem_once((const void *)k_rollout_stock2, env->ctx->device));
+    FR_CUDA(set_max_smem_once((const void *)k_rollout_stock2<true>, env->ctx->device));
+    FR_CUDA(set_max_smem_once((const void *)k_rollout_stock2<false>, env->ctx->device));
     FR_CUDA(env_time_mark(env, 0, s));
-    FR_CUDA(cudaLaunchKernelEx(&cfg, k_rollout_stock2, a));
+    if (v.narrow)
+        FR_CUDA(cudaLaunchKernelEx(&cfg, k_rollout_stock2<true>, a));
+    else
+        FR_CUDA(cudaLaunchKernelEx(&cfg, k_rollout_stock2<false>, a));
     FR_CUDA(env_time_mark(env, 1, s));
     FR_CUDA(launch_metrics_replay(v, vlog, T, metrics, s));
     return FR_OK;

@@ -319,3 +319,29 @@ def test_indicator_table_rebuilt_each_rollout_equals_kept(ctx, dev):
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(out[0], out[1]) and torch.equal(out[1], out[2]) and torch.equal(out[0], met_g)
+
+
+def test_fused_stock_rollout_64_bit_accounting(ctx, dev):
+    # prices scaled x3,000 fail env_create's 32-bit range proof, so the
+    # resident-weight fused kernel runs its owners' 64-bit accounting (the
+    # bench's market takes the 32-bit one); teacher-forced bit-exact either way
+    from types import SimpleNamespace
+    w = synth.workload_stock_2048(N=256, T=24)
+    e = w.envs
+    mkt = SimpleNamespace(close=np.ascontiguousarray(w.market.close * 3000), ind=w.market.ind,
+                          high=w.market.high * 3000, low=w.market.low * 3000)
+    mk = fr.fr_market_create(ctx, mkt)
+    env = fr.env_create(ctx, mk, start=e.start, window=e.W, n_assets=e.Ke, bps=e.bps,
+                        init_cash=100_000_000_000)
+    ens = fr.ensemble_create(ctx, w.dims, w.params, precision=fr.PREC_BF16)
+    T = w.T
+    tr = _traj(T, e.N, env.D, 30, dev)
+    met = torch.empty(e.N, 3, dtype=torch.float64, device=dev)
+    fr.rollout(env, ens, T, traj=tr, metrics=met)
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in tr.items()}
+    ref = oracle.stock_run(mkt, e.Ke, e.start, e.W, e.bps, init_cash=100_000_000_000, hmax=100,
+                           fee_bps=10, T=T, act_f32=g["act"])
+    for k in ("obs", "rew", "rew_f32", "done"):
+        assert np.array_equal(g[k], ref[k]), k
+    assert np.array_equal(met.cpu().numpy(), ref["metrics"])
