@@ -250,10 +250,13 @@ struct OwnEnv {
 // which buys what the remaining cash affords.  Returns the cash left; nb
 // receives this lane's filled shares.  cash and the loop state stay
 // warp-uniform, so every collective runs on the full warp.
+// NARROW: every order's cost and the sum of all of them fit 32 bits, so the
+// prefix scan runs on 32-bit values (same sums).
+template <bool NARROW>
 __device__ __noinline__ int64_t own_buy_greedy(int64_t cash, int64_t want, int64_t full, int64_t p, int fee,
                                                   int lane, int64_t &nb)
 {
-    const int64_t one = cost_of(1, p, fee);
+    const int64_t one = NARROW ? (int64_t)cost_of32(1u, (uint32_t)p, fee) : cost_of(1, p, fee);
     unsigned pending = __ballot_sync(FULL_MASK, want > 0);
     nb = 0;
     while (pending) {
@@ -262,7 +265,18 @@ __device__ __noinline__ int64_t own_buy_greedy(int64_t cash, int64_t want, int64
         if (!pending) break;
         mine = (pending >> lane) & 1u;
         const int64_t x = mine ? full : 0;
-        const int64_t pre = warp_incl_scan(x, lane);
+        int64_t pre;
+        if (NARROW) {
+            uint32_t y = (uint32_t)x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t z = __shfl_up_sync(FULL_MASK, y, o);
+                if (lane >= o) y += z;
+            }
+            pre = (int64_t)y;
+        } else {
+            pre = warp_incl_scan(x, lane);
+        }
         const unsigned fail = __ballot_sync(FULL_MASK, mine && pre > cash);
         if (fail == 0u) {
             if (mine) nb = want;
@@ -640,7 +654,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         // arm the next phase: one arrival, the bytes the other CTAs send
         if (ew == 0 && lane == 0 && !*abort) mbar_arrive_expect_tx(xrdy, x_tx);
         const int fee = v.fee_bps;
-        int64_t nsell[NOWN], want[NOWN], full[NOWN], ssum[NOWN], bsum[NOWN], vsum[NOWN];
+        int64_t nsell[NOWN], want[NOWN], full[NOWN], ssum[NOWN], bsum[NOWN], vsum[NOWN], wsum[NOWN];
 #pragma unroll
         for (int i = 0; i < NOWN; ++i) {
             const OwnEnv &st = own[i];
@@ -689,7 +703,11 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                 bsum[i] = (int64_t)__reduce_add_sync(FULL_MASK, f32);
                 vsum[i] = warp_sum_redux(
                     (int64_t)((uint64_t)(uint32_t)p1[i] * (uint32_t)(hcur - nsell[i] + want[i])));
+                // the wanted shares at the next prices (each below an order's
+                // notional bound, their sum below 2^32)
+                wsum[i] = (int64_t)__reduce_add_sync(FULL_MASK, (uint32_t)p1[i] * (uint32_t)want[i]);
             } else {
+                wsum[i] = 0;
                 const int64_t gs = nsell[i] * st.p;
                 full[i] = cost_of(want[i], st.p, fee);
                 ssum[i] = warp_sum_redux(gs - fee_of(gs, fee));
@@ -711,8 +729,22 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                 int64_t nb = want[i];
                 int64_t v1 = cash + vsum[i];
                 if (bsum[i] > cash1) {                 // not every buy fits: greedy partial fills
-                    cash = own_buy_greedy(cash1, want[i], full[i], st.p, fee, lane, nb);
-                    v1 = cash + warp_sum_redux(p1[i] * (st.h - nsell[i] + nb));
+                    if (NARROW) {
+                        // the value without the wanted buys, plus what was filled
+                        const bool can = want[i] > 0 && (int64_t)cost_of32(1u, (uint32_t)st.p, fee) <= cash1;
+                        if (!__any_sync(FULL_MASK, can)) {     // no order affords one share
+                            cash = cash1;
+                            nb = 0;
+                            v1 = cash1 + vsum[i] - wsum[i];
+                        } else {
+                            cash = own_buy_greedy<true>(cash1, want[i], full[i], st.p, fee, lane, nb);
+                            v1 = cash + vsum[i] - wsum[i] +
+                                 (int64_t)__reduce_add_sync(FULL_MASK, (uint32_t)p1[i] * (uint32_t)nb);
+                        }
+                    } else {
+                        cash = own_buy_greedy<false>(cash1, want[i], full[i], st.p, fee, lane, nb);
+                        v1 = cash + warp_sum_redux(p1[i] * (st.h - nsell[i] + nb));
+                    }
                 }
                 rew = v1 - st.v0;
                 st.t += 1;
