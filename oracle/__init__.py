@@ -267,6 +267,37 @@ def fp8_forward(dims, params, act_scales, x, out_act: int) -> np.ndarray:
             return np.tanh(y) if out_act else y
 
 
+def fp8_forward_exact_tail(dims, params, act_scales, x, out_act: int, n_quant: int) -> np.ndarray:
+    """fp8_forward with the first layer's inputs from column n_quant on taken
+    exactly: layer 1 is dequant(codes of x[:, :n_quant] * (1 / sx) . the
+    E4M3 weight codes of those columns) + W1[:, n_quant:] x[:, n_quant:]
+    (float64) + b1, the weight scales sw[n] those of the whole row (as
+    fp8_weights); the later layers as fp8_forward.  The model of an FP8 actor
+    whose action-independent inputs (a stock state's indicator block) enter
+    through a precomputed float table.  float64 [n][out]."""
+    x = np.asarray(x, np.float32)
+    layers = _layers(dims, params)
+    W, b = layers[0]
+    sx = np.float32(act_scales[0])
+    qw, sw = fp8_weights(W)
+    qx = e4m3_round(x[:, :n_quant] * (np.float32(1.0) / sx))
+    acc = qx @ qw[:, :n_quant].T
+    y = acc * (sx * sw).astype(np.float64) + x[:, n_quant:].astype(np.float64) @ W[:, n_quant:].astype(np.float64).T \
+        + b.astype(np.float64)
+    if len(layers) == 1:
+        return np.tanh(y) if out_act else y
+    h = np.maximum(y, 0.0).astype(np.float32)
+    for l, (W, b) in enumerate(layers[1:], start=1):
+        sx = np.float32(act_scales[l])
+        qx = e4m3_round(h * (np.float32(1.0) / sx))
+        qw, sw = fp8_weights(W)
+        y = (qx @ qw.T) * (sx * sw).astype(np.float64) + b.astype(np.float64)
+        if l + 1 < len(layers):
+            h = np.maximum(y, 0.0).astype(np.float32)
+        else:
+            return np.tanh(y) if out_act else y
+
+
 def fp8_calibrate(dims, params, obs) -> np.ndarray:
     """One agent's activation scales [L] float32: max |x_l| / 448 over the
     batch (1 where it is 0), x_l the input of layer l through the fp64

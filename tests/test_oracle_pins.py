@@ -641,6 +641,38 @@ def test_fp8_forward_is_exact_on_representable_networks():
     assert not np.array_equal(y8b, y8) and (np.abs(y8b - y8) <= bound * (1 + 1e-6)).all()
 
 
+def test_fp8_forward_exact_tail_reductions():
+    # the FP8 model with an exact input tail (the fused stock kernel's: the
+    # indicator block through a float table) reduces to the plain FP8 model
+    # when the tail is empty or zero, and to the fp64 forward on the tail
+    # when only the tail is nonzero
+    rng = np.random.default_rng(8)
+    dims = (20, 48, 16, 5)
+    params = synth.actor_params(dims, 1, seed=9)[0]
+    sc = [0.01, 0.02, 0.03]
+    x = rng.normal(0, 1, (64, 20)).astype(np.float32)
+    full = oracle.fp8_forward(dims, params, sc, x, 1)
+    assert np.array_equal(oracle.fp8_forward_exact_tail(dims, params, sc, x, 1, 20), full)
+    x0 = x.copy()
+    x0[:, 7:] = 0.0
+    assert np.array_equal(oracle.fp8_forward_exact_tail(dims, params, sc, x0, 1, 7),
+                          oracle.fp8_forward(dims, params, sc, x0, 1))
+    # a single layer with only the tail nonzero is the exact affine map
+    d1 = (20, 6)
+    p1 = synth.actor_params(d1, 1, seed=10)[0]
+    xt = x.copy()
+    xt[:, :7] = 0.0
+    W = p1[:120].reshape(6, 20).astype(np.float64)
+    b = p1[120:].astype(np.float64)
+    assert np.array_equal(oracle.fp8_forward_exact_tail(d1, p1, [0.5], xt, 0, 7),
+                          xt[:, 7:].astype(np.float64) @ W[:, 7:].T + b)
+    # and a quantised head differs from the exact one by a bounded amount
+    y = oracle.fp8_forward_exact_tail(d1, p1, [0.01], x, 0, 7)
+    ex = x.astype(np.float64) @ W.T + b
+    assert not np.array_equal(y, ex)
+    assert np.abs(y - ex).max() <= 2.0 ** -3 * (np.abs(x[:, :7].astype(np.float64)) @ np.abs(W[:, :7]).T).max() + 1e-6
+
+
 def test_fp8_calibration_scales_homogeneously():
     # zero biases: ReLU networks are positively homogeneous, so doubling the
     # batch doubles every layer's maximum and scale exactly
