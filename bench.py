@@ -502,8 +502,9 @@ def replay_line(fr, ctx, env, ens, T, dev, stream, peak_gbs, capacity=1 << 20, B
 
 
 def uneven_line(fr, ctx, dev, flush, stream, reps=3):
-    """4,096 stock envs with asset counts 10-30 and windows 5-250 days, BF16
-    fused rollout over the longest window, tiles packed by window vs not."""
+    """4,096 stock envs with asset counts 10-30 and windows 5-250 days, fused
+    rollout over the longest window: BF16 with tiles packed by window vs not,
+    the autotuned choice, FP8 fused and unfused."""
     import torch
     from paper_2501_10709_gb300 import synth
     w = synth.workload_uneven()
@@ -535,8 +536,9 @@ def uneven_line(fr, ctx, dev, flush, stream, reps=3):
                         "probe_steps": w.T}
     fr.env_tune_clear(env)
     # FP8 E4M3 actors: activation scales calibrated on 4,096 observations the
-    # BF16 ensemble visits in the first 8 steps; FP8 rollouts run the unfused
-    # path (one launch per stage per step)
+    # BF16 ensemble visits in the first 8 steps (every agent gets the same
+    # first-layer scale, so the resident-weight fused kernel runs them, tiles
+    # packed); the unfused path (one launch per stage per step) beside it
     ens8 = fr.ensemble_create(ctx, w.dims, w.params, precision=fr.PREC_FP8)
     tr = {"obs": torch.empty(8, e.N, env.D, device=dev)}
     fr.env_reset(env)
@@ -544,9 +546,15 @@ def uneven_line(fr, ctx, dev, flush, stream, reps=3):
     rows = torch.linspace(0, 8 * e.N - 1, 4096, device=dev).long()
     fr.ensemble_calibrate_sync(ens8, tr["obs"].reshape(-1, env.D)[rows].contiguous())
     del tr
+    calib = "4,096 observations from the first 8 BF16 steps"
     ts = time_graph_rollouts(fr, env, ens8, w.T, reps, 3, met, flush, stream)
+    res["fp8_fused"] = {"value": work * len(ts) / sum(ts), "ms_per_rollout": 1e3 * statistics.mean(ts),
+                        "calibration": calib, "tiles": "packed"}
+    fr.env_set_rollout_path(env, fr.PATH_UNFUSED)
+    ts = time_graph_rollouts(fr, env, ens8, w.T, reps, 3, met, flush, stream, keep_path=True)
+    fr.env_set_rollout_path(env, fr.PATH_AUTO)
     res["fp8_unfused"] = {"value": work * len(ts) / sum(ts), "ms_per_rollout": 1e3 * statistics.mean(ts),
-                          "calibration": "4,096 observations from the first 8 BF16 steps"}
+                          "calibration": calib}
     ens8.close()
     W = e.W.astype(float)
     res["tile_efficiency_unpacked"] = float((W - 1).sum() / (128 * (W.max() - 1) * ((e.N + 127) // 128)))

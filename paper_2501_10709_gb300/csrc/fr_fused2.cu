@@ -29,6 +29,7 @@
 // write of step s + 1 depends, through the step's chain, on every read of
 // step s.
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <mutex>
@@ -60,6 +61,8 @@ struct F2Layer {
 
 struct F2Plan {
     int M, H1, H2;        // agents, hidden widths
+    int fp8;              // E4M3 operands (kind::f8f6f4) instead of BF16
+    int esz, ck, kmma;    // operand bytes, elements per 16-byte core row, K per MMA
     int n1, n2;           // N of layer 1 / 2 halves (H/2)
     F2Layer l1, l2, l3;
     uint32_t cta_bytes;   // weights per CTA (multiple of 1024)
@@ -69,6 +72,11 @@ struct F2Plan {
 struct F2Image {
     F2Plan plan;
     uint8_t *img;         // device [M][2][cta_bytes]
+    // FP8: dequantisation factors sx[l] * sw[n] [M][3][256] (layer 1: the
+    // state columns' codes; layer 3: the 30 outputs) and 1 / sx[l] [M][4]
+    float *dq = nullptr;
+    float *inv_sx = nullptr;
+    uint32_t scale_version = 0;
     float *b2;            // device [M][H2]
     float *b3;            // device [M][32]
     float *wind;          // device [M][H1*240 + H1]: W1 indicator columns, then b1
@@ -81,6 +89,7 @@ struct F2Args {
     F2Plan plan;
     const uint8_t *img;
     const float *b2, *b3;
+    const float *dq, *inv_sx;   // FP8 only
     const float *Z;       // [M][n_ctx][H1]
     const int32_t *slot; // [N] asset-count slot of each env
     const int32_t *perm; // [tiles*128] env at each tile position (NULL = identity; -1 = empty)
@@ -106,6 +115,10 @@ bool f2_plan(const fr_ensemble *e, F2Plan &p)
     p.M = e->M;
     p.H1 = e->dims[1];
     p.H2 = e->dims[2];
+    p.fp8 = e->precision == FR_PREC_FP8 ? 1 : 0;
+    p.esz = p.fp8 ? 1 : 2;
+    p.ck = p.fp8 ? 16 : 8;
+    p.kmma = p.fp8 ? 32 : 16;
     if (p.H1 % 64 || p.H2 % 64 || p.H1 > 256 || p.H2 > 256) return false;
     p.n1 = p.H1 / 2;
     p.n2 = p.H2 / 2;
@@ -113,11 +126,11 @@ bool f2_plan(const fr_ensemble *e, F2Plan &p)
     auto mk = [&](F2Layer &l, int K, int N) {
         l.K = K;
         l.N = N;
-        int kc = (int)(TC_CHUNK_MAX / (uint32_t)(N * 2)) / 16 * 16;
+        int kc = (int)(TC_CHUNK_MAX / (uint32_t)(N * p.esz)) / p.kmma * p.kmma;
         l.KC = std::min(kc, K);
         l.n_chunks = (K + l.KC - 1) / l.KC;
         l.off = off;
-        off += (uint32_t)(N * K * 2);
+        off += (uint32_t)(N * K * p.esz);
     };
     mk(p.l1, KS, p.n1);
     mk(p.l2, p.H1, p.n2);
@@ -127,7 +140,7 @@ bool f2_plan(const fr_ensemble *e, F2Plan &p)
     // part in its own chunks [H1/8, H1/8 + 8) so that the partner's h1 half
     // can never land on an observation this CTA's layer 1 is still reading;
     // h2's half (layer 3) reuses chunks [0, n2/8)
-    p.a_bytes = (uint32_t)(p.H1 / 8 + KS / 8) * 2048u;
+    p.a_bytes = (uint32_t)(p.H1 / p.ck + KS / p.ck) * 2048u;
     return true;
 }
 
@@ -138,15 +151,15 @@ __host__ __device__ inline int f2_owned_rows(int M) { return (128 + 2 * M - 1) /
 // Observation bytes a CTA receives per step from the other CTAs: the 64
 // BF16 state entries (128 bytes) and the Z row index (4 bytes) of every row
 // it does not own.
-__host__ __device__ inline uint32_t f2_obs_tx_bytes(int M, int rank)
+__host__ __device__ inline uint32_t f2_obs_tx_bytes(int M, int rank, int esz)
 {
     const int rows = (127 - rank) / (2 * M) + 1;
-    return (uint32_t)(128 - rows) * 132u;
+    return (uint32_t)(128 - rows) * (uint32_t)(64 * esz + 4);
 }
 
 // h1 bytes a CTA receives per step from its partner: 128 rows of the
 // partner's H1 / 2 columns in BF16.
-__host__ __device__ inline uint32_t f2_h1_tx_bytes(const F2Plan &p) { return 128u * (uint32_t)p.n1 * 2u; }
+__host__ __device__ inline uint32_t f2_h1_tx_bytes(const F2Plan &p) { return 128u * (uint32_t)p.n1 * (uint32_t)p.esz; }
 
 // Layer-3 partial-sum bytes a CTA receives per step from the other 2M - 1
 // CTAs: 128 bytes for each of its owned rows from each.
@@ -170,8 +183,11 @@ __host__ __device__ inline F2Smem f2_smem(const F2Plan &p)
     // rows, one block per sending CTA (agent j, half h at block 2j + h)
     s.xbuf = s.a + p.a_bytes;
     s.ctx = s.xbuf + (uint32_t)(2 * p.M * f2_owned_rows(p.M)) * 128u;   // [128] int32 Z row of each env
-    s.bias = s.ctx + 512u;                          // this CTA's b2 half [128], b3 of every agent [4][32]
-    s.bars = s.bias + 1024u;
+    // this CTA's b2 half [128], b3 of every agent [4][32]; FP8: this CTA's
+    // dq1 and dq2 halves [128] each, dq3 of every agent [4][32], this
+    // agent's 1 / sx[0..2]
+    s.bias = s.ctx + 512u;
+    s.bars = s.bias + 3072u;
     s.total = s.bars + 256u;
     return s;
 }
@@ -200,13 +216,16 @@ __device__ __forceinline__ void pack8_bf16(const float *v, uint32_t *w)
 // by lane 0 of env warp 0 at the point where that warp waits on the layer's
 // operands anyway; a dedicated issuer warp would make the block 10 warps,
 // which caps every thread at 168 registers and makes the env code spill.
+template <bool FP8>
 __device__ __noinline__ void f2_layer(const F2Layer &l, uint32_t d_tmem, uint32_t a_at, uint32_t w_base,
                                          uint64_t *acc)
 {
     using namespace ptx;
     fence_proxy_async_smem();
     tc_fence_after();
-    const uint32_t idesc = idesc_bf16(128, l.N);
+    // one MMA per K step of 16 (BF16) or 32 (E4M3) elements: two 16-byte
+    // core-matrix columns of A and of B either way
+    const uint32_t idesc = FP8 ? idesc_e4m3(128, l.N) : idesc_bf16(128, l.N);
     const uint32_t lbo_b = (uint32_t)(l.N * 16);
     // the layer's resident weights are its K-major core-matrix columns end to
     // end (the image's chunks are contiguous), so both descriptors advance by
@@ -215,11 +234,18 @@ __device__ __noinline__ void f2_layer(const F2Layer &l, uint32_t d_tmem, uint32_
     uint64_t ad = smem_desc(a_at, 2048u, 128u);
     uint64_t bd = smem_desc(w_base + l.off, lbo_b, 128u);
     const uint64_t b_step = (uint64_t)((2u * lbo_b) >> 4);
-    mma_bf16(d_tmem, ad, bd, idesc, 0u);
-    for (int k = 16; k < l.K; k += 16) {
+    constexpr int KM = FP8 ? 32 : 16;
+    if (FP8)
+        mma_e4m3(d_tmem, ad, bd, idesc, 0u);
+    else
+        mma_bf16(d_tmem, ad, bd, idesc, 0u);
+    for (int k = KM; k < l.K; k += KM) {
         ad += 256u;
         bd += b_step;
-        mma_bf16(d_tmem, ad, bd, idesc, 1u);
+        if (FP8)
+            mma_e4m3(d_tmem, ad, bd, idesc, 1u);
+        else
+            mma_bf16(d_tmem, ad, bd, idesc, 1u);
     }
     mma_commit(acc);
 }
@@ -322,8 +348,8 @@ struct ObsWords {
     float pv, hv, cv;
 };
 
-template <bool NARROW>
-__device__ __forceinline__ ObsWords own_words(const F2Args &a, const OwnEnv &s, bool valid, int lane)
+template <bool NARROW, bool FP8>
+__device__ __forceinline__ ObsWords own_words(const F2Args &a, const OwnEnv &s, bool valid, int lane, float inv0)
 {
     ObsWords o;
     // NARROW prices are below 2^31: the 32-bit conversion rounds the same
@@ -331,6 +357,28 @@ __device__ __forceinline__ ObsWords own_words(const F2Args &a, const OwnEnv &s, 
                                   : 0.0f;
     o.hv = (valid && lane < s.Ke) ? __fmul_rn(__int2float_rn(s.h), 1e-2f) : 0.0f;
     o.cv = valid ? obs_scale(s.cash, 1e-8f) : 0.0f;
+    o.zrow = valid ? s.slot * a.v.n_days + s.start + s.t : 0;
+    if (FP8) {
+        // E4M3 codes of value * (1 / sx[0]) (the agents share the scale):
+        // chunk c = positions 16c .. 16c + 15 of the state, built by the
+        // lanes with c = lane & 3 from the price and holding codes of the
+        // asset lanes
+        const uint32_t mine = e4m3x2(__fmul_rn(o.pv, inv0), __fmul_rn(o.hv, inv0));   // price low, holding high
+        const uint32_t cc = e4m3x2(__fmul_rn(o.cv, inv0), 0.0f) & 0xffu;
+        uint32_t b[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int pos = 16 * (lane & 3) + u;
+            const int src = pos <= SK2 ? pos - 1 : pos - 1 - SK2;
+            const uint32_t g = __shfl_sync(FULL_MASK, mine, src & 31);
+            b[u] = pos == 0 ? cc : (pos <= SK2 ? (g & 0xffu) : (pos < NSTATE ? ((g >> 8) & 0xffu) : 0u));
+        }
+        o.w0 = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
+        o.w1 = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
+        o.w2 = b[8] | (b[9] << 8) | (b[10] << 16) | (b[11] << 24);
+        o.w3 = b[12] | (b[13] << 8) | (b[14] << 16) | (b[15] << 24);
+        return o;
+    }
     const __nv_bfloat162 ph2 = __floats2bfloat162_rn(o.pv, o.hv);      // .x price, .y holding
     const uint32_t mine = *(const uint32_t *)&ph2;
     const __nv_bfloat16 cb = __float2bfloat16_rn(o.cv);
@@ -347,7 +395,6 @@ __device__ __forceinline__ ObsWords own_words(const F2Args &a, const OwnEnv &s, 
     o.w1 = hw[2] | (hw[3] << 16);
     o.w2 = hw[4] | (hw[5] << 16);
     o.w3 = hw[6] | (hw[7] << 16);
-    o.zrow = valid ? s.slot * a.v.n_days + s.start + s.t : 0;
     return o;
 }
 
@@ -361,16 +408,23 @@ __device__ __forceinline__ void own_put16(const ObsWords &o, uint32_t at, int m,
     else st_async_v4(map_shared_rank(at, (uint32_t)m), o.w0, o.w1, o.w2, o.w3, map_shared_rank(obs_bar, (uint32_t)m));
 }
 
-// Row r's chunks to CTAs lane >> 3 and 4 + (lane >> 3), its Z row index to
-// CTA `lane`.
+// Row r's chunks to CTAs lane >> 3 and 4 + (lane >> 3) (BF16: 8 chunks) or
+// lane >> 2 (E4M3: 4 chunks), its Z row index to CTA `lane`.
+template <bool FP8>
 __device__ __forceinline__ void own_store(const ObsWords &o, int r, uint32_t a_obs, uint32_t ctx_addr, int M2,
                                           int lane, int rank, uint32_t obs_bar)
 {
     using namespace ptx;
-    const uint32_t at = a_obs + (uint32_t)(lane & 7) * 2048u + (uint32_t)(r / 8) * 128u + (uint32_t)(r % 8) * 16u;
-    const int m0 = lane >> 3;
-    if (m0 < M2) own_put16(o, at, m0, rank, obs_bar);
-    if (m0 + 4 < M2) own_put16(o, at, m0 + 4, rank, obs_bar);
+    if (FP8) {
+        const uint32_t at = a_obs + (uint32_t)(lane & 3) * 2048u + (uint32_t)(r / 8) * 128u + (uint32_t)(r % 8) * 16u;
+        const int m = lane >> 2;
+        if (m < M2) own_put16(o, at, m, rank, obs_bar);
+    } else {
+        const uint32_t at = a_obs + (uint32_t)(lane & 7) * 2048u + (uint32_t)(r / 8) * 128u + (uint32_t)(r % 8) * 16u;
+        const int m0 = lane >> 3;
+        if (m0 < M2) own_put16(o, at, m0, rank, obs_bar);
+        if (m0 + 4 < M2) own_put16(o, at, m0 + 4, rank, obs_bar);
+    }
     if (lane < M2) {
         const uint32_t c = ctx_addr + 4u * (uint32_t)r;
         if (lane == rank)
@@ -384,18 +438,18 @@ __device__ __forceinline__ void own_store(const ObsWords &o, int r, uint32_t a_o
 // Publish the next observations of this warp's owned envs: all rows' words
 // first (their shuffles overlap), then all stores, then the optional fp32
 // trajectory rows.  trow[i] < 0: no trajectory row.
-template <int NOWN, bool NARROW>
+template <int NOWN, bool NARROW, bool FP8>
 __device__ __forceinline__ void own_publish_all(const F2Args &a, const OwnEnv *own, const int *orow, const int *eidx,
                                                 uint32_t a_obs, uint32_t ctx_addr, int M2, int lane, int64_t tbase,
-                                                int rank, uint64_t *obs_bar)
+                                                int rank, uint64_t *obs_bar, float inv0)
 {
     ObsWords o[NOWN];
 #pragma unroll
-    for (int i = 0; i < NOWN; ++i) o[i] = own_words<NARROW>(a, own[i], eidx[i] >= 0, lane);
+    for (int i = 0; i < NOWN; ++i) o[i] = own_words<NARROW, FP8>(a, own[i], eidx[i] >= 0, lane, inv0);
     const uint32_t ob = ptx::smem_u32(obs_bar);
 #pragma unroll
     for (int i = 0; i < NOWN; ++i)
-        if (orow[i] < 128) own_store(o[i], orow[i], a_obs, ctx_addr, M2, lane, rank, ob);
+        if (orow[i] < 128) own_store<FP8>(o[i], orow[i], a_obs, ctx_addr, M2, lane, rank, ob);
     // this CTA's own rows: one local arrival once the warp's plain stores are done
     __syncwarp();
     if (lane == 0) ptx::mbar_arrive(obs_bar);
@@ -413,7 +467,7 @@ __device__ __forceinline__ void own_publish_all(const F2Args &a, const OwnEnv *o
 // NARROW: the env's prices, orders and a step's sells and buys fit 32 bits
 // (EnvView::narrow, proved by env_create): the accounting runs in 32-bit
 // arithmetic, with the same results.
-template <int NOWN, bool NARROW>
+template <int NOWN, bool NARROW, bool FP8>
 __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, const F2Smem L_in, uint64_t *bars,
                             volatile int *abort, int warp, int lane, int rank, int tile)
 {
@@ -435,7 +489,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
     const uint32_t xbuf = smem_u32(smem + L.xbuf);
     const int RO = f2_owned_rows(M);
     const uint32_t x_tx = f2_x_tx_bytes(M, rank);
-    const uint32_t obs_tx = f2_obs_tx_bytes(M, rank);
+    const uint32_t obs_tx = f2_obs_tx_bytes(M, rank, p.esz);
     const uint32_t h1_tx = f2_h1_tx_bytes(p);
     const uint32_t h1r_partner = map_shared_rank(smem_u32(&bars[B_H1]), (uint32_t)(rank ^ 1));
     const uint32_t ctx_addr = smem_u32(smem + L.ctx);
@@ -445,7 +499,11 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
     const int tile0 = tile * 128;
     const bool issuer = ew == 0;
     const uint32_t w_base = smem_u32(smem + L.w);
-    const uint32_t a_obs = a_base + (uint32_t)(p.H1 / 8) * 2048u;
+    const uint32_t a_obs = a_base + (uint32_t)(p.H1 / p.ck) * 2048u;
+    // FP8: this CTA's dequantisation factors and this agent's 1 / sx[l]
+    const float *bsm = (const float *)(smem + L.bias);
+    const float *dq1s = bsm + 256, *dq2s = bsm + 384, *dq3s = bsm + 512;
+    const float inv0 = FP8 ? bsm[640] : 1.0f, inv1 = FP8 ? bsm[641] : 1.0f, inv2 = FP8 ? bsm[642] : 1.0f;
     if (issuer && lane == 0) {
         // resident weights: this CTA's image, loaded once
         const uint8_t *src = a.img + (size_t)rank * p.cta_bytes;
@@ -486,7 +544,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         s.v0 = s.cash + warp_sum(s.p * (int64_t)s.h);
     }
     // observation of step 0
-    own_publish_all<NOWN, NARROW>(a, own, orow, eidx, a_obs, ctx_addr, M2, lane, 0, rank, obs_ready);
+    own_publish_all<NOWN, NARROW, FP8>(a, own, orow, eidx, a_obs, ctx_addr, M2, lane, 0, rank, obs_ready, inv0);
 
     const float *zbase = a.Z + (size_t)j * a.n_ctx_per_agent * p.H1;
     // The step loop has no early exit: its trip count is uniform, so the warp
@@ -517,7 +575,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         // arm the next phase: the owner warps' local arrivals follow, the
         // bytes of the other CTAs' rows are expected
         if (issuer && lane == 0 && !*abort) mbar_arrive_expect_tx(obs_ready, obs_tx);
-        if (issuer && lane == 0) f2_layer(p.l1, tmem, a_obs, w_base, acc);
+        if (issuer && lane == 0) f2_layer<FP8>(p.l1, tmem, a_obs, w_base, acc);
         const int nc1 = p.n1 / 2;                          // columns per warp (<= 64)
         const int c01 = col_half * nc1;
         // all of this warp's Z loads in flight at once, one L2 latency
@@ -542,25 +600,43 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                 tmem_ld16(tmem_row + (uint32_t)(c0 + cc), vv);
                 tmem_ld_wait();
                 float x[16];
+                if constexpr (FP8) {
+                    // dequantise the state part, add the table row (indicators + b1)
+                    const float *dq = dq1s + c0 + cc;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float4 z = zq[4 * q4 + i];
-                    x[4 * i + 0] = fmaxf(__uint_as_float(vv[4 * i + 0]) + z.x, 0.0f);
-                    x[4 * i + 1] = fmaxf(__uint_as_float(vv[4 * i + 1]) + z.y, 0.0f);
-                    x[4 * i + 2] = fmaxf(__uint_as_float(vv[4 * i + 2]) + z.z, 0.0f);
-                    x[4 * i + 3] = fmaxf(__uint_as_float(vv[4 * i + 3]) + z.w, 0.0f);
+                    for (int i = 0; i < 4; ++i) {
+                        const float4 z = zq[4 * q4 + i];
+                        x[4 * i + 0] = fmaxf(__fmaf_rn(__uint_as_float(vv[4 * i + 0]), dq[4 * i + 0], z.x), 0.0f);
+                        x[4 * i + 1] = fmaxf(__fmaf_rn(__uint_as_float(vv[4 * i + 1]), dq[4 * i + 1], z.y), 0.0f);
+                        x[4 * i + 2] = fmaxf(__fmaf_rn(__uint_as_float(vv[4 * i + 2]), dq[4 * i + 2], z.z), 0.0f);
+                        x[4 * i + 3] = fmaxf(__fmaf_rn(__uint_as_float(vv[4 * i + 3]), dq[4 * i + 3], z.w), 0.0f);
+                    }
+                    uint32_t w[4];
+                    e4m3_pack16(x, inv1, w);
+                    const uint32_t at = a_base + (uint32_t)((hh * p.n1 + c0 + cc) / 16) * 2048u + row_off;
+                    st_shared_v4(at, w[0], w[1], w[2], w[3]);
+                    st_async_v4(map_shared_rank(at, (uint32_t)(rank ^ 1)), w[0], w[1], w[2], w[3], h1r_partner);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float4 z = zq[4 * q4 + i];
+                        x[4 * i + 0] = fmaxf(__uint_as_float(vv[4 * i + 0]) + z.x, 0.0f);
+                        x[4 * i + 1] = fmaxf(__uint_as_float(vv[4 * i + 1]) + z.y, 0.0f);
+                        x[4 * i + 2] = fmaxf(__uint_as_float(vv[4 * i + 2]) + z.z, 0.0f);
+                        x[4 * i + 3] = fmaxf(__uint_as_float(vv[4 * i + 3]) + z.w, 0.0f);
+                    }
+                    uint32_t w0[4], w1[4];
+                    pack8_bf16(x, w0);
+                    pack8_bf16(x + 8, w1);
+                    const uint32_t at = a_base + (dst_chunk0 + (uint32_t)(cc / 8)) * 2048u + row_off;
+                    st_shared_v4(at, w0[0], w0[1], w0[2], w0[3]);
+                    st_shared_v4(at + 2048u, w1[0], w1[1], w1[2], w1[3]);
+                    // the partner's copy: asynchronous stores that complete their
+                    // bytes on the partner's h1 barrier
+                    const uint32_t pt = map_shared_rank(at, (uint32_t)(rank ^ 1));
+                    st_async_v4(pt, w0[0], w0[1], w0[2], w0[3], h1r_partner);
+                    st_async_v4(pt + 2048u, w1[0], w1[1], w1[2], w1[3], h1r_partner);
                 }
-                uint32_t w0[4], w1[4];
-                pack8_bf16(x, w0);
-                pack8_bf16(x + 8, w1);
-                const uint32_t at = a_base + (dst_chunk0 + (uint32_t)(cc / 8)) * 2048u + row_off;
-                st_shared_v4(at, w0[0], w0[1], w0[2], w0[3]);
-                st_shared_v4(at + 2048u, w1[0], w1[1], w1[2], w1[3]);
-                // the partner's copy: asynchronous stores that complete their
-                // bytes on the partner's h1 barrier
-                const uint32_t pt = map_shared_rank(at, (uint32_t)(rank ^ 1));
-                st_async_v4(pt, w0[0], w0[1], w0[2], w0[3], h1r_partner);
-                st_async_v4(pt + 2048u, w1[0], w1[1], w1[2], w1[3], h1r_partner);
             }
         }
         tc_fence_before();
@@ -569,7 +645,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         if (issuer) {
             f2_wait(h1r, ph, abort, a.err, 4u, true);
             if (lane == 0 && !*abort) mbar_arrive_expect_tx(h1r, h1_tx);     // arm the next phase
-            if (lane == 0) f2_layer(p.l2, tmem, a_base, w_base, acc);
+            if (lane == 0) f2_layer<FP8>(p.l2, tmem, a_base, w_base, acc);
             __syncwarp();
         }
         // ------------------------------------------------- E2: + b2 -> ReLU
@@ -585,14 +661,23 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                 tmem_ld16(tmem_row + (uint32_t)(c0 + cc), vv);
                 tmem_ld_wait();
                 float x[16];
+                if constexpr (FP8) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) x[i] = fmaxf(__uint_as_float(vv[i]) + b2[c0 + cc + i], 0.0f);
-                uint32_t w0[4], w1[4];
-                pack8_bf16(x, w0);
-                pack8_bf16(x + 8, w1);
-                const uint32_t at = a_base + (uint32_t)((c0 + cc) / 8) * 2048u + row_off;
-                st_shared_v4(at, w0[0], w0[1], w0[2], w0[3]);
-                st_shared_v4(at + 2048u, w1[0], w1[1], w1[2], w1[3]);
+                    for (int i = 0; i < 16; ++i)
+                        x[i] = fmaxf(__fmaf_rn(__uint_as_float(vv[i]), dq2s[c0 + cc + i], b2[c0 + cc + i]), 0.0f);
+                    uint32_t w[4];
+                    e4m3_pack16(x, inv2, w);
+                    st_shared_v4(a_base + (uint32_t)((c0 + cc) / 16) * 2048u + row_off, w[0], w[1], w[2], w[3]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) x[i] = fmaxf(__uint_as_float(vv[i]) + b2[c0 + cc + i], 0.0f);
+                    uint32_t w0[4], w1[4];
+                    pack8_bf16(x, w0);
+                    pack8_bf16(x + 8, w1);
+                    const uint32_t at = a_base + (uint32_t)((c0 + cc) / 8) * 2048u + row_off;
+                    st_shared_v4(at, w0[0], w0[1], w0[2], w0[3]);
+                    st_shared_v4(at + 2048u, w1[0], w1[1], w1[2], w1[3]);
+                }
             }
         }
         fence_proxy_async_smem();
@@ -601,7 +686,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         if (lane == 0) mbar_arrive(h2r);
         if (issuer) {
             f2_wait(h2r, ph, abort, a.err, 8u, false);
-            if (lane == 0) f2_layer(p.l3, tmem + 128u, a_base, w_base, acc);
+            if (lane == 0) f2_layer<FP8>(p.l3, tmem + 128u, a_base, w_base, acc);
             __syncwarp();
         }
         // --------------------------------- E3: partial sums to the owners
@@ -667,7 +752,11 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
             auto agent_act = [&](int jj) {
                 const float p0 = *(const float *)(xr + (size_t)(2 * jj) * RO * 128);
                 const float p1 = *(const float *)(xr + (size_t)(2 * jj + 1) * RO * 128);
-                const float y = lane < SK2 ? tanh_approx(__fadd_rn(__fadd_rn(p0, p1), b3s[32 * jj + lane])) : 0.0f;
+                // FP8: the two halves' sums of codes dequantised together (one
+                // output channel, one factor)
+                const float pre = FP8 ? __fmaf_rn(__fadd_rn(p0, p1), dq3s[32 * jj + lane], b3s[32 * jj + lane])
+                                      : __fadd_rn(__fadd_rn(p0, p1), b3s[32 * jj + lane]);
+                const float y = lane < SK2 ? tanh_approx(pre) : 0.0f;
                 return __half2float(__float2half_rn(y));
             };
             // combine (anchored weighted mean) for this lane's asset
@@ -773,8 +862,8 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
             }
         }
         if (s + 1 < T)
-            own_publish_all<NOWN, NARROW>(a, own, orow, eidx, a_obs, ctx_addr, M2, lane, (int64_t)(s + 1) * v.N,
-                                          rank, obs_ready);
+            own_publish_all<NOWN, NARROW, FP8>(a, own, orow, eidx, a_obs, ctx_addr, M2, lane,
+                                               (int64_t)(s + 1) * v.N, rank, obs_ready, inv0);
     }
     // the other CTAs' asynchronous stores of the last step have landed
     // before this CTA can exit, also when a wait gave up and the loop ran on
@@ -808,7 +897,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
     }
 }
 
-template <bool NARROW>
+template <bool NARROW, bool FP8>
 __global__ void __launch_bounds__(F2_THREADS, 1) k_rollout_stock2(const __grid_constant__ F2Args a)
 {
     using namespace ptx;
@@ -828,7 +917,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_rollout_stock2(const __grid_c
         // this CTA's owner warps (its own rows) plus one arming arrival per
         // phase that expects the other CTAs' rows; phase 0 armed here
         mbar_init(&bars[B_OBS], (uint32_t)F2_ENV_WARPS + 1u);
-        mbar_arrive_expect_tx(&bars[B_OBS], f2_obs_tx_bytes(p.M, rank));
+        mbar_arrive_expect_tx(&bars[B_OBS], f2_obs_tx_bytes(p.M, rank, p.esz));
         mbar_init(&bars[B_ACC], 1);
         // this CTA's E1 warps plus one arming arrival per phase that expects
         // the partner's half; phase 0 armed here
@@ -854,6 +943,14 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_rollout_stock2(const __grid_c
         const int jj = rank >> 1, h2 = rank & 1;
         for (int i = lane; i < 128; i += 32) bs[i] = i < p.n2 ? a.b2[(size_t)jj * p.H2 + h2 * p.n2 + i] : 0.0f;
         for (int i = lane; i < 4 * 32; i += 32) bs[128 + i] = i < p.M * 32 ? a.b3[i] : 0.0f;
+        if (FP8) {
+            for (int i = lane; i < 128; i += 32) {
+                bs[256 + i] = i < p.n1 ? a.dq[((size_t)jj * 3 + 0) * 256 + h2 * p.n1 + i] : 0.0f;
+                bs[384 + i] = i < p.n2 ? a.dq[((size_t)jj * 3 + 1) * 256 + h2 * p.n2 + i] : 0.0f;
+                bs[512 + i] = i < p.M * 32 ? a.dq[((size_t)(i / 32) * 3 + 2) * 256 + (i % 32)] : 0.0f;
+            }
+            if (lane < 3) bs[640 + lane] = a.inv_sx[(size_t)jj * 4 + lane];
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -864,9 +961,9 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_rollout_stock2(const __grid_c
     {
         // owned envs per env warp: ceil(128 / (2M * 8)) = 4, 3, 2 for M = 2..4
         switch (p.M) {
-        case 2: f2_env_loop<4, NARROW>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
-        case 3: f2_env_loop<3, NARROW>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
-        default: f2_env_loop<2, NARROW>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
+        case 2: f2_env_loop<4, NARROW, FP8>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
+        case 3: f2_env_loop<3, NARROW, FP8>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
+        default: f2_env_loop<2, NARROW, FP8>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
         }
     }
     __syncwarp();
@@ -920,36 +1017,68 @@ static void f2_free(fr_ctx *ctx, F2Image &im)
     dev_free(ctx, im.b2, (uint64_t)im.plan.M * im.plan.H2 * 4);
     dev_free(ctx, im.b3, (uint64_t)im.plan.M * 32 * 4);
     dev_free(ctx, im.wind, (uint64_t)im.plan.M * (im.plan.H1 * NIND + im.plan.H1) * 4);
+    dev_free(ctx, im.dq, (uint64_t)im.plan.M * 3 * 256 * 4);
+    dev_free(ctx, im.inv_sx, (uint64_t)im.plan.M * 4 * 4);
     im.img = nullptr;
+    im.dq = im.inv_sx = nullptr;
 }
 
-// Build the per-CTA resident images of an ensemble (host packing, once).
+// Build the per-CTA resident images of an ensemble (host packing, once;
+// FP8 again whenever the activation scales change).  FP8 weights are the
+// actor kernel's: codes of W[n][k] * (1 / sw[n]) with its per-row scales
+// sw[n] (the whole row's, indicator columns included, which enter through
+// the fp32 table unquantised), dequantised by sx[l] * sw[n].
 static int f2_build(const fr_ensemble *e, F2Image &im)
 {
     F2Plan &p = im.plan;
+    const TcImage *t = e->tc;
     std::vector<float> host((size_t)e->M * e->P);
     FR_CUDA(cudaMemcpy(host.data(), e->params, host.size() * 4, cudaMemcpyDeviceToHost));
     std::vector<uint8_t> img((size_t)p.M * 2 * p.cta_bytes, 0);
     std::vector<float> b2((size_t)p.M * p.H2), b3((size_t)p.M * 32, 0.0f);
     std::vector<float> wind((size_t)p.M * (p.H1 * NIND + p.H1));
+    std::vector<float> dq(p.fp8 ? (size_t)p.M * 3 * 256 : 0, 0.0f), inv_sx(p.fp8 ? (size_t)p.M * 4 : 0, 1.0f);
+    int cur_j = 0, cur_l = 0;            // agent and layer being packed (FP8 row scales)
     auto put = [&](uint8_t *base, const F2Layer &l, int n, int k, float w) {
         const int c = k / l.KC, kk = k % l.KC;
+        if (p.fp8) {
+            // n: row within this CTA's half; the global row is resolved by the caller
+            const uint8_t q = (uint8_t)__nv_cvt_float_to_fp8(w, __NV_SATFINITE, __NV_E4M3);
+            base[l.off + (size_t)c * l.N * l.KC + (size_t)(kk / 16) * (l.N * 16) + (size_t)(n / 8) * 128 +
+                 (size_t)(n % 8) * 16 + (size_t)(kk % 16)] = q;
+            return;
+        }
         const uint16_t b = bf16_rne(w);
         memcpy(base + l.off + (size_t)c * l.N * l.KC * 2 + coff(l.N, n, kk), &b, 2);
     };
+    // FP8 operand of global row n of layer l: w * (1 / sw[n])
+    auto wq = [&](int n, float w) { return p.fp8 ? w * (1.0f / t->sw[cur_j][cur_l][n]) : w; };
     for (int j = 0; j < p.M; ++j) {
         const float *P = host.data() + (size_t)j * e->P;
         const float *W1 = P + e->w_off[0], *B1 = P + e->b_off[0];
         const float *W2 = P + e->w_off[1], *B2 = P + e->b_off[1];
         const float *W3 = P + e->w_off[2], *B3 = P + e->b_off[2];
+        cur_j = j;
         for (int hh = 0; hh < 2; ++hh) {
             uint8_t *base = img.data() + (size_t)(2 * j + hh) * p.cta_bytes;
+            cur_l = 0;
             for (int n = 0; n < p.n1; ++n)
-                for (int k = 0; k < NSTATE; ++k) put(base, p.l1, n, k, W1[(size_t)(hh * p.n1 + n) * SD2 + k]);
+                for (int k = 0; k < NSTATE; ++k)
+                    put(base, p.l1, n, k, wq(hh * p.n1 + n, W1[(size_t)(hh * p.n1 + n) * SD2 + k]));
+            cur_l = 1;
             for (int n = 0; n < p.n2; ++n)
-                for (int k = 0; k < p.H1; ++k) put(base, p.l2, n, k, W2[(size_t)(hh * p.n2 + n) * p.H1 + k]);
+                for (int k = 0; k < p.H1; ++k)
+                    put(base, p.l2, n, k, wq(hh * p.n2 + n, W2[(size_t)(hh * p.n2 + n) * p.H1 + k]));
+            cur_l = 2;
             for (int n = 0; n < SK2; ++n)
-                for (int k = 0; k < p.n2; ++k) put(base, p.l3, n, k, W3[(size_t)n * p.H2 + hh * p.n2 + k]);
+                for (int k = 0; k < p.n2; ++k) put(base, p.l3, n, k, wq(n, W3[(size_t)n * p.H2 + hh * p.n2 + k]));
+        }
+        if (p.fp8) {
+            const int width[3] = {p.H1, p.H2, SK2};
+            for (int l = 0; l < 3; ++l) {
+                for (int n = 0; n < width[l]; ++n) dq[((size_t)j * 3 + l) * 256 + n] = t->sx[j][l] * t->sw[j][l][n];
+                inv_sx[(size_t)j * 4 + l] = 1.0f / t->sx[j][l];
+            }
         }
         for (int n = 0; n < p.H2; ++n) b2[(size_t)j * p.H2 + n] = B2[n];
         for (int n = 0; n < SK2; ++n) b3[(size_t)j * 32 + n] = B3[n];
@@ -963,9 +1092,16 @@ static int f2_build(const fr_ensemble *e, F2Image &im)
     if ((rc = dev_alloc(e->ctx, (void **)&im.img, img.size())) ||
         (rc = dev_alloc(e->ctx, (void **)&im.b2, b2.size() * 4)) ||
         (rc = dev_alloc(e->ctx, (void **)&im.b3, b3.size() * 4)) ||
-        (rc = dev_alloc(e->ctx, (void **)&im.wind, wind.size() * 4))) {
+        (rc = dev_alloc(e->ctx, (void **)&im.wind, wind.size() * 4)) ||
+        (p.fp8 && (rc = dev_alloc(e->ctx, (void **)&im.dq, dq.size() * 4))) ||
+        (p.fp8 && (rc = dev_alloc(e->ctx, (void **)&im.inv_sx, inv_sx.size() * 4)))) {
         f2_free(e->ctx, im);
         return rc;
+    }
+    if (p.fp8) {
+        FR_CUDA(cudaMemcpy(im.dq, dq.data(), dq.size() * 4, cudaMemcpyHostToDevice));
+        FR_CUDA(cudaMemcpy(im.inv_sx, inv_sx.data(), inv_sx.size() * 4, cudaMemcpyHostToDevice));
+        im.scale_version = t->scale_version;
     }
     FR_CUDA(cudaMemcpy(im.img, img.data(), img.size(), cudaMemcpyHostToDevice));
     FR_CUDA(cudaMemcpy(im.b2, b2.data(), b2.size() * 4, cudaMemcpyHostToDevice));
@@ -979,7 +1115,11 @@ bool f2_supported(const fr_env *env, const fr_ensemble *e)
 {
     const EnvView &v = env->v;
     if (v.task != FR_TASK_STOCK || v.K != SK2 || v.I != SI2 || e->combine != FR_COMBINE_MEAN ||
-        e->out_act != 1 || e->precision != FR_PREC_BF16 || v.buy_order != FR_BUY_ASCENDING)
+        e->out_act != 1 || v.buy_order != FR_BUY_ASCENDING)
+        return false;
+    // FP8: the owners publish one set of observation codes to every agent,
+    // so the agents must share the first layer's activation scale
+    if (e->precision != FR_PREC_BF16 && !(e->precision == FR_PREC_FP8 && e->tc && e->tc->scaled && e->tc->shared_l0))
         return false;
     F2Plan p;
     if (!f2_plan(e, p)) return false;
@@ -1016,11 +1156,19 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     bool found = false;
     {
         std::lock_guard<std::mutex> lk(g_f2_mu);
-        for (auto &en : g_f2)
-            if (en.ens == e) {
-                imv = en.im;
-                found = true;
+        for (size_t i = 0; i < g_f2.size(); ++i) {
+            if (g_f2[i].ens != e) continue;
+            if (g_f2[i].im.plan.fp8 && g_f2[i].im.scale_version != e->tc->scale_version) {
+                // new activation scales: repack (the old image may still be
+                // read by launches in flight on this stream)
+                FR_CUDA(cudaStreamSynchronize(s));
+                f2_free(e->ctx, g_f2[i].im);
+                g_f2.erase(g_f2.begin() + (long)i);
+                break;
             }
+            imv = g_f2[i].im;
+            found = true;
+        }
         if (!found) {
             F2Entry en{};
             en.ens = e;
@@ -1149,6 +1297,8 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     a.img = im->img;
     a.b2 = im->b2;
     a.b3 = im->b3;
+    a.dq = im->dq;
+    a.inv_sx = im->inv_sx;
     a.Z = Z;
     a.slot = env->slot_of_env;
     a.n_ctx_per_agent = n_ctx;
@@ -1176,13 +1326,11 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    FR_CUDA(set_max_smem_once((const void *)k_rollout_stock2<true>, env->ctx->device));
-    FR_CUDA(set_max_smem_once((const void *)k_rollout_stock2<false>, env->ctx->device));
+    void (*kern)(F2Args) = v.narrow ? (p.fp8 ? k_rollout_stock2<true, true> : k_rollout_stock2<true, false>)
+                                    : (p.fp8 ? k_rollout_stock2<false, true> : k_rollout_stock2<false, false>);
+    FR_CUDA(set_max_smem_once((const void *)kern, env->ctx->device));
     FR_CUDA(env_time_mark(env, 0, s));
-    if (v.narrow)
-        FR_CUDA(cudaLaunchKernelEx(&cfg, k_rollout_stock2<true>, a));
-    else
-        FR_CUDA(cudaLaunchKernelEx(&cfg, k_rollout_stock2<false>, a));
+    FR_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
     FR_CUDA(env_time_mark(env, 1, s));
     FR_CUDA(launch_metrics_replay(v, vlog, T, metrics, s));
     return FR_OK;

@@ -547,6 +547,7 @@ int tc_set_act_scales(fr_ensemble *e, const float *scales)
     FR_CUDA(cudaMemcpy(t->dq, dq.data(), dq.size() * 4, cudaMemcpyHostToDevice));
     FR_CUDA(cudaMemcpy(t->inv_sx, inv.data(), inv.size() * 4, cudaMemcpyHostToDevice));
     t->scaled = true;
+    t->scale_version += 1;
     t->shared_l0 = true;
     for (int j = 1; j < e->M; ++j) t->shared_l0 = t->shared_l0 && t->sx[j][0] == t->sx[0][0];
     return FR_OK;

@@ -71,6 +71,7 @@ struct TcImage {
     float sx[MAX_AGENTS][MAX_LAYERS];
     bool scaled = false;
     bool shared_l0 = false;   // every agent has the same layer-0 scale
+    uint32_t scale_version = 0;   // bumped whenever the activation scales change
 };
 
 

@@ -138,16 +138,18 @@ def test_fp8_crypto_argmax_agreement(ctx, dev):
     assert np.array_equal(votes_gpu.cpu().numpy(), votes)     # the vote of the GPU's own Q-values
 
 
-def test_fp8_stock_rollout_teacher_forced(ctx, dev):
-    # FP8 rollouts run the unfused path: env bit-exact on the emitted
-    # actions, actions within the FP8 tolerance of the oracle's FP8 ensemble
-    w = synth.workload_stock_2048(N=512, T=24)
+def _fp8_stock_rollout(ctx, dev, w, path, scales=None, T=24):
     e = w.envs
     mk = fr.fr_market_create(ctx, w.market)
     env = fr.env_create(ctx, mk, start=e.start, window=e.W, n_assets=e.Ke, bps=e.bps)
+    if path == "unfused":
+        fr.env_set_rollout_path(env, fr.PATH_UNFUSED)
     ens = fr.ensemble_create(ctx, w.dims, w.params, precision=fr.PREC_FP8)
-    sx = fr.ensemble_calibrate_sync(ens, torch.from_numpy(_stock_obs(4096, seed=44)).to(dev))
-    T = 24
+    if scales is None:
+        sx = fr.ensemble_calibrate_sync(ens, torch.from_numpy(_stock_obs(4096, seed=44)).to(dev))
+    else:
+        fr.ensemble_set_act_scales(ens, scales)
+        sx = scales
     tr = {"obs": torch.full((T, e.N, env.D), np.nan, device=dev),
           "act": torch.full((T, e.N, 30), np.nan, device=dev),
           "rew": torch.zeros(T, e.N, dtype=torch.int64, device=dev),
@@ -161,12 +163,102 @@ def test_fp8_stock_rollout_teacher_forced(ctx, dev):
     for k in ("obs", "rew", "done"):
         assert np.array_equal(g[k], ref[k]), k
     assert np.array_equal(met.cpu().numpy(), ref["metrics"])
-    rows = np.random.default_rng(1).choice(T * e.N, 256, replace=False)
+    return env, ens, sx, g
+
+
+@pytest.mark.parametrize("path", ["fused", "unfused"])
+def test_fp8_stock_rollout_teacher_forced(ctx, dev, path):
+    # env bit-exact on the emitted actions either way.  Unfused: every input
+    # of the first layer quantised (the actor kernel).  Fused (the agents
+    # share the first layer's scale, as calibration on observations gives):
+    # the 61 state entries quantised, the indicator block through the exact
+    # fp32 table.  Actions within the FP8 tolerance of the matching oracle
+    # model, discretised shares within one of it
+    w = synth.workload_stock_2048(N=512, T=24)
+    env, ens, sx, g = _fp8_stock_rollout(ctx, dev, w, path)
+    assert np.all(sx[:, 0] == sx[0, 0])
+    T, N = 24, w.envs.N
+    rows = np.random.default_rng(1).choice(T * N, 512, replace=False)
     obs = g["obs"].reshape(-1, env.D)[rows]
     act = g["act"].reshape(-1, 30)[rows].astype(np.float64)
-    ys = np.stack([oracle.fp8_forward(w.dims, w.params[j], sx[j], obs, 1) for j in range(3)])
+    if path == "fused":
+        ys = np.stack([oracle.fp8_forward_exact_tail(w.dims, w.params[j], sx[j], obs, 1, 61) for j in range(3)])
+    else:
+        ys = np.stack([oracle.fp8_forward(w.dims, w.params[j], sx[j], obs, 1) for j in range(3)])
     want = np.stack([oracle.ensemble_mean(ys[:, i]) for i in range(len(rows))])
-    assert _rel(act, want).max() <= FP8_TOL
+    err = _rel(act, want)
+    print(f"{path}: rel err max {err.max():.3e} median {np.median(err):.3e}")
+    assert err.max() <= FP8_TOL
+    qg = oracle.discretise_many(act.astype(np.float32), 100)
+    qw = np.array([oracle.discretise(x, 100) for x in want.ravel()])
+    assert np.mean(np.abs(qg - qw) <= 1) >= 0.999
+
+
+def test_fp8_fused_rollout_follows_new_scales_and_unshared_scales_fall_back(ctx, dev):
+    # the fused kernel's image is repacked when the activation scales change;
+    # agents with different first-layer scales run the unfused path (one set
+    # of observation codes cannot serve them), whose model is fp8_forward
+    w = synth.workload_stock_2048(N=256, T=16)
+    env, ens, sx, g0 = _fp8_stock_rollout(ctx, dev, w, "fused", T=16)
+    sx2 = (sx * np.float32(1.5)).astype(np.float32)
+    fr.ensemble_set_act_scales(ens, sx2)
+    fr.env_reset(env)
+    act = torch.full((16, w.envs.N, 30), np.nan, device=dev)
+    obs = torch.full((16, w.envs.N, env.D), np.nan, device=dev)
+    fr.rollout(env, ens, 16, traj={"act": act, "obs": obs})
+    torch.cuda.synchronize()
+    a, o = act.cpu().numpy().reshape(-1, 30), obs.cpu().numpy().reshape(-1, env.D)
+    rows = np.random.default_rng(2).choice(a.shape[0], 256, replace=False)
+    ys = np.stack([oracle.fp8_forward_exact_tail(w.dims, w.params[j], sx2[j], o[rows], 1, 61) for j in range(3)])
+    want = np.stack([oracle.ensemble_mean(ys[:, i]) for i in range(len(rows))])
+    assert _rel(a[rows].astype(np.float64), want).max() <= FP8_TOL
+    assert not np.array_equal(a, g0["act"].reshape(-1, 30))
+    # unshared layer-0 scales
+    sx3 = sx.copy()
+    sx3[1, 0] *= np.float32(1.25)
+    _, _, _, g3 = _fp8_stock_rollout(ctx, dev, w, "fused", scales=sx3, T=16)
+    o3, a3 = g3["obs"].reshape(-1, env.D)[rows], g3["act"].reshape(-1, 30)[rows].astype(np.float64)
+    ys = np.stack([oracle.fp8_forward(w.dims, w.params[j], sx3[j], o3, 1) for j in range(3)])
+    want = np.stack([oracle.ensemble_mean(ys[:, i]) for i in range(len(rows))])
+    assert _rel(a3, want).max() <= FP8_TOL
+
+
+def test_fp8_fused_packed_tiles_and_graph_replay(ctx, dev):
+    # uneven windows: packed tiles (no trajectory) equal the unpacked run;
+    # a captured reset + rollout replays to the same metrics
+    N, T = 700, 130
+    mk_np = synth.stock_market(400, 30, seed=51)
+    e = synth.stock_envs_uneven(N, 30, 400, k_lo=10, w_lo=5, w_hi=120, seed=51)
+    params = synth.actor_params(synth.STOCK_DIMS, 3, seed=52)
+    mk = fr.fr_market_create(ctx, mk_np)
+    ens = fr.ensemble_create(ctx, synth.STOCK_DIMS, params, precision=fr.PREC_FP8)
+    fr.ensemble_calibrate_sync(ens, torch.from_numpy(_stock_obs(2048, seed=46)).to(dev))
+    mets = []
+    for packing in (True, False):
+        env = fr.env_create(ctx, mk, start=e.start, window=e.W, n_assets=e.Ke, bps=e.bps)
+        fr.env_set_tile_packing(env, packing)
+        met = torch.empty(N, 3, dtype=torch.float64, device=dev)
+        fr.rollout(env, ens, T, metrics=met)
+        torch.cuda.synchronize()
+        mets.append(met.cpu().numpy())
+    assert np.array_equal(mets[0], mets[1])
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    met = torch.empty(N, 3, dtype=torch.float64, device=dev)
+    with torch.cuda.stream(side):
+        fr.env_reset(env)
+        fr.rollout(env, ens, T, metrics=met)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fr.env_reset(env)
+        fr.rollout(env, ens, T, metrics=met)
+    for _ in range(2):
+        met.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(met.cpu().numpy(), mets[1])
 
 
 def test_fp8_scales_required_and_checked(ctx, dev):
