@@ -76,6 +76,23 @@ __device__ __forceinline__ int64_t afford(int64_t c, int64_t p, int fee_bps)
     return n;
 }
 
+// afford() for an order whose full cost fits 32 bits (EnvView::narrow): the
+// largest n < want with cost_of32(n) <= c, given c below cost_of32(want).
+// cost_of32(n) lies in [n p (1 + fee/1e4), n p (1 + fee/1e4) + 1), so the
+// fp32 quotient c / (p (1 + fee/1e4)) is within one of the answer while it
+// stays below 2^20; the exact 32-bit comparisons then settle it (bounded
+// loops, like afford's).  Every cost compared is at most cost_of32(want).
+__device__ __forceinline__ uint32_t afford32(uint32_t c, uint32_t p, int fee_bps, uint32_t want)
+{
+    const float q = __fdividef((float)c, __fmul_rn((float)p, __fmaf_rn((float)fee_bps, 1e-4f, 1.0f)));
+    uint32_t n = q > 0.0f ? min((uint32_t)q, want - 1u) : 0u;
+#pragma unroll 1
+    for (int i = 0; i < 8 && n > 0 && cost_of32(n, p, fee_bps) > c; ++i) --n;
+#pragma unroll 1
+    for (int i = 0; i < 8 && n + 1u < want && cost_of32(n + 1u, p, fee_bps) <= c; ++i) ++n;
+    return n;
+}
+
 // Action in [-1,1] -> share change trunc(a * hmax).  __fmul_rz keeps the
 // product on the zero side of the exact value and integers up to hmax are
 // representable, so the truncation equals that of the exact product.

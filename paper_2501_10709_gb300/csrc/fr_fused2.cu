@@ -144,6 +144,10 @@ bool f2_plan(const fr_ensemble *e, F2Plan &p)
     return true;
 }
 
+// K position in layer 1's operands of state entry k (0 cash, 1..30 prices,
+// 31..60 holdings): prices and holdings interleaved by asset, cash last.
+__host__ __device__ inline int f2_state_pos(int k) { return k == 0 ? 2 * SK2 : (k <= SK2 ? 2 * (k - 1) : 2 * (k - 1 - SK2) + 1); }
+
 // Rows of the tile owned by one CTA: row r belongs to rank r mod 2M and sits
 // at index r / 2M of that CTA's owned rows.
 __host__ __device__ inline int f2_owned_rows(int M) { return (128 + 2 * M - 1) / (2 * M); }
@@ -216,30 +220,32 @@ __device__ __forceinline__ void pack8_bf16(const float *v, uint32_t *w)
 // by lane 0 of env warp 0 at the point where that warp waits on the layer's
 // operands anyway; a dedicated issuer warp would make the block 10 warps,
 // which caps every thread at 168 registers and makes the env code spill.
+// The layer's shape comes by value (K, N, byte offset): a reference would
+// take the address of the caller's plan and keep it in local memory.
 template <bool FP8>
-__device__ __noinline__ void f2_layer(const F2Layer &l, uint32_t d_tmem, uint32_t a_at, uint32_t w_base,
-                                         uint64_t *acc)
+__device__ __noinline__ void f2_layer(int K, int N, uint32_t off, uint32_t d_tmem, uint32_t a_at, uint32_t w_base,
+                                      uint64_t *acc)
 {
     using namespace ptx;
     fence_proxy_async_smem();
     tc_fence_after();
     // one MMA per K step of 16 (BF16) or 32 (E4M3) elements: two 16-byte
     // core-matrix columns of A and of B either way
-    const uint32_t idesc = FP8 ? idesc_e4m3(128, l.N) : idesc_bf16(128, l.N);
-    const uint32_t lbo_b = (uint32_t)(l.N * 16);
+    const uint32_t idesc = FP8 ? idesc_e4m3(128, N) : idesc_bf16(128, N);
+    const uint32_t lbo_b = (uint32_t)(N * 16);
     // the layer's resident weights are its K-major core-matrix columns end to
     // end (the image's chunks are contiguous), so both descriptors advance by
     // constant offsets per K = 16 step: 2 columns of A (4,096 B) and of B
     // (2 N 16 B), in the start-address field's 16-byte units
     uint64_t ad = smem_desc(a_at, 2048u, 128u);
-    uint64_t bd = smem_desc(w_base + l.off, lbo_b, 128u);
+    uint64_t bd = smem_desc(w_base + off, lbo_b, 128u);
     const uint64_t b_step = (uint64_t)((2u * lbo_b) >> 4);
     constexpr int KM = FP8 ? 32 : 16;
     if (FP8)
         mma_e4m3(d_tmem, ad, bd, idesc, 0u);
     else
         mma_bf16(d_tmem, ad, bd, idesc, 0u);
-    for (int k = KM; k < l.K; k += KM) {
+    for (int k = KM; k < K; k += KM) {
         ad += 256u;
         bd += b_step;
         if (FP8)
@@ -273,15 +279,20 @@ struct OwnEnv {
 // Greedy buys in ascending asset order with partial fills, for the case
 // where the orders do not all fit in `cash`: lanes whose single share no
 // longer fits drop out; a scan finds the first order that does not fit,
-// which buys what the remaining cash affords.  Returns the cash left; nb
-// receives this lane's filled shares.  cash and the loop state stay
+// which buys what the remaining cash affords.  Returns the cash left and
+// this lane's filled shares (by value: an output reference would put the
+// caller's variable in local memory).  cash and the loop state stay
 // warp-uniform, so every collective runs on the full warp.
 // NARROW: every order's cost and the sum of all of them fit 32 bits, so the
 // prefix scan runs on 32-bit values (same sums).
+struct Fill {
+    int64_t cash, nb;
+};
+
 template <bool NARROW>
-__device__ __noinline__ int64_t own_buy_greedy(int64_t cash, int64_t want, int64_t full, int64_t p, int fee,
-                                                  int lane, int64_t &nb)
+__device__ __noinline__ Fill own_buy_greedy(int64_t cash, int64_t want, int64_t full, int64_t p, int fee, int lane)
 {
+    int64_t nb;
     const int64_t one = NARROW ? (int64_t)cost_of32(1u, (uint32_t)p, fee) : cost_of(1, p, fee);
     unsigned pending = __ballot_sync(FULL_MASK, want > 0);
     nb = 0;
@@ -313,14 +324,16 @@ __device__ __noinline__ int64_t own_buy_greedy(int64_t cash, int64_t want, int64
         if (mine && lane < f) nb = want;
         int64_t cf = cash - (pre - x);
         if (lane == f) {
-            const int64_t n = afford(cf, p, fee);
+            // the failing order: cf is below its cost, so (NARROW) below 2^32
+            const int64_t n = NARROW ? (int64_t)afford32((uint32_t)cf, (uint32_t)p, fee, (uint32_t)want)
+                                     : afford(cf, p, fee);
             nb = n;
-            cf -= cost_of(n, p, fee);
+            cf -= NARROW ? (int64_t)cost_of32((uint32_t)n, (uint32_t)p, fee) : cost_of(n, p, fee);
         }
         cash = __shfl_sync(FULL_MASK, cf, f);
         pending &= ~((2u << f) - 1u);
     }
-    return cash;
+    return Fill{cash, nb};
 }
 
 // fp32 trajectory observation of the step about to be taken (optional output,
@@ -337,11 +350,16 @@ __device__ __noinline__ void own_traj_obs(const F2Args &a, float *o, float cv, f
     for (int i = lane; i < NIND; i += 32) o[NSTATE + i] = (i % SK2) < Ke ? __ldg(f + i) : 0.0f;
 }
 
-// The next observation row of env r: state positions 0..63 (cash, 30
-// prices, 30 holdings, zero padding) as BF16, chunk c = positions 8c..8c+7.
-// Every lane builds the words of chunk lane & 7 from the warp's price and
-// holding pairs, so that the stores to the cluster's CTAs spread over all
-// lanes: one 16-byte store per lane per four destination CTAs.
+// The next observation row of env r: its 61 state entries in the A
+// operand's K order, which puts asset k's price and holding side by side:
+// position 2k = price k, 2k + 1 = holding k (k < 30), 60 = cash, 61..63 zero
+// (layer 1's weight columns are packed in the same order; the dot product
+// does not depend on it).  So lane k's (price, holding) pair is one BF16x2
+// word (lane 30: cash and 0; lane 31: 0) and chunk c, positions 8c..8c+7, is
+// the words of lanes 4c..4c+3: four shuffles per row.  E4M3: lane k's pair is
+// 16 bits, two lanes make a word, chunk c (16 positions) is the words of
+// lanes 8c, 8c + 2, 8c + 4, 8c + 6.  Every lane builds the chunk it stores,
+// so that the stores to the cluster's CTAs spread over all lanes.
 struct ObsWords {
     uint32_t w0, w1, w2, w3;
     int zrow;
@@ -359,42 +377,30 @@ __device__ __forceinline__ ObsWords own_words(const F2Args &a, const OwnEnv &s, 
     o.cv = valid ? obs_scale(s.cash, 1e-8f) : 0.0f;
     o.zrow = valid ? s.slot * a.v.n_days + s.start + s.t : 0;
     if (FP8) {
-        // E4M3 codes of value * (1 / sx[0]) (the agents share the scale):
-        // chunk c = positions 16c .. 16c + 15 of the state, built by the
-        // lanes with c = lane & 3 from the price and holding codes of the
-        // asset lanes
-        const uint32_t mine = e4m3x2(__fmul_rn(o.pv, inv0), __fmul_rn(o.hv, inv0));   // price low, holding high
-        const uint32_t cc = e4m3x2(__fmul_rn(o.cv, inv0), 0.0f) & 0xffu;
-        uint32_t b[16];
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int pos = 16 * (lane & 3) + u;
-            const int src = pos <= SK2 ? pos - 1 : pos - 1 - SK2;
-            const uint32_t g = __shfl_sync(FULL_MASK, mine, src & 31);
-            b[u] = pos == 0 ? cc : (pos <= SK2 ? (g & 0xffu) : (pos < NSTATE ? ((g >> 8) & 0xffu) : 0u));
-        }
-        o.w0 = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
-        o.w1 = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
-        o.w2 = b[8] | (b[9] << 8) | (b[10] << 16) | (b[11] << 24);
-        o.w3 = b[12] | (b[13] << 8) | (b[14] << 16) | (b[15] << 24);
+        // E4M3 codes of value * (1 / sx[0]) (the agents share the scale)
+        const uint32_t pair = lane < SK2 ? e4m3x2(__fmul_rn(o.pv, inv0), __fmul_rn(o.hv, inv0))
+                                         : (lane == SK2 ? (e4m3x2(__fmul_rn(o.cv, inv0), 0.0f) & 0xffu) : 0u);
+        const uint32_t word = pair | (__shfl_down_sync(FULL_MASK, pair, 1) << 16);   // even lanes
+        const int src = 8 * (lane & 3);
+        o.w0 = __shfl_sync(FULL_MASK, word, src);
+        o.w1 = __shfl_sync(FULL_MASK, word, src + 2);
+        o.w2 = __shfl_sync(FULL_MASK, word, src + 4);
+        o.w3 = __shfl_sync(FULL_MASK, word, src + 6);
         return o;
     }
-    const __nv_bfloat162 ph2 = __floats2bfloat162_rn(o.pv, o.hv);      // .x price, .y holding
-    const uint32_t mine = *(const uint32_t *)&ph2;
-    const __nv_bfloat16 cb = __float2bfloat16_rn(o.cv);
-    const uint32_t cbits = (uint32_t)*(const uint16_t *)&cb;
-    uint32_t hw[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        const int pos = 8 * (lane & 7) + u;
-        const int src = pos <= SK2 ? pos - 1 : pos - 1 - SK2;
-        const uint32_t g = __shfl_sync(FULL_MASK, mine, src & 31);
-        hw[u] = pos == 0 ? cbits : (pos <= SK2 ? (g & 0xffffu) : (pos < NSTATE ? (g >> 16) : 0u));
+    uint32_t word;
+    if (lane < SK2) {
+        const __nv_bfloat162 ph2 = __floats2bfloat162_rn(o.pv, o.hv);      // .x price, .y holding
+        word = *(const uint32_t *)&ph2;
+    } else {
+        const __nv_bfloat16 cb = __float2bfloat16_rn(o.cv);
+        word = lane == SK2 ? (uint32_t)*(const uint16_t *)&cb : 0u;
     }
-    o.w0 = hw[0] | (hw[1] << 16);
-    o.w1 = hw[2] | (hw[3] << 16);
-    o.w2 = hw[4] | (hw[5] << 16);
-    o.w3 = hw[6] | (hw[7] << 16);
+    const int src = 4 * (lane & 7);
+    o.w0 = __shfl_sync(FULL_MASK, word, src);
+    o.w1 = __shfl_sync(FULL_MASK, word, src + 1);
+    o.w2 = __shfl_sync(FULL_MASK, word, src + 2);
+    o.w3 = __shfl_sync(FULL_MASK, word, src + 3);
     return o;
 }
 
@@ -555,6 +561,17 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
     // A packed tile runs only until its longest window is over (uniform
     // across the cluster: one value per tile).
     const int T = a.tile_w ? min(a.T, max(a.tile_w[tile] - 1, 0)) : a.T;
+    // this lane's word of each owned row in the layer-3 partial-sum buffer
+    // (fixed for the launch)
+    uint32_t xoff[NOWN];
+#pragma unroll
+    for (int i = 0; i < NOWN; ++i) {
+        const int ri = min(orow[i] / M2, RO - 1);
+        xoff[i] = L.xbuf + (uint32_t)ri * 128u + 16u * (uint32_t)((lane >> 2) ^ (ri & 7)) + 4u * (uint32_t)(lane & 3);
+    }
+    // uniform per launch: read once, not per step
+    const bool explore = a.ex.kind == FR_EXPLORE_GAUSSIAN;
+    float *const tr_act = a.tr_act;
     if (issuer) f2_wait(&bars[B_W], 0u, abort, a.err, 1u, false);
     for (int s = 0; s < T; ++s) {
         const uint32_t ph = (uint32_t)s & 1u;
@@ -575,7 +592,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         // arm the next phase: the owner warps' local arrivals follow, the
         // bytes of the other CTAs' rows are expected
         if (issuer && lane == 0 && !*abort) mbar_arrive_expect_tx(obs_ready, obs_tx);
-        if (issuer && lane == 0) f2_layer<FP8>(p.l1, tmem, a_obs, w_base, acc);
+        if (issuer && lane == 0) f2_layer<FP8>(p.l1.K, p.l1.N, p.l1.off, tmem, a_obs, w_base, acc);
         const int nc1 = p.n1 / 2;                          // columns per warp (<= 64)
         const int c01 = col_half * nc1;
         // all of this warp's Z loads in flight at once, one L2 latency
@@ -645,7 +662,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         if (issuer) {
             f2_wait(h1r, ph, abort, a.err, 4u, true);
             if (lane == 0 && !*abort) mbar_arrive_expect_tx(h1r, h1_tx);     // arm the next phase
-            if (lane == 0) f2_layer<FP8>(p.l2, tmem, a_base, w_base, acc);
+            if (lane == 0) f2_layer<FP8>(p.l2.K, p.l2.N, p.l2.off, tmem, a_base, w_base, acc);
             __syncwarp();
         }
         // ------------------------------------------------- E2: + b2 -> ReLU
@@ -686,7 +703,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         if (lane == 0) mbar_arrive(h2r);
         if (issuer) {
             f2_wait(h2r, ph, abort, a.err, 8u, false);
-            if (lane == 0) f2_layer<FP8>(p.l3, tmem + 128u, a_base, w_base, acc);
+            if (lane == 0) f2_layer<FP8>(p.l3.K, p.l3.N, p.l3.off, tmem + 128u, a_base, w_base, acc);
             __syncwarp();
         }
         // --------------------------------- E3: partial sums to the owners
@@ -740,14 +757,15 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         if (ew == 0 && lane == 0 && !*abort) mbar_arrive_expect_tx(xrdy, x_tx);
         const int fee = v.fee_bps;
         int64_t nsell[NOWN], want[NOWN], full[NOWN], ssum[NOWN], bsum[NOWN], vsum[NOWN], wsum[NOWN];
+        // The owned envs' actions first, all envs together, then (only when
+        // asked for) exploration and the recorded actions, then the trades'
+        // reductions: no out-of-line call sits between the envs' chains.
+        float actv[NOWN];
 #pragma unroll
         for (int i = 0; i < NOWN; ++i) {
-            const OwnEnv &st = own[i];
-            const int ri = min(orow[i] / M2, RO - 1);
-            const int e = eidx[i];
             // agent jj's action for this lane's asset: tanh(partial of half 0
             // + partial of half 1 + b3), rounded to fp16
-            const uint8_t *xr = smem + L.xbuf + (size_t)ri * 128 + 16 * ((lane >> 2) ^ (ri & 7)) + 4 * (lane & 3);
+            const uint8_t *xr = smem + xoff[i];
             const float *b3s = (const float *)(smem + L.bias) + 128;
             auto agent_act = [&](int jj) {
                 const float p0 = *(const float *)(xr + (size_t)(2 * jj) * RO * 128);
@@ -770,9 +788,21 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                     act = __fadd_rn(act, __fmul_rn(wj, __fsub_rn(aj, a0)));
                 }
             }
-            if (a.ex.kind == FR_EXPLORE_GAUSSIAN && e >= 0 && lane < SK2)
-                act = f2_explore(a.ex, act, (uint32_t)e, a.ex.g0 + (uint32_t)s, (uint32_t)lane);
-            if (a.tr_act && e >= 0 && lane < SK2) a.tr_act[((int64_t)s * v.N + e) * SK2 + lane] = act;
+            actv[i] = act;
+        }
+        if (explore || tr_act) {
+#pragma unroll
+            for (int i = 0; i < NOWN; ++i) {
+                const int e = eidx[i];
+                if (explore && e >= 0 && lane < SK2)
+                    actv[i] = f2_explore(a.ex, actv[i], (uint32_t)e, a.ex.g0 + (uint32_t)s, (uint32_t)lane);
+                if (tr_act && e >= 0 && lane < SK2) tr_act[((int64_t)s * v.N + e) * SK2 + lane] = actv[i];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NOWN; ++i) {
+            const OwnEnv &st = own[i];
+            const float act = actv[i];
             const bool live = run[i] && lane < st.Ke;
             float ac = isfinite(act) ? act : 0.0f;
             ac = fminf(fmaxf(ac, -1.0f), 1.0f);
@@ -804,6 +834,45 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                 vsum[i] = warp_sum_redux(p1[i] * (hcur - nsell[i] + want[i]));
             }
         }
+        // trades: every env's common case (all buys fit) first, then the
+        // greedy partial fills of the envs whose buys do not all fit, then
+        // the state updates
+        int64_t cashv[NOWN], nbv[NOWN], v1v[NOWN];
+        bool greedy[NOWN];
+#pragma unroll
+        for (int i = 0; i < NOWN; ++i) {
+            const int64_t cash1 = own[i].cash + ssum[i];
+            cashv[i] = cash1 - bsum[i];
+            nbv[i] = want[i];
+            v1v[i] = cashv[i] + vsum[i];
+            greedy[i] = run[i] && bsum[i] > cash1;
+        }
+#pragma unroll
+        for (int i = 0; i < NOWN; ++i) {
+            if (!greedy[i]) continue;                  // uniform
+            const OwnEnv &st = own[i];
+            const int64_t cash1 = st.cash + ssum[i];
+            if (NARROW) {
+                // the value without the wanted buys, plus what was filled
+                const bool can = want[i] > 0 && (int64_t)cost_of32(1u, (uint32_t)st.p, fee) <= cash1;
+                if (!__any_sync(FULL_MASK, can)) {     // no order affords one share
+                    cashv[i] = cash1;
+                    nbv[i] = 0;
+                    v1v[i] = cash1 + vsum[i] - wsum[i];
+                } else {
+                    const Fill fl = own_buy_greedy<true>(cash1, want[i], full[i], st.p, fee, lane);
+                    cashv[i] = fl.cash;
+                    nbv[i] = fl.nb;
+                    v1v[i] = fl.cash + vsum[i] - wsum[i] +
+                             (int64_t)__reduce_add_sync(FULL_MASK, (uint32_t)p1[i] * (uint32_t)fl.nb);
+                }
+            } else {
+                const Fill fl = own_buy_greedy<false>(cash1, want[i], full[i], st.p, fee, lane);
+                cashv[i] = fl.cash;
+                nbv[i] = fl.nb;
+                v1v[i] = fl.cash + warp_sum_redux(p1[i] * (st.h - nsell[i] + fl.nb));
+            }
+        }
 #pragma unroll
         for (int i = 0; i < NOWN; ++i) {
             const int e = eidx[i];
@@ -813,35 +882,14 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
             int64_t rew = 0, vlog = VLOG_NONE2;
             bool dn_out = true;
             if (run[i]) {
-                const int64_t cash1 = st.cash + ssum[i];
-                int64_t cash = cash1 - bsum[i];
-                int64_t nb = want[i];
-                int64_t v1 = cash + vsum[i];
-                if (bsum[i] > cash1) {                 // not every buy fits: greedy partial fills
-                    if (NARROW) {
-                        // the value without the wanted buys, plus what was filled
-                        const bool can = want[i] > 0 && (int64_t)cost_of32(1u, (uint32_t)st.p, fee) <= cash1;
-                        if (!__any_sync(FULL_MASK, can)) {     // no order affords one share
-                            cash = cash1;
-                            nb = 0;
-                            v1 = cash1 + vsum[i] - wsum[i];
-                        } else {
-                            cash = own_buy_greedy<true>(cash1, want[i], full[i], st.p, fee, lane, nb);
-                            v1 = cash + vsum[i] - wsum[i] +
-                                 (int64_t)__reduce_add_sync(FULL_MASK, (uint32_t)p1[i] * (uint32_t)nb);
-                        }
-                    } else {
-                        cash = own_buy_greedy<false>(cash1, want[i], full[i], st.p, fee, lane, nb);
-                        v1 = cash + warp_sum_redux(p1[i] * (st.h - nsell[i] + nb));
-                    }
-                }
+                const int64_t v1 = v1v[i];
                 rew = v1 - st.v0;
                 st.t += 1;
                 st.done = st.t == st.W - 1;
                 dn_out = st.done;
                 vlog = st.done ? -v1 - 1 : v1;
-                st.cash = cash;
-                st.h = (int32_t)(st.h - nsell[i] + nb);
+                st.cash = cashv[i];
+                st.h = (int32_t)(st.h - nsell[i] + nbv[i]);
                 st.p = p1[i];
                 st.v0 = v1;
                 if (st.done && v.auto_reset) {
@@ -1064,7 +1112,7 @@ static int f2_build(const fr_ensemble *e, F2Image &im)
             cur_l = 0;
             for (int n = 0; n < p.n1; ++n)
                 for (int k = 0; k < NSTATE; ++k)
-                    put(base, p.l1, n, k, wq(hh * p.n1 + n, W1[(size_t)(hh * p.n1 + n) * SD2 + k]));
+                    put(base, p.l1, n, f2_state_pos(k), wq(hh * p.n1 + n, W1[(size_t)(hh * p.n1 + n) * SD2 + k]));
             cur_l = 1;
             for (int n = 0; n < p.n2; ++n)
                 for (int k = 0; k < p.H1; ++k)
