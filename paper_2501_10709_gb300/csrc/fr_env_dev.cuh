@@ -78,18 +78,19 @@ __device__ __forceinline__ int64_t afford(int64_t c, int64_t p, int fee_bps)
 
 // afford() for an order whose full cost fits 32 bits (EnvView::narrow): the
 // largest n < want with cost_of32(n) <= c, given c below cost_of32(want).
-// cost_of32(n) lies in [n p (1 + fee/1e4), n p (1 + fee/1e4) + 1), so the
-// fp32 quotient c / (p (1 + fee/1e4)) is within one of the answer while it
-// stays below 2^20; the exact 32-bit comparisons then settle it (bounded
-// loops, like afford's).  Every cost compared is at most cost_of32(want).
+// With D = p (1 + fee/1e4), cost_of32(n) lies in [n D, n D + 1) and D >= 1,
+// so the answer is floor(c / D) or one less.  The fp32 quotient q is within
+// 2^-21 relative of c / D, i.e. within one of it below 2^20 (hmax <= 1e6
+// keeps every answer there), so trunc(q) exceeds the answer by -1 to 2: two
+// conditional decrements and one conditional increment, all exact 32-bit
+// comparisons of costs at most cost_of32(want), settle it without branches.
 __device__ __forceinline__ uint32_t afford32(uint32_t c, uint32_t p, int fee_bps, uint32_t want)
 {
     const float q = __fdividef((float)c, __fmul_rn((float)p, __fmaf_rn((float)fee_bps, 1e-4f, 1.0f)));
-    uint32_t n = q > 0.0f ? min((uint32_t)q, want - 1u) : 0u;
-#pragma unroll 1
-    for (int i = 0; i < 8 && n > 0 && cost_of32(n, p, fee_bps) > c; ++i) --n;
-#pragma unroll 1
-    for (int i = 0; i < 8 && n + 1u < want && cost_of32(n + 1u, p, fee_bps) <= c; ++i) ++n;
+    uint32_t n = min((uint32_t)fminf(fmaxf(q, 0.0f), 1048576.0f), want - 1u);
+    n -= (n > 0u && cost_of32(n, p, fee_bps) > c) ? 1u : 0u;
+    n -= (n > 0u && cost_of32(n, p, fee_bps) > c) ? 1u : 0u;
+    n += (n + 1u < want && cost_of32(n + 1u, p, fee_bps) <= c) ? 1u : 0u;
     return n;
 }
 
