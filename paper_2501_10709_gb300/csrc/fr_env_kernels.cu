@@ -129,7 +129,9 @@ __global__ void __launch_bounds__(kStepEnvs * 32, kStepBlocks) k_stock_step(EnvV
             }
             int rank = lane;                     // execution position of this lane's order
             // the one-share cost only matters when not every order fits
-            const int64_t one = pending && want > 0 ? cost_of(1, p, fee) : 0;
+            const int64_t one = pending && want > 0
+                                    ? (NARROW ? (int64_t)cost_of32(1u, (uint32_t)p, fee) : cost_of(1, p, fee))
+                                    : 0;
             int64_t bw = want, bf = full, bo = one, bp = p;
             if (BYSIZE && pending) {
                 // rank: orders with a larger count, or an equal count at a
@@ -159,7 +161,19 @@ __global__ void __launch_bounds__(kStepEnvs * 32, kStepBlocks) k_stock_step(EnvV
                 if (!pending) break;
                 mine = (pending >> lane) & 1u;
                 const int64_t x = mine ? bf : 0;
-                const int64_t pre = warp_incl_scan(x, lane);
+                int64_t pre;
+                if (NARROW) {
+                    // every order's cost and their sum fit 32 bits
+                    uint32_t y = (uint32_t)x;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t z = __shfl_up_sync(FULL_MASK, y, o);
+                        y += lane >= o ? z : 0u;
+                    }
+                    pre = (int64_t)y;
+                } else {
+                    pre = warp_incl_scan(x, lane);
+                }
                 const unsigned fail = __ballot_sync(FULL_MASK, mine && pre > cash);
                 if (fail == 0u) {
                     if (mine) bn = bw;
@@ -170,9 +184,11 @@ __global__ void __launch_bounds__(kStepEnvs * 32, kStepBlocks) k_stock_step(EnvV
                 if (mine && lane < f) bn = bw;
                 int64_t cf = cash - (pre - x);
                 if (lane == f) {
-                    const int64_t n = afford(cf, bp, fee);
+                    // the failing order: cf is below its cost, so (NARROW) below 2^32
+                    const int64_t n = NARROW ? (int64_t)afford32((uint32_t)cf, (uint32_t)bp, fee, (uint32_t)bw)
+                                             : afford(cf, bp, fee);
                     bn = n;
-                    cf -= cost_of(n, bp, fee);
+                    cf -= NARROW ? (int64_t)cost_of32((uint32_t)n, (uint32_t)bp, fee) : cost_of(n, bp, fee);
                 }
                 cash = __shfl_sync(FULL_MASK, cf, f);
                 pending &= ~((2u << f) - 1u);
