@@ -92,9 +92,10 @@ struct F2Args {
     const float *dq, *inv_sx;   // FP8 only
     const float *Z;       // [M][n_ctx][H1]
     const int32_t *slot; // [N] asset-count slot of each env
-    const int32_t *perm; // [tiles*128] env at each tile position (NULL = identity; -1 = empty)
+    const int32_t *perm; // [tiles*tile_rows] env at each tile position (NULL = identity; -1 = empty)
     const int32_t *tile_w; // [tiles] longest window of a tile's envs (NULL = run every tile T steps)
-    int n_pos;            // tile positions holding an env index (N, or tiles*128 with perm)
+    int n_pos;            // tile positions holding an env index (N, or tiles*tile_rows with perm)
+    int tile_rows;        // envs per tile (<= 128; the MMA rows beyond are padding)
     int n_ctx_per_agent;
     float w[MAX_AGENTS];
     int T;
@@ -148,29 +149,33 @@ bool f2_plan(const fr_ensemble *e, F2Plan &p)
 // 31..60 holdings): prices and holdings interleaved by asset, cash last.
 __host__ __device__ inline int f2_state_pos(int k) { return k == 0 ? 2 * SK2 : (k <= SK2 ? 2 * (k - 1) : 2 * (k - 1 - SK2) + 1); }
 
-// Rows of the tile owned by one CTA: row r belongs to rank r mod 2M and sits
-// at index r / 2M of that CTA's owned rows.
+// Rows of a tile owned by one CTA: row r belongs to rank r mod 2M and sits
+// at index r / 2M of that CTA's owned rows.  A tile holds tr <= 128 envs
+// (rows tr..127 of the MMAs are padding that nothing reads back); the
+// owned-row buffers are sized for 128.
 __host__ __device__ inline int f2_owned_rows(int M) { return (128 + 2 * M - 1) / (2 * M); }
+__host__ __device__ inline int f2_rows_of(int tr, int M, int rank) { return rank < tr ? (tr - 1 - rank) / (2 * M) + 1 : 0; }
 
 // Observation bytes a CTA receives per step from the other CTAs: the 64
-// BF16 state entries (128 bytes) and the Z row index (4 bytes) of every row
-// it does not own.
-__host__ __device__ inline uint32_t f2_obs_tx_bytes(int M, int rank, int esz)
+// state entries (BF16: 128 bytes, E4M3: 64) and the Z row index (4 bytes)
+// of every row of the tile it does not own.
+__host__ __device__ inline uint32_t f2_obs_tx_bytes(int M, int rank, int esz, int tr)
 {
-    const int rows = (127 - rank) / (2 * M) + 1;
-    return (uint32_t)(128 - rows) * (uint32_t)(64 * esz + 4);
+    return (uint32_t)(tr - f2_rows_of(tr, M, rank)) * (uint32_t)(64 * esz + 4);
 }
 
-// h1 bytes a CTA receives per step from its partner: 128 rows of the
-// partner's H1 / 2 columns in BF16.
-__host__ __device__ inline uint32_t f2_h1_tx_bytes(const F2Plan &p) { return 128u * (uint32_t)p.n1 * (uint32_t)p.esz; }
+// h1 bytes a CTA receives per step from its partner: the tile's rows of the
+// partner's H1 / 2 columns.
+__host__ __device__ inline uint32_t f2_h1_tx_bytes(const F2Plan &p, int tr)
+{
+    return (uint32_t)tr * (uint32_t)p.n1 * (uint32_t)p.esz;
+}
 
 // Layer-3 partial-sum bytes a CTA receives per step from the other 2M - 1
 // CTAs: 128 bytes for each of its owned rows from each.
-__host__ __device__ inline uint32_t f2_x_tx_bytes(int M, int rank)
+__host__ __device__ inline uint32_t f2_x_tx_bytes(int M, int rank, int tr)
 {
-    const int rows = (127 - rank) / (2 * M) + 1;
-    return (uint32_t)(rows * (2 * M - 1)) * 128u;
+    return (uint32_t)(f2_rows_of(tr, M, rank) * (2 * M - 1)) * 128u;
 }
 
 // shared-memory carve-up
@@ -455,7 +460,7 @@ __device__ __forceinline__ void own_publish_all(const F2Args &a, const OwnEnv *o
     const uint32_t ob = ptx::smem_u32(obs_bar);
 #pragma unroll
     for (int i = 0; i < NOWN; ++i)
-        if (orow[i] < 128) own_store<FP8>(o[i], orow[i], a_obs, ctx_addr, M2, lane, rank, ob);
+        if (orow[i] < a.tile_rows) own_store<FP8>(o[i], orow[i], a_obs, ctx_addr, M2, lane, rank, ob);
     // this CTA's own rows: one local arrival once the warp's plain stores are done
     __syncwarp();
     if (lane == 0) ptx::mbar_arrive(obs_bar);
@@ -494,15 +499,18 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
     const uint32_t row_off = (uint32_t)(r / 8) * 128u + (uint32_t)(r % 8) * 16u;
     const uint32_t xbuf = smem_u32(smem + L.xbuf);
     const int RO = f2_owned_rows(M);
-    const uint32_t x_tx = f2_x_tx_bytes(M, rank);
-    const uint32_t obs_tx = f2_obs_tx_bytes(M, rank, p.esz);
-    const uint32_t h1_tx = f2_h1_tx_bytes(p);
+    const int TR = a.tile_rows;
+    const bool row_live = r < TR;                  // this lane's epilogue row holds an env slot
+    const bool quarter_live = q * 32 < TR;         // uniform: the warp's lane quarter holds any
+    const uint32_t x_tx = f2_x_tx_bytes(M, rank, TR);
+    const uint32_t obs_tx = f2_obs_tx_bytes(M, rank, p.esz, TR);
+    const uint32_t h1_tx = f2_h1_tx_bytes(p, TR);
     const uint32_t h1r_partner = map_shared_rank(smem_u32(&bars[B_H1]), (uint32_t)(rank ^ 1));
     const uint32_t ctx_addr = smem_u32(smem + L.ctx);
     const int32_t *ctxv = (const int32_t *)(smem + L.ctx);
     uint64_t *obs_ready = &bars[B_OBS], *acc = &bars[B_ACC], *h1r = &bars[B_H1], *h2r = &bars[B_H2];
     uint64_t *xrdy = &bars[B_X];
-    const int tile0 = tile * 128;
+    const int tile0 = tile * TR;
     const bool issuer = ew == 0;
     const uint32_t w_base = smem_u32(smem + L.w);
     const uint32_t a_obs = a_base + (uint32_t)(p.H1 / p.ck) * 2048u;
@@ -527,7 +535,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
     for (int i = 0; i < NOWN; ++i) {
         orow[i] = rank + M2 * (ew + F2_ENV_WARPS * i);
         const int pos = tile0 + orow[i];
-        eidx[i] = (orow[i] < 128 && pos < a.n_pos) ? (a.perm ? a.perm[pos] : pos) : -1;
+        eidx[i] = (orow[i] < TR && pos < a.n_pos) ? (a.perm ? a.perm[pos] : pos) : -1;
         const int e = eidx[i];
         OwnEnv &s = own[i];
         s.cash = 0; s.v0 = 0; s.t = 0; s.start = 0; s.W = 2; s.Ke = 0; s.done = 1; s.slot = 0; s.p = 0; s.h = 0;
@@ -601,10 +609,11 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         const float4 *zrow = (const float4 *)(zbase + (size_t)zr * p.H1 + hh * p.n1 + c01);
         float4 zq[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) zq[i] = 4 * i < nc1 ? __ldg(zrow + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int i = 0; i < 16; ++i)
+            zq[i] = (4 * i < nc1 && row_live) ? __ldg(zrow + i) : make_float4(0.f, 0.f, 0.f, 0.f);
         f2_wait(acc, (uint32_t)(3 * s) & 1u, abort, a.err, 16u, false);
         tc_fence_after();
-        {
+        if (quarter_live) {                             // uniform; rows beyond the tile are not sent
             const int nc = nc1;
             const int c0 = c01;
             const uint32_t dst_chunk0 = (uint32_t)((hh * p.n1 + c0) / 8);
@@ -631,8 +640,10 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                     uint32_t w[4];
                     e4m3_pack16(x, inv1, w);
                     const uint32_t at = a_base + (uint32_t)((hh * p.n1 + c0 + cc) / 16) * 2048u + row_off;
-                    st_shared_v4(at, w[0], w[1], w[2], w[3]);
-                    st_async_v4(map_shared_rank(at, (uint32_t)(rank ^ 1)), w[0], w[1], w[2], w[3], h1r_partner);
+                    if (row_live) {
+                        st_shared_v4(at, w[0], w[1], w[2], w[3]);
+                        st_async_v4(map_shared_rank(at, (uint32_t)(rank ^ 1)), w[0], w[1], w[2], w[3], h1r_partner);
+                    }
                 } else {
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
@@ -646,13 +657,15 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                     pack8_bf16(x, w0);
                     pack8_bf16(x + 8, w1);
                     const uint32_t at = a_base + (dst_chunk0 + (uint32_t)(cc / 8)) * 2048u + row_off;
-                    st_shared_v4(at, w0[0], w0[1], w0[2], w0[3]);
-                    st_shared_v4(at + 2048u, w1[0], w1[1], w1[2], w1[3]);
-                    // the partner's copy: asynchronous stores that complete their
-                    // bytes on the partner's h1 barrier
-                    const uint32_t pt = map_shared_rank(at, (uint32_t)(rank ^ 1));
-                    st_async_v4(pt, w0[0], w0[1], w0[2], w0[3], h1r_partner);
-                    st_async_v4(pt + 2048u, w1[0], w1[1], w1[2], w1[3], h1r_partner);
+                    if (row_live) {
+                        st_shared_v4(at, w0[0], w0[1], w0[2], w0[3]);
+                        st_shared_v4(at + 2048u, w1[0], w1[1], w1[2], w1[3]);
+                        // the partner's copy: asynchronous stores that complete
+                        // their bytes on the partner's h1 barrier
+                        const uint32_t pt = map_shared_rank(at, (uint32_t)(rank ^ 1));
+                        st_async_v4(pt, w0[0], w0[1], w0[2], w0[3], h1r_partner);
+                        st_async_v4(pt + 2048u, w1[0], w1[1], w1[2], w1[3], h1r_partner);
+                    }
                 }
             }
         }
@@ -670,8 +683,8 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         tc_fence_after();
         {
             const float *b2 = (const float *)(smem + L.bias);
-            const int nc = p.n2 / 2;
-            const int c0 = col_half * nc;
+            const int nc = quarter_live ? p.n2 / 2 : 0;     // uniform
+            const int c0 = col_half * (p.n2 / 2);
             for (int cc = 0; cc < nc; cc += 16) {
                 uint32_t vv[16];
                 __syncwarp();
@@ -709,7 +722,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         // --------------------------------- E3: partial sums to the owners
         f2_wait(acc, (uint32_t)(3 * s + 2) & 1u, abort, a.err, 16u, false);
         tc_fence_after();
-        if (col_half == 0) {                        // one warp per lane quarter reads the 32 columns
+        if (col_half == 0 && quarter_live) {        // one warp per lane quarter reads the 32 columns
             uint32_t vv[32];
             __syncwarp();
             tmem_ld32(tmem_row + 128u, vv);
@@ -723,7 +736,9 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
             const uint32_t ri = (uint32_t)(r / M2);
             const uint32_t owner = (uint32_t)(r % M2);
             const uint32_t at = xbuf + ((uint32_t)rank * (uint32_t)RO + ri) * 128u;
-            if (owner == (uint32_t)rank) {
+            if (!row_live) {
+                // a padding row: nothing to send
+            } else if (owner == (uint32_t)rank) {
 #pragma unroll
                 for (int k = 0; k < 8; ++k)
                     st_shared_v4(at + 16u * ((uint32_t)k ^ (ri & 7u)), vv[4 * k], vv[4 * k + 1], vv[4 * k + 2],
@@ -736,6 +751,8 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                     st_async_v4(dst + 16u * ((uint32_t)k ^ (ri & 7u)), vv[4 * k], vv[4 * k + 1], vv[4 * k + 2],
                                 vv[4 * k + 3], rbar);
             }
+        }
+        if (col_half == 0) {                        // every E3 warp arrives, sending or not
             __syncwarp();
             if (lane == 0) mbar_arrive(xrdy);
         }
@@ -965,17 +982,17 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_rollout_stock2(const __grid_c
         // this CTA's owner warps (its own rows) plus one arming arrival per
         // phase that expects the other CTAs' rows; phase 0 armed here
         mbar_init(&bars[B_OBS], (uint32_t)F2_ENV_WARPS + 1u);
-        mbar_arrive_expect_tx(&bars[B_OBS], f2_obs_tx_bytes(p.M, rank, p.esz));
+        mbar_arrive_expect_tx(&bars[B_OBS], f2_obs_tx_bytes(p.M, rank, p.esz, a.tile_rows));
         mbar_init(&bars[B_ACC], 1);
         // this CTA's E1 warps plus one arming arrival per phase that expects
         // the partner's half; phase 0 armed here
         mbar_init(&bars[B_H1], (uint32_t)F2_ENV_WARPS + 1u);
-        mbar_arrive_expect_tx(&bars[B_H1], f2_h1_tx_bytes(p));
+        mbar_arrive_expect_tx(&bars[B_H1], f2_h1_tx_bytes(p, a.tile_rows));
         mbar_init(&bars[B_H2], (uint32_t)F2_ENV_WARPS);            // this CTA's E2 warps
         // this CTA's 4 E3 warps, plus one arming arrival per phase that
         // expects the other CTAs' bytes; phase 0 armed here
         mbar_init(&bars[B_X], 5u);
-        mbar_arrive_expect_tx(&bars[B_X], f2_x_tx_bytes(p.M, rank));
+        mbar_arrive_expect_tx(&bars[B_X], f2_x_tx_bytes(p.M, rank, a.tile_rows));
         mbar_init(&bars[B_END], 1);                                // the issuer's last commit
         *abort = 0;
         fence_mbar_init();
@@ -1007,9 +1024,11 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_rollout_stock2(const __grid_c
     const uint32_t tmem = *tmem_slot;
 
     {
-        // owned envs per env warp: ceil(128 / (2M * 8)) = 4, 3, 2 for M = 2..4
-        switch (p.M) {
-        case 2: f2_env_loop<4, NARROW, FP8>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
+        // owned envs per env warp: ceil(ceil(tile_rows / 2M) / 8), at least 2
+        // (at 128 rows: 4, 3, 2 for M = 2..4)
+        const int per_warp = (f2_rows_of(a.tile_rows, p.M, 0) + F2_ENV_WARPS - 1) / F2_ENV_WARPS;
+        switch (per_warp) {
+        case 4: f2_env_loop<4, NARROW, FP8>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
         case 3: f2_env_loop<3, NARROW, FP8>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
         default: f2_env_loop<2, NARROW, FP8>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
         }
@@ -1177,6 +1196,36 @@ bool f2_supported(const fr_env *env, const fr_ensemble *e)
     return f2_smem(p).total + 1024u <= (uint32_t)optin;
 }
 
+// Clusters of a launch configuration the GPU holds at once, cached per
+// kernel, cluster size and device (a host query, made at the first rollout
+// of a shape; later calls, graph captures included, read the cache).
+struct F2Occ {
+    const void *kern;
+    unsigned cluster;
+    int device, n;
+};
+static std::vector<F2Occ> g_f2_occ;
+static std::mutex g_f2_occ_mu;
+
+static cudaError_t f2_max_clusters(const void *kern, const cudaLaunchConfig_t &cfg, int device, int *n)
+{
+    std::lock_guard<std::mutex> lk(g_f2_occ_mu);
+    const unsigned cl = cfg.attrs[0].val.clusterDim.x;
+    for (const F2Occ &o : g_f2_occ)
+        if (o.kern == kern && o.cluster == cl && o.device == device) {
+            *n = o.n;
+            return cudaSuccess;
+        }
+    cudaLaunchConfig_t c = cfg;
+    c.gridDim = dim3(cl, 1, 1);
+    int k = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&k, kern, &c);
+    if (e != cudaSuccess) return e;
+    g_f2_occ.push_back(F2Occ{kern, cl, device, k});
+    *n = k;
+    return cudaSuccess;
+}
+
 // images are cached per ensemble (keyed by handle); released with the ensemble
 struct F2Entry {
     const fr_ensemble *ens;
@@ -1335,11 +1384,39 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     }
     const bool packed = may_pack && env->pack_state == 2;
 
+    void (*kern)(F2Args) = v.narrow ? (p.fp8 ? k_rollout_stock2<true, true> : k_rollout_stock2<true, false>)
+                                    : (p.fp8 ? k_rollout_stock2<false, true> : k_rollout_stock2<false, false>);
+    FR_CUDA(set_max_smem_once((const void *)kern, env->ctx->device));
+    const uint32_t smem = f2_smem(p).total + 1024u;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(F2_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)(2 * p.M);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // Envs per tile: 128 when the tiles fill the clusters the GPU holds at
+    // once (or are packed by window); otherwise the envs are spread evenly
+    // over that many clusters (at least 64 per tile), so that a batch of a
+    // few thousand envs uses every SM it can: each step's owner work and
+    // exchanges shrink with the rows, its MMAs (128 rows) do not.
+    int TR = 128;
+    if (!packed) {
+        int nc = 0;
+        FR_CUDA(f2_max_clusters((const void *)kern, cfg, env->ctx->device, &nc));
+        if (nc > 0) TR = (int)std::min<int64_t>(128, std::max<int64_t>(64, ceil_div(v.N, nc)));
+    }
+
     F2Args a;
     memset(&a, 0, sizeof(a));
     a.perm = packed ? env->pack_perm : nullptr;
     a.tile_w = packed ? env->pack_tile_w : nullptr;
     a.n_pos = packed ? tiles * 128 : v.N;
+    a.tile_rows = TR;
     a.v = v;
     a.plan = p;
     a.img = im->img;
@@ -1361,22 +1438,7 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     a.vlog = vlog;
     a.err = e->tc->err;
     a.ex = explore_of(env, env->explore_step);
-    const uint32_t smem = f2_smem(p).total + 1024u;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(2 * p.M), ceil_div(v.N, 128), 1);
-    cfg.blockDim = dim3(F2_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)(2 * p.M);
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    void (*kern)(F2Args) = v.narrow ? (p.fp8 ? k_rollout_stock2<true, true> : k_rollout_stock2<true, false>)
-                                    : (p.fp8 ? k_rollout_stock2<false, true> : k_rollout_stock2<false, false>);
-    FR_CUDA(set_max_smem_once((const void *)kern, env->ctx->device));
+    cfg.gridDim = dim3((unsigned)(2 * p.M), (unsigned)ceil_div(v.N, TR), 1);
     FR_CUDA(env_time_mark(env, 0, s));
     FR_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
     FR_CUDA(env_time_mark(env, 1, s));
