@@ -685,6 +685,7 @@ def run_gpu(args):
         k_times.append(fr.env_last_kernel_ms(env) / 1e3)
     fr.env_set_kernel_timing(env, False)
     k_dt = statistics.mean(k_times)
+    k_ctas, k_tile = fr.env_last_launch_shape(env)
     achieved = N * T * flops_env_step / k_dt / 1e12
     peak = peaks["bf16_tflops"]
     # the standalone actor kernel on one step's batch, and at a batch that
@@ -787,7 +788,7 @@ def run_gpu(args):
                      "tensor_executed_flops_per_launch": N * T * flops_exec,
                      "tensor_executed_frac_of_algorithmic": flops_exec / flops_env_step,
                      "peak_source": f"bf16_tflops burst, {peak_src}",
-                     "active_sms": 2 * M * ((N + 127) // 128),
+                     "active_sms": k_ctas, "envs_per_cluster_tile": k_tile,
                      "actor_kernel": {"rows": N, "tflops": flops_per_launch / a_dt / 1e12,
                                       "us_per_launch": a_dt * 1e6},
                      "actor_kernel_large_batch": {"rows": nb, "achieved": big_tflops,

@@ -564,6 +564,14 @@ int env_tune_clear(fr_env *env);
 int env_set_kernel_timing(fr_env *env, int32_t on);
 int env_last_kernel_ms(fr_env *env, float *ms);
 
+/* Launch shape of the last resident-weight fused stock rollout of this env
+ * (no counterpart in the paper; for roofline accounting): *ctas = thread
+ * blocks launched (clusters of 2M, one per SM), *tile_envs = envs per
+ * cluster tile (64..128: a batch that does not fill the clusters the GPU
+ * holds at once is spread over all of them).  FR_EINVAL before the first
+ * such launch or on a NULL argument. */
+int env_last_launch_shape(fr_env *env, int32_t *ctas, int32_t *tile_envs);
+
 /* ---------------------------------------------------------- replay buffer */
 typedef struct fr_replay fr_replay;
 

@@ -22,7 +22,7 @@ __all__ = [
     "fr_ctx_create", "fr_market_create", "env_create", "env_reset", "env_step",
     "env_observe", "env_get_state", "env_metrics", "env_snapshot", "env_restore",
     "env_error_count", "env_dims", "ensemble_create", "ensemble_forward",
-    "ensemble_act", "ensemble_act_noalloc", "ensemble_device_errors", "rollout", "env_set_rollout_path", "env_set_kernel_timing", "env_last_kernel_ms", "env_set_tile_packing", "env_set_table_cache",
+    "ensemble_act", "ensemble_act_noalloc", "ensemble_device_errors", "rollout", "env_set_rollout_path", "env_set_kernel_timing", "env_last_kernel_ms", "env_last_launch_shape", "env_set_tile_packing", "env_set_table_cache",
     "env_tile_packing_efficiency", "ensemble_set_weights", "ensemble_validate", "trajectory_metrics", "env_set_exploration",
     "EXPLORE_NONE", "EXPLORE_GAUSSIAN", "EXPLORE_EPS_GREEDY", "Server", "fr_server_create", "backtest_submit",
     "backtest_poll", "backtest_cancel", "fr_server_stats", "fr_server_add_pool", "backtest_fetch_traj",
@@ -292,6 +292,13 @@ def env_last_kernel_ms(env: Env) -> float:
     ms = C.c_float()
     _lib.check(lib().env_last_kernel_ms(env, C.byref(ms)), "env_last_kernel_ms")
     return ms.value
+
+
+def env_last_launch_shape(env: Env) -> tuple:
+    """(thread blocks, envs per tile) of the env's last fused stock rollout."""
+    ctas, tile = C.c_int32(), C.c_int32()
+    _lib.check(lib().env_last_launch_shape(env, C.byref(ctas), C.byref(tile)), "env_last_launch_shape")
+    return ctas.value, tile.value
 
 
 def env_error_count(env: Env) -> int:

@@ -125,6 +125,7 @@ SIGNATURES = {
     "ensemble_act_noalloc": (i32, [vp, vp, i32, vp, vp]),
     "env_set_kernel_timing": (i32, [vp, i32]),
     "env_last_kernel_ms": (i32, [vp, vp]),
+    "env_last_launch_shape": (i32, [vp, vp, vp]),
     "env_set_exploration": (i32, [vp, vp]),
     "trajectory_metrics": (i32, [vp, vp, i32, i32, i64, f64, f64, vp, vp]),
     "ensemble_set_weights": (i32, [vp, vp]),

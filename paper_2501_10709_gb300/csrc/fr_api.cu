@@ -708,6 +708,16 @@ int env_set_kernel_timing(fr_env *env, int32_t on)
     return FR_OK;
 }
 
+int env_last_launch_shape(fr_env *env, int32_t *ctas, int32_t *tile_envs)
+{
+    FR_NVTX("env_last_launch_shape");
+    FR_CHECK(env && ctas && tile_envs, FR_EINVAL, "env_last_launch_shape: NULL argument");
+    FR_CHECK(env->last_ctas > 0, FR_EINVAL, "env_last_launch_shape: no fused stock rollout launched yet");
+    *ctas = env->last_ctas;
+    *tile_envs = env->last_tile;
+    return FR_OK;
+}
+
 int env_last_kernel_ms(fr_env *env, float *ms)
 {
     FR_NVTX("env_last_kernel_ms");

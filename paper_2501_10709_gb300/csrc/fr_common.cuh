@@ -170,6 +170,7 @@ struct fr_env {
     cudaEvent_t k_ev[2];
     int k_timing;               // record on the next rollouts
     int k_recorded;             // a pair has been recorded
+    int last_ctas, last_tile;   // launch shape of the last fused stock rollout (0: none yet)
 };
 
 namespace fr {

@@ -1439,6 +1439,8 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     a.err = e->tc->err;
     a.ex = explore_of(env, env->explore_step);
     cfg.gridDim = dim3((unsigned)(2 * p.M), (unsigned)ceil_div(v.N, TR), 1);
+    env->last_ctas = (int)(cfg.gridDim.x * cfg.gridDim.y);
+    env->last_tile = TR;
     FR_CUDA(env_time_mark(env, 0, s));
     FR_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
     FR_CUDA(env_time_mark(env, 1, s));

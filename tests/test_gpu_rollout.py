@@ -205,9 +205,14 @@ def test_kernel_timing_hook(ctx, dev):
     fr.env_set_kernel_timing(env, True)
     with pytest.raises(fr.FrError):
         fr.env_last_kernel_ms(env)
+    with pytest.raises(fr.FrError):
+        fr.env_last_launch_shape(env)              # no fused launch yet
     fr.rollout(env, ens, 8)
     ms = fr.env_last_kernel_ms(env)
     assert 0.0 < ms < 1e3
+    # 256 envs do not fill the co-resident clusters: tiles of the 64-env minimum
+    ctas, tile = fr.env_last_launch_shape(env)
+    assert tile == 64 and ctas == 6 * 4
     fr.env_set_kernel_timing(env, False)
     with pytest.raises(fr.FrError):
         fr.env_last_kernel_ms(env)
