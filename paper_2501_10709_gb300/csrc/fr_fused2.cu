@@ -43,8 +43,11 @@ namespace fr {
 
 namespace {
 
-constexpr int F2_THREADS = 256;           // 8 env / epilogue warps; warp 0 also loads and issues
-constexpr int F2_ENV_WARPS = 8;
+// Warps per CTA: 8, or 16 when both hidden widths are multiples of 128 (each
+// warp then takes a quarter of its lane quarter's columns, and one or two
+// owned envs).  Every warp is an env / epilogue warp; warp 0 also loads the
+// weights and issues the MMAs.  16 warps halve each warp's epilogue and owner
+// work at 128 registers per thread (8 warps: up to 255).
 constexpr int SK2 = 30, SI2 = 8;
 constexpr int SD2 = 1 + 2 * SK2 + SI2 * SK2;   // 301
 constexpr int NSTATE = 1 + 2 * SK2;            // 61 trajectory-dependent entries
@@ -478,10 +481,12 @@ __device__ __forceinline__ void own_publish_all(const F2Args &a, const OwnEnv *o
 // NARROW: the env's prices, orders and a step's sells and buys fit 32 bits
 // (EnvView::narrow, proved by env_create): the accounting runs in 32-bit
 // arithmetic, with the same results.
-template <int NOWN, bool NARROW, bool FP8>
+template <int NOWN, bool NARROW, bool FP8, int W>
 __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, const F2Smem L_in, uint64_t *bars,
                             volatile int *abort, int warp, int lane, int rank, int tile)
 {
+    constexpr int PARTS = W / 4;                   // warps sharing a TMEM lane quarter
+    constexpr int ZQ = 128 / W;                    // float4 Z values per lane (the warp's columns / 4)
     using namespace ptx;
     const F2Args a = a_in;
     const F2Smem L = L_in;
@@ -492,7 +497,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
     const int j = rank >> 1, hh = rank & 1;
     const int ew = warp;                           // 0..7
     const int q = warp & 3;                        // TMEM lane quarter
-    const int col_half = ew >> 2;                  // 0 or 1: which half of the columns this warp reads
+    const int col_half = ew >> 2;                  // 0 .. PARTS - 1: which part of the columns this warp reads
     const int r = q * 32 + lane;                   // epilogue row
     const uint32_t tmem_row = tmem + ((uint32_t)(q * 32) << 16);
     const uint32_t a_base = smem_u32(smem + L.a);
@@ -533,7 +538,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
     int orow[NOWN], eidx[NOWN];                    // tile row; env index (-1: no env there)
 #pragma unroll
     for (int i = 0; i < NOWN; ++i) {
-        orow[i] = rank + M2 * (ew + F2_ENV_WARPS * i);
+        orow[i] = rank + M2 * (ew + W * i);
         const int pos = tile0 + orow[i];
         eidx[i] = (orow[i] < TR && pos < a.n_pos) ? (a.perm ? a.perm[pos] : pos) : -1;
         const int e = eidx[i];
@@ -601,15 +606,15 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         // bytes of the other CTAs' rows are expected
         if (issuer && lane == 0 && !*abort) mbar_arrive_expect_tx(obs_ready, obs_tx);
         if (issuer && lane == 0) f2_layer<FP8>(p.l1.K, p.l1.N, p.l1.off, tmem, a_obs, w_base, acc);
-        const int nc1 = p.n1 / 2;                          // columns per warp (<= 64)
+        const int nc1 = p.n1 / PARTS;                      // columns per warp (<= 64 / 32)
         const int c01 = col_half * nc1;
         // all of this warp's Z loads in flight at once, one L2 latency
         // clamped: after an aborted wait the row index may be stale
         const int zr = min(max(ctxv[r], 0), a.n_ctx_per_agent - 1);
         const float4 *zrow = (const float4 *)(zbase + (size_t)zr * p.H1 + hh * p.n1 + c01);
-        float4 zq[16];
+        float4 zq[ZQ];
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
+        for (int i = 0; i < ZQ; ++i)
             zq[i] = (4 * i < nc1 && row_live) ? __ldg(zrow + i) : make_float4(0.f, 0.f, 0.f, 0.f);
         f2_wait(acc, (uint32_t)(3 * s) & 1u, abort, a.err, 16u, false);
         tc_fence_after();
@@ -618,7 +623,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
             const int c0 = c01;
             const uint32_t dst_chunk0 = (uint32_t)((hh * p.n1 + c0) / 8);
 #pragma unroll
-            for (int q4 = 0; q4 < 4; ++q4) {
+            for (int q4 = 0; q4 < ZQ / 4; ++q4) {
                 const int cc = 16 * q4;
                 if (cc >= nc) continue;
                 uint32_t vv[16];
@@ -683,8 +688,8 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         tc_fence_after();
         {
             const float *b2 = (const float *)(smem + L.bias);
-            const int nc = quarter_live ? p.n2 / 2 : 0;     // uniform
-            const int c0 = col_half * (p.n2 / 2);
+            const int nc = quarter_live ? p.n2 / PARTS : 0;     // uniform
+            const int c0 = col_half * (p.n2 / PARTS);
             for (int cc = 0; cc < nc; cc += 16) {
                 uint32_t vv[16];
                 __syncwarp();
@@ -962,8 +967,8 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
     }
 }
 
-template <bool NARROW, bool FP8>
-__global__ void __launch_bounds__(F2_THREADS, 1) k_rollout_stock2(const __grid_constant__ F2Args a)
+template <bool NARROW, bool FP8, int W>
+__global__ void __launch_bounds__(32 * W, 1) k_rollout_stock2(const __grid_constant__ F2Args a)
 {
     using namespace ptx;
     extern __shared__ uint8_t smem_raw[];
@@ -981,14 +986,14 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_rollout_stock2(const __grid_c
         mbar_init(&bars[B_W], 1);
         // this CTA's owner warps (its own rows) plus one arming arrival per
         // phase that expects the other CTAs' rows; phase 0 armed here
-        mbar_init(&bars[B_OBS], (uint32_t)F2_ENV_WARPS + 1u);
+        mbar_init(&bars[B_OBS], (uint32_t)W + 1u);
         mbar_arrive_expect_tx(&bars[B_OBS], f2_obs_tx_bytes(p.M, rank, p.esz, a.tile_rows));
         mbar_init(&bars[B_ACC], 1);
         // this CTA's E1 warps plus one arming arrival per phase that expects
         // the partner's half; phase 0 armed here
-        mbar_init(&bars[B_H1], (uint32_t)F2_ENV_WARPS + 1u);
+        mbar_init(&bars[B_H1], (uint32_t)W + 1u);
         mbar_arrive_expect_tx(&bars[B_H1], f2_h1_tx_bytes(p, a.tile_rows));
-        mbar_init(&bars[B_H2], (uint32_t)F2_ENV_WARPS);            // this CTA's E2 warps
+        mbar_init(&bars[B_H2], (uint32_t)W);                       // this CTA's E2 warps
         // this CTA's 4 E3 warps, plus one arming arrival per phase that
         // expects the other CTAs' bytes; phase 0 armed here
         mbar_init(&bars[B_X], 5u);
@@ -1026,11 +1031,17 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_rollout_stock2(const __grid_c
     {
         // owned envs per env warp: ceil(ceil(tile_rows / 2M) / 8), at least 2
         // (at 128 rows: 4, 3, 2 for M = 2..4)
-        const int per_warp = (f2_rows_of(a.tile_rows, p.M, 0) + F2_ENV_WARPS - 1) / F2_ENV_WARPS;
-        switch (per_warp) {
-        case 4: f2_env_loop<4, NARROW, FP8>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
-        case 3: f2_env_loop<3, NARROW, FP8>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
-        default: f2_env_loop<2, NARROW, FP8>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
+        const int per_warp = (f2_rows_of(a.tile_rows, p.M, 0) + W - 1) / W;
+        if (W == 16) {
+            // 16 warps: at most ceil(ceil(128 / 4) / 16) = 2 envs per warp
+            if (per_warp <= 1) f2_env_loop<1, NARROW, FP8, W>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile);
+            else f2_env_loop<2, NARROW, FP8, W>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile);
+        } else {
+            switch (per_warp) {
+            case 4: f2_env_loop<4, NARROW, FP8, W>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
+            case 3: f2_env_loop<3, NARROW, FP8, W>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
+            default: f2_env_loop<2, NARROW, FP8, W>(a, tmem, smem, L, bars, abort, warp, lane, rank, tile); break;
+            }
         }
     }
     __syncwarp();
@@ -1384,12 +1395,20 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     }
     const bool packed = may_pack && env->pack_state == 2;
 
-    void (*kern)(F2Args) = v.narrow ? (p.fp8 ? k_rollout_stock2<true, true> : k_rollout_stock2<true, false>)
-                                    : (p.fp8 ? k_rollout_stock2<false, true> : k_rollout_stock2<false, false>);
+    // 16 warps when every warp's share of a hidden layer is whole 16-column
+    // groups (H1, H2 multiples of 128), else 8
+    const int W = (p.H1 % 128 == 0 && p.H2 % 128 == 0) ? 16 : 8;
+    void (*kern)(F2Args);
+    if (W == 16)
+        kern = v.narrow ? (p.fp8 ? k_rollout_stock2<true, true, 16> : k_rollout_stock2<true, false, 16>)
+                        : (p.fp8 ? k_rollout_stock2<false, true, 16> : k_rollout_stock2<false, false, 16>);
+    else
+        kern = v.narrow ? (p.fp8 ? k_rollout_stock2<true, true, 8> : k_rollout_stock2<true, false, 8>)
+                        : (p.fp8 ? k_rollout_stock2<false, true, 8> : k_rollout_stock2<false, false, 8>);
     FR_CUDA(set_max_smem_once((const void *)kern, env->ctx->device));
     const uint32_t smem = f2_smem(p).total + 1024u;
     cudaLaunchConfig_t cfg = {};
-    cfg.blockDim = dim3(F2_THREADS, 1, 1);
+    cfg.blockDim = dim3((unsigned)(32 * W), 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
