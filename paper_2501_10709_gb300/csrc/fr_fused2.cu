@@ -727,10 +727,16 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         // --------------------------------- E3: partial sums to the owners
         f2_wait(acc, (uint32_t)(3 * s + 2) & 1u, abort, a.err, 16u, false);
         tc_fence_after();
-        if (col_half == 0 && quarter_live) {        // one warp per lane quarter reads the 32 columns
-            uint32_t vv[32];
+        if (quarter_live) {
+            // every warp of the lane quarter reads its part of the 32 columns
+            // (EC = 32 / PARTS of them, EC / 4 16-byte groups)
+            constexpr int EC = 32 / PARTS;
+            uint32_t vv[EC];
             __syncwarp();
-            tmem_ld32(tmem_row + 128u, vv);
+            if constexpr (EC == 8)
+                tmem_ld8(tmem_row + 128u + (uint32_t)(EC * col_half), vv);
+            else
+                tmem_ld16(tmem_row + 128u + (uint32_t)(EC * col_half), vv);
             tmem_ld_wait();
             // row r's partial sums to block `rank` of its owner's buffer, at
             // owned row r / 2M; column group k stored at group k ^ (row & 7),
@@ -741,26 +747,25 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
             const uint32_t ri = (uint32_t)(r / M2);
             const uint32_t owner = (uint32_t)(r % M2);
             const uint32_t at = xbuf + ((uint32_t)rank * (uint32_t)RO + ri) * 128u;
+            const uint32_t k0 = (uint32_t)(EC / 4 * col_half);
             if (!row_live) {
                 // a padding row: nothing to send
             } else if (owner == (uint32_t)rank) {
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    st_shared_v4(at + 16u * ((uint32_t)k ^ (ri & 7u)), vv[4 * k], vv[4 * k + 1], vv[4 * k + 2],
-                                 vv[4 * k + 3]);
+                for (int k = 0; k < EC / 4; ++k)
+                    st_shared_v4(at + 16u * ((k0 + (uint32_t)k) ^ (ri & 7u)), vv[4 * k], vv[4 * k + 1],
+                                 vv[4 * k + 2], vv[4 * k + 3]);
             } else {
                 const uint32_t dst = map_shared_rank(at, owner);
                 const uint32_t rbar = map_shared_rank(smem_u32(xrdy), owner);
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    st_async_v4(dst + 16u * ((uint32_t)k ^ (ri & 7u)), vv[4 * k], vv[4 * k + 1], vv[4 * k + 2],
-                                vv[4 * k + 3], rbar);
+                for (int k = 0; k < EC / 4; ++k)
+                    st_async_v4(dst + 16u * ((k0 + (uint32_t)k) ^ (ri & 7u)), vv[4 * k], vv[4 * k + 1],
+                                vv[4 * k + 2], vv[4 * k + 3], rbar);
             }
         }
-        if (col_half == 0) {                        // every E3 warp arrives, sending or not
-            __syncwarp();
-            if (lane == 0) mbar_arrive(xrdy);
-        }
+        __syncwarp();                               // every warp arrives, sending or not
+        if (lane == 0) mbar_arrive(xrdy);
         tc_fence_before();
         // --------------------------------------------- owners: trade, publish
         // The owned envs are processed in lockstep, so that their reductions
@@ -994,9 +999,9 @@ __global__ void __launch_bounds__(32 * W, 1) k_rollout_stock2(const __grid_const
         mbar_init(&bars[B_H1], (uint32_t)W + 1u);
         mbar_arrive_expect_tx(&bars[B_H1], f2_h1_tx_bytes(p, a.tile_rows));
         mbar_init(&bars[B_H2], (uint32_t)W);                       // this CTA's E2 warps
-        // this CTA's 4 E3 warps, plus one arming arrival per phase that
+        // this CTA's W E3 warps, plus one arming arrival per phase that
         // expects the other CTAs' bytes; phase 0 armed here
-        mbar_init(&bars[B_X], 5u);
+        mbar_init(&bars[B_X], (uint32_t)W + 1u);
         mbar_arrive_expect_tx(&bars[B_X], f2_x_tx_bytes(p.M, rank, a.tile_rows));
         mbar_init(&bars[B_END], 1);                                // the issuer's last commit
         *abort = 0;
