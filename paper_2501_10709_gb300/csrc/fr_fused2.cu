@@ -1,7 +1,8 @@
 // fr_fused2.cu -- fused stock rollout with resident weights.
 //
-// One thread-block cluster of 2M CTAs owns a tile of 128 envs for all T
-// steps.  CTA (j, h) -- cluster rank 2j + h -- holds output half h of every
+// One thread-block cluster of 2M CTAs owns a tile of up to 128 envs for all
+// T steps (a batch too small to fill the co-resident clusters is spread over
+// all of them, at least 64 envs per tile).  CTA (j, h) -- cluster rank 2j + h -- holds output half h of every
 // hidden layer of agent j, so each agent's BF16 weights stay resident in
 // shared memory, split over a CTA pair, and are never re-read per step:
 //
@@ -18,8 +19,9 @@
 //            and applies tanh (one exchange instead of a partner exchange
 //            followed by a push of the finished actions).
 //
-// Env r of the tile is owned by the CTA of rank r mod 2M: one warp per env,
-// lane = asset, state in registers.  The owner combines the agents' actions
+// Env r of the tile is owned by the CTA of rank r mod 2M: one warp per env
+// (8 or 16 warps per CTA, one to four envs each), lane = asset, state in
+// registers.  The owner combines the agents' actions
 // (anchored weighted mean, Sec. 5.2.1), discretises, trades, and writes the
 // env's next observation row straight into every CTA's A operand.  The
 // step's three cluster exchanges (observation rows, h1 halves, layer-3
@@ -616,6 +618,16 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
 #pragma unroll
         for (int i = 0; i < ZQ; ++i)
             zq[i] = (4 * i < nc1 && row_live) ? __ldg(zrow + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        // The next step's row is the next day's (ctx + 1) for every env that
+        // keeps stepping: start pulling it into L1 now, a whole step ahead of
+        // its loads (a hint only: a reset env reads its own row, a miss costs
+        // what a load costs without it).  One 128-byte line per 32 floats.
+        if (row_live && zr + 1 < a.n_ctx_per_agent) {
+            const float *znext = zbase + (size_t)(zr + 1) * p.H1 + hh * p.n1 + c01;
+#pragma unroll
+            for (int i = 0; i < ZQ; i += 8)
+                if (4 * i < nc1) asm volatile("prefetch.global.L1 [%0];" ::"l"(znext + 4 * i));
+        }
         f2_wait(acc, (uint32_t)(3 * s) & 1u, abort, a.err, 16u, false);
         tc_fence_after();
         if (quarter_live) {                             // uniform; rows beyond the tile are not sent

@@ -57,6 +57,17 @@ def _stock_rollout_check(ctx, dev, w, precision, T, sample_rows=256):
     return g
 
 
+@pytest.mark.parametrize("dims", [(301, 192, 128, 30), (301, 128, 64, 30)])
+def test_fused_stock_rollout_8_warp_shapes_teacher_forced(ctx, dev, dims):
+    # hidden widths that are not both multiples of 128 run the resident
+    # kernel's 8-warp form (the metric shape runs 16 warps); 1,024 envs span
+    # several clusters and a ragged last tile
+    from dataclasses import replace
+    w = synth.workload_stock_2048(N=1000, T=20)
+    w = replace(w, dims=dims, params=synth.actor_params(dims, 3, seed=71))
+    _stock_rollout_check(ctx, dev, w, fr.PREC_BF16, 20)
+
+
 @pytest.mark.parametrize("precision", [fr.PREC_FP32, fr.PREC_BF16, fr.PREC_FP16])
 def test_stock_rollout_small_teacher_forced(ctx, dev, precision):
     w = synth.workload_stock_small()
