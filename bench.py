@@ -755,9 +755,9 @@ def run_gpu(args):
             e2e_times.append(time.perf_counter() - t0)
     e2e_value = world * env_steps / statistics.mean(e2e_times)
 
-    # env_reset, the indicator table (rows, then the dense fp32 layer part),
-    # the fused rollout kernel, the metrics replay
-    launches_per_rollout = 5
+    # env_reset, the indicator table, the fused rollout kernel, the metrics
+    # replay
+    launches_per_rollout = 4
     line = {
         "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
