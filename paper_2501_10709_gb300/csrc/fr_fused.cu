@@ -862,7 +862,8 @@ __global__ void k_metrics_replay(EnvView v, const int64_t *vlog, int T, double *
 
 // The same replay without auto-reset (one episode per env, no restarts in
 // the log), with the work off the serial chain done in parallel.  A block
-// takes 16 envs and walks the log in segments of 256 steps:
+// takes 16 envs and walks the log in segments of 64 steps, the two phases
+// pipelined (phase 1 of segment k + 1 runs while phase 2 runs on segment k):
 //  * phase 1, warp-wide: warp w handles envs 2w and 2w + 1, 32 steps per
 //    instruction: each valid step's return v1 / v0 - 1 (v0 the previous
 //    valid step's value, carried across chunks), the running peak (a prefix
@@ -873,97 +874,108 @@ __global__ void k_metrics_replay(EnvView v, const int64_t *vlog, int T, double *
 //    order -- one division per step on the dependent chain instead of three.
 // Every value is computed by the same operations as acc_push, so the result
 // equals the one-thread-per-env replay bit for bit.
-constexpr int RP_ENVS = 16, RP_SEG = 256;
+constexpr int RP_ENVS = 16, RP_SEG = 64, RP_PROD = 8, RP_THREADS = 32 * (RP_PROD + 1);
 
-__global__ void __launch_bounds__(256) k_metrics_replay2(EnvView v, const int64_t *vlog, int T, double *metrics)
+__global__ void __launch_bounds__(RP_THREADS) k_metrics_replay2(EnvView v, const int64_t *vlog, int T, double *metrics)
 {
-    __shared__ double rho_s[RP_ENVS][RP_SEG + 1];
-    __shared__ unsigned valid_s[RP_ENVS][RP_SEG / 32];
+    // two segment buffers: warps 0..7 fill one (phase 1) while warp 8's
+    // lanes run the Welford chains over the other (phase 2); named barriers
+    // 1 + b (segment in buffer b ready) and 3 + b (buffer b read)
+    __shared__ double rho_s[2][RP_ENVS][RP_SEG + 1];
+    __shared__ unsigned valid_s[2][RP_ENVS][RP_SEG / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int e_base = blockIdx.x * RP_ENVS;
+    const int nseg = (T + RP_SEG - 1) / RP_SEG;
+    // phase-2 chain state (warp RP_PROD, lanes 0..15, one env each)
+    const int ce = e_base + lane;
+    const bool chain = warp == RP_PROD && lane < RP_ENVS && ce < v.N;
+    double mu = chain ? v.mu[ce] : 0.0, m2 = chain ? v.m2[ce] : 0.0;
+    int n = chain ? v.t[ce] : 0;
     // phase-1 carries of this warp's two envs
     int64_t vlast_c[2], peak_c[2];
     double mdd_c[2];
     int n_c[2];
-    for (int q = 0; q < 2; ++q) {
-        const int e = e_base + 2 * warp + q;
-        const bool in = e < v.N;
-        vlast_c[q] = in ? v.vlast[e] : 1;
-        peak_c[q] = in ? v.peak[e] : 1;
-        mdd_c[q] = in ? v.mdd[e] : 0.0;
-        n_c[q] = in ? v.t[e] : 0;
-    }
-    // phase-2 chain state (threads 0..15, one env each)
-    const int ce = e_base + threadIdx.x;
-    const bool chain = threadIdx.x < RP_ENVS && ce < v.N;
-    double mu = chain ? v.mu[ce] : 0.0, m2 = chain ? v.m2[ce] : 0.0;
-    int n = chain ? v.t[ce] : 0;
-    for (int seg = 0; seg < T; seg += RP_SEG) {
-        const int len = min(RP_SEG, T - seg);
+    if (warp < RP_PROD) {
         for (int q = 0; q < 2; ++q) {
-            const int el = 2 * warp + q, e = e_base + el;
-            if (e >= v.N) continue;                                   // warp-uniform
-            for (int c = 0; c < len; c += 32) {
-                const int t = seg + c + lane;
-                const int64_t x = c + lane < len ? vlog[(int64_t)t * v.N + e] : VLOG_NONE;
-                const bool valid = x != VLOG_NONE;
-                const int64_t v1 = x < 0 ? -x - 1 : x;
-                const unsigned vm = __ballot_sync(FULL_MASK, valid);
-                if (lane == 0) valid_s[el][c / 32] = vm;
-                if (vm == 0u) continue;
-                const unsigned below = vm & ((1u << lane) - 1u);
-                const int pl = below ? 31 - __clz(below) : 0;
-                const int64_t prev = __shfl_sync(FULL_MASK, v1, pl);
-                const int64_t v0 = below ? prev : vlast_c[q];
-                double r = 0.0;
-                if (valid) r = __dsub_rn(__ddiv_rn((double)v1, (double)v0), 1.0);
-                rho_s[el][c + lane] = r;
-                int64_t pk = valid ? v1 : INT64_MIN;
+            const int e = e_base + 2 * warp + q;
+            const bool in = e < v.N;
+            vlast_c[q] = in ? v.vlast[e] : 1;
+            peak_c[q] = in ? v.peak[e] : 1;
+            mdd_c[q] = in ? v.mdd[e] : 0.0;
+            n_c[q] = in ? v.t[e] : 0;
+        }
+        for (int k = 0; k < nseg; ++k) {
+            const int b = k & 1, seg = k * RP_SEG, len = min(RP_SEG, T - seg);
+            if (k >= 2) ptx::named_bar_sync(3u + (uint32_t)b, RP_THREADS);     // the chains are done with it
+            for (int q = 0; q < 2; ++q) {
+                const int el = 2 * warp + q, e = e_base + el;
+                if (e >= v.N) continue;                                   // warp-uniform
+                for (int c = 0; c < len; c += 32) {
+                    const int t = seg + c + lane;
+                    const int64_t x = c + lane < len ? vlog[(int64_t)t * v.N + e] : VLOG_NONE;
+                    const bool valid = x != VLOG_NONE;
+                    const int64_t v1 = x < 0 ? -x - 1 : x;
+                    const unsigned vm = __ballot_sync(FULL_MASK, valid);
+                    if (lane == 0) valid_s[b][el][c / 32] = vm;
+                    if (vm == 0u) continue;
+                    const unsigned below = vm & ((1u << lane) - 1u);
+                    const int pl = below ? 31 - __clz(below) : 0;
+                    const int64_t prev = __shfl_sync(FULL_MASK, v1, pl);
+                    const int64_t v0 = below ? prev : vlast_c[q];
+                    double r = 0.0;
+                    if (valid) r = __dsub_rn(__ddiv_rn((double)v1, (double)v0), 1.0);
+                    rho_s[b][el][c + lane] = r;
+                    int64_t pk = valid ? v1 : INT64_MIN;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int64_t y = __shfl_up_sync(FULL_MASK, pk, o);
-                    if (lane >= o && y > pk) pk = y;
-                }
-                if (peak_c[q] > pk) pk = peak_c[q];
-                double dmin = mdd_c[q];
-                if (valid && v1 < pk) {
-                    const double dd = __dsub_rn(__ddiv_rn((double)v1, (double)pk), 1.0);
-                    if (dd < dmin) dmin = dd;
-                }
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int64_t y = __shfl_up_sync(FULL_MASK, pk, o);
+                        if (lane >= o && y > pk) pk = y;
+                    }
+                    if (peak_c[q] > pk) pk = peak_c[q];
+                    double dmin = mdd_c[q];
+                    if (valid && v1 < pk) {
+                        const double dd = __dsub_rn(__ddiv_rn((double)v1, (double)pk), 1.0);
+                        if (dd < dmin) dmin = dd;
+                    }
 #pragma unroll
-                for (int o = 16; o; o >>= 1) dmin = fmin(dmin, __shfl_xor_sync(FULL_MASK, dmin, o));
-                mdd_c[q] = dmin;
-                vlast_c[q] = __shfl_sync(FULL_MASK, v1, 31 - __clz(vm));
-                peak_c[q] = __shfl_sync(FULL_MASK, pk, 31);
-                n_c[q] += __popc(vm);
+                    for (int o = 16; o; o >>= 1) dmin = fmin(dmin, __shfl_xor_sync(FULL_MASK, dmin, o));
+                    mdd_c[q] = dmin;
+                    vlast_c[q] = __shfl_sync(FULL_MASK, v1, 31 - __clz(vm));
+                    peak_c[q] = __shfl_sync(FULL_MASK, pk, 31);
+                    n_c[q] += __popc(vm);
+                }
+            }
+            ptx::named_bar_arrive(1u + (uint32_t)b, RP_THREADS);               // segment k ready
+        }
+        for (int q = 0; q < 2; ++q) {
+            const int e = e_base + 2 * warp + q;
+            if (e < v.N && lane == 0) {
+                v.mdd[e] = mdd_c[q];
+                v.peak[e] = peak_c[q];
+                v.vlast[e] = vlast_c[q];
+                v.t[e] = n_c[q];
             }
         }
-        __syncthreads();
+    } else {
+        for (int k = 0; k < nseg; ++k) {
+            const int b = k & 1, len = min(RP_SEG, T - k * RP_SEG);
+            ptx::named_bar_sync(1u + (uint32_t)b, RP_THREADS);
+            if (chain) {
+                for (int c = 0; c < len; ++c) {
+                    if (!((valid_s[b][lane][c >> 5] >> (c & 31)) & 1u)) continue;
+                    const double r = rho_s[b][lane][c];
+                    n += 1;
+                    const double delta = __dsub_rn(r, mu);
+                    mu = __dadd_rn(mu, __ddiv_rn(delta, (double)n));
+                    m2 = __dadd_rn(m2, __dmul_rn(delta, __dsub_rn(r, mu)));
+                }
+            }
+            // the producers wait on this only for the segment two ahead
+            if (k + 2 < nseg) ptx::named_bar_arrive(3u + (uint32_t)b, RP_THREADS);
+        }
         if (chain) {
-            const int el = threadIdx.x;
-            for (int c = 0; c < len; ++c) {
-                if (!((valid_s[el][c >> 5] >> (c & 31)) & 1u)) continue;
-                const double r = rho_s[el][c];
-                n += 1;
-                const double delta = __dsub_rn(r, mu);
-                mu = __dadd_rn(mu, __ddiv_rn(delta, (double)n));
-                m2 = __dadd_rn(m2, __dmul_rn(delta, __dsub_rn(r, mu)));
-            }
-        }
-        __syncthreads();
-    }
-    // write back: the chain thread owns mu / m2; the phase-1 warp owns the rest
-    if (chain) {
-        v.mu[ce] = mu;
-        v.m2[ce] = m2;
-    }
-    for (int q = 0; q < 2; ++q) {
-        const int e = e_base + 2 * warp + q;
-        if (e < v.N && lane == 0) {
-            v.mdd[e] = mdd_c[q];
-            v.peak[e] = peak_c[q];
-            v.vlast[e] = vlast_c[q];
-            v.t[e] = n_c[q];
+            v.mu[ce] = mu;
+            v.m2[ce] = m2;
         }
     }
     __syncthreads();
@@ -1181,7 +1193,7 @@ cudaError_t launch_metrics_replay(const EnvView &v, const int64_t *vlog, int T, 
                                   cudaStream_t s)
 {
     if (!v.auto_reset) {
-        k_metrics_replay2<<<ceil_div(v.N, RP_ENVS), 256, 0, s>>>(v, vlog, T, metrics);
+        k_metrics_replay2<<<ceil_div(v.N, RP_ENVS), RP_THREADS, 0, s>>>(v, vlog, T, metrics);
         return cudaGetLastError();
     }
     // auto-reset: one thread per env, spread over every SM: the replay is
