@@ -410,11 +410,11 @@ ENV_STEP_BYTES = 377 + 1398
 
 # DRAM bytes (read + write) of one 256-step k_rollout_stock2 launch on the
 # 2,048-env workload, from an ncu capture of `bench.py --profile fused --T 256`
-# (dram__bytes_read.sum + dram__bytes_write.sum) of the 138-CTA build (envs
-# spread over every co-resident cluster); the kernel this file times.
-K_ROLLOUT_STOCK2_DRAM_BYTES = 3.89e6
+# (dram__bytes_read.sum + dram__bytes_write.sum) of the 138-CTA, 16-warp
+# build; the kernel this file times.
+K_ROLLOUT_STOCK2_DRAM_BYTES = 3.84e6
 K_ROLLOUT_STOCK2_TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_rollout_stock2, "
-                                 "bench.py --profile fused --T 256, one launch, the 138-CTA build")
+                                 "bench.py --profile fused --T 256, one launch, the 138-CTA 16-warp build")
 
 
 def env_step_line(fr, ctx, mk, w, dev, stream, N=1 << 20, T=4, warm=2):
