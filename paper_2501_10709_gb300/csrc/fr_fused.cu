@@ -221,12 +221,49 @@ __device__ __noinline__ int64_t afford_out_of_line(int64_t c, int64_t p, int fee
     return afford(c, p, fee_bps);
 }
 
-// Hidden-layer epilogue for row r: TMEM -> +bias -> ReLU -> BF16 (hi / lo)
-// or FP16 into the A operand of the next layer.
+// Eight pre-activation values x + b of row r -> ReLU -> the next layer's A
+// operand chunk c.  BF16 and FP16 take the ReLU inside the conversion
+// (cvt.rn.relu: max(x, 0) rounded, as max then round gives); the split
+// format rounds the ReLU'd value into its hi and lo parts.
+__device__ __forceinline__ void put8_relu(const float *z8, uint32_t a_base, uint32_t a_part, int fmt,
+                                          uint32_t row_off, int c)
+{
+    using namespace ptx;
+    const uint32_t at = a_base + (uint32_t)c * 2048u + row_off;
+    uint32_t w[4];
+    if (fmt == FMT_SPLIT) {
+        float v8[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v8[i] = fmaxf(z8[i], 0.0f);
+        uint32_t wl[4];
+        split_pack8(v8, w, wl);
+        st_shared_v4(at + a_part, wl[0], wl[1], wl[2], wl[3]);
+    } else if (fmt == FMT_F16) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = relu_f16x2_sat(z8[2 * i], z8[2 * i + 1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = relu_bf16x2(z8[2 * i], z8[2 * i + 1]);
+    }
+    st_shared_v4(at, w[0], w[1], w[2], w[3]);
+}
+
+// Hidden-layer epilogue for row r: TMEM -> +bias -> ReLU -> the next layer's
+// operand format, 32 columns per TMEM wait (two loads in flight), the bias
+// read four columns per load (the layer's bias row is 1 KB aligned).
 __device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, const float *bl, int N, uint32_t a_base,
                                                 uint32_t a_part, int fmt, uint32_t row_off)
 {
     using namespace ptx;
+    const float4 *bl4 = (const float4 *)bl;
+    auto group8 = [&](const uint32_t *v, int c) {      // columns c .. c + 7
+        const float4 b0 = __ldg(bl4 + c / 4), b1 = __ldg(bl4 + c / 4 + 1);
+        const float z8[8] = {__uint_as_float(v[0]) + b0.x, __uint_as_float(v[1]) + b0.y,
+                             __uint_as_float(v[2]) + b0.z, __uint_as_float(v[3]) + b0.w,
+                             __uint_as_float(v[4]) + b1.x, __uint_as_float(v[5]) + b1.y,
+                             __uint_as_float(v[6]) + b1.z, __uint_as_float(v[7]) + b1.w};
+        put8_relu(z8, a_base, a_part, fmt, row_off, c / 8);
+    };
     int c0 = 0;
     for (; c0 + 64 <= N; c0 += 64) {             // two loads in flight per wait
         uint32_t v[32], w[32];
@@ -235,20 +272,9 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, const float *
         tmem_ld32(tmem_row + (uint32_t)c0 + 32u, w);
         tmem_ld_wait();
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            float x[8];
+        for (int g = 0; g < 4; ++g) group8(v + g * 8, c0 + g * 8);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) x[i] = fmaxf(__uint_as_float(v[g * 8 + i]) + __ldg(bl + c0 + g * 8 + i), 0.0f);
-            put8(x, a_base, a_part, fmt, row_off, c0 / 8 + g);
-        }
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            float x[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-                x[i] = fmaxf(__uint_as_float(w[g * 8 + i]) + __ldg(bl + c0 + 32 + g * 8 + i), 0.0f);
-            put8(x, a_base, a_part, fmt, row_off, c0 / 8 + 4 + g);
-        }
+        for (int g = 0; g < 4; ++g) group8(w + g * 8, c0 + 32 + g * 8);
     }
     for (; c0 + 32 <= N; c0 += 32) {
         uint32_t v[32];
@@ -256,12 +282,7 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, const float *
         tmem_ld32(tmem_row + (uint32_t)c0, v);
         tmem_ld_wait();
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            float x[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) x[i] = fmaxf(__uint_as_float(v[g * 8 + i]) + __ldg(bl + c0 + g * 8 + i), 0.0f);
-            put8(x, a_base, a_part, fmt, row_off, c0 / 8 + g);
-        }
+        for (int g = 0; g < 4; ++g) group8(v + g * 8, c0 + g * 8);
     }
     if (c0 < N) {                                   // a 16-column tail
         uint32_t v[16];
@@ -269,12 +290,7 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, const float *
         tmem_ld16(tmem_row + (uint32_t)c0, v);
         tmem_ld_wait();
 #pragma unroll
-        for (int g = 0; g < 2; ++g) {
-            float x[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) x[i] = fmaxf(__uint_as_float(v[g * 8 + i]) + __ldg(bl + c0 + g * 8 + i), 0.0f);
-            put8(x, a_base, a_part, fmt, row_off, c0 / 8 + g);
-        }
+        for (int g = 0; g < 2; ++g) group8(v + g * 8, c0 + g * 8);
     }
 }
 

@@ -215,15 +215,6 @@ __device__ __forceinline__ bool f2_wait(uint64_t *bar, uint32_t parity, volatile
     return ptx::warp_wait_all(bar, parity, cluster_scope, abort, err, code, TC_WAIT_NS);
 }
 
-__device__ __forceinline__ void pack8_bf16(const float *v, uint32_t *w)
-{
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-        w[i] = *(const uint32_t *)&b;
-    }
-}
-
 // ------------------------------------------------------------- MMA issue
 // One layer of this CTA's agent half: K-steps of 16 over the resident
 // weight chunks, accumulator in TMEM, completion signalled on `acc`.  Issued
@@ -662,17 +653,23 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                         st_async_v4(map_shared_rank(at, (uint32_t)(rank ^ 1)), w[0], w[1], w[2], w[3], h1r_partner);
                     }
                 } else {
+                    // + Z, then ReLU inside the BF16 conversion
+                    uint32_t w0[4], w1[4];
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const float4 z = zq[4 * q4 + i];
-                        x[4 * i + 0] = fmaxf(__uint_as_float(vv[4 * i + 0]) + z.x, 0.0f);
-                        x[4 * i + 1] = fmaxf(__uint_as_float(vv[4 * i + 1]) + z.y, 0.0f);
-                        x[4 * i + 2] = fmaxf(__uint_as_float(vv[4 * i + 2]) + z.z, 0.0f);
-                        x[4 * i + 3] = fmaxf(__uint_as_float(vv[4 * i + 3]) + z.w, 0.0f);
+                        const uint32_t lo = relu_bf16x2(__uint_as_float(vv[4 * i + 0]) + z.x,
+                                                        __uint_as_float(vv[4 * i + 1]) + z.y);
+                        const uint32_t hi = relu_bf16x2(__uint_as_float(vv[4 * i + 2]) + z.z,
+                                                        __uint_as_float(vv[4 * i + 3]) + z.w);
+                        if (i < 2) {
+                            w0[2 * i] = lo;
+                            w0[2 * i + 1] = hi;
+                        } else {
+                            w1[2 * i - 4] = lo;
+                            w1[2 * i - 3] = hi;
+                        }
                     }
-                    uint32_t w0[4], w1[4];
-                    pack8_bf16(x, w0);
-                    pack8_bf16(x + 8, w1);
                     const uint32_t at = a_base + (dst_chunk0 + (uint32_t)(cc / 8)) * 2048u + row_off;
                     if (row_live) {
                         st_shared_v4(at, w0[0], w0[1], w0[2], w0[3]);
@@ -716,11 +713,25 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
                     e4m3_pack16(x, inv2, w);
                     st_shared_v4(a_base + (uint32_t)((c0 + cc) / 16) * 2048u + row_off, w[0], w[1], w[2], w[3]);
                 } else {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) x[i] = fmaxf(__uint_as_float(vv[i]) + b2[c0 + cc + i], 0.0f);
+                    // + b2 (four per shared load), then ReLU inside the BF16
+                    // conversion
+                    const float4 *b4 = (const float4 *)(b2 + c0 + cc);
                     uint32_t w0[4], w1[4];
-                    pack8_bf16(x, w0);
-                    pack8_bf16(x + 8, w1);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float4 bb = b4[i];
+                        const uint32_t lo = relu_bf16x2(__uint_as_float(vv[4 * i + 0]) + bb.x,
+                                                        __uint_as_float(vv[4 * i + 1]) + bb.y);
+                        const uint32_t hi = relu_bf16x2(__uint_as_float(vv[4 * i + 2]) + bb.z,
+                                                        __uint_as_float(vv[4 * i + 3]) + bb.w);
+                        if (i < 2) {
+                            w0[2 * i] = lo;
+                            w0[2 * i + 1] = hi;
+                        } else {
+                            w1[2 * i - 4] = lo;
+                            w1[2 * i - 3] = hi;
+                        }
+                    }
                     const uint32_t at = a_base + (uint32_t)((c0 + cc) / 8) * 2048u + row_off;
                     st_shared_v4(at, w0[0], w0[1], w0[2], w0[3]);
                     st_shared_v4(at + 2048u, w1[0], w1[1], w1[2], w1[3]);
