@@ -512,6 +512,16 @@ int env_tile_packing_efficiency(const fr_env *env, float *eff);
  * are captured with the rollout into a graph).  No counterpart in the paper. */
 int env_set_table_cache(fr_env *env, int32_t on);
 
+/* Split fused stock rollouts (no counterpart in the paper).  on = 1 (the
+ * default): a fused stock rollout of 64 steps or more, without tile packing,
+ * trajectory outputs or auto-reset, runs as two launches of the resident
+ * kernel, and the FP64 metrics replay of the first half runs beside the
+ * second launch (which goes on an internal stream of the highest priority,
+ * ordered with `stream` by events, so that the rollout is still one ordered
+ * operation on `stream` and can be captured into a graph).  Results are
+ * those of one launch, bit for bit.  on = 0: always one launch. */
+int env_set_rollout_split(fr_env *env, int32_t on);
+
 /* Autotuner of the batched rollouts (no counterpart in the paper: the
  * project's own choice of launch shape).  Times, for this env batch and
  * ensemble, the launch configurations the library has for the pair and keeps

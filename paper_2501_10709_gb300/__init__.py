@@ -22,7 +22,7 @@ __all__ = [
     "fr_ctx_create", "fr_market_create", "env_create", "env_reset", "env_step",
     "env_observe", "env_get_state", "env_metrics", "env_snapshot", "env_restore",
     "env_error_count", "env_dims", "ensemble_create", "ensemble_forward",
-    "ensemble_act", "ensemble_act_noalloc", "ensemble_device_errors", "rollout", "env_set_rollout_path", "env_set_kernel_timing", "env_last_kernel_ms", "env_last_launch_shape", "env_set_tile_packing", "env_set_table_cache",
+    "ensemble_act", "ensemble_act_noalloc", "ensemble_device_errors", "rollout", "env_set_rollout_path", "env_set_kernel_timing", "env_last_kernel_ms", "env_last_launch_shape", "env_set_tile_packing", "env_set_table_cache", "env_set_rollout_split",
     "env_tile_packing_efficiency", "ensemble_set_weights", "ensemble_validate", "trajectory_metrics", "env_set_exploration",
     "EXPLORE_NONE", "EXPLORE_GAUSSIAN", "EXPLORE_EPS_GREEDY", "Server", "fr_server_create", "backtest_submit",
     "backtest_poll", "backtest_cancel", "fr_server_stats", "fr_server_add_pool", "backtest_fetch_traj",
@@ -266,6 +266,10 @@ def env_restore(env: Env, blob: bytes):
 
 def env_set_rollout_path(env: Env, path: int):
     _lib.check(lib().env_set_rollout_path(env, int(path)), "env_set_rollout_path")
+
+
+def env_set_rollout_split(env: Env, on: bool):
+    _lib.check(lib().env_set_rollout_split(env, 1 if on else 0), "env_set_rollout_split")
 
 
 def env_set_table_cache(env: Env, on: bool):

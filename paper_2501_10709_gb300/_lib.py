@@ -132,6 +132,7 @@ SIGNATURES = {
     "ensemble_validate": (i32, [vp, vp, i32, f64, vp, vp, vp]),
     "env_set_tile_packing": (i32, [vp, i32]),
     "env_set_table_cache": (i32, [vp, i32]),
+    "env_set_rollout_split": (i32, [vp, i32]),
     "env_tile_packing_efficiency": (i32, [vp, vp]),
     "fr_server_create": (i32, [vp, vp, vp]),
     "fr_server_destroy": (None, [vp]),

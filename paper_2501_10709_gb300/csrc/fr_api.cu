@@ -532,6 +532,9 @@ void env_destroy(fr_env *env)
     dev_free(env->ctx, env->pack_tile_w, 4ull * tiles);
     for (int i = 0; i < 2; ++i)
         if (env->k_ev[i]) cudaEventDestroy(env->k_ev[i]);
+    for (int i = 0; i < 2; ++i)
+        if (env->split_ev[i]) cudaEventDestroy(env->split_ev[i]);
+    if (env->split_stream) cudaStreamDestroy(env->split_stream);
     delete env;
 }
 
@@ -684,6 +687,14 @@ int env_set_table_cache(fr_env *env, int32_t on)
     FR_NVTX("env_set_table_cache");
     FR_CHECK(env, FR_EINVAL, "env_set_table_cache: NULL env");
     env->z_cache_off = on ? 0 : 1;
+    return FR_OK;
+}
+
+int env_set_rollout_split(fr_env *env, int32_t on)
+{
+    FR_NVTX("env_set_rollout_split");
+    FR_CHECK(env, FR_EINVAL, "env_set_rollout_split: NULL env");
+    env->split_off = on ? 0 : 1;
     return FR_OK;
 }
 

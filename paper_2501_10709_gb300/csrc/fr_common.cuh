@@ -171,6 +171,12 @@ struct fr_env {
     int k_timing;               // record on the next rollouts
     int k_recorded;             // a pair has been recorded
     int last_ctas, last_tile;   // launch shape of the last fused stock rollout (0: none yet)
+    // split fused stock rollouts: the second launch's stream (highest
+    // priority) and its two ordering events (created at first use)
+    cudaStream_t split_stream;
+    cudaEvent_t split_ev[2];
+    int split_prio;
+    int split_off;              // 1: never split (env_set_rollout_split)
 };
 
 namespace fr {
@@ -342,8 +348,12 @@ int tc_forward_tiled(const fr_ensemble *e, const float *obs, int ld, int n, floa
 // Whether the fused persistent rollout supports this env / ensemble pair.
 bool tc_rollout_supported(const fr_env *env, const fr_ensemble *e);
 // FP64 episode accumulators from a rollout's value log (fr_fused.cu)
+// t0 (NULL: the env's step counters) gives each env's step count before the
+// logged steps.  With t0 the caller has already advanced the counters: the
+// replay without auto-reset leaves them alone, the one with auto-reset
+// writes them (its count restarts with every episode, as the kernel's).
 cudaError_t launch_metrics_replay(const EnvView &v, const int64_t *vlog, int T, double *metrics,
-                                  cudaStream_t s);
+                                  cudaStream_t s, const int32_t *t0 = nullptr);
 // fused stock rollout with resident weights (fr_fused2.cu)
 bool f2_supported(const fr_env *env, const fr_ensemble *e);
 int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, double *metrics,

@@ -834,13 +834,13 @@ __global__ void __launch_bounds__(FU_THREADS, TASK == FR_TASK_CRYPTO ? 3 : 1)
 // Replays the value log through the FP64 episode accumulators in time order
 // (one thread per env), advancing the step counters, latching finished
 // episodes under auto-reset, and writing the metrics when asked.
-__global__ void k_metrics_replay(EnvView v, const int64_t *vlog, int T, double *metrics)
+__global__ void k_metrics_replay(EnvView v, const int64_t *vlog, int T, double *metrics, const int32_t *t0)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= v.N) return;
     double mu = v.mu[e], m2 = v.m2[e], mdd = v.mdd[e];
     int64_t peak = v.peak[e], vlast = v.vlast[e];
-    int n = v.t[e];
+    int n = t0 ? t0[e] : v.t[e];
     double *Lt = v.latched + (int64_t)e * 4;
     for (int s = 0; s < T; ++s) {
         const int64_t x = vlog[(int64_t)s * v.N + e];
@@ -892,7 +892,8 @@ __global__ void k_metrics_replay(EnvView v, const int64_t *vlog, int T, double *
 // equals the one-thread-per-env replay bit for bit.
 constexpr int RP_ENVS = 16, RP_SEG = 64, RP_PROD = 8, RP_THREADS = 32 * (RP_PROD + 1);
 
-__global__ void __launch_bounds__(RP_THREADS) k_metrics_replay2(EnvView v, const int64_t *vlog, int T, double *metrics)
+__global__ void __launch_bounds__(RP_THREADS) k_metrics_replay2(EnvView v, const int64_t *vlog, int T, double *metrics,
+                                                                 const int32_t *t0)
 {
     // two segment buffers: warps 0..7 fill one (phase 1) while warp 8's
     // lanes run the Welford chains over the other (phase 2); named barriers
@@ -906,7 +907,7 @@ __global__ void __launch_bounds__(RP_THREADS) k_metrics_replay2(EnvView v, const
     const int ce = e_base + lane;
     const bool chain = warp == RP_PROD && lane < RP_ENVS && ce < v.N;
     double mu = chain ? v.mu[ce] : 0.0, m2 = chain ? v.m2[ce] : 0.0;
-    int n = chain ? v.t[ce] : 0;
+    int n = chain ? (t0 ? t0[ce] : v.t[ce]) : 0;
     // phase-1 carries of this warp's two envs
     int64_t vlast_c[2], peak_c[2];
     double mdd_c[2];
@@ -918,7 +919,7 @@ __global__ void __launch_bounds__(RP_THREADS) k_metrics_replay2(EnvView v, const
             vlast_c[q] = in ? v.vlast[e] : 1;
             peak_c[q] = in ? v.peak[e] : 1;
             mdd_c[q] = in ? v.mdd[e] : 0.0;
-            n_c[q] = in ? v.t[e] : 0;
+            n_c[q] = in ? (t0 ? t0[e] : v.t[e]) : 0;
         }
         for (int k = 0; k < nseg; ++k) {
             const int b = k & 1, seg = k * RP_SEG, len = min(RP_SEG, T - seg);
@@ -969,7 +970,7 @@ __global__ void __launch_bounds__(RP_THREADS) k_metrics_replay2(EnvView v, const
                 v.mdd[e] = mdd_c[q];
                 v.peak[e] = peak_c[q];
                 v.vlast[e] = vlast_c[q];
-                v.t[e] = n_c[q];
+                if (!t0) v.t[e] = n_c[q];
             }
         }
     } else {
@@ -1206,16 +1207,16 @@ int tc_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
 }
 
 cudaError_t launch_metrics_replay(const EnvView &v, const int64_t *vlog, int T, double *metrics,
-                                  cudaStream_t s)
+                                  cudaStream_t s, const int32_t *t0)
 {
     if (!v.auto_reset) {
-        k_metrics_replay2<<<ceil_div(v.N, RP_ENVS), RP_THREADS, 0, s>>>(v, vlog, T, metrics);
+        k_metrics_replay2<<<ceil_div(v.N, RP_ENVS), RP_THREADS, 0, s>>>(v, vlog, T, metrics, t0);
         return cudaGetLastError();
     }
     // auto-reset: one thread per env, spread over every SM: the replay is
     // bound by the FP64 units, and 2,048 envs in blocks of 256 would use 8 SMs
     const int per_block = std::min(256, std::max(16, (int)ceil_div(v.N, 152) + 15) / 16 * 16);
-    k_metrics_replay<<<ceil_div(v.N, per_block), per_block, 0, s>>>(v, vlog, T, metrics);
+    k_metrics_replay<<<ceil_div(v.N, per_block), per_block, 0, s>>>(v, vlog, T, metrics, t0);
     return cudaGetLastError();
 }
 

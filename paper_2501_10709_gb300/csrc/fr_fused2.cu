@@ -111,6 +111,7 @@ struct F2Args {
     float *tr_rew_f32;
     uint8_t *tr_done;
     int64_t *vlog;
+    int32_t *t0_out;      // [N] each env's step count at the launch's start (for the replay)
     unsigned *err;
     Explore ex;           // exploration of the combined actions
 };
@@ -554,6 +555,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
             }
         }
         s.v0 = s.cash + warp_sum(s.p * (int64_t)s.h);
+        if (e >= 0 && lane == 0) a.t0_out[e] = s.t;
     }
     // observation of step 0
     own_publish_all<NOWN, NARROW, FP8>(a, own, orow, eidx, a_obs, ctx_addr, M2, lane, 0, rank, obs_ready, inv0);
@@ -990,6 +992,7 @@ __device__ void f2_env_loop(const F2Args &a_in, uint32_t tmem, uint8_t *smem, co
         if (lane == 0) {
             v.cash[e] = own[i].cash;
             v.done[e] = own[i].done ? 1 : 0;
+            v.t[e] = own[i].t;
         }
         if (lane < SK2) v.hold[(int64_t)e * KP + lane] = lane < own[i].Ke ? own[i].h : 0;
     }
@@ -1396,7 +1399,8 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
         env->zbuf_bytes = x_b + z_b;
         env->z_serial = 0;
     }
-    const uint64_t vlog_b = (uint64_t)T * v.N * 8;
+    // the value log, then two [N] arrays of start step counts
+    const uint64_t vlog_b = (((uint64_t)T * v.N * 8 + 255) & ~255ull) + 2 * (((uint64_t)v.N * 4 + 255) & ~255ull);
     if (env->scratch_bytes < vlog_b) {
         FR_CUDA(cudaStreamSynchronize(s));
         dev_free(env->ctx, env->scratch, env->scratch_bytes);
@@ -1407,6 +1411,8 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
         env->scratch_bytes = vlog_b;
     }
     int64_t *vlog = (int64_t *)env->scratch;
+    int32_t *t0a = (int32_t *)((char *)env->scratch + (((uint64_t)T * v.N * 8 + 255) & ~255ull));
+    int32_t *t0b = (int32_t *)((char *)t0a + (((uint64_t)v.N * 4 + 255) & ~255ull));
     float *Z = (float *)((char *)env->zbuf + x_b);
     if (env->z_serial != e->serial || env->z_cache_off) {
         // Z[j][ctx][n] = W1_j[n, indicators] . x[ctx] + b1_j[n]
@@ -1519,15 +1525,58 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     a.tr_rew_f32 = traj->rew_f32;
     a.tr_done = traj->done;
     a.vlog = vlog;
+    a.t0_out = t0a;
     a.err = e->tc->err;
     a.ex = explore_of(env, env->explore_step);
     cfg.gridDim = dim3((unsigned)(2 * p.M), (unsigned)ceil_div(v.N, TR), 1);
     env->last_ctas = (int)(cfg.gridDim.x * cfg.gridDim.y);
     env->last_tile = TR;
+    // Split rollout: the FP64 replay of a rollout's value log is a chain of
+    // dependent divisions per env that no parallelism shortens.  Long
+    // rollouts without packing, trajectory outputs or auto-reset run as two
+    // launches; the replay of the first half runs on the idle SMs while the
+    // second half's launch runs on a higher-priority stream, and only the
+    // second half's replay follows the kernel.  Every env's arithmetic is
+    // that of one launch (a rollout in pieces is the same rollout).
+    const bool split = !packed && !want_traj && !v.auto_reset && T >= 64 && !env->split_off;
     FR_CUDA(env_time_mark(env, 0, s));
-    FR_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
+    if (!split) {
+        FR_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
+        FR_CUDA(env_time_mark(env, 1, s));
+        FR_CUDA(launch_metrics_replay(v, vlog, T, metrics, s, t0a));
+        return FR_OK;
+    }
+    if (!env->split_stream) {
+        int lo = 0, hi = 0;
+        FR_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        FR_CUDA(cudaStreamCreateWithPriority(&env->split_stream, cudaStreamNonBlocking, hi));
+        for (int i = 0; i < 2; ++i) FR_CUDA(cudaEventCreateWithFlags(&env->split_ev[i], cudaEventDisableTiming));
+        env->split_prio = hi;
+    }
+    const int T1 = T / 2, T2 = T - T1;
+    F2Args b = a;
+    a.T = T1;
+    b.T = T2;
+    b.vlog = vlog + (int64_t)T1 * v.N;
+    b.t0_out = t0b;
+    b.ex.g0 = a.ex.g0 + (uint32_t)T1;
+    FR_CUDA(cudaLaunchKernelEx(&cfg, kern, a));                    // steps [0, T1)
+    FR_CUDA(cudaEventRecord(env->split_ev[0], s));
+    cudaLaunchConfig_t cfg2 = cfg;
+    cudaLaunchAttribute attr2[2];
+    attr2[0] = attr[0];
+    attr2[1].id = cudaLaunchAttributePriority;
+    attr2[1].val.priority = env->split_prio;
+    cfg2.attrs = attr2;
+    cfg2.numAttrs = 2;
+    cfg2.stream = env->split_stream;
+    FR_CUDA(cudaStreamWaitEvent(env->split_stream, env->split_ev[0], 0));
+    FR_CUDA(cudaLaunchKernelEx(&cfg2, kern, b));                   // steps [T1, T), beside the replay
+    FR_CUDA(cudaEventRecord(env->split_ev[1], env->split_stream));
+    FR_CUDA(launch_metrics_replay(v, vlog, T1, nullptr, s, t0a));  // accumulators through step T1
+    FR_CUDA(cudaStreamWaitEvent(s, env->split_ev[1], 0));
     FR_CUDA(env_time_mark(env, 1, s));
-    FR_CUDA(launch_metrics_replay(v, vlog, T, metrics, s));
+    FR_CUDA(launch_metrics_replay(v, b.vlog, T2, metrics, s, t0b));
     return FR_OK;
 }
 
