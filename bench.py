@@ -755,9 +755,9 @@ def run_gpu(args):
             e2e_times.append(time.perf_counter() - t0)
     e2e_value = world * env_steps / statistics.mean(e2e_times)
 
-    # env_reset, the indicator table, the fused rollout kernel's two launches
-    # (a split rollout) and the two halves' metrics replays
-    launches_per_rollout = 6
+    # env_reset, the indicator table, the fused rollout kernel's four launches
+    # (a rollout split in four pieces) and the pieces' metrics replays
+    launches_per_rollout = 10
     line = {
         "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,

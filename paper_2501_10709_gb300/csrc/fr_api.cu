@@ -532,7 +532,7 @@ void env_destroy(fr_env *env)
     dev_free(env->ctx, env->pack_tile_w, 4ull * tiles);
     for (int i = 0; i < 2; ++i)
         if (env->k_ev[i]) cudaEventDestroy(env->k_ev[i]);
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 5; ++i)
         if (env->split_ev[i]) cudaEventDestroy(env->split_ev[i]);
     if (env->split_stream) cudaStreamDestroy(env->split_stream);
     delete env;

@@ -171,10 +171,10 @@ struct fr_env {
     int k_timing;               // record on the next rollouts
     int k_recorded;             // a pair has been recorded
     int last_ctas, last_tile;   // launch shape of the last fused stock rollout (0: none yet)
-    // split fused stock rollouts: the second launch's stream (highest
-    // priority) and its two ordering events (created at first use)
+    // split fused stock rollouts: the pieces' stream (highest priority) and
+    // its ordering events (created at first use)
     cudaStream_t split_stream;
-    cudaEvent_t split_ev[2];
+    cudaEvent_t split_ev[5];    // one per piece, and the rollout's start
     int split_prio;
     int split_off;              // 1: never split (env_set_rollout_split)
 };

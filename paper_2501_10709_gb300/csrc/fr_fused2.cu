@@ -207,6 +207,9 @@ __host__ __device__ inline F2Smem f2_smem(const F2Plan &p)
     return s;
 }
 
+// pieces of a split rollout (launches of the resident kernel per rollout)
+constexpr int F2_PIECES_MAX = 4;
+
 // barrier slots
 enum { B_W = 0, B_OBS, B_ACC, B_H1, B_H2, B_X, B_END, B_COUNT };
 
@@ -1399,8 +1402,9 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
         env->zbuf_bytes = x_b + z_b;
         env->z_serial = 0;
     }
-    // the value log, then two [N] arrays of start step counts
-    const uint64_t vlog_b = (((uint64_t)T * v.N * 8 + 255) & ~255ull) + 2 * (((uint64_t)v.N * 4 + 255) & ~255ull);
+    // the value log, then one [N] array of start step counts per launch
+    const uint64_t t0_b = ((uint64_t)v.N * 4 + 255) & ~255ull;
+    const uint64_t vlog_b = (((uint64_t)T * v.N * 8 + 255) & ~255ull) + (uint64_t)F2_PIECES_MAX * t0_b;
     if (env->scratch_bytes < vlog_b) {
         FR_CUDA(cudaStreamSynchronize(s));
         dev_free(env->ctx, env->scratch, env->scratch_bytes);
@@ -1412,7 +1416,6 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     }
     int64_t *vlog = (int64_t *)env->scratch;
     int32_t *t0a = (int32_t *)((char *)env->scratch + (((uint64_t)T * v.N * 8 + 255) & ~255ull));
-    int32_t *t0b = (int32_t *)((char *)t0a + (((uint64_t)v.N * 4 + 255) & ~255ull));
     float *Z = (float *)((char *)env->zbuf + x_b);
     if (env->z_serial != e->serial || env->z_cache_off) {
         // Z[j][ctx][n] = W1_j[n, indicators] . x[ctx] + b1_j[n]
@@ -1533,14 +1536,17 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     env->last_tile = TR;
     // Split rollout: the FP64 replay of a rollout's value log is a chain of
     // dependent divisions per env that no parallelism shortens.  Long
-    // rollouts without packing, trajectory outputs or auto-reset run as two
-    // launches; the replay of the first half runs on the idle SMs while the
-    // second half's launch runs on a higher-priority stream, and only the
-    // second half's replay follows the kernel.  Every env's arithmetic is
-    // that of one launch (a rollout in pieces is the same rollout).
-    const bool split = !packed && !want_traj && !v.auto_reset && T >= 64 && !env->split_off;
+    // rollouts without packing, trajectory outputs or auto-reset run as K
+    // launches (K = T / 64, at most 4) on an internal stream of the highest
+    // priority; the replay of each piece runs on `stream` on the idle SMs
+    // while the next piece's launch runs, so only the last piece's replay
+    // follows the kernel.  Events order the two streams, so the rollout stays
+    // one ordered (and graph-capturable) operation on `stream`.  Every env's
+    // arithmetic is that of one launch (a rollout in pieces is the same
+    // rollout).
+    const int K = (!packed && !want_traj && !v.auto_reset && !env->split_off) ? std::min(F2_PIECES_MAX, T / 64) : 1;
     FR_CUDA(env_time_mark(env, 0, s));
-    if (!split) {
+    if (K <= 1) {
         FR_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
         FR_CUDA(env_time_mark(env, 1, s));
         FR_CUDA(launch_metrics_replay(v, vlog, T, metrics, s, t0a));
@@ -1550,18 +1556,10 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
         int lo = 0, hi = 0;
         FR_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
         FR_CUDA(cudaStreamCreateWithPriority(&env->split_stream, cudaStreamNonBlocking, hi));
-        for (int i = 0; i < 2; ++i) FR_CUDA(cudaEventCreateWithFlags(&env->split_ev[i], cudaEventDisableTiming));
+        for (int i = 0; i <= F2_PIECES_MAX; ++i)
+            FR_CUDA(cudaEventCreateWithFlags(&env->split_ev[i], cudaEventDisableTiming));
         env->split_prio = hi;
     }
-    const int T1 = T / 2, T2 = T - T1;
-    F2Args b = a;
-    a.T = T1;
-    b.T = T2;
-    b.vlog = vlog + (int64_t)T1 * v.N;
-    b.t0_out = t0b;
-    b.ex.g0 = a.ex.g0 + (uint32_t)T1;
-    FR_CUDA(cudaLaunchKernelEx(&cfg, kern, a));                    // steps [0, T1)
-    FR_CUDA(cudaEventRecord(env->split_ev[0], s));
     cudaLaunchConfig_t cfg2 = cfg;
     cudaLaunchAttribute attr2[2];
     attr2[0] = attr[0];
@@ -1570,13 +1568,29 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     cfg2.attrs = attr2;
     cfg2.numAttrs = 2;
     cfg2.stream = env->split_stream;
-    FR_CUDA(cudaStreamWaitEvent(env->split_stream, env->split_ev[0], 0));
-    FR_CUDA(cudaLaunchKernelEx(&cfg2, kern, b));                   // steps [T1, T), beside the replay
-    FR_CUDA(cudaEventRecord(env->split_ev[1], env->split_stream));
-    FR_CUDA(launch_metrics_replay(v, vlog, T1, nullptr, s, t0a));  // accumulators through step T1
-    FR_CUDA(cudaStreamWaitEvent(s, env->split_ev[1], 0));
-    FR_CUDA(env_time_mark(env, 1, s));
-    FR_CUDA(launch_metrics_replay(v, b.vlog, T2, metrics, s, t0b));
+    FR_CUDA(cudaEventRecord(env->split_ev[F2_PIECES_MAX], s));
+    FR_CUDA(cudaStreamWaitEvent(env->split_stream, env->split_ev[F2_PIECES_MAX], 0));
+    int s0 = 0;
+    for (int k = 0; k < K; ++k) {
+        const int Tk = (k + 1) * T / K - s0;
+        F2Args b = a;
+        b.T = Tk;
+        b.vlog = vlog + (int64_t)s0 * v.N;
+        b.t0_out = (int32_t *)((char *)t0a + (uint64_t)k * t0_b);
+        b.ex.g0 = a.ex.g0 + (uint32_t)s0;
+        FR_CUDA(cudaLaunchKernelEx(&cfg2, kern, b));               // steps [s0, s0 + Tk)
+        FR_CUDA(cudaEventRecord(env->split_ev[k], env->split_stream));
+        s0 += Tk;
+    }
+    s0 = 0;
+    for (int k = 0; k < K; ++k) {
+        const int Tk = (k + 1) * T / K - s0;
+        FR_CUDA(cudaStreamWaitEvent(s, env->split_ev[k], 0));
+        if (k == K - 1) FR_CUDA(env_time_mark(env, 1, s));
+        FR_CUDA(launch_metrics_replay(v, vlog + (int64_t)s0 * v.N, Tk, k == K - 1 ? metrics : nullptr, s,
+                                      (const int32_t *)((const char *)t0a + (uint64_t)k * t0_b)));
+        s0 += Tk;
+    }
     return FR_OK;
 }
 

@@ -310,10 +310,11 @@ def test_rollout_graph_capture(ctx, dev, case):
 
 
 def test_split_rollout_equals_one_launch_and_replays_in_a_graph(ctx, dev):
-    # 100 steps without trajectory outputs run as two launches with the first
-    # half's replay beside the second launch; state and FP64 metrics equal the
-    # single launch bit for bit, directly and as a graph replay
-    w = synth.workload_stock_2048(N=700, T=100)
+    # 200 steps without trajectory outputs run as three launches (66, 67, 67
+    # steps), each piece's FP64 replay beside the next piece's launch; state
+    # and metrics equal the single launch bit for bit, directly and as a
+    # graph replay
+    w = synth.workload_stock_2048(N=700, T=200)
     e = w.envs
     mk = fr.fr_market_create(ctx, w.market)
     ens = fr.ensemble_create(ctx, w.dims, w.params, precision=fr.PREC_BF16)
@@ -322,7 +323,7 @@ def test_split_rollout_equals_one_launch_and_replays_in_a_graph(ctx, dev):
         env = _stock_env(ctx, mk, e)
         fr.env_set_rollout_split(env, split)
         met = torch.empty(e.N, 3, dtype=torch.float64, device=dev)
-        fr.rollout(env, ens, 100, metrics=met)
+        fr.rollout(env, ens, 200, metrics=met)
         cash = torch.empty(e.N, dtype=torch.int64, device=dev)
         hold = torch.empty(e.N, 30, dtype=torch.int32, device=dev)
         steps = torch.empty(e.N, dtype=torch.int32, device=dev)
@@ -332,14 +333,14 @@ def test_split_rollout_equals_one_launch_and_replays_in_a_graph(ctx, dev):
         out.append([x.cpu().numpy() for x in (met, cash, hold, steps, done)])
     for x, y in zip(out[0], out[1]):
         assert np.array_equal(x, y)
-    # a second split rollout continues from the first (accumulators carried)
+    # a second split rollout (two pieces) continues from the first
     met2 = torch.empty(e.N, 3, dtype=torch.float64, device=dev)
-    fr.rollout(env, ens, 80, metrics=met2)
+    fr.rollout(env, ens, 130, metrics=met2)
     env1 = _stock_env(ctx, mk, e)
     fr.env_set_rollout_split(env1, False)
     met1 = torch.empty(e.N, 3, dtype=torch.float64, device=dev)
-    fr.rollout(env1, ens, 100, metrics=met1)
-    fr.rollout(env1, ens, 80, metrics=met1)
+    fr.rollout(env1, ens, 200, metrics=met1)
+    fr.rollout(env1, ens, 130, metrics=met1)
     torch.cuda.synchronize()
     assert torch.equal(met2, met1)
     # captured: reset + split rollout, replayed
@@ -348,13 +349,13 @@ def test_split_rollout_equals_one_launch_and_replays_in_a_graph(ctx, dev):
     met3 = torch.empty(e.N, 3, dtype=torch.float64, device=dev)
     with torch.cuda.stream(side):
         fr.env_reset(env)
-        fr.rollout(env, ens, 100, metrics=met3)
+        fr.rollout(env, ens, 200, metrics=met3)
     torch.cuda.current_stream().wait_stream(side)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
         fr.env_reset(env)
-        fr.rollout(env, ens, 100, metrics=met3)
+        fr.rollout(env, ens, 200, metrics=met3)
     for _ in range(2):
         met3.fill_(float("nan"))
         g.replay()
