@@ -1093,53 +1093,78 @@ __global__ void __launch_bounds__(32 * W, 1) k_rollout_stock2(const __grid_const
 // The indicator table: Z[j][ctx][n] = sum_c W1_j[n][c] x[ctx][c] + b1_j[n]
 // over the 240 indicator entries c, with x[ctx][i*30 + k] = ind[day][i][k]
 // for assets k < the slot's count, else 0 (ctx = slot * days + day).  A block
-// takes ZT_ROWS contexts of one agent: their rows in shared memory, thread n
-// output n, the weights read [c][n] (coalesced, L2-resident), sums in c
-// order in fp32.  Replaces a generic SIMT GEMM of 64 x 64 tiles that left
-// most of the GPU idle on this shape (1,000 contexts x 240 x 256 x 3 agents).
-constexpr int ZT_ROWS = 8;
+// takes ZT_ROWS contexts x ZT_COLS outputs of one agent.  The contexts' rows
+// and the tile's weight columns (read [c][n]) are copied into shared memory
+// by asynchronous 16-byte copies issued all at once, so the block waits for
+// memory once rather than once per indicator entry; each thread then sums 4
+// contexts x 2 outputs, in c order in fp32.  The grid (32 x 4 x 3 blocks on
+// 1,000 contexts, H1 = 256, 3 agents) is one wave of two blocks per SM.
+constexpr int ZT_ROWS = 32, ZT_COLS = 64;
+constexpr uint32_t ZT_SMEM = (uint32_t)(ZT_ROWS * NIND + NIND * ZT_COLS + ZT_ROWS) * 4u;
 
 __global__ void __launch_bounds__(256) k_ztable(const float *__restrict__ ind, int n_days,
                                                  const int32_t *__restrict__ slot_ke, int n_ctx,
                                                  const float *__restrict__ wind, int H1, float *__restrict__ Z)
 {
-    __shared__ __align__(16) float xs[ZT_ROWS][NIND];
-    const int j = blockIdx.y;
-    const int ctx0 = blockIdx.x * ZT_ROWS;
-    for (int i = threadIdx.x; i < ZT_ROWS * NIND; i += blockDim.x) {
-        const int r = i / NIND, c = i % NIND, ctx = ctx0 + r;
-        float x = 0.0f;
-        if (ctx < n_ctx) {
-            const int slot = ctx / n_days, day = ctx % n_days;
-            if ((c % SK2) < slot_ke[slot]) x = __ldg(ind + (int64_t)day * NIND + c);
-        }
-        xs[r][c] = x;
+    extern __shared__ __align__(16) float zsm[];
+    float *xs = zsm;                               // [ZT_ROWS][NIND]
+    float *ws = zsm + ZT_ROWS * NIND;              // [NIND][ZT_COLS]
+    int *kes = (int *)(ws + NIND * ZT_COLS);       // [ZT_ROWS] assets of each row's slot
+    const int j = blockIdx.z, n0 = blockIdx.y * ZT_COLS, ctx0 = blockIdx.x * ZT_ROWS;
+    const int tid = threadIdx.x;
+    // H1 is a multiple of 64 and the buffers are 256-byte aligned, so every
+    // copy below starts on a 16-byte boundary
+    const float *w = wind + (size_t)j * ((size_t)H1 * NIND + H1);
+    for (int i = tid; i < NIND * (ZT_COLS / 4); i += blockDim.x) {
+        const int c = i / (ZT_COLS / 4), q = i % (ZT_COLS / 4);
+        ptx::cp_async16(ptx::smem_u32(ws + c * ZT_COLS + q * 4), w + (size_t)c * H1 + n0 + q * 4);
+    }
+    for (int i = tid; i < ZT_ROWS * (NIND / 4); i += blockDim.x) {
+        const int r = i / (NIND / 4), q = i % (NIND / 4), ctx = ctx0 + r;
+        float *dst = xs + r * NIND + q * 4;
+        if (ctx < n_ctx)
+            ptx::cp_async16(ptx::smem_u32(dst), ind + (size_t)(ctx % n_days) * NIND + q * 4);
+        else
+            *(float4 *)dst = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    ptx::cp_async_commit();
+    if (tid < ZT_ROWS) kes[tid] = ctx0 + tid < n_ctx ? slot_ke[(ctx0 + tid) / n_days] : SK2;
+    ptx::cp_async_wait<0>();
+    __syncthreads();
+    // zero the assets a row's slot does not hold
+    for (int i = tid; i < ZT_ROWS * NIND; i += blockDim.x) {
+        const int r = i / NIND, c = i % NIND;
+        if (c % SK2 >= kes[r]) xs[i] = 0.0f;
     }
     __syncthreads();
-    const int n = threadIdx.x;
-    if (n >= H1) return;
-    const float *w = wind + (size_t)j * ((size_t)H1 * NIND + H1);
-    float acc[ZT_ROWS];
-#pragma unroll
-    for (int r = 0; r < ZT_ROWS; ++r) acc[r] = 0.0f;
-#pragma unroll 4
+    const int tn = tid & 31, tr = tid >> 5;        // outputs n0 + 2 tn + {0, 1}, rows 4 tr + {0 .. 3}
+    const float *xr = xs + tr * 4 * NIND;
+    float a0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, a1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 2
     for (int c = 0; c < NIND; c += 4) {
-        const float w0 = __ldg(w + (size_t)(c + 0) * H1 + n), w1 = __ldg(w + (size_t)(c + 1) * H1 + n);
-        const float w2 = __ldg(w + (size_t)(c + 2) * H1 + n), w3 = __ldg(w + (size_t)(c + 3) * H1 + n);
+        float2 wv[4];
 #pragma unroll
-        for (int r = 0; r < ZT_ROWS; ++r) {
-            const float4 x = *(const float4 *)&xs[r][c];
-            acc[r] = fmaf(x.x, w0, acc[r]);
-            acc[r] = fmaf(x.y, w1, acc[r]);
-            acc[r] = fmaf(x.z, w2, acc[r]);
-            acc[r] = fmaf(x.w, w3, acc[r]);
+        for (int k = 0; k < 4; ++k) wv[k] = *(const float2 *)(ws + (c + k) * ZT_COLS + 2 * tn);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float4 x = *(const float4 *)(xr + r * NIND + c);
+            a0[r] = fmaf(x.x, wv[0].x, a0[r]);
+            a1[r] = fmaf(x.x, wv[0].y, a1[r]);
+            a0[r] = fmaf(x.y, wv[1].x, a0[r]);
+            a1[r] = fmaf(x.y, wv[1].y, a1[r]);
+            a0[r] = fmaf(x.z, wv[2].x, a0[r]);
+            a1[r] = fmaf(x.z, wv[2].y, a1[r]);
+            a0[r] = fmaf(x.w, wv[3].x, a0[r]);
+            a1[r] = fmaf(x.w, wv[3].y, a1[r]);
         }
     }
-    const float b = __ldg(w + (size_t)H1 * NIND + n);
+    const float2 b = __ldg((const float2 *)(w + (size_t)H1 * NIND + n0 + 2 * tn));
     float *zj = Z + (size_t)j * n_ctx * H1;
 #pragma unroll
-    for (int r = 0; r < ZT_ROWS; ++r)
-        if (ctx0 + r < n_ctx) zj[(size_t)(ctx0 + r) * H1 + n] = acc[r] + b;
+    for (int r = 0; r < 4; ++r) {
+        const int ctx = ctx0 + tr * 4 + r;
+        if (ctx < n_ctx) *(float2 *)(zj + (size_t)ctx * H1 + n0 + 2 * tn) = make_float2(a0[r] + b.x, a1[r] + b.y);
+    }
 }
 
 inline uint16_t bf16_rne(float f)
@@ -1419,8 +1444,9 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     float *Z = (float *)((char *)env->zbuf + x_b);
     if (env->z_serial != e->serial || env->z_cache_off) {
         // Z[j][ctx][n] = W1_j[n, indicators] . x[ctx] + b1_j[n]
-        k_ztable<<<dim3((unsigned)ceil_div(n_ctx, ZT_ROWS), (unsigned)p.M), 256, 0, s>>>(
-            v.ind, v.n_days, env->slot_ke, n_ctx, im->wind, p.H1, Z);
+        FR_CUDA(set_max_smem_once((const void *)k_ztable, env->ctx->device));
+        k_ztable<<<dim3((unsigned)ceil_div(n_ctx, ZT_ROWS), (unsigned)(p.H1 / ZT_COLS), (unsigned)p.M), 256,
+                   ZT_SMEM, s>>>(v.ind, v.n_days, env->slot_ke, n_ctx, im->wind, p.H1, Z);
         FR_CUDA(cudaGetLastError());
         env->z_serial = e->serial;
     }
@@ -1540,10 +1566,10 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     // launches (K = T / 64, at most 4) on an internal stream of the highest
     // priority; the replay of each piece runs on `stream` on the idle SMs
     // while the next piece's launch runs, so only the last piece's replay
-    // follows the kernel.  Events order the two streams, so the rollout stays
-    // one ordered (and graph-capturable) operation on `stream`.  Every env's
-    // arithmetic is that of one launch (a rollout in pieces is the same
-    // rollout).
+    // (a short piece: T / 8 steps) follows the kernel.  Events order the
+    // two streams, so the rollout stays one ordered (and graph-capturable)
+    // operation on `stream`.  Every env's arithmetic is that of one launch
+    // (a rollout in pieces is the same rollout).
     const int K = (!packed && !want_traj && !v.auto_reset && !env->split_off) ? std::min(F2_PIECES_MAX, T / 64) : 1;
     FR_CUDA(env_time_mark(env, 0, s));
     if (K <= 1) {
@@ -1570,9 +1596,17 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     cfg2.stream = env->split_stream;
     FR_CUDA(cudaEventRecord(env->split_ev[F2_PIECES_MAX], s));
     FR_CUDA(cudaStreamWaitEvent(env->split_stream, env->split_ev[F2_PIECES_MAX], 0));
+    // the pieces' ends: the last piece is short (T / 8), so that the replay
+    // left after the kernel is short; the others share the rest evenly
+    int ends[F2_PIECES_MAX];
+    {
+        const int tl = std::max(16, T / 8), rest = T - tl;
+        for (int k = 0; k < K - 1; ++k) ends[k] = (k + 1) * rest / (K - 1);
+        ends[K - 1] = T;
+    }
     int s0 = 0;
     for (int k = 0; k < K; ++k) {
-        const int Tk = (k + 1) * T / K - s0;
+        const int Tk = ends[k] - s0;
         F2Args b = a;
         b.T = Tk;
         b.vlog = vlog + (int64_t)s0 * v.N;
@@ -1584,7 +1618,7 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     }
     s0 = 0;
     for (int k = 0; k < K; ++k) {
-        const int Tk = (k + 1) * T / K - s0;
+        const int Tk = ends[k] - s0;
         FR_CUDA(cudaStreamWaitEvent(s, env->split_ev[k], 0));
         if (k == K - 1) FR_CUDA(env_time_mark(env, 1, s));
         FR_CUDA(launch_metrics_replay(v, vlog + (int64_t)s0 * v.N, Tk, k == K - 1 ? metrics : nullptr, s,
