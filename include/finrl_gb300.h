@@ -369,10 +369,10 @@ int ensemble_act(const fr_ensemble *ens, const float *obs, int32_t n,
  * is called.  A batch whose scratch would not fit (roughly
  * (2*hidden + out)*M floats per row on the fp32 path, out*M on the
  * tensor-core paths) fails with FR_EINVAL and a message giving the largest
- * batch for this ensemble.  The first call on a device looks up the array's
- * device address and keeps it for the life of the process; make that first
- * call before any stream capture.  After cudaDeviceReset no handle of this
- * library, this call included, may be used again.  All calls share the one
+ * batch for this ensemble.  Each call looks up the array's device address
+ * on the ensemble's device (a host query that allocates nothing).  After
+ * cudaDeviceReset no handle of this library, this call included, may be
+ * used again.  All calls share the one
  * array and it keeps the last call's contents: calls whose work overlaps on
  * the GPU (different streams, or different threads) race and must be
  * serialised by the caller. */

@@ -10,8 +10,6 @@
 // file-scope device array of fixed size that every GPU loading the library
 // holds until the process exits.  It calls no cudaMalloc, cudaFree or other
 // allocating routine.
-#include <mutex>
-
 #include "fr_common.cuh"
 
 namespace fr {
@@ -24,25 +22,17 @@ constexpr uint64_t kNoAllocFloats = (16ull << 20) / sizeof(float);
 
 static __device__ __align__(256) float g_noalloc_scratch[kNoAllocFloats];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-float *g_scratch_dev[kMaxDevices] = {};
-
 // Device address of the scratch array on the current device.  In host code
-// the array's name is only a host-side stand-in, so the address has to come
-// from the runtime, once per device, with that device current.
-int scratch_address(int device, float **out)
+// the array's name is only a host-side stand-in, so the address comes from
+// the runtime, looked up on every call (a host query that allocates
+// nothing; no address is kept that a device reset could leave stale).
+int scratch_address(float **out)
 {
-    FR_CHECK(device >= 0 && device < kMaxDevices, FR_EINVAL, "ensemble_act_noalloc: device %d", device);
-    std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_scratch_dev[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
-                                                     "cudaGetSymbolAddress(scratch)");
-        g_scratch_dev[device] = (float *)p;
-    }
-    *out = g_scratch_dev[device];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
+                                                 "cudaGetSymbolAddress(scratch)");
+    *out = (float *)p;
     return FR_OK;
 }
 
@@ -71,7 +61,7 @@ extern "C" int ensemble_act_noalloc(const fr_ensemble *e, const float *obs, int3
              (unsigned long long)(kNoAllocFloats / per_row));
     FR_CUDA(cudaSetDevice(e->ctx->device));
     float *scratch = nullptr;
-    int rc = scratch_address(e->ctx->device, &scratch);
+    int rc = scratch_address(&scratch);
     if (rc) return rc;
     // Every element of both regions is written before it is read, so
     // nothing has to start at zero: y first (per-agent outputs), then the

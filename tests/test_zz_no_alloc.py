@@ -53,6 +53,28 @@ def test_noalloc_matches_ensemble_act_twice(precision):
     assert err.max() <= REL_TOL[precision]
 
 
+def test_noalloc_bf16_equals_the_large_batch_kernel():
+    """40,000 rows (313 tiles of 128, above one per SM): ensemble_act runs the
+    tiling pass and the large-batch kernel, the allocation-free call the
+    single-agent kernel; same products, order and roundings, so the actions
+    are identical."""
+    build.build()
+    ctx = fr.fr_ctx_create(0)
+    dev = torch.device("cuda:0")
+    dims = synth.STOCK_DIMS
+    params = synth.actor_params(dims, 3, seed=14)
+    ens = fr.ensemble_create(ctx, dims, params, precision=fr.PREC_BF16)
+    n = 40_000                     # 3 x 30 outputs per row: within the fixed scratch
+    assert n > ctx.sm_count * 128
+    obs = torch.from_numpy(_obs(n, dims)).to(dev)
+    ref = torch.empty(n, 30, device=dev)
+    fr.ensemble_act(ens, obs, ref)
+    got = torch.full((n, 30), float("nan"), device=dev)
+    fr.ensemble_act_noalloc(ens, obs, got)
+    torch.cuda.synchronize()
+    assert torch.equal(got, ref)
+
+
 def test_noalloc_vote_and_size_limit():
     build.build()
     ctx = fr.fr_ctx_create(0)
