@@ -742,12 +742,14 @@ def run_gpu(args):
     # state (every env live for the whole horizon)
     fr.env_reset(env)
     snap = fr.env_snapshot(env)
+    # the host state in page-locked memory, as a caller streaming states would keep it
+    host_snap = torch.frombuffer(bytearray(snap), dtype=torch.uint8).pin_memory()
     host_met = torch.empty(N, 3, dtype=torch.float64, pin_memory=True)
     e2e_times = []
     for i in range(args.warmup + max(2, args.steps // 2)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        fr.env_restore(env, snap)
+        fr.env_restore(env, host_snap)
         fr.rollout(env, ens_bf16, T, metrics=metrics)
         host_met.copy_(metrics, non_blocking=True)
         torch.cuda.synchronize()

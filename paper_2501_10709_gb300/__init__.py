@@ -260,7 +260,16 @@ def env_snapshot(env: Env) -> bytes:
     return buf.raw[:n.value]
 
 
-def env_restore(env: Env, blob: bytes):
+def env_restore(env: Env, blob):
+    """blob: the bytes env_snapshot returned, or a contiguous CPU uint8
+    tensor holding them (page-locked memory copies to the device faster)."""
+    if not isinstance(blob, bytes):
+        import torch
+        if (not isinstance(blob, torch.Tensor) or blob.device.type != "cpu" or blob.dtype != torch.uint8
+                or not blob.is_contiguous()):
+            raise ValueError("env_restore: the snapshot must be bytes or a contiguous CPU uint8 tensor")
+        _lib.check(lib().env_restore(env, C.c_void_p(blob.data_ptr()), blob.numel()), "env_restore")
+        return
     _lib.check(lib().env_restore(env, blob, len(blob)), "env_restore")
 
 

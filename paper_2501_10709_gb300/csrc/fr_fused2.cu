@@ -1096,10 +1096,12 @@ __global__ void __launch_bounds__(32 * W, 1) k_rollout_stock2(const __grid_const
 // takes ZT_ROWS contexts x ZT_COLS outputs of one agent.  The contexts' rows
 // and the tile's weight columns (read [c][n]) are copied into shared memory
 // by asynchronous 16-byte copies issued all at once, so the block waits for
-// memory once rather than once per indicator entry; each thread then sums 4
-// contexts x 2 outputs, in c order in fp32.  The grid (32 x 4 x 3 blocks on
-// 1,000 contexts, H1 = 256, 3 agents) is one wave of two blocks per SM.
-constexpr int ZT_ROWS = 32, ZT_COLS = 64;
+// memory once rather than once per indicator entry; each thread then sums
+// ZT_ROWS / 8 contexts x 2 outputs, in c order in fp32.  40 contexts per
+// block: 1,000 contexts x 256 outputs x 3 agents make 300 blocks, one wave
+// at two blocks (100 KB of shared memory each) per SM.
+constexpr int ZT_ROWS = 40, ZT_COLS = 64, ZT_RPT = ZT_ROWS / 8;
+static_assert(ZT_ROWS % 8 == 0 && ZT_ROWS <= 256, "8 warps of ZT_RPT rows; one thread per row's slot");
 constexpr uint32_t ZT_SMEM = (uint32_t)(ZT_ROWS * NIND + NIND * ZT_COLS + ZT_ROWS) * 4u;
 
 __global__ void __launch_bounds__(256) k_ztable(const float *__restrict__ ind, int n_days,
@@ -1137,16 +1139,18 @@ __global__ void __launch_bounds__(256) k_ztable(const float *__restrict__ ind, i
         if (c % SK2 >= kes[r]) xs[i] = 0.0f;
     }
     __syncthreads();
-    const int tn = tid & 31, tr = tid >> 5;        // outputs n0 + 2 tn + {0, 1}, rows 4 tr + {0 .. 3}
-    const float *xr = xs + tr * 4 * NIND;
-    float a0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, a1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    const int tn = tid & 31, tr = tid >> 5;        // outputs n0 + 2 tn + {0, 1}, rows ZT_RPT tr + {0 ..}
+    const float *xr = xs + tr * ZT_RPT * NIND;
+    float a0[ZT_RPT], a1[ZT_RPT];
+#pragma unroll
+    for (int r = 0; r < ZT_RPT; ++r) a0[r] = a1[r] = 0.0f;
 #pragma unroll 2
     for (int c = 0; c < NIND; c += 4) {
         float2 wv[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) wv[k] = *(const float2 *)(ws + (c + k) * ZT_COLS + 2 * tn);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < ZT_RPT; ++r) {
             const float4 x = *(const float4 *)(xr + r * NIND + c);
             a0[r] = fmaf(x.x, wv[0].x, a0[r]);
             a1[r] = fmaf(x.x, wv[0].y, a1[r]);
@@ -1161,8 +1165,8 @@ __global__ void __launch_bounds__(256) k_ztable(const float *__restrict__ ind, i
     const float2 b = __ldg((const float2 *)(w + (size_t)H1 * NIND + n0 + 2 * tn));
     float *zj = Z + (size_t)j * n_ctx * H1;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int ctx = ctx0 + tr * 4 + r;
+    for (int r = 0; r < ZT_RPT; ++r) {
+        const int ctx = ctx0 + tr * ZT_RPT + r;
         if (ctx < n_ctx) *(float2 *)(zj + (size_t)ctx * H1 + n0 + 2 * tn) = make_float2(a0[r] + b.x, a1[r] + b.y);
     }
 }

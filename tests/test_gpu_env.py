@@ -196,6 +196,12 @@ def test_snapshot_restore_continues_bit_exact(ctx, dev):
     assert torch.equal(m1, m2)
     with pytest.raises(fr.FrError):
         fr.env_restore(env2, blob[:-8])
+    # the same snapshot from page-locked memory restores the same state
+    env3 = _stock_env(ctx, mk, e)
+    fr.env_restore(env3, torch.frombuffer(bytearray(blob), dtype=torch.uint8).pin_memory())
+    assert fr.env_snapshot(env3) == blob
+    with pytest.raises(ValueError):
+        fr.env_restore(env3, torch.zeros(len(blob), dtype=torch.int32))
 
 
 def test_invalid_configurations_are_rejected(ctx):
