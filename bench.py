@@ -445,7 +445,8 @@ def env_step_line(fr, ctx, mk, w, dev, stream, N=1 << 20, T=4, warm=2):
     achieved = N * ENV_STEP_BYTES / dt / 1e9
     del obs, act
     env.close()
-    return {"kernel": f"k_stock_step<f32 actions> with observation out, {N} envs, {T} timed steps",
+    return {"kernel": f"k_stock_step_h<f32 actions> (two envs per warp) with observation out, {N} envs, "
+                      f"{T} timed steps",
             "bytes_per_env_step": ENV_STEP_BYTES, "us_per_step": dt * 1e6, "achieved": achieved,
             "unit": "GB/s"}
 

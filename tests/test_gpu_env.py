@@ -128,6 +128,29 @@ def test_stock_all_tiny_action_sequences(ctx, dev):
     _check_stock(res, ref, T)
 
 
+def test_stock_tiny_action_sequences_in_a_30_asset_market(ctx, dev):
+    """The same 15,625 sequences with two live assets of a 30-asset market:
+    the two-envs-per-warp step kernel (30 assets, 8 indicators, 32-bit
+    accounting) against the oracle, neighbouring envs in one warp taking
+    different fills."""
+    close = np.full((4, 30), 1000, np.int64)
+    close[:, :2] = [[310, 655], [290, 700], [333, 640], [301, 689]]
+    mk_np = SimpleNamespace(close=close, ind=np.zeros((4, 8, 30), np.float32))
+    seqs = list(itertools.product(itertools.product(range(-2, 3), repeat=2), repeat=3))
+    N, T = len(seqs), 3
+    acts = np.zeros((T, N, 30), np.int32)
+    acts[:, :, :2] = np.array(seqs, np.int32).transpose(1, 0, 2)
+    bps = np.zeros((N, 30), np.int16)
+    bps[:, :2] = [37, -64]
+    ref = oracle.stock_run(mk_np, np.full(N, 2), np.zeros(N), np.full(N, 4), bps, init_cash=1500,
+                           hmax=2, fee_bps=250, T=T, act_i32=acts)
+    mk = fr.fr_market_create(ctx, mk_np)
+    env = fr.env_create(ctx, mk, start=np.zeros(N), window=4, n_assets=np.full(N, 2), bps=bps,
+                        init_cash=1500, hmax=2, fee_bps=250)
+    res = _run_stock_steps(env, acts, fr.ACT_I32_SHARES, dev)
+    _check_stock(res, ref, T)
+
+
 @pytest.mark.parametrize("auto_reset", [False, True])
 def test_crypto_prescribed_bit_exact(ctx, dev, auto_reset):
     mk_np = synth.crypto_market(30_000, seed=9)
