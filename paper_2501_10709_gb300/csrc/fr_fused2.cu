@@ -1601,11 +1601,16 @@ int f2_rollout(fr_env *env, const fr_ensemble *e, int T, const fr_traj *traj, do
     FR_CUDA(cudaEventRecord(env->split_ev[F2_PIECES_MAX], s));
     FR_CUDA(cudaStreamWaitEvent(env->split_stream, env->split_ev[F2_PIECES_MAX], 0));
     // the pieces' ends: the last piece is short (T / 8), so that the replay
-    // left after the kernel is short; the others share the rest evenly
+    // left after the kernel is short, the one before it T / 4, and the
+    // others share the rest evenly (80, 80, 64 and 32 steps at T = 256;
+    // measured 1.720 ms per rollout against 1.747 with 74, 75, 75 and 32)
     int ends[F2_PIECES_MAX];
     {
-        const int tl = std::max(16, T / 8), rest = T - tl;
-        for (int k = 0; k < K - 1; ++k) ends[k] = (k + 1) * rest / (K - 1);
+        const int tl = std::max(16, T / 8), tp = std::max(16, T / 4);
+        const int head = K >= 3 ? T - tl - tp : T - tl;        // the evenly shared steps
+        const int nh = K >= 3 ? K - 2 : K - 1;                 // pieces sharing them
+        for (int k = 0; k < nh; ++k) ends[k] = (k + 1) * head / nh;
+        if (K >= 3) ends[K - 2] = T - tl;
         ends[K - 1] = T;
     }
     int s0 = 0;
