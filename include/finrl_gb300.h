@@ -513,13 +513,15 @@ int env_tile_packing_efficiency(const fr_env *env, float *eff);
 int env_set_table_cache(fr_env *env, int32_t on);
 
 /* Split fused stock rollouts (no counterpart in the paper).  on = 1 (the
- * default): a fused stock rollout of 64 steps or more, without tile packing,
- * trajectory outputs or auto-reset, runs as two launches of the resident
- * kernel, and the FP64 metrics replay of the first half runs beside the
- * second launch (which goes on an internal stream of the highest priority,
- * ordered with `stream` by events, so that the rollout is still one ordered
- * operation on `stream` and can be captured into a graph).  Results are
- * those of one launch, bit for bit.  on = 0: always one launch. */
+ * default): a fused stock rollout of T >= 128 steps, without tile packing,
+ * trajectory outputs or auto-reset, runs as K = min(4, T / 64) launches of
+ * the resident kernel (the last T / 8 steps, the one before it T / 4, the
+ * others sharing the rest evenly) on an internal stream of the highest
+ * priority, and the FP64 metrics replay of each piece runs on `stream`
+ * beside the next piece, so that only the last piece's replay follows the
+ * kernel.  Events order the two streams, so the rollout is still one
+ * ordered operation on `stream` and can be captured into a graph.  Results
+ * are those of one launch, bit for bit.  on = 0: always one launch. */
 int env_set_rollout_split(fr_env *env, int32_t on);
 
 /* Autotuner of the batched rollouts (no counterpart in the paper: the
